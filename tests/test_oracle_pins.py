@@ -1,0 +1,260 @@
+"""Pins for the FP64 CPU oracle: each test checks the oracle against something other
+than itself -- values printed in the paper, published known answers, closed forms,
+library routines, invariances and brute force on tiny inputs."""
+import json
+import math
+import os
+from itertools import combinations
+
+import numpy as np
+import pytest
+from scipy.spatial.distance import cdist
+from scipy.stats import chisquare
+
+import oracle
+from paper_2406_06488_gb300 import workloads
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+def _rand_pair(nx, ny, p, seed, shift=0.0):
+    spec = workloads.TwoSampleSpec(nx=nx, ny=ny, p=p, y_mean=shift, data_seed=seed)
+    return workloads.gaussian_pair(spec)
+
+
+# --------------------------------------------------------------------------- Philox
+def test_philox_known_answers():
+    kat = _load("philox4x32_10_kat.json")
+    for v in kat["vectors"]:
+        ctr = [int(h, 16) for h in v["counter"]]
+        key = [int(h, 16) for h in v["key"]]
+        want = [int(h, 16) for h in v["out"]]
+        got = oracle.philox4x32_10(ctr, key)
+        assert [int(g) for g in got] == want
+
+
+# --------------------------------------------------------------- permutation stream
+def test_stream_draw0_is_identity():
+    for nx, ny in [(1, 1), (5, 4), (100, 37)]:
+        s = oracle.perm_select(123, nx, ny, 0, 1)[0]
+        assert s[:nx].all() and not s[nx:].any()
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (1, 9), (9, 1), (4, 4), (37, 64), (300, 5)])
+def test_stream_exact_count(nx, ny):
+    sel = oracle.perm_select(7, nx, ny, 1, 500)
+    assert (sel.sum(axis=1) == nx).all()
+
+
+def test_stream_uniform_over_subsets():
+    # nx = 2, ny = 3: every one of the C(5, 2) = 10 subsets has probability 1/10.
+    nx, ny, draws = 2, 3, 40000
+    sel = oracle.perm_select(2024, nx, ny, 1, draws)
+    idx = {c: k for k, c in enumerate(combinations(range(5), 2))}
+    counts = np.zeros(len(idx))
+    for row in sel:
+        counts[idx[tuple(np.flatnonzero(row))]] += 1
+    assert chisquare(counts).pvalue > 1e-4
+
+
+def test_stream_inclusion_and_pair_frequency():
+    # E[s_i] = nx/n and E[s_i s_j] = nx(nx-1)/(n(n-1)) for a uniform nx-subset.
+    nx, ny, draws = 13, 19, 20000
+    n = nx + ny
+    sel = oracle.perm_select(99, nx, ny, 1, draws).astype(np.float64)
+    p1 = nx / n
+    se1 = math.sqrt(p1 * (1 - p1) / draws)
+    assert np.abs(sel.mean(axis=0) - p1).max() < 5 * se1
+    p2 = nx * (nx - 1) / (n * (n - 1))
+    pair = (sel.T @ sel) / draws
+    off = pair[~np.eye(n, dtype=bool)]
+    se2 = math.sqrt(p2 * (1 - p2) / draws)
+    assert np.abs(off - p2).max() < 6 * se2
+
+
+def test_stream_depends_on_seed_and_draw():
+    a = oracle.perm_select(1, 50, 50, 1, 3)
+    b = oracle.perm_select(2, 50, 50, 1, 3)
+    assert not (a == b).all()
+    assert not (a[0] == a[1]).all()
+    # counter-based: draw b does not depend on where the batch starts
+    c = oracle.perm_select(1, 50, 50, 2, 2)
+    assert (c == a[1:]).all()
+
+
+# ---------------------------------------------------------- Algorithm 2 / swapping
+def test_alg2_worked_example():
+    g = _load("alg2_worked_example.json")
+    got = oracle.alg2_indices(g["nx"], g["ny"], g["idx_p1"])
+    for key in ["i1", "i2", "i1s", "i2s", "j1", "j2", "j1s", "j2s"]:
+        assert got[key] == g[key], key
+
+
+def _rows(names, X, Y):
+    out = []
+    for nm in names:
+        src = X if nm[0] == "x" else Y
+        out.append(src[int(nm[1:]) - 1])
+    return np.stack(out)
+
+
+@pytest.mark.parametrize("stat", ["ed", "mmd"])
+def test_block_swap_equals_recomputation_on_worked_example(stat):
+    # Section 4.1: the statistic assembled from the three blocks (Algorithm 1) for the
+    # relabeling of the toy example equals the statistic recomputed on
+    # x* = (y2, x4, x5, y1, x2), y* = (x1, x3, y3, y4).
+    g = _load("alg2_worked_example.json")
+    X, Y = _rand_pair(5, 4, 3, seed=11)
+    sel = np.zeros((1, 9), dtype=bool)
+    sel[0, np.asarray(g["idx_p1"]) - 1] = True
+    via_blocks = oracle.test_blocks(X, Y, sel, stat, 1.7)[0]
+    xs = _rows(g["x_star"], X, Y).astype(np.float64)
+    ys = _rows(g["y_star"], X, Y).astype(np.float64)
+    direct = oracle.stat_direct(xs, ys, stat, 1.7)
+    assert abs(via_blocks - direct) <= 1e-13 * max(1.0, abs(direct))
+
+
+@pytest.mark.parametrize("stat", ["ed", "mmd"])
+@pytest.mark.parametrize("nx,ny,p", [(7, 11, 3), (40, 25, 6), (120, 180, 2), (1, 5, 4), (5, 1, 4)])
+def test_three_implementations_agree(stat, nx, ny, p):
+    # Algorithm 4 (recompute), Algorithm 5 (pooled matrix) and Algorithm 1
+    # (block swapping) give the same statistics on the same relabelings.
+    X, Y = _rand_pair(nx, ny, p, seed=nx * 1000 + ny, shift=0.3)
+    sel = oracle.perm_select(5, nx, ny, 0, 40)
+    a = oracle.test_direct(X, Y, sel, stat, 2.0)
+    b = oracle.test_pooled(X, Y, sel, stat, 2.0)
+    c = oracle.test_blocks(X, Y, sel, stat, 2.0)
+    scale = np.abs(a).max() + 1e-300
+    assert np.abs(a - b).max() <= 1e-12 * scale
+    assert np.abs(a - c).max() <= 1e-12 * scale
+
+
+# ------------------------------------------------------------------ statistic pins
+def test_distances_match_library_routine():
+    X, Y = _rand_pair(30, 20, 7, seed=3)
+    ref = cdist(X.astype(np.float64), Y.astype(np.float64))
+    assert np.allclose(oracle.block_matrix(X, Y, "ed"), ref, rtol=1e-13, atol=0)
+    sig = 2.5
+    kref = np.exp(-ref ** 2 / (2 * sig * sig))
+    assert np.allclose(oracle.block_matrix(X, Y, "mmd", sig), kref, rtol=1e-12, atol=0)
+
+
+def _ed_1d_closed_form(x, y):
+    # For scalars, sum_{k,l} |z_k - z_l| = 2 * sum_k (2k - m - 1) z_(k) over the sorted
+    # sample z_(1) <= ... <= z_(m); the cross sum follows from the pooled sum.
+    def all_pairs(z):
+        z = np.sort(z)
+        m = z.size
+        k = np.arange(1, m + 1, dtype=np.float64)
+        return 2.0 * np.sum((2 * k - m - 1) * z)
+    sxx, syy = all_pairs(x), all_pairs(y)
+    sww = all_pairs(np.concatenate([x, y]))
+    sxy = 0.5 * (sww - sxx - syy)
+    nx, ny = x.size, y.size
+    return 2 * sxy / (nx * ny) - sxx / nx ** 2 - syy / ny ** 2
+
+
+@pytest.mark.parametrize("nx,ny", [(300, 200), (1, 50), (64, 64)])
+def test_ed_p1_closed_form(nx, ny):
+    X, Y = _rand_pair(nx, ny, 1, seed=nx + 7 * ny, shift=0.4)
+    want = _ed_1d_closed_form(X[:, 0].astype(np.float64), Y[:, 0].astype(np.float64))
+    got = oracle.stat_direct(X, Y, "ed")
+    assert abs(got - want) <= 1e-11 * abs(want)
+
+
+def test_ed_and_mmd_nonnegative_and_symmetric():
+    for seed in range(5):
+        X, Y = _rand_pair(17 + seed, 9 + 3 * seed, 4, seed=seed, shift=0.1 * seed)
+        ed = oracle.stat_direct(X, Y, "ed")
+        mmd = oracle.stat_direct(X, Y, "mmd", 1.3)
+        assert ed >= 0 and mmd >= 0
+        assert abs(ed - oracle.stat_direct(Y, X, "ed")) <= 1e-13 * ed
+        assert abs(mmd - oracle.stat_direct(Y, X, "mmd", 1.3)) <= 1e-12 * mmd
+
+
+def test_invariances():
+    X, Y = _rand_pair(25, 31, 5, seed=8, shift=0.5)
+    X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
+    ed = oracle.stat_direct(X64, Y64, "ed")
+    mmd = oracle.stat_direct(X64, Y64, "mmd", 2.0)
+    c = np.arange(5, dtype=np.float64) - 2.0
+    assert abs(oracle.stat_direct(X64 + c, Y64 + c, "ed") - ed) <= 1e-11 * ed
+    q, _ = np.linalg.qr(np.random.default_rng(1).standard_normal((5, 5)))
+    assert abs(oracle.stat_direct(X64 @ q, Y64 @ q, "ed") - ed) <= 1e-11 * ed
+    assert abs(oracle.stat_direct(X64 @ q, Y64 @ q, "mmd", 2.0) - mmd) <= 1e-11 * mmd
+    assert abs(oracle.stat_direct(3 * X64, 3 * Y64, "ed") - 3 * ed) <= 1e-12 * ed
+    assert abs(oracle.stat_direct(3 * X64, 3 * Y64, "mmd", 6.0) - mmd) <= 1e-12 * mmd
+
+
+def test_identical_samples_give_zero():
+    X, _ = _rand_pair(30, 30, 4, seed=4)
+    D = cdist(X.astype(np.float64), X.astype(np.float64))
+    assert abs(oracle.stat_direct(X, X, "ed")) <= 1e-13 * D.mean()
+    assert abs(oracle.stat_direct(X, X, "mmd", 1.0)) <= 1e-13
+
+
+def test_pvalue_definition():
+    # Section 3.1: (1 + #{stat* >= stat_o}) / (1 + b)
+    p, nge = oracle.pvalue([1.0, 2.0, 3.0, 0.5], 2.0)
+    assert nge == 2 and p == pytest.approx(3.0 / 5.0, abs=0)
+    p, nge = oracle.pvalue([], 1.0)
+    assert nge == 0 and p == 1.0
+
+
+def test_identity_draw_reproduces_observed():
+    X, Y = _rand_pair(20, 30, 5, seed=6, shift=0.2)
+    res = oracle.permutation_test(X, Y, B=10, seed=3, stat="ed")
+    assert res["observed"] == oracle.stat_direct(X, Y, "ed")
+
+
+# ------------------------------------------------------------- exhaustive checks
+@pytest.mark.parametrize("stat", ["ed", "mmd"])
+@pytest.mark.parametrize("shift", [0.0, 0.8])
+def test_exhaustive_70(stat, shift):
+    X, Y = _rand_pair(4, 4, 3, seed=21, shift=shift)
+    sel, stats = oracle.exhaustive(X, Y, stat, 1.5)
+    assert sel.shape == (70, 8) and (sel.sum(axis=1) == 4).all()
+    # all 70 distinct, lexicographic, first one the identity
+    assert len({tuple(r) for r in sel}) == 70
+    assert sel[0, :4].all()
+    # each value equals direct recomputation
+    direct = oracle.test_direct(X, Y, sel, stat, 1.5)
+    assert np.abs(direct - stats).max() <= 1e-13 * np.abs(stats).max()
+    # complements are bitwise equal (canonical evaluation, nx == ny)
+    key = {tuple(r): s for r, s in zip(sel, stats)}
+    for r, s in zip(sel, stats):
+        assert key[tuple(~r)] == s
+    observed = stats[0]
+    p_exact = np.count_nonzero(stats >= observed) / 70.0
+    assert p_exact >= 2 / 70  # identity and its complement
+    # The Monte-Carlo estimator on draws of the stream approaches p_exact.
+    B = 100000
+    draws = oracle.perm_select(77, 4, 4, 1, B)
+    mc = np.fromiter((key[tuple(r)] for r in draws), dtype=np.float64, count=B)
+    p_mc = (1 + np.count_nonzero(mc >= observed)) / (B + 1)
+    se = math.sqrt(p_exact * (1 - p_exact) / B) + 1e-12
+    assert abs(p_mc - p_exact) <= 4 * se + 2.0 / B
+
+
+def test_permutation_mean_closed_form():
+    # Under a uniform random nx-subset s: E[s_i] = nx/n, E[s_i s_j] = nx(nx-1)/(n(n-1)).
+    # With W the pooled distance matrix, T = s'Ws, L = s'W1, S = 1'W1:
+    #   ED* = 2(L - T)/(nx ny) - T/nx^2 - (S - 2L + T)/ny^2.
+    nx, ny, p = 30, 45, 6
+    n = nx + ny
+    X, Y = _rand_pair(nx, ny, p, seed=13, shift=0.3)
+    Wm = cdist(np.vstack([X, Y]).astype(np.float64), np.vstack([X, Y]).astype(np.float64))
+    S = Wm.sum()
+    tr = np.trace(Wm)
+    ET = nx / n * tr + nx * (nx - 1) / (n * (n - 1)) * (S - tr)
+    EL = nx / n * S
+    want = 2 * (EL - ET) / (nx * ny) - ET / nx ** 2 - (S - 2 * EL + ET) / ny ** 2
+    B = 4000
+    res = oracle.permutation_test(X, Y, B=B, seed=9, stat="ed", method="blocks")
+    st = res["stats"]
+    assert abs(st.mean() - want) <= 5 * st.std() / math.sqrt(B)
