@@ -1,0 +1,147 @@
+/*
+ * ept.h -- C ABI of libept, GB300 (sm_103a) efficient permutation two-sample tests
+ * for the energy distance (ED) and the Gaussian-kernel maximum mean discrepancy
+ * (MMD), after Chaibub Neto, arXiv 2406.06488.
+ *
+ * The problem (Section 3.1): samples x (nx x p) and y (ny x p) from F_X and F_Y;
+ * test H0: F_X = F_Y with the permutation test of Algorithm 1.  The library
+ *   (1) builds the three blocks D_XX, D_YY, D_XY of Euclidean distances (or
+ *       Gaussian kernel values) once (Algorithm 1, block construction;
+ *       Algorithm 3; Appendix A.1), D_YX never stored (the memory-saving
+ *       variant described after Algorithm 1);
+ *   (2) assembles every permuted statistic from those blocks (Algorithm 1,
+ *       permutation loop; Section 4.1 "swapping"), as batched quadratic forms
+ *       s' C s over 0/1 relabeling vectors s on the tensor cores;
+ *   (3) returns the observed statistic (Eq. 1 or Eq. 2), the permuted statistics
+ *       and the permutation p-value (1 + #{stat* >= stat_o}) / (1 + B)
+ *       (Section 3.1; Algorithm 1, last line).
+ *
+ * Conventions for every entry point:
+ *   - Every function returns an ept_status; no exception or abort crosses the ABI.
+ *     On an error the outputs are left unwritten and ept_last_error() describes it.
+ *   - Array arguments are plain pointers.  When `on_device` is non-zero, every
+ *     array argument of that call (inputs and outputs, except the host-side
+ *     ept_result) is a device pointer on the context's device; otherwise every
+ *     one is a host pointer and the library copies through pinned staging memory.
+ *   - Inputs are borrowed for the duration of the call; the caller owns all
+ *     memory it passes.  Device scratch is owned by the context and reused.
+ *   - Calls on one context are serialised by a mutex; the library is safe to
+ *     call from several threads.  `stream` (a cudaStream_t, may be NULL) orders
+ *     the work after the caller's prior work on that stream; synchronous calls
+ *     return when their results are ready.
+ *   - X and Y are FP32, row-major, one sample per row (x_i in row i, Section 3).
+ */
+#ifndef EPT_H
+#define EPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EPT_ABI_VERSION 1
+
+typedef enum {
+    EPT_OK = 0,
+    EPT_EINVAL = 1,       /* bad argument: sizes, NaN/Inf data, malformed relabeling */
+    EPT_ENOMEM = 2,       /* device memory or the context's budget exhausted */
+    EPT_EBUSY = 3,        /* serving: no slot or memory for this request now */
+    EPT_ECUDA = 4,        /* a CUDA call failed (message in ept_last_error) */
+    EPT_ETIMEOUT = 5,     /* a device-side bounded wait gave up, or ept_wait timed out */
+    EPT_ECANCELLED = 6,   /* serving: the request was cancelled */
+    EPT_ENOTFOUND = 7,    /* serving: unknown ticket */
+    EPT_EUNSUPPORTED = 8  /* the device is not an sm_103 GPU, or a mode is unavailable */
+} ept_status;
+
+typedef enum {
+    EPT_STAT_ED = 0,         /* energy distance V-statistic, Eq. 1 */
+    EPT_STAT_MMD_GAUSS = 1   /* biased MMD^2, Eq. 2, k(x,y) = exp(-||x-y||^2 / (2 sigma^2)) */
+} ept_stat;
+
+typedef enum {
+    /* plain path: FP32 SIMT block build and FP32 SIMT permutation contraction,
+       one launch per phase, no CUDA graph: the comparison baseline */
+    EPT_PREC_PLAIN_FP32 = 0,
+    /* tuned path: blocks stored FP32, the contraction s' C s on tcgen05 tensor cores
+       with C split into BF16 hi + lo parts accumulated in FP32 in tensor memory */
+    EPT_PREC_SPLIT_BF16 = 1
+} ept_precision;
+
+typedef struct ept_ctx ept_ctx;
+
+typedef struct {
+    double observed;      /* statistic of the original labels, Eq. 1 / Eq. 2 */
+    double p_value;       /* (1 + n_ge) / (1 + B); 1 when B = 0 */
+    int64_t n_ge;         /* #{b : stat*_b >= observed}, compared in FP64 */
+    int64_t n_near_tie;   /* #{b : |stat*_b - observed| <= 1e-5 * |observed|} */
+    int64_t n_fixup;      /* near-duplicate pairs whose distance was recomputed in FP64 */
+    double ms_build;      /* device time of the block phase (norms .. packing) */
+    double ms_perm;       /* device time of relabeling draws + contraction + combine */
+    double ms_total;      /* device time of the whole call, copies included */
+    double ms_masks;      /* device time of the relabeling draws alone */
+    double ms_contract;   /* device time of the contraction kernel alone (CUDA events
+                             recorded on the stream it is launched on) */
+} ept_result;
+
+/* Library ABI version (EPT_ABI_VERSION of the build). */
+int ept_abi_version(void);
+
+/* Message describing the last error on the calling thread (owned by the library;
+   valid until the next call on this thread).  Never NULL. */
+const char *ept_last_error(void);
+
+/* Create a context on CUDA device `device`.  mem_budget_bytes caps the device
+   scratch the context may hold (0 = no cap).  Fails with EPT_EUNSUPPORTED if the
+   device is not compute capability 10.3.  *out receives the context. */
+ept_status ept_create(ept_ctx **out, int device, size_t mem_budget_bytes);
+
+/* Destroy a context and free its device and pinned memory.  NULL is accepted. */
+ept_status ept_destroy(ept_ctx *ctx);
+
+/* Device scratch bytes a test of this shape needs (0 on invalid sizes). */
+size_t ept_estimate_bytes(int64_t nx, int64_t ny, int64_t p, int64_t B, int prec);
+
+/* One permutation test (Algorithm 1).
+   X: nx*p floats, Y: ny*p floats (row-major).  stat: ept_stat.  sigma: Gaussian
+   bandwidth, > 0 for MMD, ignored for ED.  B >= 0 permutations; draw b (1..B) of the
+   permutation stream of `seed` (ept_perm_masks) is relabeling b.
+   perm_stats: B doubles (may be NULL), perm_stats[b-1] = statistic of draw b.
+   out: host struct, required.  Errors: EPT_EINVAL for nx < 1, ny < 1, p < 1, B < 0,
+   sigma <= 0 with MMD, non-finite data; EPT_ENOMEM over budget. */
+ept_status ept_test(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, int64_t ny,
+                    int64_t p, int on_device, int stat, double sigma, int64_t B, uint64_t seed,
+                    int prec, double *perm_stats, ept_result *out, void *stream);
+
+/* The same test on caller-given relabelings (testing, exhaustive enumeration).
+   masks: n_masks * ceil((nx+ny)/32) uint32 words, row-major by relabeling; pooled
+   row t (x rows first, then y rows) is bit t%32 of word t/32; a set bit sends the
+   row to x*.  Each relabeling must have exactly nx bits set and none at t >= nx+ny
+   (EPT_EINVAL otherwise).  The observed statistic is the identity relabeling,
+   evaluated by the same kernels.  perm_stats: n_masks doubles (may be NULL). */
+ept_status ept_test_masks(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, int64_t ny,
+                          int64_t p, int on_device, int stat, double sigma,
+                          const uint32_t *masks, int64_t n_masks, int prec,
+                          double *perm_stats, ept_result *out, void *stream);
+
+/* Draws b0 .. b0+count-1 of the permutation stream of `seed` (Algorithm 2's
+   SampleWithoutReplacement, fixed as Philox4x32-10 + Knuth's selection sampling;
+   draw 0 is the identity), generated on the GPU, written row-major as in
+   ept_test_masks: count * ceil((nx+ny)/32) words. */
+ept_status ept_perm_masks(ept_ctx *ctx, uint64_t seed, int64_t nx, int64_t ny, int64_t b0,
+                          int64_t count, uint32_t *out, int on_device, void *stream);
+
+/* Phase 1 alone (Algorithm 1, block construction; Algorithm 3): writes the pooled
+   (nx+ny) x (nx+ny) matrix [[D_XX, D_XY], [D_XY', D_YY]] (or kernel values) as the
+   library built it, expanded from its packed upper storage into a row-major FP32
+   array D_out of (nx+ny)^2 floats.  For checking the blocks; not on the hot path. */
+ept_status ept_build_blocks(ept_ctx *ctx, const float *X, int64_t nx, const float *Y,
+                            int64_t ny, int64_t p, int on_device, int stat, double sigma,
+                            int prec, float *D_out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EPT_H */

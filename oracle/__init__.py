@@ -112,6 +112,10 @@ def _load(path=None):
     lib.eo_exhaustive.argtypes = [f32p, i64, f32p, i64, i64, ctypes.c_int, ctypes.c_double, i64,
                                   u8p, f64p]
     lib.eo_exhaustive.restype = i64
+    lib.eo_stat_select_mt.argtypes = [f32p, i64, f32p, i64, i64, ctypes.c_int, ctypes.c_double, u8p]
+    lib.eo_stat_select_mt.restype = ctypes.c_double
+    lib.eo_pooled_moments.argtypes = [f32p, i64, f32p, i64, i64, ctypes.c_int, ctypes.c_double, f64p, f64p]
+    lib.eo_pooled_moments.restype = None
     lib.eo_num_threads.argtypes = []
     lib.eo_num_threads.restype = ctypes.c_int
     _lib = lib
@@ -272,6 +276,44 @@ def permutation_test(X, Y, B: int, seed: int, stat="ed", sigma: float = 1.0,
     stats = all_stats[1:]
     p, nge = pvalue(stats, observed)
     return {"observed": observed, "stats": stats, "p_value": p, "n_ge": nge}
+
+
+def stat_select(X, Y, sel, stat="ed", sigma: float = 1.0) -> float:
+    """Eq. 1 / Eq. 2 of ONE relabeling (bool [n]) recomputed from the permuted raw
+    rows (Algorithm 4), threads splitting the rows.  For sampled checks at full size."""
+    lib = _load()
+    X = _f32(X)
+    Y = _f32(Y)
+    s = np.ascontiguousarray(sel, dtype=np.uint8)
+    if s.shape != (X.shape[0] + Y.shape[0],):
+        raise ValueError("relabeling must have nx + ny entries")
+    return float(lib.eo_stat_select_mt(_ptr(X, ctypes.c_float), X.shape[0], _ptr(Y, ctypes.c_float), Y.shape[0],
+                                       X.shape[1], _stat_code(stat), float(sigma), _ptr(s, ctypes.c_uint8)))
+
+
+def pooled_moments(X, Y, stat="ed", sigma: float = 1.0):
+    """(S, trace) of the pooled matrix W of Algorithm 3 entries over all pooled pairs."""
+    lib = _load()
+    X = _f32(X)
+    Y = _f32(Y)
+    S = ctypes.c_double(0.0)
+    tr = ctypes.c_double(0.0)
+    lib.eo_pooled_moments(_ptr(X, ctypes.c_float), X.shape[0], _ptr(Y, ctypes.c_float), Y.shape[0], X.shape[1],
+                          _stat_code(stat), float(sigma), ctypes.byref(S), ctypes.byref(tr))
+    return float(S.value), float(tr.value)
+
+
+def permutation_mean(S: float, trace: float, nx: int, ny: int, stat="ed") -> float:
+    """Closed-form mean of the permutation distribution of Eq. 1 / Eq. 2 under a uniform
+    random nx-subset s of the pooled rows: with E[s_i] = nx/n and
+    E[s_i s_j] = nx(nx-1)/(n(n-1)), E[T] = nx/n tr + nx(nx-1)/(n(n-1)) (S - tr) for
+    T = s'Ws, E[L] = nx/n S for L = s'W1, and the statistic is linear in (T, L):
+    ED = 2(L - T)/(nx ny) - T/nx^2 - (S - 2L + T)/ny^2, MMD = -(that expression)."""
+    n = nx + ny
+    ET = nx / n * trace + nx * (nx - 1) / (n * (n - 1)) * (S - trace)
+    EL = nx / n * S
+    ed = 2 * (EL - ET) / (nx * ny) - ET / nx ** 2 - (S - 2 * EL + ET) / ny ** 2
+    return ed if _stat_code(stat) == STAT_ED else -ed
 
 
 def exhaustive(X, Y, stat="ed", sigma: float = 1.0, max_count: int = 1_000_000):

@@ -546,6 +546,84 @@ int64_t eo_exhaustive(const float *X, int64_t nx, const float *Y, int64_t ny, in
     return rc == 0 ? count : -1;
 }
 
+/* ------------------------------------------------------------------------- */
+/* The statistic of ONE relabeling sel[n] (Eq. 1 / Eq. 2 recomputed from the
+ * permuted raw rows, as in Algorithm 4), with the pairwise sums split over OpenMP
+ * threads by rows and the per-row sums added in row order.  For checking sampled
+ * outputs at sizes where one relabeling already costs O(n^2 p). */
+double eo_stat_select_mt(const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p, int stat,
+                         double sigma, const uint8_t *sel)
+{
+    const int64_t n = nx + ny;
+    double *w = eo_pool(X, nx, Y, ny, p);
+    int64_t *ix = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    int64_t *iy = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    double *rxx = (double *)calloc((size_t)n, sizeof(double));
+    double *ryy = (double *)calloc((size_t)n, sizeof(double));
+    double *rxy = (double *)calloc((size_t)n, sizeof(double));
+    if (!w || !ix || !iy || !rxx || !ryy || !rxy) {
+        free(w); free(ix); free(iy); free(rxx); free(ryy); free(rxy);
+        return NAN;
+    }
+    int64_t a = 0, c = 0;
+    for (int64_t t = 0; t < n; ++t) {
+        if (sel[t]) ix[a++] = t;
+        else iy[c++] = t;
+    }
+    double res = NAN;
+    if (a == nx) {
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int64_t k = 0; k < nx; ++k) {
+            double s1 = 0.0, s2 = 0.0;
+            for (int64_t l = 0; l < ny; ++l) s1 += eo_entry(w + ix[k] * p, w + iy[l] * p, p, stat, sigma);
+            for (int64_t l = 0; l < nx; ++l) s2 += eo_entry(w + ix[k] * p, w + ix[l] * p, p, stat, sigma);
+            rxy[k] = s1;
+            rxx[k] = s2;
+        }
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int64_t k = 0; k < ny; ++k) {
+            double s3 = 0.0;
+            for (int64_t l = 0; l < ny; ++l) s3 += eo_entry(w + iy[k] * p, w + iy[l] * p, p, stat, sigma);
+            ryy[k] = s3;
+        }
+        double sxx = 0.0, syy = 0.0, sxy = 0.0;
+        for (int64_t k = 0; k < nx; ++k) { sxx += rxx[k]; sxy += rxy[k]; }
+        for (int64_t k = 0; k < ny; ++k) syy += ryy[k];
+        res = eo_combine(sxx, syy, sxy, nx, ny, stat);
+    }
+    free(w); free(ix); free(iy); free(rxx); free(ryy); free(rxy);
+    return res;
+}
+
+/* Sum of all entries S = 1'W1 and trace of the pooled matrix W (distances or kernel
+ * values of Algorithm 3 over all pooled pairs), for the closed-form mean of the
+ * permutation distribution. */
+void eo_pooled_moments(const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p, int stat,
+                       double sigma, double *S_out, double *trace_out)
+{
+    const int64_t n = nx + ny;
+    double *w = eo_pool(X, nx, Y, ny, p);
+    double *rs = (double *)calloc((size_t)n, sizeof(double));
+    double *dg = (double *)calloc((size_t)n, sizeof(double));
+    if (!w || !rs || !dg) {
+        free(w); free(rs); free(dg);
+        *S_out = NAN; *trace_out = NAN;
+        return;
+    }
+#pragma omp parallel for schedule(dynamic, 8)
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t j = 0; j < n; ++j) s += eo_entry(w + i * p, w + j * p, p, stat, sigma);
+        rs[i] = s;
+        dg[i] = eo_entry(w + i * p, w + i * p, p, stat, sigma);
+    }
+    double S = 0.0, tr = 0.0;
+    for (int64_t i = 0; i < n; ++i) { S += rs[i]; tr += dg[i]; }
+    *S_out = S;
+    *trace_out = tr;
+    free(w); free(rs); free(dg);
+}
+
 int eo_num_threads(void)
 {
 #ifdef _OPENMP

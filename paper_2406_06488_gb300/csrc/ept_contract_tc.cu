@@ -1,0 +1,466 @@
+// ept_contract_tc.cu -- the permutation contraction on 5th-generation tensor cores.
+//
+// What it computes (Algorithm 1, permutation loop, rewritten as quadratic forms):
+// for relabeling column b with indicator s_b (s_b[t] = 1 iff pooled row t goes to
+// x*), the statistic needs Q_b = s_b' C s_b, where C is the packed, centred,
+// upper-scaled pooled matrix (see ept_kernels.cu, packing).  Work unit (q, m):
+// chunk q = (panel I, K-blocks [kb0, kb1)), relabeling tile m (128 columns):
+//     U[b, i]        = sum_{j in chunk} s_b[j] * C[i, j]        (tensor cores)
+//     partial[q][b]  = sum_{i in panel I} s_b[i] * U[b, i]      (epilogue)
+// and Q_b = sum_q partial[q][b] (FP64, ept_kernels.cu).
+//
+// Mapping onto tcgen05 (kind::f16, cta_group::1):
+//   A (M = 128 relabelings x K = 64 pooled columns): 0/1 values, exact in BF16,
+//     expanded from the bit masks by four producer warps straight into the
+//     128-byte-swizzled K-major shared-memory layout;
+//   B (N = 256 panel rows x K = 64): the packed C block, split C = hi + lo in BF16,
+//     loaded by TMA (two 32 KB boxes per K-block);
+//   D (128 x 256 FP32) in tensor memory: D += A * B_hi, then D += A * B_lo, so the
+//     hi and lo products accumulate in one FP32 accumulator.
+//   Two accumulators (512 TMEM columns) let the epilogue of one unit overlap the
+//   main loop of the next.  The epilogue lane owns one relabeling: it reads its
+//   256 columns, keeps those whose panel row is in x* for that relabeling, and sums.
+//
+// Roles (320 threads): warp 0 = TMA producer, warp 1 = MMA issuer (and TMEM
+// owner), warps 2-5 = epilogue, warps 6-9 = relabeling-tile producers.  Every
+// wait on an mbarrier is bounded (2 s); on expiry the kernel records an error
+// code, raises a CTA-wide abort flag, drains its own copies and MMAs (bounded
+// again), frees its tensor memory and returns.
+#include <cuda.h>
+#include <cstdio>
+#include <cstring>
+
+#include "ept_internal.cuh"
+
+namespace ept {
+
+namespace {
+
+constexpr int TC_M = 128;
+constexpr int TC_N = PANEL;                       // 256
+constexpr int STAGES = 2;
+constexpr int A_BYTES = TC_M * KB * 2;            // 16 KB
+constexpr int B_BYTES = TC_N * KB * 2;            // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + 2 * B_BYTES;
+constexpr int NUM_THREADS = 320;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*barriers*/ + 1024 /*alignment*/;
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+
+// error codes recorded in Counters::err_code
+constexpr unsigned long long ERR_WAIT_TMA = 0x101, ERR_WAIT_MMA = 0x102, ERR_WAIT_EPI = 0x103,
+                             ERR_WAIT_MASK = 0x104, ERR_DRAIN = 0x105;
+
+struct Bars {
+    unsigned long long a_full[STAGES];   // 128 producer-thread arrivals
+    unsigned long long b_full[STAGES];   // 1 arrival + TMA transaction bytes
+    unsigned long long empty[STAGES];    // 1 arrival (tcgen05.commit)
+    unsigned long long acc_full[2];      // 1 arrival (tcgen05.commit)
+    unsigned long long acc_empty[2];     // 128 epilogue-thread arrivals
+    unsigned long long drain;            // 1 arrival (final tcgen05.commit)
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: true when the phase completed; false when the CTA is aborting or
+// the wait expired (then the abort flag is raised and the error recorded).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          Counters *ctr, unsigned long long code) {
+    unsigned long long t0 = 0;
+    for (uint32_t it = 0;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 255u) {
+            if (*abort_flag) return false;
+            const unsigned long long now = gtimer();
+            if (t0 == 0) {
+                t0 = now;
+            } else if (now - t0 > WAIT_NS) {
+                *abort_flag = 1;
+                atomicCAS(&ctr->err_code, 0ull, code);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const void *tmap, int c0, int c1, int c2, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor, K-major, 128-byte swizzle: start address >> 4
+// (bits 0-13), leading byte offset 16 B (unused for swizzled K-major), stride byte
+// offset 1024 B between 8-row groups (bits 32-45), descriptor version 1 (bit 46),
+// swizzle mode 2 = 128 B (bits 61-63).
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9
+// and 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                           ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d_tmem), "l"(a), "l"(b), "r"(IDESC), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// 0/1 bits of `byte` -> eight BF16 values (1.0 = 0x3F80), element e = bit e.
+__device__ __forceinline__ uint4 expand8(uint32_t byte) {
+    uint4 v;
+    v.x = (byte & 1u) * 0x3F80u + (byte & 2u) * 0x1FC00000u;
+    v.y = ((byte >> 2) & 1u) * 0x3F80u + ((byte >> 2) & 2u) * 0x1FC00000u;
+    v.z = ((byte >> 4) & 1u) * 0x3F80u + ((byte >> 4) & 2u) * 0x1FC00000u;
+    v.w = ((byte >> 6) & 1u) * 0x3F80u + ((byte >> 6) & 2u) * 0x1FC00000u;
+    return v;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+          "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+          "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    k_contract_tc(const __grid_constant__ CUtensorMap tmap_hi, const __grid_constant__ CUtensorMap tmap_lo,
+                  const uint32_t *__restrict__ maskT, const Chunk *__restrict__ chunks, int64_t nunits,
+                  int64_t MT, int64_t Bp, int64_t NKB, float *__restrict__ partial, Counters *ctr) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    Bars *bars = reinterpret_cast<Bars *>(smem + STAGES * STAGE_BYTES);
+    volatile int *abort_flag = &bars->abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(su32(&bars->a_full[s]), 128);
+            mbar_init(su32(&bars->b_full[s]), 1);
+            mbar_init(su32(&bars->empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(su32(&bars->acc_full[a]), 1);
+            mbar_init(su32(&bars->acc_empty[a]), 128);
+        }
+        mbar_init(su32(&bars->drain), 1);
+        bars->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                         su32(&bars->tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem_base = bars->tmem_base;
+
+    if (warp == 0) {
+        // ---------------- TMA producer: packed C hi / lo blocks ----------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int armed[STAGES];   // parity of the last phase armed on each stage, -1 = none
+            for (int s2 = 0; s2 < STAGES; ++s2) armed[s2] = -1;
+            bool ok = true;
+            for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+                const Chunk ch = chunks[u / MT];
+                for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
+                    if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_TMA)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t bfull = su32(&bars->b_full[stage]);
+                    mbar_arrive_tx(bfull, 2 * B_BYTES);
+                    const int blk = (int)blk_index(ch.I, kb, NKB);
+                    uint8_t *st = smem + stage * STAGE_BYTES;
+                    tma_load_3d(su32(st + A_BYTES), &tmap_hi, 0, 0, blk, bfull);
+                    tma_load_3d(su32(st + A_BYTES + B_BYTES), &tmap_lo, 0, 0, blk, bfull);
+                    armed[stage] = (int)phase;
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                // drain: the copies armed last on each stage complete that phase of
+                // b_full; wait for it (bounded) before the CTA may exit
+                for (int s2 = 0; s2 < STAGES; ++s2) {
+                    if (armed[s2] < 0) continue;
+                    const unsigned long long t0 = gtimer();
+                    while (!mbar_try(su32(&bars->b_full[s2]), (uint32_t)armed[s2])) {
+                        if (gtimer() - t0 > WAIT_NS) {
+                            atomicCAS(&ctr->err_code, 0ull, ERR_DRAIN);
+                            break;
+                        }
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            int stage = 0, acc = 0;
+            uint32_t phase = 0, acc_phase = 0;
+            bool ok = true;
+            for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+                const Chunk ch = chunks[u / MT];
+                if (!mbar_wait(su32(&bars->acc_empty[acc]), acc_phase ^ 1u, abort_flag, ctr, ERR_WAIT_MMA)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * TC_N);
+                bool first = true;
+                for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
+                    if (!mbar_wait(su32(&bars->a_full[stage]), phase, abort_flag, ctr, ERR_WAIT_MMA) ||
+                        !mbar_wait(su32(&bars->b_full[stage]), phase, abort_flag, ctr, ERR_WAIT_MMA)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t sa = su32(smem + stage * STAGE_BYTES);
+                    const uint64_t da = desc_sw128(sa);
+                    const uint64_t dhi = desc_sw128(sa + A_BYTES);
+                    const uint64_t dlo = desc_sw128(sa + A_BYTES + B_BYTES);
+#pragma unroll
+                    for (int k = 0; k < KB / 16; ++k)
+                        mma_bf16(d_tmem, da + 2 * k, dhi + 2 * k, (first && k == 0) ? 0u : 1u);
+#pragma unroll
+                    for (int k = 0; k < KB / 16; ++k) mma_bf16(d_tmem, da + 2 * k, dlo + 2 * k, 1u);
+                    mma_commit(su32(&bars->empty[stage]));
+                    first = false;
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(su32(&bars->acc_full[acc]));
+                if (++acc == 2) {
+                    acc = 0;
+                    acc_phase ^= 1u;
+                }
+            }
+            // drain every MMA this thread issued before the CTA frees its tensor memory
+            mma_commit(su32(&bars->drain));
+            unsigned long long t0 = gtimer();
+            while (!mbar_try(su32(&bars->drain), 0)) {
+                if (gtimer() - t0 > WAIT_NS) {
+                    atomicCAS(&ctr->err_code, 0ull, ERR_DRAIN);
+                    break;
+                }
+            }
+        }
+    } else if (warp < 6) {
+        // ---------------- epilogue ----------------
+        const int quarter = warp & 3;           // TMEM lanes this warp may access
+        const int row = quarter * 32 + lane;    // relabeling within the tile
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+            const int64_t q = u / MT, m = u % MT;
+            const Chunk ch = chunks[q];
+            const int64_t b = m * TC_M + row;
+            uint32_t bits[8];
+#pragma unroll
+            for (int g = 0; g < 8; ++g) bits[g] = maskT[((int64_t)ch.I * 8 + g) * Bp + b];
+            if (!mbar_wait(su32(&bars->acc_full[acc]), acc_phase, abort_flag, ctr, ERR_WAIT_EPI)) break;
+            fence_after();
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * TC_N);
+#pragma unroll 1
+            for (int g = 0; g < 8; ++g) {
+                uint32_t v[32];
+                tmem_ld32(tbase + (uint32_t)(g * 32), v);
+                const uint32_t w = bits[g];
+#pragma unroll
+                for (int e = 0; e < 32; e += 4) {
+                    s0 += ((w >> e) & 1u) ? __uint_as_float(v[e]) : 0.f;
+                    s1 += ((w >> (e + 1)) & 1u) ? __uint_as_float(v[e + 1]) : 0.f;
+                    s2 += ((w >> (e + 2)) & 1u) ? __uint_as_float(v[e + 2]) : 0.f;
+                    s3 += ((w >> (e + 3)) & 1u) ? __uint_as_float(v[e + 3]) : 0.f;
+                }
+            }
+            fence_before();
+            mbar_arrive(su32(&bars->acc_empty[acc]));
+            partial[q * Bp + b] = (s0 + s1) + (s2 + s3);
+            if (++acc == 2) {
+                acc = 0;
+                acc_phase ^= 1u;
+            }
+        }
+    } else {
+        // ---------------- relabeling-tile producers ----------------
+        const int r = threadIdx.x - 192;   // 0..127: row of the A tile
+        int stage = 0;
+        uint32_t phase = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+            const int64_t q = u / MT, m = u % MT;
+            const Chunk ch = chunks[q];
+            const int64_t b = m * TC_M + r;
+            for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
+                const uint32_t w0 = maskT[(int64_t)(2 * kb) * Bp + b];
+                const uint32_t w1 = maskT[(int64_t)(2 * kb + 1) * Bp + b];
+                if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_MASK)) {
+                    ok = false;
+                    break;
+                }
+                uint8_t *arow = smem + stage * STAGE_BYTES + r * 128;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const uint32_t byte = ((c < 4 ? w0 : w1) >> (8 * (c & 3))) & 0xFFu;
+                    const uint4 v = expand8(byte);
+                    const uint32_t dst = su32(arow + ((c ^ (r & 7)) << 4));
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(v.x), "r"(v.y),
+                                 "r"(v.z), "r"(v.w)
+                                 : "memory");
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(su32(&bars->a_full[stage]));
+                if (++stage == STAGES) {
+                    stage = 0;
+                    phase ^= 1u;
+                }
+            }
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_contract_tc(const void *tmap_hi, const void *tmap_lo, const uint32_t *maskT,
+                               const Chunk *chunks, const Geom &g, float *partial, Counters *ctr, int num_sms,
+                               cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int64_t MT = g.Bp / TC_M;
+    const int64_t nunits = g.nchunks * MT;
+    int64_t grid = num_sms;
+    if (grid > nunits) grid = nunits;
+    if (grid < 1) return cudaSuccess;
+    CUtensorMap th, tl;
+    memcpy(&th, tmap_hi, sizeof(CUtensorMap));
+    memcpy(&tl, tmap_lo, sizeof(CUtensorMap));
+    k_contract_tc<<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(th, tl, maskT, chunks, nunits, MT, g.Bp, g.NKB,
+                                                                  partial, ctr);
+    return cudaGetLastError();
+}
+
+// cuTensorMapEncodeTiled is a driver-API call; it is looked up through the runtime
+// so that libept does not link libcuda (and still loads on machines without a GPU).
+using EncodeTiledFn = decltype(&cuTensorMapEncodeTiled);
+
+static EncodeTiledFn encode_fn(char *err, size_t errlen) {
+    static EncodeTiledFn fn = nullptr;
+    if (fn) return fn;
+    void *ptr = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !ptr) {
+        snprintf(err, errlen, "cuTensorMapEncodeTiled unavailable (%s, query %d)", cudaGetErrorString(e), (int)q);
+        return nullptr;
+    }
+    fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    return fn;
+}
+
+bool encode_block_tmaps(void *tmap_hi, void *tmap_lo, const uint16_t *Chi, const uint16_t *Clo, int64_t nblk,
+                        char *err, size_t errlen) {
+    EncodeTiledFn enc = encode_fn(err, errlen);
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)KB, (cuuint64_t)PANEL, (cuuint64_t)nblk};
+    const cuuint64_t strides[2] = {(cuuint64_t)KB * 2, (cuuint64_t)KB * 2 * PANEL};
+    const cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)PANEL, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    void *ptrs[2] = {(void *)Chi, (void *)Clo};
+    void *outs[2] = {tmap_hi, tmap_lo};
+    for (int k = 0; k < 2; ++k) {
+        CUresult r = enc((CUtensorMap *)outs[k], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ptrs[k], dims,
+                                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            snprintf(err, errlen, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+            return false;
+        }
+    }
+    return true;
+}
+
+}  // namespace ept

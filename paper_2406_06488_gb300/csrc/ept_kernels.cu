@@ -1,0 +1,658 @@
+// ept_kernels.cu -- SIMT kernels of libept: permutation stream, block build,
+// centring and packing, the plain FP32 contraction and the final combination.
+#include "ept_internal.cuh"
+
+#include <cuda_bf16.h>
+#include <cstdint>
+
+namespace ept {
+
+Geom make_geom(int64_t nx, int64_t ny, int64_t p, int64_t ncols) {
+    Geom g;
+    g.nx = nx; g.ny = ny; g.n = nx + ny; g.p = p;
+    g.n_pad = (g.n + PANEL - 1) / PANEL * PANEL;
+    g.NP = g.n_pad / PANEL;
+    g.NKB = g.n_pad / KB;
+    g.nblk = blk_off(g.NP, g.NKB);
+    g.nw = g.n_pad / 32;
+    g.ncols = ncols;
+    g.Bp = (ncols + COL_PAD - 1) / COL_PAD * COL_PAD;
+    int64_t q = 0;
+    for (int64_t I = 0; I < g.NP; ++I) {
+        const int64_t len = g.NKB - KB_PER_PANEL * I;
+        q += (len + CHUNK_KB - 1) / CHUNK_KB;
+    }
+    g.nchunks = q;
+    return g;
+}
+
+// ---------------------------------------------------------------------------
+// Permutation stream.  Philox4x32-10 (Salmon et al., SC'11): counter words 0 and 2
+// are multiplied by the two Philox multipliers; the high halves are mixed with
+// words 1 and 3 and the round key; the key advances by the two Weyl constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint32_t lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// spread the 16 low bits of v to the even bit positions of a word
+__device__ __forceinline__ uint32_t spread16(uint32_t v) {
+    v &= 0xFFFFu;
+    v = (v | (v << 8)) & 0x00FF00FFu;
+    v = (v | (v << 4)) & 0x0F0F0F0Fu;
+    v = (v | (v << 2)) & 0x33333333u;
+    v = (v | (v << 1)) & 0x55555555u;
+    return v;
+}
+
+// One warp per relabeling column c.  Draw b = b_first + c of the stream:
+// b = 0 is the identity; b >= 1 is Knuth's selection sampling (Algorithm S) over
+// the n pooled slots, slot t kept iff floor(u_t * (n - t) / 2^64) < need, with
+// u_t the 64-bit word (t mod 2) of Philox4x32-10(counter = (t/2, 0, b lo, b hi),
+// key = (seed lo, seed hi)).  The 32 lanes draw 64 consecutive slots at once; the
+// sequential dependence through `need` is resolved by a fixed-point iteration
+// over warp ballots: with every earlier decision known, a slot's decision is
+// determined, so iterating "decide from the previous guesses" reaches the unique
+// sequential solution in at most 65 rounds (almost always 1 or 2).
+__global__ void __launch_bounds__(256) k_perm_masks(uint64_t seed, int nx, int ny, int64_t b_first,
+                                                    int64_t count, int64_t ncols, int nw,
+                                                    uint32_t *__restrict__ maskT) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= ncols) return;
+    const int n = nx + ny;
+    uint32_t *col = maskT + c;
+    if (c >= count) {
+        for (int w = lane; w < nw; w += 32) col[(int64_t)w * ncols] = 0u;
+        return;
+    }
+    const int64_t b = b_first + c;
+    if (b == 0) {
+        for (int w = lane; w < nw; w += 32) {
+            const int lo = w * 32;
+            uint32_t v;
+            if (lo + 32 <= nx) v = 0xFFFFFFFFu;
+            else if (lo >= nx) v = 0u;
+            else v = (1u << (nx - lo)) - 1u;
+            col[(int64_t)w * ncols] = v;
+        }
+        return;
+    }
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    const uint32_t blo = (uint32_t)(uint64_t)b, bhi = (uint32_t)((uint64_t)b >> 32);
+    const unsigned lt = (1u << lane) - 1u;
+    int need = nx;
+    for (int base = 0; base < nw * 32; base += 64) {
+        const int t0 = base + 2 * lane, t1 = t0 + 1;
+        long long r0 = 0x7FFFFFFFFFFFFFFFLL, r1 = 0x7FFFFFFFFFFFFFFFLL;
+        if (t0 < n && need > 0) {
+            const uint4 w = philox4x32_10(make_uint4((uint32_t)(t0 >> 1), 0u, blo, bhi), key);
+            const uint64_t u0 = ((uint64_t)w.y << 32) | (uint64_t)w.x;
+            r0 = (long long)__umul64hi(u0, (uint64_t)(n - t0));
+            if (t1 < n) {
+                const uint64_t u1 = ((uint64_t)w.w << 32) | (uint64_t)w.z;
+                r1 = (long long)__umul64hi(u1, (uint64_t)(n - t1));
+            }
+        }
+        bool s0 = r0 < need, s1 = r1 < need;
+        for (int it = 0; it < 70; ++it) {
+            const unsigned m0 = __ballot_sync(0xFFFFFFFFu, s0);
+            const unsigned m1 = __ballot_sync(0xFFFFFFFFu, s1);
+            const int before = __popc(m0 & lt) + __popc(m1 & lt);
+            const bool n0 = r0 < (long long)(need - before);
+            const bool n1 = r1 < (long long)(need - before - (n0 ? 1 : 0));
+            const unsigned changed = __ballot_sync(0xFFFFFFFFu, (n0 != s0) || (n1 != s1));
+            s0 = n0;
+            s1 = n1;
+            if (changed == 0u) break;
+        }
+        const unsigned m0 = __ballot_sync(0xFFFFFFFFu, s0);
+        const unsigned m1 = __ballot_sync(0xFFFFFFFFu, s1);
+        need -= __popc(m0) + __popc(m1);
+        if (lane == 0) {
+            const int w = base >> 5;
+            col[(int64_t)w * ncols] = spread16(m0) | (spread16(m1) << 1);
+            col[(int64_t)(w + 1) * ncols] = spread16(m0 >> 16) | (spread16(m1 >> 16) << 1);
+        }
+    }
+}
+
+void launch_perm_masks(uint64_t seed, int nx, int ny, int64_t b_first, int64_t count, int64_t ncols,
+                       int nw, uint32_t *maskT, cudaStream_t s) {
+    const int warps = 8;
+    const int64_t grid = (ncols + warps - 1) / warps;
+    k_perm_masks<<<(unsigned)grid, warps * 32, 0, s>>>(seed, nx, ny, b_first, count, ncols, nw, maskT);
+}
+
+// Caller-given relabelings, row-major [m][nwu], become columns 1..n_masks of maskT;
+// column 0 is written as the identity by the caller.  A relabeling with a popcount
+// other than nx, or with bits at t >= n, is counted in ctr->bad_mask.
+__global__ void k_user_masks(const uint32_t *__restrict__ user, int64_t n_masks, int nwu, int nx, int n,
+                             int64_t ncols, int nw, uint32_t *__restrict__ maskT, Counters *ctr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t m = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (m >= n_masks) return;
+    const uint32_t *row = user + m * nwu;
+    uint32_t *col = maskT + (m + 1);
+    int cnt = 0;
+    bool bad = false;
+    for (int w = lane; w < nw; w += 32) {
+        uint32_t v = (w < nwu) ? row[w] : 0u;
+        const int lo = w * 32;
+        if (lo + 32 > n) {
+            const uint32_t valid = (lo >= n) ? 0u : ((1u << (n - lo)) - 1u);
+            if (v & ~valid) bad = true;
+            v &= valid;
+        }
+        cnt += __popc(v);
+        col[(int64_t)w * ncols] = v;
+    }
+    for (int off = 16; off; off >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, off);
+    bad = __any_sync(0xFFFFFFFFu, bad);
+    if (lane == 0 && (bad || cnt != nx)) atomicAdd(&ctr->bad_mask, 1ull);
+}
+
+void launch_user_masks(const uint32_t *user, int64_t n_masks, int nwu, int nx, int n, int64_t ncols,
+                       int nw, uint32_t *maskT, Counters *ctr, cudaStream_t s) {
+    if (n_masks <= 0) return;
+    const int warps = 8;
+    k_user_masks<<<(unsigned)((n_masks + warps - 1) / warps), warps * 32, 0, s>>>(user, n_masks, nwu, nx, n,
+                                                                                 ncols, nw, maskT, ctr);
+}
+
+// maskT columns 0..count-1 -> row-major [count][nwu]
+__global__ void k_masks_to_rows(const uint32_t *__restrict__ maskT, int64_t ncols, int nw, int64_t count,
+                                int nwu, uint32_t *__restrict__ rows) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= count * nwu) return;
+    const int64_t c = idx / nwu;
+    const int w = (int)(idx % nwu);
+    rows[idx] = maskT[(int64_t)w * ncols + c];
+}
+
+void launch_masks_to_rows(const uint32_t *maskT, int64_t ncols, int nw, int64_t count, int nwu,
+                          uint32_t *rows, cudaStream_t s) {
+    const int64_t tot = count * nwu;
+    if (tot <= 0) return;
+    k_masks_to_rows<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(maskT, ncols, nw, count, nwu, rows);
+}
+
+// ---------------------------------------------------------------------------
+__global__ void k_check_finite(const float *__restrict__ a, int64_t count, Counters *ctr) {
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+         i += (int64_t)gridDim.x * blockDim.x)
+        bad |= !isfinite(a[i]);
+    if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicAdd(&ctr->nonfinite, 1ull);
+}
+
+void launch_check_finite(const float *a, int64_t count, Counters *ctr, cudaStream_t s) {
+    if (count <= 0) return;
+    int64_t grid = (count + 255) / 256;
+    if (grid > 4096) grid = 4096;
+    k_check_finite<<<(unsigned)grid, 256, 0, s>>>(a, count, ctr);
+}
+
+__device__ __forceinline__ const float *pooled_row(const float *X, const float *Y, int64_t nx, int64_t i,
+                                                   int64_t p) {
+    return (i < nx) ? X + i * p : Y + (i - nx) * p;
+}
+
+// Squared row norms ||z_i||^2 of the pooled rows, exact products summed in FP64 and
+// rounded once to FP32 (padded rows: 0).  One warp per row.
+__global__ void k_norms(const float *__restrict__ X, const float *__restrict__ Y, int64_t nx, int64_t n,
+                        int64_t n_pad, int64_t p, float *__restrict__ norms) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n_pad) return;
+    double acc = 0.0;
+    if (i < n) {
+        const float *z = pooled_row(X, Y, nx, i, p);
+        for (int64_t k = lane; k < p; k += 32) {
+            const double v = (double)z[k];
+            acc = fma(v, v, acc);
+        }
+    }
+    for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
+    if (lane == 0) norms[i] = (float)acc;
+}
+
+void launch_norms(const float *X, const float *Y, const Geom &g, float *norms, cudaStream_t s) {
+    const int warps = 8;
+    k_norms<<<(unsigned)((g.n_pad + warps - 1) / warps), warps * 32, 0, s>>>(X, Y, g.nx, g.n, g.n_pad, g.p,
+                                                                              norms);
+}
+
+// ---------------------------------------------------------------------------
+// Block build, SIMT FP32 (Algorithm 1 block construction; Algorithm 3 entries
+// through the expansion ||x||^2 + ||y||^2 - 2 x.y).  One CTA computes half of a
+// stored 256x64 block (128 rows x 64 columns): 256 threads, 8x4 outputs each,
+// K-loop over p in steps of 16 staged through shared memory.
+// Epilogue: d2 = max(0, n_i + n_j - 2 g_ij); a pair with d2 < tau (n_i + n_j)
+// (cancellation-prone near-duplicate) is recomputed directly as sum (x - y)^2 in
+// FP64; then sqrt (ED) or exp(-d2 / (2 sigma^2)) (MMD); the diagonal is exactly 0
+// (ED) or 1 (MMD); padded rows and columns are 0.
+__device__ __forceinline__ float finish_entry(float d2, int stat, float neg_inv_2s2) {
+    return stat == 0 ? sqrtf(d2) : expf(d2 * neg_inv_2s2);
+}
+
+__global__ void __launch_bounds__(256) k_build_simt(const float *__restrict__ X, const float *__restrict__ Y,
+                                                    const float *__restrict__ norms, int64_t nx, int64_t n,
+                                                    int64_t p, int64_t NKB, int stat, float neg_inv_2s2,
+                                                    float tau, const int2 *__restrict__ blk_info,
+                                                    float *__restrict__ D, Counters *ctr) {
+    __shared__ float As[16][128 + 4];
+    __shared__ float Bs[16][64 + 4];
+    const int64_t blk = blockIdx.x;
+    const int h = blockIdx.y;
+    const int2 bi = blk_info[blk];
+    const int64_t row0 = (int64_t)bi.x * PANEL + h * 128;
+    const int64_t col0 = (int64_t)bi.y * KB;
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    float acc[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
+
+    for (int64_t k0 = 0; k0 < p; k0 += 16) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int idx = e * 256 + t, r = idx >> 4, k = idx & 15;
+            const int64_t i = row0 + r;
+            float v = 0.f;
+            if (i < n && k0 + k < p) v = pooled_row(X, Y, nx, i, p)[k0 + k];
+            As[k][r] = v;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int idx = e * 256 + t, cc = idx >> 4, k = idx & 15;
+            const int64_t j = col0 + cc;
+            float v = 0.f;
+            if (j < n && k0 + k < p) v = pooled_row(X, Y, nx, j, p)[k0 + k];
+            Bs[k][cc] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[k][ty * 8]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[k][ty * 8 + 4]);
+            const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[a][c] = fmaf(av[a], bv[c], acc[a][c]);
+        }
+        __syncthreads();
+    }
+    unsigned fixups = 0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+        const int64_t i = row0 + ty * 8 + a;
+        float out[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int64_t j = col0 + tx * 4 + c;
+            float v = 0.f;
+            if (i < n && j < n) {
+                if (i == j) {
+                    v = (stat == 0) ? 0.f : 1.f;
+                } else {
+                    const float ni = norms[i], nj = norms[j];
+                    float d2 = fmaxf(0.f, ni + nj - 2.f * acc[a][c]);
+                    if (d2 < tau * (ni + nj)) {
+                        const float *zi = pooled_row(X, Y, nx, i, p), *zj = pooled_row(X, Y, nx, j, p);
+                        double s = 0.0;
+                        for (int64_t k = 0; k < p; ++k) {
+                            const double d = (double)zi[k] - (double)zj[k];
+                            s = fma(d, d, s);
+                        }
+                        ++fixups;
+                        v = (stat == 0) ? (float)sqrt(s) : (float)exp(s * (double)neg_inv_2s2);
+                    } else {
+                        v = finish_entry(d2, stat, neg_inv_2s2);
+                    }
+                }
+            }
+            out[c] = v;
+        }
+        const int64_t off = (blk * PANEL + h * 128 + ty * 8 + a) * KB + tx * 4;
+        *reinterpret_cast<float4 *>(D + off) = make_float4(out[0], out[1], out[2], out[3]);
+    }
+    if (fixups) atomicAdd(&ctr->n_fixup, (unsigned long long)fixups);
+}
+
+void launch_build_simt(const float *X, const float *Y, const float *norms, const Geom &g, int stat,
+                       double sigma, double tau, const int2 *blk_info, float *D, Counters *ctr,
+                       cudaStream_t s) {
+    const float neg = (stat == 0) ? 0.f : (float)(-1.0 / (2.0 * sigma * sigma));
+    dim3 grid((unsigned)g.nblk, 2);
+    k_build_simt<<<grid, 256, 0, s>>>(X, Y, norms, g.nx, g.n, g.p, g.NKB, stat, neg, (float)tau, blk_info, D,
+                                     ctr);
+}
+
+// ---------------------------------------------------------------------------
+// Row and column partial sums of each stored block, for the row sums r = W 1
+// (the lower part of W is the transpose of the stored strictly-upper blocks, so
+// their column sums supply it).  Each 64-long row segment and each 32-long column
+// segment is summed in FP32 after subtracting its first entry (so the summands are
+// the O(spread) differences, not the O(mean) values), then the shift is added
+// back in FP64.  One CTA (8 warps) per block, one row per warp step, lane l owns
+// columns 2l and 2l+1.
+__global__ void __launch_bounds__(256) k_blocksums(const float *__restrict__ D, double *__restrict__ rowpart,
+                                                   double *__restrict__ colpart) {
+    __shared__ double cs[8][64];
+    const int64_t blk = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const float *base = D + blk * (int64_t)(PANEL * KB);
+    float cref0 = 0.f, cref1 = 0.f, cacc0 = 0.f, cacc1 = 0.f;
+    for (int rr = 0; rr < 32; ++rr) {
+        const int r = warp * 32 + rr;
+        const float2 v = *reinterpret_cast<const float2 *>(base + (int64_t)r * KB + 2 * lane);
+        const float ref = __shfl_sync(0xFFFFFFFFu, v.x, 0);
+        float s = (v.x - ref) + (v.y - ref);
+        for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
+        if (lane == 0) rowpart[blk * PANEL + r] = (double)s + 64.0 * (double)ref;
+        if (rr == 0) {
+            cref0 = v.x;
+            cref1 = v.y;
+        }
+        cacc0 += v.x - cref0;
+        cacc1 += v.y - cref1;
+    }
+    cs[warp][2 * lane] = (double)cacc0 + 32.0 * (double)cref0;
+    cs[warp][2 * lane + 1] = (double)cacc1 + 32.0 * (double)cref1;
+    __syncthreads();
+    if (threadIdx.x < 64) {
+        double acc = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) acc += cs[w][threadIdx.x];
+        colpart[blk * KB + threadIdx.x] = acc;
+    }
+}
+
+void launch_blocksums(const float *D, const Geom &g, double *rowpart, double *colpart, cudaStream_t s) {
+    k_blocksums<<<(unsigned)g.nblk, 256, 0, s>>>(D, rowpart, colpart);
+}
+
+// r_i = sum over the stored blocks of row i's panel (its own row segments) + sum
+// over the earlier panels J < panel(i) of column i's segments, in fixed order.
+__global__ void k_rowsum_reduce(const double *__restrict__ rowpart, const double *__restrict__ colpart,
+                                int64_t n, int64_t n_pad, int64_t NKB, double *__restrict__ r) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    if (i >= n) {
+        r[i] = 0.0;
+        return;
+    }
+    const int64_t I = i / PANEL, rr = i % PANEL;
+    double acc = 0.0;
+    for (int64_t kb = KB_PER_PANEL * I; kb < NKB; ++kb) acc += rowpart[blk_index(I, kb, NKB) * PANEL + rr];
+    const int64_t kbi = i / KB, ci = i % KB;
+    for (int64_t J = 0; J < I; ++J) acc += colpart[blk_index(J, kbi, NKB) * KB + ci];
+    r[i] = acc;
+}
+
+void launch_rowsum_reduce(const double *rowpart, const double *colpart, const Geom &g, double *r,
+                          cudaStream_t s) {
+    k_rowsum_reduce<<<(unsigned)((g.n_pad + 255) / 256), 256, 0, s>>>(rowpart, colpart, g.n, g.n_pad, g.NKB, r);
+}
+
+// Deterministic block-wide FP64 sum (fixed strided order, fixed tree).
+__device__ double block_sum_1024(double v, double *sh) {
+    const int t = threadIdx.x;
+    sh[t] = v;
+    __syncthreads();
+    for (int off = 512; off; off >>= 1) {
+        if (t < off) sh[t] += sh[t + off];
+        __syncthreads();
+    }
+    const double s = sh[0];
+    __syncthreads();
+    return s;
+}
+
+// Centring.  u_i = r_i / n - S / (2 n^2) (double centring, S = 1'W1), rounded to FP32;
+// the centred matrix is W~ = W - u 1' - 1 u'.  Whatever u is, Eq. 1 / Eq. 2 of a
+// relabeling s equal sign * (cT s'Cs + S~/ny^2) where C is W~ with its diagonal
+// lowered by kappa r~_i, r~ = W~ 1 = r - n u - (1'u) 1, S~ = 1'r~, kappa = 2 nx / n,
+// cT = (n/(nx ny))^2, sign = -1 (ED) or +1 (MMD): the linear term s'W~1 equals
+// s' diag(r~) s because s_i^2 = s_i.  dcorr_i = kappa r~_i.  Single CTA.
+__global__ void __launch_bounds__(1024) k_center(const double *__restrict__ r, int64_t n, int64_t nx,
+                                                 int64_t ny, int64_t n_pad, float *__restrict__ u,
+                                                 double *__restrict__ dcorr, StatConst *sc, int stat) {
+    __shared__ double sh[1024];
+    const int t = threadIdx.x;
+    double part = 0.0;
+    for (int64_t i = t; i < n; i += 1024) part += r[i];
+    const double S = block_sum_1024(part, sh);
+    const double fn = (double)n;
+    part = 0.0;
+    for (int64_t i = t; i < n_pad; i += 1024) {
+        float ui = 0.f;
+        if (i < n) ui = (float)(r[i] / fn - S / (2.0 * fn * fn));
+        u[i] = ui;
+        part += (double)ui;
+    }
+    const double U = block_sum_1024(part, sh);
+    const double kappa = 2.0 * (double)nx / fn;
+    part = 0.0;
+    for (int64_t i = t; i < n_pad; i += 1024) {
+        double rt = 0.0;
+        if (i < n) rt = r[i] - fn * (double)u[i] - U;
+        dcorr[i] = kappa * rt;
+        part += rt;
+    }
+    const double St = block_sum_1024(part, sh);
+    if (t == 0) {
+        const double q = fn / ((double)nx * (double)ny);
+        sc->cT = q * q;
+        sc->S_tilde = St;
+        sc->inv_ny2 = 1.0 / ((double)ny * (double)ny);
+        sc->sign = (stat == 0) ? -1.0 : 1.0;
+    }
+}
+
+void launch_center(const double *r, const Geom &g, float *u, double *dcorr, StatConst *sc, int stat,
+                   cudaStream_t s) {
+    k_center<<<1, 1024, 0, s>>>(r, g.n, g.nx, g.ny, g.n_pad, u, dcorr, sc, stat);
+}
+
+// Packing.  Stored entry (i, j), j >= 256*panel(i):
+//   j > i:  2 * ((D_ij - u_i) - u_j)      (upper triangle counted twice: s'Cs over
+//                                           the upper triangle = the full form)
+//   j = i:  D_ii - 2 u_i - dcorr_i
+//   j < i or padding: 0
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_pack(const float *__restrict__ D, const float *__restrict__ u,
+                                              const double *__restrict__ dcorr, int64_t n,
+                                              const int2 *__restrict__ blk_info, float *__restrict__ C32,
+                                              uint16_t *__restrict__ Chi, uint16_t *__restrict__ Clo) {
+    const int64_t blk = blockIdx.x;
+    const int2 bi = blk_info[blk];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t j0 = (int64_t)bi.y * KB + 2 * lane;
+    const float uj0 = (j0 < n) ? u[j0] : 0.f, uj1 = (j0 + 1 < n) ? u[j0 + 1] : 0.f;
+    for (int rr = 0; rr < 32; ++rr) {
+        const int r = warp * 32 + rr;
+        const int64_t i = (int64_t)bi.x * PANEL + r;
+        const int64_t off = (blk * PANEL + r) * KB + 2 * lane;
+        const float2 d = *reinterpret_cast<const float2 *>(D + off);
+        float w[2];
+        const float dv[2] = {d.x, d.y};
+        const float uj[2] = {uj0, uj1};
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int64_t j = j0 + e;
+            float v = 0.f;
+            if (i < n && j < n && j >= i) {
+                const float ui = u[i];
+                if (j == i) v = (float)((double)dv[e] - 2.0 * (double)ui - dcorr[i]);
+                else v = 2.f * ((dv[e] - ui) - uj[e]);
+            }
+            w[e] = v;
+        }
+        if (BF16) {
+            __nv_bfloat16 h0 = __float2bfloat16_rn(w[0]), h1 = __float2bfloat16_rn(w[1]);
+            __nv_bfloat16 l0 = __float2bfloat16_rn(w[0] - __bfloat162float(h0));
+            __nv_bfloat16 l1 = __float2bfloat16_rn(w[1] - __bfloat162float(h1));
+            const uint32_t hv = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            const uint32_t lv = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            *reinterpret_cast<uint32_t *>(Chi + off) = hv;
+            *reinterpret_cast<uint32_t *>(Clo + off) = lv;
+        } else {
+            *reinterpret_cast<float2 *>(C32 + off) = make_float2(w[0], w[1]);
+        }
+    }
+}
+
+void launch_pack_fp32(const float *D, const float *u, const double *dcorr, const Geom &g,
+                      const int2 *blk_info, float *C, cudaStream_t s) {
+    k_pack<false><<<(unsigned)g.nblk, 256, 0, s>>>(D, u, dcorr, g.n, blk_info, C, nullptr, nullptr);
+}
+
+void launch_pack_bf16(const float *D, const float *u, const double *dcorr, const Geom &g,
+                      const int2 *blk_info, uint16_t *Chi, uint16_t *Clo, cudaStream_t s) {
+    k_pack<true><<<(unsigned)g.nblk, 256, 0, s>>>(D, u, dcorr, g.n, blk_info, nullptr, Chi, Clo);
+}
+
+// ---------------------------------------------------------------------------
+// Plain FP32 contraction (the comparison path).  For work chunk q (panel I,
+// K-blocks [kb0, kb1)), half h of the panel's rows and 64 relabeling columns:
+//   U[b, i] = sum_{j in chunk} s_b[j] C[i, j]     (FP32 FMA, masks as 0/1 floats)
+//   partial[(2q + h)][b] = sum_{i in half} s_b[i] U[b, i]
+// 256 threads, each 4 relabelings x 8 rows; columns staged 32 at a time.
+__global__ void __launch_bounds__(256) k_contract_simt(const float *__restrict__ C, const uint32_t *__restrict__ maskT,
+                                                       const Chunk *__restrict__ chunks, int64_t NKB, int64_t Bp,
+                                                       float *__restrict__ partial) {
+    __shared__ float Cs[32][128 + 4];
+    __shared__ uint32_t Ms[64];
+    const int q = blockIdx.x >> 1, h = blockIdx.x & 1;
+    const Chunk ch = chunks[q];
+    const int64_t b0 = (int64_t)blockIdx.y * 64;
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    float acc[4][8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int r = 0; r < 8; ++r) acc[a][r] = 0.f;
+
+    for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
+        const float *blkp = C + blk_index(ch.I, kb, NKB) * (int64_t)(PANEL * KB) + (int64_t)h * 128 * KB;
+        for (int sub = 0; sub < 2; ++sub) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+                const int idx = e * 256 + t, r = idx >> 5, j = idx & 31;
+                Cs[j][r] = blkp[(int64_t)r * KB + sub * 32 + j];
+            }
+            if (t < 64) Ms[t] = maskT[(int64_t)(2 * kb + sub) * Bp + b0 + t];
+            __syncthreads();
+            uint32_t mw[4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a) mw[a] = Ms[ty * 4 + a];
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j) {
+                const float4 c0 = *reinterpret_cast<const float4 *>(&Cs[j][tx * 8]);
+                const float4 c1 = *reinterpret_cast<const float4 *>(&Cs[j][tx * 8 + 4]);
+                const float cv[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a) {
+                    const float f = ((mw[a] >> j) & 1u) ? 1.f : 0.f;
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) acc[a][r] = fmaf(f, cv[r], acc[a][r]);
+                }
+            }
+            __syncthreads();
+        }
+    }
+    // rows tx*8 .. tx*8+7 of this half lie in one mask word
+    const int64_t word = (int64_t)ch.I * (PANEL / 32) + h * 4 + (tx >> 2);
+    const int shift = (tx & 3) * 8;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int64_t b = b0 + ty * 4 + a;
+        const uint32_t bits = (maskT[word * Bp + b] >> shift) & 0xFFu;
+        float v = 0.f;
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v += ((bits >> r) & 1u) ? acc[a][r] : 0.f;
+        for (int off = 8; off; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
+        if (tx == 0) partial[(int64_t)(2 * q + h) * Bp + b] = v;
+    }
+}
+
+void launch_contract_simt(const float *C, const uint32_t *maskT, const Chunk *chunks, const Geom &g,
+                          float *partial, cudaStream_t s) {
+    dim3 grid((unsigned)(g.nchunks * 2), (unsigned)(g.Bp / 64));
+    k_contract_simt<<<grid, 256, 0, s>>>(C, maskT, chunks, g.NKB, g.Bp, partial);
+}
+
+// ---------------------------------------------------------------------------
+// Final combination (Algorithm 1, statistic and p-value lines): per relabeling
+// column b, Q_b = sum of its partials in fixed order (FP64), stat_b =
+// sign * (cT Q_b + S~/ny^2).  Then, against stat_0 (the identity, evaluated by the
+// same kernels), count stat_b >= stat_0 and near-ties |stat_b - stat_0| <= 1e-5 |stat_0|.
+__global__ void k_combine_stats(const float *__restrict__ partial, int64_t nparts, int64_t Bp, int64_t ncols,
+                                const StatConst *__restrict__ sc, double *__restrict__ stats) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= ncols) return;
+    double q = 0.0;
+    for (int64_t k = 0; k < nparts; ++k) q += (double)partial[k * Bp + b];
+    stats[b] = sc->sign * (sc->cT * q + sc->S_tilde * sc->inv_ny2);
+}
+
+__global__ void k_combine_count(const double *__restrict__ stats, int64_t ncols, Counters *ctr) {
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const double obs = stats[0];
+    int ge = 0, near = 0;
+    if (b >= 1 && b < ncols) {
+        const double v = stats[b];
+        ge = v >= obs;
+        near = fabs(v - obs) <= 1e-5 * fabs(obs);
+    }
+    ge = __syncthreads_count(ge);
+    near = __syncthreads_count(near);
+    if (threadIdx.x == 0) {
+        if (ge) atomicAdd(&ctr->n_ge, (unsigned long long)ge);
+        if (near) atomicAdd(&ctr->n_near, (unsigned long long)near);
+    }
+}
+
+void launch_combine(const float *partial, int64_t nparts, const Geom &g, const StatConst *sc, double *stats,
+                    Counters *ctr, cudaStream_t s) {
+    const unsigned grid = (unsigned)((g.ncols + 255) / 256);
+    k_combine_stats<<<grid, 256, 0, s>>>(partial, nparts, g.Bp, g.ncols, sc, stats);
+    k_combine_count<<<grid, 256, 0, s>>>(stats, g.ncols, ctr);
+}
+
+// ---------------------------------------------------------------------------
+// Expand the packed upper storage into a full row-major n x n matrix (checking aid).
+__global__ void k_expand(const float *__restrict__ D, int64_t n, int64_t NKB, float *__restrict__ out) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    int64_t i = idx / n, j = idx % n;
+    if (j / PANEL < i / PANEL) {
+        const int64_t tmp = i;
+        i = j;
+        j = tmp;
+    }
+    const int64_t I = i / PANEL, kb = j / KB;
+    out[idx] = D[(blk_index(I, kb, NKB) * PANEL + (i - I * PANEL)) * KB + (j - kb * KB)];
+}
+
+void launch_expand_blocks(const float *D, const Geom &g, float *out, cudaStream_t s) {
+    const int64_t tot = g.n * g.n;
+    k_expand<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(D, g.n, g.NKB, out);
+}
+
+}  // namespace ept

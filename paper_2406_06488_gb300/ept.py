@@ -1,0 +1,246 @@
+"""Thin ctypes binding of libept (include/ept.h): argument marshalling only.
+
+Every step of a test runs in libept's CUDA kernels; there is no CPU fallback.  If
+``_build/libept.so`` is missing the import of the library fails with an error
+telling how to build it.
+
+Arrays may be numpy arrays (host memory: the library copies them to the GPU) or
+CUDA torch tensors (device memory: the library works in place and returns the
+permuted statistics as a CUDA tensor).  One call may not mix the two.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libept.so")
+
+STAT = {"ed": 0, "mmd": 1}
+PREC = {"plain_fp32": 0, "split_bf16": 1}
+STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT_ECUDA", 5: "EPT_ETIMEOUT",
+          6: "EPT_ECANCELLED", 7: "EPT_ENOTFOUND", 8: "EPT_EUNSUPPORTED"}
+
+# every entry point declared in include/ept.h
+EXPORTS = ["ept_abi_version", "ept_last_error", "ept_create", "ept_destroy", "ept_estimate_bytes", "ept_test",
+           "ept_test_masks", "ept_perm_masks", "ept_build_blocks"]
+
+
+class EptError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__("%s: %s" % (STATUS.get(status, str(status)), message))
+        self.status = status
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("observed", ctypes.c_double), ("p_value", ctypes.c_double), ("n_ge", ctypes.c_int64),
+                ("n_near_tie", ctypes.c_int64), ("n_fixup", ctypes.c_int64), ("ms_build", ctypes.c_double),
+                ("ms_perm", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_masks", ctypes.c_double),
+                ("ms_contract", ctypes.c_double)]
+
+
+@dataclass
+class Result:
+    observed: float
+    p_value: float
+    n_ge: int
+    n_near_tie: int
+    n_fixup: int
+    ms_build: float
+    ms_perm: float
+    ms_total: float
+    ms_masks: float
+    ms_contract: float
+    stats: Optional[object] = field(default=None, repr=False)
+
+
+def _result(r, buf) -> "Result":
+    return Result(r.observed, r.p_value, r.n_ge, r.n_near_tie, r.n_fixup, r.ms_build, r.ms_perm, r.ms_total,
+                  r.ms_masks, r.ms_contract, buf)
+
+
+_lib = None
+
+
+def load():
+    """Load libept.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libept.so is not built (%s); run `python -c \"import __graft_entry__ as g; g.build()\"`"
+                           % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, u64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
+    lib.ept_abi_version.argtypes = []
+    lib.ept_abi_version.restype = i32
+    lib.ept_last_error.argtypes = []
+    lib.ept_last_error.restype = ctypes.c_char_p
+    lib.ept_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_size_t]
+    lib.ept_create.restype = i32
+    lib.ept_destroy.argtypes = [vp]
+    lib.ept_destroy.restype = i32
+    lib.ept_estimate_bytes.argtypes = [i64, i64, i64, i64, i32]
+    lib.ept_estimate_bytes.restype = ctypes.c_size_t
+    lib.ept_test.argtypes = [vp, vp, i64, vp, i64, i64, i32, i32, f64, i64, u64, i32, vp, ctypes.POINTER(_Result), vp]
+    lib.ept_test.restype = i32
+    lib.ept_test_masks.argtypes = [vp, vp, i64, vp, i64, i64, i32, i32, f64, vp, i64, i32, vp,
+                                   ctypes.POINTER(_Result), vp]
+    lib.ept_test_masks.restype = i32
+    lib.ept_perm_masks.argtypes = [vp, u64, i64, i64, i64, i64, vp, i32, vp]
+    lib.ept_perm_masks.restype = i32
+    lib.ept_build_blocks.argtypes = [vp, vp, i64, vp, i64, i64, i32, i32, f64, i32, vp, vp]
+    lib.ept_build_blocks.restype = i32
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise EptError(status, load().ept_last_error().decode(errors="replace"))
+
+
+def _is_torch_cuda(a) -> bool:
+    return type(a).__module__.startswith("torch") and getattr(a, "is_cuda", False)
+
+
+def _stat(stat) -> int:
+    if isinstance(stat, str):
+        return STAT[stat.lower()]
+    return int(stat)
+
+
+def _prec(prec) -> int:
+    if isinstance(prec, str):
+        return PREC[prec.lower()]
+    return int(prec)
+
+
+def estimate_bytes(nx: int, ny: int, p: int, B: int, prec="split_bf16") -> int:
+    return int(load().ept_estimate_bytes(nx, ny, p, B, _prec(prec)))
+
+
+class Context:
+    """One libept context on one CUDA device (owns its scratch memory and stream)."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0):
+        lib = load()
+        h = ctypes.c_void_p()
+        _check(lib.ept_create(ctypes.byref(h), int(device), int(budget_bytes)))
+        self._h = h
+        self.device = int(device)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            load().ept_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ helpers
+    def _arrays(self, X, Y):
+        dev = _is_torch_cuda(X)
+        if dev != _is_torch_cuda(Y):
+            raise TypeError("X and Y must both be numpy arrays or both CUDA tensors")
+        if dev:
+            import torch
+            if X.dtype != torch.float32 or Y.dtype != torch.float32:
+                raise TypeError("X and Y must be float32")
+            X = X.contiguous()
+            Y = Y.contiguous()
+            if X.dim() != 2 or Y.dim() != 2 or X.shape[1] != Y.shape[1]:
+                raise ValueError("X and Y must be 2-D with the same number of columns")
+            stream = torch.cuda.current_stream(X.device).cuda_stream
+            return X, Y, X.data_ptr(), Y.data_ptr(), 1, stream
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        if X.ndim != 2 or Y.ndim != 2 or X.shape[1] != Y.shape[1]:
+            raise ValueError("X and Y must be 2-D with the same number of columns")
+        return X, Y, X.ctypes.data, Y.ctypes.data, 0, None
+
+    def _stats_buffer(self, X, count: int, on_dev: int):
+        if count <= 0:
+            return None, None
+        if on_dev:
+            import torch
+            buf = torch.empty(count, dtype=torch.float64, device=X.device)
+            return buf, buf.data_ptr()
+        buf = np.empty(count, dtype=np.float64)
+        return buf, buf.ctypes.data
+
+    # ------------------------------------------------------------------ API
+    def test(self, X, Y, B: int, seed: int = 0, stat="ed", sigma: float = 1.0, prec="split_bf16",
+             want_stats: bool = True) -> Result:
+        """Permutation test (Algorithm 1): observed statistic, B permuted statistics
+        (draws 1..B of the stream of `seed`) and the p-value."""
+        X, Y, px, py, on_dev, stream = self._arrays(X, Y)
+        buf, pbuf = self._stats_buffer(X, B if want_stats else 0, on_dev)
+        r = _Result()
+        _check(load().ept_test(self._h, px, X.shape[0], py, Y.shape[0], X.shape[1], on_dev, _stat(stat),
+                               float(sigma), int(B), ctypes.c_uint64(seed), _prec(prec), pbuf, ctypes.byref(r),
+                               stream))
+        return _result(r, buf)
+
+    def test_masks(self, X, Y, masks, stat="ed", sigma: float = 1.0, prec="split_bf16") -> Result:
+        """The test on caller-given relabelings: masks [count, ceil(n/32)] uint32
+        (pooled row t = bit t%32 of word t//32; set = row goes to x*)."""
+        X, Y, px, py, on_dev, stream = self._arrays(X, Y)
+        if on_dev:
+            import torch
+            if not _is_torch_cuda(masks):
+                raise TypeError("masks must be a CUDA tensor when X and Y are")
+            masks = masks.contiguous()
+            count = masks.shape[0]
+            pm = masks.data_ptr()
+        else:
+            masks = np.ascontiguousarray(masks, dtype=np.uint32)
+            if masks.ndim != 2:
+                raise ValueError("masks must be 2-D")
+            count = masks.shape[0]
+            pm = masks.ctypes.data if count > 0 else None
+        n = X.shape[0] + Y.shape[0]
+        if count > 0 and masks.shape[1] != (n + 31) // 32:
+            raise ValueError("masks need ceil(n/32) = %d words per relabeling" % ((n + 31) // 32))
+        buf, pbuf = self._stats_buffer(X, count, on_dev)
+        r = _Result()
+        _check(load().ept_test_masks(self._h, px, X.shape[0], py, Y.shape[0], X.shape[1], on_dev, _stat(stat),
+                                     float(sigma), pm, int(count), _prec(prec), pbuf, ctypes.byref(r), stream))
+        return _result(r, buf)
+
+    def perm_masks(self, seed: int, nx: int, ny: int, b0: int, count: int) -> np.ndarray:
+        """Draws b0 .. b0+count-1 of the permutation stream, generated on the GPU:
+        uint32 [count, ceil((nx+ny)/32)]."""
+        nwu = (nx + ny + 31) // 32
+        out = np.zeros((count, nwu), dtype=np.uint32)
+        _check(load().ept_perm_masks(self._h, ctypes.c_uint64(seed), nx, ny, b0, count,
+                                     out.ctypes.data if count else None, 0, None))
+        return out
+
+    def build_blocks(self, X, Y, stat="ed", sigma: float = 1.0, prec="split_bf16") -> np.ndarray:
+        """Phase 1 alone: the pooled [[D_XX, D_XY], [D_XY', D_YY]] as built (FP32 numpy)."""
+        X, Y, px, py, on_dev, stream = self._arrays(X, Y)
+        n = X.shape[0] + Y.shape[0]
+        if on_dev:
+            import torch
+            out = torch.empty((n, n), dtype=torch.float32, device=X.device)
+            pout = out.data_ptr()
+        else:
+            out = np.empty((n, n), dtype=np.float32)
+            pout = out.ctypes.data
+        _check(load().ept_build_blocks(self._h, px, X.shape[0], py, Y.shape[0], X.shape[1], on_dev, _stat(stat),
+                                       float(sigma), _prec(prec), pout, stream))
+        return out

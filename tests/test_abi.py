@@ -1,0 +1,52 @@
+"""CPU checks of the C ABI: the library builds for sm_103a, loads, and exports every
+entry point include/ept.h declares (no compute call is made without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "ept.h")) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ept_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2406_06488_gb300 import _build
+    return _build.build()
+
+
+def test_header_and_binding_agree():
+    from paper_2406_06488_gb300 import ept
+    assert _declared() == sorted(ept.EXPORTS)
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    lib = ctypes.CDLL(lib_path)
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_abi_version_and_errors_without_gpu(lib_path):
+    from paper_2406_06488_gb300 import ept
+    lib = ept.load()
+    assert lib.ept_abi_version() == 1
+    # creating a context without a GPU fails cleanly with a status, not a crash
+    h = ctypes.c_void_p()
+    st = lib.ept_create(ctypes.byref(h), 0, 0)
+    assert st != 0
+    assert isinstance(lib.ept_last_error(), bytes)
+    # size estimates are pure host arithmetic
+    assert ept.estimate_bytes(2000, 3000, 1000, 10000) > 0
+    assert ept.estimate_bytes(0, 3, 1, 1) == 0
+
+
+def test_destroy_null_is_ok(lib_path):
+    from paper_2406_06488_gb300 import ept
+    assert ept.load().ept_destroy(None) == 0
