@@ -305,10 +305,10 @@ ept_status run_test(ept_ctx *c, const float *X, int64_t nx, const float *Y, int6
     // relabelings: column 0 identity, then draws 1..B or the caller's masks
     uint32_t *maskT = (uint32_t *)(A + P.off_maskT);
     if (user_masks) {
-        launch_perm_masks(seed, (int)nx, (int)ny, 0, 1, g.Bp, (int)g.nw, maskT, s);
-        launch_user_masks(dmasks, B, (int)nwu, (int)nx, (int)g.n, g.Bp, (int)g.nw, maskT, ctr, s);
+        launch_perm_masks(seed, (int)nx, (int)ny, 0, 1, g.Bp, (int)g.nw, g.comp, maskT, s);
+        launch_user_masks(dmasks, B, (int)nwu, (int)nx, (int)g.n, g.Bp, (int)g.nw, g.comp, maskT, ctr, s);
     } else {
-        launch_perm_masks(seed, (int)nx, (int)ny, 0, g.ncols, g.Bp, (int)g.nw, maskT, s);
+        launch_perm_masks(seed, (int)nx, (int)ny, 0, g.ncols, g.Bp, (int)g.nw, g.comp, maskT, s);
     }
     CK(cudaGetLastError());
     CK(cudaEventRecord(c->ev[5], s));
@@ -464,7 +464,7 @@ ept_status ept_perm_masks(ept_ctx *c, uint64_t seed, int64_t nx, int64_t ny, int
     if (st != EPT_OK) return st;
     uint32_t *maskT = (uint32_t *)c->arena;
     uint32_t *rows = on_device ? out : (uint32_t *)(c->arena + bytesT);
-    launch_perm_masks(seed, (int)nx, (int)ny, b0, count, count, (int)nw, maskT, s);
+    launch_perm_masks(seed, (int)nx, (int)ny, b0, count, count, (int)nw, false, maskT, s);
     launch_masks_to_rows(maskT, count, (int)nw, count, (int)nwu, rows, s);
     CK(cudaGetLastError());
     if (!on_device) CK(cudaMemcpyAsync(out, rows, bytesR, cudaMemcpyDeviceToHost, s));

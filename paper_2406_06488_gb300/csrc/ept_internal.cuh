@@ -15,6 +15,13 @@
 // that the 32 lanes of a warp read 32 consecutive relabelings of one word.
 // Column 0 is always the identity relabeling (the observed statistic); columns
 // 1..B are the permuted ones; padding columns are all-zero.
+//
+// Contracted group.  Eq. 1 and Eq. 2 are symmetric in x and y, so a relabeling can
+// be described by either of its two groups.  The quadratic form is taken over the
+// SMALLER group (x* when nx <= ny, otherwise y*): the sums over the larger group are
+// then differences S - 2L + T of sums over the smaller one, and using the smaller
+// group keeps the rounding errors of T small relative to the statistic when the
+// sample sizes are very unequal.  When ny < nx the stored masks mark y* (`comp`).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -33,6 +40,9 @@ struct Geom {
     int64_t ncols;   // relabeling columns actually used (identity + permuted)
     int64_t Bp;      // ncols padded to COL_PAD
     int64_t nchunks; // contraction work chunks (panel, K-block range)
+    bool comp;       // masks mark y* (ny < nx) instead of x*
+    int64_t m;       // size of the contracted group: min(nx, ny)
+    int64_t other;   // size of the other group: max(nx, ny)
 };
 
 __host__ __device__ inline int64_t blk_off(int64_t I, int64_t NKB) { return I * NKB - 2 * I * (I - 1); }
@@ -49,7 +59,7 @@ struct Chunk { int I, kb0, kb1, pad; };
 struct StatConst {
     double cT;        // (n / (nx ny))^2
     double S_tilde;   // sum of all entries of the centred matrix
-    double inv_ny2;   // 1 / ny^2
+    double inv_o2;    // 1 / other^2 (the larger group's size)
     double sign;      // -1 for ED, +1 for MMD
 };
 
@@ -64,9 +74,9 @@ struct Counters {
 
 // ---- launchers (ept_kernels.cu) ----
 void launch_perm_masks(uint64_t seed, int nx, int ny, int64_t b_first, int64_t count, int64_t ncols,
-                       int nw, uint32_t *maskT, cudaStream_t s);
+                       int nw, bool comp, uint32_t *maskT, cudaStream_t s);
 void launch_user_masks(const uint32_t *user, int64_t n_masks, int nwu, int nx, int n, int64_t ncols,
-                       int nw, uint32_t *maskT, Counters *ctr, cudaStream_t s);
+                       int nw, bool comp, uint32_t *maskT, Counters *ctr, cudaStream_t s);
 void launch_masks_to_rows(const uint32_t *maskT, int64_t ncols, int nw, int64_t count, int nwu,
                           uint32_t *rows, cudaStream_t s);
 void launch_check_finite(const float *a, int64_t count, Counters *ctr, cudaStream_t s);

@@ -23,6 +23,9 @@ Geom make_geom(int64_t nx, int64_t ny, int64_t p, int64_t ncols) {
         q += (len + CHUNK_KB - 1) / CHUNK_KB;
     }
     g.nchunks = q;
+    g.comp = ny < nx;
+    g.m = g.comp ? ny : nx;
+    g.other = g.comp ? nx : ny;
     return g;
 }
 
@@ -54,6 +57,14 @@ __device__ __forceinline__ uint32_t spread16(uint32_t v) {
     return v;
 }
 
+// bits of word w that belong to real pooled rows t < n
+__device__ __forceinline__ uint32_t valid_bits(int w, int n) {
+    const int lo = w * 32;
+    if (lo + 32 <= n) return 0xFFFFFFFFu;
+    if (lo >= n) return 0u;
+    return (1u << (n - lo)) - 1u;
+}
+
 // One warp per relabeling column c.  Draw b = b_first + c of the stream:
 // b = 0 is the identity; b >= 1 is Knuth's selection sampling (Algorithm S) over
 // the n pooled slots, slot t kept iff floor(u_t * (n - t) / 2^64) < need, with
@@ -63,8 +74,9 @@ __device__ __forceinline__ uint32_t spread16(uint32_t v) {
 // over warp ballots: with every earlier decision known, a slot's decision is
 // determined, so iterating "decide from the previous guesses" reaches the unique
 // sequential solution in at most 65 rounds (almost always 1 or 2).
+// comp: store the complement (the y* members) of every real draw.
 __global__ void __launch_bounds__(256) k_perm_masks(uint64_t seed, int nx, int ny, int64_t b_first,
-                                                    int64_t count, int64_t ncols, int nw,
+                                                    int64_t count, int64_t ncols, int nw, int comp,
                                                     uint32_t *__restrict__ maskT) {
     const int lane = threadIdx.x & 31;
     const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -78,12 +90,8 @@ __global__ void __launch_bounds__(256) k_perm_masks(uint64_t seed, int nx, int n
     const int64_t b = b_first + c;
     if (b == 0) {
         for (int w = lane; w < nw; w += 32) {
-            const int lo = w * 32;
-            uint32_t v;
-            if (lo + 32 <= nx) v = 0xFFFFFFFFu;
-            else if (lo >= nx) v = 0u;
-            else v = (1u << (nx - lo)) - 1u;
-            col[(int64_t)w * ncols] = v;
+            const uint32_t v = valid_bits(w, nx);
+            col[(int64_t)w * ncols] = comp ? (~v & valid_bits(w, n)) : v;
         }
         return;
     }
@@ -120,24 +128,31 @@ __global__ void __launch_bounds__(256) k_perm_masks(uint64_t seed, int nx, int n
         need -= __popc(m0) + __popc(m1);
         if (lane == 0) {
             const int w = base >> 5;
-            col[(int64_t)w * ncols] = spread16(m0) | (spread16(m1) << 1);
-            col[(int64_t)(w + 1) * ncols] = spread16(m0 >> 16) | (spread16(m1 >> 16) << 1);
+            uint32_t v0 = spread16(m0) | (spread16(m1) << 1);
+            uint32_t v1 = spread16(m0 >> 16) | (spread16(m1 >> 16) << 1);
+            if (comp) {
+                v0 = ~v0 & valid_bits(w, n);
+                v1 = ~v1 & valid_bits(w + 1, n);
+            }
+            col[(int64_t)w * ncols] = v0;
+            col[(int64_t)(w + 1) * ncols] = v1;
         }
     }
 }
 
 void launch_perm_masks(uint64_t seed, int nx, int ny, int64_t b_first, int64_t count, int64_t ncols,
-                       int nw, uint32_t *maskT, cudaStream_t s) {
+                       int nw, bool comp, uint32_t *maskT, cudaStream_t s) {
     const int warps = 8;
     const int64_t grid = (ncols + warps - 1) / warps;
-    k_perm_masks<<<(unsigned)grid, warps * 32, 0, s>>>(seed, nx, ny, b_first, count, ncols, nw, maskT);
+    k_perm_masks<<<(unsigned)grid, warps * 32, 0, s>>>(seed, nx, ny, b_first, count, ncols, nw, comp ? 1 : 0,
+                                                       maskT);
 }
 
 // Caller-given relabelings, row-major [m][nwu], become columns 1..n_masks of maskT;
 // column 0 is written as the identity by the caller.  A relabeling with a popcount
 // other than nx, or with bits at t >= n, is counted in ctr->bad_mask.
 __global__ void k_user_masks(const uint32_t *__restrict__ user, int64_t n_masks, int nwu, int nx, int n,
-                             int64_t ncols, int nw, uint32_t *__restrict__ maskT, Counters *ctr) {
+                             int64_t ncols, int nw, int comp, uint32_t *__restrict__ maskT, Counters *ctr) {
     const int lane = threadIdx.x & 31;
     const int64_t m = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (m >= n_masks) return;
@@ -147,14 +162,11 @@ __global__ void k_user_masks(const uint32_t *__restrict__ user, int64_t n_masks,
     bool bad = false;
     for (int w = lane; w < nw; w += 32) {
         uint32_t v = (w < nwu) ? row[w] : 0u;
-        const int lo = w * 32;
-        if (lo + 32 > n) {
-            const uint32_t valid = (lo >= n) ? 0u : ((1u << (n - lo)) - 1u);
-            if (v & ~valid) bad = true;
-            v &= valid;
-        }
+        const uint32_t valid = valid_bits(w, n);
+        if (v & ~valid) bad = true;
+        v &= valid;
         cnt += __popc(v);
-        col[(int64_t)w * ncols] = v;
+        col[(int64_t)w * ncols] = comp ? (~v & valid_bits(w, n)) : v;
     }
     for (int off = 16; off; off >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, off);
     bad = __any_sync(0xFFFFFFFFu, bad);
@@ -162,11 +174,11 @@ __global__ void k_user_masks(const uint32_t *__restrict__ user, int64_t n_masks,
 }
 
 void launch_user_masks(const uint32_t *user, int64_t n_masks, int nwu, int nx, int n, int64_t ncols,
-                       int nw, uint32_t *maskT, Counters *ctr, cudaStream_t s) {
+                       int nw, bool comp, uint32_t *maskT, Counters *ctr, cudaStream_t s) {
     if (n_masks <= 0) return;
     const int warps = 8;
     k_user_masks<<<(unsigned)((n_masks + warps - 1) / warps), warps * 32, 0, s>>>(user, n_masks, nwu, nx, n,
-                                                                                 ncols, nw, maskT, ctr);
+                                                                                 ncols, nw, comp ? 1 : 0, maskT, ctr);
 }
 
 // maskT columns 0..count-1 -> row-major [count][nwu]
@@ -345,34 +357,48 @@ void launch_build_simt(const float *X, const float *Y, const float *norms, const
 // ---------------------------------------------------------------------------
 // Row and column partial sums of each stored block, for the row sums r = W 1
 // (the lower part of W is the transpose of the stored strictly-upper blocks, so
-// their column sums supply it).  Each 64-long row segment and each 32-long column
-// segment is summed in FP32 after subtracting its first entry (so the summands are
-// the O(spread) differences, not the O(mean) values), then the shift is added
-// back in FP64.  One CTA (8 warps) per block, one row per warp step, lane l owns
-// columns 2l and 2l+1.
+// their column sums supply it).  Sums are accumulated as unevaluated FP32 pairs
+// (hi, lo) with Knuth's TwoSum, an error-free transformation (the rounding error of
+// every addition is carried in lo), then widened to FP64: about twice the FP32
+// precision at FP32 cost.  One CTA (8 warps) per block, one row per warp step,
+// lane l owns columns 2l and 2l+1.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
 __global__ void __launch_bounds__(256) k_blocksums(const float *__restrict__ D, double *__restrict__ rowpart,
                                                    double *__restrict__ colpart) {
     __shared__ double cs[8][64];
     const int64_t blk = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float *base = D + blk * (int64_t)(PANEL * KB);
-    float cref0 = 0.f, cref1 = 0.f, cacc0 = 0.f, cacc1 = 0.f;
+    float ch0 = 0.f, cl0 = 0.f, ch1 = 0.f, cl1 = 0.f;
     for (int rr = 0; rr < 32; ++rr) {
         const int r = warp * 32 + rr;
         const float2 v = *reinterpret_cast<const float2 *>(base + (int64_t)r * KB + 2 * lane);
-        const float ref = __shfl_sync(0xFFFFFFFFu, v.x, 0);
-        float s = (v.x - ref) + (v.y - ref);
-        for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
-        if (lane == 0) rowpart[blk * PANEL + r] = (double)s + 64.0 * (double)ref;
-        if (rr == 0) {
-            cref0 = v.x;
-            cref1 = v.y;
+        float s, e;
+        two_sum(v.x, v.y, s, e);
+        for (int off = 16; off; off >>= 1) {
+            const float s2 = __shfl_xor_sync(0xFFFFFFFFu, s, off);
+            const float e2 = __shfl_xor_sync(0xFFFFFFFFu, e, off);
+            float t, f;
+            two_sum(s, s2, t, f);
+            s = t;
+            e = (e + e2) + f;
         }
-        cacc0 += v.x - cref0;
-        cacc1 += v.y - cref1;
+        if (lane == 0) rowpart[blk * PANEL + r] = (double)s + (double)e;
+        float t, f;
+        two_sum(ch0, v.x, t, f);
+        ch0 = t;
+        cl0 += f;
+        two_sum(ch1, v.y, t, f);
+        ch1 = t;
+        cl1 += f;
     }
-    cs[warp][2 * lane] = (double)cacc0 + 32.0 * (double)cref0;
-    cs[warp][2 * lane + 1] = (double)cacc1 + 32.0 * (double)cref1;
+    cs[warp][2 * lane] = (double)ch0 + (double)cl0;
+    cs[warp][2 * lane + 1] = (double)ch1 + (double)cl1;
     __syncthreads();
     if (threadIdx.x < 64) {
         double acc = 0.0;
@@ -424,14 +450,19 @@ __device__ double block_sum_1024(double v, double *sh) {
 }
 
 // Centring.  u_i = r_i / n - S / (2 n^2) (double centring, S = 1'W1), rounded to FP32;
-// the centred matrix is W~ = W - u 1' - 1 u'.  Whatever u is, Eq. 1 / Eq. 2 of a
-// relabeling s equal sign * (cT s'Cs + S~/ny^2) where C is W~ with its diagonal
-// lowered by kappa r~_i, r~ = W~ 1 = r - n u - (1'u) 1, S~ = 1'r~, kappa = 2 nx / n,
-// cT = (n/(nx ny))^2, sign = -1 (ED) or +1 (MMD): the linear term s'W~1 equals
-// s' diag(r~) s because s_i^2 = s_i.  dcorr_i = kappa r~_i.  Single CTA.
+// the centred matrix is W~ = W - u 1' - 1 u'.  Let s mark the contracted group (size
+// m, the other group has size o; see ept_internal.cuh).  Writing Eq. 1 with
+// T = s'W~s, L = s'W~1 and S~ = 1'W~1 (the sums over the other group are
+// S~ - 2L + T, the cross sums L - T) gives, whatever u is,
+//     ED = -cT T + cL L - S~/o^2,  cT = (n/(nx ny))^2,  cL = 2n/(m o^2),
+// and MMD^2 (Eq. 2) is the same expression with the opposite sign.  Because
+// s_i^2 = s_i, L = s' diag(r~) s with r~ = W~ 1 = r - n u - (1'u) 1, so
+//     stat = sign * (cT s'Cs + S~/o^2),  C = W~ - kappa diag(r~),  kappa = cL/cT = 2m/n,
+// sign = -1 (ED) or +1 (MMD).  dcorr_i = kappa r~_i.  Single CTA.
 __global__ void __launch_bounds__(1024) k_center(const double *__restrict__ r, int64_t n, int64_t nx,
-                                                 int64_t ny, int64_t n_pad, float *__restrict__ u,
-                                                 double *__restrict__ dcorr, StatConst *sc, int stat) {
+                                                 int64_t ny, int64_t m, int64_t other, int64_t n_pad,
+                                                 float *__restrict__ u, double *__restrict__ dcorr, StatConst *sc,
+                                                 int stat) {
     __shared__ double sh[1024];
     const int t = threadIdx.x;
     double part = 0.0;
@@ -446,7 +477,7 @@ __global__ void __launch_bounds__(1024) k_center(const double *__restrict__ r, i
         part += (double)ui;
     }
     const double U = block_sum_1024(part, sh);
-    const double kappa = 2.0 * (double)nx / fn;
+    const double kappa = 2.0 * (double)m / fn;
     part = 0.0;
     for (int64_t i = t; i < n_pad; i += 1024) {
         double rt = 0.0;
@@ -459,14 +490,14 @@ __global__ void __launch_bounds__(1024) k_center(const double *__restrict__ r, i
         const double q = fn / ((double)nx * (double)ny);
         sc->cT = q * q;
         sc->S_tilde = St;
-        sc->inv_ny2 = 1.0 / ((double)ny * (double)ny);
+        sc->inv_o2 = 1.0 / ((double)other * (double)other);
         sc->sign = (stat == 0) ? -1.0 : 1.0;
     }
 }
 
 void launch_center(const double *r, const Geom &g, float *u, double *dcorr, StatConst *sc, int stat,
                    cudaStream_t s) {
-    k_center<<<1, 1024, 0, s>>>(r, g.n, g.nx, g.ny, g.n_pad, u, dcorr, sc, stat);
+    k_center<<<1, 1024, 0, s>>>(r, g.n, g.nx, g.ny, g.m, g.other, g.n_pad, u, dcorr, sc, stat);
 }
 
 // Packing.  Stored entry (i, j), j >= 256*panel(i):
@@ -600,7 +631,7 @@ void launch_contract_simt(const float *C, const uint32_t *maskT, const Chunk *ch
 // ---------------------------------------------------------------------------
 // Final combination (Algorithm 1, statistic and p-value lines): per relabeling
 // column b, Q_b = sum of its partials in fixed order (FP64), stat_b =
-// sign * (cT Q_b + S~/ny^2).  Then, against stat_0 (the identity, evaluated by the
+// sign * (cT Q_b + S~/o^2).  Then, against stat_0 (the identity, evaluated by the
 // same kernels), count stat_b >= stat_0 and near-ties |stat_b - stat_0| <= 1e-5 |stat_0|.
 __global__ void k_combine_stats(const float *__restrict__ partial, int64_t nparts, int64_t Bp, int64_t ncols,
                                 const StatConst *__restrict__ sc, double *__restrict__ stats) {
@@ -608,7 +639,7 @@ __global__ void k_combine_stats(const float *__restrict__ partial, int64_t npart
     if (b >= ncols) return;
     double q = 0.0;
     for (int64_t k = 0; k < nparts; ++k) q += (double)partial[k * Bp + b];
-    stats[b] = sc->sign * (sc->cT * q + sc->S_tilde * sc->inv_ny2);
+    stats[b] = sc->sign * (sc->cT * q + sc->S_tilde * sc->inv_o2);
 }
 
 __global__ void k_combine_count(const double *__restrict__ stats, int64_t ncols, Counters *ctr) {
