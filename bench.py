@@ -35,6 +35,9 @@ if ROOT not in sys.path:
 METRIC = "permuted stats/s & p99 test latency, tuned vs plain FP32 GPU at rel err ≤1e-5"
 UNIT = "permuted stats/s"
 KERNELS_PER_STEP = 12  # libept kernels launched by one ept_test call
+# dram read + write bytes of one k_contract_tc launch on the highdim workload, from the ncu
+# capture summarised in profiles/k_contract_tc_highdim_ed.md (None once the kernel changes)
+CONTRACT_TRAFFIC = {"highdim": 64.42e6}
 
 
 def _args():
@@ -47,6 +50,8 @@ def _args():
     ap.add_argument("--plain-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="run only --warmup + 1 tuned steps (a short program to capture under ncu)")
     return ap.parse_args()
 
 
@@ -214,6 +219,13 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
+    if args.profile:
+        for _ in range(args.warmup + 1):
+            step("split_bf16")
+        torch.cuda.synchronize()
+        ctx.close()
+        return 0
+
     # ---- tuned path, inputs resident on the device
     for _ in range(args.warmup):
         step("split_bf16")
@@ -314,7 +326,8 @@ def run_ours(args):
                        "ms_per_step": statistics.mean(plain_ms), "p50_ms": statistics.median(plain_ms),
                        "p99_ms": psorted[-1], "steps": args.plain_steps},
         "roofline": {"bound": "tensor", "achieved": achieved_tflops, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / peak, "traffic": None, "kernel": "k_contract_tc",
+                     "frac": achieved_tflops / peak, "traffic": CONTRACT_TRAFFIC.get(args.workload),
+                     "kernel": "k_contract_tc",
                      "peak_kind": "%s bf16 dense burst" % peak_kind,
                      "algorithmic_flops_per_launch": alg_flops,
                      "mma_flops_per_launch": mma_flops,
