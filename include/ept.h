@@ -140,6 +140,32 @@ ept_status ept_build_blocks(ept_ctx *ctx, const float *X, int64_t nx, const floa
                             int64_t ny, int64_t p, int on_device, int stat, double sigma,
                             int prec, float *D_out, void *stream);
 
+/* Size of the device array that ept_test_static uses as its only scratch memory
+   (16 MiB; it is part of the library image, so every GPU that loads libept holds it
+   until the process exits). */
+#define EPT_STATIC_SCRATCH_BYTES (16u << 20)
+
+/* ept_test_static -- the split-BF16 test of ept_test that allocates nothing.  The
+   paper has no counterpart: this is a service for callers that cannot call
+   cudaMalloc, such as a host application whose own memory pool already owns all
+   of the GPU's memory, or a latency-critical loop in which an allocation (which
+   can synchronise the whole device) is not acceptable.
+   All scratch lives in one file-scope device array of EPT_STATIC_SCRATCH_BYTES; a
+   test whose scratch does not fit (roughly nx + ny above ~1500 at B = 10^4, or more
+   permutations for smaller n) is rejected with EPT_EINVAL and a message giving the
+   bytes it needs.  The call runs on the calling thread's current device and on
+   `stream` (NULL = the legacy default stream); its first call on a device looks up
+   the array's device address (cudaGetSymbolAddress) and caches it, so make that
+   first call before any stream capture.  X, Y and perm_stats (B doubles, may be
+   NULL) are DEVICE pointers; out is a host struct (ms_total is host wall time, the
+   other timing fields are 0).  Every call reuses the same array: each call clears
+   what must start at zero, calls from one process are serialised, and calls that
+   overlap on the GPU (e.g. from several processes) race on the array.  It calls no
+   cudaMalloc, cudaFree or other allocating routine. */
+ept_status ept_test_static(const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p,
+                           int stat, double sigma, int64_t B, uint64_t seed, double *perm_stats,
+                           ept_result *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

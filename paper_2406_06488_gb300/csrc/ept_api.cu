@@ -95,6 +95,11 @@ Plan make_plan(const Geom &g, int prec, bool host_in, int64_t n_user_masks) {
 
 }  // namespace
 
+namespace ept {
+// lets other translation units of the library report an error message
+void set_last_error(const char *msg) { g_err = msg; }
+}  // namespace ept
+
 struct ept_ctx {
     int device = 0;
     int num_sms = 0;

@@ -27,7 +27,7 @@ STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT
 
 # every entry point declared in include/ept.h
 EXPORTS = ["ept_abi_version", "ept_last_error", "ept_create", "ept_destroy", "ept_estimate_bytes", "ept_test",
-           "ept_test_masks", "ept_perm_masks", "ept_build_blocks"]
+           "ept_test_masks", "ept_perm_masks", "ept_build_blocks", "ept_test_static"]
 
 
 class EptError(RuntimeError):
@@ -95,6 +95,8 @@ def load():
     lib.ept_perm_masks.restype = i32
     lib.ept_build_blocks.argtypes = [vp, vp, i64, vp, i64, i64, i32, i32, f64, i32, vp, vp]
     lib.ept_build_blocks.restype = i32
+    lib.ept_test_static.argtypes = [vp, i64, vp, i64, i64, i32, f64, i64, u64, vp, ctypes.POINTER(_Result), vp]
+    lib.ept_test_static.restype = i32
     _lib = lib
     return lib
 
