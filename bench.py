@@ -34,16 +34,16 @@ if ROOT not in sys.path:
 
 METRIC = "permuted stats/s & p99 test latency, tuned vs plain FP32 GPU at rel err ≤1e-5"
 UNIT = "permuted stats/s"
-KERNELS_PER_STEP = 12  # libept kernels launched by one ept_test call
+KERNELS_PER_STEP = 13  # libept kernels launched by one ept_test call (split-BF16 path)
 # dram read + write bytes of one k_contract_tc launch on the highdim workload, from the ncu
 # capture summarised in profiles/k_contract_tc_highdim_ed.md (None once the kernel changes)
-CONTRACT_TRAFFIC = {"highdim": 64.42e6}
+CONTRACT_TRAFFIC = {"highdim": 64.42e6}  # k_contract_tc unchanged since that capture
 
 
 def _args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="highdim", choices=["highdim", "mmd", "small"])

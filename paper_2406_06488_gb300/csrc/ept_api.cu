@@ -48,7 +48,8 @@ struct Plan {
     int64_t n_user_masks;
     size_t off_X, off_Y, off_norms, off_blkinfo, off_chunks, off_D, off_rowpart, off_colpart, off_r, off_u,
         off_dcorr, off_sc, off_hi, off_lo, off_maskT, off_umask, off_partial, off_stats, off_ctr, total;
-    int64_t nparts;
+    size_t off_zh, off_zl, off_tiles, off_Spart, off_Upart, off_Stpart;
+    int64_t nparts, p_pad, ntiles;
 };
 
 Plan make_plan(const Geom &g, int prec, bool host_in, int64_t n_user_masks) {
@@ -76,11 +77,20 @@ Plan make_plan(const Geom &g, int prec, bool host_in, int64_t n_user_masks) {
     P.off_u = take((size_t)g.n_pad * 4);
     P.off_dcorr = take((size_t)g.n_pad * 8);
     P.off_sc = take(sizeof(StatConst));
+    P.off_Spart = take((size_t)g.NP * 8);
+    P.off_Upart = take((size_t)g.NP * 8);
+    P.off_Stpart = take((size_t)g.NP * 8);
+    P.p_pad = (g.p + BUILD_KB - 1) / BUILD_KB * BUILD_KB;
+    P.ntiles = g.NP * (g.NP + 1);
     if (prec == EPT_PREC_SPLIT_BF16) {
         P.off_hi = take(blk_elems * 2);
         P.off_lo = take(blk_elems * 2);
+        P.off_zh = take((size_t)g.n_pad * P.p_pad * 2);
+        P.off_zl = take((size_t)g.n_pad * P.p_pad * 2);
+        P.off_tiles = take((size_t)P.ntiles * sizeof(int4));
     } else {
         P.off_hi = P.off_lo = 0;
+        P.off_zh = P.off_zl = P.off_tiles = 0;
     }
     P.off_maskT = take((size_t)g.nw * g.Bp * 4);
     const int64_t nwu = (g.n + 31) / 32;
@@ -105,6 +115,8 @@ struct ept_ctx {
     int num_sms = 0;
     size_t budget = 0;
     cudaStream_t stream = nullptr;
+    cudaStream_t side = nullptr;        // relabeling draws run here, beside the block build
+    cudaEvent_t ev_side[3] = {};        // fork, draws start, draws done
     std::mutex mu;
     uint8_t *arena = nullptr;
     size_t arena_cap = 0;
@@ -113,6 +125,7 @@ struct ept_ctx {
     cudaEvent_t ev[7] = {};
     std::vector<int2> h_blkinfo;
     std::vector<Chunk> h_chunks;
+    std::vector<int4> h_tiles;
 };
 
 namespace {
@@ -202,6 +215,10 @@ ept_status validate(int64_t nx, int64_t ny, int64_t p, int stat, double sigma, i
 void fill_tables(ept_ctx *c, const Geom &g) {
     c->h_blkinfo.resize((size_t)g.nblk);
     c->h_chunks.clear();
+    c->h_tiles.clear();
+    for (int64_t I = 0; I < g.NP; ++I)
+        for (int64_t J = I; J < g.NP; ++J)
+            for (int h = 0; h < 2; ++h) c->h_tiles.push_back(make_int4((int)I, h, (int)J, 0));
     for (int64_t I = 0; I < g.NP; ++I) {
         for (int64_t kb = KB_PER_PANEL * I; kb < g.NKB; ++kb)
             c->h_blkinfo[(size_t)blk_index(I, kb, g.NKB)] = make_int2((int)I, (int)kb);
@@ -229,17 +246,29 @@ ept_status run_blocks(ept_ctx *c, const Plan &P, const float *X, const float *Y,
     Counters *ctr = (Counters *)(A + P.off_ctr);
     launch_check_finite(X, g.nx * g.p, ctr, s);
     launch_check_finite(Y, g.ny * g.p, ctr, s);
-    launch_norms(X, Y, g, norms, s);
-    launch_build_simt(X, Y, norms, g, stat, sigma, NEAR_DUP_TAU, blkinfo, D, ctr, s);
+    if (P.prec == EPT_PREC_SPLIT_BF16) {
+        uint16_t *zh = (uint16_t *)(A + P.off_zh), *zl = (uint16_t *)(A + P.off_zl);
+        launch_split_rows(X, Y, g, P.p_pad, zh, zl, norms, ctr, s);
+        alignas(64) CUtensorMap tm[4];
+        char emsg[160];
+        if (!encode_rows_tmaps(tm, zh, zl, g.n_pad, P.p_pad, emsg, sizeof(emsg))) return fail(EPT_ECUDA, "%s", emsg);
+        CK(launch_build_tc(tm, (const int4 *)(A + P.off_tiles), (int)P.ntiles, P.p_pad, norms, X, Y, g, stat, sigma,
+                           NEAR_DUP_TAU, D, ctr, c->num_sms, s));
+    } else {
+        launch_norms(X, Y, g, norms, s);
+        launch_build_simt(X, Y, norms, g, stat, sigma, NEAR_DUP_TAU, blkinfo, D, ctr, s);
+    }
     CK(cudaGetLastError());
     if (!pack) return EPT_OK;
     double *rowpart = (double *)(A + P.off_rowpart), *colpart = (double *)(A + P.off_colpart);
     double *r = (double *)(A + P.off_r), *dcorr = (double *)(A + P.off_dcorr);
     float *u = (float *)(A + P.off_u);
     StatConst *sc = (StatConst *)(A + P.off_sc);
+    double *Spart = (double *)(A + P.off_Spart), *Upart = (double *)(A + P.off_Upart);
+    double *Stpart = (double *)(A + P.off_Stpart);
     launch_blocksums(D, g, rowpart, colpart, s);
-    launch_rowsum_reduce(rowpart, colpart, g, r, s);
-    launch_center(r, g, u, dcorr, sc, stat, s);
+    launch_rowsum_reduce(rowpart, colpart, g, r, Spart, s);
+    launch_center(r, Spart, g, u, dcorr, Upart, Stpart, sc, stat, s);
     if (P.prec == EPT_PREC_SPLIT_BF16)
         launch_pack_bf16(D, u, dcorr, g, blkinfo, (uint16_t *)(A + P.off_hi), (uint16_t *)(A + P.off_lo), s);
     else
@@ -269,7 +298,8 @@ ept_status run_test(ept_ctx *c, const float *X, int64_t nx, const float *Y, int6
     const int64_t nwu = (g.n + 31) / 32;
     // pinned staging: tables + (host inputs) + results
     const size_t tab_bytes = align_up(c->h_blkinfo.size() * sizeof(int2), 256) +
-                             align_up(c->h_chunks.size() * sizeof(Chunk), 256);
+                             align_up(c->h_chunks.size() * sizeof(Chunk), 256) +
+                             align_up(c->h_tiles.size() * sizeof(int4), 256);
     const size_t xin = align_up((size_t)nx * p * 4, 256), yin = align_up((size_t)ny * p * 4, 256);
     const size_t in_bytes = host_in ? xin + yin + (user_masks ? align_up((size_t)B * nwu * 4, 256) : 0) : 0;
     const size_t res_bytes = align_up((size_t)g.ncols * 8, 256) + align_up(sizeof(Counters), 256);
@@ -300,22 +330,34 @@ ept_status run_test(ept_ctx *c, const float *X, int64_t nx, const float *Y, int6
     CK(cudaMemcpyAsync(A + P.off_blkinfo, pin_tab, c->h_blkinfo.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
     CK(cudaMemcpyAsync(A + P.off_chunks, pin_tab + align_up(c->h_blkinfo.size() * sizeof(int2), 256),
                        c->h_chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice, s));
+    if (prec == EPT_PREC_SPLIT_BF16) {
+        uint8_t *tsrc = pin_tab + align_up(c->h_blkinfo.size() * sizeof(int2), 256) +
+                        align_up(c->h_chunks.size() * sizeof(Chunk), 256);
+        memcpy(tsrc, c->h_tiles.data(), c->h_tiles.size() * sizeof(int4));
+        CK(cudaMemcpyAsync(A + P.off_tiles, tsrc, c->h_tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+    }
     Counters *ctr = (Counters *)(A + P.off_ctr);
     CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
     CK(cudaEventRecord(c->ev[1], s));
 
-    if ((st = run_blocks(c, P, dX, dY, stat, sigma, true, s)) != EPT_OK) return st;
-    CK(cudaEventRecord(c->ev[2], s));
-
-    // relabelings: column 0 identity, then draws 1..B or the caller's masks
+    // relabelings on the side stream, beside the block build: column 0 identity, then
+    // draws 1..B or the caller's masks (they need only the uploads recorded in ev[1])
+    cudaStream_t s2 = c->side;
+    CK(cudaStreamWaitEvent(s2, c->ev[1], 0));
+    CK(cudaEventRecord(c->ev_side[1], s2));
     uint32_t *maskT = (uint32_t *)(A + P.off_maskT);
     if (user_masks) {
-        launch_perm_masks(seed, (int)nx, (int)ny, 0, 1, g.Bp, (int)g.nw, g.comp, maskT, s);
-        launch_user_masks(dmasks, B, (int)nwu, (int)nx, (int)g.n, g.Bp, (int)g.nw, g.comp, maskT, ctr, s);
+        launch_perm_masks(seed, (int)nx, (int)ny, 0, 1, g.Bp, (int)g.nw, g.comp, maskT, s2);
+        launch_user_masks(dmasks, B, (int)nwu, (int)nx, (int)g.n, g.Bp, (int)g.nw, g.comp, maskT, ctr, s2);
     } else {
-        launch_perm_masks(seed, (int)nx, (int)ny, 0, g.ncols, g.Bp, (int)g.nw, g.comp, maskT, s);
+        launch_perm_masks(seed, (int)nx, (int)ny, 0, g.ncols, g.Bp, (int)g.nw, g.comp, maskT, s2);
     }
     CK(cudaGetLastError());
+    CK(cudaEventRecord(c->ev_side[2], s2));
+
+    if ((st = run_blocks(c, P, dX, dY, stat, sigma, true, s)) != EPT_OK) return st;
+    CK(cudaEventRecord(c->ev[2], s));
+    CK(cudaStreamWaitEvent(s, c->ev_side[2], 0));
     CK(cudaEventRecord(c->ev[5], s));
     float *partial = (float *)(A + P.off_partial);
     const Chunk *chunks = (const Chunk *)(A + P.off_chunks);
@@ -332,7 +374,8 @@ ept_status run_test(ept_ctx *c, const float *X, int64_t nx, const float *Y, int6
     }
     CK(cudaEventRecord(c->ev[6], s));
     double *stats = (double *)(A + P.off_stats);
-    launch_combine(partial, P.nparts, g, (const StatConst *)(A + P.off_sc), stats, ctr, s);
+    launch_combine(partial, P.nparts, g, (const StatConst *)(A + P.off_sc), (const double *)(A + P.off_Stpart), stats,
+                   ctr, s);
     CK(cudaGetLastError());
     CK(cudaEventRecord(c->ev[3], s));
 
@@ -368,7 +411,7 @@ ept_status run_test(ept_ctx *c, const float *X, int64_t nx, const float *Y, int6
     out->ms_perm = ms;
     cudaEventElapsedTime(&ms, c->ev[0], c->ev[4]);
     out->ms_total = ms;
-    cudaEventElapsedTime(&ms, c->ev[2], c->ev[5]);
+    cudaEventElapsedTime(&ms, c->ev_side[1], c->ev_side[2]);
     out->ms_masks = ms;
     cudaEventElapsedTime(&ms, c->ev[5], c->ev[6]);
     out->ms_contract = ms;
@@ -405,6 +448,8 @@ ept_status ept_create(ept_ctx **out, int device, size_t mem_budget_bytes) {
     DeviceGuard dg(device);
     cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     for (int k = 0; k < 7 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev_side[k]);
     if (e != cudaSuccess) {
         ept_destroy(c);
         return fail(EPT_ECUDA, "stream/event creation failed: %s", cudaGetErrorString(e));
@@ -422,6 +467,10 @@ ept_status ept_destroy(ept_ctx *c) {
         if (c->pinned) cudaFreeHost(c->pinned);
         for (int k = 0; k < 7; ++k)
             if (c->ev[k]) cudaEventDestroy(c->ev[k]);
+        if (c->side) cudaStreamSynchronize(c->side);
+        for (int k = 0; k < 3; ++k)
+            if (c->ev_side[k]) cudaEventDestroy(c->ev_side[k]);
+        if (c->side) cudaStreamDestroy(c->side);
         if (c->stream) cudaStreamDestroy(c->stream);
     }
     delete c;
@@ -493,7 +542,8 @@ ept_status ept_build_blocks(ept_ctx *c, const float *X, int64_t nx, const float 
     const size_t total = P.total + (on_device ? 0 : align_up(out_bytes, 1024));
     if ((st = ensure_arena(c, total, s)) != EPT_OK) return st;
     fill_tables(c, g);
-    const size_t tab_bytes = align_up(c->h_blkinfo.size() * sizeof(int2), 256);
+    const size_t tab_bytes = align_up(c->h_blkinfo.size() * sizeof(int2), 256) +
+                             align_up(c->h_tiles.size() * sizeof(int4), 256);
     const size_t xin = align_up((size_t)nx * p * 4, 256);
     const size_t in_bytes = host_in ? xin + align_up((size_t)ny * p * 4, 256) : 0;
     if ((st = ensure_pinned(c, tab_bytes + in_bytes + 256)) != EPT_OK) return st;
@@ -508,6 +558,11 @@ ept_status ept_build_blocks(ept_ctx *c, const float *X, int64_t nx, const float 
     }
     memcpy(c->pinned, c->h_blkinfo.data(), c->h_blkinfo.size() * sizeof(int2));
     CK(cudaMemcpyAsync(A + P.off_blkinfo, c->pinned, c->h_blkinfo.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    if (prec == EPT_PREC_SPLIT_BF16) {
+        uint8_t *tsrc = c->pinned + align_up(c->h_blkinfo.size() * sizeof(int2), 256);
+        memcpy(tsrc, c->h_tiles.data(), c->h_tiles.size() * sizeof(int4));
+        CK(cudaMemcpyAsync(A + P.off_tiles, tsrc, c->h_tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+    }
     Counters *ctr = (Counters *)(A + P.off_ctr);
     CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
     if ((st = run_blocks(c, P, dX, dY, stat, sigma, false, s)) != EPT_OK) return st;

@@ -1,0 +1,340 @@
+// ept_build_tc.cu -- the block build (phase 1) on tcgen05 tensor cores.
+//
+// Algorithm 1 builds D_XX, D_YY and D_XY once (Algorithm 3 entries; the Gaussian
+// kernel of Appendix A.1 for MMD).  Here the distinct entries of the pooled upper
+// storage are built from the norm expansion d^2 = ||z_i||^2 + ||z_j||^2 - 2 z_i.z_j
+// with the Gram term on the tensor cores in split FP16: every pooled row is scaled by
+// a power of two c (so that max |c z| < 2^14, inside FP16's range; exact) and split
+// c z = hi + lo (hi = fp16(c z), lo = fp16(c z - hi)); then
+//     c^2 z_i.z_j ~ hi_i.hi_j + hi_i.lo_j + lo_i.hi_j
+// (three MMAs per K-step into one FP32 accumulator in tensor memory; the dropped
+// lo_i.lo_j term and the residual of the split are below 2^-21 of each product, so
+// the entries are about as accurate as an FP32 Gram), and the epilogue multiplies
+// by 1/c^2 (exact).
+// The epilogue forms d^2, recomputes cancellation-prone near-duplicate pairs
+// (d^2 < tau (||z_i||^2 + ||z_j||^2)) directly in FP64, applies sqrt (ED) or
+// exp(-d^2 / (2 sigma^2)) (MMD), forces the diagonal to 0 / 1, zeroes padding, and
+// writes the FP32 entries into the packed upper blocks.
+//
+// Tile = 128 rows (half of a 256-row panel I) x 256 columns (panel J >= I, four
+// K-blocks); K loop over p in steps of 64 with TMA loads of the four operand tiles
+// (A hi/lo 128 x 64, B hi/lo 256 x 64, 128-byte swizzle); two TMEM accumulators so
+// the epilogue of one tile overlaps the main loop of the next.  Roles (192
+// threads): warp 0 TMA, warp 1 MMA + TMEM owner, warps 2-5 epilogue.  All waits
+// are bounded as in the contraction kernel.
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <cstdio>
+#include <cstring>
+
+#include "ept_internal.cuh"
+#include "ept_tc_common.cuh"
+
+namespace ept {
+
+namespace {
+
+using namespace tc;
+
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int BK = 64;
+constexpr int STAGES = 2;
+constexpr int A_BYTES = BM * BK * 2;                  // 16 KB
+constexpr int B_BYTES = BN * BK * 2;                  // 32 KB
+constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 96 KB: A hi, A lo, B hi, B lo
+constexpr int NUM_THREADS = 192;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 1024;
+// kind::f16 instruction descriptor with A = B = FP16 (format 0), D = FP32, K-major
+constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+constexpr unsigned long long ERR_WAIT_TMA = 0x201, ERR_WAIT_MMA = 0x202, ERR_WAIT_EPI = 0x203, ERR_DRAIN = 0x205;
+
+struct Bars {
+    unsigned long long full[STAGES];      // 1 arrival + TMA transaction bytes
+    unsigned long long empty[STAGES];     // 1 arrival (tcgen05.commit)
+    unsigned long long acc_full[2];       // 1 arrival (tcgen05.commit)
+    unsigned long long acc_empty[2];      // 128 epilogue-thread arrivals
+    unsigned long long drain;
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+__device__ __forceinline__ const float *row_ptr(const float *X, const float *Y, int64_t nx, int64_t i, int64_t p) {
+    return (i < nx) ? X + i * p : Y + (i - nx) * p;
+}
+
+// Power-of-two scale c with max |c z| < 2^14 (c = 1 when every input is 0); the
+// exponent is clamped to [-60, 60] so that c^2 and 1/c^2 stay normal FP32 numbers
+// (inputs above 2^74 would overflow the FP32 norms in any case).
+__device__ __forceinline__ float gram_scale(const Counters *ctr) {
+    const float mx = __uint_as_float((uint32_t)ctr->maxabs_bits);
+    if (!(mx > 0.f)) return 1.f;
+    int e;
+    frexpf(mx, &e);              // mx = f 2^e, 0.5 <= f < 1
+    int k = 14 - e;              // mx c < 2^14
+    k = k < -60 ? -60 : (k > 60 ? 60 : k);
+    return ldexpf(1.f, k);
+}
+
+// Pooled rows -> scaled FP16 hi / lo parts [n_pad x p_pad] (zero padding) and squared
+// norms of the unscaled rows (exact products accumulated in FP64, rounded once).
+// One warp per row.
+__global__ void k_split_rows(const float *__restrict__ X, const float *__restrict__ Y, int64_t nx, int64_t n,
+                             int64_t n_pad, int64_t p, int64_t p_pad, __half *__restrict__ Zh,
+                             __half *__restrict__ Zl, float *__restrict__ norms, const Counters *__restrict__ ctr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n_pad) return;
+    const float c = gram_scale(ctr);
+    const float *z = (i < n) ? row_ptr(X, Y, nx, i, p) : nullptr;
+    double acc = 0.0;
+    for (int64_t k = 2 * lane; k < p_pad; k += 64) {
+        float v0 = 0.f, v1 = 0.f;
+        if (z && k < p) v0 = z[k];
+        if (z && k + 1 < p) v1 = z[k + 1];
+        acc = fma((double)v0, (double)v0, acc);
+        acc = fma((double)v1, (double)v1, acc);
+        const float w0 = v0 * c, w1 = v1 * c;
+        const __half h0 = __float2half_rn(w0), h1 = __float2half_rn(w1);
+        const __half l0 = __float2half_rn(w0 - __half2float(h0));
+        const __half l1 = __float2half_rn(w1 - __half2float(h1));
+        *reinterpret_cast<__half2 *>(Zh + i * p_pad + k) = __halves2half2(h0, h1);
+        *reinterpret_cast<__half2 *>(Zl + i * p_pad + k) = __halves2half2(l0, l1);
+    }
+    for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
+    if (lane == 0) norms[i] = (float)acc;
+}
+
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    k_build_tc(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
+               const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl,
+               const int4 *__restrict__ tiles, int ntiles, int kblocks, const float *__restrict__ norms,
+               const float *__restrict__ X, const float *__restrict__ Y, int64_t nx, int64_t n, int64_t p,
+               int64_t NKB, int stat, float neg_inv_2s2, float tau, float *__restrict__ D, Counters *ctr) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    Bars *bars = reinterpret_cast<Bars *>(smem + STAGES * STAGE_BYTES);
+    volatile int *abort_flag = &bars->abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(su32(&bars->full[s]), 1);
+            mbar_init(su32(&bars->empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(su32(&bars->acc_full[a]), 1);
+            mbar_init(su32(&bars->acc_empty[a]), 128);
+        }
+        mbar_init(su32(&bars->drain), 1);
+        bars->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                         su32(&bars->tmem_base))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem_base = bars->tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int armed[STAGES];
+            for (int s2 = 0; s2 < STAGES; ++s2) armed[s2] = -1;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int4 tile = tiles[t];
+                const int rowA = tile.x * PANEL + tile.y * BM;
+                const int rowB = tile.z * PANEL;
+                for (int kk = 0; kk < kblocks; ++kk) {
+                    if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_TMA)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t full = su32(&bars->full[stage]);
+                    mbar_arrive_tx(full, STAGE_BYTES);
+                    uint8_t *st = smem + stage * STAGE_BYTES;
+                    tma_load_2d(su32(st), &tm_ah, kk * BK, rowA, full);
+                    tma_load_2d(su32(st + A_BYTES), &tm_al, kk * BK, rowA, full);
+                    tma_load_2d(su32(st + 2 * A_BYTES), &tm_bh, kk * BK, rowB, full);
+                    tma_load_2d(su32(st + 2 * A_BYTES + B_BYTES), &tm_bl, kk * BK, rowB, full);
+                    armed[stage] = (int)phase;
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                for (int s2 = 0; s2 < STAGES; ++s2) {
+                    if (armed[s2] < 0) continue;
+                    const unsigned long long t0 = gtimer();
+                    while (!mbar_try(su32(&bars->full[s2]), (uint32_t)armed[s2])) {
+                        if (gtimer() - t0 > WAIT_NS) {
+                            atomicCAS(&ctr->err_code, 0ull, ERR_DRAIN);
+                            break;
+                        }
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int stage = 0, acc = 0;
+            uint32_t phase = 0, acc_phase = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                if (!mbar_wait(su32(&bars->acc_empty[acc]), acc_phase ^ 1u, abort_flag, ctr, ERR_WAIT_MMA)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
+                for (int kk = 0; kk < kblocks; ++kk) {
+                    if (!mbar_wait(su32(&bars->full[stage]), phase, abort_flag, ctr, ERR_WAIT_MMA)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t sa = su32(smem + stage * STAGE_BYTES);
+                    const uint64_t dah = desc_sw128(sa), dal = desc_sw128(sa + A_BYTES);
+                    const uint64_t dbh = desc_sw128(sa + 2 * A_BYTES), dbl = desc_sw128(sa + 2 * A_BYTES + B_BYTES);
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k) {
+                        mma_bf16(d_tmem, dah + 2 * k, dbh + 2 * k, IDESC, (kk == 0 && k == 0) ? 0u : 1u);
+                        mma_bf16(d_tmem, dah + 2 * k, dbl + 2 * k, IDESC, 1u);
+                        mma_bf16(d_tmem, dal + 2 * k, dbh + 2 * k, IDESC, 1u);
+                    }
+                    mma_commit(su32(&bars->empty[stage]));
+                    if (++stage == STAGES) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(su32(&bars->acc_full[acc]));
+                if (++acc == 2) {
+                    acc = 0;
+                    acc_phase ^= 1u;
+                }
+            }
+            mma_commit(su32(&bars->drain));
+            const unsigned long long t0 = gtimer();
+            while (!mbar_try(su32(&bars->drain), 0)) {
+                if (gtimer() - t0 > WAIT_NS) {
+                    atomicCAS(&ctr->err_code, 0ull, ERR_DRAIN);
+                    break;
+                }
+            }
+        }
+    } else {
+        // ---------------- epilogue: one tile row per thread ----------------
+        const int quarter = warp & 3;
+        const int rt = quarter * 32 + lane;   // row within the 128-row tile
+        const float cinv = 1.f / gram_scale(ctr);
+        const float inv_c2 = cinv * cinv;     // exact: a power of two
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        unsigned fixups = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+            const int4 tile = tiles[t];
+            const int rp = tile.y * BM + rt;                 // row within panel I
+            const int64_t i = (int64_t)tile.x * PANEL + rp;  // pooled row
+            const float ni = (i < n) ? norms[i] : 0.f;
+            if (!mbar_wait(su32(&bars->acc_full[acc]), acc_phase, abort_flag, ctr, ERR_WAIT_EPI)) break;
+            fence_after();
+            const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
+#pragma unroll 1
+            for (int g = 0; g < BN / 32; ++g) {
+                uint32_t v[32];
+                tmem_ld32(tbase + (uint32_t)(g * 32), v);
+                const int64_t j0 = (int64_t)tile.z * PANEL + g * 32;
+                const float nj_l = (j0 + lane < n) ? norms[j0 + lane] : 0.f;
+                float out[32];
+#pragma unroll
+                for (int e = 0; e < 32; ++e) {
+                    const float nj = __shfl_sync(0xFFFFFFFFu, nj_l, e);
+                    const int64_t j = j0 + e;
+                    float val = 0.f;
+                    if (i < n && j < n) {
+                        if (i == j) {
+                            val = (stat == 0) ? 0.f : 1.f;
+                        } else {
+                            const float d2 = fmaxf(0.f, ni + nj - 2.f * (__uint_as_float(v[e]) * inv_c2));
+                            if (d2 < tau * (ni + nj)) {
+                                const float *zi = row_ptr(X, Y, nx, i, p), *zj = row_ptr(X, Y, nx, j, p);
+                                double s = 0.0;
+                                for (int64_t k = 0; k < p; ++k) {
+                                    const double d = (double)zi[k] - (double)zj[k];
+                                    s = fma(d, d, s);
+                                }
+                                ++fixups;
+                                val = (stat == 0) ? (float)sqrt(s) : (float)exp(s * (double)neg_inv_2s2);
+                            } else {
+                                val = (stat == 0) ? sqrtf(d2) : expf(d2 * neg_inv_2s2);
+                            }
+                        }
+                    }
+                    out[e] = val;
+                }
+                const int64_t kb = (int64_t)tile.z * KB_PER_PANEL + (g >> 1);
+                float *dst = D + (blk_index(tile.x, kb, NKB) * PANEL + rp) * KB + (g & 1) * 32;
+#pragma unroll
+                for (int e = 0; e < 32; e += 4)
+                    *reinterpret_cast<float4 *>(dst + e) = make_float4(out[e], out[e + 1], out[e + 2], out[e + 3]);
+            }
+            fence_before();
+            mbar_arrive(su32(&bars->acc_empty[acc]));
+            if (++acc == 2) {
+                acc = 0;
+                acc_phase ^= 1u;
+            }
+        }
+        if (fixups) atomicAdd(&ctr->n_fixup, (unsigned long long)fixups);
+    }
+
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem_base) : "memory");
+    }
+}
+
+}  // namespace
+
+void launch_split_rows(const float *X, const float *Y, const Geom &g, int64_t p_pad, uint16_t *Zh, uint16_t *Zl,
+                       float *norms, const Counters *ctr, cudaStream_t s) {
+    const int warps = 8;
+    k_split_rows<<<(unsigned)((g.n_pad + warps - 1) / warps), warps * 32, 0, s>>>(
+        X, Y, g.nx, g.n, g.n_pad, g.p, p_pad, (__half *)Zh, (__half *)Zl, norms, ctr);
+}
+
+cudaError_t launch_build_tc(const void *tmaps, const int4 *tiles, int ntiles, int64_t p_pad, const float *norms,
+                            const float *X, const float *Y, const Geom &g, int stat, double sigma, double tau, float *D,
+                            Counters *ctr, int num_sms, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_build_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (ntiles < 1) return cudaSuccess;
+    const CUtensorMap *tm = (const CUtensorMap *)tmaps;
+    const float neg = (stat == 0) ? 0.f : (float)(-1.0 / (2.0 * sigma * sigma));
+    const int grid = ntiles < num_sms ? ntiles : num_sms;
+    k_build_tc<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(tm[0], tm[1], tm[2], tm[3], tiles, ntiles, (int)(p_pad / BK),
+                                                     norms, X, Y, g.nx, g.n, g.p, g.NKB, stat, neg, (float)tau, D,
+                                                     ctr);
+    return cudaGetLastError();
+}
+
+}  // namespace ept

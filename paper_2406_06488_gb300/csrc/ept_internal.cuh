@@ -58,7 +58,7 @@ struct Chunk { int I, kb0, kb1, pad; };
 // device parameters of the statistic's final combination
 struct StatConst {
     double cT;        // (n / (nx ny))^2
-    double S_tilde;   // sum of all entries of the centred matrix
+    double S_tilde;   // unused: S~ is summed from the per-panel parts by the combination
     double inv_o2;    // 1 / other^2 (the larger group's size)
     double sign;      // -1 for ED, +1 for MMD
 };
@@ -70,6 +70,7 @@ struct Counters {
     unsigned long long bad_mask;
     unsigned long long nonfinite;
     unsigned long long err_code;   // device-side bounded waits that gave up, etc.
+    unsigned long long maxabs_bits;  // bit pattern of max |x| over the finite inputs (FP32, as an integer)
 };
 
 // ---- launchers (ept_kernels.cu) ----
@@ -85,10 +86,11 @@ void launch_build_simt(const float *X, const float *Y, const float *norms, const
                        double sigma, double tau, const int2 *blk_info, float *D, Counters *ctr,
                        cudaStream_t s);
 void launch_blocksums(const float *D, const Geom &g, double *rowpart, double *colpart, cudaStream_t s);
-void launch_rowsum_reduce(const double *rowpart, const double *colpart, const Geom &g, double *r,
+// r: n_pad doubles; Spart, Upart, Stpart: one double per panel (NP)
+void launch_rowsum_reduce(const double *rowpart, const double *colpart, const Geom &g, double *r, double *Spart,
                           cudaStream_t s);
-void launch_center(const double *r, const Geom &g, float *u, double *dcorr, StatConst *sc, int stat,
-                   cudaStream_t s);
+void launch_center(const double *r, const double *Spart, const Geom &g, float *u, double *dcorr, double *Upart,
+                   double *Stpart, StatConst *sc, int stat, cudaStream_t s);
 void launch_pack_fp32(const float *D, const float *u, const double *dcorr, const Geom &g,
                       const int2 *blk_info, float *C, cudaStream_t s);
 void launch_pack_bf16(const float *D, const float *u, const double *dcorr, const Geom &g,
@@ -96,7 +98,7 @@ void launch_pack_bf16(const float *D, const float *u, const double *dcorr, const
 void launch_contract_simt(const float *C, const uint32_t *maskT, const Chunk *chunks, const Geom &g,
                           float *partial, cudaStream_t s);
 void launch_combine(const float *partial, int64_t nparts, const Geom &g, const StatConst *sc,
-                    double *stats, Counters *ctr, cudaStream_t s);
+                    const double *Stpart, double *stats, Counters *ctr, cudaStream_t s);
 void launch_expand_blocks(const float *D, const Geom &g, float *out, cudaStream_t s);
 
 // ---- tcgen05 contraction (ept_contract_tc.cu) ----
@@ -107,5 +109,19 @@ cudaError_t launch_contract_tc(const void *tmap_hi, const void *tmap_lo, const u
 // Encodes the two TMA tensor maps over the packed hi/lo blocks (host side).
 bool encode_block_tmaps(void *tmap_hi, void *tmap_lo, const uint16_t *Chi, const uint16_t *Clo,
                         int64_t nblk, char *err, size_t errlen);
+// Encodes four TMA tensor maps over the FP16 hi/lo pooled rows [n_pad x p_pad]:
+// (hi, lo) with 64 x 128 boxes, then (hi, lo) with 64 x 256 boxes.
+bool encode_rows_tmaps(void *tmaps4, const uint16_t *Zh, const uint16_t *Zl, int64_t n_pad, int64_t p_pad,
+                       char *err, size_t errlen);
+
+// ---- tcgen05 block build (ept_build_tc.cu) ----
+constexpr int BUILD_KB = 64;   // p is padded to a multiple of this
+// Zh, Zl: the scaled FP16 hi / lo parts (the scale comes from ctr->maxabs_bits)
+void launch_split_rows(const float *X, const float *Y, const Geom &g, int64_t p_pad, uint16_t *Zh, uint16_t *Zl,
+                       float *norms, const Counters *ctr, cudaStream_t s);
+// tiles: (panel I, half h, column panel J >= I); tmaps: the four maps of encode_rows_tmaps
+cudaError_t launch_build_tc(const void *tmaps, const int4 *tiles, int ntiles, int64_t p_pad, const float *norms,
+                            const float *X, const float *Y, const Geom &g, int stat, double sigma, double tau,
+                            float *D, Counters *ctr, int num_sms, cudaStream_t s);
 
 }  // namespace ept

@@ -199,12 +199,20 @@ void launch_masks_to_rows(const uint32_t *maskT, int64_t ncols, int nw, int64_t 
 }
 
 // ---------------------------------------------------------------------------
+// Counts non-finite inputs and records max |x| (non-negative FP32 values order like
+// their bit patterns, so an integer atomicMax on the bits gives the maximum).
 __global__ void k_check_finite(const float *__restrict__ a, int64_t count, Counters *ctr) {
     bool bad = false;
+    uint32_t mx = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-         i += (int64_t)gridDim.x * blockDim.x)
-        bad |= !isfinite(a[i]);
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = a[i];
+        if (isfinite(v)) mx = max(mx, __float_as_uint(fabsf(v)));
+        else bad = true;
+    }
+    for (int off = 16; off; off >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
     if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicAdd(&ctr->nonfinite, 1ull);
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(&ctr->maxabs_bits, (unsigned long long)mx);
 }
 
 void launch_check_finite(const float *a, int64_t count, Counters *ctr, cudaStream_t s) {
@@ -373,29 +381,35 @@ __global__ void __launch_bounds__(256) k_blocksums(const float *__restrict__ D, 
     __shared__ double cs[8][64];
     const int64_t blk = blockIdx.x;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float *base = D + blk * (int64_t)(PANEL * KB);
+    const float *base = D + blk * (int64_t)(PANEL * KB) + (int64_t)(warp * 32) * KB + 2 * lane;
     float ch0 = 0.f, cl0 = 0.f, ch1 = 0.f, cl1 = 0.f;
-    for (int rr = 0; rr < 32; ++rr) {
-        const int r = warp * 32 + rr;
-        const float2 v = *reinterpret_cast<const float2 *>(base + (int64_t)r * KB + 2 * lane);
-        float s, e;
-        two_sum(v.x, v.y, s, e);
-        for (int off = 16; off; off >>= 1) {
-            const float s2 = __shfl_xor_sync(0xFFFFFFFFu, s, off);
-            const float e2 = __shfl_xor_sync(0xFFFFFFFFu, e, off);
+#pragma unroll 1
+    for (int r0 = 0; r0 < 32; r0 += 8) {
+        float2 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = *reinterpret_cast<const float2 *>(base + (int64_t)(r0 + q) * KB);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            float s, e;
+            two_sum(v[q].x, v[q].y, s, e);
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                const float s2 = __shfl_xor_sync(0xFFFFFFFFu, s, off);
+                const float e2 = __shfl_xor_sync(0xFFFFFFFFu, e, off);
+                float t, f;
+                two_sum(s, s2, t, f);
+                s = t;
+                e = (e + e2) + f;
+            }
+            if (lane == 0) rowpart[blk * PANEL + warp * 32 + r0 + q] = (double)s + (double)e;
             float t, f;
-            two_sum(s, s2, t, f);
-            s = t;
-            e = (e + e2) + f;
+            two_sum(ch0, v[q].x, t, f);
+            ch0 = t;
+            cl0 += f;
+            two_sum(ch1, v[q].y, t, f);
+            ch1 = t;
+            cl1 += f;
         }
-        if (lane == 0) rowpart[blk * PANEL + r] = (double)s + (double)e;
-        float t, f;
-        two_sum(ch0, v.x, t, f);
-        ch0 = t;
-        cl0 += f;
-        two_sum(ch1, v.y, t, f);
-        ch1 = t;
-        cl1 += f;
     }
     cs[warp][2 * lane] = (double)ch0 + (double)cl0;
     cs[warp][2 * lane + 1] = (double)ch1 + (double)cl1;
@@ -414,39 +428,50 @@ void launch_blocksums(const float *D, const Geom &g, double *rowpart, double *co
 
 // r_i = sum over the stored blocks of row i's panel (its own row segments) + sum
 // over the earlier panels J < panel(i) of column i's segments, in fixed order.
-__global__ void k_rowsum_reduce(const double *__restrict__ rowpart, const double *__restrict__ colpart,
-                                int64_t n, int64_t n_pad, int64_t NKB, double *__restrict__ r) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_pad) return;
-    if (i >= n) {
-        r[i] = 0.0;
-        return;
-    }
-    const int64_t I = i / PANEL, rr = i % PANEL;
+// One CTA of 256 threads per panel; Spart[panel] = sum of its r_i (fixed tree).
+__global__ void __launch_bounds__(256) k_rowsum_reduce(const double *__restrict__ rowpart,
+                                                       const double *__restrict__ colpart, int64_t n, int64_t NKB,
+                                                       double *__restrict__ r, double *__restrict__ Spart) {
+    __shared__ double sh[256];
+    const int64_t I = blockIdx.x, rr = threadIdx.x;
+    const int64_t i = I * PANEL + rr;
     double acc = 0.0;
-    for (int64_t kb = KB_PER_PANEL * I; kb < NKB; ++kb) acc += rowpart[blk_index(I, kb, NKB) * PANEL + rr];
-    const int64_t kbi = i / KB, ci = i % KB;
-    for (int64_t J = 0; J < I; ++J) acc += colpart[blk_index(J, kbi, NKB) * KB + ci];
+    if (i < n) {
+        for (int64_t kb = KB_PER_PANEL * I; kb < NKB; ++kb) acc += rowpart[blk_index(I, kb, NKB) * PANEL + rr];
+        const int64_t kbi = i / KB, ci = i % KB;
+        for (int64_t J = 0; J < I; ++J) acc += colpart[blk_index(J, kbi, NKB) * KB + ci];
+    }
     r[i] = acc;
+    sh[rr] = acc;
+    __syncthreads();
+    for (int off = 128; off; off >>= 1) {
+        if (rr < off) sh[rr] += sh[rr + off];
+        __syncthreads();
+    }
+    if (rr == 0) Spart[I] = sh[0];
 }
 
-void launch_rowsum_reduce(const double *rowpart, const double *colpart, const Geom &g, double *r,
+void launch_rowsum_reduce(const double *rowpart, const double *colpart, const Geom &g, double *r, double *Spart,
                           cudaStream_t s) {
-    k_rowsum_reduce<<<(unsigned)((g.n_pad + 255) / 256), 256, 0, s>>>(rowpart, colpart, g.n, g.n_pad, g.NKB, r);
+    k_rowsum_reduce<<<(unsigned)g.NP, 256, 0, s>>>(rowpart, colpart, g.n, g.NKB, r, Spart);
 }
 
-// Deterministic block-wide FP64 sum (fixed strided order, fixed tree).
-__device__ double block_sum_1024(double v, double *sh) {
+// Deterministic sum of a short array in fixed order.
+__device__ __forceinline__ double ordered_sum(const double *a, int64_t m) {
+    double s = 0.0;
+    for (int64_t k = 0; k < m; ++k) s += a[k];
+    return s;
+}
+
+__device__ __forceinline__ double block_sum_256(double v, double *sh) {
     const int t = threadIdx.x;
     sh[t] = v;
     __syncthreads();
-    for (int off = 512; off; off >>= 1) {
+    for (int off = 128; off; off >>= 1) {
         if (t < off) sh[t] += sh[t + off];
         __syncthreads();
     }
-    const double s = sh[0];
-    __syncthreads();
-    return s;
+    return sh[0];
 }
 
 // Centring.  u_i = r_i / n - S / (2 n^2) (double centring, S = 1'W1), rounded to FP32;
@@ -458,46 +483,56 @@ __device__ double block_sum_1024(double v, double *sh) {
 // and MMD^2 (Eq. 2) is the same expression with the opposite sign.  Because
 // s_i^2 = s_i, L = s' diag(r~) s with r~ = W~ 1 = r - n u - (1'u) 1, so
 //     stat = sign * (cT s'Cs + S~/o^2),  C = W~ - kappa diag(r~),  kappa = cL/cT = 2m/n,
-// sign = -1 (ED) or +1 (MMD).  dcorr_i = kappa r~_i.  Single CTA.
-__global__ void __launch_bounds__(1024) k_center(const double *__restrict__ r, int64_t n, int64_t nx,
-                                                 int64_t ny, int64_t m, int64_t other, int64_t n_pad,
-                                                 float *__restrict__ u, double *__restrict__ dcorr, StatConst *sc,
-                                                 int stat) {
-    __shared__ double sh[1024];
-    const int t = threadIdx.x;
-    double part = 0.0;
-    for (int64_t i = t; i < n; i += 1024) part += r[i];
-    const double S = block_sum_1024(part, sh);
-    const double fn = (double)n;
-    part = 0.0;
-    for (int64_t i = t; i < n_pad; i += 1024) {
-        float ui = 0.f;
-        if (i < n) ui = (float)(r[i] / fn - S / (2.0 * fn * fn));
-        u[i] = ui;
-        part += (double)ui;
-    }
-    const double U = block_sum_1024(part, sh);
-    const double kappa = 2.0 * (double)m / fn;
-    part = 0.0;
-    for (int64_t i = t; i < n_pad; i += 1024) {
-        double rt = 0.0;
-        if (i < n) rt = r[i] - fn * (double)u[i] - U;
-        dcorr[i] = kappa * rt;
-        part += rt;
-    }
-    const double St = block_sum_1024(part, sh);
-    if (t == 0) {
-        const double q = fn / ((double)nx * (double)ny);
-        sc->cT = q * q;
-        sc->S_tilde = St;
-        sc->inv_o2 = 1.0 / ((double)other * (double)other);
-        sc->sign = (stat == 0) ? -1.0 : 1.0;
+// sign = -1 (ED) or +1 (MMD).  dcorr_i = kappa r~_i.
+// Only r~ must be exact (it is, in FP64, for the FP32 u actually stored); u itself
+// may be any value, so it is formed with multiplications by precomputed reciprocals.
+// Step 1 (one CTA per panel): u_i, Upart[panel] = sum of the u_i as doubles.
+__global__ void __launch_bounds__(256) k_center_u(const double *__restrict__ r, const double *__restrict__ Spart,
+                                                  int64_t NP, int64_t n, double inv_n, double inv_2n2,
+                                                  float *__restrict__ u, double *__restrict__ Upart) {
+    __shared__ double sh[256];
+    const double S = ordered_sum(Spart, NP);
+    const int64_t i = (int64_t)blockIdx.x * PANEL + threadIdx.x;
+    float ui = 0.f;
+    if (i < n) ui = (float)(r[i] * inv_n - S * inv_2n2);
+    u[i] = ui;
+    const double tot = block_sum_256((double)ui, sh);
+    if (threadIdx.x == 0) Upart[blockIdx.x] = tot;
+}
+
+// Step 2 (one CTA per panel): r~_i, dcorr_i = kappa r~_i, Stpart[panel] = sum of r~_i;
+// block 0 also writes the constants of the final combination.
+__global__ void __launch_bounds__(256) k_center_r(const double *__restrict__ r, const float *__restrict__ u,
+                                                  const double *__restrict__ Upart, int64_t NP, int64_t n,
+                                                  double kappa, double cT, double inv_o2, double sign,
+                                                  double *__restrict__ dcorr, double *__restrict__ Stpart,
+                                                  StatConst *sc) {
+    __shared__ double sh[256];
+    const double U = ordered_sum(Upart, NP);
+    const int64_t i = (int64_t)blockIdx.x * PANEL + threadIdx.x;
+    double rt = 0.0;
+    if (i < n) rt = r[i] - (double)n * (double)u[i] - U;
+    dcorr[i] = kappa * rt;
+    const double tot = block_sum_256(rt, sh);
+    if (threadIdx.x == 0) {
+        Stpart[blockIdx.x] = tot;
+        if (blockIdx.x == 0) {
+            sc->cT = cT;
+            sc->inv_o2 = inv_o2;
+            sc->sign = sign;
+            sc->S_tilde = 0.0;
+        }
     }
 }
 
-void launch_center(const double *r, const Geom &g, float *u, double *dcorr, StatConst *sc, int stat,
-                   cudaStream_t s) {
-    k_center<<<1, 1024, 0, s>>>(r, g.n, g.nx, g.ny, g.m, g.other, g.n_pad, u, dcorr, sc, stat);
+void launch_center(const double *r, const double *Spart, const Geom &g, float *u, double *dcorr, double *Upart,
+                   double *Stpart, StatConst *sc, int stat, cudaStream_t s) {
+    const double fn = (double)g.n;
+    const double q = fn / ((double)g.nx * (double)g.ny);
+    k_center_u<<<(unsigned)g.NP, 256, 0, s>>>(r, Spart, g.NP, g.n, 1.0 / fn, 1.0 / (2.0 * fn * fn), u, Upart);
+    k_center_r<<<(unsigned)g.NP, 256, 0, s>>>(r, u, Upart, g.NP, g.n, 2.0 * (double)g.m / fn, q * q,
+                                             1.0 / ((double)g.other * (double)g.other), stat == 0 ? -1.0 : 1.0, dcorr,
+                                             Stpart, sc);
 }
 
 // Packing.  Stored entry (i, j), j >= 256*panel(i):
@@ -514,36 +549,45 @@ __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ D, const
     const int2 bi = blk_info[blk];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t j0 = (int64_t)bi.y * KB + 2 * lane;
-    const float uj0 = (j0 < n) ? u[j0] : 0.f, uj1 = (j0 + 1 < n) ? u[j0 + 1] : 0.f;
-    for (int rr = 0; rr < 32; ++rr) {
-        const int r = warp * 32 + rr;
-        const int64_t i = (int64_t)bi.x * PANEL + r;
-        const int64_t off = (blk * PANEL + r) * KB + 2 * lane;
-        const float2 d = *reinterpret_cast<const float2 *>(D + off);
-        float w[2];
-        const float dv[2] = {d.x, d.y};
-        const float uj[2] = {uj0, uj1};
+    const float uj[2] = {(j0 < n) ? u[j0] : 0.f, (j0 + 1 < n) ? u[j0 + 1] : 0.f};
+    const int64_t row0 = (int64_t)bi.x * PANEL + warp * 32;
+#pragma unroll 1
+    for (int r0 = 0; r0 < 32; r0 += 8) {
+        float2 d[8];
+        float ui[8];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int64_t j = j0 + e;
-            float v = 0.f;
-            if (i < n && j < n && j >= i) {
-                const float ui = u[i];
-                if (j == i) v = (float)((double)dv[e] - 2.0 * (double)ui - dcorr[i]);
-                else v = 2.f * ((dv[e] - ui) - uj[e]);
-            }
-            w[e] = v;
+        for (int q = 0; q < 8; ++q) {
+            d[q] = *reinterpret_cast<const float2 *>(D + (blk * PANEL + warp * 32 + r0 + q) * KB + 2 * lane);
+            const int64_t i = row0 + r0 + q;
+            ui[q] = (i < n) ? u[i] : 0.f;
         }
-        if (BF16) {
-            __nv_bfloat16 h0 = __float2bfloat16_rn(w[0]), h1 = __float2bfloat16_rn(w[1]);
-            __nv_bfloat16 l0 = __float2bfloat16_rn(w[0] - __bfloat162float(h0));
-            __nv_bfloat16 l1 = __float2bfloat16_rn(w[1] - __bfloat162float(h1));
-            const uint32_t hv = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-            const uint32_t lv = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-            *reinterpret_cast<uint32_t *>(Chi + off) = hv;
-            *reinterpret_cast<uint32_t *>(Clo + off) = lv;
-        } else {
-            *reinterpret_cast<float2 *>(C32 + off) = make_float2(w[0], w[1]);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t i = row0 + r0 + q;
+            const int64_t off = (blk * PANEL + warp * 32 + r0 + q) * KB + 2 * lane;
+            const float dv[2] = {d[q].x, d[q].y};
+            float w[2];
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int64_t j = j0 + e;
+                float v = 0.f;
+                if (i < n && j < n && j >= i) {
+                    if (j == i) v = (float)((double)dv[e] - 2.0 * (double)ui[q] - dcorr[i]);
+                    else v = 2.f * ((dv[e] - ui[q]) - uj[e]);
+                }
+                w[e] = v;
+            }
+            if (BF16) {
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(w[0]), h1 = __float2bfloat16_rn(w[1]);
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(w[0] - __bfloat162float(h0));
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(w[1] - __bfloat162float(h1));
+                const uint32_t hv = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                const uint32_t lv = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+                *reinterpret_cast<uint32_t *>(Chi + off) = hv;
+                *reinterpret_cast<uint32_t *>(Clo + off) = lv;
+            } else {
+                *reinterpret_cast<float2 *>(C32 + off) = make_float2(w[0], w[1]);
+            }
         }
     }
 }
@@ -634,12 +678,14 @@ void launch_contract_simt(const float *C, const uint32_t *maskT, const Chunk *ch
 // sign * (cT Q_b + S~/o^2).  Then, against stat_0 (the identity, evaluated by the
 // same kernels), count stat_b >= stat_0 and near-ties |stat_b - stat_0| <= 1e-5 |stat_0|.
 __global__ void k_combine_stats(const float *__restrict__ partial, int64_t nparts, int64_t Bp, int64_t ncols,
-                                const StatConst *__restrict__ sc, double *__restrict__ stats) {
+                                const StatConst *__restrict__ sc, const double *__restrict__ Stpart, int64_t NP,
+                                double *__restrict__ stats) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= ncols) return;
+    const double St = ordered_sum(Stpart, NP);
     double q = 0.0;
     for (int64_t k = 0; k < nparts; ++k) q += (double)partial[k * Bp + b];
-    stats[b] = sc->sign * (sc->cT * q + sc->S_tilde * sc->inv_o2);
+    stats[b] = sc->sign * (sc->cT * q + St * sc->inv_o2);
 }
 
 __global__ void k_combine_count(const double *__restrict__ stats, int64_t ncols, Counters *ctr) {
@@ -659,10 +705,10 @@ __global__ void k_combine_count(const double *__restrict__ stats, int64_t ncols,
     }
 }
 
-void launch_combine(const float *partial, int64_t nparts, const Geom &g, const StatConst *sc, double *stats,
-                    Counters *ctr, cudaStream_t s) {
+void launch_combine(const float *partial, int64_t nparts, const Geom &g, const StatConst *sc,
+                    const double *Stpart, double *stats, Counters *ctr, cudaStream_t s) {
     const unsigned grid = (unsigned)((g.ncols + 255) / 256);
-    k_combine_stats<<<grid, 256, 0, s>>>(partial, nparts, g.Bp, g.ncols, sc, stats);
+    k_combine_stats<<<grid, 256, 0, s>>>(partial, nparts, g.Bp, g.ncols, sc, Stpart, g.NP, stats);
     k_combine_count<<<grid, 256, 0, s>>>(stats, g.ncols, ctr);
 }
 

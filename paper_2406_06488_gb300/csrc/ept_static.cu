@@ -53,6 +53,7 @@ inline size_t up(size_t v) { return (v + 1023) / 1024 * 1024; }
 
 struct StaticPlan {
     size_t norms, blkinfo, chunks, D, rowpart, colpart, r, u, dcorr, sc, hi, lo, maskT, partial, stats, ctr, total;
+    size_t Spart, Upart, Stpart;
 };
 
 StaticPlan static_plan(const Geom &g) {
@@ -74,6 +75,9 @@ StaticPlan static_plan(const Geom &g) {
     P.u = take((size_t)g.n_pad * 4);
     P.dcorr = take((size_t)g.n_pad * 8);
     P.sc = take(sizeof(StatConst));
+    P.Spart = take((size_t)g.NP * 8);
+    P.Upart = take((size_t)g.NP * 8);
+    P.Stpart = take((size_t)g.NP * 8);
     P.hi = take(elems * 2);
     P.lo = take(elems * 2);
     P.maskT = take((size_t)g.nw * g.Bp * 4);
@@ -195,9 +199,10 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     float *u = (float *)(A + P.u);
     StatConst *sc = (StatConst *)(A + P.sc);
     uint16_t *hi = (uint16_t *)(A + P.hi), *lo = (uint16_t *)(A + P.lo);
+    double *Spart = (double *)(A + P.Spart), *Upart = (double *)(A + P.Upart), *Stpart = (double *)(A + P.Stpart);
     launch_blocksums(D, g, rowpart, colpart, s);
-    launch_rowsum_reduce(rowpart, colpart, g, r, s);
-    launch_center(r, g, u, dcorr, sc, stat, s);
+    launch_rowsum_reduce(rowpart, colpart, g, r, Spart, s);
+    launch_center(r, Spart, g, u, dcorr, Upart, Stpart, sc, stat, s);
     launch_pack_bf16(D, u, dcorr, g, blkinfo, hi, lo, s);
     uint32_t *maskT = (uint32_t *)(A + P.maskT);
     launch_perm_masks(seed, (int)nx, (int)ny, 0, g.ncols, g.Bp, (int)g.nw, g.comp, maskT, s);
@@ -208,7 +213,7 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     float *partial = (float *)(A + P.partial);
     SCK(launch_contract_tc(&th, &tl, maskT, chunks, g, partial, ctr, sd->num_sms, s));
     double *stats = (double *)(A + P.stats);
-    launch_combine(partial, g.nchunks, g, sc, stats, ctr, s);
+    launch_combine(partial, g.nchunks, g, sc, Stpart, stats, ctr, s);
     SCK(cudaGetLastError());
     if (perm_stats && B > 0)
         SCK(cudaMemcpyAsync(perm_stats, stats + 1, (size_t)B * 8, cudaMemcpyDeviceToDevice, s));

@@ -55,13 +55,15 @@ def test_masks_bit_exact(ctx, nx, ny, seed, b0, count):
 
 
 # ------------------------------------------------------------------ block build
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("stat", ["ed", "mmd"])
 @pytest.mark.parametrize("nx,ny,p", [(1, 1, 1), (5, 4, 3), (100, 100, 10), (37, 300, 17), (129, 130, 64),
-                                     (300, 257, 1000)])
-def test_blocks_match_oracle(ctx, stat, nx, ny, p):
+                                     (300, 257, 1000), (600, 700, 65)])
+def test_blocks_match_oracle(ctx, prec, stat, nx, ny, p):
+    # split_bf16 builds the Gram term on the tensor cores (hi/lo split), plain_fp32 with FP32 FMA
     X, Y = _pair(nx, ny, p, seed=nx + ny + p)
     sigma = float(np.sqrt(p))
-    D = ctx.build_blocks(X, Y, stat, sigma)
+    D = ctx.build_blocks(X, Y, stat, sigma, prec=prec)
     Z = np.vstack([X, Y])
     ref = oracle.block_matrix(Z, Z, stat, sigma)
     diag = np.diag(D)
