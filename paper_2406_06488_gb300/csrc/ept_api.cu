@@ -48,7 +48,7 @@ struct Plan {
     int64_t n_user_masks;
     size_t off_X, off_Y, off_norms, off_blkinfo, off_chunks, off_D, off_rowpart, off_colpart, off_r, off_u,
         off_dcorr, off_sc, off_hi, off_lo, off_maskT, off_umask, off_partial, off_stats, off_ctr, total;
-    size_t off_zh, off_zl, off_tiles, off_Spart, off_Upart, off_Stpart;
+    size_t off_zh, off_zl, off_tiles, off_Spart, off_Upart, off_Stpart, off_iscale;
     int64_t nparts, p_pad, ntiles;
 };
 
@@ -77,7 +77,8 @@ Plan make_plan(const Geom &g, int prec, bool host_in, int64_t n_user_masks) {
     P.off_u = take((size_t)g.n_pad * 4);
     P.off_dcorr = take((size_t)g.n_pad * 8);
     P.off_sc = take(sizeof(StatConst));
-    P.off_Spart = take((size_t)g.NP * 8);
+    P.off_Spart = take((size_t)(g.n_pad / 32) * 8);
+    P.off_iscale = take((size_t)g.n_pad * 4);
     P.off_Upart = take((size_t)g.NP * 8);
     P.off_Stpart = take((size_t)g.NP * 8);
     P.p_pad = (g.p + BUILD_KB - 1) / BUILD_KB * BUILD_KB;
@@ -244,17 +245,18 @@ ept_status run_blocks(ept_ctx *c, const Plan &P, const float *X, const float *Y,
     int2 *blkinfo = (int2 *)(A + P.off_blkinfo);
     float *D = (float *)(A + P.off_D);
     Counters *ctr = (Counters *)(A + P.off_ctr);
-    launch_check_finite(X, g.nx * g.p, ctr, s);
-    launch_check_finite(Y, g.ny * g.p, ctr, s);
     if (P.prec == EPT_PREC_SPLIT_BF16) {
         uint16_t *zh = (uint16_t *)(A + P.off_zh), *zl = (uint16_t *)(A + P.off_zl);
-        launch_split_rows(X, Y, g, P.p_pad, zh, zl, norms, ctr, s);
+        float *iscale = (float *)(A + P.off_iscale);
+        launch_split_rows(X, Y, g, P.p_pad, zh, zl, norms, iscale, ctr, s);   // also counts non-finite inputs
         alignas(64) CUtensorMap tm[4];
         char emsg[160];
         if (!encode_rows_tmaps(tm, zh, zl, g.n_pad, P.p_pad, emsg, sizeof(emsg))) return fail(EPT_ECUDA, "%s", emsg);
-        CK(launch_build_tc(tm, (const int4 *)(A + P.off_tiles), (int)P.ntiles, P.p_pad, norms, X, Y, g, stat, sigma,
-                           NEAR_DUP_TAU, D, ctr, c->num_sms, s));
+        CK(launch_build_tc(tm, (const int4 *)(A + P.off_tiles), (int)P.ntiles, P.p_pad, norms, iscale, X, Y, g, stat,
+                           sigma, NEAR_DUP_TAU, D, ctr, c->num_sms, s));
     } else {
+        launch_check_finite(X, g.nx * g.p, ctr, s);
+        launch_check_finite(Y, g.ny * g.p, ctr, s);
         launch_norms(X, Y, g, norms, s);
         launch_build_simt(X, Y, norms, g, stat, sigma, NEAR_DUP_TAU, blkinfo, D, ctr, s);
     }

@@ -3,14 +3,14 @@
 // Algorithm 1 builds D_XX, D_YY and D_XY once (Algorithm 3 entries; the Gaussian
 // kernel of Appendix A.1 for MMD).  Here the distinct entries of the pooled upper
 // storage are built from the norm expansion d^2 = ||z_i||^2 + ||z_j||^2 - 2 z_i.z_j
-// with the Gram term on the tensor cores in split FP16: every pooled row is scaled by
-// a power of two c (so that max |c z| < 2^14, inside FP16's range; exact) and split
-// c z = hi + lo (hi = fp16(c z), lo = fp16(c z - hi)); then
-//     c^2 z_i.z_j ~ hi_i.hi_j + hi_i.lo_j + lo_i.hi_j
+// with the Gram term on the tensor cores in split FP16: every pooled row i is scaled
+// by its own power of two c_i (so that max_k |c_i z_ik| < 2^14, inside FP16's range;
+// exact) and split c_i z_i = hi_i + lo_i (hi = fp16(c z), lo = fp16(c z - hi)); then
+//     c_i c_j z_i.z_j ~ hi_i.hi_j + hi_i.lo_j + lo_i.hi_j
 // (three MMAs per K-step into one FP32 accumulator in tensor memory; the dropped
 // lo_i.lo_j term and the residual of the split are below 2^-21 of each product, so
 // the entries are about as accurate as an FP32 Gram), and the epilogue multiplies
-// by 1/c^2 (exact).
+// by 1/c_i and 1/c_j (exact).
 // The epilogue forms d^2, recomputes cancellation-prone near-duplicate pairs
 // (d^2 < tau (||z_i||^2 + ||z_j||^2)) directly in FP64, applies sqrt (ED) or
 // exp(-d^2 / (2 sigma^2)) (MMD), forces the diagonal to 0 / 1, zeroes padding, and
@@ -65,35 +65,48 @@ __device__ __forceinline__ const float *row_ptr(const float *X, const float *Y, 
     return (i < nx) ? X + i * p : Y + (i - nx) * p;
 }
 
-// Power-of-two scale c with max |c z| < 2^14 (c = 1 when every input is 0); the
-// exponent is clamped to [-60, 60] so that c^2 and 1/c^2 stay normal FP32 numbers
-// (inputs above 2^74 would overflow the FP32 norms in any case).
-__device__ __forceinline__ float gram_scale(const Counters *ctr) {
-    const float mx = __uint_as_float((uint32_t)ctr->maxabs_bits);
-    if (!(mx > 0.f)) return 1.f;
-    int e;
-    frexpf(mx, &e);              // mx = f 2^e, 0.5 <= f < 1
-    int k = 14 - e;              // mx c < 2^14
-    k = k < -60 ? -60 : (k > 60 ? 60 : k);
-    return ldexpf(1.f, k);
-}
-
-// Pooled rows -> scaled FP16 hi / lo parts [n_pad x p_pad] (zero padding) and squared
-// norms of the unscaled rows (exact products accumulated in FP64, rounded once).
-// One warp per row.
+// Pooled row i -> FP16 hi / lo parts of c_i z_i [n_pad x p_pad] (zero padding), the
+// inverse scale 1/c_i, and the squared norm of the unscaled row (exact products
+// accumulated in FP64, rounded once).  c_i = 2^k with max |c_i z_i| < 2^14, k clamped
+// to [-60, 60] so that 1/c_i 1/c_j stays a normal FP32 number (rows above 2^74 would
+// overflow the FP32 norms in any case).  Non-finite inputs are counted.  One warp
+// per row.
 __global__ void k_split_rows(const float *__restrict__ X, const float *__restrict__ Y, int64_t nx, int64_t n,
                              int64_t n_pad, int64_t p, int64_t p_pad, __half *__restrict__ Zh,
-                             __half *__restrict__ Zl, float *__restrict__ norms, const Counters *__restrict__ ctr) {
+                             __half *__restrict__ Zl, float *__restrict__ norms, float *__restrict__ inv_scale,
+                             Counters *ctr) {
     const int lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= n_pad) return;
-    const float c = gram_scale(ctr);
     const float *z = (i < n) ? row_ptr(X, Y, nx, i, p) : nullptr;
+    uint32_t mx = 0;
+    bool bad = false;
+    if (z) {
+        for (int64_t k = lane; k < p; k += 32) {
+            const float v = z[k];
+            if (isfinite(v)) mx = max(mx, __float_as_uint(fabsf(v)));
+            else bad = true;
+        }
+    }
+    for (int off = 16; off; off >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
+    if (__any_sync(0xFFFFFFFFu, bad)) {
+        if (lane == 0) atomicAdd(&ctr->nonfinite, 1ull);
+    }
+    int k2 = 0;
+    if (mx) {
+        int e;
+        frexpf(__uint_as_float(mx), &e);   // max = f 2^e, 0.5 <= f < 1
+        k2 = 14 - e;
+        k2 = k2 < -60 ? -60 : (k2 > 60 ? 60 : k2);
+    }
+    const float c = ldexpf(1.f, k2);
     double acc = 0.0;
     for (int64_t k = 2 * lane; k < p_pad; k += 64) {
         float v0 = 0.f, v1 = 0.f;
         if (z && k < p) v0 = z[k];
         if (z && k + 1 < p) v1 = z[k + 1];
+        if (!isfinite(v0)) v0 = 0.f;
+        if (!isfinite(v1)) v1 = 0.f;
         acc = fma((double)v0, (double)v0, acc);
         acc = fma((double)v1, (double)v1, acc);
         const float w0 = v0 * c, w1 = v1 * c;
@@ -104,14 +117,17 @@ __global__ void k_split_rows(const float *__restrict__ X, const float *__restric
         *reinterpret_cast<__half2 *>(Zl + i * p_pad + k) = __halves2half2(l0, l1);
     }
     for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
-    if (lane == 0) norms[i] = (float)acc;
+    if (lane == 0) {
+        norms[i] = (float)acc;
+        inv_scale[i] = ldexpf(1.f, -k2);
+    }
 }
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_build_tc(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
                const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl,
                const int4 *__restrict__ tiles, int ntiles, int kblocks, const float *__restrict__ norms,
-               const float *__restrict__ X, const float *__restrict__ Y, int64_t nx, int64_t n, int64_t p,
+               const float *__restrict__ inv_scale, const float *__restrict__ X, const float *__restrict__ Y, int64_t nx, int64_t n, int64_t p,
                int64_t NKB, int stat, float neg_inv_2s2, float tau, float *__restrict__ D, Counters *ctr) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -239,8 +255,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         // ---------------- epilogue: one tile row per thread ----------------
         const int quarter = warp & 3;
         const int rt = quarter * 32 + lane;   // row within the 128-row tile
-        const float cinv = 1.f / gram_scale(ctr);
-        const float inv_c2 = cinv * cinv;     // exact: a power of two
         int acc = 0;
         uint32_t acc_phase = 0;
         unsigned fixups = 0;
@@ -249,6 +263,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const int rp = tile.y * BM + rt;                 // row within panel I
             const int64_t i = (int64_t)tile.x * PANEL + rp;  // pooled row
             const float ni = (i < n) ? norms[i] : 0.f;
+            const float si = (i < n) ? inv_scale[i] : 0.f;
             if (!mbar_wait(su32(&bars->acc_full[acc]), acc_phase, abort_flag, ctr, ERR_WAIT_EPI)) break;
             fence_after();
             const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
@@ -258,17 +273,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 tmem_ld32(tbase + (uint32_t)(g * 32), v);
                 const int64_t j0 = (int64_t)tile.z * PANEL + g * 32;
                 const float nj_l = (j0 + lane < n) ? norms[j0 + lane] : 0.f;
+                const float sj_l = (j0 + lane < n) ? inv_scale[j0 + lane] : 0.f;
                 float out[32];
 #pragma unroll
                 for (int e = 0; e < 32; ++e) {
                     const float nj = __shfl_sync(0xFFFFFFFFu, nj_l, e);
+                    const float sj = __shfl_sync(0xFFFFFFFFu, sj_l, e);
                     const int64_t j = j0 + e;
                     float val = 0.f;
                     if (i < n && j < n) {
                         if (i == j) {
                             val = (stat == 0) ? 0.f : 1.f;
                         } else {
-                            const float d2 = fmaxf(0.f, ni + nj - 2.f * (__uint_as_float(v[e]) * inv_c2));
+                            const float gij = (__uint_as_float(v[e]) * si) * sj;   // exact rescaling
+                            const float d2 = fmaxf(0.f, ni + nj - 2.f * gij);
                             if (d2 < tau * (ni + nj)) {
                                 const float *zi = row_ptr(X, Y, nx, i, p), *zj = row_ptr(X, Y, nx, j, p);
                                 double s = 0.0;
@@ -312,15 +330,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 }  // namespace
 
 void launch_split_rows(const float *X, const float *Y, const Geom &g, int64_t p_pad, uint16_t *Zh, uint16_t *Zl,
-                       float *norms, const Counters *ctr, cudaStream_t s) {
+                       float *norms, float *inv_scale, Counters *ctr, cudaStream_t s) {
     const int warps = 8;
     k_split_rows<<<(unsigned)((g.n_pad + warps - 1) / warps), warps * 32, 0, s>>>(
-        X, Y, g.nx, g.n, g.n_pad, g.p, p_pad, (__half *)Zh, (__half *)Zl, norms, ctr);
+        X, Y, g.nx, g.n, g.n_pad, g.p, p_pad, (__half *)Zh, (__half *)Zl, norms, inv_scale, ctr);
 }
 
 cudaError_t launch_build_tc(const void *tmaps, const int4 *tiles, int ntiles, int64_t p_pad, const float *norms,
-                            const float *X, const float *Y, const Geom &g, int stat, double sigma, double tau, float *D,
-                            Counters *ctr, int num_sms, cudaStream_t s) {
+                            const float *inv_scale, const float *X, const float *Y, const Geom &g, int stat,
+                            double sigma, double tau, float *D, Counters *ctr, int num_sms, cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_build_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
@@ -332,8 +350,8 @@ cudaError_t launch_build_tc(const void *tmaps, const int4 *tiles, int ntiles, in
     const float neg = (stat == 0) ? 0.f : (float)(-1.0 / (2.0 * sigma * sigma));
     const int grid = ntiles < num_sms ? ntiles : num_sms;
     k_build_tc<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(tm[0], tm[1], tm[2], tm[3], tiles, ntiles, (int)(p_pad / BK),
-                                                     norms, X, Y, g.nx, g.n, g.p, g.NKB, stat, neg, (float)tau, D,
-                                                     ctr);
+                                                     norms, inv_scale, X, Y, g.nx, g.n, g.p, g.NKB, stat, neg,
+                                                     (float)tau, D, ctr);
     return cudaGetLastError();
 }
 

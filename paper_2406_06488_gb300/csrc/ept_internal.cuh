@@ -86,7 +86,7 @@ void launch_build_simt(const float *X, const float *Y, const float *norms, const
                        double sigma, double tau, const int2 *blk_info, float *D, Counters *ctr,
                        cudaStream_t s);
 void launch_blocksums(const float *D, const Geom &g, double *rowpart, double *colpart, cudaStream_t s);
-// r: n_pad doubles; Spart, Upart, Stpart: one double per panel (NP)
+// r: n_pad doubles; Spart: n_pad / 32 doubles; Upart, Stpart: one double per panel (NP)
 void launch_rowsum_reduce(const double *rowpart, const double *colpart, const Geom &g, double *r, double *Spart,
                           cudaStream_t s);
 void launch_center(const double *r, const double *Spart, const Geom &g, float *u, double *dcorr, double *Upart,
@@ -116,12 +116,13 @@ bool encode_rows_tmaps(void *tmaps4, const uint16_t *Zh, const uint16_t *Zl, int
 
 // ---- tcgen05 block build (ept_build_tc.cu) ----
 constexpr int BUILD_KB = 64;   // p is padded to a multiple of this
-// Zh, Zl: the scaled FP16 hi / lo parts (the scale comes from ctr->maxabs_bits)
+// Zh, Zl: FP16 hi / lo parts of the rows scaled by per-row powers of two; inv_scale[i]
+// is the inverse scale of row i; non-finite inputs are counted in ctr->nonfinite.
 void launch_split_rows(const float *X, const float *Y, const Geom &g, int64_t p_pad, uint16_t *Zh, uint16_t *Zl,
-                       float *norms, const Counters *ctr, cudaStream_t s);
+                       float *norms, float *inv_scale, Counters *ctr, cudaStream_t s);
 // tiles: (panel I, half h, column panel J >= I); tmaps: the four maps of encode_rows_tmaps
 cudaError_t launch_build_tc(const void *tmaps, const int4 *tiles, int ntiles, int64_t p_pad, const float *norms,
-                            const float *X, const float *Y, const Geom &g, int stat, double sigma, double tau,
-                            float *D, Counters *ctr, int num_sms, cudaStream_t s);
+                            const float *inv_scale, const float *X, const float *Y, const Geom &g, int stat,
+                            double sigma, double tau, float *D, Counters *ctr, int num_sms, cudaStream_t s);
 
 }  // namespace ept

@@ -30,31 +30,16 @@ Geom make_geom(int64_t nx, int64_t ny, int64_t p, int64_t ncols) {
 }
 
 // ---------------------------------------------------------------------------
-// Permutation stream.  Philox4x32-10 (Salmon et al., SC'11): counter words 0 and 2
-// are multiplied by the two Philox multipliers; the high halves are mixed with
-// words 1 and 3 and the round key; the key advances by the two Weyl constants.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        const uint32_t lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x);
-        const uint32_t lo1 = 0xCD9E8D57u * c.z;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-        k.x += 0x9E3779B9u;
-        k.y += 0xBB67AE85u;
-    }
-    return c;
-}
-
-// spread the 16 low bits of v to the even bit positions of a word
-__device__ __forceinline__ uint32_t spread16(uint32_t v) {
-    v &= 0xFFFFu;
-    v = (v | (v << 8)) & 0x00FF00FFu;
-    v = (v | (v << 4)) & 0x0F0F0F0Fu;
-    v = (v | (v << 2)) & 0x33333333u;
-    v = (v | (v << 1)) & 0x55555555u;
-    return v;
+// Permutation stream: Philox4x32-10 (Salmon et al., SC'11) drives Knuth's selection
+// sampling; see k_perm_masks.
+// floor(u * m / 2^64) for a 64-bit u and a 32-bit m, from two 32x32->64 products:
+// with u = uh 2^32 + ul, the value is floor((uh m + floor(ul m / 2^32)) / 2^32)
+// (the dropped low word of ul m cannot carry across a multiple of 2^32), and
+// uh m + floor(ul m / 2^32) < 2^64.  Equal to the high word of the 128-bit product.
+__device__ __forceinline__ uint64_t mulhi_64x32(uint64_t u, uint32_t m) {
+    const uint64_t a = (uint64_t)(uint32_t)(u >> 32) * m;
+    const uint64_t b = (uint64_t)(uint32_t)u * m;
+    return (a + (b >> 32)) >> 32;
 }
 
 // bits of word w that belong to real pooled rows t < n
@@ -65,13 +50,20 @@ __device__ __forceinline__ uint32_t valid_bits(int w, int n) {
     return (1u << (n - lo)) - 1u;
 }
 
-// One warp per relabeling column c.  Draw b = b_first + c of the stream:
+// One warp per relabeling column c.  Philox4x32-10: each round multiplies counter
+// words 0 and 2 by the two Philox multipliers (one wide multiply gives both
+// halves), mixes the high halves with words 1 and 3 and the round key, and the key
+// advances by the two Weyl constants between rounds.
+// Draw b = b_first + c of the stream:
 // b = 0 is the identity; b >= 1 is Knuth's selection sampling (Algorithm S) over
 // the n pooled slots, slot t kept iff floor(u_t * (n - t) / 2^64) < need, with
 // u_t the 64-bit word (t mod 2) of Philox4x32-10(counter = (t/2, 0, b lo, b hi),
-// key = (seed lo, seed hi)).  The 32 lanes draw 64 consecutive slots at once; the
-// sequential dependence through `need` is resolved by a fixed-point iteration
-// over warp ballots: with every earlier decision known, a slot's decision is
+// key = (seed lo, seed hi)).  The warp draws 64 consecutive slots at once: lane l
+// runs the Philox call of slots base+2l and base+2l+1 and forms their two
+// floor(u (n - t) / 2^64) values; shuffles then place slot base+l on lane l (first
+// word) and slot base+32+l on lane l (second word), so one ballot is one output
+// word.  The sequential dependence through `need` is resolved by a fixed-point
+// iteration over ballots: with every earlier decision known a slot's decision is
 // determined, so iterating "decide from the previous guesses" reaches the unique
 // sequential solution in at most 65 rounds (almost always 1 or 2).
 // comp: store the complement (the y* members) of every real draw.
@@ -95,41 +87,61 @@ __global__ void __launch_bounds__(256) k_perm_masks(uint64_t seed, int nx, int n
         }
         return;
     }
-    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    // Philox round keys of this seed (the key schedule adds the two Weyl constants)
+    uint32_t kx[10], ky[10];
+    kx[0] = (uint32_t)seed;
+    ky[0] = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        kx[r] = kx[r - 1] + 0x9E3779B9u;
+        ky[r] = ky[r - 1] + 0xBB67AE85u;
+    }
     const uint32_t blo = (uint32_t)(uint64_t)b, bhi = (uint32_t)((uint64_t)b >> 32);
     const unsigned lt = (1u << lane) - 1u;
+    const int src = lane >> 1;
+    const bool odd = lane & 1;
     int need = nx;
     for (int base = 0; base < nw * 32; base += 64) {
-        const int t0 = base + 2 * lane, t1 = t0 + 1;
-        long long r0 = 0x7FFFFFFFFFFFFFFFLL, r1 = 0x7FFFFFFFFFFFFFFFLL;
-        if (t0 < n && need > 0) {
-            const uint4 w = philox4x32_10(make_uint4((uint32_t)(t0 >> 1), 0u, blo, bhi), key);
-            const uint64_t u0 = ((uint64_t)w.y << 32) | (uint64_t)w.x;
-            r0 = (long long)__umul64hi(u0, (uint64_t)(n - t0));
-            if (t1 < n) {
-                const uint64_t u1 = ((uint64_t)w.w << 32) | (uint64_t)w.z;
-                r1 = (long long)__umul64hi(u1, (uint64_t)(n - t1));
+        const int tp = base + 2 * lane;   // this lane's Philox slots tp, tp + 1
+        uint32_t ra = 0xFFFFFFFFu, rb = 0xFFFFFFFFu;   // "never kept"
+        if (tp < n && need > 0) {
+            uint32_t x0 = (uint32_t)(tp >> 1), x1 = 0u, x2 = blo, x3 = bhi;
+#pragma unroll
+            for (int r = 0; r < 10; ++r) {
+                const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+                const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+                const uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ kx[r];
+                const uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ ky[r];
+                x1 = (uint32_t)p1;
+                x3 = (uint32_t)p0;
+                x0 = y0;
+                x2 = y2;
             }
+            ra = (uint32_t)mulhi_64x32(((uint64_t)x1 << 32) | x0, (uint32_t)(n - tp));
+            if (tp + 1 < n) rb = (uint32_t)mulhi_64x32(((uint64_t)x3 << 32) | x2, (uint32_t)(n - tp - 1));
         }
+        // slot base + lane  <- (ra or rb) of lane lane/2;  slot base + 32 + lane <- of lane 16 + lane/2
+        const uint32_t a0 = __shfl_sync(0xFFFFFFFFu, ra, src), b0 = __shfl_sync(0xFFFFFFFFu, rb, src);
+        const uint32_t a1 = __shfl_sync(0xFFFFFFFFu, ra, src + 16), b1 = __shfl_sync(0xFFFFFFFFu, rb, src + 16);
+        const int r0 = (int)min(odd ? b0 : a0, 0x7FFFFFFFu);
+        const int r1 = (int)min(odd ? b1 : a1, 0x7FFFFFFFu);
         bool s0 = r0 < need, s1 = r1 < need;
+        unsigned m0 = __ballot_sync(0xFFFFFFFFu, s0), m1 = __ballot_sync(0xFFFFFFFFu, s1);
         for (int it = 0; it < 70; ++it) {
-            const unsigned m0 = __ballot_sync(0xFFFFFFFFu, s0);
-            const unsigned m1 = __ballot_sync(0xFFFFFFFFu, s1);
-            const int before = __popc(m0 & lt) + __popc(m1 & lt);
-            const bool n0 = r0 < (long long)(need - before);
-            const bool n1 = r1 < (long long)(need - before - (n0 ? 1 : 0));
-            const unsigned changed = __ballot_sync(0xFFFFFFFFu, (n0 != s0) || (n1 != s1));
-            s0 = n0;
-            s1 = n1;
-            if (changed == 0u) break;
+            const int before0 = __popc(m0 & lt);
+            const int before1 = __popc(m0) + __popc(m1 & lt);
+            const bool n0 = r0 < need - before0;
+            const bool n1 = r1 < need - before1;
+            const unsigned nm0 = __ballot_sync(0xFFFFFFFFu, n0), nm1 = __ballot_sync(0xFFFFFFFFu, n1);
+            const bool same = (nm0 == m0) && (nm1 == m1);
+            m0 = nm0;
+            m1 = nm1;
+            if (same) break;
         }
-        const unsigned m0 = __ballot_sync(0xFFFFFFFFu, s0);
-        const unsigned m1 = __ballot_sync(0xFFFFFFFFu, s1);
         need -= __popc(m0) + __popc(m1);
         if (lane == 0) {
             const int w = base >> 5;
-            uint32_t v0 = spread16(m0) | (spread16(m1) << 1);
-            uint32_t v1 = spread16(m0 >> 16) | (spread16(m1 >> 16) << 1);
+            uint32_t v0 = m0, v1 = m1;
             if (comp) {
                 v0 = ~v0 & valid_bits(w, n);
                 v1 = ~v1 & valid_bits(w + 1, n);
@@ -380,45 +392,57 @@ __global__ void __launch_bounds__(256) k_blocksums(const float *__restrict__ D, 
                                                    double *__restrict__ colpart) {
     __shared__ double cs[8][64];
     const int64_t blk = blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const float *base = D + blk * (int64_t)(PANEL * KB) + (int64_t)(warp * 32) * KB + 2 * lane;
-    float ch0 = 0.f, cl0 = 0.f, ch1 = 0.f, cl1 = 0.f;
-#pragma unroll 1
-    for (int r0 = 0; r0 < 32; r0 += 8) {
-        float2 v[8];
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const float *base = D + blk * (int64_t)(PANEL * KB);
+    // row sums: thread t owns row t (64 contiguous values, no cross-thread traffic)
+    {
+        const float4 *row = reinterpret_cast<const float4 *>(base + (int64_t)t * KB);
+        float4 v[16];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = *reinterpret_cast<const float2 *>(base + (int64_t)(r0 + q) * KB);
+        for (int q = 0; q < 16; ++q) v[q] = row[q];
+        float h = 0.f, l = 0.f;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            float s, e;
-            two_sum(v[q].x, v[q].y, s, e);
+        for (int q = 0; q < 16; ++q) {
+            const float e4[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
 #pragma unroll
-            for (int off = 16; off; off >>= 1) {
-                const float s2 = __shfl_xor_sync(0xFFFFFFFFu, s, off);
-                const float e2 = __shfl_xor_sync(0xFFFFFFFFu, e, off);
-                float t, f;
-                two_sum(s, s2, t, f);
-                s = t;
-                e = (e + e2) + f;
+            for (int k = 0; k < 4; ++k) {
+                float s2, f;
+                two_sum(h, e4[k], s2, f);
+                h = s2;
+                l += f;
             }
-            if (lane == 0) rowpart[blk * PANEL + warp * 32 + r0 + q] = (double)s + (double)e;
-            float t, f;
-            two_sum(ch0, v[q].x, t, f);
-            ch0 = t;
-            cl0 += f;
-            two_sum(ch1, v[q].y, t, f);
-            ch1 = t;
-            cl1 += f;
         }
+        rowpart[blk * PANEL + t] = (double)h + (double)l;
     }
-    cs[warp][2 * lane] = (double)ch0 + (double)cl0;
-    cs[warp][2 * lane + 1] = (double)ch1 + (double)cl1;
+    // column sums: warp w covers rows 32w..32w+31, lane l columns 2l and 2l+1
+    {
+        const float *cbase = base + (int64_t)(warp * 32) * KB + 2 * lane;
+        float ch0 = 0.f, cl0 = 0.f, ch1 = 0.f, cl1 = 0.f;
+#pragma unroll 1
+        for (int r0 = 0; r0 < 32; r0 += 8) {
+            float2 v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = *reinterpret_cast<const float2 *>(cbase + (int64_t)(r0 + q) * KB);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float s2, f;
+                two_sum(ch0, v[q].x, s2, f);
+                ch0 = s2;
+                cl0 += f;
+                two_sum(ch1, v[q].y, s2, f);
+                ch1 = s2;
+                cl1 += f;
+            }
+        }
+        cs[warp][2 * lane] = (double)ch0 + (double)cl0;
+        cs[warp][2 * lane + 1] = (double)ch1 + (double)cl1;
+    }
     __syncthreads();
-    if (threadIdx.x < 64) {
+    if (t < 64) {
         double acc = 0.0;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) acc += cs[w][threadIdx.x];
-        colpart[blk * KB + threadIdx.x] = acc;
+        for (int w = 0; w < 8; ++w) acc += cs[w][t];
+        colpart[blk * KB + t] = acc;
     }
 }
 
@@ -427,33 +451,42 @@ void launch_blocksums(const float *D, const Geom &g, double *rowpart, double *co
 }
 
 // r_i = sum over the stored blocks of row i's panel (its own row segments) + sum
-// over the earlier panels J < panel(i) of column i's segments, in fixed order.
-// One CTA of 256 threads per panel; Spart[panel] = sum of its r_i (fixed tree).
+// over the earlier panels J < panel(i) of column i's segments.  Eight threads per
+// row take every eighth term and combine by a fixed shuffle tree (deterministic).
+// CTA = 32 rows (256 threads); Spart[CTA] = sum of its rows' r_i.
 __global__ void __launch_bounds__(256) k_rowsum_reduce(const double *__restrict__ rowpart,
                                                        const double *__restrict__ colpart, int64_t n, int64_t NKB,
                                                        double *__restrict__ r, double *__restrict__ Spart) {
-    __shared__ double sh[256];
-    const int64_t I = blockIdx.x, rr = threadIdx.x;
-    const int64_t i = I * PANEL + rr;
+    __shared__ double sh[32];
+    const int sub = threadIdx.x & 7, rl = threadIdx.x >> 3;
+    const int64_t i = (int64_t)blockIdx.x * 32 + rl;
+    const int64_t I = i / PANEL, rr = i % PANEL;
     double acc = 0.0;
     if (i < n) {
-        for (int64_t kb = KB_PER_PANEL * I; kb < NKB; ++kb) acc += rowpart[blk_index(I, kb, NKB) * PANEL + rr];
+        const int64_t nkb = NKB - KB_PER_PANEL * I;          // stored K-blocks of panel I
+        const int64_t base = blk_off(I, NKB);
+        for (int64_t k = sub; k < nkb; k += 8) acc += rowpart[(base + k) * PANEL + rr];
         const int64_t kbi = i / KB, ci = i % KB;
-        for (int64_t J = 0; J < I; ++J) acc += colpart[blk_index(J, kbi, NKB) * KB + ci];
+        for (int64_t J = sub; J < I; J += 8) acc += colpart[blk_index(J, kbi, NKB) * KB + ci];
     }
-    r[i] = acc;
-    sh[rr] = acc;
+    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 4);
+    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
+    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
+    if (sub == 0) {
+        r[i] = acc;
+        sh[rl] = acc;
+    }
     __syncthreads();
-    for (int off = 128; off; off >>= 1) {
-        if (rr < off) sh[rr] += sh[rr + off];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < 32; ++k) s += sh[k];
+        Spart[blockIdx.x] = s;
     }
-    if (rr == 0) Spart[I] = sh[0];
 }
 
 void launch_rowsum_reduce(const double *rowpart, const double *colpart, const Geom &g, double *r, double *Spart,
                           cudaStream_t s) {
-    k_rowsum_reduce<<<(unsigned)g.NP, 256, 0, s>>>(rowpart, colpart, g.n, g.NKB, r, Spart);
+    k_rowsum_reduce<<<(unsigned)(g.n_pad / 32), 256, 0, s>>>(rowpart, colpart, g.n, g.NKB, r, Spart);
 }
 
 // Deterministic sum of a short array in fixed order.
@@ -488,10 +521,13 @@ __device__ __forceinline__ double block_sum_256(double v, double *sh) {
 // may be any value, so it is formed with multiplications by precomputed reciprocals.
 // Step 1 (one CTA per panel): u_i, Upart[panel] = sum of the u_i as doubles.
 __global__ void __launch_bounds__(256) k_center_u(const double *__restrict__ r, const double *__restrict__ Spart,
-                                                  int64_t NP, int64_t n, double inv_n, double inv_2n2,
+                                                  int64_t nS, int64_t n, double inv_n, double inv_2n2,
                                                   float *__restrict__ u, double *__restrict__ Upart) {
     __shared__ double sh[256];
-    const double S = ordered_sum(Spart, NP);
+    __shared__ double bS;
+    if (threadIdx.x == 0) bS = ordered_sum(Spart, nS);
+    __syncthreads();
+    const double S = bS;
     const int64_t i = (int64_t)blockIdx.x * PANEL + threadIdx.x;
     float ui = 0.f;
     if (i < n) ui = (float)(r[i] * inv_n - S * inv_2n2);
@@ -508,7 +544,10 @@ __global__ void __launch_bounds__(256) k_center_r(const double *__restrict__ r, 
                                                   double *__restrict__ dcorr, double *__restrict__ Stpart,
                                                   StatConst *sc) {
     __shared__ double sh[256];
-    const double U = ordered_sum(Upart, NP);
+    __shared__ double bU;
+    if (threadIdx.x == 0) bU = ordered_sum(Upart, NP);
+    __syncthreads();
+    const double U = bU;
     const int64_t i = (int64_t)blockIdx.x * PANEL + threadIdx.x;
     double rt = 0.0;
     if (i < n) rt = r[i] - (double)n * (double)u[i] - U;
@@ -529,7 +568,8 @@ void launch_center(const double *r, const double *Spart, const Geom &g, float *u
                    double *Stpart, StatConst *sc, int stat, cudaStream_t s) {
     const double fn = (double)g.n;
     const double q = fn / ((double)g.nx * (double)g.ny);
-    k_center_u<<<(unsigned)g.NP, 256, 0, s>>>(r, Spart, g.NP, g.n, 1.0 / fn, 1.0 / (2.0 * fn * fn), u, Upart);
+    k_center_u<<<(unsigned)g.NP, 256, 0, s>>>(r, Spart, g.n_pad / 32, g.n, 1.0 / fn, 1.0 / (2.0 * fn * fn), u,
+                                             Upart);
     k_center_r<<<(unsigned)g.NP, 256, 0, s>>>(r, u, Upart, g.NP, g.n, 2.0 * (double)g.m / fn, q * q,
                                              1.0 / ((double)g.other * (double)g.other), stat == 0 ? -1.0 : 1.0, dcorr,
                                              Stpart, sc);
@@ -677,15 +717,23 @@ void launch_contract_simt(const float *C, const uint32_t *maskT, const Chunk *ch
 // column b, Q_b = sum of its partials in fixed order (FP64), stat_b =
 // sign * (cT Q_b + S~/o^2).  Then, against stat_0 (the identity, evaluated by the
 // same kernels), count stat_b >= stat_0 and near-ties |stat_b - stat_0| <= 1e-5 |stat_0|.
-__global__ void k_combine_stats(const float *__restrict__ partial, int64_t nparts, int64_t Bp, int64_t ncols,
-                                const StatConst *__restrict__ sc, const double *__restrict__ Stpart, int64_t NP,
-                                double *__restrict__ stats) {
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= ncols) return;
-    const double St = ordered_sum(Stpart, NP);
-    double q = 0.0;
-    for (int64_t k = 0; k < nparts; ++k) q += (double)partial[k * Bp + b];
-    stats[b] = sc->sign * (sc->cT * q + St * sc->inv_o2);
+__global__ void __launch_bounds__(256) k_combine_stats(const float *__restrict__ partial, int64_t nparts, int64_t Bp,
+                                                       int64_t ncols, const StatConst *__restrict__ sc,
+                                                       const double *__restrict__ Stpart, int64_t NP,
+                                                       double *__restrict__ stats) {
+    // four threads per column: thread q of a column sums partials q, q+4, ...; the
+    // four sums are combined by a fixed shuffle tree (deterministic)
+    __shared__ double bSt;
+    if (threadIdx.x == 0) bSt = ordered_sum(Stpart, NP);
+    __syncthreads();
+    const int q = threadIdx.x & 3;
+    const int64_t b = (int64_t)blockIdx.x * 64 + (threadIdx.x >> 2);
+    double acc = 0.0;
+    if (b < ncols)
+        for (int64_t k = q; k < nparts; k += 4) acc += (double)partial[k * Bp + b];
+    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
+    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
+    if (b < ncols && q == 0) stats[b] = sc->sign * (sc->cT * acc + bSt * sc->inv_o2);
 }
 
 __global__ void k_combine_count(const double *__restrict__ stats, int64_t ncols, Counters *ctr) {
@@ -707,9 +755,9 @@ __global__ void k_combine_count(const double *__restrict__ stats, int64_t ncols,
 
 void launch_combine(const float *partial, int64_t nparts, const Geom &g, const StatConst *sc,
                     const double *Stpart, double *stats, Counters *ctr, cudaStream_t s) {
-    const unsigned grid = (unsigned)((g.ncols + 255) / 256);
-    k_combine_stats<<<grid, 256, 0, s>>>(partial, nparts, g.Bp, g.ncols, sc, Stpart, g.NP, stats);
-    k_combine_count<<<grid, 256, 0, s>>>(stats, g.ncols, ctr);
+    k_combine_stats<<<(unsigned)((g.ncols + 63) / 64), 256, 0, s>>>(partial, nparts, g.Bp, g.ncols, sc, Stpart, g.NP,
+                                                                   stats);
+    k_combine_count<<<(unsigned)((g.ncols + 255) / 256), 256, 0, s>>>(stats, g.ncols, ctr);
 }
 
 // ---------------------------------------------------------------------------

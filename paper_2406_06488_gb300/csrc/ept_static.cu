@@ -75,7 +75,7 @@ StaticPlan static_plan(const Geom &g) {
     P.u = take((size_t)g.n_pad * 4);
     P.dcorr = take((size_t)g.n_pad * 8);
     P.sc = take(sizeof(StatConst));
-    P.Spart = take((size_t)g.NP * 8);
+    P.Spart = take((size_t)(g.n_pad / 32) * 8);
     P.Upart = take((size_t)g.NP * 8);
     P.Stpart = take((size_t)g.NP * 8);
     P.hi = take(elems * 2);
