@@ -125,6 +125,31 @@ ept_status ept_test_masks(ept_ctx *ctx, const float *X, int64_t nx, const float 
                           const uint32_t *masks, int64_t n_masks, int prec,
                           double *perm_stats, ept_result *out, void *stream);
 
+/* One test of a batch (ept_test_batch): the arguments of ept_test. */
+typedef struct {
+    const float *X;        /* nx * p floats, row-major */
+    const float *Y;        /* ny * p floats, row-major */
+    int64_t nx, ny, p;
+    int stat;              /* ept_stat */
+    double sigma;          /* Gaussian bandwidth (MMD) */
+    int64_t B;             /* permutations */
+    uint64_t seed;         /* permutation-stream seed */
+    double *perm_stats;    /* B doubles or NULL */
+} ept_test_desc;
+
+/* Many independent tests of different sizes in one batched run (Algorithm 1 for
+   each): every phase is one launch over all tests (the tests' work units share the
+   GPU), and a repeated call with the same shapes on the context's own stream
+   (stream = NULL) replays the captured CUDA graph of the whole run.  Per-test
+   results go to results[0 .. n_tests-1]; each test's draws come from its own
+   seed exactly as in ept_test, and the statistics equal ept_test's within
+   rounding.  on_device applies to every X, Y and perm_stats of the batch.
+   The contraction's chunk length is autotuned on the first call for a batch shape
+   (environment: EPT_AUTOTUNE=0 disables it; EPT_AUTOTUNE_CACHE=<file> keeps the
+   choices across processes). */
+ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_tests, int on_device,
+                          int prec, ept_result *results, void *stream);
+
 /* Draws b0 .. b0+count-1 of the permutation stream of `seed` (Algorithm 2's
    SampleWithoutReplacement, fixed as Philox4x32-10 + Knuth's selection sampling;
    draw 0 is the identity), generated on the GPU, written row-major as in

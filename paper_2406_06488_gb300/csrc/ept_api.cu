@@ -1,13 +1,17 @@
 // ept_api.cu -- host side of the libept C ABI (include/ept.h): contexts, device
-// scratch, validation, and the order of the kernels of one permutation test.
+// scratch, validation, batch planning, the order of the kernels of a batched run,
+// CUDA-graph replay of repeated batches, and the contraction-chunk autotuner.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -40,68 +44,199 @@ ept_status fail(ept_status st, const char *fmt, ...) {
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-// Device scratch layout of one test, as byte offsets into the context's arena.
-struct Plan {
-    Geom g;
-    int prec;
-    bool host_in;
-    int64_t n_user_masks;
-    size_t off_X, off_Y, off_norms, off_blkinfo, off_chunks, off_D, off_rowpart, off_colpart, off_r, off_u,
-        off_dcorr, off_sc, off_hi, off_lo, off_maskT, off_umask, off_partial, off_stats, off_ctr, total;
-    size_t off_zh, off_zl, off_tiles, off_Spart, off_Upart, off_Stpart, off_iscale;
-    int64_t nparts, p_pad, ntiles;
+// pairs with d^2 < tau (||x||^2 + ||y||^2) are recomputed directly in FP64: the norm
+// expansion amplifies rounding by at most 1/tau on the pairs it keeps
+const double NEAR_DUP_TAU = 1.0 / 4.0;
+const int CHUNK_CANDIDATES[3] = {8, 16, 32};
+
+// Host description of one test of a batch.
+struct TestSpec {
+    const float *X, *Y;
+    int64_t nx, ny, p, B;
+    int stat;
+    double sigma;
+    uint64_t seed;
+    const uint32_t *user_masks;   // B relabelings (ept_test_masks), same memory space as X
+    double *perm_stats;           // B doubles or null, same memory space as X
 };
 
-Plan make_plan(const Geom &g, int prec, bool host_in, int64_t n_user_masks) {
-    Plan P;
-    P.g = g;
+ept_status validate(int64_t nx, int64_t ny, int64_t p, int stat, double sigma, int prec) {
+    if (nx < 1 || ny < 1) return fail(EPT_EINVAL, "nx and ny must be >= 1 (got %lld, %lld)", (long long)nx, (long long)ny);
+    if (p < 1) return fail(EPT_EINVAL, "p must be >= 1 (got %lld)", (long long)p);
+    if (nx + ny > (int64_t)1 << 22) return fail(EPT_EINVAL, "nx + ny = %lld exceeds 2^22", (long long)(nx + ny));
+    if (stat != EPT_STAT_ED && stat != EPT_STAT_MMD_GAUSS) return fail(EPT_EINVAL, "unknown statistic %d", stat);
+    if (stat == EPT_STAT_MMD_GAUSS && !(sigma > 0.0 && std::isfinite(sigma)))
+        return fail(EPT_EINVAL, "MMD needs a finite bandwidth sigma > 0");
+    if (prec != EPT_PREC_PLAIN_FP32 && prec != EPT_PREC_SPLIT_BF16) return fail(EPT_EINVAL, "unknown precision %d", prec);
+    return EPT_OK;
+}
+
+// Geometry, offsets, tables and device-scratch layout of one batched run.
+struct Plan {
+    int n_tests = 0;
+    int prec = 0;
+    bool host_in = false;
+    std::vector<TestDesc> desc;
+    std::vector<int64_t> pre_rows, pre_panels, pre_cols, pre_units, pre_simt;
+    std::vector<BlkInfo> blk;
+    std::vector<Tile> tiles;
+    std::vector<Chunk> chunks;
+    std::vector<size_t> in_off;       // per test: byte offset of its X (then Y, then masks) in the input region
+    int64_t nrows = 0, npan = 0, ncols_pad = 0, nunits = 0, nsimt = 0, nblk = 0, nmask = 0, nchunk = 0, npart = 0,
+            nstats = 0, p_stride = 0;
+    size_t in_bytes = 0;              // host inputs copied into the arena
+    // byte offsets in the arena; the first tab_bytes are the uploaded tables
+    size_t off_desc, off_pre_rows, off_pre_panels, off_pre_cols, off_pre_units, off_pre_simt, off_blk, off_tiles,
+        off_chunks, tab_bytes;
+    size_t off_in, off_norms, off_iscale, off_u, off_Zh, off_Zl, off_D, off_Chi, off_Clo, off_rowpart, off_colpart,
+        off_r, off_Spart, off_dcorr, off_Upart, off_Stpart, off_maskT, off_partial, off_stats, off_observed, off_ctr,
+        total;
+};
+
+void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host_in, int chunk_kb) {
+    P = Plan();
+    P.n_tests = (int)specs.size();
     P.prec = prec;
     P.host_in = host_in;
-    P.n_user_masks = n_user_masks;
+    const bool tc = prec == EPT_PREC_SPLIT_BF16;
+    auto push_pre = [](std::vector<int64_t> &v, int64_t add) { v.push_back(v.back() + add); };
+    P.pre_rows = P.pre_panels = P.pre_cols = P.pre_units = P.pre_simt = std::vector<int64_t>(1, 0);
+    size_t in_bytes = 0;
+    for (int t = 0; t < P.n_tests; ++t) {
+        const TestSpec &s = specs[t];
+        TestDesc d;
+        memset(&d, 0, sizeof(d));
+        d.nx = s.nx;
+        d.ny = s.ny;
+        d.n = s.nx + s.ny;
+        d.p = s.p;
+        d.B = s.B;
+        d.n_pad = (d.n + PANEL - 1) / PANEL * PANEL;
+        d.NP = d.n_pad / PANEL;
+        d.NKB = d.n_pad / KB;
+        d.nblk = blk_off(d.NP, d.NKB);
+        d.nw = d.n_pad / 32;
+        d.nwu = (int)((d.n + 31) / 32);
+        d.ncols = s.B + 1;
+        d.Bp = (d.ncols + COL_PAD - 1) / COL_PAD * COL_PAD;
+        d.MT = d.Bp / TC_TILE_M;
+        d.p_pad = (d.p + BUILD_KB - 1) / BUILD_KB * BUILD_KB;
+        d.kblocks = (int)(d.p_pad / BUILD_KB);
+        d.comp = d.ny < d.nx;
+        d.m = d.comp ? d.ny : d.nx;
+        d.other = d.comp ? d.nx : d.ny;
+        d.stat = s.stat;
+        d.seed = s.seed;
+        d.neg_inv_2s2 = (s.stat == EPT_STAT_ED) ? 0.f : (float)(-1.0 / (2.0 * s.sigma * s.sigma));
+        d.tau = (float)NEAR_DUP_TAU;
+        const double fn = (double)d.n, q = fn / ((double)d.nx * (double)d.ny);
+        d.cT = q * q;
+        d.inv_o2 = 1.0 / ((double)d.other * (double)d.other);
+        d.sign = (s.stat == EPT_STAT_ED) ? -1.0 : 1.0;
+        d.kappa = 2.0 * (double)d.m / fn;
+        d.inv_n = 1.0 / fn;
+        d.inv_2n2 = 1.0 / (2.0 * fn * fn);
+        d.row0 = P.nrows;
+        d.blk0 = P.nblk;
+        d.pan0 = P.npan;
+        d.sp0 = P.nrows / 32;
+        d.mask0 = P.nmask;
+        d.chunk0 = P.nchunk;
+        d.col0 = P.nstats;
+        for (int64_t I = 0; I < d.NP; ++I) {
+            for (int64_t kb = KB_PER_PANEL * I; kb < d.NKB; ++kb) P.blk.push_back(BlkInfo{t, (int)I, (int)kb, 0});
+            for (int64_t kb = KB_PER_PANEL * I; kb < d.NKB; kb += chunk_kb)
+                P.chunks.push_back(Chunk{(int)I, (int)kb, (int)std::min<int64_t>(kb + chunk_kb, d.NKB), 0});
+            if (tc)
+                for (int64_t J = I; J < d.NP; ++J)
+                    for (int h = 0; h < 2; ++h) P.tiles.push_back(Tile{t, (int)I, (int)J, h});
+        }
+        d.nchunks = (int64_t)P.chunks.size() - d.chunk0;
+        d.nparts = tc ? d.nchunks : 2 * d.nchunks;
+        d.part0 = P.npart;
+        P.nrows += d.n_pad;
+        P.nblk += d.nblk;
+        P.npan += d.NP;
+        P.nmask += d.nw * d.Bp;
+        P.nchunk += d.nchunks;
+        P.npart += d.nparts * d.Bp;
+        P.nstats += d.ncols;
+        P.p_stride = std::max(P.p_stride, d.p_pad);
+        push_pre(P.pre_rows, d.n_pad);
+        push_pre(P.pre_panels, d.NP);
+        push_pre(P.pre_cols, d.Bp);
+        push_pre(P.pre_units, d.nchunks * d.MT);
+        push_pre(P.pre_simt, d.nchunks * 2 * (d.Bp / 64));
+        P.in_off.push_back(in_bytes);
+        if (host_in) {
+            in_bytes += align_up((size_t)d.nx * d.p * 4, 256) + align_up((size_t)d.ny * d.p * 4, 256);
+            if (s.user_masks) in_bytes += align_up((size_t)s.B * d.nwu * 4, 256);
+        }
+        P.desc.push_back(d);
+    }
+    P.ncols_pad = P.pre_cols.back();
+    P.nunits = P.pre_units.back();
+    P.nsimt = P.pre_simt.back();
+    P.in_bytes = in_bytes;
+
     size_t o = 0;
     auto take = [&](size_t bytes) {
         const size_t at = o;
-        o = align_up(o + std::max<size_t>(bytes, 1), 1024);
+        o = align_up(o + std::max<size_t>(bytes, 1), 256);
         return at;
     };
-    const size_t blk_elems = (size_t)g.nblk * PANEL * KB;
-    P.off_X = host_in ? take((size_t)g.nx * g.p * 4) : 0;
-    P.off_Y = host_in ? take((size_t)g.ny * g.p * 4) : 0;
-    P.off_norms = take((size_t)g.n_pad * 4);
-    P.off_blkinfo = take((size_t)g.nblk * sizeof(int2));
-    P.off_chunks = take((size_t)g.nchunks * sizeof(Chunk));
-    P.off_D = take(blk_elems * 4);
-    P.off_rowpart = take((size_t)g.nblk * PANEL * 8);
-    P.off_colpart = take((size_t)g.nblk * KB * 8);
-    P.off_r = take((size_t)g.n_pad * 8);
-    P.off_u = take((size_t)g.n_pad * 4);
-    P.off_dcorr = take((size_t)g.n_pad * 8);
-    P.off_sc = take(sizeof(StatConst));
-    P.off_Spart = take((size_t)(g.n_pad / 32) * 8);
-    P.off_iscale = take((size_t)g.n_pad * 4);
-    P.off_Upart = take((size_t)g.NP * 8);
-    P.off_Stpart = take((size_t)g.NP * 8);
-    P.p_pad = (g.p + BUILD_KB - 1) / BUILD_KB * BUILD_KB;
-    P.ntiles = g.NP * (g.NP + 1);
-    if (prec == EPT_PREC_SPLIT_BF16) {
-        P.off_hi = take(blk_elems * 2);
-        P.off_lo = take(blk_elems * 2);
-        P.off_zh = take((size_t)g.n_pad * P.p_pad * 2);
-        P.off_zl = take((size_t)g.n_pad * P.p_pad * 2);
-        P.off_tiles = take((size_t)P.ntiles * sizeof(int4));
-    } else {
-        P.off_hi = P.off_lo = 0;
-        P.off_zh = P.off_zl = P.off_tiles = 0;
-    }
-    P.off_maskT = take((size_t)g.nw * g.Bp * 4);
-    const int64_t nwu = (g.n + 31) / 32;
-    P.off_umask = (host_in && n_user_masks > 0) ? take((size_t)n_user_masks * nwu * 4) : 0;
-    P.nparts = (prec == EPT_PREC_SPLIT_BF16) ? g.nchunks : 2 * g.nchunks;
-    P.off_partial = take((size_t)P.nparts * g.Bp * 4);
-    P.off_stats = take((size_t)g.ncols * 8);
-    P.off_ctr = take(sizeof(Counters));
+    const size_t nt1 = (size_t)P.n_tests + 1;
+    P.off_desc = take(sizeof(TestDesc) * P.n_tests);
+    P.off_pre_rows = take(8 * nt1);
+    P.off_pre_panels = take(8 * nt1);
+    P.off_pre_cols = take(8 * nt1);
+    P.off_pre_units = take(8 * nt1);
+    P.off_pre_simt = take(8 * nt1);
+    P.off_blk = take(sizeof(BlkInfo) * P.blk.size());
+    P.off_tiles = take(sizeof(Tile) * P.tiles.size());
+    P.off_chunks = take(sizeof(Chunk) * P.chunks.size());
+    P.tab_bytes = o;
+    o = align_up(o, 1024);
+    const size_t elems = (size_t)P.nblk * PANEL * KB;
+    P.off_in = take(P.in_bytes);
+    P.off_norms = take((size_t)P.nrows * 4);
+    P.off_iscale = take((size_t)P.nrows * 4);
+    P.off_u = take((size_t)P.nrows * 4);
+    P.off_Zh = tc ? take((size_t)P.nrows * P.p_stride * 2) : 0;
+    P.off_Zl = tc ? take((size_t)P.nrows * P.p_stride * 2) : 0;
+    P.off_D = take(elems * 4);
+    P.off_Chi = tc ? take(elems * 2) : 0;
+    P.off_Clo = tc ? take(elems * 2) : 0;
+    P.off_rowpart = take((size_t)P.nblk * PANEL * 8);
+    P.off_colpart = take((size_t)P.nblk * KB * 8);
+    P.off_r = take((size_t)P.nrows * 8);
+    P.off_Spart = take((size_t)(P.nrows / 32) * 8);
+    P.off_dcorr = take((size_t)P.nrows * 8);
+    P.off_Upart = take((size_t)P.npan * 8);
+    P.off_Stpart = take((size_t)P.npan * 8);
+    P.off_maskT = take((size_t)P.nmask * 4);
+    P.off_partial = take((size_t)P.npart * 4);
+    P.off_stats = take((size_t)P.nstats * 8);
+    P.off_observed = take((size_t)P.n_tests * 8);
+    P.off_ctr = take(sizeof(Counters) * P.n_tests);
     P.total = o;
-    return P;
+}
+
+std::vector<TestSpec> one_test(const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p, int stat,
+                               double sigma, int64_t B, uint64_t seed, const uint32_t *masks, double *perm_stats) {
+    TestSpec s;
+    s.X = X;
+    s.Y = Y;
+    s.nx = nx;
+    s.ny = ny;
+    s.p = p;
+    s.B = B;
+    s.stat = stat;
+    s.sigma = sigma;
+    s.seed = seed;
+    s.user_masks = masks;
+    s.perm_stats = perm_stats;
+    return std::vector<TestSpec>(1, s);
 }
 
 }  // namespace
@@ -111,22 +246,30 @@ namespace ept {
 void set_last_error(const char *msg) { g_err = msg; }
 }  // namespace ept
 
+struct GraphCache {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int64_t> key;    // shapes + precision + memory space + chunk length
+    uint8_t *arena = nullptr;
+    cudaStream_t stream = nullptr;
+};
+
 struct ept_ctx {
     int device = 0;
     int num_sms = 0;
     size_t budget = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;        // relabeling draws run here, beside the block build
-    cudaEvent_t ev_side[3] = {};        // fork, draws start, draws done
+    cudaEvent_t ev[7] = {};
+    cudaEvent_t ev_side[3] = {};
     std::mutex mu;
     uint8_t *arena = nullptr;
     size_t arena_cap = 0;
     uint8_t *pinned = nullptr;
     size_t pinned_cap = 0;
-    cudaEvent_t ev[7] = {};
-    std::vector<int2> h_blkinfo;
-    std::vector<Chunk> h_chunks;
-    std::vector<int4> h_tiles;
+    GraphCache graph;
+    std::map<std::vector<int64_t>, int> tuned_chunk;   // autotuner cache: batch shape -> chunk length
+    bool autotune = true;
+    std::string tune_file;
 };
 
 namespace {
@@ -142,12 +285,19 @@ struct DeviceGuard {
     }
 };
 
+void drop_graph(ept_ctx *c) {
+    if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
+    c->graph = GraphCache();
+}
+
 ept_status ensure_arena(ept_ctx *c, size_t bytes, cudaStream_t s) {
     if (c->budget && bytes > c->budget)
-        return fail(EPT_ENOMEM, "test needs %zu bytes of device scratch, over the context budget of %zu", bytes,
+        return fail(EPT_ENOMEM, "this run needs %zu bytes of device scratch, over the context budget of %zu", bytes,
                     c->budget);
     if (bytes <= c->arena_cap) return EPT_OK;
     CK(cudaStreamSynchronize(s));
+    CK(cudaStreamSynchronize(c->stream));
+    drop_graph(c);
     if (c->arena) {
         cudaFree(c->arena);
         c->arena = nullptr;
@@ -166,6 +316,7 @@ ept_status ensure_arena(ept_ctx *c, size_t bytes, cudaStream_t s) {
 
 ept_status ensure_pinned(ept_ctx *c, size_t bytes) {
     if (bytes <= c->pinned_cap) return EPT_OK;
+    drop_graph(c);   // a captured graph reads the old staging area
     if (c->pinned) cudaFreeHost(c->pinned);
     c->pinned = nullptr;
     c->pinned_cap = 0;
@@ -180,244 +331,358 @@ ept_status ensure_pinned(ept_ctx *c, size_t bytes) {
     return EPT_OK;
 }
 
-bool is_pinned_host(const void *p) {
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return a.type == cudaMemoryTypeHost;
+// Pinned staging layout: [tables (tab_bytes)] [inputs (in_bytes)] [results].
+struct Staging {
+    size_t tables, inputs, res_ctr, res_obs, res_stats, total;
+};
+
+Staging staging_layout(const Plan &P) {
+    Staging S;
+    size_t o = 0;
+    S.tables = o;
+    o = align_up(o + P.tab_bytes, 256);
+    S.inputs = o;
+    o = align_up(o + P.in_bytes, 256);
+    S.res_ctr = o;
+    o = align_up(o + sizeof(Counters) * P.n_tests, 256);
+    S.res_obs = o;
+    o = align_up(o + 8 * (size_t)P.n_tests, 256);
+    S.res_stats = o;
+    o = align_up(o + (P.host_in ? 8 * (size_t)P.nstats : 0), 256);
+    S.total = o;
+    return S;
 }
 
-// host -> device copy of `bytes` from `src`, through the pinned staging area at
-// `stage` when src is pageable
-ept_status h2d(void *dst, const void *src, size_t bytes, uint8_t *stage, cudaStream_t s) {
-    if (bytes == 0) return EPT_OK;
-    if (is_pinned_host(src)) {
-        CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, s));
-    } else {
-        memcpy(stage, src, bytes);
-        CK(cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyHostToDevice, s));
-    }
-    return EPT_OK;
-}
-
-ept_status validate(int64_t nx, int64_t ny, int64_t p, int stat, double sigma, int prec) {
-    if (nx < 1 || ny < 1) return fail(EPT_EINVAL, "nx and ny must be >= 1 (got %lld, %lld)", (long long)nx, (long long)ny);
-    if (p < 1) return fail(EPT_EINVAL, "p must be >= 1 (got %lld)", (long long)p);
-    if (nx + ny > (int64_t)1 << 22) return fail(EPT_EINVAL, "nx + ny = %lld exceeds 2^22", (long long)(nx + ny));
-    if (stat != EPT_STAT_ED && stat != EPT_STAT_MMD_GAUSS) return fail(EPT_EINVAL, "unknown statistic %d", stat);
-    if (stat == EPT_STAT_MMD_GAUSS && !(sigma > 0.0 && std::isfinite(sigma)))
-        return fail(EPT_EINVAL, "MMD needs a finite bandwidth sigma > 0");
-    if (prec != EPT_PREC_PLAIN_FP32 && prec != EPT_PREC_SPLIT_BF16) return fail(EPT_EINVAL, "unknown precision %d", prec);
-    return EPT_OK;
-}
-
-void fill_tables(ept_ctx *c, const Geom &g) {
-    c->h_blkinfo.resize((size_t)g.nblk);
-    c->h_chunks.clear();
-    c->h_tiles.clear();
-    for (int64_t I = 0; I < g.NP; ++I)
-        for (int64_t J = I; J < g.NP; ++J)
-            for (int h = 0; h < 2; ++h) c->h_tiles.push_back(make_int4((int)I, h, (int)J, 0));
-    for (int64_t I = 0; I < g.NP; ++I) {
-        for (int64_t kb = KB_PER_PANEL * I; kb < g.NKB; ++kb)
-            c->h_blkinfo[(size_t)blk_index(I, kb, g.NKB)] = make_int2((int)I, (int)kb);
-        for (int64_t kb = KB_PER_PANEL * I; kb < g.NKB; kb += CHUNK_KB) {
-            Chunk ch;
-            ch.I = (int)I;
-            ch.kb0 = (int)kb;
-            ch.kb1 = (int)std::min<int64_t>(kb + CHUNK_KB, g.NKB);
-            ch.pad = 0;
-            c->h_chunks.push_back(ch);
+// Host-side staging of one run: device pointers into the descriptors, tables and
+// (host inputs) the input rows into the pinned area.  Everything the device work
+// reads from the host goes through this area, so a captured graph can be replayed
+// after re-staging.
+void stage_host(ept_ctx *c, Plan &P, const std::vector<TestSpec> &specs, bool on_device) {
+    const Staging S = staging_layout(P);
+    uint8_t *A = c->arena, *pin = c->pinned;
+    for (int t = 0; t < P.n_tests; ++t) {
+        TestDesc &d = P.desc[t];
+        const TestSpec &s = specs[t];
+        if (on_device) {
+            d.X = s.X;
+            d.Y = s.Y;
+            d.user_masks = s.user_masks;
+            d.out_stats = s.perm_stats;
+        } else {
+            const size_t xo = P.in_off[t], yo = xo + align_up((size_t)d.nx * d.p * 4, 256);
+            const size_t mo = yo + align_up((size_t)d.ny * d.p * 4, 256);
+            memcpy(pin + S.inputs + xo, s.X, (size_t)d.nx * d.p * 4);
+            memcpy(pin + S.inputs + yo, s.Y, (size_t)d.ny * d.p * 4);
+            d.X = (const float *)(A + P.off_in + xo);
+            d.Y = (const float *)(A + P.off_in + yo);
+            if (s.user_masks) {
+                memcpy(pin + S.inputs + mo, s.user_masks, (size_t)s.B * d.nwu * 4);
+                d.user_masks = (const uint32_t *)(A + P.off_in + mo);
+            } else {
+                d.user_masks = nullptr;
+            }
+            d.out_stats = nullptr;   // copied back to the host and scattered there
         }
     }
+    uint8_t *tab = pin + S.tables;
+    memcpy(tab + P.off_desc, P.desc.data(), sizeof(TestDesc) * P.n_tests);
+    memcpy(tab + P.off_pre_rows, P.pre_rows.data(), 8 * P.pre_rows.size());
+    memcpy(tab + P.off_pre_panels, P.pre_panels.data(), 8 * P.pre_panels.size());
+    memcpy(tab + P.off_pre_cols, P.pre_cols.data(), 8 * P.pre_cols.size());
+    memcpy(tab + P.off_pre_units, P.pre_units.data(), 8 * P.pre_units.size());
+    memcpy(tab + P.off_pre_simt, P.pre_simt.data(), 8 * P.pre_simt.size());
+    if (!P.blk.empty()) memcpy(tab + P.off_blk, P.blk.data(), sizeof(BlkInfo) * P.blk.size());
+    if (!P.tiles.empty()) memcpy(tab + P.off_tiles, P.tiles.data(), sizeof(Tile) * P.tiles.size());
+    if (!P.chunks.empty()) memcpy(tab + P.off_chunks, P.chunks.data(), sizeof(Chunk) * P.chunks.size());
 }
 
-const double NEAR_DUP_TAU = 1.0 / 16.0;
-
-// Phase 1: blocks, centring constants and the packed contraction operand.
-ept_status run_blocks(ept_ctx *c, const Plan &P, const float *X, const float *Y, int stat, double sigma,
-                      bool pack, cudaStream_t s) {
-    const Geom &g = P.g;
+Batch device_view(ept_ctx *c, const Plan &P) {
     uint8_t *A = c->arena;
-    float *norms = (float *)(A + P.off_norms);
-    int2 *blkinfo = (int2 *)(A + P.off_blkinfo);
-    float *D = (float *)(A + P.off_D);
-    Counters *ctr = (Counters *)(A + P.off_ctr);
-    if (P.prec == EPT_PREC_SPLIT_BF16) {
-        uint16_t *zh = (uint16_t *)(A + P.off_zh), *zl = (uint16_t *)(A + P.off_zl);
-        float *iscale = (float *)(A + P.off_iscale);
-        launch_split_rows(X, Y, g, P.p_pad, zh, zl, norms, iscale, ctr, s);   // also counts non-finite inputs
-        alignas(64) CUtensorMap tm[4];
-        char emsg[160];
-        if (!encode_rows_tmaps(tm, zh, zl, g.n_pad, P.p_pad, emsg, sizeof(emsg))) return fail(EPT_ECUDA, "%s", emsg);
-        CK(launch_build_tc(tm, (const int4 *)(A + P.off_tiles), (int)P.ntiles, P.p_pad, norms, iscale, X, Y, g, stat,
-                           sigma, NEAR_DUP_TAU, D, ctr, c->num_sms, s));
-    } else {
-        launch_check_finite(X, g.nx * g.p, ctr, s);
-        launch_check_finite(Y, g.ny * g.p, ctr, s);
-        launch_norms(X, Y, g, norms, s);
-        launch_build_simt(X, Y, norms, g, stat, sigma, NEAR_DUP_TAU, blkinfo, D, ctr, s);
-    }
-    CK(cudaGetLastError());
-    if (!pack) return EPT_OK;
-    double *rowpart = (double *)(A + P.off_rowpart), *colpart = (double *)(A + P.off_colpart);
-    double *r = (double *)(A + P.off_r), *dcorr = (double *)(A + P.off_dcorr);
-    float *u = (float *)(A + P.off_u);
-    StatConst *sc = (StatConst *)(A + P.off_sc);
-    double *Spart = (double *)(A + P.off_Spart), *Upart = (double *)(A + P.off_Upart);
-    double *Stpart = (double *)(A + P.off_Stpart);
-    launch_blocksums(D, g, rowpart, colpart, s);
-    launch_rowsum_reduce(rowpart, colpart, g, r, Spart, s);
-    launch_center(r, Spart, g, u, dcorr, Upart, Stpart, sc, stat, s);
-    if (P.prec == EPT_PREC_SPLIT_BF16)
-        launch_pack_bf16(D, u, dcorr, g, blkinfo, (uint16_t *)(A + P.off_hi), (uint16_t *)(A + P.off_lo), s);
-    else
-        launch_pack_fp32(D, u, dcorr, g, blkinfo, D, s);
-    CK(cudaGetLastError());
-    return EPT_OK;
+    Batch b;
+    memset(&b, 0, sizeof(b));
+    b.n_tests = P.n_tests;
+    b.desc = (const TestDesc *)(A + P.off_desc);
+    b.pre.rows = (const int64_t *)(A + P.off_pre_rows);
+    b.pre.panels = (const int64_t *)(A + P.off_pre_panels);
+    b.pre.cols = (const int64_t *)(A + P.off_pre_cols);
+    b.pre.units = (const int64_t *)(A + P.off_pre_units);
+    b.pre.simt = (const int64_t *)(A + P.off_pre_simt);
+    b.blk = (const BlkInfo *)(A + P.off_blk);
+    b.tiles = (const Tile *)(A + P.off_tiles);
+    b.chunks = (const Chunk *)(A + P.off_chunks);
+    b.nblk_total = P.nblk;
+    b.ntiles = (int64_t)P.tiles.size();
+    b.nrows_total = P.nrows;
+    b.npan_total = P.npan;
+    b.ncols_total = P.ncols_pad;
+    b.nunits_total = P.nunits;
+    b.nsimt_total = P.nsimt;
+    b.p_stride = P.p_stride;
+    b.norms = (float *)(A + P.off_norms);
+    b.iscale = (float *)(A + P.off_iscale);
+    b.u = (float *)(A + P.off_u);
+    b.Zh = (uint16_t *)(A + P.off_Zh);
+    b.Zl = (uint16_t *)(A + P.off_Zl);
+    b.Chi = (uint16_t *)(A + P.off_Chi);
+    b.Clo = (uint16_t *)(A + P.off_Clo);
+    b.D = (float *)(A + P.off_D);
+    b.partial = (float *)(A + P.off_partial);
+    b.rowpart = (double *)(A + P.off_rowpart);
+    b.colpart = (double *)(A + P.off_colpart);
+    b.r = (double *)(A + P.off_r);
+    b.Spart = (double *)(A + P.off_Spart);
+    b.dcorr = (double *)(A + P.off_dcorr);
+    b.Upart = (double *)(A + P.off_Upart);
+    b.Stpart = (double *)(A + P.off_Stpart);
+    b.stats = (double *)(A + P.off_stats);
+    b.observed = (double *)(A + P.off_observed);
+    b.maskT = (uint32_t *)(A + P.off_maskT);
+    b.ctr = (Counters *)(A + P.off_ctr);
+    return b;
 }
 
-// The whole test.  user_masks == nullptr: draws 1..B of the stream of `seed`.
-ept_status run_test(ept_ctx *c, const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p, int on_device,
-                    int stat, double sigma, int64_t B, uint64_t seed, const uint32_t *user_masks, int prec,
-                    double *perm_stats, ept_result *out, void *stream) {
-    if (!c) return fail(EPT_EINVAL, "null context");
-    if (!X || !Y || !out) return fail(EPT_EINVAL, "null X, Y or result pointer");
-    if (B < 0) return fail(EPT_EINVAL, "B must be >= 0");
-    if (B > ((int64_t)1 << 31)) return fail(EPT_EINVAL, "B exceeds 2^31");
-    ept_status st = validate(nx, ny, p, stat, sigma, prec);
-    if (st != EPT_OK) return st;
-    std::lock_guard<std::mutex> lock(c->mu);
-    DeviceGuard dg(c->device);
-    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
-    const Geom g = make_geom(nx, ny, p, B + 1);
-    const bool host_in = !on_device;
-    const Plan P = make_plan(g, prec, host_in, user_masks ? B : 0);
-    if ((st = ensure_arena(c, P.total, s)) != EPT_OK) return st;
-    fill_tables(c, g);
-    const int64_t nwu = (g.n + 31) / 32;
-    // pinned staging: tables + (host inputs) + results
-    const size_t tab_bytes = align_up(c->h_blkinfo.size() * sizeof(int2), 256) +
-                             align_up(c->h_chunks.size() * sizeof(Chunk), 256) +
-                             align_up(c->h_tiles.size() * sizeof(int4), 256);
-    const size_t xin = align_up((size_t)nx * p * 4, 256), yin = align_up((size_t)ny * p * 4, 256);
-    const size_t in_bytes = host_in ? xin + yin + (user_masks ? align_up((size_t)B * nwu * 4, 256) : 0) : 0;
-    const size_t res_bytes = align_up((size_t)g.ncols * 8, 256) + align_up(sizeof(Counters), 256);
-    if ((st = ensure_pinned(c, tab_bytes + in_bytes + res_bytes)) != EPT_OK) return st;
-    uint8_t *A = c->arena;
-    uint8_t *pin = c->pinned;
-    uint8_t *pin_tab = pin, *pin_in = pin + tab_bytes, *pin_res = pin + tab_bytes + in_bytes;
-
-    CK(cudaEventRecord(c->ev[0], s));
-    const float *dX = X, *dY = Y;
-    const uint32_t *dmasks = user_masks;
-    if (host_in) {
-        float *xx = (float *)(A + P.off_X), *yy = (float *)(A + P.off_Y);
-        if ((st = h2d(xx, X, (size_t)nx * p * 4, pin_in, s)) != EPT_OK) return st;
-        if ((st = h2d(yy, Y, (size_t)ny * p * 4, pin_in + xin, s)) != EPT_OK) return st;
-        dX = xx;
-        dY = yy;
-        if (user_masks && B > 0) {
-            uint32_t *um = (uint32_t *)(A + P.off_umask);
-            if ((st = h2d(um, user_masks, (size_t)B * nwu * 4, pin_in + xin + yin, s)) != EPT_OK) return st;
-            dmasks = um;
-        }
-    }
-    // tables
-    memcpy(pin_tab, c->h_blkinfo.data(), c->h_blkinfo.size() * sizeof(int2));
-    memcpy(pin_tab + align_up(c->h_blkinfo.size() * sizeof(int2), 256), c->h_chunks.data(),
-           c->h_chunks.size() * sizeof(Chunk));
-    CK(cudaMemcpyAsync(A + P.off_blkinfo, pin_tab, c->h_blkinfo.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
-    CK(cudaMemcpyAsync(A + P.off_chunks, pin_tab + align_up(c->h_blkinfo.size() * sizeof(int2), 256),
-                       c->h_chunks.size() * sizeof(Chunk), cudaMemcpyHostToDevice, s));
-    if (prec == EPT_PREC_SPLIT_BF16) {
-        uint8_t *tsrc = pin_tab + align_up(c->h_blkinfo.size() * sizeof(int2), 256) +
-                        align_up(c->h_chunks.size() * sizeof(Chunk), 256);
-        memcpy(tsrc, c->h_tiles.data(), c->h_tiles.size() * sizeof(int4));
-        CK(cudaMemcpyAsync(A + P.off_tiles, tsrc, c->h_tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
-    }
-    Counters *ctr = (Counters *)(A + P.off_ctr);
-    CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
+// The device work of one run, enqueued on s (and the side stream).  With `timed`,
+// events mark the phases (not used while capturing a graph).
+ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed) {
+    const Staging S = staging_layout(P);
+    uint8_t *A = c->arena, *pin = c->pinned;
+    const Batch b = device_view(c, P);
+    const bool tc = P.prec == EPT_PREC_SPLIT_BF16;
+    if (timed) CK(cudaEventRecord(c->ev[0], s));
+    CK(cudaMemcpyAsync(A, pin + S.tables, P.tab_bytes, cudaMemcpyHostToDevice, s));
+    if (P.host_in && P.in_bytes)
+        CK(cudaMemcpyAsync(A + P.off_in, pin + S.inputs, P.in_bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(b.ctr, 0, sizeof(Counters) * P.n_tests, s));
     CK(cudaEventRecord(c->ev[1], s));
 
-    // relabelings on the side stream, beside the block build: column 0 identity, then
-    // draws 1..B or the caller's masks (they need only the uploads recorded in ev[1])
+    // relabelings on the side stream, beside the block build
     cudaStream_t s2 = c->side;
     CK(cudaStreamWaitEvent(s2, c->ev[1], 0));
-    CK(cudaEventRecord(c->ev_side[1], s2));
-    uint32_t *maskT = (uint32_t *)(A + P.off_maskT);
-    if (user_masks) {
-        launch_perm_masks(seed, (int)nx, (int)ny, 0, 1, g.Bp, (int)g.nw, g.comp, maskT, s2);
-        launch_user_masks(dmasks, B, (int)nwu, (int)nx, (int)g.n, g.Bp, (int)g.nw, g.comp, maskT, ctr, s2);
-    } else {
-        launch_perm_masks(seed, (int)nx, (int)ny, 0, g.ncols, g.Bp, (int)g.nw, g.comp, maskT, s2);
-    }
+    if (timed) CK(cudaEventRecord(c->ev_side[1], s2));
+    launch_masks(b, s2);
     CK(cudaGetLastError());
     CK(cudaEventRecord(c->ev_side[2], s2));
 
-    if ((st = run_blocks(c, P, dX, dY, stat, sigma, true, s)) != EPT_OK) return st;
-    CK(cudaEventRecord(c->ev[2], s));
+    // phase 1: blocks, centring, packing
+    if (tc) {
+        launch_split_rows(b, s);
+        alignas(64) CUtensorMap tm[4];
+        char emsg[160];
+        if (!encode_rows_tmaps(tm, b.Zh, b.Zl, P.nrows, P.p_stride, emsg, sizeof(emsg)))
+            return fail(EPT_ECUDA, "%s", emsg);
+        CK(launch_build_tc(b, tm, c->num_sms, s));
+    } else {
+        launch_norms(b, s);
+        launch_build_simt(b, s);
+    }
+    launch_blocksums(b, s);
+    launch_rowsum_reduce(b, s);
+    launch_center(b, s);
+    launch_pack(b, tc, s);
+    CK(cudaGetLastError());
+    if (timed) CK(cudaEventRecord(c->ev[2], s));
+
+    // phase 2: contraction, combination
     CK(cudaStreamWaitEvent(s, c->ev_side[2], 0));
-    CK(cudaEventRecord(c->ev[5], s));
-    float *partial = (float *)(A + P.off_partial);
-    const Chunk *chunks = (const Chunk *)(A + P.off_chunks);
-    if (prec == EPT_PREC_SPLIT_BF16) {
+    if (timed) CK(cudaEventRecord(c->ev[5], s));
+    if (tc) {
         alignas(64) CUtensorMap th, tl;
         char emsg[160];
-        if (!encode_block_tmaps(&th, &tl, (const uint16_t *)(A + P.off_hi), (const uint16_t *)(A + P.off_lo), g.nblk,
-                                emsg, sizeof(emsg)))
-            return fail(EPT_ECUDA, "%s", emsg);
-        CK(launch_contract_tc(&th, &tl, maskT, chunks, g, partial, ctr, c->num_sms, s));
+        if (!encode_block_tmaps(&th, &tl, b.Chi, b.Clo, P.nblk, emsg, sizeof(emsg))) return fail(EPT_ECUDA, "%s", emsg);
+        CK(launch_contract_tc(b, &th, &tl, c->num_sms, s));
     } else {
-        launch_contract_simt((const float *)(A + P.off_D), maskT, chunks, g, partial, s);
+        launch_contract_simt(b, s);
         CK(cudaGetLastError());
     }
-    CK(cudaEventRecord(c->ev[6], s));
-    double *stats = (double *)(A + P.off_stats);
-    launch_combine(partial, P.nparts, g, (const StatConst *)(A + P.off_sc), (const double *)(A + P.off_Stpart), stats,
-                   ctr, s);
+    if (timed) CK(cudaEventRecord(c->ev[6], s));
+    launch_combine(b, s);
     CK(cudaGetLastError());
-    CK(cudaEventRecord(c->ev[3], s));
+    if (timed) CK(cudaEventRecord(c->ev[3], s));
 
-    double *h_stats = (double *)pin_res;
-    Counters *h_ctr = (Counters *)(pin_res + align_up((size_t)g.ncols * 8, 256));
-    CK(cudaMemcpyAsync(h_ctr, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-    if (on_device) {
-        CK(cudaMemcpyAsync(h_stats, stats, 8, cudaMemcpyDeviceToHost, s));
-        if (perm_stats && B > 0)
-            CK(cudaMemcpyAsync(perm_stats, stats + 1, (size_t)B * 8, cudaMemcpyDeviceToDevice, s));
-    } else {
-        CK(cudaMemcpyAsync(h_stats, stats, (size_t)g.ncols * 8, cudaMemcpyDeviceToHost, s));
-    }
-    CK(cudaEventRecord(c->ev[4], s));
-    CK(cudaStreamSynchronize(s));
-
-    if (h_ctr->nonfinite) return fail(EPT_EINVAL, "X or Y holds NaN or Inf");
-    if (h_ctr->bad_mask)
-        return fail(EPT_EINVAL, "%llu relabeling(s) do not have exactly nx = %lld members among the n rows",
-                    (unsigned long long)h_ctr->bad_mask, (long long)nx);
-    if (h_ctr->err_code)
-        return fail(EPT_ETIMEOUT, "device-side bounded wait gave up (code 0x%llx)", (unsigned long long)h_ctr->err_code);
-    if (!on_device && perm_stats && B > 0) memcpy(perm_stats, h_stats + 1, (size_t)B * 8);
-    out->observed = h_stats[0];
-    out->n_ge = (int64_t)h_ctr->n_ge;
-    out->n_near_tie = (int64_t)h_ctr->n_near;
-    out->n_fixup = (int64_t)h_ctr->n_fixup;
-    out->p_value = (1.0 + (double)out->n_ge) / (1.0 + (double)B);
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]);
-    out->ms_build = ms;
-    cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
-    out->ms_perm = ms;
-    cudaEventElapsedTime(&ms, c->ev[0], c->ev[4]);
-    out->ms_total = ms;
-    cudaEventElapsedTime(&ms, c->ev_side[1], c->ev_side[2]);
-    out->ms_masks = ms;
-    cudaEventElapsedTime(&ms, c->ev[5], c->ev[6]);
-    out->ms_contract = ms;
+    CK(cudaMemcpyAsync(pin + S.res_ctr, b.ctr, sizeof(Counters) * P.n_tests, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(pin + S.res_obs, b.observed, 8 * (size_t)P.n_tests, cudaMemcpyDeviceToHost, s));
+    if (P.host_in) CK(cudaMemcpyAsync(pin + S.res_stats, b.stats, 8 * (size_t)P.nstats, cudaMemcpyDeviceToHost, s));
+    if (timed) CK(cudaEventRecord(c->ev[4], s));
     return EPT_OK;
+}
+
+// Results of a finished run (host side).
+ept_status collect(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &specs, ept_result *out, bool timed) {
+    const Staging S = staging_layout(P);
+    const Counters *ctr = (const Counters *)(c->pinned + S.res_ctr);
+    const double *obs = (const double *)(c->pinned + S.res_obs);
+    const double *stats = (const double *)(c->pinned + S.res_stats);
+    for (int t = 0; t < P.n_tests; ++t) {
+        if (ctr[t].nonfinite) return fail(EPT_EINVAL, "test %d: X or Y holds NaN or Inf", t);
+        if (ctr[t].bad_mask)
+            return fail(EPT_EINVAL, "test %d: %llu relabeling(s) do not have exactly nx = %lld members among the n rows",
+                        t, (unsigned long long)ctr[t].bad_mask, (long long)P.desc[t].nx);
+    }
+    if (P.n_tests > 0 && ctr[0].err_code)
+        return fail(EPT_ETIMEOUT, "device-side bounded wait gave up (code 0x%llx)", (unsigned long long)ctr[0].err_code);
+    float ms_build = 0.f, ms_perm = 0.f, ms_total = 0.f, ms_masks = 0.f, ms_contract = 0.f;
+    if (timed) {
+        cudaEventElapsedTime(&ms_build, c->ev[1], c->ev[2]);
+        cudaEventElapsedTime(&ms_perm, c->ev[2], c->ev[3]);
+        cudaEventElapsedTime(&ms_total, c->ev[0], c->ev[4]);
+        cudaEventElapsedTime(&ms_masks, c->ev_side[1], c->ev_side[2]);
+        cudaEventElapsedTime(&ms_contract, c->ev[5], c->ev[6]);
+    }
+    for (int t = 0; t < P.n_tests; ++t) {
+        const TestDesc &d = P.desc[t];
+        ept_result &r = out[t];
+        r.observed = obs[t];
+        r.n_ge = (int64_t)ctr[t].n_ge;
+        r.n_near_tie = (int64_t)ctr[t].n_near;
+        r.n_fixup = (int64_t)ctr[t].n_fixup;
+        r.p_value = (1.0 + (double)r.n_ge) / (1.0 + (double)d.B);
+        r.ms_build = ms_build;
+        r.ms_perm = ms_perm;
+        r.ms_total = ms_total;
+        r.ms_masks = ms_masks;
+        r.ms_contract = ms_contract;
+        if (P.host_in && specs[t].perm_stats && d.B > 0)
+            memcpy(specs[t].perm_stats, stats + d.col0 + 1, (size_t)d.B * 8);
+    }
+    return EPT_OK;
+}
+
+std::vector<int64_t> shape_key(const std::vector<TestSpec> &specs, int prec, bool on_device) {
+    std::vector<int64_t> k;
+    k.push_back(prec);
+    k.push_back(on_device ? 1 : 0);
+    for (const TestSpec &s : specs) {
+        k.push_back(s.nx);
+        k.push_back(s.ny);
+        k.push_back(s.p);
+        k.push_back(s.B);
+        k.push_back(s.user_masks ? 1 : 0);
+        k.push_back(s.perm_stats ? 1 : 0);
+    }
+    return k;
+}
+
+// key of the autotuner: the batch's padded shapes (what the unit decomposition sees)
+std::vector<int64_t> tune_key(const std::vector<TestSpec> &specs, int prec) {
+    std::vector<int64_t> k;
+    k.push_back(prec);
+    for (const TestSpec &s : specs) {
+        k.push_back((s.nx + s.ny + PANEL - 1) / PANEL);
+        k.push_back((s.B + 1 + COL_PAD - 1) / COL_PAD);
+    }
+    return k;
+}
+
+void save_tune_file(ept_ctx *c) {
+    if (c->tune_file.empty()) return;
+    FILE *f = fopen(c->tune_file.c_str(), "w");
+    if (!f) return;
+    for (auto &kv : c->tuned_chunk) {
+        fprintf(f, "%d", kv.second);
+        for (int64_t v : kv.first) fprintf(f, " %lld", (long long)v);
+        fprintf(f, "\n");
+    }
+    fclose(f);
+}
+
+void load_tune_file(ept_ctx *c) {
+    if (c->tune_file.empty()) return;
+    FILE *f = fopen(c->tune_file.c_str(), "r");
+    if (!f) return;
+    char line[1 << 16];
+    while (fgets(line, sizeof(line), f)) {
+        char *p = line, *end = nullptr;
+        const long chunk = strtol(p, &end, 10);
+        if (end == p) continue;
+        std::vector<int64_t> key;
+        p = end;
+        for (;;) {
+            const long long v = strtoll(p, &end, 10);
+            if (end == p) break;
+            key.push_back(v);
+            p = end;
+        }
+        if (chunk == 8 || chunk == 16 || chunk == 32) c->tuned_chunk[key] = (int)chunk;
+    }
+    fclose(f);
+}
+
+// One run of a batch: plan, stage, enqueue (or replay a captured graph), wait, collect.
+ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bool on_device, int chunk_kb,
+                    bool use_graph, ept_result *out, void *stream, float *device_ms) {
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    Plan P;
+    plan_batch(P, specs, prec, !on_device, chunk_kb);
+    ept_status st = ensure_arena(c, P.total, s);
+    if (st != EPT_OK) return st;
+    const Staging S = staging_layout(P);
+    if ((st = ensure_pinned(c, S.total)) != EPT_OK) return st;
+    if (s != c->stream) CK(cudaStreamSynchronize(c->stream));
+    stage_host(c, P, specs, on_device);
+    if (use_graph && s == c->stream) {
+        std::vector<int64_t> key = shape_key(specs, prec, on_device);
+        key.push_back(chunk_kb);
+        if (!(c->graph.exec && c->graph.key == key && c->graph.arena == c->arena)) {
+            drop_graph(c);
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            st = enqueue_device(c, P, s, false);
+            const cudaError_t e_end = cudaStreamEndCapture(s, &g);
+            if (st != EPT_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (e_end != cudaSuccess) return fail(EPT_ECUDA, "graph capture failed: %s", cudaGetErrorString(e_end));
+            cudaGraphExec_t ex = nullptr;
+            const cudaError_t e_in = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e_in != cudaSuccess) return fail(EPT_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e_in));
+            c->graph.exec = ex;
+            c->graph.key = key;
+            c->graph.arena = c->arena;
+        }
+        CK(cudaEventRecord(c->ev[0], s));
+        CK(cudaGraphLaunch(c->graph.exec, s));
+        CK(cudaEventRecord(c->ev[4], s));
+        CK(cudaStreamSynchronize(s));
+        if ((st = collect(c, P, specs, out, false)) != EPT_OK) return st;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->ev[0], c->ev[4]);
+        for (int t = 0; t < P.n_tests; ++t) out[t].ms_total = ms;
+        if (device_ms) *device_ms = ms;
+        return EPT_OK;
+    }
+    if ((st = enqueue_device(c, P, s, true)) != EPT_OK) return st;
+    CK(cudaStreamSynchronize(s));
+    if ((st = collect(c, P, specs, out, true)) != EPT_OK) return st;
+    if (device_ms) cudaEventElapsedTime(device_ms, c->ev[5], c->ev[6]);
+    return EPT_OK;
+}
+
+// Contraction chunk length for this batch shape: from the cache, or (first time)
+// by timing the contraction with each candidate on this very batch.  Each tuning
+// run is a complete, correct test, so the last one's results are returned when it
+// is the one chosen.
+ept_status run_tuned(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bool on_device, bool use_graph,
+                     ept_result *out, void *stream) {
+    if (!c->autotune) return run_once(c, specs, prec, on_device, CHUNK_KB_DEFAULT, use_graph, out, stream, nullptr);
+    const std::vector<int64_t> key = tune_key(specs, prec);
+    auto it = c->tuned_chunk.find(key);
+    if (it != c->tuned_chunk.end()) return run_once(c, specs, prec, on_device, it->second, use_graph, out, stream, nullptr);
+    int best = CHUNK_KB_DEFAULT;
+    float best_ms = 1e30f;
+    for (int k = 0; k < 3; ++k) {
+        float ms = 0.f;
+        ept_status st = run_once(c, specs, prec, on_device, CHUNK_CANDIDATES[k], false, out, stream, &ms);
+        if (st != EPT_OK) return st;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = CHUNK_CANDIDATES[k];
+        }
+    }
+    c->tuned_chunk[key] = best;
+    save_tune_file(c);
+    return run_once(c, specs, prec, on_device, best, use_graph, out, stream, nullptr);
 }
 
 }  // namespace
@@ -447,6 +712,11 @@ ept_status ept_create(ept_ctx **out, int device, size_t mem_budget_bytes) {
     c->device = device;
     c->num_sms = prop.multiProcessorCount;
     c->budget = mem_budget_bytes;
+    const char *at = getenv("EPT_AUTOTUNE");
+    c->autotune = !(at && at[0] == '0');
+    const char *tf = getenv("EPT_AUTOTUNE_CACHE");
+    if (tf) c->tune_file = tf;
+    load_tune_file(c);
     DeviceGuard dg(device);
     cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
     for (int k = 0; k < 7 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
@@ -465,11 +735,12 @@ ept_status ept_destroy(ept_ctx *c) {
     {
         DeviceGuard dg(c->device);
         if (c->stream) cudaStreamSynchronize(c->stream);
+        if (c->side) cudaStreamSynchronize(c->side);
+        drop_graph(c);
         if (c->arena) cudaFree(c->arena);
         if (c->pinned) cudaFreeHost(c->pinned);
         for (int k = 0; k < 7; ++k)
             if (c->ev[k]) cudaEventDestroy(c->ev[k]);
-        if (c->side) cudaStreamSynchronize(c->side);
         for (int k = 0; k < 3; ++k)
             if (c->ev_side[k]) cudaEventDestroy(c->ev_side[k]);
         if (c->side) cudaStreamDestroy(c->side);
@@ -482,23 +753,59 @@ ept_status ept_destroy(ept_ctx *c) {
 size_t ept_estimate_bytes(int64_t nx, int64_t ny, int64_t p, int64_t B, int prec) {
     if (nx < 1 || ny < 1 || p < 1 || B < 0 || nx + ny > ((int64_t)1 << 22)) return 0;
     if (prec != EPT_PREC_PLAIN_FP32 && prec != EPT_PREC_SPLIT_BF16) return 0;
-    const Geom g = make_geom(nx, ny, p, B + 1);
-    return make_plan(g, prec, true, 0).total;
+    Plan P;
+    plan_batch(P, one_test(nullptr, nx, nullptr, ny, p, 0, 1.0, B, 0, nullptr, nullptr), prec, true, 8);
+    return P.total;
 }
 
 ept_status ept_test(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p, int on_device,
                     int stat, double sigma, int64_t B, uint64_t seed, int prec, double *perm_stats, ept_result *out,
                     void *stream) {
-    return run_test(ctx, X, nx, Y, ny, p, on_device, stat, sigma, B, seed, nullptr, prec, perm_stats, out, stream);
+    if (!ctx) return fail(EPT_EINVAL, "null context");
+    if (!X || !Y || !out) return fail(EPT_EINVAL, "null X, Y or result pointer");
+    if (B < 0 || B > ((int64_t)1 << 31)) return fail(EPT_EINVAL, "B must be in [0, 2^31]");
+    ept_status st = validate(nx, ny, p, stat, sigma, prec);
+    if (st != EPT_OK) return st;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    return run_tuned(ctx, one_test(X, nx, Y, ny, p, stat, sigma, B, seed, nullptr, perm_stats), prec, on_device != 0,
+                     false, out, stream);
 }
 
 ept_status ept_test_masks(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p,
                           int on_device, int stat, double sigma, const uint32_t *masks, int64_t n_masks, int prec,
                           double *perm_stats, ept_result *out, void *stream) {
+    if (!ctx) return fail(EPT_EINVAL, "null context");
+    if (!X || !Y || !out) return fail(EPT_EINVAL, "null X, Y or result pointer");
+    if (n_masks < 0 || n_masks > ((int64_t)1 << 31)) return fail(EPT_EINVAL, "n_masks must be in [0, 2^31]");
     if (n_masks > 0 && !masks) return fail(EPT_EINVAL, "null masks");
-    static const uint32_t dummy = 0;
-    return run_test(ctx, X, nx, Y, ny, p, on_device, stat, sigma, n_masks, 0, masks ? masks : &dummy, prec,
-                    perm_stats, out, stream);
+    ept_status st = validate(nx, ny, p, stat, sigma, prec);
+    if (st != EPT_OK) return st;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    return run_once(ctx, one_test(X, nx, Y, ny, p, stat, sigma, n_masks, 0, n_masks > 0 ? masks : nullptr, perm_stats),
+                    prec, on_device != 0, CHUNK_KB_DEFAULT, false, out, stream, nullptr);
+}
+
+ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_tests, int on_device, int prec,
+                          ept_result *results, void *stream) {
+    if (!ctx) return fail(EPT_EINVAL, "null context");
+    if (n_tests < 0 || n_tests > (1 << 20)) return fail(EPT_EINVAL, "n_tests must be in [0, 2^20]");
+    if (n_tests == 0) return EPT_OK;
+    if (!tests || !results) return fail(EPT_EINVAL, "null tests or results");
+    std::vector<TestSpec> specs;
+    specs.reserve((size_t)n_tests);
+    for (int64_t t = 0; t < n_tests; ++t) {
+        const ept_test_desc &q = tests[t];
+        if (!q.X || !q.Y) return fail(EPT_EINVAL, "test %lld: null X or Y", (long long)t);
+        if (q.B < 0 || q.B > ((int64_t)1 << 31)) return fail(EPT_EINVAL, "test %lld: B must be in [0, 2^31]", (long long)t);
+        ept_status st = validate(q.nx, q.ny, q.p, q.stat, q.sigma, prec);
+        if (st != EPT_OK) return fail(st, "test %lld: %s", (long long)t, g_err.c_str());
+        specs.push_back(one_test(q.X, q.nx, q.Y, q.ny, q.p, q.stat, q.sigma, q.B, q.seed, nullptr, q.perm_stats)[0]);
+    }
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    return run_tuned(ctx, specs, prec, on_device != 0, true, results, stream);
 }
 
 ept_status ept_perm_masks(ept_ctx *c, uint64_t seed, int64_t nx, int64_t ny, int64_t b0, int64_t count,
@@ -520,7 +827,7 @@ ept_status ept_perm_masks(ept_ctx *c, uint64_t seed, int64_t nx, int64_t ny, int
     if (st != EPT_OK) return st;
     uint32_t *maskT = (uint32_t *)c->arena;
     uint32_t *rows = on_device ? out : (uint32_t *)(c->arena + bytesT);
-    launch_perm_masks(seed, (int)nx, (int)ny, b0, count, count, (int)nw, false, maskT, s);
+    launch_perm_masks_plain(seed, (int)nx, (int)ny, b0, count, (int)nw, maskT, s);
     launch_masks_to_rows(maskT, count, (int)nw, count, (int)nwu, rows, s);
     CK(cudaGetLastError());
     if (!on_device) CK(cudaMemcpyAsync(out, rows, bytesR, cudaMemcpyDeviceToHost, s));
@@ -537,45 +844,39 @@ ept_status ept_build_blocks(ept_ctx *c, const float *X, int64_t nx, const float 
     std::lock_guard<std::mutex> lock(c->mu);
     DeviceGuard dg(c->device);
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
-    const Geom g = make_geom(nx, ny, p, 1);
-    const bool host_in = !on_device;
-    const Plan P = make_plan(g, prec, host_in, 0);
-    const size_t out_bytes = (size_t)g.n * g.n * 4;
-    const size_t total = P.total + (on_device ? 0 : align_up(out_bytes, 1024));
-    if ((st = ensure_arena(c, total, s)) != EPT_OK) return st;
-    fill_tables(c, g);
-    const size_t tab_bytes = align_up(c->h_blkinfo.size() * sizeof(int2), 256) +
-                             align_up(c->h_tiles.size() * sizeof(int4), 256);
-    const size_t xin = align_up((size_t)nx * p * 4, 256);
-    const size_t in_bytes = host_in ? xin + align_up((size_t)ny * p * 4, 256) : 0;
-    if ((st = ensure_pinned(c, tab_bytes + in_bytes + 256)) != EPT_OK) return st;
+    const std::vector<TestSpec> specs = one_test(X, nx, Y, ny, p, stat, sigma, 0, 0, nullptr, nullptr);
+    Plan P;
+    plan_batch(P, specs, prec, !on_device, CHUNK_KB_DEFAULT);
+    const size_t out_bytes = (size_t)(nx + ny) * (nx + ny) * 4;
+    if ((st = ensure_arena(c, P.total + (on_device ? 0 : align_up(out_bytes, 1024)), s)) != EPT_OK) return st;
+    const Staging S = staging_layout(P);
+    if ((st = ensure_pinned(c, S.total)) != EPT_OK) return st;
+    if (s != c->stream) CK(cudaStreamSynchronize(c->stream));
+    stage_host(c, P, specs, on_device != 0);
     uint8_t *A = c->arena;
-    const float *dX = X, *dY = Y;
-    if (host_in) {
-        float *xx = (float *)(A + P.off_X), *yy = (float *)(A + P.off_Y);
-        if ((st = h2d(xx, X, (size_t)nx * p * 4, c->pinned + tab_bytes, s)) != EPT_OK) return st;
-        if ((st = h2d(yy, Y, (size_t)ny * p * 4, c->pinned + tab_bytes + xin, s)) != EPT_OK) return st;
-        dX = xx;
-        dY = yy;
-    }
-    memcpy(c->pinned, c->h_blkinfo.data(), c->h_blkinfo.size() * sizeof(int2));
-    CK(cudaMemcpyAsync(A + P.off_blkinfo, c->pinned, c->h_blkinfo.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    const Batch b = device_view(c, P);
+    CK(cudaMemcpyAsync(A, c->pinned + S.tables, P.tab_bytes, cudaMemcpyHostToDevice, s));
+    if (P.host_in && P.in_bytes)
+        CK(cudaMemcpyAsync(A + P.off_in, c->pinned + S.inputs, P.in_bytes, cudaMemcpyHostToDevice, s));
+    CK(cudaMemsetAsync(b.ctr, 0, sizeof(Counters), s));
     if (prec == EPT_PREC_SPLIT_BF16) {
-        uint8_t *tsrc = c->pinned + align_up(c->h_blkinfo.size() * sizeof(int2), 256);
-        memcpy(tsrc, c->h_tiles.data(), c->h_tiles.size() * sizeof(int4));
-        CK(cudaMemcpyAsync(A + P.off_tiles, tsrc, c->h_tiles.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+        launch_split_rows(b, s);
+        alignas(64) CUtensorMap tm[4];
+        char emsg[160];
+        if (!encode_rows_tmaps(tm, b.Zh, b.Zl, P.nrows, P.p_stride, emsg, sizeof(emsg))) return fail(EPT_ECUDA, "%s", emsg);
+        CK(launch_build_tc(b, tm, c->num_sms, s));
+    } else {
+        launch_norms(b, s);
+        launch_build_simt(b, s);
     }
-    Counters *ctr = (Counters *)(A + P.off_ctr);
-    CK(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
-    if ((st = run_blocks(c, P, dX, dY, stat, sigma, false, s)) != EPT_OK) return st;
     float *dout = on_device ? D_out : (float *)(A + P.total);
-    launch_expand_blocks((const float *)(A + P.off_D), g, dout, s);
+    launch_expand_blocks(b.D, nx + ny, P.desc[0].NKB, dout, s);
     CK(cudaGetLastError());
-    Counters h;
-    CK(cudaMemcpyAsync(&h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    Counters *h = (Counters *)(c->pinned + S.res_ctr);
+    CK(cudaMemcpyAsync(h, b.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
     if (!on_device) CK(cudaMemcpyAsync(D_out, dout, out_bytes, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    if (h.nonfinite) return fail(EPT_EINVAL, "X or Y holds NaN or Inf");
+    if (h->nonfinite) return fail(EPT_EINVAL, "X or Y holds NaN or Inf");
     return EPT_OK;
 }
 

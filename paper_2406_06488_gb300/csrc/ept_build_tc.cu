@@ -61,24 +61,25 @@ struct Bars {
     int abort_flag;
 };
 
-__device__ __forceinline__ const float *row_ptr(const float *X, const float *Y, int64_t nx, int64_t i, int64_t p) {
-    return (i < nx) ? X + i * p : Y + (i - nx) * p;
+__device__ __forceinline__ const float *row_ptr(const TestDesc &d, int64_t i) {
+    return (i < d.nx) ? d.X + i * d.p : d.Y + (i - d.nx) * d.p;
 }
 
-// Pooled row i -> FP16 hi / lo parts of c_i z_i [n_pad x p_pad] (zero padding), the
-// inverse scale 1/c_i, and the squared norm of the unscaled row (exact products
-// accumulated in FP64, rounded once).  c_i = 2^k with max |c_i z_i| < 2^14, k clamped
-// to [-60, 60] so that 1/c_i 1/c_j stays a normal FP32 number (rows above 2^74 would
-// overflow the FP32 norms in any case).  Non-finite inputs are counted.  One warp
-// per row.
-__global__ void k_split_rows(const float *__restrict__ X, const float *__restrict__ Y, int64_t nx, int64_t n,
-                             int64_t n_pad, int64_t p, int64_t p_pad, __half *__restrict__ Zh,
-                             __half *__restrict__ Zl, float *__restrict__ norms, float *__restrict__ inv_scale,
-                             Counters *ctr) {
+// Pooled row i of a test -> FP16 hi / lo parts of c_i z_i (zero padding up to the
+// test's p_pad), the inverse scale 1/c_i, and the squared norm of the unscaled row
+// (exact products accumulated in FP64, rounded once).  c_i = 2^k with
+// max |c_i z_i| < 2^14, k clamped to [-60, 60] so that 1/c_i 1/c_j stays a normal
+// FP32 number (rows above 2^74 would overflow the FP32 norms in any case).
+// Non-finite inputs are counted.  One warp per row of the batch.
+__global__ void __launch_bounds__(256) k_split_rows(const Batch bt) {
     const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n_pad) return;
-    const float *z = (i < n) ? row_ptr(X, Y, nx, i, p) : nullptr;
+    const int64_t gr = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gr >= bt.nrows_total) return;
+    const int t = find_test(bt.pre.rows, bt.n_tests, gr);
+    const TestDesc d = bt.desc[t];
+    const int64_t i = gr - d.row0;
+    const int64_t p = d.p;
+    const float *z = (i < d.n) ? row_ptr(d, i) : nullptr;
     uint32_t mx = 0;
     bool bad = false;
     if (z) {
@@ -90,7 +91,7 @@ __global__ void k_split_rows(const float *__restrict__ X, const float *__restric
     }
     for (int off = 16; off; off >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
     if (__any_sync(0xFFFFFFFFu, bad)) {
-        if (lane == 0) atomicAdd(&ctr->nonfinite, 1ull);
+        if (lane == 0) atomicAdd(&bt.ctr[t].nonfinite, 1ull);
     }
     int k2 = 0;
     if (mx) {
@@ -100,8 +101,9 @@ __global__ void k_split_rows(const float *__restrict__ X, const float *__restric
         k2 = k2 < -60 ? -60 : (k2 > 60 ? 60 : k2);
     }
     const float c = ldexpf(1.f, k2);
+    __half *zh = (__half *)bt.Zh + gr * bt.p_stride, *zl = (__half *)bt.Zl + gr * bt.p_stride;
     double acc = 0.0;
-    for (int64_t k = 2 * lane; k < p_pad; k += 64) {
+    for (int64_t k = 2 * lane; k < d.p_pad; k += 64) {
         float v0 = 0.f, v1 = 0.f;
         if (z && k < p) v0 = z[k];
         if (z && k + 1 < p) v1 = z[k + 1];
@@ -113,22 +115,21 @@ __global__ void k_split_rows(const float *__restrict__ X, const float *__restric
         const __half h0 = __float2half_rn(w0), h1 = __float2half_rn(w1);
         const __half l0 = __float2half_rn(w0 - __half2float(h0));
         const __half l1 = __float2half_rn(w1 - __half2float(h1));
-        *reinterpret_cast<__half2 *>(Zh + i * p_pad + k) = __halves2half2(h0, h1);
-        *reinterpret_cast<__half2 *>(Zl + i * p_pad + k) = __halves2half2(l0, l1);
+        *reinterpret_cast<__half2 *>(zh + k) = __halves2half2(h0, h1);
+        *reinterpret_cast<__half2 *>(zl + k) = __halves2half2(l0, l1);
     }
     for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
     if (lane == 0) {
-        norms[i] = (float)acc;
-        inv_scale[i] = ldexpf(1.f, -k2);
+        bt.norms[gr] = (float)acc;
+        bt.iscale[gr] = ldexpf(1.f, -k2);
     }
 }
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_build_tc(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
-               const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl,
-               const int4 *__restrict__ tiles, int ntiles, int kblocks, const float *__restrict__ norms,
-               const float *__restrict__ inv_scale, const float *__restrict__ X, const float *__restrict__ Y, int64_t nx, int64_t n, int64_t p,
-               int64_t NKB, int stat, float neg_inv_2s2, float tau, float *__restrict__ D, Counters *ctr) {
+               const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl, const Batch bt) {
+    Counters *ctr = bt.ctr;   // bounded-wait errors are recorded in test 0's counters
+    const int ntiles = (int)bt.ntiles;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     Bars *bars = reinterpret_cast<Bars *>(smem + STAGES * STAGE_BYTES);
@@ -167,9 +168,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             for (int s2 = 0; s2 < STAGES; ++s2) armed[s2] = -1;
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                const int4 tile = tiles[t];
-                const int rowA = tile.x * PANEL + tile.y * BM;
-                const int rowB = tile.z * PANEL;
+                const Tile tile = bt.tiles[t];
+                const int64_t row0 = bt.desc[tile.t].row0;
+                const int rowA = (int)row0 + tile.I * PANEL + tile.h * BM;
+                const int rowB = (int)row0 + tile.J * PANEL;
+                const int kblocks = bt.desc[tile.t].kblocks;
                 for (int kk = 0; kk < kblocks; ++kk) {
                     if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_TMA)) {
                         ok = false;
@@ -208,6 +211,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             uint32_t phase = 0, acc_phase = 0;
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int kblocks = bt.desc[bt.tiles[t].t].kblocks;
                 if (!mbar_wait(su32(&bars->acc_empty[acc]), acc_phase ^ 1u, abort_flag, ctr, ERR_WAIT_MMA)) {
                     ok = false;
                     break;
@@ -257,11 +261,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int rt = quarter * 32 + lane;   // row within the 128-row tile
         int acc = 0;
         uint32_t acc_phase = 0;
-        unsigned fixups = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-            const int4 tile = tiles[t];
-            const int rp = tile.y * BM + rt;                 // row within panel I
-            const int64_t i = (int64_t)tile.x * PANEL + rp;  // pooled row
+            const Tile tile = bt.tiles[t];
+            const TestDesc d = bt.desc[tile.t];
+            const int64_t n = d.n, p = d.p, NKB = d.NKB;
+            const int stat = d.stat;
+            const float neg_inv_2s2 = d.neg_inv_2s2, tau = d.tau;
+            const float *norms = bt.norms + d.row0, *inv_scale = bt.iscale + d.row0;
+            unsigned fixups = 0;
+            const int rp = tile.h * BM + rt;                 // row within panel I
+            const int64_t i = (int64_t)tile.I * PANEL + rp;  // pooled row of the test
             const float ni = (i < n) ? norms[i] : 0.f;
             const float si = (i < n) ? inv_scale[i] : 0.f;
             if (!mbar_wait(su32(&bars->acc_full[acc]), acc_phase, abort_flag, ctr, ERR_WAIT_EPI)) break;
@@ -271,7 +280,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             for (int g = 0; g < BN / 32; ++g) {
                 uint32_t v[32];
                 tmem_ld32(tbase + (uint32_t)(g * 32), v);
-                const int64_t j0 = (int64_t)tile.z * PANEL + g * 32;
+                const int64_t j0 = (int64_t)tile.J * PANEL + g * 32;
                 const float nj_l = (j0 + lane < n) ? norms[j0 + lane] : 0.f;
                 const float sj_l = (j0 + lane < n) ? inv_scale[j0 + lane] : 0.f;
                 float out[32];
@@ -288,7 +297,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                             const float gij = (__uint_as_float(v[e]) * si) * sj;   // exact rescaling
                             const float d2 = fmaxf(0.f, ni + nj - 2.f * gij);
                             if (d2 < tau * (ni + nj)) {
-                                const float *zi = row_ptr(X, Y, nx, i, p), *zj = row_ptr(X, Y, nx, j, p);
+                                const float *zi = row_ptr(d, i), *zj = row_ptr(d, j);
                                 double s = 0.0;
                                 for (int64_t k = 0; k < p; ++k) {
                                     const double d = (double)zi[k] - (double)zj[k];
@@ -303,20 +312,20 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     }
                     out[e] = val;
                 }
-                const int64_t kb = (int64_t)tile.z * KB_PER_PANEL + (g >> 1);
-                float *dst = D + (blk_index(tile.x, kb, NKB) * PANEL + rp) * KB + (g & 1) * 32;
+                const int64_t kb = (int64_t)tile.J * KB_PER_PANEL + (g >> 1);
+                float *dst = bt.D + ((d.blk0 + blk_index(tile.I, kb, NKB)) * PANEL + rp) * KB + (g & 1) * 32;
 #pragma unroll
                 for (int e = 0; e < 32; e += 4)
                     *reinterpret_cast<float4 *>(dst + e) = make_float4(out[e], out[e + 1], out[e + 2], out[e + 3]);
             }
             fence_before();
             mbar_arrive(su32(&bars->acc_empty[acc]));
+            if (fixups) atomicAdd(&bt.ctr[tile.t].n_fixup, (unsigned long long)fixups);
             if (++acc == 2) {
                 acc = 0;
                 acc_phase ^= 1u;
             }
         }
-        if (fixups) atomicAdd(&ctr->n_fixup, (unsigned long long)fixups);
     }
 
     fence_before();
@@ -329,29 +338,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
 }  // namespace
 
-void launch_split_rows(const float *X, const float *Y, const Geom &g, int64_t p_pad, uint16_t *Zh, uint16_t *Zl,
-                       float *norms, float *inv_scale, Counters *ctr, cudaStream_t s) {
-    const int warps = 8;
-    k_split_rows<<<(unsigned)((g.n_pad + warps - 1) / warps), warps * 32, 0, s>>>(
-        X, Y, g.nx, g.n, g.n_pad, g.p, p_pad, (__half *)Zh, (__half *)Zl, norms, inv_scale, ctr);
+void launch_split_rows(const Batch &b, cudaStream_t s) {
+    if (b.nrows_total <= 0) return;
+    k_split_rows<<<(unsigned)((b.nrows_total + 7) / 8), 256, 0, s>>>(b);
 }
 
-cudaError_t launch_build_tc(const void *tmaps, const int4 *tiles, int ntiles, int64_t p_pad, const float *norms,
-                            const float *inv_scale, const float *X, const float *Y, const Geom &g, int stat,
-                            double sigma, double tau, float *D, Counters *ctr, int num_sms, cudaStream_t s) {
+cudaError_t launch_build_tc(const Batch &b, const void *tmaps, int num_sms, cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k_build_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (ntiles < 1) return cudaSuccess;
+    if (b.ntiles < 1) return cudaSuccess;
     const CUtensorMap *tm = (const CUtensorMap *)tmaps;
-    const float neg = (stat == 0) ? 0.f : (float)(-1.0 / (2.0 * sigma * sigma));
-    const int grid = ntiles < num_sms ? ntiles : num_sms;
-    k_build_tc<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(tm[0], tm[1], tm[2], tm[3], tiles, ntiles, (int)(p_pad / BK),
-                                                     norms, inv_scale, X, Y, g.nx, g.n, g.p, g.NKB, stat, neg,
-                                                     (float)tau, D, ctr);
+    const int grid = b.ntiles < num_sms ? (int)b.ntiles : num_sms;
+    k_build_tc<<<grid, NUM_THREADS, SMEM_BYTES, s>>>(tm[0], tm[1], tm[2], tm[3], b);
     return cudaGetLastError();
 }
 

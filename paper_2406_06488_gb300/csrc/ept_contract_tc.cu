@@ -52,7 +52,8 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*barriers*/ + 1024 /*ali
 constexpr unsigned long long ERR_WAIT_TMA = 0x101, ERR_WAIT_MMA = 0x102, ERR_WAIT_EPI = 0x103,
                              ERR_WAIT_MASK = 0x104, ERR_DRAIN = 0x105;
 
-constexpr uint32_t IDESC = idesc_bf16_f32(TC_M, TC_N);
+// kind::f16 instruction descriptor with A = B = FP16 (format 0), D = FP32, K-major
+constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 
 struct Bars {
     unsigned long long a_full[STAGES];   // 128 producer-thread arrivals
@@ -65,10 +66,35 @@ struct Bars {
     int abort_flag;
 };
 
+// the test fields, chunk and relabeling tile of global work unit u, read once into
+// registers (the asm statements' memory clobbers would otherwise force reloads)
+struct Unit {
+    Chunk ch;
+    int64_t q, m, Bp, mask0, part0, blk0, NKB;
+};
+
+__device__ __forceinline__ Unit decode_unit(const Batch &bt, int64_t u) {
+    const int t = find_test(bt.pre.units, bt.n_tests, u);
+    const TestDesc *d = &bt.desc[t];
+    Unit x;
+    const int64_t lu = u - bt.pre.units[t];
+    const int64_t MT = d->MT;
+    x.q = lu / MT;
+    x.m = lu % MT;
+    x.Bp = d->Bp;
+    x.mask0 = d->mask0;
+    x.part0 = d->part0;
+    x.blk0 = d->blk0;
+    x.NKB = d->NKB;
+    x.ch = bt.chunks[d->chunk0 + x.q];
+    return x;
+}
+
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_contract_tc(const __grid_constant__ CUtensorMap tmap_hi, const __grid_constant__ CUtensorMap tmap_lo,
-                  const uint32_t *__restrict__ maskT, const Chunk *__restrict__ chunks, int64_t nunits,
-                  int64_t MT, int64_t Bp, int64_t NKB, float *__restrict__ partial, Counters *ctr) {
+                  const Batch bt) {
+    Counters *ctr = bt.ctr;   // bounded-wait errors are recorded in test 0's counters
+    const int64_t nunits = bt.nunits_total;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     Bars *bars = reinterpret_cast<Bars *>(smem + STAGES * STAGE_BYTES);
@@ -109,7 +135,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             for (int s2 = 0; s2 < STAGES; ++s2) armed[s2] = -1;
             bool ok = true;
             for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
-                const Chunk ch = chunks[u / MT];
+                const Unit x = decode_unit(bt, u);
+                const Chunk ch = x.ch;
                 for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
                     if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_TMA)) {
                         ok = false;
@@ -117,7 +144,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     }
                     const uint32_t bfull = su32(&bars->b_full[stage]);
                     mbar_arrive_tx(bfull, 2 * B_BYTES);
-                    const int blk = (int)blk_index(ch.I, kb, NKB);
+                    const int blk = (int)(x.blk0 + blk_index(ch.I, kb, x.NKB));
                     uint8_t *st = smem + stage * STAGE_BYTES;
                     tma_load_3d(su32(st + A_BYTES), &tmap_hi, 0, 0, blk, bfull);
                     tma_load_3d(su32(st + A_BYTES + B_BYTES), &tmap_lo, 0, 0, blk, bfull);
@@ -150,7 +177,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             uint32_t phase = 0, acc_phase = 0;
             bool ok = true;
             for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
-                const Chunk ch = chunks[u / MT];
+                const Chunk ch = decode_unit(bt, u).ch;
                 if (!mbar_wait(su32(&bars->acc_empty[acc]), acc_phase ^ 1u, abort_flag, ctr, ERR_WAIT_MMA)) {
                     ok = false;
                     break;
@@ -205,9 +232,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-            const int64_t q = u / MT, m = u % MT;
-            const Chunk ch = chunks[q];
-            const int64_t b = m * TC_M + row;
+            const Unit x = decode_unit(bt, u);
+            const Chunk ch = x.ch;
+            const int64_t Bp = x.Bp;
+            const uint32_t *maskT = bt.maskT + x.mask0;
+            const int64_t b = x.m * TC_M + row;
             uint32_t bits[8];
 #pragma unroll
             for (int g = 0; g < 8; ++g) bits[g] = maskT[((int64_t)ch.I * 8 + g) * Bp + b];
@@ -230,7 +259,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
             fence_before();
             mbar_arrive(su32(&bars->acc_empty[acc]));
-            partial[q * Bp + b] = (s0 + s1) + (s2 + s3);
+            bt.partial[x.part0 + x.q * Bp + b] = (s0 + s1) + (s2 + s3);
             if (++acc == 2) {
                 acc = 0;
                 acc_phase ^= 1u;
@@ -243,9 +272,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         uint32_t phase = 0;
         bool ok = true;
         for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
-            const int64_t q = u / MT, m = u % MT;
-            const Chunk ch = chunks[q];
-            const int64_t b = m * TC_M + r;
+            const Unit x = decode_unit(bt, u);
+            const Chunk ch = x.ch;
+            const int64_t Bp = x.Bp;
+            const uint32_t *maskT = bt.maskT + x.mask0;
+            const int64_t b = x.m * TC_M + r;
             for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
                 const uint32_t w0 = maskT[(int64_t)(2 * kb) * Bp + b];
                 const uint32_t w1 = maskT[(int64_t)(2 * kb + 1) * Bp + b];
@@ -283,8 +314,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
 }  // namespace
 
-cudaError_t launch_contract_tc(const void *tmap_hi, const void *tmap_lo, const uint32_t *maskT,
-                               const Chunk *chunks, const Geom &g, float *partial, Counters *ctr, int num_sms,
+cudaError_t launch_contract_tc(const Batch &b, const void *tmap_hi, const void *tmap_lo, int num_sms,
                                cudaStream_t s) {
     static bool attr_set = false;
     if (!attr_set) {
@@ -293,16 +323,13 @@ cudaError_t launch_contract_tc(const void *tmap_hi, const void *tmap_lo, const u
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int64_t MT = g.Bp / TC_M;
-    const int64_t nunits = g.nchunks * MT;
     int64_t grid = num_sms;
-    if (grid > nunits) grid = nunits;
+    if (grid > b.nunits_total) grid = b.nunits_total;
     if (grid < 1) return cudaSuccess;
     CUtensorMap th, tl;
     memcpy(&th, tmap_hi, sizeof(CUtensorMap));
     memcpy(&tl, tmap_lo, sizeof(CUtensorMap));
-    k_contract_tc<<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(th, tl, maskT, chunks, nunits, MT, g.Bp, g.NKB,
-                                                                  partial, ctr);
+    k_contract_tc<<<(unsigned)grid, NUM_THREADS, SMEM_BYTES, s>>>(th, tl, b);
     return cudaGetLastError();
 }
 
@@ -324,12 +351,12 @@ static EncodeTiledFn encode_fn(char *err, size_t errlen) {
     return fn;
 }
 
-bool encode_rows_tmaps(void *tmaps4, const uint16_t *Zh, const uint16_t *Zl, int64_t n_pad, int64_t p_pad,
+bool encode_rows_tmaps(void *tmaps4, const uint16_t *Zh, const uint16_t *Zl, int64_t nrows, int64_t p_stride,
                        char *err, size_t errlen) {
     EncodeTiledFn enc = encode_fn(err, errlen);
     if (!enc) return false;
-    const cuuint64_t dims[2] = {(cuuint64_t)p_pad, (cuuint64_t)n_pad};
-    const cuuint64_t strides[1] = {(cuuint64_t)p_pad * 2};
+    const cuuint64_t dims[2] = {(cuuint64_t)p_stride, (cuuint64_t)nrows};
+    const cuuint64_t strides[1] = {(cuuint64_t)p_stride * 2};
     const cuuint32_t estr[2] = {1, 1};
     const cuuint32_t box_a[2] = {64, 128}, box_b[2] = {64, 256};
     CUtensorMap *out = (CUtensorMap *)tmaps4;

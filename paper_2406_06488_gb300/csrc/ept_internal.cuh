@@ -1,4 +1,5 @@
-// ept_internal.cuh -- layouts and launchers shared by libept's translation units.
+// ept_internal.cuh -- layouts, batch descriptors and launchers shared by libept's
+// translation units.
 //
 // Packed block storage.  The pooled matrix W = [[D_XX, D_XY], [D_XY', D_YY]] of the
 // n = nx + ny pooled rows (x rows first) is symmetric, so only its upper part is
@@ -22,46 +23,29 @@
 // then differences S - 2L + T of sums over the smaller one, and using the smaller
 // group keeps the rounding errors of T small relative to the statistic when the
 // sample sizes are very unequal.  When ny < nx the stored masks mark y* (`comp`).
+//
+// Batches.  Every kernel works on a batch of independent tests (a single test is a
+// batch of one).  Each test's arrays live at its own offsets in the batch's
+// concatenated buffers (TestDesc); a kernel maps its global work index to a test
+// by binary search in a prefix-sum array over the tests (BatchPrefix).
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
 
 namespace ept {
 
-constexpr int PANEL = 256;   // rows per panel (MMA N of the contraction)
-constexpr int KB = 64;       // columns per K-block (one 128-byte swizzle row of BF16)
+constexpr int PANEL = 256;       // rows per panel (MMA N of the contraction)
+constexpr int KB = 64;           // columns per K-block (one 128-byte swizzle row of 16-bit values)
 constexpr int KB_PER_PANEL = PANEL / KB;
-constexpr int CHUNK_KB = 16; // K-blocks per contraction work unit (1024 columns)
-constexpr int COL_PAD = 256; // relabeling columns padded to this multiple
-
-struct Geom {
-    int64_t nx, ny, n, p;
-    int64_t n_pad, NP, NKB, nblk, nw;
-    int64_t ncols;   // relabeling columns actually used (identity + permuted)
-    int64_t Bp;      // ncols padded to COL_PAD
-    int64_t nchunks; // contraction work chunks (panel, K-block range)
-    bool comp;       // masks mark y* (ny < nx) instead of x*
-    int64_t m;       // size of the contracted group: min(nx, ny)
-    int64_t other;   // size of the other group: max(nx, ny)
-};
+constexpr int CHUNK_KB_DEFAULT = 16;  // K-blocks per contraction work unit (1024 columns)
+constexpr int COL_PAD = 256;     // relabeling columns padded to this multiple
+constexpr int BUILD_KB = 64;     // p is padded to a multiple of this for the tensor-core build
+constexpr int TC_TILE_M = 128;   // relabelings per contraction work unit
 
 __host__ __device__ inline int64_t blk_off(int64_t I, int64_t NKB) { return I * NKB - 2 * I * (I - 1); }
 __host__ __device__ inline int64_t blk_index(int64_t I, int64_t kb, int64_t NKB) {
     return blk_off(I, NKB) + (kb - KB_PER_PANEL * I);
 }
-
-Geom make_geom(int64_t nx, int64_t ny, int64_t p, int64_t ncols);
-
-// chunk q of the contraction: panel I, K-blocks [kb0, kb1)
-struct Chunk { int I, kb0, kb1, pad; };
-
-// device parameters of the statistic's final combination
-struct StatConst {
-    double cT;        // (n / (nx ny))^2
-    double S_tilde;   // unused: S~ is summed from the per-panel parts by the combination
-    double inv_o2;    // 1 / other^2 (the larger group's size)
-    double sign;      // -1 for ED, +1 for MMD
-};
 
 struct Counters {
     unsigned long long n_ge;
@@ -69,60 +53,123 @@ struct Counters {
     unsigned long long n_fixup;
     unsigned long long bad_mask;
     unsigned long long nonfinite;
-    unsigned long long err_code;   // device-side bounded waits that gave up, etc.
-    unsigned long long maxabs_bits;  // bit pattern of max |x| over the finite inputs (FP32, as an integer)
+    unsigned long long err_code;     // device-side bounded waits that gave up (kept in test 0)
+    unsigned int max_d_bits;         // max |D_ij| over the stored blocks (FP32 bits; non-negative values
+    unsigned int max_u_bits;         //   order like their bit patterns), max |u_i|,
+    unsigned int max_dc_bits;        //   max |dcorr_i|: they bound |C| for the FP16 scale of the packing
+    unsigned int pad_;
 };
 
-// ---- launchers (ept_kernels.cu) ----
-void launch_perm_masks(uint64_t seed, int nx, int ny, int64_t b_first, int64_t count, int64_t ncols,
-                       int nw, bool comp, uint32_t *maskT, cudaStream_t s);
-void launch_user_masks(const uint32_t *user, int64_t n_masks, int nwu, int nx, int n, int64_t ncols,
-                       int nw, bool comp, uint32_t *maskT, Counters *ctr, cudaStream_t s);
-void launch_masks_to_rows(const uint32_t *maskT, int64_t ncols, int nw, int64_t count, int nwu,
-                          uint32_t *rows, cudaStream_t s);
-void launch_check_finite(const float *a, int64_t count, Counters *ctr, cudaStream_t s);
-void launch_norms(const float *X, const float *Y, const Geom &g, float *norms, cudaStream_t s);
-void launch_build_simt(const float *X, const float *Y, const float *norms, const Geom &g, int stat,
-                       double sigma, double tau, const int2 *blk_info, float *D, Counters *ctr,
-                       cudaStream_t s);
-void launch_blocksums(const float *D, const Geom &g, double *rowpart, double *colpart, cudaStream_t s);
-// r: n_pad doubles; Spart: n_pad / 32 doubles; Upart, Stpart: one double per panel (NP)
-void launch_rowsum_reduce(const double *rowpart, const double *colpart, const Geom &g, double *r, double *Spart,
-                          cudaStream_t s);
-void launch_center(const double *r, const double *Spart, const Geom &g, float *u, double *dcorr, double *Upart,
-                   double *Stpart, StatConst *sc, int stat, cudaStream_t s);
-void launch_pack_fp32(const float *D, const float *u, const double *dcorr, const Geom &g,
-                      const int2 *blk_info, float *C, cudaStream_t s);
-void launch_pack_bf16(const float *D, const float *u, const double *dcorr, const Geom &g,
-                      const int2 *blk_info, uint16_t *Chi, uint16_t *Clo, cudaStream_t s);
-void launch_contract_simt(const float *C, const uint32_t *maskT, const Chunk *chunks, const Geom &g,
-                          float *partial, cudaStream_t s);
-void launch_combine(const float *partial, int64_t nparts, const Geom &g, const StatConst *sc,
-                    const double *Stpart, double *stats, Counters *ctr, cudaStream_t s);
-void launch_expand_blocks(const float *D, const Geom &g, float *out, cudaStream_t s);
+// Power-of-two scale c of a test's packed contraction operand, from the bound
+// |C_ij| <= 2 (max|D| + 2 max|u|) + max|dcorr|: c |C| < 2^14, inside FP16's range.
+// The exponent is clamped to [-60, 60] (c and 1/c stay normal FP32 numbers).
+__device__ __forceinline__ float packed_scale(const Counters &k) {
+    const float bound = 2.f * (__uint_as_float(k.max_d_bits) + 2.f * __uint_as_float(k.max_u_bits)) +
+                        __uint_as_float(k.max_dc_bits);
+    if (!(bound > 0.f) || !(bound < 3.0e38f)) return 1.f;
+    int e;
+    frexpf(bound, &e);   // bound = f 2^e, 0.5 <= f < 1
+    int k2 = 14 - e;
+    k2 = k2 < -60 ? -60 : (k2 > 60 ? 60 : k2);
+    return ldexpf(1.f, k2);
+}
 
-// ---- tcgen05 contraction (ept_contract_tc.cu) ----
-// Returns cudaSuccess or the launch error.  Chi/Clo: packed BF16 hi/lo parts.
-cudaError_t launch_contract_tc(const void *tmap_hi, const void *tmap_lo, const uint32_t *maskT,
-                               const Chunk *chunks, const Geom &g, float *partial, Counters *ctr,
-                               int num_sms, cudaStream_t s);
-// Encodes the two TMA tensor maps over the packed hi/lo blocks (host side).
-bool encode_block_tmaps(void *tmap_hi, void *tmap_lo, const uint16_t *Chi, const uint16_t *Clo,
-                        int64_t nblk, char *err, size_t errlen);
-// Encodes four TMA tensor maps over the FP16 hi/lo pooled rows [n_pad x p_pad]:
-// (hi, lo) with 64 x 128 boxes, then (hi, lo) with 64 x 256 boxes.
-bool encode_rows_tmaps(void *tmaps4, const uint16_t *Zh, const uint16_t *Zl, int64_t n_pad, int64_t p_pad,
+// chunk q of a test's contraction: panel I, K-blocks [kb0, kb1)
+struct Chunk { int I, kb0, kb1, pad; };
+// a stored block of the batch: test t, panel I, K-block kb
+struct BlkInfo { int t, I, kb, pad; };
+// a build tile of the batch: test t, rows of panel I (half h), columns of panel J >= I
+struct Tile { int t, I, J, h; };
+
+// One test of a batch as the kernels see it.  Offsets are element offsets into the
+// batch's concatenated buffers.
+struct TestDesc {
+    const float *X, *Y;              // device rows (nx x p, ny x p)
+    const uint32_t *user_masks;      // caller relabelings (row-major, nwu words each) or null
+    double *out_stats;               // device destination of the B permuted statistics, or null
+    int64_t nx, ny, n, p, B;
+    int64_t n_pad, NP, NKB, nblk, nw, ncols, Bp, MT, nchunks, nparts, m, other, p_pad;
+    int64_t row0;     // rows: norms, inverse scales, r, u, dcorr, FP16 rows (n_pad)
+    int64_t blk0;     // blocks: D, C hi/lo, row parts (x256), column parts (x64) (nblk)
+    int64_t pan0;     // panels: Upart, Stpart (NP)
+    int64_t sp0;      // row groups of 32: Spart (n_pad / 32)
+    int64_t mask0;    // mask words (nw * Bp)
+    int64_t chunk0;   // chunk table (nchunks)
+    int64_t part0;    // partials (nparts * Bp)
+    int64_t col0;     // statistics (ncols)
+    uint64_t seed;
+    int32_t stat, comp, kblocks, nwu;
+    float neg_inv_2s2, tau;
+    double cT, inv_o2, sign, kappa, inv_n, inv_2n2;
+};
+
+// Prefix sums over the tests (n_tests + 1 entries each) of the work dimensions.
+struct BatchPrefix {
+    const int64_t *rows;    // n_pad
+    const int64_t *panels;  // NP
+    const int64_t *cols;    // Bp
+    const int64_t *units;   // nchunks * MT (tensor-core contraction work units)
+    const int64_t *simt;    // nchunks * 2 * (Bp / 64) (plain contraction work items)
+};
+
+// Device view of one batched run.
+struct Batch {
+    int n_tests;
+    const TestDesc *desc;
+    BatchPrefix pre;
+    const BlkInfo *blk;
+    const Tile *tiles;
+    const Chunk *chunks;
+    int64_t nblk_total, ntiles, nrows_total, npan_total, ncols_total, nunits_total, nsimt_total;
+    int64_t p_stride;                    // row stride of the FP16 rows (max p_pad)
+    float *norms, *iscale, *u;
+    uint16_t *Zh, *Zl, *Chi, *Clo;
+    float *D, *partial;
+    double *rowpart, *colpart, *r, *Spart, *dcorr, *Upart, *Stpart, *stats, *observed;
+    uint32_t *maskT;
+    Counters *ctr;
+};
+
+__device__ __forceinline__ int find_test(const int64_t *pre, int nt, int64_t g) {
+    int lo = 0, hi = nt - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---- launchers (ept_kernels.cu) ----
+void launch_norms(const Batch &b, cudaStream_t s);                       // plain path: norms + finite check
+void launch_build_simt(const Batch &b, cudaStream_t s);
+void launch_blocksums(const Batch &b, cudaStream_t s);
+void launch_rowsum_reduce(const Batch &b, cudaStream_t s);
+void launch_center(const Batch &b, cudaStream_t s);
+void launch_pack(const Batch &b, bool split, cudaStream_t s);   // split: FP16 hi/lo (tensor-core path)
+void launch_masks(const Batch &b, cudaStream_t s);                       // draws or caller masks
+void launch_contract_simt(const Batch &b, cudaStream_t s);
+void launch_combine(const Batch &b, cudaStream_t s);                     // statistics, counts, outputs
+
+// single-draw-stream export (ept_perm_masks): columns 0..count-1 = draws b0..b0+count-1
+void launch_perm_masks_plain(uint64_t seed, int nx, int ny, int64_t b0, int64_t count, int nw, uint32_t *maskT,
+                             cudaStream_t s);
+void launch_masks_to_rows(const uint32_t *maskT, int64_t ncols, int nw, int64_t count, int nwu, uint32_t *rows,
+                          cudaStream_t s);
+void launch_expand_blocks(const float *D, int64_t n, int64_t NKB, float *out, cudaStream_t s);
+
+// ---- tensor-core kernels (ept_build_tc.cu, ept_contract_tc.cu) ----
+void launch_split_rows(const Batch &b, cudaStream_t s);                  // FP16 hi/lo rows, norms, checks
+cudaError_t launch_build_tc(const Batch &b, const void *tmaps4, int num_sms, cudaStream_t s);
+cudaError_t launch_contract_tc(const Batch &b, const void *tmap_hi, const void *tmap_lo, int num_sms,
+                               cudaStream_t s);
+// TMA descriptors: the packed hi/lo blocks [nblk_total x 256 x 64] and the FP16
+// rows [nrows x p_stride] (hi, lo with 64 x 128 boxes, then hi, lo with 64 x 256 boxes)
+bool encode_block_tmaps(void *tmap_hi, void *tmap_lo, const uint16_t *Chi, const uint16_t *Clo, int64_t nblk,
+                        char *err, size_t errlen);
+bool encode_rows_tmaps(void *tmaps4, const uint16_t *Zh, const uint16_t *Zl, int64_t nrows, int64_t p_stride,
                        char *err, size_t errlen);
 
-// ---- tcgen05 block build (ept_build_tc.cu) ----
-constexpr int BUILD_KB = 64;   // p is padded to a multiple of this
-// Zh, Zl: FP16 hi / lo parts of the rows scaled by per-row powers of two; inv_scale[i]
-// is the inverse scale of row i; non-finite inputs are counted in ctr->nonfinite.
-void launch_split_rows(const float *X, const float *Y, const Geom &g, int64_t p_pad, uint16_t *Zh, uint16_t *Zl,
-                       float *norms, float *inv_scale, Counters *ctr, cudaStream_t s);
-// tiles: (panel I, half h, column panel J >= I); tmaps: the four maps of encode_rows_tmaps
-cudaError_t launch_build_tc(const void *tmaps, const int4 *tiles, int ntiles, int64_t p_pad, const float *norms,
-                            const float *inv_scale, const float *X, const float *Y, const Geom &g, int stat,
-                            double sigma, double tau, float *D, Counters *ctr, int num_sms, cudaStream_t s);
+void set_last_error(const char *msg);   // ept_api.cu
 
 }  // namespace ept

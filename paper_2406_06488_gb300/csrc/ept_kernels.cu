@@ -1,37 +1,17 @@
-// ept_kernels.cu -- SIMT kernels of libept: permutation stream, block build,
-// centring and packing, the plain FP32 contraction and the final combination.
+// ept_kernels.cu -- SIMT kernels of libept: relabeling draws, the plain FP32 block
+// build, centring and packing, the plain FP32 contraction and the final
+// combination.  Every kernel processes a batch of tests (ept_internal.cuh).
 #include "ept_internal.cuh"
 
-#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cstdint>
 
 namespace ept {
 
-Geom make_geom(int64_t nx, int64_t ny, int64_t p, int64_t ncols) {
-    Geom g;
-    g.nx = nx; g.ny = ny; g.n = nx + ny; g.p = p;
-    g.n_pad = (g.n + PANEL - 1) / PANEL * PANEL;
-    g.NP = g.n_pad / PANEL;
-    g.NKB = g.n_pad / KB;
-    g.nblk = blk_off(g.NP, g.NKB);
-    g.nw = g.n_pad / 32;
-    g.ncols = ncols;
-    g.Bp = (ncols + COL_PAD - 1) / COL_PAD * COL_PAD;
-    int64_t q = 0;
-    for (int64_t I = 0; I < g.NP; ++I) {
-        const int64_t len = g.NKB - KB_PER_PANEL * I;
-        q += (len + CHUNK_KB - 1) / CHUNK_KB;
-    }
-    g.nchunks = q;
-    g.comp = ny < nx;
-    g.m = g.comp ? ny : nx;
-    g.other = g.comp ? nx : ny;
-    return g;
-}
-
 // ---------------------------------------------------------------------------
 // Permutation stream: Philox4x32-10 (Salmon et al., SC'11) drives Knuth's selection
-// sampling; see k_perm_masks.
+// sampling; see draw_column.
+
 // floor(u * m / 2^64) for a 64-bit u and a 32-bit m, from two 32x32->64 products:
 // with u = uh 2^32 + ul, the value is floor((uh m + floor(ul m / 2^32)) / 2^32)
 // (the dropped low word of ul m cannot carry across a multiple of 2^32), and
@@ -50,44 +30,32 @@ __device__ __forceinline__ uint32_t valid_bits(int w, int n) {
     return (1u << (n - lo)) - 1u;
 }
 
-// One warp per relabeling column c.  Philox4x32-10: each round multiplies counter
-// words 0 and 2 by the two Philox multipliers (one wide multiply gives both
-// halves), mixes the high halves with words 1 and 3 and the round key, and the key
-// advances by the two Weyl constants between rounds.
-// Draw b = b_first + c of the stream:
-// b = 0 is the identity; b >= 1 is Knuth's selection sampling (Algorithm S) over
-// the n pooled slots, slot t kept iff floor(u_t * (n - t) / 2^64) < need, with
-// u_t the 64-bit word (t mod 2) of Philox4x32-10(counter = (t/2, 0, b lo, b hi),
-// key = (seed lo, seed hi)).  The warp draws 64 consecutive slots at once: lane l
-// runs the Philox call of slots base+2l and base+2l+1 and forms their two
-// floor(u (n - t) / 2^64) values; shuffles then place slot base+l on lane l (first
-// word) and slot base+32+l on lane l (second word), so one ballot is one output
-// word.  The sequential dependence through `need` is resolved by a fixed-point
-// iteration over ballots: with every earlier decision known a slot's decision is
-// determined, so iterating "decide from the previous guesses" reaches the unique
-// sequential solution in at most 65 rounds (almost always 1 or 2).
-// comp: store the complement (the y* members) of every real draw.
-__global__ void __launch_bounds__(256) k_perm_masks(uint64_t seed, int nx, int ny, int64_t b_first,
-                                                    int64_t count, int64_t ncols, int nw, int comp,
-                                                    uint32_t *__restrict__ maskT) {
+// One warp writes one relabeling column (words w = 0..nw-1 at col[w * stride]).
+// Philox4x32-10: each round multiplies counter words 0 and 2 by the two Philox
+// multipliers (one wide multiply gives both halves), mixes the high halves with words
+// 1 and 3 and the round key, and the key advances by the two Weyl constants.
+// Draw b of the stream: b = 0 is the identity; b >= 1 is Knuth's selection sampling
+// (Algorithm S) over the n pooled slots, slot t kept iff floor(u_t (n - t) / 2^64)
+// < need, with u_t the 64-bit word (t mod 2) of Philox4x32-10(counter = (t/2, 0,
+// b lo, b hi), key = (seed lo, seed hi)).  The warp draws 64 consecutive slots at
+// once: lane l runs the Philox call of slots base+2l and base+2l+1 and forms their
+// two floor(u (n - t) / 2^64) values; shuffles then place slot base+l on lane l
+// (first word) and slot base+32+l on lane l (second word), so one ballot is one
+// output word.  The sequential dependence through `need` is resolved by a
+// fixed-point iteration over ballots: with every earlier decision known a slot's
+// decision is determined, so iterating "decide from the previous guesses" reaches
+// the unique sequential solution in at most 65 rounds (almost always 1 or 2).
+// comp: store the complement (the y* members).
+__device__ void draw_column(uint64_t seed, int nx, int n, int64_t b, int nw, bool comp, uint32_t *col,
+                            int64_t stride) {
     const int lane = threadIdx.x & 31;
-    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (c >= ncols) return;
-    const int n = nx + ny;
-    uint32_t *col = maskT + c;
-    if (c >= count) {
-        for (int w = lane; w < nw; w += 32) col[(int64_t)w * ncols] = 0u;
-        return;
-    }
-    const int64_t b = b_first + c;
     if (b == 0) {
         for (int w = lane; w < nw; w += 32) {
             const uint32_t v = valid_bits(w, nx);
-            col[(int64_t)w * ncols] = comp ? (~v & valid_bits(w, n)) : v;
+            col[(int64_t)w * stride] = comp ? (~v & valid_bits(w, n)) : v;
         }
         return;
     }
-    // Philox round keys of this seed (the key schedule adds the two Weyl constants)
     uint32_t kx[10], ky[10];
     kx[0] = (uint32_t)seed;
     ky[0] = (uint32_t)(seed >> 32);
@@ -120,19 +88,16 @@ __global__ void __launch_bounds__(256) k_perm_masks(uint64_t seed, int nx, int n
             ra = (uint32_t)mulhi_64x32(((uint64_t)x1 << 32) | x0, (uint32_t)(n - tp));
             if (tp + 1 < n) rb = (uint32_t)mulhi_64x32(((uint64_t)x3 << 32) | x2, (uint32_t)(n - tp - 1));
         }
-        // slot base + lane  <- (ra or rb) of lane lane/2;  slot base + 32 + lane <- of lane 16 + lane/2
         const uint32_t a0 = __shfl_sync(0xFFFFFFFFu, ra, src), b0 = __shfl_sync(0xFFFFFFFFu, rb, src);
         const uint32_t a1 = __shfl_sync(0xFFFFFFFFu, ra, src + 16), b1 = __shfl_sync(0xFFFFFFFFu, rb, src + 16);
         const int r0 = (int)min(odd ? b0 : a0, 0x7FFFFFFFu);
         const int r1 = (int)min(odd ? b1 : a1, 0x7FFFFFFFu);
-        bool s0 = r0 < need, s1 = r1 < need;
-        unsigned m0 = __ballot_sync(0xFFFFFFFFu, s0), m1 = __ballot_sync(0xFFFFFFFFu, s1);
+        unsigned m0 = __ballot_sync(0xFFFFFFFFu, r0 < need), m1 = __ballot_sync(0xFFFFFFFFu, r1 < need);
         for (int it = 0; it < 70; ++it) {
             const int before0 = __popc(m0 & lt);
             const int before1 = __popc(m0) + __popc(m1 & lt);
-            const bool n0 = r0 < need - before0;
-            const bool n1 = r1 < need - before1;
-            const unsigned nm0 = __ballot_sync(0xFFFFFFFFu, n0), nm1 = __ballot_sync(0xFFFFFFFFu, n1);
+            const unsigned nm0 = __ballot_sync(0xFFFFFFFFu, r0 < need - before0);
+            const unsigned nm1 = __ballot_sync(0xFFFFFFFFu, r1 < need - before1);
             const bool same = (nm0 == m0) && (nm1 == m1);
             m0 = nm0;
             m1 = nm1;
@@ -146,56 +111,70 @@ __global__ void __launch_bounds__(256) k_perm_masks(uint64_t seed, int nx, int n
                 v0 = ~v0 & valid_bits(w, n);
                 v1 = ~v1 & valid_bits(w + 1, n);
             }
-            col[(int64_t)w * ncols] = v0;
-            col[(int64_t)(w + 1) * ncols] = v1;
+            col[(int64_t)w * stride] = v0;
+            col[(int64_t)(w + 1) * stride] = v1;
         }
     }
 }
 
-void launch_perm_masks(uint64_t seed, int nx, int ny, int64_t b_first, int64_t count, int64_t ncols,
-                       int nw, bool comp, uint32_t *maskT, cudaStream_t s) {
-    const int warps = 8;
-    const int64_t grid = (ncols + warps - 1) / warps;
-    k_perm_masks<<<(unsigned)grid, warps * 32, 0, s>>>(seed, nx, ny, b_first, count, ncols, nw, comp ? 1 : 0,
-                                                       maskT);
-}
-
-// Caller-given relabelings, row-major [m][nwu], become columns 1..n_masks of maskT;
-// column 0 is written as the identity by the caller.  A relabeling with a popcount
-// other than nx, or with bits at t >= n, is counted in ctr->bad_mask.
-__global__ void k_user_masks(const uint32_t *__restrict__ user, int64_t n_masks, int nwu, int nx, int n,
-                             int64_t ncols, int nw, int comp, uint32_t *__restrict__ maskT, Counters *ctr) {
+// One warp per relabeling column of the batch: column 0 of a test is the identity,
+// columns 1..B its draws 1..B (or the caller's relabelings, validated: exactly nx
+// members among the n rows), padding columns are zero.
+__global__ void __launch_bounds__(256) k_masks(const Batch bt) {
     const int lane = threadIdx.x & 31;
-    const int64_t m = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (m >= n_masks) return;
-    const uint32_t *row = user + m * nwu;
-    uint32_t *col = maskT + (m + 1);
-    int cnt = 0;
-    bool bad = false;
-    for (int w = lane; w < nw; w += 32) {
-        uint32_t v = (w < nwu) ? row[w] : 0u;
-        const uint32_t valid = valid_bits(w, n);
-        if (v & ~valid) bad = true;
-        v &= valid;
-        cnt += __popc(v);
-        col[(int64_t)w * ncols] = comp ? (~v & valid_bits(w, n)) : v;
+    const int64_t gc = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gc >= bt.ncols_total) return;
+    const int t = find_test(bt.pre.cols, bt.n_tests, gc);
+    const TestDesc d = bt.desc[t];
+    const int64_t c = gc - bt.pre.cols[t];
+    const int n = (int)d.n, nw = (int)d.nw;
+    uint32_t *col = bt.maskT + d.mask0 + c;
+    if (c >= d.ncols) {
+        for (int w = lane; w < nw; w += 32) col[(int64_t)w * d.Bp] = 0u;
+        return;
     }
-    for (int off = 16; off; off >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, off);
-    bad = __any_sync(0xFFFFFFFFu, bad);
-    if (lane == 0 && (bad || cnt != nx)) atomicAdd(&ctr->bad_mask, 1ull);
+    if (c >= 1 && d.user_masks) {
+        const uint32_t *row = d.user_masks + (c - 1) * d.nwu;
+        int cnt = 0;
+        bool bad = false;
+        for (int w = lane; w < nw; w += 32) {
+            uint32_t v = (w < d.nwu) ? row[w] : 0u;
+            const uint32_t valid = valid_bits(w, n);
+            if (v & ~valid) bad = true;
+            v &= valid;
+            cnt += __popc(v);
+            col[(int64_t)w * d.Bp] = d.comp ? (~v & valid) : v;
+        }
+        for (int off = 16; off; off >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, off);
+        bad = __any_sync(0xFFFFFFFFu, bad);
+        if (lane == 0 && (bad || cnt != d.nx)) atomicAdd(&bt.ctr[t].bad_mask, 1ull);
+        return;
+    }
+    draw_column(d.seed, (int)d.nx, n, c, nw, d.comp != 0, col, d.Bp);
 }
 
-void launch_user_masks(const uint32_t *user, int64_t n_masks, int nwu, int nx, int n, int64_t ncols,
-                       int nw, bool comp, uint32_t *maskT, Counters *ctr, cudaStream_t s) {
-    if (n_masks <= 0) return;
-    const int warps = 8;
-    k_user_masks<<<(unsigned)((n_masks + warps - 1) / warps), warps * 32, 0, s>>>(user, n_masks, nwu, nx, n,
-                                                                                 ncols, nw, comp ? 1 : 0, maskT, ctr);
+void launch_masks(const Batch &b, cudaStream_t s) {
+    if (b.ncols_total <= 0) return;
+    k_masks<<<(unsigned)((b.ncols_total + 7) / 8), 256, 0, s>>>(b);
+}
+
+// the stream itself, for export: column c = draw b0 + c
+__global__ void __launch_bounds__(256) k_perm_masks_plain(uint64_t seed, int nx, int ny, int64_t b0, int64_t count,
+                                                          int nw, uint32_t *__restrict__ maskT) {
+    const int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (c >= count) return;
+    draw_column(seed, nx, nx + ny, b0 + c, nw, false, maskT + c, count);
+}
+
+void launch_perm_masks_plain(uint64_t seed, int nx, int ny, int64_t b0, int64_t count, int nw, uint32_t *maskT,
+                             cudaStream_t s) {
+    if (count <= 0) return;
+    k_perm_masks_plain<<<(unsigned)((count + 7) / 8), 256, 0, s>>>(seed, nx, ny, b0, count, nw, maskT);
 }
 
 // maskT columns 0..count-1 -> row-major [count][nwu]
-__global__ void k_masks_to_rows(const uint32_t *__restrict__ maskT, int64_t ncols, int nw, int64_t count,
-                                int nwu, uint32_t *__restrict__ rows) {
+__global__ void k_masks_to_rows(const uint32_t *__restrict__ maskT, int64_t ncols, int nw, int64_t count, int nwu,
+                                uint32_t *__restrict__ rows) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= count * nwu) return;
     const int64_t c = idx / nwu;
@@ -203,69 +182,50 @@ __global__ void k_masks_to_rows(const uint32_t *__restrict__ maskT, int64_t ncol
     rows[idx] = maskT[(int64_t)w * ncols + c];
 }
 
-void launch_masks_to_rows(const uint32_t *maskT, int64_t ncols, int nw, int64_t count, int nwu,
-                          uint32_t *rows, cudaStream_t s) {
+void launch_masks_to_rows(const uint32_t *maskT, int64_t ncols, int nw, int64_t count, int nwu, uint32_t *rows,
+                          cudaStream_t s) {
     const int64_t tot = count * nwu;
     if (tot <= 0) return;
     k_masks_to_rows<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(maskT, ncols, nw, count, nwu, rows);
 }
 
 // ---------------------------------------------------------------------------
-// Counts non-finite inputs and records max |x| (non-negative FP32 values order like
-// their bit patterns, so an integer atomicMax on the bits gives the maximum).
-__global__ void k_check_finite(const float *__restrict__ a, int64_t count, Counters *ctr) {
-    bool bad = false;
-    uint32_t mx = 0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const float v = a[i];
-        if (isfinite(v)) mx = max(mx, __float_as_uint(fabsf(v)));
-        else bad = true;
-    }
-    for (int off = 16; off; off >>= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
-    if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicAdd(&ctr->nonfinite, 1ull);
-    if ((threadIdx.x & 31) == 0 && mx) atomicMax(&ctr->maxabs_bits, (unsigned long long)mx);
+__device__ __forceinline__ const float *pooled_row(const TestDesc &d, int64_t i) {
+    return (i < d.nx) ? d.X + i * d.p : d.Y + (i - d.nx) * d.p;
 }
 
-void launch_check_finite(const float *a, int64_t count, Counters *ctr, cudaStream_t s) {
-    if (count <= 0) return;
-    int64_t grid = (count + 255) / 256;
-    if (grid > 4096) grid = 4096;
-    k_check_finite<<<(unsigned)grid, 256, 0, s>>>(a, count, ctr);
-}
-
-__device__ __forceinline__ const float *pooled_row(const float *X, const float *Y, int64_t nx, int64_t i,
-                                                   int64_t p) {
-    return (i < nx) ? X + i * p : Y + (i - nx) * p;
-}
-
-// Squared row norms ||z_i||^2 of the pooled rows, exact products summed in FP64 and
-// rounded once to FP32 (padded rows: 0).  One warp per row.
-__global__ void k_norms(const float *__restrict__ X, const float *__restrict__ Y, int64_t nx, int64_t n,
-                        int64_t n_pad, int64_t p, float *__restrict__ norms) {
+// Plain path: squared row norms ||z_i||^2 of the pooled rows, exact products summed
+// in FP64 and rounded once to FP32 (padded rows: 0), and the count of non-finite
+// inputs.  One warp per row of the batch.
+__global__ void __launch_bounds__(256) k_norms(const Batch bt) {
     const int lane = threadIdx.x & 31;
-    const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n_pad) return;
+    const int64_t gr = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (gr >= bt.nrows_total) return;
+    const int t = find_test(bt.pre.rows, bt.n_tests, gr);
+    const TestDesc d = bt.desc[t];
+    const int64_t i = gr - d.row0;
     double acc = 0.0;
-    if (i < n) {
-        const float *z = pooled_row(X, Y, nx, i, p);
-        for (int64_t k = lane; k < p; k += 32) {
-            const double v = (double)z[k];
-            acc = fma(v, v, acc);
+    bool bad = false;
+    if (i < d.n) {
+        const float *z = pooled_row(d, i);
+        for (int64_t k = lane; k < d.p; k += 32) {
+            const float v = z[k];
+            bad |= !isfinite(v);
+            acc = fma((double)v, (double)v, acc);
         }
     }
     for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
-    if (lane == 0) norms[i] = (float)acc;
+    if (__any_sync(0xFFFFFFFFu, bad) && lane == 0) atomicAdd(&bt.ctr[t].nonfinite, 1ull);
+    if (lane == 0) bt.norms[gr] = (float)acc;
 }
 
-void launch_norms(const float *X, const float *Y, const Geom &g, float *norms, cudaStream_t s) {
-    const int warps = 8;
-    k_norms<<<(unsigned)((g.n_pad + warps - 1) / warps), warps * 32, 0, s>>>(X, Y, g.nx, g.n, g.n_pad, g.p,
-                                                                              norms);
+void launch_norms(const Batch &b, cudaStream_t s) {
+    if (b.nrows_total <= 0) return;
+    k_norms<<<(unsigned)((b.nrows_total + 7) / 8), 256, 0, s>>>(b);
 }
 
 // ---------------------------------------------------------------------------
-// Block build, SIMT FP32 (Algorithm 1 block construction; Algorithm 3 entries
+// Plain block build, SIMT FP32 (Algorithm 1 block construction; Algorithm 3 entries
 // through the expansion ||x||^2 + ||y||^2 - 2 x.y).  One CTA computes half of a
 // stored 256x64 block (128 rows x 64 columns): 256 threads, 8x4 outputs each,
 // K-loop over p in steps of 16 staged through shared memory.
@@ -273,22 +233,16 @@ void launch_norms(const float *X, const float *Y, const Geom &g, float *norms, c
 // (cancellation-prone near-duplicate) is recomputed directly as sum (x - y)^2 in
 // FP64; then sqrt (ED) or exp(-d2 / (2 sigma^2)) (MMD); the diagonal is exactly 0
 // (ED) or 1 (MMD); padded rows and columns are 0.
-__device__ __forceinline__ float finish_entry(float d2, int stat, float neg_inv_2s2) {
-    return stat == 0 ? sqrtf(d2) : expf(d2 * neg_inv_2s2);
-}
-
-__global__ void __launch_bounds__(256) k_build_simt(const float *__restrict__ X, const float *__restrict__ Y,
-                                                    const float *__restrict__ norms, int64_t nx, int64_t n,
-                                                    int64_t p, int64_t NKB, int stat, float neg_inv_2s2,
-                                                    float tau, const int2 *__restrict__ blk_info,
-                                                    float *__restrict__ D, Counters *ctr) {
+__global__ void __launch_bounds__(256) k_build_simt(const Batch bt) {
     __shared__ float As[16][128 + 4];
     __shared__ float Bs[16][64 + 4];
-    const int64_t blk = blockIdx.x;
+    const int64_t gb = blockIdx.x;
     const int h = blockIdx.y;
-    const int2 bi = blk_info[blk];
-    const int64_t row0 = (int64_t)bi.x * PANEL + h * 128;
-    const int64_t col0 = (int64_t)bi.y * KB;
+    const BlkInfo bi = bt.blk[gb];
+    const TestDesc d = bt.desc[bi.t];
+    const int64_t n = d.n, p = d.p;
+    const int64_t row0 = (int64_t)bi.I * PANEL + h * 128;
+    const int64_t col0 = (int64_t)bi.kb * KB;
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
     float acc[8][4];
 #pragma unroll
@@ -302,7 +256,7 @@ __global__ void __launch_bounds__(256) k_build_simt(const float *__restrict__ X,
             const int idx = e * 256 + t, r = idx >> 4, k = idx & 15;
             const int64_t i = row0 + r;
             float v = 0.f;
-            if (i < n && k0 + k < p) v = pooled_row(X, Y, nx, i, p)[k0 + k];
+            if (i < n && k0 + k < p) v = __ldg(pooled_row(d, i) + k0 + k);
             As[k][r] = v;
         }
 #pragma unroll
@@ -310,7 +264,7 @@ __global__ void __launch_bounds__(256) k_build_simt(const float *__restrict__ X,
             const int idx = e * 256 + t, cc = idx >> 4, k = idx & 15;
             const int64_t j = col0 + cc;
             float v = 0.f;
-            if (j < n && k0 + k < p) v = pooled_row(X, Y, nx, j, p)[k0 + k];
+            if (j < n && k0 + k < p) v = __ldg(pooled_row(d, j) + k0 + k);
             Bs[k][cc] = v;
         }
         __syncthreads();
@@ -328,6 +282,8 @@ __global__ void __launch_bounds__(256) k_build_simt(const float *__restrict__ X,
         }
         __syncthreads();
     }
+    const float neg = d.neg_inv_2s2, tau = d.tau;
+    const int stat = d.stat;
     unsigned fixups = 0;
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
@@ -341,37 +297,33 @@ __global__ void __launch_bounds__(256) k_build_simt(const float *__restrict__ X,
                 if (i == j) {
                     v = (stat == 0) ? 0.f : 1.f;
                 } else {
-                    const float ni = norms[i], nj = norms[j];
-                    float d2 = fmaxf(0.f, ni + nj - 2.f * acc[a][c]);
+                    const float ni = __ldg(bt.norms + d.row0 + i), nj = __ldg(bt.norms + d.row0 + j);
+                    const float d2 = fmaxf(0.f, ni + nj - 2.f * acc[a][c]);
                     if (d2 < tau * (ni + nj)) {
-                        const float *zi = pooled_row(X, Y, nx, i, p), *zj = pooled_row(X, Y, nx, j, p);
+                        const float *zi = pooled_row(d, i), *zj = pooled_row(d, j);
                         double s = 0.0;
                         for (int64_t k = 0; k < p; ++k) {
-                            const double d = (double)zi[k] - (double)zj[k];
-                            s = fma(d, d, s);
+                            const double df = (double)zi[k] - (double)zj[k];
+                            s = fma(df, df, s);
                         }
                         ++fixups;
-                        v = (stat == 0) ? (float)sqrt(s) : (float)exp(s * (double)neg_inv_2s2);
+                        v = (stat == 0) ? (float)sqrt(s) : (float)exp(s * (double)neg);
                     } else {
-                        v = finish_entry(d2, stat, neg_inv_2s2);
+                        v = (stat == 0) ? sqrtf(d2) : expf(d2 * neg);
                     }
                 }
             }
             out[c] = v;
         }
-        const int64_t off = (blk * PANEL + h * 128 + ty * 8 + a) * KB + tx * 4;
-        *reinterpret_cast<float4 *>(D + off) = make_float4(out[0], out[1], out[2], out[3]);
+        const int64_t off = (gb * PANEL + h * 128 + ty * 8 + a) * KB + tx * 4;
+        *reinterpret_cast<float4 *>(bt.D + off) = make_float4(out[0], out[1], out[2], out[3]);
     }
-    if (fixups) atomicAdd(&ctr->n_fixup, (unsigned long long)fixups);
+    if (fixups) atomicAdd(&bt.ctr[bi.t].n_fixup, (unsigned long long)fixups);
 }
 
-void launch_build_simt(const float *X, const float *Y, const float *norms, const Geom &g, int stat,
-                       double sigma, double tau, const int2 *blk_info, float *D, Counters *ctr,
-                       cudaStream_t s) {
-    const float neg = (stat == 0) ? 0.f : (float)(-1.0 / (2.0 * sigma * sigma));
-    dim3 grid((unsigned)g.nblk, 2);
-    k_build_simt<<<grid, 256, 0, s>>>(X, Y, norms, g.nx, g.n, g.p, g.NKB, stat, neg, (float)tau, blk_info, D,
-                                     ctr);
+void launch_build_simt(const Batch &b, cudaStream_t s) {
+    if (b.nblk_total <= 0) return;
+    k_build_simt<<<dim3((unsigned)b.nblk_total, 2), 256, 0, s>>>(b);
 }
 
 // ---------------------------------------------------------------------------
@@ -380,20 +332,18 @@ void launch_build_simt(const float *X, const float *Y, const float *norms, const
 // their column sums supply it).  Sums are accumulated as unevaluated FP32 pairs
 // (hi, lo) with Knuth's TwoSum, an error-free transformation (the rounding error of
 // every addition is carried in lo), then widened to FP64: about twice the FP32
-// precision at FP32 cost.  One CTA (8 warps) per block, one row per warp step,
-// lane l owns columns 2l and 2l+1.
+// precision at FP32 cost.  One CTA per stored block of the batch.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     s = a + b;
     const float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
 }
 
-__global__ void __launch_bounds__(256) k_blocksums(const float *__restrict__ D, double *__restrict__ rowpart,
-                                                   double *__restrict__ colpart) {
+__global__ void __launch_bounds__(256) k_blocksums(const Batch bt) {
     __shared__ double cs[8][64];
-    const int64_t blk = blockIdx.x;
+    const int64_t gb = blockIdx.x;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const float *base = D + blk * (int64_t)(PANEL * KB);
+    const float *base = bt.D + gb * (int64_t)(PANEL * KB);
     // row sums: thread t owns row t (64 contiguous values, no cross-thread traffic)
     {
         const float4 *row = reinterpret_cast<const float4 *>(base + (int64_t)t * KB);
@@ -412,7 +362,12 @@ __global__ void __launch_bounds__(256) k_blocksums(const float *__restrict__ D, 
                 l += f;
             }
         }
-        rowpart[blk * PANEL + t] = (double)h + (double)l;
+        bt.rowpart[gb * PANEL + t] = (double)h + (double)l;
+        float mx = 0.f;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[q].x), fabsf(v[q].y)), fmaxf(fabsf(v[q].z), fabsf(v[q].w))));
+        for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
+        if (lane == 0) atomicMax(&bt.ctr[bt.blk[gb].t].max_d_bits, __float_as_uint(mx));
     }
     // column sums: warp w covers rows 32w..32w+31, lane l columns 2l and 2l+1
     {
@@ -442,57 +397,62 @@ __global__ void __launch_bounds__(256) k_blocksums(const float *__restrict__ D, 
         double acc = 0.0;
 #pragma unroll
         for (int w = 0; w < 8; ++w) acc += cs[w][t];
-        colpart[blk * KB + t] = acc;
+        bt.colpart[gb * KB + t] = acc;
     }
 }
 
-void launch_blocksums(const float *D, const Geom &g, double *rowpart, double *colpart, cudaStream_t s) {
-    k_blocksums<<<(unsigned)g.nblk, 256, 0, s>>>(D, rowpart, colpart);
+void launch_blocksums(const Batch &b, cudaStream_t s) {
+    if (b.nblk_total <= 0) return;
+    k_blocksums<<<(unsigned)b.nblk_total, 256, 0, s>>>(b);
 }
 
 // r_i = sum over the stored blocks of row i's panel (its own row segments) + sum
 // over the earlier panels J < panel(i) of column i's segments.  Eight threads per
 // row take every eighth term and combine by a fixed shuffle tree (deterministic).
-// CTA = 32 rows (256 threads); Spart[CTA] = sum of its rows' r_i.
-__global__ void __launch_bounds__(256) k_rowsum_reduce(const double *__restrict__ rowpart,
-                                                       const double *__restrict__ colpart, int64_t n, int64_t NKB,
-                                                       double *__restrict__ r, double *__restrict__ Spart) {
+// CTA = 32 rows of one test (256 threads); Spart[CTA] = sum of its rows' r_i.
+__global__ void __launch_bounds__(256) k_rowsum_reduce(const Batch bt) {
     __shared__ double sh[32];
     const int sub = threadIdx.x & 7, rl = threadIdx.x >> 3;
-    const int64_t i = (int64_t)blockIdx.x * 32 + rl;
-    const int64_t I = i / PANEL, rr = i % PANEL;
+    const int64_t gr = (int64_t)blockIdx.x * 32 + rl;
+    const int t = find_test(bt.pre.rows, bt.n_tests, (int64_t)blockIdx.x * 32);
+    const TestDesc d = bt.desc[t];
+    const int64_t i = gr - d.row0;
+    const int64_t I = i / PANEL, rr = i % PANEL, NKB = d.NKB;
     double acc = 0.0;
-    if (i < n) {
-        const int64_t nkb = NKB - KB_PER_PANEL * I;          // stored K-blocks of panel I
-        const int64_t base = blk_off(I, NKB);
-        for (int64_t k = sub; k < nkb; k += 8) acc += rowpart[(base + k) * PANEL + rr];
+    if (i < d.n) {
+        const int64_t nkb = NKB - KB_PER_PANEL * I;
+        const int64_t base = d.blk0 + blk_off(I, NKB);
+        for (int64_t k = sub; k < nkb; k += 8) acc += bt.rowpart[(base + k) * PANEL + rr];
         const int64_t kbi = i / KB, ci = i % KB;
-        for (int64_t J = sub; J < I; J += 8) acc += colpart[blk_index(J, kbi, NKB) * KB + ci];
+        for (int64_t J = sub; J < I; J += 8) acc += bt.colpart[(d.blk0 + blk_index(J, kbi, NKB)) * KB + ci];
     }
     acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 4);
     acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
     acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
     if (sub == 0) {
-        r[i] = acc;
+        bt.r[gr] = acc;
         sh[rl] = acc;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
         for (int k = 0; k < 32; ++k) s += sh[k];
-        Spart[blockIdx.x] = s;
+        bt.Spart[blockIdx.x] = s;
     }
 }
 
-void launch_rowsum_reduce(const double *rowpart, const double *colpart, const Geom &g, double *r, double *Spart,
-                          cudaStream_t s) {
-    k_rowsum_reduce<<<(unsigned)(g.n_pad / 32), 256, 0, s>>>(rowpart, colpart, g.n, g.NKB, r, Spart);
+void launch_rowsum_reduce(const Batch &b, cudaStream_t s) {
+    if (b.nrows_total <= 0) return;
+    k_rowsum_reduce<<<(unsigned)(b.nrows_total / 32), 256, 0, s>>>(b);
 }
 
-// Deterministic sum of a short array in fixed order.
-__device__ __forceinline__ double ordered_sum(const double *a, int64_t m) {
+// Deterministic sum of a short array in fixed order (one warp: strided lane sums,
+// then a fixed shuffle tree).
+__device__ __forceinline__ double warp_ordered_sum(const double *a, int64_t m) {
+    const int lane = threadIdx.x & 31;
     double s = 0.0;
-    for (int64_t k = 0; k < m; ++k) s += a[k];
+    for (int64_t k = lane; k < m; k += 32) s += a[k];
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, off);
     return s;
 }
 
@@ -519,60 +479,56 @@ __device__ __forceinline__ double block_sum_256(double v, double *sh) {
 // sign = -1 (ED) or +1 (MMD).  dcorr_i = kappa r~_i.
 // Only r~ must be exact (it is, in FP64, for the FP32 u actually stored); u itself
 // may be any value, so it is formed with multiplications by precomputed reciprocals.
-// Step 1 (one CTA per panel): u_i, Upart[panel] = sum of the u_i as doubles.
-__global__ void __launch_bounds__(256) k_center_u(const double *__restrict__ r, const double *__restrict__ Spart,
-                                                  int64_t nS, int64_t n, double inv_n, double inv_2n2,
-                                                  float *__restrict__ u, double *__restrict__ Upart) {
+// Step 1 (one CTA per panel of the batch): u_i, Upart[panel] = sum of the u_i.
+__global__ void __launch_bounds__(256) k_center_u(const Batch bt) {
     __shared__ double sh[256];
     __shared__ double bS;
-    if (threadIdx.x == 0) bS = ordered_sum(Spart, nS);
+    const int64_t gp = blockIdx.x;
+    const int t = find_test(bt.pre.panels, bt.n_tests, gp);
+    const TestDesc d = bt.desc[t];
+    if (threadIdx.x < 32) {
+        const double S = warp_ordered_sum(bt.Spart + d.sp0, d.n_pad / 32);
+        if (threadIdx.x == 0) bS = S;
+    }
     __syncthreads();
-    const double S = bS;
-    const int64_t i = (int64_t)blockIdx.x * PANEL + threadIdx.x;
+    const int64_t i = (gp - d.pan0) * PANEL + threadIdx.x;
     float ui = 0.f;
-    if (i < n) ui = (float)(r[i] * inv_n - S * inv_2n2);
-    u[i] = ui;
+    if (i < d.n) ui = (float)(bt.r[d.row0 + i] * d.inv_n - bS * d.inv_2n2);
+    bt.u[d.row0 + i] = ui;
+    float mx = fabsf(ui);
+    for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(&bt.ctr[t].max_u_bits, __float_as_uint(mx));
     const double tot = block_sum_256((double)ui, sh);
-    if (threadIdx.x == 0) Upart[blockIdx.x] = tot;
+    if (threadIdx.x == 0) bt.Upart[gp] = tot;
 }
 
-// Step 2 (one CTA per panel): r~_i, dcorr_i = kappa r~_i, Stpart[panel] = sum of r~_i;
-// block 0 also writes the constants of the final combination.
-__global__ void __launch_bounds__(256) k_center_r(const double *__restrict__ r, const float *__restrict__ u,
-                                                  const double *__restrict__ Upart, int64_t NP, int64_t n,
-                                                  double kappa, double cT, double inv_o2, double sign,
-                                                  double *__restrict__ dcorr, double *__restrict__ Stpart,
-                                                  StatConst *sc) {
+// Step 2 (one CTA per panel): r~_i, dcorr_i = kappa r~_i, Stpart[panel] = sum of r~_i.
+__global__ void __launch_bounds__(256) k_center_r(const Batch bt) {
     __shared__ double sh[256];
     __shared__ double bU;
-    if (threadIdx.x == 0) bU = ordered_sum(Upart, NP);
-    __syncthreads();
-    const double U = bU;
-    const int64_t i = (int64_t)blockIdx.x * PANEL + threadIdx.x;
-    double rt = 0.0;
-    if (i < n) rt = r[i] - (double)n * (double)u[i] - U;
-    dcorr[i] = kappa * rt;
-    const double tot = block_sum_256(rt, sh);
-    if (threadIdx.x == 0) {
-        Stpart[blockIdx.x] = tot;
-        if (blockIdx.x == 0) {
-            sc->cT = cT;
-            sc->inv_o2 = inv_o2;
-            sc->sign = sign;
-            sc->S_tilde = 0.0;
-        }
+    const int64_t gp = blockIdx.x;
+    const int t = find_test(bt.pre.panels, bt.n_tests, gp);
+    const TestDesc d = bt.desc[t];
+    if (threadIdx.x < 32) {
+        const double U = warp_ordered_sum(bt.Upart + d.pan0, d.NP);
+        if (threadIdx.x == 0) bU = U;
     }
+    __syncthreads();
+    const int64_t i = (gp - d.pan0) * PANEL + threadIdx.x;
+    double rt = 0.0;
+    if (i < d.n) rt = bt.r[d.row0 + i] - (double)d.n * (double)bt.u[d.row0 + i] - bU;
+    bt.dcorr[d.row0 + i] = d.kappa * rt;
+    float mx = (float)fabs(d.kappa * rt);
+    for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(&bt.ctr[t].max_dc_bits, __float_as_uint(mx));
+    const double tot = block_sum_256(rt, sh);
+    if (threadIdx.x == 0) bt.Stpart[gp] = tot;
 }
 
-void launch_center(const double *r, const double *Spart, const Geom &g, float *u, double *dcorr, double *Upart,
-                   double *Stpart, StatConst *sc, int stat, cudaStream_t s) {
-    const double fn = (double)g.n;
-    const double q = fn / ((double)g.nx * (double)g.ny);
-    k_center_u<<<(unsigned)g.NP, 256, 0, s>>>(r, Spart, g.n_pad / 32, g.n, 1.0 / fn, 1.0 / (2.0 * fn * fn), u,
-                                             Upart);
-    k_center_r<<<(unsigned)g.NP, 256, 0, s>>>(r, u, Upart, g.NP, g.n, 2.0 * (double)g.m / fn, q * q,
-                                             1.0 / ((double)g.other * (double)g.other), stat == 0 ? -1.0 : 1.0, dcorr,
-                                             Stpart, sc);
+void launch_center(const Batch &b, cudaStream_t s) {
+    if (b.npan_total <= 0) return;
+    k_center_u<<<(unsigned)b.npan_total, 256, 0, s>>>(b);
+    k_center_r<<<(unsigned)b.npan_total, 256, 0, s>>>(b);
 }
 
 // Packing.  Stored entry (i, j), j >= 256*panel(i):
@@ -580,32 +536,37 @@ void launch_center(const double *r, const double *Spart, const Geom &g, float *u
 //                                           the upper triangle = the full form)
 //   j = i:  D_ii - 2 u_i - dcorr_i
 //   j < i or padding: 0
-template <bool BF16>
-__global__ void __launch_bounds__(256) k_pack(const float *__restrict__ D, const float *__restrict__ u,
-                                              const double *__restrict__ dcorr, int64_t n,
-                                              const int2 *__restrict__ blk_info, float *__restrict__ C32,
-                                              uint16_t *__restrict__ Chi, uint16_t *__restrict__ Clo) {
-    const int64_t blk = blockIdx.x;
-    const int2 bi = blk_info[blk];
+// FP32 in place (plain path), or (tuned path) c C split into FP16 hi + lo parts,
+// hi = fp16(c C), lo = fp16(c C - hi), with the test's power-of-two scale c
+// (packed_scale): |c C - hi - lo| <= 2^-22 |c C|.  One CTA per block.
+template <bool SPLIT>
+__global__ void __launch_bounds__(256) k_pack(const Batch bt) {
+    const int64_t gb = blockIdx.x;
+    const BlkInfo bi = bt.blk[gb];
+    const TestDesc d = bt.desc[bi.t];
+    const int64_t n = d.n;
+    const float *u = bt.u + d.row0;
+    const double *dcorr = bt.dcorr + d.row0;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t j0 = (int64_t)bi.y * KB + 2 * lane;
+    const int64_t j0 = (int64_t)bi.kb * KB + 2 * lane;
     const float uj[2] = {(j0 < n) ? u[j0] : 0.f, (j0 + 1 < n) ? u[j0 + 1] : 0.f};
-    const int64_t row0 = (int64_t)bi.x * PANEL + warp * 32;
+    const int64_t row0 = (int64_t)bi.I * PANEL + warp * 32;
+    const float cs = SPLIT ? packed_scale(bt.ctr[bi.t]) : 1.f;
 #pragma unroll 1
     for (int r0 = 0; r0 < 32; r0 += 8) {
-        float2 d[8];
+        float2 dv8[8];
         float ui[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            d[q] = *reinterpret_cast<const float2 *>(D + (blk * PANEL + warp * 32 + r0 + q) * KB + 2 * lane);
+            dv8[q] = *reinterpret_cast<const float2 *>(bt.D + (gb * PANEL + warp * 32 + r0 + q) * KB + 2 * lane);
             const int64_t i = row0 + r0 + q;
             ui[q] = (i < n) ? u[i] : 0.f;
         }
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int64_t i = row0 + r0 + q;
-            const int64_t off = (blk * PANEL + warp * 32 + r0 + q) * KB + 2 * lane;
-            const float dv[2] = {d[q].x, d[q].y};
+            const int64_t off = (gb * PANEL + warp * 32 + r0 + q) * KB + 2 * lane;
+            const float dv[2] = {dv8[q].x, dv8[q].y};
             float w[2];
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
@@ -617,45 +578,48 @@ __global__ void __launch_bounds__(256) k_pack(const float *__restrict__ D, const
                 }
                 w[e] = v;
             }
-            if (BF16) {
-                const __nv_bfloat16 h0 = __float2bfloat16_rn(w[0]), h1 = __float2bfloat16_rn(w[1]);
-                const __nv_bfloat16 l0 = __float2bfloat16_rn(w[0] - __bfloat162float(h0));
-                const __nv_bfloat16 l1 = __float2bfloat16_rn(w[1] - __bfloat162float(h1));
-                const uint32_t hv = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-                const uint32_t lv = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-                *reinterpret_cast<uint32_t *>(Chi + off) = hv;
-                *reinterpret_cast<uint32_t *>(Clo + off) = lv;
+            if (SPLIT) {
+                const float a0 = w[0] * cs, a1 = w[1] * cs;   // exact: cs is a power of two
+                const __half h0 = __float2half_rn(a0), h1 = __float2half_rn(a1);
+                const __half l0 = __float2half_rn(a0 - __half2float(h0));
+                const __half l1 = __float2half_rn(a1 - __half2float(h1));
+                const uint32_t hv = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+                const uint32_t lv = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+                *reinterpret_cast<uint32_t *>(bt.Chi + off) = hv;
+                *reinterpret_cast<uint32_t *>(bt.Clo + off) = lv;
             } else {
-                *reinterpret_cast<float2 *>(C32 + off) = make_float2(w[0], w[1]);
+                *reinterpret_cast<float2 *>(bt.D + off) = make_float2(w[0], w[1]);
             }
         }
     }
 }
 
-void launch_pack_fp32(const float *D, const float *u, const double *dcorr, const Geom &g,
-                      const int2 *blk_info, float *C, cudaStream_t s) {
-    k_pack<false><<<(unsigned)g.nblk, 256, 0, s>>>(D, u, dcorr, g.n, blk_info, C, nullptr, nullptr);
-}
-
-void launch_pack_bf16(const float *D, const float *u, const double *dcorr, const Geom &g,
-                      const int2 *blk_info, uint16_t *Chi, uint16_t *Clo, cudaStream_t s) {
-    k_pack<true><<<(unsigned)g.nblk, 256, 0, s>>>(D, u, dcorr, g.n, blk_info, nullptr, Chi, Clo);
+void launch_pack(const Batch &b, bool split, cudaStream_t s) {
+    if (b.nblk_total <= 0) return;
+    if (split) k_pack<true><<<(unsigned)b.nblk_total, 256, 0, s>>>(b);
+    else k_pack<false><<<(unsigned)b.nblk_total, 256, 0, s>>>(b);
 }
 
 // ---------------------------------------------------------------------------
-// Plain FP32 contraction (the comparison path).  For work chunk q (panel I,
-// K-blocks [kb0, kb1)), half h of the panel's rows and 64 relabeling columns:
+// Plain FP32 contraction (the comparison path).  Work item = (test, chunk q =
+// (panel I, K-blocks [kb0, kb1)), half h of the panel's rows, 64 relabeling columns):
 //   U[b, i] = sum_{j in chunk} s_b[j] C[i, j]     (FP32 FMA, masks as 0/1 floats)
 //   partial[(2q + h)][b] = sum_{i in half} s_b[i] U[b, i]
 // 256 threads, each 4 relabelings x 8 rows; columns staged 32 at a time.
-__global__ void __launch_bounds__(256) k_contract_simt(const float *__restrict__ C, const uint32_t *__restrict__ maskT,
-                                                       const Chunk *__restrict__ chunks, int64_t NKB, int64_t Bp,
-                                                       float *__restrict__ partial) {
+__global__ void __launch_bounds__(256) k_contract_simt(const Batch bt) {
     __shared__ float Cs[32][128 + 4];
     __shared__ uint32_t Ms[64];
-    const int q = blockIdx.x >> 1, h = blockIdx.x & 1;
-    const Chunk ch = chunks[q];
-    const int64_t b0 = (int64_t)blockIdx.y * 64;
+    const int64_t w = blockIdx.x;
+    const int tt = find_test(bt.pre.simt, bt.n_tests, w);
+    const TestDesc d = bt.desc[tt];
+    const int64_t lw = w - bt.pre.simt[tt];
+    const int64_t tiles = d.Bp / 64;
+    const int64_t q = lw / (2 * tiles), rem = lw % (2 * tiles);
+    const int h = (int)(rem / tiles);
+    const int64_t b0 = (rem % tiles) * 64;
+    const Chunk ch = bt.chunks[d.chunk0 + q];
+    const uint32_t *maskT = bt.maskT + d.mask0;
+    const int64_t Bp = d.Bp;
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
     float acc[4][8];
 #pragma unroll
@@ -664,7 +628,7 @@ __global__ void __launch_bounds__(256) k_contract_simt(const float *__restrict__
         for (int r = 0; r < 8; ++r) acc[a][r] = 0.f;
 
     for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
-        const float *blkp = C + blk_index(ch.I, kb, NKB) * (int64_t)(PANEL * KB) + (int64_t)h * 128 * KB;
+        const float *blkp = bt.D + (d.blk0 + blk_index(ch.I, kb, d.NKB)) * (int64_t)(PANEL * KB) + (int64_t)h * 128 * KB;
         for (int sub = 0; sub < 2; ++sub) {
 #pragma unroll
             for (int e = 0; e < 16; ++e) {
@@ -702,66 +666,77 @@ __global__ void __launch_bounds__(256) k_contract_simt(const float *__restrict__
 #pragma unroll
         for (int r = 0; r < 8; ++r) v += ((bits >> r) & 1u) ? acc[a][r] : 0.f;
         for (int off = 8; off; off >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, off);
-        if (tx == 0) partial[(int64_t)(2 * q + h) * Bp + b] = v;
+        if (tx == 0) bt.partial[d.part0 + (2 * q + h) * Bp + b] = v;
     }
 }
 
-void launch_contract_simt(const float *C, const uint32_t *maskT, const Chunk *chunks, const Geom &g,
-                          float *partial, cudaStream_t s) {
-    dim3 grid((unsigned)(g.nchunks * 2), (unsigned)(g.Bp / 64));
-    k_contract_simt<<<grid, 256, 0, s>>>(C, maskT, chunks, g.NKB, g.Bp, partial);
+void launch_contract_simt(const Batch &b, cudaStream_t s) {
+    if (b.nsimt_total <= 0) return;
+    k_contract_simt<<<(unsigned)b.nsimt_total, 256, 0, s>>>(b);
 }
 
 // ---------------------------------------------------------------------------
 // Final combination (Algorithm 1, statistic and p-value lines): per relabeling
-// column b, Q_b = sum of its partials in fixed order (FP64), stat_b =
+// column b, Q_b = sum of its partials (four threads per column, every fourth
+// partial each, then a fixed shuffle tree: deterministic), stat_b =
 // sign * (cT Q_b + S~/o^2).  Then, against stat_0 (the identity, evaluated by the
 // same kernels), count stat_b >= stat_0 and near-ties |stat_b - stat_0| <= 1e-5 |stat_0|.
-__global__ void __launch_bounds__(256) k_combine_stats(const float *__restrict__ partial, int64_t nparts, int64_t Bp,
-                                                       int64_t ncols, const StatConst *__restrict__ sc,
-                                                       const double *__restrict__ Stpart, int64_t NP,
-                                                       double *__restrict__ stats) {
-    // four threads per column: thread q of a column sums partials q, q+4, ...; the
-    // four sums are combined by a fixed shuffle tree (deterministic)
+// A CTA covers 64 columns of one test (the column padding is a multiple of 256).
+__global__ void __launch_bounds__(256) k_combine_stats(const Batch bt) {
     __shared__ double bSt;
-    if (threadIdx.x == 0) bSt = ordered_sum(Stpart, NP);
+    const int64_t gc0 = (int64_t)blockIdx.x * 64;
+    const int t = find_test(bt.pre.cols, bt.n_tests, gc0);
+    const TestDesc d = bt.desc[t];
+    if (threadIdx.x < 32) {
+        const double St = warp_ordered_sum(bt.Stpart + d.pan0, d.NP);
+        if (threadIdx.x == 0) bSt = St;
+    }
     __syncthreads();
     const int q = threadIdx.x & 3;
-    const int64_t b = (int64_t)blockIdx.x * 64 + (threadIdx.x >> 2);
+    const int64_t c = gc0 + (threadIdx.x >> 2) - bt.pre.cols[t];
+    const float *part = bt.partial + d.part0;
     double acc = 0.0;
-    if (b < ncols)
-        for (int64_t k = q; k < nparts; k += 4) acc += (double)partial[k * Bp + b];
+    if (c < d.ncols)
+        for (int64_t k = q; k < d.nparts; k += 4) acc += (double)part[k * d.Bp + c];
     acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
     acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
-    if (b < ncols && q == 0) stats[b] = sc->sign * (sc->cT * acc + bSt * sc->inv_o2);
+    // the tensor-core path accumulates c Q (packed operand scaled by c); 1/c is exact
+    const double inv_c = (d.nparts == d.nchunks) ? 1.0 / (double)packed_scale(bt.ctr[t]) : 1.0;
+    if (c < d.ncols && q == 0) bt.stats[d.col0 + c] = d.sign * (d.cT * (acc * inv_c) + bSt * d.inv_o2);
 }
 
-__global__ void k_combine_count(const double *__restrict__ stats, int64_t ncols, Counters *ctr) {
-    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const double obs = stats[0];
+// Counting and outputs: a CTA covers 256 columns of one test.
+__global__ void __launch_bounds__(256) k_combine_count(const Batch bt) {
+    const int64_t gc = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int t = find_test(bt.pre.cols, bt.n_tests, (int64_t)blockIdx.x * 256);
+    const TestDesc d = bt.desc[t];
+    const int64_t c = gc - bt.pre.cols[t];
+    const double obs = bt.stats[d.col0];
     int ge = 0, near = 0;
-    if (b >= 1 && b < ncols) {
-        const double v = stats[b];
+    if (c >= 1 && c < d.ncols) {
+        const double v = bt.stats[d.col0 + c];
         ge = v >= obs;
         near = fabs(v - obs) <= 1e-5 * fabs(obs);
+        if (d.out_stats) d.out_stats[c - 1] = v;
     }
+    if (c == 0) bt.observed[t] = obs;
     ge = __syncthreads_count(ge);
     near = __syncthreads_count(near);
     if (threadIdx.x == 0) {
-        if (ge) atomicAdd(&ctr->n_ge, (unsigned long long)ge);
-        if (near) atomicAdd(&ctr->n_near, (unsigned long long)near);
+        if (ge) atomicAdd(&bt.ctr[t].n_ge, (unsigned long long)ge);
+        if (near) atomicAdd(&bt.ctr[t].n_near, (unsigned long long)near);
     }
 }
 
-void launch_combine(const float *partial, int64_t nparts, const Geom &g, const StatConst *sc,
-                    const double *Stpart, double *stats, Counters *ctr, cudaStream_t s) {
-    k_combine_stats<<<(unsigned)((g.ncols + 63) / 64), 256, 0, s>>>(partial, nparts, g.Bp, g.ncols, sc, Stpart, g.NP,
-                                                                   stats);
-    k_combine_count<<<(unsigned)((g.ncols + 255) / 256), 256, 0, s>>>(stats, g.ncols, ctr);
+void launch_combine(const Batch &b, cudaStream_t s) {
+    if (b.ncols_total <= 0) return;
+    k_combine_stats<<<(unsigned)(b.ncols_total / 64), 256, 0, s>>>(b);
+    k_combine_count<<<(unsigned)(b.ncols_total / 256), 256, 0, s>>>(b);
 }
 
 // ---------------------------------------------------------------------------
-// Expand the packed upper storage into a full row-major n x n matrix (checking aid).
+// Expand one test's packed upper storage into a full row-major n x n matrix
+// (checking aid).
 __global__ void k_expand(const float *__restrict__ D, int64_t n, int64_t NKB, float *__restrict__ out) {
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n * n) return;
@@ -775,9 +750,10 @@ __global__ void k_expand(const float *__restrict__ D, int64_t n, int64_t NKB, fl
     out[idx] = D[(blk_index(I, kb, NKB) * PANEL + (i - I * PANEL)) * KB + (j - kb * KB)];
 }
 
-void launch_expand_blocks(const float *D, const Geom &g, float *out, cudaStream_t s) {
-    const int64_t tot = g.n * g.n;
-    k_expand<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(D, g.n, g.NKB, out);
+void launch_expand_blocks(const float *D, int64_t n, int64_t NKB, float *out, cudaStream_t s) {
+    const int64_t tot = n * n;
+    if (tot <= 0) return;
+    k_expand<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(D, n, NKB, out);
 }
 
 }  // namespace ept

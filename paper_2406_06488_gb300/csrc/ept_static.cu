@@ -33,8 +33,6 @@
 
 namespace ept {
 
-void set_last_error(const char *msg);  // ept_api.cu
-
 namespace {
 
 __device__ __align__(256) uint8_t g_static_scratch[EPT_STATIC_SCRATCH_BYTES];
@@ -49,14 +47,15 @@ constexpr int MAX_DEVICES = 64;
 StaticDevice g_static_dev[MAX_DEVICES];
 std::mutex g_static_mu;
 
-inline size_t up(size_t v) { return (v + 1023) / 1024 * 1024; }
+inline size_t up(size_t v) { return (v + 255) / 256 * 256; }
 
+// Layout of one test's scratch inside the static array (byte offsets).
 struct StaticPlan {
-    size_t norms, blkinfo, chunks, D, rowpart, colpart, r, u, dcorr, sc, hi, lo, maskT, partial, stats, ctr, total;
-    size_t Spart, Upart, Stpart;
+    size_t desc, pre, blk, chunks, norms, iscale, u, D, hi, lo, rowpart, colpart, r, Spart, dcorr, Upart, Stpart,
+        maskT, partial, stats, observed, ctr, total;
 };
 
-StaticPlan static_plan(const Geom &g) {
+StaticPlan static_plan(const TestDesc &d) {
     StaticPlan P;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -64,50 +63,53 @@ StaticPlan static_plan(const Geom &g) {
         o = up(o + (bytes ? bytes : 1));
         return at;
     };
-    const size_t elems = (size_t)g.nblk * PANEL * KB;
-    P.norms = take((size_t)g.n_pad * 4);
-    P.blkinfo = take((size_t)g.nblk * sizeof(int2));
-    P.chunks = take((size_t)g.nchunks * sizeof(Chunk));
+    const size_t elems = (size_t)d.nblk * PANEL * KB;
+    P.desc = take(sizeof(TestDesc));
+    P.pre = take(5 * 2 * sizeof(int64_t));
+    P.blk = take((size_t)d.nblk * sizeof(BlkInfo));
+    P.chunks = take((size_t)d.nchunks * sizeof(Chunk));
+    P.norms = take((size_t)d.n_pad * 4);
+    P.iscale = take((size_t)d.n_pad * 4);
+    P.u = take((size_t)d.n_pad * 4);
     P.D = take(elems * 4);
-    P.rowpart = take((size_t)g.nblk * PANEL * 8);
-    P.colpart = take((size_t)g.nblk * KB * 8);
-    P.r = take((size_t)g.n_pad * 8);
-    P.u = take((size_t)g.n_pad * 4);
-    P.dcorr = take((size_t)g.n_pad * 8);
-    P.sc = take(sizeof(StatConst));
-    P.Spart = take((size_t)(g.n_pad / 32) * 8);
-    P.Upart = take((size_t)g.NP * 8);
-    P.Stpart = take((size_t)g.NP * 8);
     P.hi = take(elems * 2);
     P.lo = take(elems * 2);
-    P.maskT = take((size_t)g.nw * g.Bp * 4);
-    P.partial = take((size_t)g.nchunks * g.Bp * 4);
-    P.stats = take((size_t)g.ncols * 8);
+    P.rowpart = take((size_t)d.nblk * PANEL * 8);
+    P.colpart = take((size_t)d.nblk * KB * 8);
+    P.r = take((size_t)d.n_pad * 8);
+    P.Spart = take((size_t)(d.n_pad / 32) * 8);
+    P.dcorr = take((size_t)d.n_pad * 8);
+    P.Upart = take((size_t)d.NP * 8);
+    P.Stpart = take((size_t)d.NP * 8);
+    P.maskT = take((size_t)d.nw * d.Bp * 4);
+    P.partial = take((size_t)d.nchunks * d.Bp * 4);
+    P.stats = take((size_t)d.ncols * 8);
+    P.observed = take(8);
     P.ctr = take(sizeof(Counters));
     P.total = o;
     return P;
 }
 
-// The block table (stored block -> panel, K-block) and the chunk table, written on
-// the device so that no host staging memory is needed.
-__global__ void k_static_tables(int NP, int NKB, int64_t nblk, int2 *blk_info, Chunk *chunks) {
+// Writes the test's descriptor, the prefix sums of a batch of one, the block table
+// and the chunk table into the static array, on the device (no host staging).
+__global__ void k_static_tables(const TestDesc d, TestDesc *desc, int64_t *pre, BlkInfo *blk, Chunk *chunks) {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b < nblk) {
+    if (b < d.nblk) {
         int I = 0;
-        while (I + 1 < NP && blk_off(I + 1, NKB) <= b) ++I;
-        blk_info[b] = make_int2(I, (int)(b - blk_off(I, NKB)) + KB_PER_PANEL * I);
+        while (I + 1 < d.NP && blk_off(I + 1, d.NKB) <= b) ++I;
+        blk[b] = BlkInfo{0, I, (int)(b - blk_off(I, d.NKB)) + KB_PER_PANEL * I, 0};
     }
     if (b == 0) {
+        *desc = d;
+        const int64_t tot[5] = {d.n_pad, d.NP, d.Bp, d.nchunks * d.MT, d.nchunks * 2 * (d.Bp / 64)};
+        for (int k = 0; k < 5; ++k) {
+            pre[2 * k] = 0;
+            pre[2 * k + 1] = tot[k];
+        }
         int q = 0;
-        for (int I = 0; I < NP; ++I)
-            for (int kb = KB_PER_PANEL * I; kb < NKB; kb += CHUNK_KB) {
-                Chunk ch;
-                ch.I = I;
-                ch.kb0 = kb;
-                ch.kb1 = (kb + CHUNK_KB < NKB) ? kb + CHUNK_KB : NKB;
-                ch.pad = 0;
-                chunks[q++] = ch;
-            }
+        for (int I = 0; I < d.NP; ++I)
+            for (int kb = KB_PER_PANEL * I; kb < d.NKB; kb += CHUNK_KB_DEFAULT)
+                chunks[q++] = Chunk{I, kb, (kb + CHUNK_KB_DEFAULT < d.NKB) ? kb + CHUNK_KB_DEFAULT : (int)d.NKB, 0};
     }
 }
 
@@ -166,8 +168,45 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     if (stat != EPT_STAT_ED && stat != EPT_STAT_MMD_GAUSS) return err(EPT_EINVAL, "unknown statistic %d", stat);
     if (stat == EPT_STAT_MMD_GAUSS && !(sigma > 0.0 && sigma < 1e300))
         return err(EPT_EINVAL, "MMD needs a finite bandwidth sigma > 0");
-    const Geom g = make_geom(nx, ny, p, B + 1);
-    const StaticPlan P = static_plan(g);
+    // the test, described as a batch of one (same layout rules as ept_test)
+    TestDesc d;
+    memset(&d, 0, sizeof(d));
+    d.X = X;
+    d.Y = Y;
+    d.out_stats = perm_stats;
+    d.nx = nx;
+    d.ny = ny;
+    d.n = nx + ny;
+    d.p = p;
+    d.B = B;
+    d.n_pad = (d.n + PANEL - 1) / PANEL * PANEL;
+    d.NP = d.n_pad / PANEL;
+    d.NKB = d.n_pad / KB;
+    d.nblk = blk_off(d.NP, d.NKB);
+    d.nw = d.n_pad / 32;
+    d.nwu = (int)((d.n + 31) / 32);
+    d.ncols = B + 1;
+    d.Bp = (d.ncols + COL_PAD - 1) / COL_PAD * COL_PAD;
+    d.MT = d.Bp / TC_TILE_M;
+    for (int64_t I = 0; I < d.NP; ++I) d.nchunks += (d.NKB - KB_PER_PANEL * I + CHUNK_KB_DEFAULT - 1) / CHUNK_KB_DEFAULT;
+    d.nparts = d.nchunks;
+    d.p_pad = (p + BUILD_KB - 1) / BUILD_KB * BUILD_KB;
+    d.kblocks = (int)(d.p_pad / BUILD_KB);
+    d.comp = ny < nx;
+    d.m = d.comp ? ny : nx;
+    d.other = d.comp ? nx : ny;
+    d.stat = stat;
+    d.seed = seed;
+    d.neg_inv_2s2 = (stat == EPT_STAT_ED) ? 0.f : (float)(-1.0 / (2.0 * sigma * sigma));
+    d.tau = 1.f / 4.f;
+    const double fn = (double)d.n, q = fn / ((double)nx * (double)ny);
+    d.cT = q * q;
+    d.inv_o2 = 1.0 / ((double)d.other * (double)d.other);
+    d.sign = (stat == EPT_STAT_ED) ? -1.0 : 1.0;
+    d.kappa = 2.0 * (double)d.m / fn;
+    d.inv_n = 1.0 / fn;
+    d.inv_2n2 = 1.0 / (2.0 * fn * fn);
+    const StaticPlan P = static_plan(d);
     if (P.total > (size_t)EPT_STATIC_SCRATCH_BYTES)
         return err(EPT_EINVAL,
                    "this test needs %zu bytes of scratch; ept_test_static has %zu (EPT_STATIC_SCRATCH_BYTES): "
@@ -183,44 +222,63 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     cudaStream_t s = (cudaStream_t)stream;
     uint8_t *A = sd->scratch;
 
-    Counters *ctr = (Counters *)(A + P.ctr);
-    SCK(cudaMemsetAsync(ctr, 0, sizeof(Counters), s));
-    int2 *blkinfo = (int2 *)(A + P.blkinfo);
-    Chunk *chunks = (Chunk *)(A + P.chunks);
-    k_static_tables<<<(unsigned)((g.nblk + 255) / 256), 256, 0, s>>>((int)g.NP, (int)g.NKB, g.nblk, blkinfo, chunks);
-    float *norms = (float *)(A + P.norms);
-    float *D = (float *)(A + P.D);
-    launch_check_finite(X, nx * p, ctr, s);
-    launch_check_finite(Y, ny * p, ctr, s);
-    launch_norms(X, Y, g, norms, s);
-    launch_build_simt(X, Y, norms, g, stat, sigma, 1.0 / 16.0, blkinfo, D, ctr, s);
-    double *rowpart = (double *)(A + P.rowpart), *colpart = (double *)(A + P.colpart);
-    double *r = (double *)(A + P.r), *dcorr = (double *)(A + P.dcorr);
-    float *u = (float *)(A + P.u);
-    StatConst *sc = (StatConst *)(A + P.sc);
-    uint16_t *hi = (uint16_t *)(A + P.hi), *lo = (uint16_t *)(A + P.lo);
-    double *Spart = (double *)(A + P.Spart), *Upart = (double *)(A + P.Upart), *Stpart = (double *)(A + P.Stpart);
-    launch_blocksums(D, g, rowpart, colpart, s);
-    launch_rowsum_reduce(rowpart, colpart, g, r, Spart, s);
-    launch_center(r, Spart, g, u, dcorr, Upart, Stpart, sc, stat, s);
-    launch_pack_bf16(D, u, dcorr, g, blkinfo, hi, lo, s);
-    uint32_t *maskT = (uint32_t *)(A + P.maskT);
-    launch_perm_masks(seed, (int)nx, (int)ny, 0, g.ncols, g.Bp, (int)g.nw, g.comp, maskT, s);
+    Batch b;
+    memset(&b, 0, sizeof(b));
+    b.n_tests = 1;
+    b.desc = (const TestDesc *)(A + P.desc);
+    int64_t *pre = (int64_t *)(A + P.pre);
+    b.pre.rows = pre;
+    b.pre.panels = pre + 2;
+    b.pre.cols = pre + 4;
+    b.pre.units = pre + 6;
+    b.pre.simt = pre + 8;
+    b.blk = (const BlkInfo *)(A + P.blk);
+    b.chunks = (const Chunk *)(A + P.chunks);
+    b.nblk_total = d.nblk;
+    b.nrows_total = d.n_pad;
+    b.npan_total = d.NP;
+    b.ncols_total = d.Bp;
+    b.nunits_total = d.nchunks * d.MT;
+    b.norms = (float *)(A + P.norms);
+    b.iscale = (float *)(A + P.iscale);
+    b.u = (float *)(A + P.u);
+    b.D = (float *)(A + P.D);
+    b.Chi = (uint16_t *)(A + P.hi);
+    b.Clo = (uint16_t *)(A + P.lo);
+    b.rowpart = (double *)(A + P.rowpart);
+    b.colpart = (double *)(A + P.colpart);
+    b.r = (double *)(A + P.r);
+    b.Spart = (double *)(A + P.Spart);
+    b.dcorr = (double *)(A + P.dcorr);
+    b.Upart = (double *)(A + P.Upart);
+    b.Stpart = (double *)(A + P.Stpart);
+    b.maskT = (uint32_t *)(A + P.maskT);
+    b.partial = (float *)(A + P.partial);
+    b.stats = (double *)(A + P.stats);
+    b.observed = (double *)(A + P.observed);
+    b.ctr = (Counters *)(A + P.ctr);
+
+    SCK(cudaMemsetAsync(b.ctr, 0, sizeof(Counters), s));
+    k_static_tables<<<(unsigned)((d.nblk + 255) / 256), 256, 0, s>>>(d, (TestDesc *)(A + P.desc), pre,
+                                                                      (BlkInfo *)(A + P.blk), (Chunk *)(A + P.chunks));
+    launch_norms(b, s);
+    launch_build_simt(b, s);
+    launch_blocksums(b, s);
+    launch_rowsum_reduce(b, s);
+    launch_center(b, s);
+    launch_pack(b, true, s);
+    launch_masks(b, s);
     SCK(cudaGetLastError());
     alignas(64) CUtensorMap th, tl;
     char emsg[160];
-    if (!encode_block_tmaps(&th, &tl, hi, lo, g.nblk, emsg, sizeof(emsg))) return err(EPT_ECUDA, "%s", emsg);
-    float *partial = (float *)(A + P.partial);
-    SCK(launch_contract_tc(&th, &tl, maskT, chunks, g, partial, ctr, sd->num_sms, s));
-    double *stats = (double *)(A + P.stats);
-    launch_combine(partial, g.nchunks, g, sc, Stpart, stats, ctr, s);
+    if (!encode_block_tmaps(&th, &tl, b.Chi, b.Clo, d.nblk, emsg, sizeof(emsg))) return err(EPT_ECUDA, "%s", emsg);
+    SCK(launch_contract_tc(b, &th, &tl, sd->num_sms, s));
+    launch_combine(b, s);
     SCK(cudaGetLastError());
-    if (perm_stats && B > 0)
-        SCK(cudaMemcpyAsync(perm_stats, stats + 1, (size_t)B * 8, cudaMemcpyDeviceToDevice, s));
     Counters h;
     double observed = 0.0;
-    SCK(cudaMemcpyAsync(&h, ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
-    SCK(cudaMemcpyAsync(&observed, stats, 8, cudaMemcpyDeviceToHost, s));
+    SCK(cudaMemcpyAsync(&h, b.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    SCK(cudaMemcpyAsync(&observed, b.observed, 8, cudaMemcpyDeviceToHost, s));
     SCK(cudaStreamSynchronize(s));
     if (h.nonfinite) return err(EPT_EINVAL, "X or Y holds NaN or Inf");
     if (h.err_code)

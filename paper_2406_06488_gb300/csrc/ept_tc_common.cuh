@@ -121,13 +121,13 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                  : "memory");
 }
 
-// 0/1 bits of `byte` -> eight BF16 values (1.0 = 0x3F80), element e = bit e.
+// 0/1 bits of `byte` -> eight FP16 values (1.0 = 0x3C00), element e = bit e.
 __device__ __forceinline__ uint4 expand8(uint32_t byte) {
     uint4 v;
-    v.x = (byte & 1u) * 0x3F80u + (byte & 2u) * 0x1FC00000u;
-    v.y = ((byte >> 2) & 1u) * 0x3F80u + ((byte >> 2) & 2u) * 0x1FC00000u;
-    v.z = ((byte >> 4) & 1u) * 0x3F80u + ((byte >> 4) & 2u) * 0x1FC00000u;
-    v.w = ((byte >> 6) & 1u) * 0x3F80u + ((byte >> 6) & 2u) * 0x1FC00000u;
+    v.x = (byte & 1u) * 0x3C00u + (byte & 2u) * 0x1E000000u;
+    v.y = ((byte >> 2) & 1u) * 0x3C00u + ((byte >> 2) & 2u) * 0x1E000000u;
+    v.z = ((byte >> 4) & 1u) * 0x3C00u + ((byte >> 4) & 2u) * 0x1E000000u;
+    v.w = ((byte >> 6) & 1u) * 0x3C00u + ((byte >> 6) & 2u) * 0x1E000000u;
     return v;
 }
 

@@ -27,13 +27,19 @@ STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT
 
 # every entry point declared in include/ept.h
 EXPORTS = ["ept_abi_version", "ept_last_error", "ept_create", "ept_destroy", "ept_estimate_bytes", "ept_test",
-           "ept_test_masks", "ept_perm_masks", "ept_build_blocks", "ept_test_static"]
+           "ept_test_masks", "ept_perm_masks", "ept_build_blocks", "ept_test_static", "ept_test_batch"]
 
 
 class EptError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__("%s: %s" % (STATUS.get(status, str(status)), message))
         self.status = status
+
+
+class _TestDesc(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("Y", ctypes.c_void_p), ("nx", ctypes.c_int64), ("ny", ctypes.c_int64),
+                ("p", ctypes.c_int64), ("stat", ctypes.c_int), ("sigma", ctypes.c_double), ("B", ctypes.c_int64),
+                ("seed", ctypes.c_uint64), ("perm_stats", ctypes.c_void_p)]
 
 
 class _Result(ctypes.Structure):
@@ -97,6 +103,8 @@ def load():
     lib.ept_build_blocks.restype = i32
     lib.ept_test_static.argtypes = [vp, i64, vp, i64, i64, i32, f64, i64, u64, vp, ctypes.POINTER(_Result), vp]
     lib.ept_test_static.restype = i32
+    lib.ept_test_batch.argtypes = [vp, ctypes.POINTER(_TestDesc), i64, i32, i32, ctypes.POINTER(_Result), vp]
+    lib.ept_test_batch.restype = i32
     _lib = lib
     return lib
 
@@ -222,6 +230,33 @@ class Context:
         _check(load().ept_test_masks(self._h, px, X.shape[0], py, Y.shape[0], X.shape[1], on_dev, _stat(stat),
                                      float(sigma), pm, int(count), _prec(prec), pbuf, ctypes.byref(r), stream))
         return _result(r, buf)
+
+    def test_batch(self, tests, prec="split_bf16", want_stats: bool = True):
+        """Many tests in one batched run.  tests: sequence of dicts with keys X, Y, B and
+        optionally seed, stat, sigma (all X/Y numpy, or all CUDA tensors).  Returns a
+        list of Result (stats: B permuted statistics each when want_stats)."""
+        n = len(tests)
+        if n == 0:
+            return []
+        descs = (_TestDesc * n)()
+        keep, bufs = [], []
+        on_dev = None
+        stream = None
+        for k, t in enumerate(tests):
+            X, Y, px, py, dev, st = self._arrays(t["X"], t["Y"])
+            if on_dev is None:
+                on_dev, stream = dev, st
+            elif on_dev != dev:
+                raise TypeError("all tests of a batch must use the same memory space")
+            B = int(t["B"])
+            buf, pbuf = self._stats_buffer(X, B if want_stats else 0, dev)
+            keep.append((X, Y))
+            bufs.append(buf)
+            descs[k] = _TestDesc(px, py, X.shape[0], Y.shape[0], X.shape[1], _stat(t.get("stat", "ed")),
+                                 float(t.get("sigma", 1.0)), B, int(t.get("seed", 0)), pbuf)
+        res = (_Result * n)()
+        _check(load().ept_test_batch(self._h, descs, n, on_dev, _prec(prec), res, None))
+        return [_result(res[k], bufs[k]) for k in range(n)]
 
     def perm_masks(self, seed: int, nx: int, ny: int, b0: int, count: int) -> np.ndarray:
         """Draws b0 .. b0+count-1 of the permutation stream, generated on the GPU:

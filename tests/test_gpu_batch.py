@@ -1,0 +1,99 @@
+"""Batched runs (many uneven tests in one run, CUDA-graph replay) against single-test
+runs and the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_06488_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_06488_gb300 import ept
+    c = ept.Context(0)
+    yield c
+    c.close()
+
+
+def _uneven(n_tests, seed, max_n=900, max_p=70, max_B=700):
+    r = np.random.default_rng(seed)
+    tests = []
+    for k in range(n_tests):
+        nx, ny = int(r.integers(1, max_n)), int(r.integers(1, max_n))
+        p = int(r.integers(1, max_p))
+        stat = "ed" if k % 3 else "mmd"
+        spec = workloads.TwoSampleSpec(nx=nx, ny=ny, p=p, y_mean=0.1 * (k % 2), data_seed=seed * 1000 + k)
+        X, Y = workloads.gaussian_pair(spec)
+        tests.append(dict(X=X, Y=Y, B=int(r.integers(0, max_B)), seed=k + 7, stat=stat, sigma=float(np.sqrt(p))))
+    return tests
+
+
+def _close(a, b, tol=REL_TOL):
+    a, b = np.asarray(a), np.asarray(b)
+    return a.shape == b.shape and (a.size == 0 or np.max(np.abs(a - b) / np.abs(b)) <= tol)
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "plain_fp32"])
+def test_batch_equals_single_tests(ctx, prec):
+    tests = _uneven(24, seed=1)
+    res = ctx.test_batch(tests, prec=prec)
+    for t, r in zip(tests, res):
+        single = ctx.test(t["X"], t["Y"], B=t["B"], seed=t["seed"], stat=t["stat"], sigma=t["sigma"], prec=prec)
+        assert abs(r.observed - single.observed) <= REL_TOL * abs(single.observed)
+        if t["B"] > 0:
+            assert _close(r.stats, single.stats)
+        near = single.n_near_tie
+        assert abs(r.n_ge - single.n_ge) <= near
+        assert r.p_value == (1.0 + r.n_ge) / (1.0 + t["B"])
+
+
+@pytest.mark.parametrize("prec", ["split_bf16", "plain_fp32"])
+def test_batch_against_oracle(ctx, prec):
+    tests = _uneven(8, seed=2, max_n=120, max_p=12, max_B=200)
+    res = ctx.test_batch(tests, prec=prec)
+    for t, r in zip(tests, res):
+        ref = oracle.permutation_test(t["X"], t["Y"], B=t["B"], seed=t["seed"], stat=t["stat"], sigma=t["sigma"])
+        assert abs(r.observed - ref["observed"]) <= REL_TOL * abs(ref["observed"])
+        if t["B"] > 0:
+            assert _close(r.stats, ref["stats"])
+            near = np.abs(ref["stats"] - ref["observed"]) <= 1e-5 * abs(ref["observed"])
+            assert abs(r.n_ge - ref["n_ge"]) <= int(near.sum())
+
+
+def test_batch_graph_replay_with_new_data(ctx):
+    shapes = _uneven(12, seed=3)
+    first = ctx.test_batch(shapes)            # captures (or autotunes, then captures)
+    again = ctx.test_batch(shapes)            # replays the graph
+    for a, b in zip(first, again):
+        assert a.observed == b.observed and a.n_ge == b.n_ge
+        assert np.array_equal(np.asarray(a.stats), np.asarray(b.stats))
+    # same shapes, new data and seeds: the replay must see the new inputs
+    fresh = _uneven(12, seed=4)
+    for f, s in zip(fresh, shapes):
+        X = np.random.default_rng(99).standard_normal(s["X"].shape).astype(np.float32)
+        f.update(X=X, Y=s["Y"] * 1.5, B=s["B"], stat=s["stat"], sigma=s["sigma"], seed=s["seed"] + 100)
+    got = ctx.test_batch(fresh)
+    for t, r in zip(fresh, got):
+        single = ctx.test(t["X"], t["Y"], B=t["B"], seed=t["seed"], stat=t["stat"], sigma=t["sigma"])
+        assert abs(r.observed - single.observed) <= REL_TOL * abs(single.observed)
+        if t["B"] > 0:
+            assert _close(r.stats, single.stats)
+
+
+def test_batch_device_inputs(ctx):
+    import torch
+    tests = _uneven(6, seed=5)
+    host = ctx.test_batch(tests)
+    dev = [dict(t, X=torch.from_numpy(t["X"]).cuda(), Y=torch.from_numpy(t["Y"]).cuda()) for t in tests]
+    got = ctx.test_batch(dev)
+    torch.cuda.synchronize()
+    for a, b, t in zip(host, got, tests):
+        assert a.observed == b.observed and a.n_ge == b.n_ge
+        if t["B"] > 0:
+            assert np.array_equal(np.asarray(a.stats), b.stats.cpu().numpy())
