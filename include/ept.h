@@ -144,11 +144,56 @@ typedef struct {
    results go to results[0 .. n_tests-1]; each test's draws come from its own
    seed exactly as in ept_test, and the statistics equal ept_test's within
    rounding.  on_device applies to every X, Y and perm_stats of the batch.
+   With a caller stream, the run starts after that stream's prior work (a graph
+   replays on the context's stream, ordered after it) and the call returns when
+   the results are ready.
    The contraction's chunk length is autotuned on the first call for a batch shape
    (environment: EPT_AUTOTUNE=0 disables it; EPT_AUTOTUNE_CACHE=<file> keeps the
    choices across processes). */
 ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_tests, int on_device,
                           int prec, ept_result *results, void *stream);
+
+/* Context options (ept_set_option).  EPT_OPT_GRAPHS (default 1): capture and
+   replay CUDA graphs of repeated batches; with 0 every run is launched directly
+   and the per-phase times of ept_result are filled in.  EPT_OPT_AUTOTUNE (default
+   1 unless the environment sets EPT_AUTOTUNE=0): the contraction chunk autotuner.
+   EPT_OPT_SERVE_LANES (default 3, 1..16): serving batches in flight at once;
+   EPT_OPT_SERVE_SLOTS (default 256): serving requests in flight at once; both
+   before the first ept_submit.  EPT_EINVAL for an unknown option or value. */
+enum {
+    EPT_OPT_GRAPHS = 1,
+    EPT_OPT_AUTOTUNE = 2,
+    EPT_OPT_SERVE_LANES = 3,
+    EPT_OPT_SERVE_SLOTS = 4
+};
+ept_status ept_set_option(ept_ctx *ctx, int option, int64_t value);
+
+/* Serving.  ept_submit queues one test (inputs are HOST pointers, copied before it
+   returns, so the caller may free them) and returns a ticket.  A scheduler thread
+   of the context admits queued requests in arrival order while request slots and
+   the device-memory budget (the context's mem_budget_bytes, or 80% of the free
+   device memory when 0) allow, runs everything admitted as one batch, and keeps
+   several batches in flight at once, so requests that arrive while others run are
+   started beside them (continuous batching).  Errors: EPT_ENOMEM if the request
+   can never fit the budget, EPT_EBUSY if the queue is full.  Results equal
+   ept_test's on the same inputs within rounding.  A request whose data is
+   rejected on the device (NaN/Inf) fails alone; the rest of its batch is kept. */
+ept_status ept_submit(ept_ctx *ctx, const ept_test_desc *request, int prec, uint64_t *ticket);
+
+/* *done = 1 when the request has finished (or was cancelled), else 0. */
+ept_status ept_poll(ept_ctx *ctx, uint64_t ticket, int *done);
+
+/* Waits for the request (timeout_ms < 0: no limit) and releases the ticket: its
+   B permuted statistics go to perm_stats (host, may be NULL), the result to out;
+   for a served request out->ms_total is its latency from ept_submit to the
+   scheduler seeing it finished (host clock), and the other times are 0.
+   EPT_ETIMEOUT when not finished in time (the ticket stays valid),
+   EPT_ECANCELLED for a cancelled request, EPT_ENOTFOUND for an unknown ticket. */
+ept_status ept_wait(ept_ctx *ctx, uint64_t ticket, double *perm_stats, ept_result *out, int64_t timeout_ms);
+
+/* Cancels a request: removed if still queued; if already running, its result is
+   discarded when its batch finishes.  The ticket must still be waited on. */
+ept_status ept_cancel(ept_ctx *ctx, uint64_t ticket);
 
 /* Draws b0 .. b0+count-1 of the permutation stream of `seed` (Algorithm 2's
    SampleWithoutReplacement, fixed as Philox4x32-10 + Knuth's selection sampling;

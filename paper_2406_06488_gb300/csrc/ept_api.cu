@@ -11,8 +11,15 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <new>
 #include <string>
 #include <vector>
@@ -253,7 +260,12 @@ struct GraphCache {
     cudaStream_t stream = nullptr;
 };
 
+namespace {
+struct Server;
+}
+
 struct ept_ctx {
+    Server *server = nullptr;           // serving scheduler, started by the first ept_submit
     int device = 0;
     int num_sms = 0;
     size_t budget = 0;
@@ -269,6 +281,10 @@ struct ept_ctx {
     GraphCache graph;
     std::map<std::vector<int64_t>, int> tuned_chunk;   // autotuner cache: batch shape -> chunk length
     bool autotune = true;
+    bool graphs = true;                 // replay captured graphs of repeated batches
+    int serve_lanes = 3;                // serving: batches in flight at once
+    int serve_slots = 256;              // serving: requests in flight at once
+    cudaEvent_t ev_user = nullptr;      // orders the context's stream after a caller's stream
     std::string tune_file;
 };
 
@@ -507,19 +523,37 @@ ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed)
 }
 
 // Results of a finished run (host side).
-ept_status collect(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &specs, ept_result *out, bool timed) {
+// With `per_test`, a test whose input was rejected on the device gets its own
+// status and message there and the others are still returned (serving); without
+// it, the first such test fails the whole call.
+struct TestError {
+    ept_status st;
+    std::string msg;
+};
+
+ept_status test_error(const Plan &P, const Counters *ctr, int t) {
+    if (ctr[t].nonfinite) return fail(EPT_EINVAL, "test %d: X or Y holds NaN or Inf", t);
+    if (ctr[t].bad_mask)
+        return fail(EPT_EINVAL, "test %d: %llu relabeling(s) do not have exactly nx = %lld members among the n rows", t,
+                    (unsigned long long)ctr[t].bad_mask, (long long)P.desc[t].nx);
+    return EPT_OK;
+}
+
+ept_status collect(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &specs, ept_result *out, bool timed,
+                   std::vector<TestError> *per_test = nullptr) {
     const Staging S = staging_layout(P);
     const Counters *ctr = (const Counters *)(c->pinned + S.res_ctr);
     const double *obs = (const double *)(c->pinned + S.res_obs);
     const double *stats = (const double *)(c->pinned + S.res_stats);
-    for (int t = 0; t < P.n_tests; ++t) {
-        if (ctr[t].nonfinite) return fail(EPT_EINVAL, "test %d: X or Y holds NaN or Inf", t);
-        if (ctr[t].bad_mask)
-            return fail(EPT_EINVAL, "test %d: %llu relabeling(s) do not have exactly nx = %lld members among the n rows",
-                        t, (unsigned long long)ctr[t].bad_mask, (long long)P.desc[t].nx);
-    }
     if (P.n_tests > 0 && ctr[0].err_code)
         return fail(EPT_ETIMEOUT, "device-side bounded wait gave up (code 0x%llx)", (unsigned long long)ctr[0].err_code);
+    if (per_test) per_test->assign(P.n_tests, TestError{EPT_OK, std::string()});
+    for (int t = 0; t < P.n_tests; ++t) {
+        const ept_status st = test_error(P, ctr, t);
+        if (st == EPT_OK) continue;
+        if (!per_test) return st;
+        (*per_test)[t] = TestError{st, g_err};
+    }
     float ms_build = 0.f, ms_perm = 0.f, ms_total = 0.f, ms_masks = 0.f, ms_contract = 0.f;
     if (timed) {
         cudaEventElapsedTime(&ms_build, c->ev[1], c->ev[2]);
@@ -619,7 +653,13 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
     if ((st = ensure_pinned(c, S.total)) != EPT_OK) return st;
     if (s != c->stream) CK(cudaStreamSynchronize(c->stream));
     stage_host(c, P, specs, on_device);
-    if (use_graph && s == c->stream) {
+    if (use_graph && c->graphs) {
+        // the graph runs on the context's stream, after the caller's stream's prior work
+        if (s != c->stream) {
+            CK(cudaEventRecord(c->ev_user, s));
+            CK(cudaStreamWaitEvent(c->stream, c->ev_user, 0));
+            s = c->stream;
+        }
         std::vector<int64_t> key = shape_key(specs, prec, on_device);
         key.push_back(chunk_kb);
         if (!(c->graph.exec && c->graph.key == key && c->graph.arena == c->arena)) {
@@ -685,6 +725,279 @@ ept_status run_tuned(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, b
     return run_once(c, specs, prec, on_device, best, use_graph, out, stream, nullptr);
 }
 
+// ---------------------------------------------------------------------------
+// Serving (continuous batching).  ept_submit copies a request and queues it.  A
+// scheduler thread admits queued requests in arrival order while request slots
+// and the device-memory budget allow, packs everything admitted into one batched
+// run (all phases as grouped launches over the batch) and starts it on a free
+// lane: an internal sub-context with its own streams and pinned staging, whose
+// device scratch comes from the server's stream-ordered memory pool and goes back
+// to it when the lane's work is done.  Several lanes run at once, so requests that
+// arrive while others are on the GPU start in the next batch and overlap with
+// them on the device.  A host callback at the end of each lane's work wakes the
+// scheduler.
+enum ReqState { REQ_PENDING = 0, REQ_RUNNING = 1, REQ_DONE = 2, REQ_CANCELLED = 3 };
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    TestSpec spec;
+    std::vector<float> X, Y;
+    std::vector<double> stats;
+    ept_result res;
+    int prec = 0;
+    int state = REQ_PENDING;
+    bool cancel_req = false;
+    ept_status status = EPT_OK;
+    std::string err;
+    size_t bytes = 0;   // device scratch of this request alone (admission estimate)
+    Clock::time_point t_submit;
+};
+
+struct Lane {
+    ept_ctx *ctx = nullptr;
+    bool busy = false;
+    std::vector<Request *> reqs;
+    std::vector<TestSpec> specs;
+    Plan plan;
+    size_t bytes = 0;   // device scratch held by the lane's run
+    uint8_t *arena = nullptr;
+    cudaEvent_t done = nullptr;
+};
+
+struct Server {
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::atomic<uint64_t> wakeups{0};
+    std::deque<Request *> pending;
+    std::unordered_map<uint64_t, Request *> reqs;
+    std::vector<Lane> lanes;
+    cudaMemPool_t pool = nullptr;
+    size_t budget = 0, in_use = 0;
+    int max_slots = 256, slots = 0;
+    uint64_t next_ticket = 1;
+    bool stop = false;
+    size_t max_pending = 1 << 16;
+};
+
+void CUDART_CB lane_finished(void *arg) {
+    Server *S = (Server *)arg;
+    S->wakeups.fetch_add(1);
+    S->cv_work.notify_all();   // no lock: the scheduler also wakes on a short timeout
+}
+
+ept_status lane_enqueue(Server *S, Lane &L) {
+    ept_ctx *c = L.ctx;
+    cudaStream_t s = c->stream;
+    const Staging SL = staging_layout(L.plan);
+    ept_status st = ensure_pinned(c, SL.total);
+    if (st != EPT_OK) return st;
+    void *mem = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&mem, L.plan.total, S->pool, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(EPT_ENOMEM, "device scratch of %zu bytes not available: %s", (size_t)L.plan.total,
+                    cudaGetErrorString(e));
+    }
+    L.arena = (uint8_t *)mem;
+    c->arena = L.arena;   // the kernels and staging address the lane's scratch through the context
+    c->arena_cap = L.plan.total;
+    stage_host(c, L.plan, L.specs, false);
+    st = enqueue_device(c, L.plan, s, false);
+    c->arena = nullptr;
+    c->arena_cap = 0;
+    e = cudaFreeAsync(L.arena, s);   // returns to the pool once the run's work is done
+    L.arena = nullptr;
+    if (st != EPT_OK) return st;
+    if (e != cudaSuccess) return fail(EPT_ECUDA, "cudaFreeAsync: %s", cudaGetErrorString(e));
+    CK(cudaEventRecord(L.done, s));
+    CK(cudaLaunchHostFunc(s, lane_finished, S));
+    return EPT_OK;
+}
+
+void finish_requests(Server *S, Lane &L, ept_status st, const std::string &msg, const ept_result *out,
+                     const std::vector<TestError> *per_test) {
+    const Clock::time_point now = Clock::now();
+    for (size_t k = 0; k < L.reqs.size(); ++k) {
+        Request *r = L.reqs[k];
+        r->status = st;
+        r->err = msg;
+        if (st == EPT_OK && per_test && (*per_test)[k].st != EPT_OK) {
+            r->status = (*per_test)[k].st;
+            r->err = (*per_test)[k].msg;
+        }
+        if (r->status == EPT_OK) {
+            r->res = out[k];
+            r->res.ms_build = r->res.ms_perm = r->res.ms_masks = r->res.ms_contract = 0.f;
+            r->res.ms_total = (float)std::chrono::duration<double, std::milli>(now - r->t_submit).count();
+        }
+        r->state = r->cancel_req ? REQ_CANCELLED : REQ_DONE;
+        S->slots -= 1;
+    }
+    S->in_use -= L.bytes;
+    L.bytes = 0;
+    L.busy = false;
+    L.reqs.clear();
+    L.specs.clear();
+    S->cv_done.notify_all();
+}
+
+// Takes the next batch from the queue for a free lane (lock held): requests of the
+// first request's precision in arrival order, while slots and memory allow.  The
+// batch's exact scratch size is planned; requests are handed back from the end
+// until it fits.
+bool form_batch(Server *S, Lane &L) {
+    if (S->pending.empty()) return false;
+    const int prec = S->pending.front()->prec;
+    std::vector<Request *> batch;
+    size_t est = 0;
+    for (auto it = S->pending.begin(); it != S->pending.end();) {
+        Request *r = *it;
+        if (r->prec != prec) {
+            ++it;
+            continue;
+        }
+        if (S->slots + (int)batch.size() >= S->max_slots) break;
+        if (S->in_use + est + r->bytes > S->budget) break;   // arrival order: no overtaking
+        batch.push_back(r);
+        est += r->bytes;
+        it = S->pending.erase(it);
+    }
+    std::vector<TestSpec> specs;
+    for (Request *r : batch) specs.push_back(r->spec);
+    while (!batch.empty()) {
+        plan_batch(L.plan, specs, prec, true, CHUNK_KB_DEFAULT);
+        if (S->in_use + L.plan.total <= S->budget) break;
+        // hand the last one back, at its place in arrival order
+        Request *r = batch.back();
+        batch.pop_back();
+        specs.pop_back();
+        auto pos = S->pending.begin();
+        while (pos != S->pending.end() && (*pos)->ticket < r->ticket) ++pos;
+        S->pending.insert(pos, r);
+    }
+    if (batch.empty()) return false;
+    L.busy = true;
+    L.reqs = batch;
+    L.specs = specs;
+    L.bytes = L.plan.total;
+    S->in_use += L.bytes;
+    S->slots += (int)batch.size();
+    for (Request *r : batch) r->state = REQ_RUNNING;
+    return true;
+}
+
+void serve_loop(Server *S, int device) {
+    cudaSetDevice(device);
+    std::unique_lock<std::mutex> lk(S->mu);
+    for (;;) {
+        const uint64_t seen = S->wakeups.load();
+        bool progressed = false;
+        for (Lane &L : S->lanes) {
+            if (!L.busy) continue;
+            const cudaError_t q = cudaEventQuery(L.done);
+            if (q == cudaErrorNotReady) continue;
+            std::vector<ept_result> out(L.reqs.size());
+            std::vector<TestError> per_test;
+            ept_status st = EPT_OK;
+            if (q != cudaSuccess) st = fail(EPT_ECUDA, "serving run failed: %s", cudaGetErrorString(q));
+            else st = collect(L.ctx, L.plan, L.specs, out.data(), false, &per_test);
+            finish_requests(S, L, st, st == EPT_OK ? std::string() : g_err, out.data(), &per_test);
+            progressed = true;
+        }
+        bool any_busy = false;
+        for (Lane &L : S->lanes) any_busy |= L.busy;
+        if (S->stop && !any_busy) break;
+        if (!S->stop) {
+            for (Lane &L : S->lanes) {
+                if (L.busy || !form_batch(S, L)) continue;
+                lk.unlock();
+                const ept_status st = lane_enqueue(S, L);
+                const std::string msg = g_err;
+                if (st != EPT_OK) cudaStreamSynchronize(L.ctx->stream);   // nothing of it stays in flight
+                lk.lock();
+                if (st != EPT_OK) finish_requests(S, L, st, msg, nullptr, nullptr);
+                progressed = true;
+            }
+        }
+        if (!progressed)
+            S->cv_work.wait_for(lk, std::chrono::milliseconds(any_busy ? 1 : 50),
+                                [S, seen] { return S->wakeups.load() != seen || S->stop; });
+    }
+}
+
+ept_status serve_start(ept_ctx *c) {
+    if (c->server) return EPT_OK;
+    DeviceGuard dg(c->device);
+    std::unique_ptr<Server> S(new (std::nothrow) Server());
+    if (!S) return fail(EPT_ENOMEM, "host allocation failed");
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        free_b = 0;
+    }
+    S->budget = c->budget ? c->budget : (size_t)(0.8 * (double)free_b);
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = c->device;
+    CK(cudaMemPoolCreate(&S->pool, &props));
+    uint64_t keep = S->budget;   // freed scratch stays in the pool for the next batch
+    cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    ept_status st = EPT_OK;
+    S->max_slots = c->serve_slots;
+    for (int k = 0; k < c->serve_lanes && st == EPT_OK; ++k) {
+        Lane L;
+        if ((st = ept_create(&L.ctx, c->device, 0)) != EPT_OK) break;
+        L.ctx->autotune = false;
+        if (cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            ept_destroy(L.ctx);
+            st = fail(EPT_ECUDA, "event creation failed");
+            break;
+        }
+        S->lanes.push_back(L);
+    }
+    if (st != EPT_OK) {
+        for (Lane &M : S->lanes) {
+            cudaEventDestroy(M.done);
+            ept_destroy(M.ctx);
+        }
+        cudaMemPoolDestroy(S->pool);
+        return st;
+    }
+    S->th = std::thread(serve_loop, S.get(), c->device);
+    c->server = S.release();
+    return EPT_OK;
+}
+
+void serve_stop(ept_ctx *c) {
+    Server *S = c->server;
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        for (Request *r : S->pending) r->state = REQ_CANCELLED;
+        S->pending.clear();
+        S->cv_done.notify_all();
+    }
+    S->cv_work.notify_all();
+    if (S->th.joinable()) S->th.join();
+    DeviceGuard dg(c->device);
+    for (Lane &L : S->lanes) {
+        cudaEventDestroy(L.done);
+        ept_destroy(L.ctx);
+    }
+    cudaMemPoolDestroy(S->pool);
+    for (auto &kv : S->reqs) delete kv.second;
+    delete S;
+    c->server = nullptr;
+}
+
 }  // namespace
 
 extern "C" {
@@ -722,6 +1035,7 @@ ept_status ept_create(ept_ctx **out, int device, size_t mem_budget_bytes) {
     for (int k = 0; k < 7 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev[k]);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev_side[k]);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_user, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         ept_destroy(c);
         return fail(EPT_ECUDA, "stream/event creation failed: %s", cudaGetErrorString(e));
@@ -732,6 +1046,7 @@ ept_status ept_create(ept_ctx **out, int device, size_t mem_budget_bytes) {
 
 ept_status ept_destroy(ept_ctx *c) {
     if (!c) return EPT_OK;
+    serve_stop(c);
     {
         DeviceGuard dg(c->device);
         if (c->stream) cudaStreamSynchronize(c->stream);
@@ -743,6 +1058,7 @@ ept_status ept_destroy(ept_ctx *c) {
             if (c->ev[k]) cudaEventDestroy(c->ev[k]);
         for (int k = 0; k < 3; ++k)
             if (c->ev_side[k]) cudaEventDestroy(c->ev_side[k]);
+        if (c->ev_user) cudaEventDestroy(c->ev_user);
         if (c->side) cudaStreamDestroy(c->side);
         if (c->stream) cudaStreamDestroy(c->stream);
     }
@@ -877,6 +1193,138 @@ ept_status ept_build_blocks(ept_ctx *c, const float *X, int64_t nx, const float 
     if (!on_device) CK(cudaMemcpyAsync(D_out, dout, out_bytes, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     if (h->nonfinite) return fail(EPT_EINVAL, "X or Y holds NaN or Inf");
+    return EPT_OK;
+}
+
+ept_status ept_set_option(ept_ctx *c, int option, int64_t value) {
+    if (!c) return fail(EPT_EINVAL, "null context");
+    std::lock_guard<std::mutex> lock(c->mu);
+    switch (option) {
+    case EPT_OPT_GRAPHS:
+        c->graphs = value != 0;
+        if (!c->graphs) {
+            DeviceGuard dg(c->device);
+            drop_graph(c);
+        }
+        return EPT_OK;
+    case EPT_OPT_AUTOTUNE:
+        c->autotune = value != 0;
+        return EPT_OK;
+    case EPT_OPT_SERVE_LANES:
+    case EPT_OPT_SERVE_SLOTS:
+        if (c->server) return fail(EPT_EINVAL, "serving options must be set before the first ept_submit");
+        if (option == EPT_OPT_SERVE_LANES) {
+            if (value < 1 || value > 16) return fail(EPT_EINVAL, "serving lanes must be in [1, 16]");
+            c->serve_lanes = (int)value;
+        } else {
+            if (value < 1 || value > (1 << 16)) return fail(EPT_EINVAL, "serving slots must be in [1, 65536]");
+            c->serve_slots = (int)value;
+        }
+        return EPT_OK;
+    default:
+        return fail(EPT_EINVAL, "unknown option %d", option);
+    }
+}
+
+ept_status ept_submit(ept_ctx *c, const ept_test_desc *q, int prec, uint64_t *ticket) {
+    if (!c || !q || !ticket) return fail(EPT_EINVAL, "null context, request or ticket");
+    if (!q->X || !q->Y) return fail(EPT_EINVAL, "null X or Y");
+    if (q->B < 0 || q->B > ((int64_t)1 << 31)) return fail(EPT_EINVAL, "B must be in [0, 2^31]");
+    ept_status st = validate(q->nx, q->ny, q->p, q->stat, q->sigma, prec);
+    if (st != EPT_OK) return st;
+    {
+        std::lock_guard<std::mutex> lock(c->mu);
+        if ((st = serve_start(c)) != EPT_OK) return st;
+    }
+    Server *S = c->server;
+    Request *r = new (std::nothrow) Request();
+    if (!r) return fail(EPT_ENOMEM, "host allocation failed");
+    r->X.assign(q->X, q->X + q->nx * q->p);
+    r->Y.assign(q->Y, q->Y + q->ny * q->p);
+    r->stats.assign((size_t)q->B, 0.0);
+    r->spec = one_test(r->X.data(), q->nx, r->Y.data(), q->ny, q->p, q->stat, q->sigma, q->B, q->seed, nullptr,
+                       q->B > 0 ? r->stats.data() : nullptr)[0];
+    r->prec = prec;
+    Plan P;
+    plan_batch(P, std::vector<TestSpec>(1, r->spec), prec, true, CHUNK_KB_DEFAULT);
+    r->bytes = P.total;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (r->bytes > S->budget) {
+        delete r;
+        return fail(EPT_ENOMEM, "request needs %zu bytes of device scratch, over the serving budget of %zu",
+                    (size_t)P.total, S->budget);
+    }
+    if (S->pending.size() >= S->max_pending) {
+        delete r;
+        return fail(EPT_EBUSY, "serving queue is full (%zu pending requests)", S->pending.size());
+    }
+    r->ticket = S->next_ticket++;
+    r->t_submit = Clock::now();
+    S->reqs[r->ticket] = r;
+    S->pending.push_back(r);
+    *ticket = r->ticket;
+    S->wakeups.fetch_add(1);
+    S->cv_work.notify_all();
+    return EPT_OK;
+}
+
+ept_status ept_poll(ept_ctx *c, uint64_t ticket, int *done) {
+    if (!c || !done) return fail(EPT_EINVAL, "null context or output");
+    Server *S = c->server;
+    if (!S) return fail(EPT_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(EPT_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    *done = it->second->state >= REQ_DONE;
+    return EPT_OK;
+}
+
+ept_status ept_wait(ept_ctx *c, uint64_t ticket, double *perm_stats, ept_result *out, int64_t timeout_ms) {
+    if (!c) return fail(EPT_EINVAL, "null context");
+    Server *S = c->server;
+    if (!S) return fail(EPT_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(EPT_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Request *r = it->second;
+    const auto pred = [r] { return r->state >= REQ_DONE; };
+    if (timeout_ms < 0) S->cv_done.wait(lk, pred);
+    else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred))
+        return fail(EPT_ETIMEOUT, "request %llu not finished after %lld ms", (unsigned long long)ticket,
+                    (long long)timeout_ms);
+    S->reqs.erase(it);
+    const int state = r->state;
+    const ept_status st = r->status;
+    const std::string msg = r->err;
+    if (state == REQ_DONE && st == EPT_OK) {
+        if (out) *out = r->res;
+        if (perm_stats && !r->stats.empty()) memcpy(perm_stats, r->stats.data(), r->stats.size() * 8);
+    }
+    delete r;
+    if (state == REQ_CANCELLED) return fail(EPT_ECANCELLED, "request %llu was cancelled", (unsigned long long)ticket);
+    if (st != EPT_OK) return fail(st, "%s", msg.c_str());
+    return EPT_OK;
+}
+
+ept_status ept_cancel(ept_ctx *c, uint64_t ticket) {
+    if (!c) return fail(EPT_EINVAL, "null context");
+    Server *S = c->server;
+    if (!S) return fail(EPT_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(EPT_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Request *r = it->second;
+    if (r->state == REQ_PENDING) {
+        for (auto p = S->pending.begin(); p != S->pending.end(); ++p)
+            if (*p == r) {
+                S->pending.erase(p);
+                break;
+            }
+        r->state = REQ_CANCELLED;
+        S->cv_done.notify_all();
+    } else if (r->state == REQ_RUNNING) {
+        r->cancel_req = true;   // its batch finishes; the result is discarded
+    }
     return EPT_OK;
 }
 

@@ -27,7 +27,8 @@ STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT
 
 # every entry point declared in include/ept.h
 EXPORTS = ["ept_abi_version", "ept_last_error", "ept_create", "ept_destroy", "ept_estimate_bytes", "ept_test",
-           "ept_test_masks", "ept_perm_masks", "ept_build_blocks", "ept_test_static", "ept_test_batch"]
+           "ept_test_masks", "ept_perm_masks", "ept_build_blocks", "ept_test_static", "ept_test_batch",
+           "ept_set_option", "ept_submit", "ept_poll", "ept_wait", "ept_cancel"]
 
 
 class EptError(RuntimeError):
@@ -105,6 +106,16 @@ def load():
     lib.ept_test_static.restype = i32
     lib.ept_test_batch.argtypes = [vp, ctypes.POINTER(_TestDesc), i64, i32, i32, ctypes.POINTER(_Result), vp]
     lib.ept_test_batch.restype = i32
+    lib.ept_set_option.argtypes = [vp, i32, i64]
+    lib.ept_set_option.restype = i32
+    lib.ept_submit.argtypes = [vp, ctypes.POINTER(_TestDesc), i32, ctypes.POINTER(u64)]
+    lib.ept_submit.restype = i32
+    lib.ept_poll.argtypes = [vp, u64, ctypes.POINTER(i32)]
+    lib.ept_poll.restype = i32
+    lib.ept_wait.argtypes = [vp, u64, vp, ctypes.POINTER(_Result), i64]
+    lib.ept_wait.restype = i32
+    lib.ept_cancel.argtypes = [vp, u64]
+    lib.ept_cancel.restype = i32
     _lib = lib
     return lib
 
@@ -132,6 +143,9 @@ def _prec(prec) -> int:
 
 def estimate_bytes(nx: int, ny: int, p: int, B: int, prec="split_bf16") -> int:
     return int(load().ept_estimate_bytes(nx, ny, p, B, _prec(prec)))
+
+
+OPTION = {"graphs": 1, "autotune": 2, "serve_lanes": 3, "serve_slots": 4}
 
 
 class Context:
@@ -235,28 +249,47 @@ class Context:
         """Many tests in one batched run.  tests: sequence of dicts with keys X, Y, B and
         optionally seed, stat, sigma (all X/Y numpy, or all CUDA tensors).  Returns a
         list of Result (stats: B permuted statistics each when want_stats)."""
-        n = len(tests)
-        if n == 0:
-            return []
-        descs = (_TestDesc * n)()
-        keep, bufs = [], []
-        on_dev = None
-        stream = None
-        for k, t in enumerate(tests):
-            X, Y, px, py, dev, st = self._arrays(t["X"], t["Y"])
-            if on_dev is None:
-                on_dev, stream = dev, st
-            elif on_dev != dev:
-                raise TypeError("all tests of a batch must use the same memory space")
-            B = int(t["B"])
-            buf, pbuf = self._stats_buffer(X, B if want_stats else 0, dev)
-            keep.append((X, Y))
-            bufs.append(buf)
-            descs[k] = _TestDesc(px, py, X.shape[0], Y.shape[0], X.shape[1], _stat(t.get("stat", "ed")),
-                                 float(t.get("sigma", 1.0)), B, int(t.get("seed", 0)), pbuf)
-        res = (_Result * n)()
-        _check(load().ept_test_batch(self._h, descs, n, on_dev, _prec(prec), res, None))
-        return [_result(res[k], bufs[k]) for k in range(n)]
+        return self.prepare_batch(tests, prec, want_stats).run()
+
+    def prepare_batch(self, tests, prec="split_bf16", want_stats: bool = True) -> "PreparedBatch":
+        """The descriptors and output buffers of a batch, built once; `run()` runs it
+        (again) on whatever the arrays hold at that time."""
+        return PreparedBatch(self, tests, prec, want_stats)
+
+    def set_option(self, option: str, value: int) -> None:
+        _check(load().ept_set_option(self._h, OPTION[option], int(value)))
+
+    # ------------------------------------------------------------------ serving
+    def submit(self, X, Y, B: int, seed: int = 0, stat="ed", sigma: float = 1.0, prec="split_bf16") -> int:
+        """Queue one test (host arrays, copied before returning); returns a ticket."""
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        Y = np.ascontiguousarray(Y, dtype=np.float32)
+        d = _TestDesc(X.ctypes.data, Y.ctypes.data, X.shape[0], Y.shape[0], X.shape[1], _stat(stat), float(sigma),
+                      int(B), int(seed), None)
+        t = ctypes.c_uint64(0)
+        _check(load().ept_submit(self._h, ctypes.byref(d), _prec(prec), ctypes.byref(t)))
+        self._pending_B = getattr(self, "_pending_B", {})
+        self._pending_B[t.value] = int(B)
+        return t.value
+
+    def poll(self, ticket: int) -> bool:
+        done = ctypes.c_int(0)
+        _check(load().ept_poll(self._h, ctypes.c_uint64(ticket), ctypes.byref(done)))
+        return bool(done.value)
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> Result:
+        B = getattr(self, "_pending_B", {}).get(ticket, 0)
+        buf = np.empty(B, dtype=np.float64) if B > 0 else None
+        r = _Result()
+        st = load().ept_wait(self._h, ctypes.c_uint64(ticket), buf.ctypes.data if buf is not None else None,
+                             ctypes.byref(r), int(timeout_ms))
+        if st != 5:   # a timeout keeps the ticket
+            self._pending_B.pop(ticket, None)
+        _check(st)
+        return _result(r, buf)
+
+    def cancel(self, ticket: int) -> None:
+        _check(load().ept_cancel(self._h, ctypes.c_uint64(ticket)))
 
     def perm_masks(self, seed: int, nx: int, ny: int, b0: int, count: int) -> np.ndarray:
         """Draws b0 .. b0+count-1 of the permutation stream, generated on the GPU:
@@ -281,3 +314,34 @@ class Context:
         _check(load().ept_build_blocks(self._h, px, X.shape[0], py, Y.shape[0], X.shape[1], on_dev, _stat(stat),
                                        float(sigma), _prec(prec), pout, stream))
         return out
+
+
+class PreparedBatch:
+    """A batch of tests with its descriptors and output buffers built once."""
+
+    def __init__(self, ctx: Context, tests, prec, want_stats: bool):
+        self.ctx = ctx
+        self.n = n = len(tests)
+        self.prec = _prec(prec)
+        self.descs = (_TestDesc * max(n, 1))()
+        self.res = (_Result * max(n, 1))()
+        self.keep, self.bufs = [], []
+        self.on_dev, self.stream = 0, None
+        for k, t in enumerate(tests):
+            X, Y, px, py, dev, st = ctx._arrays(t["X"], t["Y"])
+            if k == 0:
+                self.on_dev, self.stream = dev, st
+            elif self.on_dev != dev:
+                raise TypeError("all tests of a batch must use the same memory space")
+            B = int(t["B"])
+            buf, pbuf = ctx._stats_buffer(X, B if want_stats else 0, dev)
+            self.keep.append((X, Y))
+            self.bufs.append(buf)
+            self.descs[k] = _TestDesc(px, py, X.shape[0], Y.shape[0], X.shape[1], _stat(t.get("stat", "ed")),
+                                      float(t.get("sigma", 1.0)), B, int(t.get("seed", 0)), pbuf)
+
+    def run(self):
+        if self.n == 0:
+            return []
+        _check(load().ept_test_batch(self.ctx._h, self.descs, self.n, self.on_dev, self.prec, self.res, self.stream))
+        return [_result(self.res[k], self.bufs[k]) for k in range(self.n)]

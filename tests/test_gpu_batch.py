@@ -97,3 +97,36 @@ def test_batch_device_inputs(ctx):
         assert a.observed == b.observed and a.n_ge == b.n_ge
         if t["B"] > 0:
             assert np.array_equal(np.asarray(a.stats), b.stats.cpu().numpy())
+
+
+def test_prepared_batch_in_place_update_and_no_graph(ctx):
+    import torch
+    tests = _uneven(10, seed=6)
+    dev = [dict(t, X=torch.from_numpy(t["X"]).cuda(), Y=torch.from_numpy(t["Y"]).cuda()) for t in tests]
+    pb = ctx.prepare_batch(dev)
+    pb.run()
+    first = [(r.observed, r.n_ge) for r in pb.run()]   # graph replay
+    # overwrite the inputs in place (on torch's stream): the replay must see the new data
+    for d in dev:
+        d["X"].mul_(1.25).add_(0.05)
+    got = pb.run()
+    for t, d, r in zip(tests, dev, got):
+        single = ctx.test(d["X"].cpu().numpy(), d["Y"].cpu().numpy(), B=t["B"], seed=t["seed"], stat=t["stat"],
+                          sigma=t["sigma"])
+        assert abs(r.observed - single.observed) <= REL_TOL * abs(single.observed)
+    assert any(a[0] != r.observed for a, r in zip(first, got))
+    # the same batch launched directly: identical results, per-phase times filled in
+    ctx.set_option("graphs", 0)
+    try:
+        direct = pb.run()
+    finally:
+        ctx.set_option("graphs", 1)
+    for a, b in zip(got, direct):
+        assert a.observed == b.observed and a.n_ge == b.n_ge
+    assert direct[0].ms_contract > 0 and direct[0].ms_build > 0
+
+
+def test_set_option_rejects_unknown(ctx):
+    from paper_2406_06488_gb300 import ept
+    with pytest.raises(ept.EptError):
+        ctx.set_option("serve_lanes", 0)
