@@ -47,6 +47,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="highdim", choices=["highdim", "mmd", "small", "batched", "serving"])
+    ap.add_argument("--tests", type=int, default=512, help="batched: tests per step")
     ap.add_argument("--rates", default="10,100,1000", help="serving: request rates (1/s) swept")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests per rate (at most)")
     ap.add_argument("--serve-plain-rate", type=float, default=10.0,
@@ -379,7 +380,7 @@ def run_batched(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2406_06488_gb300 import ept
-    specs, tests = _batched_tests()
+    specs, tests = _batched_tests(args.tests)
     dev = [dict(t, X=torch.from_numpy(t["X"]).cuda(), Y=torch.from_numpy(t["Y"]).cuda()) for t in tests]
     ctx = ept.Context(local)
     pb = ctx.prepare_batch(dev)
@@ -463,8 +464,8 @@ def run_batched(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f16", "data": "synthetic",
-        "config": {"workload": "batched: 512 independent ED tests per step, nx, ny ~ U{50..2000}, p ~ U{20..500}, "
-                               "half null / half Y mean 0.1, B=5000 each, one batched run replayed from a CUDA graph",
+        "config": {"workload": "batched: %d independent ED tests per step, nx, ny ~ U{50..2000}, p ~ U{20..500}, "
+                               "half null / half Y mean 0.1, B=5000 each, one batched run replayed from a CUDA graph" % len(specs),
                    "precision": "blocks FP32, contraction FP16 hi+lo split on tcgen05, FP32 accumulate, FP64 combine",
                    "l2": "flushed between steps (256 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},

@@ -475,7 +475,7 @@ ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed)
     cudaStream_t s2 = c->side;
     CK(cudaStreamWaitEvent(s2, c->ev[1], 0));
     if (timed) CK(cudaEventRecord(c->ev_side[1], s2));
-    launch_masks(b, s2);
+    launch_masks(b, c->num_sms, s2);
     CK(cudaGetLastError());
     CK(cudaEventRecord(c->ev_side[2], s2));
 

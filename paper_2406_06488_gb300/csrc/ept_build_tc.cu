@@ -45,7 +45,8 @@ constexpr int A_BYTES = BM * BK * 2;                  // 16 KB
 constexpr int B_BYTES = BN * BK * 2;                  // 32 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 96 KB: A hi, A lo, B hi, B lo
 constexpr int NUM_THREADS = 192;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 1024;
+// stages | barriers (1 KB) | per-epilogue-warp column norms and scales (4 x 2 KB) | alignment slack
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 4 * PANEL * 8 + 1024;
 // kind::f16 instruction descriptor with A = B = FP16 (format 0), D = FP32, K-major
 constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 
@@ -257,22 +258,38 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
     } else {
         // ---------------- epilogue: one tile row per thread ----------------
+        // Each warp stages the tile's 256 column norms and inverse scales in its own
+        // shared-memory slice (read back as broadcasts), computes each group of 32
+        // entries without branches, patches padding and the diagonal with selects, and
+        // recomputes the rare cancellation-prone entries afterwards (same thread, so
+        // its later store wins).
         const int quarter = warp & 3;
         const int rt = quarter * 32 + lane;   // row within the 128-row tile
+        float2 *colv = reinterpret_cast<float2 *>(smem + STAGES * STAGE_BYTES + 1024) + (warp - 2) * PANEL;
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const Tile tile = bt.tiles[t];
-            const TestDesc d = bt.desc[tile.t];
-            const int64_t n = d.n, p = d.p, NKB = d.NKB;
+            const TestDesc &d = bt.desc[tile.t];
+            const int64_t n = d.n, p = d.p, NKB = d.NKB, nx = d.nx;
+            const float *X = d.X, *Y = d.Y;
             const int stat = d.stat;
             const float neg_inv_2s2 = d.neg_inv_2s2, tau = d.tau;
+            const float diag_val = (stat == 0) ? 0.f : 1.f;
             const float *norms = bt.norms + d.row0, *inv_scale = bt.iscale + d.row0;
+            float *Dblk = bt.D + (d.blk0 + blk_index(tile.I, (int64_t)tile.J * KB_PER_PANEL, NKB)) * PANEL * KB;
             unsigned fixups = 0;
             const int rp = tile.h * BM + rt;                 // row within panel I
             const int64_t i = (int64_t)tile.I * PANEL + rp;  // pooled row of the test
             const float ni = (i < n) ? norms[i] : 0.f;
             const float si = (i < n) ? inv_scale[i] : 0.f;
+            __syncwarp();
+#pragma unroll
+            for (int c = lane; c < PANEL; c += 32) {
+                const int64_t j = (int64_t)tile.J * PANEL + c;
+                colv[c] = (j < n) ? make_float2(norms[j], inv_scale[j]) : make_float2(0.f, 0.f);
+            }
+            __syncwarp();
             if (!mbar_wait(su32(&bars->acc_full[acc]), acc_phase, abort_flag, ctr, ERR_WAIT_EPI)) break;
             fence_after();
             const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
@@ -281,42 +298,53 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 uint32_t v[32];
                 tmem_ld32(tbase + (uint32_t)(g * 32), v);
                 const int64_t j0 = (int64_t)tile.J * PANEL + g * 32;
-                const float nj_l = (j0 + lane < n) ? norms[j0 + lane] : 0.f;
-                const float sj_l = (j0 + lane < n) ? inv_scale[j0 + lane] : 0.f;
                 float out[32];
+                uint32_t fix = 0;
 #pragma unroll
                 for (int e = 0; e < 32; ++e) {
-                    const float nj = __shfl_sync(0xFFFFFFFFu, nj_l, e);
-                    const float sj = __shfl_sync(0xFFFFFFFFu, sj_l, e);
-                    const int64_t j = j0 + e;
-                    float val = 0.f;
-                    if (i < n && j < n) {
-                        if (i == j) {
-                            val = (stat == 0) ? 0.f : 1.f;
-                        } else {
-                            const float gij = (__uint_as_float(v[e]) * si) * sj;   // exact rescaling
-                            const float d2 = fmaxf(0.f, ni + nj - 2.f * gij);
-                            if (d2 < tau * (ni + nj)) {
-                                const float *zi = row_ptr(d, i), *zj = row_ptr(d, j);
-                                double s = 0.0;
-                                for (int64_t k = 0; k < p; ++k) {
-                                    const double d = (double)zi[k] - (double)zj[k];
-                                    s = fma(d, d, s);
-                                }
-                                ++fixups;
-                                val = (stat == 0) ? (float)sqrt(s) : (float)exp(s * (double)neg_inv_2s2);
-                            } else {
-                                val = (stat == 0) ? sqrtf(d2) : expf(d2 * neg_inv_2s2);
-                            }
-                        }
-                    }
+                    const float2 cj = colv[g * 32 + e];
+                    const float gij = (__uint_as_float(v[e]) * si) * cj.y;   // exact rescaling
+                    const float sn = ni + cj.x;
+                    const float d2 = fmaxf(0.f, sn - 2.f * gij);
+                    fix |= (d2 < tau * sn) ? (1u << e) : 0u;
+                    float val;
+                    if (stat == 0) asm("sqrt.approx.f32 %0, %1;" : "=f"(val) : "f"(d2));
+                    else val = expf(d2 * neg_inv_2s2);
                     out[e] = val;
                 }
-                const int64_t kb = (int64_t)tile.J * KB_PER_PANEL + (g >> 1);
-                float *dst = bt.D + ((d.blk0 + blk_index(tile.I, kb, NKB)) * PANEL + rp) * KB + (g & 1) * 32;
+                // padding rows / columns hold 0; the diagonal is exactly 0 (ED) / 1 (MMD)
+                const uint32_t jvalid =
+                    (j0 >= n) ? 0u : ((j0 + 32 <= n) ? 0xFFFFFFFFu : ((1u << (uint32_t)(n - j0)) - 1u));
+                const uint32_t valid = (i < n) ? jvalid : 0u;
+                const int64_t dj = i - j0;
+                const uint32_t diag = (dj >= 0 && dj < 32 && i < n) ? (1u << (uint32_t)dj) : 0u;
+                if (valid != 0xFFFFFFFFu || diag) {
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        if (!((valid >> e) & 1u)) out[e] = 0.f;
+                        if ((diag >> e) & 1u) out[e] = diag_val;
+                    }
+                }
+                fix &= valid & ~diag;
+                float *dst = Dblk + ((int64_t)(g >> 1) * PANEL + rp) * KB + (g & 1) * 32;
 #pragma unroll
                 for (int e = 0; e < 32; e += 4)
                     *reinterpret_cast<float4 *>(dst + e) = make_float4(out[e], out[e + 1], out[e + 2], out[e + 3]);
+                // cancellation-prone pairs: d^2 directly in FP64
+                while (fix) {
+                    const int e = __ffs(fix) - 1;
+                    fix &= fix - 1u;
+                    const int64_t j = j0 + e;
+                    const float *zi = (i < nx) ? X + i * p : Y + (i - nx) * p;
+                    const float *zj = (j < nx) ? X + j * p : Y + (j - nx) * p;
+                    double sq = 0.0;
+                    for (int64_t k = 0; k < p; ++k) {
+                        const double df = (double)zi[k] - (double)zj[k];
+                        sq = fma(df, df, sq);
+                    }
+                    ++fixups;
+                    dst[e] = (stat == 0) ? (float)sqrt(sq) : (float)exp(sq * (double)neg_inv_2s2);
+                }
             }
             fence_before();
             mbar_arrive(su32(&bars->acc_empty[acc]));

@@ -41,6 +41,10 @@ constexpr int CHUNK_KB_DEFAULT = 16;  // K-blocks per contraction work unit (102
 constexpr int COL_PAD = 256;     // relabeling columns padded to this multiple
 constexpr int BUILD_KB = 64;     // p is padded to a multiple of this for the tensor-core build
 constexpr int TC_TILE_M = 128;   // relabelings per contraction work unit
+// cap on the relabeling-draw blocks per SM (0: none, one warp per column).  Capping
+// lets the draws share SMs with the tensor-core build, but the draws are
+// latency-bound and run fastest at full occupancy, which measured best overall.
+constexpr int MASK_CTAS_PER_SM = 0;
 
 __host__ __device__ inline int64_t blk_off(int64_t I, int64_t NKB) { return I * NKB - 2 * I * (I - 1); }
 __host__ __device__ inline int64_t blk_index(int64_t I, int64_t kb, int64_t NKB) {
@@ -147,7 +151,7 @@ void launch_blocksums(const Batch &b, cudaStream_t s);
 void launch_rowsum_reduce(const Batch &b, cudaStream_t s);
 void launch_center(const Batch &b, cudaStream_t s);
 void launch_pack(const Batch &b, bool split, cudaStream_t s);   // split: FP16 hi/lo (tensor-core path)
-void launch_masks(const Batch &b, cudaStream_t s);                       // draws or caller masks
+void launch_masks(const Batch &b, int num_sms, cudaStream_t s);          // draws or caller masks
 void launch_contract_simt(const Batch &b, cudaStream_t s);
 void launch_combine(const Batch &b, cudaStream_t s);                     // statistics, counts, outputs
 

@@ -5,6 +5,7 @@
 
 #include <cuda_fp16.h>
 #include <cstdint>
+#include <cstdlib>
 
 namespace ept {
 
@@ -30,22 +31,61 @@ __device__ __forceinline__ uint32_t valid_bits(int w, int n) {
     return (1u << (n - lo)) - 1u;
 }
 
-// One warp writes one relabeling column (words w = 0..nw-1 at col[w * stride]).
-// Philox4x32-10: each round multiplies counter words 0 and 2 by the two Philox
-// multipliers (one wide multiply gives both halves), mixes the high halves with words
-// 1 and 3 and the round key, and the key advances by the two Weyl constants.
-// Draw b of the stream: b = 0 is the identity; b >= 1 is Knuth's selection sampling
-// (Algorithm S) over the n pooled slots, slot t kept iff floor(u_t (n - t) / 2^64)
-// < need, with u_t the 64-bit word (t mod 2) of Philox4x32-10(counter = (t/2, 0,
-// b lo, b hi), key = (seed lo, seed hi)).  The warp draws 64 consecutive slots at
-// once: lane l runs the Philox call of slots base+2l and base+2l+1 and forms their
-// two floor(u (n - t) / 2^64) values; shuffles then place slot base+l on lane l
-// (first word) and slot base+32+l on lane l (second word), so one ballot is one
-// output word.  The sequential dependence through `need` is resolved by a
-// fixed-point iteration over ballots: with every earlier decision known a slot's
-// decision is determined, so iterating "decide from the previous guesses" reaches
-// the unique sequential solution in at most 65 rounds (almost always 1 or 2).
-// comp: store the complement (the y* members).
+// Philox4x32-10 of counter (c0, 0, blo, bhi) under the precomputed round keys: each
+// round multiplies counter words 0 and 2 by the two Philox multipliers (one wide
+// multiply gives both halves) and mixes the high halves with words 1 and 3 and the
+// round key.  Returns the two 64-bit output words (word 0 = (x1:x0), word 1 = (x3:x2)).
+__device__ __forceinline__ void philox_words(uint32_t c0, uint32_t blo, uint32_t bhi, const uint32_t *kx,
+                                             const uint32_t *ky, uint64_t &w0, uint64_t &w1) {
+    uint32_t x0 = c0, x1 = 0u, x2 = blo, x3 = bhi;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
+        const uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ kx[r];
+        const uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ ky[r];
+        x1 = (uint32_t)p1;
+        x3 = (uint32_t)p0;
+        x0 = y0;
+        x2 = y2;
+    }
+    w0 = ((uint64_t)x1 << 32) | x0;
+    w1 = ((uint64_t)x3 << 32) | x2;
+}
+
+// Decisions of one 64-slot window: lane l holds the ranks r0 (slot base+l) and r1
+// (slot base+32+l); returns the two ballots (kept slots) and lowers `need`.  The
+// sequential dependence through `need` is resolved by a fixed-point iteration over
+// ballots: with every earlier decision known a slot's decision is determined, so
+// iterating "decide from the previous guesses" reaches the unique sequential
+// solution in at most 65 rounds (almost always 1 or 2).
+__device__ __forceinline__ void decide_window(int r0, int r1, unsigned lt, int &need, unsigned &m0, unsigned &m1) {
+    m0 = __ballot_sync(0xFFFFFFFFu, r0 < need);
+    m1 = __ballot_sync(0xFFFFFFFFu, r1 < need);
+    for (int it = 0; it < 70; ++it) {
+        const int before0 = __popc(m0 & lt);
+        const int before1 = __popc(m0) + __popc(m1 & lt);
+        const unsigned nm0 = __ballot_sync(0xFFFFFFFFu, r0 < need - before0);
+        const unsigned nm1 = __ballot_sync(0xFFFFFFFFu, r1 < need - before1);
+        const bool same = (nm0 == m0) && (nm1 == m1);
+        m0 = nm0;
+        m1 = nm1;
+        if (same) break;
+    }
+    need -= __popc(m0) + __popc(m1);
+}
+
+// One warp writes one relabeling column (words w = 0..nw-1 at col[w * stride]; nw is
+// a multiple of 8).  Draw b of the stream: b = 0 is the identity; b >= 1 is Knuth's
+// selection sampling (Algorithm S) over the n pooled slots, slot t kept iff
+// floor(u_t (n - t) / 2^64) < need, with u_t the 64-bit word (t mod 2) of
+// Philox4x32-10(counter = (t/2, 0, b lo, b hi), key = (seed lo, seed hi)).  The warp
+// takes 128 consecutive slots per step: lane l runs the Philox calls of slots
+// base+2l, base+2l+1 and base+64+2l, base+64+2l+1 (two independent chains, so that
+// few warps per SM keep the integer pipes busy) and forms their floor(u (n - t) /
+// 2^64) values; shuffles then place slot base+l on lane l (first word) and slot
+// base+32+l on lane l (second word) of each 64-slot window, so one ballot is one
+// output word.  comp: store the complement (the y* members).
 __device__ void draw_column(uint64_t seed, int nx, int n, int64_t b, int nw, bool comp, uint32_t *col,
                             int64_t stride) {
     const int lane = threadIdx.x & 31;
@@ -69,93 +109,106 @@ __device__ void draw_column(uint64_t seed, int nx, int n, int64_t b, int nw, boo
     const int src = lane >> 1;
     const bool odd = lane & 1;
     int need = nx;
-    for (int base = 0; base < nw * 32; base += 64) {
-        const int tp = base + 2 * lane;   // this lane's Philox slots tp, tp + 1
-        uint32_t ra = 0xFFFFFFFFu, rb = 0xFFFFFFFFu;   // "never kept"
-        if (tp < n && need > 0) {
-            uint32_t x0 = (uint32_t)(tp >> 1), x1 = 0u, x2 = blo, x3 = bhi;
-#pragma unroll
-            for (int r = 0; r < 10; ++r) {
-                const uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)x0;
-                const uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)x2;
-                const uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ kx[r];
-                const uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ ky[r];
-                x1 = (uint32_t)p1;
-                x3 = (uint32_t)p0;
-                x0 = y0;
-                x2 = y2;
-            }
-            ra = (uint32_t)mulhi_64x32(((uint64_t)x1 << 32) | x0, (uint32_t)(n - tp));
-            if (tp + 1 < n) rb = (uint32_t)mulhi_64x32(((uint64_t)x3 << 32) | x2, (uint32_t)(n - tp - 1));
+    for (int base = 0; base < nw * 32; base += 128) {
+        // ranks of this lane's four slots ("never kept" past the end or once need is 0)
+        uint32_t ra = 0xFFFFFFFFu, rb = 0xFFFFFFFFu, rc = 0xFFFFFFFFu, rd = 0xFFFFFFFFu;
+        if (need > 0) {
+            const int tp = base + 2 * lane, tq = tp + 64;
+            uint64_t u0, u1, u2, u3;
+            philox_words((uint32_t)(tp >> 1), blo, bhi, kx, ky, u0, u1);
+            philox_words((uint32_t)(tq >> 1), blo, bhi, kx, ky, u2, u3);
+            if (tp < n) ra = (uint32_t)mulhi_64x32(u0, (uint32_t)(n - tp));
+            if (tp + 1 < n) rb = (uint32_t)mulhi_64x32(u1, (uint32_t)(n - tp - 1));
+            if (tq < n) rc = (uint32_t)mulhi_64x32(u2, (uint32_t)(n - tq));
+            if (tq + 1 < n) rd = (uint32_t)mulhi_64x32(u3, (uint32_t)(n - tq - 1));
         }
-        const uint32_t a0 = __shfl_sync(0xFFFFFFFFu, ra, src), b0 = __shfl_sync(0xFFFFFFFFu, rb, src);
-        const uint32_t a1 = __shfl_sync(0xFFFFFFFFu, ra, src + 16), b1 = __shfl_sync(0xFFFFFFFFu, rb, src + 16);
-        const int r0 = (int)min(odd ? b0 : a0, 0x7FFFFFFFu);
-        const int r1 = (int)min(odd ? b1 : a1, 0x7FFFFFFFu);
-        unsigned m0 = __ballot_sync(0xFFFFFFFFu, r0 < need), m1 = __ballot_sync(0xFFFFFFFFu, r1 < need);
-        for (int it = 0; it < 70; ++it) {
-            const int before0 = __popc(m0 & lt);
-            const int before1 = __popc(m0) + __popc(m1 & lt);
-            const unsigned nm0 = __ballot_sync(0xFFFFFFFFu, r0 < need - before0);
-            const unsigned nm1 = __ballot_sync(0xFFFFFFFFu, r1 < need - before1);
-            const bool same = (nm0 == m0) && (nm1 == m1);
-            m0 = nm0;
-            m1 = nm1;
-            if (same) break;
+        unsigned m[4];
+        {
+            const uint32_t a0 = __shfl_sync(0xFFFFFFFFu, ra, src), b0 = __shfl_sync(0xFFFFFFFFu, rb, src);
+            const uint32_t a1 = __shfl_sync(0xFFFFFFFFu, ra, src + 16), b1 = __shfl_sync(0xFFFFFFFFu, rb, src + 16);
+            const int r0 = (int)min(odd ? b0 : a0, 0x7FFFFFFFu);
+            const int r1 = (int)min(odd ? b1 : a1, 0x7FFFFFFFu);
+            decide_window(r0, r1, lt, need, m[0], m[1]);
         }
-        need -= __popc(m0) + __popc(m1);
-        if (lane == 0) {
-            const int w = base >> 5;
-            uint32_t v0 = m0, v1 = m1;
-            if (comp) {
-                v0 = ~v0 & valid_bits(w, n);
-                v1 = ~v1 & valid_bits(w + 1, n);
-            }
-            col[(int64_t)w * stride] = v0;
-            col[(int64_t)(w + 1) * stride] = v1;
+        {
+            const uint32_t a0 = __shfl_sync(0xFFFFFFFFu, rc, src), b0 = __shfl_sync(0xFFFFFFFFu, rd, src);
+            const uint32_t a1 = __shfl_sync(0xFFFFFFFFu, rc, src + 16), b1 = __shfl_sync(0xFFFFFFFFu, rd, src + 16);
+            const int r0 = (int)min(odd ? b0 : a0, 0x7FFFFFFFu);
+            const int r1 = (int)min(odd ? b1 : a1, 0x7FFFFFFFu);
+            decide_window(r0, r1, lt, need, m[2], m[3]);
+        }
+        if (lane < 4) {
+            const int w = (base >> 5) + lane;
+            uint32_t v = lane == 0 ? m[0] : lane == 1 ? m[1] : lane == 2 ? m[2] : m[3];
+            if (comp) v = ~v & valid_bits(w, n);
+            col[(int64_t)w * stride] = v;
         }
     }
 }
 
-// One warp per relabeling column of the batch: column 0 of a test is the identity,
-// columns 1..B its draws 1..B (or the caller's relabelings, validated: exactly nx
-// members among the n rows), padding columns are zero.
-__global__ void __launch_bounds__(256) k_masks(const Batch bt) {
+// Relabeling columns of the batch, one warp per column: column 0 of a test is the
+// identity, columns 1..B its draws 1..B (or the caller's relabelings, validated:
+// exactly nx members among the n rows), padding columns are zero.  Warps stride over
+// the columns, so the grid may be capped (MASK_CTAS_PER_SM).
+__global__ void __launch_bounds__(128) k_masks(const Batch bt) {
     const int lane = threadIdx.x & 31;
-    const int64_t gc = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (gc >= bt.ncols_total) return;
-    const int t = find_test(bt.pre.cols, bt.n_tests, gc);
-    const TestDesc d = bt.desc[t];
-    const int64_t c = gc - bt.pre.cols[t];
-    const int n = (int)d.n, nw = (int)d.nw;
-    uint32_t *col = bt.maskT + d.mask0 + c;
-    if (c >= d.ncols) {
-        for (int w = lane; w < nw; w += 32) col[(int64_t)w * d.Bp] = 0u;
-        return;
-    }
-    if (c >= 1 && d.user_masks) {
-        const uint32_t *row = d.user_masks + (c - 1) * d.nwu;
-        int cnt = 0;
-        bool bad = false;
-        for (int w = lane; w < nw; w += 32) {
-            uint32_t v = (w < d.nwu) ? row[w] : 0u;
-            const uint32_t valid = valid_bits(w, n);
-            if (v & ~valid) bad = true;
-            v &= valid;
-            cnt += __popc(v);
-            col[(int64_t)w * d.Bp] = d.comp ? (~v & valid) : v;
+    const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t gc = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gc < bt.ncols_total;
+         gc += nwarps) {
+        const int t = find_test(bt.pre.cols, bt.n_tests, gc);
+        const TestDesc &d = bt.desc[t];
+        const int64_t c = gc - bt.pre.cols[t];
+        const int n = (int)d.n, nw = (int)d.nw;
+        const int64_t Bp = d.Bp;
+        uint32_t *col = bt.maskT + d.mask0 + c;
+        if (c >= d.ncols) {
+            for (int w = lane; w < nw; w += 32) col[(int64_t)w * Bp] = 0u;
+            continue;
         }
-        for (int off = 16; off; off >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, off);
-        bad = __any_sync(0xFFFFFFFFu, bad);
-        if (lane == 0 && (bad || cnt != d.nx)) atomicAdd(&bt.ctr[t].bad_mask, 1ull);
-        return;
+        if (c >= 1 && d.user_masks) {
+            const int nwu = d.nwu, nx = (int)d.nx;
+            const bool comp = d.comp != 0;
+            const uint32_t *row = d.user_masks + (c - 1) * nwu;
+            int cnt = 0;
+            bool bad = false;
+            for (int w = lane; w < nw; w += 32) {
+                uint32_t v = (w < nwu) ? row[w] : 0u;
+                const uint32_t valid = valid_bits(w, n);
+                if (v & ~valid) bad = true;
+                v &= valid;
+                cnt += __popc(v);
+                col[(int64_t)w * Bp] = comp ? (~v & valid) : v;
+            }
+            for (int off = 16; off; off >>= 1) cnt += __shfl_xor_sync(0xFFFFFFFFu, cnt, off);
+            bad = __any_sync(0xFFFFFFFFu, bad);
+            if (lane == 0 && (bad || cnt != nx)) atomicAdd(&bt.ctr[t].bad_mask, 1ull);
+            continue;
+        }
+        draw_column(d.seed, (int)d.nx, n, c, nw, d.comp != 0, col, Bp);
     }
-    draw_column(d.seed, (int)d.nx, n, c, nw, d.comp != 0, col, d.Bp);
 }
 
-void launch_masks(const Batch &b, cudaStream_t s) {
+// Blocks per SM of the draw kernel: MASK_CTAS_PER_SM, or the environment's
+// EPT_MASK_BLOCKS_PER_SM (0: one warp per column, no cap).
+static int mask_blocks_per_sm() {
+    static const int v = [] {
+        const char *e = getenv("EPT_MASK_BLOCKS_PER_SM");
+        if (!e || !*e) return MASK_CTAS_PER_SM;
+        const int k = atoi(e);
+        return k < 0 ? MASK_CTAS_PER_SM : (k > 64 ? 64 : k);
+    }();
+    return v;
+}
+
+void launch_masks(const Batch &b, int num_sms, cudaStream_t s) {
     if (b.ncols_total <= 0) return;
-    k_masks<<<(unsigned)((b.ncols_total + 7) / 8), 256, 0, s>>>(b);
+    int64_t blocks = (b.ncols_total + 3) / 4;
+    const int per_sm = mask_blocks_per_sm();
+    if (per_sm > 0) {
+        const int64_t cap = (int64_t)(num_sms > 0 ? num_sms : 1) * per_sm;
+        if (blocks > cap) blocks = cap;
+    }
+    k_masks<<<(unsigned)blocks, 128, 0, s>>>(b);
 }
 
 // the stream itself, for export: column c = draw b0 + c
