@@ -109,7 +109,10 @@ size_t ept_estimate_bytes(int64_t nx, int64_t ny, int64_t p, int64_t B, int prec
    permutation stream of `seed` (ept_perm_masks) is relabeling b.
    perm_stats: B doubles (may be NULL), perm_stats[b-1] = statistic of draw b.
    out: host struct, required.  Errors: EPT_EINVAL for nx < 1, ny < 1, p < 1, B < 0,
-   sigma <= 0 with MMD, non-finite data; EPT_ENOMEM over budget. */
+   sigma <= 0 with MMD, non-finite data; EPT_ENOMEM over budget.
+   A repeated call with the same shapes replays the CUDA graph captured by the
+   first (EPT_OPT_GRAPHS); then only out->ms_total is timed (the per-phase times
+   are filled in when graphs are off). */
 ept_status ept_test(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, int64_t ny,
                     int64_t p, int on_device, int stat, double sigma, int64_t B, uint64_t seed,
                     int prec, double *perm_stats, ept_result *out, void *stream);

@@ -126,7 +126,7 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
         d.nwu = (int)((d.n + 31) / 32);
         d.ncols = s.B + 1;
         d.Bp = (d.ncols + COL_PAD - 1) / COL_PAD * COL_PAD;
-        d.MT = d.Bp / TC_TILE_M;
+        d.MT = d.Bp / TC_TILE_N;
         d.p_pad = (d.p + BUILD_KB - 1) / BUILD_KB * BUILD_KB;
         d.kblocks = (int)(d.p_pad / BUILD_KB);
         d.comp = d.ny < d.nx;
@@ -159,7 +159,8 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
                     for (int h = 0; h < 2; ++h) P.tiles.push_back(Tile{t, (int)I, (int)J, h});
         }
         d.nchunks = (int64_t)P.chunks.size() - d.chunk0;
-        d.nparts = tc ? d.nchunks : 2 * d.nchunks;
+        d.nparts = 2 * d.nchunks;   // (chunk, row half)
+        d.scaled = tc ? 1 : 0;
         d.part0 = P.npart;
         P.nrows += d.n_pad;
         P.nblk += d.nblk;
@@ -172,7 +173,7 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
         push_pre(P.pre_rows, d.n_pad);
         push_pre(P.pre_panels, d.NP);
         push_pre(P.pre_cols, d.Bp);
-        push_pre(P.pre_units, d.nchunks * d.MT);
+        push_pre(P.pre_units, tc_units(d));
         push_pre(P.pre_simt, d.nchunks * 2 * (d.Bp / 64));
         P.in_off.push_back(in_bytes);
         if (host_in) {
@@ -1085,7 +1086,7 @@ ept_status ept_test(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, in
     std::lock_guard<std::mutex> lock(ctx->mu);
     DeviceGuard dg(ctx->device);
     return run_tuned(ctx, one_test(X, nx, Y, ny, p, stat, sigma, B, seed, nullptr, perm_stats), prec, on_device != 0,
-                     false, out, stream);
+                     true, out, stream);
 }
 
 ept_status ept_test_masks(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p,

@@ -48,7 +48,7 @@ constexpr int NUM_THREADS = 192;
 // stages | barriers (1 KB) | per-epilogue-warp column norms and scales (4 x 2 KB) | alignment slack
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 4 * PANEL * 8 + 1024;
 // kind::f16 instruction descriptor with A = B = FP16 (format 0), D = FP32, K-major
-constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+constexpr uint32_t IDESC = idesc_f16_f32(BM, BN);
 
 constexpr unsigned long long ERR_WAIT_TMA = 0x201, ERR_WAIT_MMA = 0x202, ERR_WAIT_EPI = 0x203, ERR_DRAIN = 0x205;
 
@@ -230,9 +230,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     const uint64_t dbh = desc_sw128(sa + 2 * A_BYTES), dbl = desc_sw128(sa + 2 * A_BYTES + B_BYTES);
 #pragma unroll
                     for (int k = 0; k < BK / 16; ++k) {
-                        mma_bf16(d_tmem, dah + 2 * k, dbh + 2 * k, IDESC, (kk == 0 && k == 0) ? 0u : 1u);
-                        mma_bf16(d_tmem, dah + 2 * k, dbl + 2 * k, IDESC, 1u);
-                        mma_bf16(d_tmem, dal + 2 * k, dbh + 2 * k, IDESC, 1u);
+                        mma_f16(d_tmem, dah + 2 * k, dbh + 2 * k, IDESC, (kk == 0 && k == 0) ? 0u : 1u);
+                        mma_f16(d_tmem, dah + 2 * k, dbl + 2 * k, IDESC, 1u);
+                        mma_f16(d_tmem, dal + 2 * k, dbh + 2 * k, IDESC, 1u);
                     }
                     mma_commit(su32(&bars->empty[stage]));
                     if (++stage == STAGES) {

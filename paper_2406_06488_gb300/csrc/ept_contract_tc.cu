@@ -3,23 +3,29 @@
 // What it computes (Algorithm 1, permutation loop, rewritten as quadratic forms):
 // for relabeling column b with indicator s_b (s_b[t] = 1 iff pooled row t goes to
 // x*), the statistic needs Q_b = s_b' C s_b, where C is the packed, centred,
-// upper-scaled pooled matrix (see ept_kernels.cu, packing).  Work unit (q, m):
-// chunk q = (panel I, K-blocks [kb0, kb1)), relabeling tile m (128 columns):
-//     U[b, i]        = sum_{j in chunk} s_b[j] * C[i, j]        (tensor cores)
-//     partial[q][b]  = sum_{i in panel I} s_b[i] * U[b, i]      (epilogue)
-// and Q_b = sum_q partial[q][b] (FP64, ept_kernels.cu).
+// upper-scaled pooled matrix (see ept_kernels.cu, packing).  Work unit (q, m, h):
+// chunk q = (panel I, K-blocks [kb0, kb1)), relabeling tile m (256 columns), half h
+// of the panel's rows (128 rows):
+//     U[i, b]              = sum_{j in chunk} C[i, j] s_b[j]     (tensor cores)
+//     partial[2q + h][b]   = sum_{i in half h} s_b[i] U[i, b]    (epilogue)
+// and Q_b = sum over parts (FP64, ept_kernels.cu).
 //
-// Mapping onto tcgen05 (kind::f16, cta_group::1):
-//   A (M = 128 relabelings x K = 64 pooled columns): 0/1 values, exact in BF16,
-//     expanded from the bit masks by four producer warps straight into the
-//     128-byte-swizzled K-major shared-memory layout;
-//   B (N = 256 panel rows x K = 64): the packed C block, split C = hi + lo in BF16,
-//     loaded by TMA (two 32 KB boxes per K-block);
-//   D (128 x 256 FP32) in tensor memory: D += A * B_hi, then D += A * B_lo, so the
-//     hi and lo products accumulate in one FP32 accumulator.
-//   Two accumulators (512 TMEM columns) let the epilogue of one unit overlap the
-//   main loop of the next.  The epilogue lane owns one relabeling: it reads its
-//   256 columns, keeps those whose panel row is in x* for that relabeling, and sums.
+// Mapping onto tcgen05 (kind::f16, cta_group::1), M = 128 rows of C, N = 256
+// relabelings, K = 64 pooled columns per stage:
+//   A (128 x 64): the packed C half-block, the test's C scaled by a power of two and
+//     split hi + lo in FP16, loaded by TMA (two 16 KB boxes, 128-byte swizzle);
+//   B (256 x 64): 0/1 relabeling values, exact in FP16, expanded from the bit masks
+//     by four producer warps straight into the 128-byte-swizzled K-major layout;
+//   D (128 x 256 FP32) in tensor memory: D += A_hi * B, then D += A_lo * B.
+//   With the relabelings as N, one stage moves 32 KB through TMA for 2 x 128 x 256 x
+//   64 multiply-adds (half of what the relabelings-as-M mapping needs), and three
+//   64 KB stages fit in shared memory.  Two accumulators (512 TMEM columns) let the
+//   epilogue of one unit overlap the main loop of the next.
+//   Epilogue: TMEM lane = row i; a warp reads 32 relabelings at a time, takes the
+//   mask bits of its 32 rows for them with a 32 x 32 bit transpose (ballots), masks
+//   its values, and sums over its 32 rows with a butterfly transpose-reduce (lane e
+//   ends with relabeling e's sum).  The four warps' sums meet in shared memory and
+//   are added in a fixed order.
 //
 // Roles (320 threads): warp 0 = TMA producer, warp 1 = MMA issuer (and TMEM
 // owner), warps 2-5 = epilogue, warps 6-9 = relabeling-tile producers.  Every
@@ -39,38 +45,40 @@ namespace {
 
 using namespace tc;
 
-constexpr int TC_M = 128;
-constexpr int TC_N = PANEL;                       // 256
-constexpr int STAGES = 2;
-constexpr int A_BYTES = TC_M * KB * 2;            // 16 KB
+constexpr int TC_M = 128;                         // rows of C per unit (half a panel)
+constexpr int TC_N = TC_TILE_N;                   // relabelings per unit (256)
+constexpr int STAGES = 3;
+constexpr int A_BYTES = TC_M * KB * 2;            // 16 KB (hi or lo)
 constexpr int B_BYTES = TC_N * KB * 2;            // 32 KB
-constexpr int STAGE_BYTES = A_BYTES + 2 * B_BYTES;
+constexpr int STAGE_BYTES = 2 * A_BYTES + B_BYTES;   // A hi | A lo | B
+constexpr int RED_BYTES = 2 * 4 * TC_N * 4;       // epilogue sums: 2 buffers x 4 warps x 256 floats
 constexpr int NUM_THREADS = 320;
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*barriers*/ + 1024 /*alignment*/;
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*barriers*/ + RED_BYTES + 1024 /*alignment*/;
 
 // error codes recorded in Counters::err_code
 constexpr unsigned long long ERR_WAIT_TMA = 0x101, ERR_WAIT_MMA = 0x102, ERR_WAIT_EPI = 0x103,
                              ERR_WAIT_MASK = 0x104, ERR_DRAIN = 0x105;
 
-// kind::f16 instruction descriptor with A = B = FP16 (format 0), D = FP32, K-major
-constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+constexpr uint32_t IDESC = idesc_f16_f32(TC_M, TC_N);
 
 struct Bars {
-    unsigned long long a_full[STAGES];   // 128 producer-thread arrivals
-    unsigned long long b_full[STAGES];   // 1 arrival + TMA transaction bytes
+    unsigned long long b_full[STAGES];   // 128 producer-thread arrivals (relabeling tile)
+    unsigned long long a_full[STAGES];   // 1 arrival + TMA transaction bytes (C half-block)
     unsigned long long empty[STAGES];    // 1 arrival (tcgen05.commit)
     unsigned long long acc_full[2];      // 1 arrival (tcgen05.commit)
     unsigned long long acc_empty[2];     // 128 epilogue-thread arrivals
+    unsigned long long red;              // 128 epilogue-thread arrivals per unit
     unsigned long long drain;            // 1 arrival (final tcgen05.commit)
     uint32_t tmem_base;
     int abort_flag;
 };
 
-// the test fields, chunk and relabeling tile of global work unit u, read once into
-// registers (the asm statements' memory clobbers would otherwise force reloads)
+// the test fields, chunk, relabeling tile and row half of global work unit u, read
+// once into registers (the asm statements' memory clobbers would otherwise force
+// reloads).  Units of a test are ordered (q, m, h).
 struct Unit {
     Chunk ch;
-    int64_t q, m, Bp, mask0, part0, blk0, NKB;
+    int64_t q, m, h, Bp, mask0, part0, blk0, NKB;
 };
 
 __device__ __forceinline__ Unit decode_unit(const Batch &bt, int64_t u) {
@@ -79,8 +87,9 @@ __device__ __forceinline__ Unit decode_unit(const Batch &bt, int64_t u) {
     Unit x;
     const int64_t lu = u - bt.pre.units[t];
     const int64_t MT = d->MT;
-    x.q = lu / MT;
-    x.m = lu % MT;
+    x.h = lu & 1;
+    x.q = (lu >> 1) / MT;
+    x.m = (lu >> 1) % MT;
     x.Bp = d->Bp;
     x.mask0 = d->mask0;
     x.part0 = d->part0;
@@ -98,19 +107,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     Bars *bars = reinterpret_cast<Bars *>(smem + STAGES * STAGE_BYTES);
+    float *red = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + 1024);
     volatile int *abort_flag = &bars->abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(su32(&bars->a_full[s]), 128);
-            mbar_init(su32(&bars->b_full[s]), 1);
+            mbar_init(su32(&bars->b_full[s]), 128);
+            mbar_init(su32(&bars->a_full[s]), 1);
             mbar_init(su32(&bars->empty[s]), 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(su32(&bars->acc_full[a]), 1);
             mbar_init(su32(&bars->acc_empty[a]), 128);
         }
+        mbar_init(su32(&bars->red), 128);
         mbar_init(su32(&bars->drain), 1);
         bars->abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -127,7 +138,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const uint32_t tmem_base = bars->tmem_base;
 
     if (warp == 0) {
-        // ---------------- TMA producer: packed C hi / lo blocks ----------------
+        // ---------------- TMA producer: packed C hi / lo half-blocks ----------------
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
@@ -137,17 +148,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
                 const Unit x = decode_unit(bt, u);
                 const Chunk ch = x.ch;
+                const int row = (int)x.h * TC_M;
                 for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
                     if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_TMA)) {
                         ok = false;
                         break;
                     }
-                    const uint32_t bfull = su32(&bars->b_full[stage]);
-                    mbar_arrive_tx(bfull, 2 * B_BYTES);
+                    const uint32_t afull = su32(&bars->a_full[stage]);
+                    mbar_arrive_tx(afull, 2 * A_BYTES);
                     const int blk = (int)(x.blk0 + blk_index(ch.I, kb, x.NKB));
                     uint8_t *st = smem + stage * STAGE_BYTES;
-                    tma_load_3d(su32(st + A_BYTES), &tmap_hi, 0, 0, blk, bfull);
-                    tma_load_3d(su32(st + A_BYTES + B_BYTES), &tmap_lo, 0, 0, blk, bfull);
+                    tma_load_3d(su32(st), &tmap_hi, 0, row, blk, afull);
+                    tma_load_3d(su32(st + A_BYTES), &tmap_lo, 0, row, blk, afull);
                     armed[stage] = (int)phase;
                     if (++stage == STAGES) {
                         stage = 0;
@@ -157,11 +169,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
             if (!ok) {
                 // drain: the copies armed last on each stage complete that phase of
-                // b_full; wait for it (bounded) before the CTA may exit
+                // a_full; wait for it (bounded) before the CTA may exit
                 for (int s2 = 0; s2 < STAGES; ++s2) {
                     if (armed[s2] < 0) continue;
                     const unsigned long long t0 = gtimer();
-                    while (!mbar_try(su32(&bars->b_full[s2]), (uint32_t)armed[s2])) {
+                    while (!mbar_try(su32(&bars->a_full[s2]), (uint32_t)armed[s2])) {
                         if (gtimer() - t0 > WAIT_NS) {
                             atomicCAS(&ctr->err_code, 0ull, ERR_DRAIN);
                             break;
@@ -193,14 +205,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     }
                     fence_after();
                     const uint32_t sa = su32(smem + stage * STAGE_BYTES);
-                    const uint64_t da = desc_sw128(sa);
-                    const uint64_t dhi = desc_sw128(sa + A_BYTES);
-                    const uint64_t dlo = desc_sw128(sa + A_BYTES + B_BYTES);
+                    const uint64_t dhi = desc_sw128(sa);
+                    const uint64_t dlo = desc_sw128(sa + A_BYTES);
+                    const uint64_t db = desc_sw128(sa + 2 * A_BYTES);
 #pragma unroll
                     for (int k = 0; k < KB / 16; ++k)
-                        mma_bf16(d_tmem, da + 2 * k, dhi + 2 * k, IDESC, (first && k == 0) ? 0u : 1u);
+                        mma_f16(d_tmem, dhi + 2 * k, db + 2 * k, IDESC, (first && k == 0) ? 0u : 1u);
 #pragma unroll
-                    for (int k = 0; k < KB / 16; ++k) mma_bf16(d_tmem, da + 2 * k, dlo + 2 * k, IDESC, 1u);
+                    for (int k = 0; k < KB / 16; ++k) mma_f16(d_tmem, dlo + 2 * k, db + 2 * k, IDESC, 1u);
                     mma_commit(su32(&bars->empty[stage]));
                     first = false;
                     if (++stage == STAGES) {
@@ -227,39 +239,63 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
     } else if (warp < 6) {
         // ---------------- epilogue ----------------
-        const int quarter = warp & 3;           // TMEM lanes this warp may access
-        const int row = quarter * 32 + lane;    // relabeling within the tile
+        const int quarter = warp & 3;           // TMEM lanes (rows) this warp may access
+        const int et = threadIdx.x - 64;        // 0..127
         int acc = 0;
-        uint32_t acc_phase = 0;
+        uint32_t acc_phase = 0, red_phase = 0;
+        int rbuf = 0;
         for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
             const Unit x = decode_unit(bt, u);
             const Chunk ch = x.ch;
             const int64_t Bp = x.Bp;
-            const uint32_t *maskT = bt.maskT + x.mask0;
-            const int64_t b = x.m * TC_M + row;
-            uint32_t bits[8];
+            // mask word of this warp's 32 rows, for the unit's 256 relabelings
+            const uint32_t *wrow = bt.maskT + x.mask0 + ((int64_t)ch.I * 8 + x.h * 4 + quarter) * Bp + x.m * TC_N;
+            uint32_t words[8];
 #pragma unroll
-            for (int g = 0; g < 8; ++g) bits[g] = maskT[((int64_t)ch.I * 8 + g) * Bp + b];
+            for (int g = 0; g < 8; ++g) words[g] = wrow[g * 32 + lane];
             if (!mbar_wait(su32(&bars->acc_full[acc]), acc_phase, abort_flag, ctr, ERR_WAIT_EPI)) break;
             fence_after();
-            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
             const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * TC_N);
+            float *myred = red + (rbuf * 4 + quarter) * TC_N;
 #pragma unroll 1
             for (int g = 0; g < 8; ++g) {
                 uint32_t v[32];
                 tmem_ld32(tbase + (uint32_t)(g * 32), v);
-                const uint32_t w = bits[g];
+                // bit e of `mine` = s_{b_e}[row of this lane], b_e = relabeling 32 g + e
+                uint32_t mine = 0;
 #pragma unroll
-                for (int e = 0; e < 32; e += 4) {
-                    s0 += ((w >> e) & 1u) ? __uint_as_float(v[e]) : 0.f;
-                    s1 += ((w >> (e + 1)) & 1u) ? __uint_as_float(v[e + 1]) : 0.f;
-                    s2 += ((w >> (e + 2)) & 1u) ? __uint_as_float(v[e + 2]) : 0.f;
-                    s3 += ((w >> (e + 3)) & 1u) ? __uint_as_float(v[e + 3]) : 0.f;
+                for (int l = 0; l < 32; ++l) {
+                    const uint32_t col = __ballot_sync(0xFFFFFFFFu, (words[g] >> l) & 1u);
+                    mine = (lane == l) ? col : mine;
                 }
+                float xv[32];
+#pragma unroll
+                for (int e = 0; e < 32; ++e) xv[e] = ((mine >> e) & 1u) ? __uint_as_float(v[e]) : 0.f;
+                // butterfly transpose-reduce: lane e ends with the sum over the warp's rows of column e
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) {
+                    const bool upper = (lane & off) != 0;
+#pragma unroll
+                    for (int k = 0; k < off; ++k) {
+                        const float send = upper ? xv[k] : xv[k + off];
+                        const float keep = upper ? xv[k + off] : xv[k];
+                        xv[k] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, off);
+                    }
+                }
+                myred[g * 32 + lane] = xv[0];
             }
             fence_before();
             mbar_arrive(su32(&bars->acc_empty[acc]));
-            bt.partial[x.part0 + x.q * Bp + b] = (s0 + s1) + (s2 + s3);
+            // the four warps' sums, added in a fixed order
+            mbar_arrive(su32(&bars->red));
+            if (!mbar_wait(su32(&bars->red), red_phase, abort_flag, ctr, ERR_WAIT_EPI)) break;
+            const float *rb = red + rbuf * 4 * TC_N;
+            float *out = bt.partial + x.part0 + (2 * x.q + x.h) * Bp + x.m * TC_N;
+#pragma unroll
+            for (int c = et; c < TC_N; c += 128)
+                out[c] = (rb[c] + rb[TC_N + c]) + (rb[2 * TC_N + c] + rb[3 * TC_N + c]);
+            red_phase ^= 1u;
+            rbuf ^= 1;
             if (++acc == 2) {
                 acc = 0;
                 acc_phase ^= 1u;
@@ -267,7 +303,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
     } else {
         // ---------------- relabeling-tile producers ----------------
-        const int r = threadIdx.x - 192;   // 0..127: row of the A tile
+        // The mask words of a stage are loaded two stages ahead, so that their L2
+        // latency overlaps the expansion of the stages before.
+        const int r = threadIdx.x - 192;   // 0..127: rows r and r + 128 of the B tile
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
@@ -275,27 +313,45 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const Unit x = decode_unit(bt, u);
             const Chunk ch = x.ch;
             const int64_t Bp = x.Bp;
-            const uint32_t *maskT = bt.maskT + x.mask0;
-            const int64_t b = x.m * TC_M + r;
+            const uint32_t *maskT = bt.maskT + x.mask0 + x.m * TC_N + r;
+            // words 2 kb and 2 kb + 1 of relabelings r and r + 128
+            auto load4 = [&](int kb, uint4 &w) {
+                const uint32_t *p0 = maskT + (int64_t)(2 * kb) * Bp;
+                w.x = p0[0];
+                w.y = p0[Bp];
+                w.z = p0[128];
+                w.w = p0[Bp + 128];
+            };
+            uint4 cur = make_uint4(0, 0, 0, 0), nxt = make_uint4(0, 0, 0, 0);
+            load4(ch.kb0, cur);
+            if (ch.kb0 + 1 < ch.kb1) load4(ch.kb0 + 1, nxt);
             for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
-                const uint32_t w0 = maskT[(int64_t)(2 * kb) * Bp + b];
-                const uint32_t w1 = maskT[(int64_t)(2 * kb + 1) * Bp + b];
+                uint4 nn = make_uint4(0, 0, 0, 0);
+                if (kb + 2 < ch.kb1) load4(kb + 2, nn);
                 if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_MASK)) {
                     ok = false;
                     break;
                 }
-                uint8_t *arow = smem + stage * STAGE_BYTES + r * 128;
+                uint8_t *tile = smem + stage * STAGE_BYTES + 2 * A_BYTES;
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const uint32_t byte = ((c < 4 ? w0 : w1) >> (8 * (c & 3))) & 0xFFu;
-                    const uint4 v = expand8(byte);
-                    const uint32_t dst = su32(arow + ((c ^ (r & 7)) << 4));
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(v.x), "r"(v.y),
-                                 "r"(v.z), "r"(v.w)
-                                 : "memory");
+                for (int half = 0; half < 2; ++half) {
+                    const int rr = r + half * 128;
+                    const uint32_t wa = half ? cur.z : cur.x, wb = half ? cur.w : cur.y;
+                    uint8_t *brow = tile + rr * 128;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const uint32_t byte = ((c < 4 ? wa : wb) >> (8 * (c & 3))) & 0xFFu;
+                        const uint4 v = expand8(byte);
+                        const uint32_t dst = su32(brow + ((c ^ (rr & 7)) << 4));
+                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(v.x), "r"(v.y),
+                                     "r"(v.z), "r"(v.w)
+                                     : "memory");
+                    }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(su32(&bars->a_full[stage]));
+                mbar_arrive(su32(&bars->b_full[stage]));
+                cur = nxt;
+                nxt = nn;
                 if (++stage == STAGES) {
                     stage = 0;
                     phase ^= 1u;
@@ -380,15 +436,14 @@ bool encode_block_tmaps(void *tmap_hi, void *tmap_lo, const uint16_t *Chi, const
     if (!enc) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)KB, (cuuint64_t)PANEL, (cuuint64_t)nblk};
     const cuuint64_t strides[2] = {(cuuint64_t)KB * 2, (cuuint64_t)KB * 2 * PANEL};
-    const cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)PANEL, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)TC_M, 1};   // 128 rows of a block per copy
     const cuuint32_t estr[3] = {1, 1, 1};
     void *ptrs[2] = {(void *)Chi, (void *)Clo};
     void *outs[2] = {tmap_hi, tmap_lo};
     for (int k = 0; k < 2; ++k) {
-        CUresult r = enc((CUtensorMap *)outs[k], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, ptrs[k], dims,
-                                            strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                                            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        CUresult r = enc((CUtensorMap *)outs[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, ptrs[k], dims, strides, box,
+                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (r != CUDA_SUCCESS) {
             snprintf(err, errlen, "cuTensorMapEncodeTiled failed (%d)", (int)r);
             return false;

@@ -40,7 +40,7 @@ constexpr int KB_PER_PANEL = PANEL / KB;
 constexpr int CHUNK_KB_DEFAULT = 16;  // K-blocks per contraction work unit (1024 columns)
 constexpr int COL_PAD = 256;     // relabeling columns padded to this multiple
 constexpr int BUILD_KB = 64;     // p is padded to a multiple of this for the tensor-core build
-constexpr int TC_TILE_M = 128;   // relabelings per contraction work unit
+constexpr int TC_TILE_N = 256;   // relabelings per contraction work unit (the MMA's N)
 // cap on the relabeling-draw blocks per SM (0: none, one warp per column).  Capping
 // lets the draws share SMs with the tensor-core build, but the draws are
 // latency-bound and run fastest at full occupancy, which measured best overall.
@@ -103,6 +103,7 @@ struct TestDesc {
     int64_t col0;     // statistics (ncols)
     uint64_t seed;
     int32_t stat, comp, kblocks, nwu;
+    int32_t scaled, pad_;            // scaled: the partials carry the packing scale (tensor-core path)
     float neg_inv_2s2, tau;
     double cT, inv_o2, sign, kappa, inv_n, inv_2n2;
 };
@@ -112,7 +113,7 @@ struct BatchPrefix {
     const int64_t *rows;    // n_pad
     const int64_t *panels;  // NP
     const int64_t *cols;    // Bp
-    const int64_t *units;   // nchunks * MT (tensor-core contraction work units)
+    const int64_t *units;   // tc_units (tensor-core contraction work units)
     const int64_t *simt;    // nchunks * 2 * (Bp / 64) (plain contraction work items)
 };
 
@@ -133,6 +134,9 @@ struct Batch {
     uint32_t *maskT;
     Counters *ctr;
 };
+
+// tensor-core contraction work units of a test: chunk x relabeling tile x row half
+__host__ __device__ inline int64_t tc_units(const TestDesc &d) { return d.nchunks * d.MT * 2; }
 
 __device__ __forceinline__ int find_test(const int64_t *pre, int nt, int64_t g) {
     int lo = 0, hi = nt - 1;

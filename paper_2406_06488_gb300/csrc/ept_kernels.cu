@@ -754,7 +754,7 @@ __global__ void __launch_bounds__(256) k_combine_stats(const Batch bt) {
     acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
     acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
     // the tensor-core path accumulates c Q (packed operand scaled by c); 1/c is exact
-    const double inv_c = (d.nparts == d.nchunks) ? 1.0 / (double)packed_scale(bt.ctr[t]) : 1.0;
+    const double inv_c = d.scaled ? 1.0 / (double)packed_scale(bt.ctr[t]) : 1.0;
     if (c < d.ncols && q == 0) bt.stats[d.col0 + c] = d.sign * (d.cT * (acc * inv_c) + bSt * d.inv_o2);
 }
 

@@ -82,7 +82,7 @@ StaticPlan static_plan(const TestDesc &d) {
     P.Upart = take((size_t)d.NP * 8);
     P.Stpart = take((size_t)d.NP * 8);
     P.maskT = take((size_t)d.nw * d.Bp * 4);
-    P.partial = take((size_t)d.nchunks * d.Bp * 4);
+    P.partial = take((size_t)d.nparts * d.Bp * 4);
     P.stats = take((size_t)d.ncols * 8);
     P.observed = take(8);
     P.ctr = take(sizeof(Counters));
@@ -101,7 +101,7 @@ __global__ void k_static_tables(const TestDesc d, TestDesc *desc, int64_t *pre, 
     }
     if (b == 0) {
         *desc = d;
-        const int64_t tot[5] = {d.n_pad, d.NP, d.Bp, d.nchunks * d.MT, d.nchunks * 2 * (d.Bp / 64)};
+        const int64_t tot[5] = {d.n_pad, d.NP, d.Bp, tc_units(d), d.nchunks * 2 * (d.Bp / 64)};
         for (int k = 0; k < 5; ++k) {
             pre[2 * k] = 0;
             pre[2 * k + 1] = tot[k];
@@ -187,9 +187,10 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     d.nwu = (int)((d.n + 31) / 32);
     d.ncols = B + 1;
     d.Bp = (d.ncols + COL_PAD - 1) / COL_PAD * COL_PAD;
-    d.MT = d.Bp / TC_TILE_M;
+    d.MT = d.Bp / TC_TILE_N;
     for (int64_t I = 0; I < d.NP; ++I) d.nchunks += (d.NKB - KB_PER_PANEL * I + CHUNK_KB_DEFAULT - 1) / CHUNK_KB_DEFAULT;
-    d.nparts = d.nchunks;
+    d.nparts = 2 * d.nchunks;
+    d.scaled = 1;
     d.p_pad = (p + BUILD_KB - 1) / BUILD_KB * BUILD_KB;
     d.kblocks = (int)(d.p_pad / BUILD_KB);
     d.comp = ny < nx;
@@ -238,7 +239,7 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     b.nrows_total = d.n_pad;
     b.npan_total = d.NP;
     b.ncols_total = d.Bp;
-    b.nunits_total = d.nchunks * d.MT;
+    b.nunits_total = tc_units(d);
     b.norms = (float *)(A + P.norms);
     b.iscale = (float *)(A + P.iscale);
     b.u = (float *)(A + P.u);

@@ -1,6 +1,7 @@
 // ept_tc_common.cuh -- helpers shared by libept's tcgen05 kernels: mbarriers with
 // bounded waits, TMA tile loads, tensor-memory fences and loads, shared-memory matrix
-// descriptors and the BF16 MMA (kind::f16, cta_group::1, FP32 accumulation).
+// descriptors and the 16-bit MMA (kind::f16 with FP16 operands, cta_group::1, FP32
+// accumulation).
 #pragma once
 #include <cuda.h>
 #include <cstdint>
@@ -98,15 +99,29 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     return d;
 }
 
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9
-// and 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t idesc_bf16_f32(int M, int N) {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Shared-memory matrix descriptor of a K-major tile in the 64-byte swizzle layout:
+// rows of 64 bytes (32 16-bit values), 8-row atoms of 512 bytes (stride byte offset
+// 512), the 16-byte chunks of row r XOR-swizzled by (r / 2) mod 4 (layout type 4).
+// Stepping K by 16 elements inside the row advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = B = FP16 (format 0
+// in bits 7-9 and 10-12), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t idesc_f16_f32(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 // D (tensor memory) += A (smem) * B (smem)^T, or D = A * B^T when accumulate == 0;
 // issued by one thread.
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
                                          uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
