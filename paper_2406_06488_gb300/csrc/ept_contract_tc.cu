@@ -27,8 +27,11 @@
 //   ends with relabeling e's sum).  The four warps' sums meet in shared memory and
 //   are added in a fixed order.
 //
-// Roles (320 threads): warp 0 = TMA producer, warp 1 = MMA issuer (and TMEM
-// owner), warps 2-5 = epilogue, warps 6-9 = relabeling-tile producers.  Every
+// Roles (576 threads): warp 0 = TMA producer, warp 1 = MMA issuer (and TMEM
+// owner), warps 2-9 = epilogue (two warps per TMEM lane quarter, each taking half
+// of the relabelings), warps 10-17 = relabeling-tile producers (one B row each).
+// Two epilogue and two producer warps per SM sub-partition hide each other's
+// shared-memory and L2 latencies.  Every
 // wait on an mbarrier is bounded (2 s); on expiry the kernel records an error
 // code, raises a CTA-wide abort flag, drains its own copies and MMAs (bounded
 // again), frees its tensor memory and returns.
@@ -52,7 +55,9 @@ constexpr int A_BYTES = TC_M * KB * 2;            // 16 KB (hi or lo)
 constexpr int B_BYTES = TC_N * KB * 2;            // 32 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + B_BYTES;   // A hi | A lo | B
 constexpr int RED_BYTES = 2 * 4 * TC_N * 4;       // epilogue sums: 2 buffers x 4 warps x 256 floats
-constexpr int NUM_THREADS = 320;
+constexpr int NUM_THREADS = 576;
+constexpr int EPI_THREADS = 256;                  // warps 2-9
+constexpr int PROD_THREADS = 256;                 // warps 10-17
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*barriers*/ + RED_BYTES + 1024 /*alignment*/;
 
 // error codes recorded in Counters::err_code
@@ -61,17 +66,19 @@ constexpr unsigned long long ERR_WAIT_TMA = 0x101, ERR_WAIT_MMA = 0x102, ERR_WAI
 
 constexpr uint32_t IDESC = idesc_f16_f32(TC_M, TC_N);
 
+// the barrier region (1 KB): Bars at its start, the 128-byte nibble table at byte 512
 struct Bars {
-    unsigned long long b_full[STAGES];   // 128 producer-thread arrivals (relabeling tile)
+    unsigned long long b_full[STAGES];   // 256 producer-thread arrivals (relabeling tile)
     unsigned long long a_full[STAGES];   // 1 arrival + TMA transaction bytes (C half-block)
     unsigned long long empty[STAGES];    // 1 arrival (tcgen05.commit)
     unsigned long long acc_full[2];      // 1 arrival (tcgen05.commit)
-    unsigned long long acc_empty[2];     // 128 epilogue-thread arrivals
-    unsigned long long red;              // 128 epilogue-thread arrivals per unit
+    unsigned long long acc_empty[2];     // 256 epilogue-thread arrivals
+    unsigned long long red;              // 256 epilogue-thread arrivals per unit
     unsigned long long drain;            // 1 arrival (final tcgen05.commit)
     uint32_t tmem_base;
     int abort_flag;
 };
+static_assert(sizeof(Bars) <= 512, "barriers overlap the nibble table");
 
 // the test fields, chunk, relabeling tile and row half of global work unit u, read
 // once into registers (the asm statements' memory clobbers would otherwise force
@@ -111,17 +118,24 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     volatile int *abort_flag = &bars->abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
+    // nibble -> four FP16 values (1.0 where the bit is set), for the relabeling producers
+    uint2 *lut = reinterpret_cast<uint2 *>(smem + STAGES * STAGE_BYTES + 512);
+    if (threadIdx.x < 16) {
+        const uint32_t n = threadIdx.x;
+        lut[n] = make_uint2((n & 1u) * 0x3C00u + (n & 2u) * 0x1E000000u,
+                            ((n >> 2) & 1u) * 0x3C00u + ((n >> 2) & 2u) * 0x1E000000u);
+    }
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            mbar_init(su32(&bars->b_full[s]), 128);
+            mbar_init(su32(&bars->b_full[s]), PROD_THREADS);
             mbar_init(su32(&bars->a_full[s]), 1);
             mbar_init(su32(&bars->empty[s]), 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(su32(&bars->acc_full[a]), 1);
-            mbar_init(su32(&bars->acc_empty[a]), 128);
+            mbar_init(su32(&bars->acc_empty[a]), EPI_THREADS);
         }
-        mbar_init(su32(&bars->red), 128);
+        mbar_init(su32(&bars->red), EPI_THREADS);
         mbar_init(su32(&bars->drain), 1);
         bars->abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -237,10 +251,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 }
             }
         }
-    } else if (warp < 6) {
+    } else if (warp < 10) {
         // ---------------- epilogue ----------------
         const int quarter = warp & 3;           // TMEM lanes (rows) this warp may access
-        const int et = threadIdx.x - 64;        // 0..127
+        const int g0 = ((warp - 2) >> 2) * 4;   // this warp's four groups of 32 relabelings
+        const int et = threadIdx.x - 64;        // 0..255
         int acc = 0;
         uint32_t acc_phase = 0, red_phase = 0;
         int rbuf = 0;
@@ -248,20 +263,22 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const Unit x = decode_unit(bt, u);
             const Chunk ch = x.ch;
             const int64_t Bp = x.Bp;
-            // mask word of this warp's 32 rows, for the unit's 256 relabelings
-            const uint32_t *wrow = bt.maskT + x.mask0 + ((int64_t)ch.I * 8 + x.h * 4 + quarter) * Bp + x.m * TC_N;
-            uint32_t words[8];
+            // mask word of this warp's 32 rows, for the warp's 128 relabelings
+            const uint32_t *wrow =
+                bt.maskT + x.mask0 + ((int64_t)ch.I * 8 + x.h * 4 + quarter) * Bp + x.m * TC_N + g0 * 32;
+            uint32_t words[4];
 #pragma unroll
-            for (int g = 0; g < 8; ++g) words[g] = wrow[g * 32 + lane];
+            for (int g = 0; g < 4; ++g) words[g] = wrow[g * 32 + lane];
             if (!mbar_wait(su32(&bars->acc_full[acc]), acc_phase, abort_flag, ctr, ERR_WAIT_EPI)) break;
             fence_after();
-            const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * TC_N);
-            float *myred = red + (rbuf * 4 + quarter) * TC_N;
+            const uint32_t tbase =
+                tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * TC_N) + (uint32_t)(g0 * 32);
+            float *myred = red + (rbuf * 4 + quarter) * TC_N + g0 * 32;
 #pragma unroll 1
-            for (int g = 0; g < 8; ++g) {
+            for (int g = 0; g < 4; ++g) {
                 uint32_t v[32];
                 tmem_ld32(tbase + (uint32_t)(g * 32), v);
-                // bit e of `mine` = s_{b_e}[row of this lane], b_e = relabeling 32 g + e
+                // bit e of `mine` = s_{b_e}[row of this lane], b_e = relabeling 32 (g0 + g) + e
                 uint32_t mine = 0;
 #pragma unroll
                 for (int l = 0; l < 32; ++l) {
@@ -286,14 +303,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             }
             fence_before();
             mbar_arrive(su32(&bars->acc_empty[acc]));
-            // the four warps' sums, added in a fixed order
+            // the four row quarters' sums, added in a fixed order
             mbar_arrive(su32(&bars->red));
             if (!mbar_wait(su32(&bars->red), red_phase, abort_flag, ctr, ERR_WAIT_EPI)) break;
             const float *rb = red + rbuf * 4 * TC_N;
             float *out = bt.partial + x.part0 + (2 * x.q + x.h) * Bp + x.m * TC_N;
-#pragma unroll
-            for (int c = et; c < TC_N; c += 128)
-                out[c] = (rb[c] + rb[TC_N + c]) + (rb[2 * TC_N + c] + rb[3 * TC_N + c]);
+            out[et] = (rb[et] + rb[TC_N + et]) + (rb[2 * TC_N + et] + rb[3 * TC_N + et]);
             red_phase ^= 1u;
             rbuf ^= 1;
             if (++acc == 2) {
@@ -305,7 +320,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         // ---------------- relabeling-tile producers ----------------
         // The mask words of a stage are loaded two stages ahead, so that their L2
         // latency overlaps the expansion of the stages before.
-        const int r = threadIdx.x - 192;   // 0..127: rows r and r + 128 of the B tile
+        const int r = threadIdx.x - 320;   // 0..255: row r of the B tile
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
@@ -314,39 +329,32 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const Chunk ch = x.ch;
             const int64_t Bp = x.Bp;
             const uint32_t *maskT = bt.maskT + x.mask0 + x.m * TC_N + r;
-            // words 2 kb and 2 kb + 1 of relabelings r and r + 128
-            auto load4 = [&](int kb, uint4 &w) {
+            // words 2 kb and 2 kb + 1 of relabeling r
+            auto load2 = [&](int kb, uint2 &w) {
                 const uint32_t *p0 = maskT + (int64_t)(2 * kb) * Bp;
                 w.x = p0[0];
                 w.y = p0[Bp];
-                w.z = p0[128];
-                w.w = p0[Bp + 128];
             };
-            uint4 cur = make_uint4(0, 0, 0, 0), nxt = make_uint4(0, 0, 0, 0);
-            load4(ch.kb0, cur);
-            if (ch.kb0 + 1 < ch.kb1) load4(ch.kb0 + 1, nxt);
+            uint2 cur = make_uint2(0, 0), nxt = make_uint2(0, 0);
+            load2(ch.kb0, cur);
+            if (ch.kb0 + 1 < ch.kb1) load2(ch.kb0 + 1, nxt);
             for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
-                uint4 nn = make_uint4(0, 0, 0, 0);
-                if (kb + 2 < ch.kb1) load4(kb + 2, nn);
+                uint2 nn = make_uint2(0, 0);
+                if (kb + 2 < ch.kb1) load2(kb + 2, nn);
                 if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_MASK)) {
                     ok = false;
                     break;
                 }
-                uint8_t *tile = smem + stage * STAGE_BYTES + 2 * A_BYTES;
+                uint8_t *brow = smem + stage * STAGE_BYTES + 2 * A_BYTES + r * 128;
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    const int rr = r + half * 128;
-                    const uint32_t wa = half ? cur.z : cur.x, wb = half ? cur.w : cur.y;
-                    uint8_t *brow = tile + rr * 128;
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        const uint32_t byte = ((c < 4 ? wa : wb) >> (8 * (c & 3))) & 0xFFu;
-                        const uint4 v = expand8(byte);
-                        const uint32_t dst = su32(brow + ((c ^ (rr & 7)) << 4));
-                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(v.x), "r"(v.y),
-                                     "r"(v.z), "r"(v.w)
-                                     : "memory");
-                    }
+                for (int c = 0; c < 8; ++c) {
+                    const uint32_t w = c < 4 ? cur.x : cur.y;
+                    const uint2 lo = lut[(w >> (8 * (c & 3))) & 15u];
+                    const uint2 hi = lut[(w >> (8 * (c & 3) + 4)) & 15u];
+                    const uint32_t dst = su32(brow + ((c ^ (r & 7)) << 4));
+                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(lo.x), "r"(lo.y),
+                                 "r"(hi.x), "r"(hi.y)
+                                 : "memory");
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(su32(&bars->b_full[stage]));
