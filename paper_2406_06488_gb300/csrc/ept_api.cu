@@ -88,19 +88,74 @@ struct Plan {
     std::vector<BlkInfo> blk;
     std::vector<Tile> tiles;
     std::vector<Chunk> chunks;
+    std::vector<int64_t> sched, sched_off;   // contraction schedule: units of CTA c = sched[sched_off[c] ..)
+    int tc_grid = 0;                         // contraction CTAs
     std::vector<size_t> in_off;       // per test: byte offset of its X (then Y, then masks) in the input region
     int64_t nrows = 0, npan = 0, ncols_pad = 0, nunits = 0, nsimt = 0, nblk = 0, nmask = 0, nchunk = 0, npart = 0,
             nstats = 0, p_stride = 0;
     size_t in_bytes = 0;              // host inputs copied into the arena
     // byte offsets in the arena; the first tab_bytes are the uploaded tables
     size_t off_desc, off_pre_rows, off_pre_panels, off_pre_cols, off_pre_units, off_pre_simt, off_blk, off_tiles,
-        off_chunks, tab_bytes;
+        off_chunks, off_sched, off_sched_off, tab_bytes;
     size_t off_in, off_norms, off_iscale, off_u, off_Zh, off_Zl, off_D, off_Chi, off_Clo, off_rowpart, off_colpart,
         off_r, off_Spart, off_dcorr, off_Upart, off_Stpart, off_maskT, off_partial, off_stats, off_observed, off_ctr,
         total;
 };
 
-void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host_in, int chunk_kb) {
+// The fields of a test's descriptor that do not depend on its shape (statistic,
+// bandwidth, seed); a cached plan is refreshed with them on every run.
+void set_test_params(TestDesc &d, const TestSpec &s) {
+    d.stat = s.stat;
+    d.seed = s.seed;
+    d.neg_inv_2s2 = (s.stat == EPT_STAT_ED) ? 0.f : (float)(-1.0 / (2.0 * s.sigma * s.sigma));
+    d.sign = (s.stat == EPT_STAT_ED) ? -1.0 : 1.0;
+}
+
+// Static schedule of the tensor-core contraction: units sorted by length (K-blocks,
+// longest first, stable so that units of one chunk stay together) and dealt to the
+// CTAs in snake order, which balances the CTAs' total work far better than a plain
+// stride when each CTA gets few units.
+void plan_schedule(Plan &P, int num_sms) {
+    P.sched.clear();
+    P.sched_off.clear();
+    P.tc_grid = 0;
+    if (P.nunits <= 0) return;
+    const int64_t G = std::min<int64_t>(std::max(num_sms, 1), P.nunits);
+    P.tc_grid = (int)G;
+    // unit lengths
+    std::vector<int> len((size_t)P.nunits);
+    int maxlen = 0;
+    for (int t = 0; t < P.n_tests; ++t) {
+        const TestDesc &d = P.desc[t];
+        const int64_t u0 = P.pre_units[t], nu = P.pre_units[t + 1] - u0;
+        for (int64_t lu = 0; lu < nu; ++lu) {
+            const Chunk &ch = P.chunks[(size_t)(d.chunk0 + (lu >> 1) / d.MT)];
+            const int l = ch.kb1 - ch.kb0;
+            len[(size_t)(u0 + lu)] = l;
+            maxlen = std::max(maxlen, l);
+        }
+    }
+    // counting sort, longest first
+    std::vector<int64_t> start((size_t)maxlen + 2, 0);
+    for (int64_t u = 0; u < P.nunits; ++u) start[(size_t)(maxlen - len[(size_t)u]) + 1]++;
+    for (size_t k = 1; k < start.size(); ++k) start[k] += start[k - 1];
+    std::vector<int64_t> order((size_t)P.nunits);
+    for (int64_t u = 0; u < P.nunits; ++u) order[(size_t)start[(size_t)(maxlen - len[(size_t)u])]++] = u;
+    // snake deal: position k goes to CTA (k % G) on even rounds, G - 1 - (k % G) on odd ones
+    auto cta_of = [G](int64_t k) {
+        const int64_t r = k / G, c = k % G;
+        return (r & 1) ? G - 1 - c : c;
+    };
+    P.sched_off.assign((size_t)G + 1, 0);
+    for (int64_t k = 0; k < P.nunits; ++k) P.sched_off[(size_t)cta_of(k) + 1]++;
+    for (int64_t c = 0; c < G; ++c) P.sched_off[(size_t)c + 1] += P.sched_off[(size_t)c];
+    std::vector<int64_t> fill(P.sched_off.begin(), P.sched_off.end() - 1);
+    P.sched.resize((size_t)P.nunits);
+    for (int64_t k = 0; k < P.nunits; ++k) P.sched[(size_t)fill[(size_t)cta_of(k)]++] = order[(size_t)k];
+}
+
+void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host_in, int chunk_kb,
+                int num_sms = 160) {
     P = Plan();
     P.n_tests = (int)specs.size();
     P.prec = prec;
@@ -132,14 +187,11 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
         d.comp = d.ny < d.nx;
         d.m = d.comp ? d.ny : d.nx;
         d.other = d.comp ? d.nx : d.ny;
-        d.stat = s.stat;
-        d.seed = s.seed;
-        d.neg_inv_2s2 = (s.stat == EPT_STAT_ED) ? 0.f : (float)(-1.0 / (2.0 * s.sigma * s.sigma));
+        set_test_params(d, s);
         d.tau = (float)NEAR_DUP_TAU;
         const double fn = (double)d.n, q = fn / ((double)d.nx * (double)d.ny);
         d.cT = q * q;
         d.inv_o2 = 1.0 / ((double)d.other * (double)d.other);
-        d.sign = (s.stat == EPT_STAT_ED) ? -1.0 : 1.0;
         d.kappa = 2.0 * (double)d.m / fn;
         d.inv_n = 1.0 / fn;
         d.inv_2n2 = 1.0 / (2.0 * fn * fn);
@@ -184,6 +236,7 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
     }
     P.ncols_pad = P.pre_cols.back();
     P.nunits = P.pre_units.back();
+    if (tc) plan_schedule(P, num_sms);
     P.nsimt = P.pre_simt.back();
     P.in_bytes = in_bytes;
 
@@ -203,6 +256,8 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
     P.off_blk = take(sizeof(BlkInfo) * P.blk.size());
     P.off_tiles = take(sizeof(Tile) * P.tiles.size());
     P.off_chunks = take(sizeof(Chunk) * P.chunks.size());
+    P.off_sched = take(8 * P.sched.size());
+    P.off_sched_off = take(8 * P.sched_off.size());
     P.tab_bytes = o;
     o = align_up(o, 1024);
     const size_t elems = (size_t)P.nblk * PANEL * KB;
@@ -286,6 +341,11 @@ struct ept_ctx {
     int serve_lanes = 3;                // serving: batches in flight at once
     int serve_slots = 256;              // serving: requests in flight at once
     cudaEvent_t ev_user = nullptr;      // orders the context's stream after a caller's stream
+    // plan of the last run, reused while the batch shape repeats; tables_staged: the
+    // pinned staging area still holds its constant tables
+    Plan *plan = nullptr;
+    std::vector<int64_t> plan_key;
+    bool tables_staged = false;
     std::string tune_file;
 };
 
@@ -345,6 +405,7 @@ ept_status ensure_pinned(ept_ctx *c, size_t bytes) {
         return fail(EPT_ENOMEM, "cudaHostAlloc(%zu bytes) failed: %s", cap, cudaGetErrorString(e));
     }
     c->pinned_cap = cap;
+    c->tables_staged = false;
     return EPT_OK;
 }
 
@@ -374,7 +435,7 @@ Staging staging_layout(const Plan &P) {
 // (host inputs) the input rows into the pinned area.  Everything the device work
 // reads from the host goes through this area, so a captured graph can be replayed
 // after re-staging.
-void stage_host(ept_ctx *c, Plan &P, const std::vector<TestSpec> &specs, bool on_device) {
+void stage_host(ept_ctx *c, Plan &P, const std::vector<TestSpec> &specs, bool on_device, bool tables = true) {
     const Staging S = staging_layout(P);
     uint8_t *A = c->arena, *pin = c->pinned;
     for (int t = 0; t < P.n_tests; ++t) {
@@ -403,6 +464,7 @@ void stage_host(ept_ctx *c, Plan &P, const std::vector<TestSpec> &specs, bool on
     }
     uint8_t *tab = pin + S.tables;
     memcpy(tab + P.off_desc, P.desc.data(), sizeof(TestDesc) * P.n_tests);
+    if (!tables) return;   // the shape-dependent tables are already in place
     memcpy(tab + P.off_pre_rows, P.pre_rows.data(), 8 * P.pre_rows.size());
     memcpy(tab + P.off_pre_panels, P.pre_panels.data(), 8 * P.pre_panels.size());
     memcpy(tab + P.off_pre_cols, P.pre_cols.data(), 8 * P.pre_cols.size());
@@ -411,6 +473,10 @@ void stage_host(ept_ctx *c, Plan &P, const std::vector<TestSpec> &specs, bool on
     if (!P.blk.empty()) memcpy(tab + P.off_blk, P.blk.data(), sizeof(BlkInfo) * P.blk.size());
     if (!P.tiles.empty()) memcpy(tab + P.off_tiles, P.tiles.data(), sizeof(Tile) * P.tiles.size());
     if (!P.chunks.empty()) memcpy(tab + P.off_chunks, P.chunks.data(), sizeof(Chunk) * P.chunks.size());
+    if (!P.sched.empty()) {
+        memcpy(tab + P.off_sched, P.sched.data(), 8 * P.sched.size());
+        memcpy(tab + P.off_sched_off, P.sched_off.data(), 8 * P.sched_off.size());
+    }
 }
 
 Batch device_view(ept_ctx *c, const Plan &P) {
@@ -427,6 +493,9 @@ Batch device_view(ept_ctx *c, const Plan &P) {
     b.blk = (const BlkInfo *)(A + P.off_blk);
     b.tiles = (const Tile *)(A + P.off_tiles);
     b.chunks = (const Chunk *)(A + P.off_chunks);
+    b.sched = P.sched.empty() ? nullptr : (const int64_t *)(A + P.off_sched);
+    b.sched_off = P.sched.empty() ? nullptr : (const int64_t *)(A + P.off_sched_off);
+    b.tc_grid = P.tc_grid;
     b.nblk_total = P.nblk;
     b.ntiles = (int64_t)P.tiles.size();
     b.nrows_total = P.nrows;
@@ -646,14 +715,26 @@ void load_tune_file(ept_ctx *c) {
 ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bool on_device, int chunk_kb,
                     bool use_graph, ept_result *out, void *stream, float *device_ms) {
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
-    Plan P;
-    plan_batch(P, specs, prec, !on_device, chunk_kb);
+    std::vector<int64_t> pkey = shape_key(specs, prec, on_device);
+    pkey.push_back(chunk_kb);
+    if (!c->plan) {
+        c->plan = new (std::nothrow) Plan();
+        if (!c->plan) return fail(EPT_ENOMEM, "host allocation failed");
+    }
+    if (c->plan_key != pkey) {
+        plan_batch(*c->plan, specs, prec, !on_device, chunk_kb, c->num_sms);
+        c->plan_key = pkey;
+        c->tables_staged = false;
+    }
+    Plan &P = *c->plan;
+    for (int t = 0; t < P.n_tests; ++t) set_test_params(P.desc[t], specs[t]);
     ept_status st = ensure_arena(c, P.total, s);
     if (st != EPT_OK) return st;
     const Staging S = staging_layout(P);
     if ((st = ensure_pinned(c, S.total)) != EPT_OK) return st;
     if (s != c->stream) CK(cudaStreamSynchronize(c->stream));
-    stage_host(c, P, specs, on_device);
+    stage_host(c, P, specs, on_device, !c->tables_staged);
+    c->tables_staged = true;
     if (use_graph && c->graphs) {
         // the graph runs on the context's stream, after the caller's stream's prior work
         if (s != c->stream) {
@@ -869,7 +950,7 @@ bool form_batch(Server *S, Lane &L) {
     std::vector<TestSpec> specs;
     for (Request *r : batch) specs.push_back(r->spec);
     while (!batch.empty()) {
-        plan_batch(L.plan, specs, prec, true, CHUNK_KB_DEFAULT);
+        plan_batch(L.plan, specs, prec, true, CHUNK_KB_DEFAULT, L.ctx->num_sms);
         if (S->in_use + L.plan.total <= S->budget) break;
         // hand the last one back, at its place in arrival order
         Request *r = batch.back();
@@ -1055,6 +1136,7 @@ ept_status ept_destroy(ept_ctx *c) {
         drop_graph(c);
         if (c->arena) cudaFree(c->arena);
         if (c->pinned) cudaFreeHost(c->pinned);
+        delete c->plan;
         for (int k = 0; k < 7; ++k)
             if (c->ev[k]) cudaEventDestroy(c->ev[k]);
         for (int k = 0; k < 3; ++k)
@@ -1169,6 +1251,7 @@ ept_status ept_build_blocks(ept_ctx *c, const float *X, int64_t nx, const float 
     const Staging S = staging_layout(P);
     if ((st = ensure_pinned(c, S.total)) != EPT_OK) return st;
     if (s != c->stream) CK(cudaStreamSynchronize(c->stream));
+    c->tables_staged = false;   // the staging area now holds this call's tables
     stage_host(c, P, specs, on_device != 0);
     uint8_t *A = c->arena;
     const Batch b = device_view(c, P);

@@ -117,6 +117,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     float *red = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + 1024);
     volatile int *abort_flag = &bars->abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // this CTA's units: its slice of the schedule, or every gridDim.x-th unit
+    const int64_t k_first = bt.sched ? bt.sched_off[blockIdx.x] : (int64_t)blockIdx.x;
+    const int64_t k_end = bt.sched ? bt.sched_off[blockIdx.x + 1] : nunits;
+    const int64_t k_step = bt.sched ? 1 : (int64_t)gridDim.x;
+    const int64_t *sched = bt.sched;
+    auto unit_at = [sched](int64_t k) { return sched ? sched[k] : k; };
 
     // nibble -> four FP16 values (1.0 where the bit is set), for the relabeling producers
     uint2 *lut = reinterpret_cast<uint2 *>(smem + STAGES * STAGE_BYTES + 512);
@@ -159,7 +165,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             int armed[STAGES];   // parity of the last phase armed on each stage, -1 = none
             for (int s2 = 0; s2 < STAGES; ++s2) armed[s2] = -1;
             bool ok = true;
-            for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+            for (int64_t k = k_first; k < k_end && ok; k += k_step) {
+                const int64_t u = unit_at(k);
                 const Unit x = decode_unit(bt, u);
                 const Chunk ch = x.ch;
                 const int row = (int)x.h * TC_M;
@@ -202,7 +209,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             int stage = 0, acc = 0;
             uint32_t phase = 0, acc_phase = 0;
             bool ok = true;
-            for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+            for (int64_t k = k_first; k < k_end && ok; k += k_step) {
+                const int64_t u = unit_at(k);
                 const Chunk ch = decode_unit(bt, u).ch;
                 if (!mbar_wait(su32(&bars->acc_empty[acc]), acc_phase ^ 1u, abort_flag, ctr, ERR_WAIT_MMA)) {
                     ok = false;
@@ -259,7 +267,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         int acc = 0;
         uint32_t acc_phase = 0, red_phase = 0;
         int rbuf = 0;
-        for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        for (int64_t k = k_first; k < k_end; k += k_step) {
+            const int64_t u = unit_at(k);
             const Unit x = decode_unit(bt, u);
             const Chunk ch = x.ch;
             const int64_t Bp = x.Bp;
@@ -324,7 +333,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
-        for (int64_t u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        for (int64_t k = k_first; k < k_end && ok; k += k_step) {
+                const int64_t u = unit_at(k);
             const Unit x = decode_unit(bt, u);
             const Chunk ch = x.ch;
             const int64_t Bp = x.Bp;
@@ -387,7 +397,7 @@ cudaError_t launch_contract_tc(const Batch &b, const void *tmap_hi, const void *
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    int64_t grid = num_sms;
+    int64_t grid = b.sched ? (int64_t)b.tc_grid : (int64_t)num_sms;
     if (grid > b.nunits_total) grid = b.nunits_total;
     if (grid < 1) return cudaSuccess;
     CUtensorMap th, tl;

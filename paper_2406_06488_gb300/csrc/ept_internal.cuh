@@ -125,6 +125,8 @@ struct Batch {
     const BlkInfo *blk;
     const Tile *tiles;
     const Chunk *chunks;
+    const int64_t *sched, *sched_off;    // contraction schedule per CTA (null: units strided over the grid)
+    int tc_grid;                         // contraction CTAs when scheduled
     int64_t nblk_total, ntiles, nrows_total, npan_total, ncols_total, nunits_total, nsimt_total;
     int64_t p_stride;                    // row stride of the FP16 rows (max p_pad)
     float *norms, *iscale, *u;

@@ -130,3 +130,22 @@ def test_set_option_rejects_unknown(ctx):
     from paper_2406_06488_gb300 import ept
     with pytest.raises(ept.EptError):
         ctx.set_option("serve_lanes", 0)
+
+
+def test_repeated_shape_follows_stat_sigma_seed(ctx):
+    # same shapes, different statistic / bandwidth / seed: the cached plan and the
+    # replayed graph must pick up the new per-test parameters
+    from paper_2406_06488_gb300 import ept
+    spec = workloads.TwoSampleSpec(nx=150, ny=170, p=9, y_mean=0.2, data_seed=44)
+    X, Y = workloads.gaussian_pair(spec)
+    runs = [dict(stat="ed", sigma=1.0, seed=1), dict(stat="mmd", sigma=2.5, seed=1),
+            dict(stat="mmd", sigma=0.7, seed=9), dict(stat="ed", sigma=1.0, seed=9)]
+    for kw in runs + runs:
+        got = ctx.test(X, Y, B=300, **kw)
+        fresh = ept.Context(0)
+        try:
+            want = fresh.test(X, Y, B=300, **kw)
+        finally:
+            fresh.close()
+        assert got.observed == want.observed and got.n_ge == want.n_ge
+        assert np.array_equal(np.asarray(got.stats), np.asarray(want.stats))
