@@ -160,6 +160,10 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    replay CUDA graphs of repeated batches; with 0 every run is launched directly
    and the per-phase times of ept_result are filled in.  EPT_OPT_AUTOTUNE (default
    1 unless the environment sets EPT_AUTOTUNE=0): the contraction chunk autotuner.
+   EPT_OPT_DRAW_MODE (default 0): relabeling-draw kernel, 0 = automatic (a thread
+   per column when the batch has at least 1024 columns per SM, else a warp per
+   column), 1 = a warp per column, 2 = a thread per column; the draws are
+   identical in every mode.
    EPT_OPT_SERVE_LANES (default 3, 1..16): serving batches in flight at once;
    EPT_OPT_SERVE_SLOTS (default 256): serving requests in flight at once; both
    before the first ept_submit.  EPT_EINVAL for an unknown option or value. */
@@ -167,7 +171,8 @@ enum {
     EPT_OPT_GRAPHS = 1,
     EPT_OPT_AUTOTUNE = 2,
     EPT_OPT_SERVE_LANES = 3,
-    EPT_OPT_SERVE_SLOTS = 4
+    EPT_OPT_SERVE_SLOTS = 4,
+    EPT_OPT_DRAW_MODE = 5
 };
 ept_status ept_set_option(ept_ctx *ctx, int option, int64_t value);
 

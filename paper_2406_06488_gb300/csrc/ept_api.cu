@@ -89,6 +89,7 @@ struct Plan {
     std::vector<Tile> tiles;
     std::vector<Chunk> chunks;
     std::vector<int64_t> sched, sched_off;   // contraction schedule: units of CTA c = sched[sched_off[c] ..)
+    bool user_masks = false;                 // some test brings its own relabelings
     int tc_grid = 0;                         // contraction CTAs
     std::vector<size_t> in_off;       // per test: byte offset of its X (then Y, then masks) in the input region
     int64_t nrows = 0, npan = 0, ncols_pad = 0, nunits = 0, nsimt = 0, nblk = 0, nmask = 0, nchunk = 0, npart = 0,
@@ -227,6 +228,7 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
         push_pre(P.pre_cols, d.Bp);
         push_pre(P.pre_units, tc_units(d));
         push_pre(P.pre_simt, d.nchunks * 2 * (d.Bp / 64));
+        P.user_masks |= s.user_masks != nullptr;
         P.in_off.push_back(in_bytes);
         if (host_in) {
             in_bytes += align_up((size_t)d.nx * d.p * 4, 256) + align_up((size_t)d.ny * d.p * 4, 256);
@@ -338,6 +340,7 @@ struct ept_ctx {
     std::map<std::vector<int64_t>, int> tuned_chunk;   // autotuner cache: batch shape -> chunk length
     bool autotune = true;
     bool graphs = true;                 // replay captured graphs of repeated batches
+    int draw_mode = 0;                  // relabeling draws: 0 automatic, DRAW_WARPS, DRAW_LANES
     int serve_lanes = 3;                // serving: batches in flight at once
     int serve_slots = 256;              // serving: requests in flight at once
     cudaEvent_t ev_user = nullptr;      // orders the context's stream after a caller's stream
@@ -545,7 +548,12 @@ ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed)
     cudaStream_t s2 = c->side;
     CK(cudaStreamWaitEvent(s2, c->ev[1], 0));
     if (timed) CK(cudaEventRecord(c->ev_side[1], s2));
-    launch_masks(b, c->num_sms, s2);
+    int mode = c->draw_mode;
+    if (mode == 0)
+        mode = (!P.user_masks && P.ncols_pad >= DRAW_LANES_MIN_COLS_PER_SM * (int64_t)c->num_sms) ? DRAW_LANES
+                                                                                                  : DRAW_WARPS;
+    if (P.user_masks) mode = DRAW_WARPS;   // caller relabelings are validated by the warp kernel
+    launch_masks(b, c->num_sms, mode, s2);
     CK(cudaGetLastError());
     CK(cudaEventRecord(c->ev_side[2], s2));
 
@@ -1293,6 +1301,12 @@ ept_status ept_set_option(ept_ctx *c, int option, int64_t value) {
         return EPT_OK;
     case EPT_OPT_AUTOTUNE:
         c->autotune = value != 0;
+        return EPT_OK;
+    case EPT_OPT_DRAW_MODE:
+        if (value < 0 || value > 2) return fail(EPT_EINVAL, "draw mode must be 0, 1 or 2");
+        c->draw_mode = (int)value;
+        c->plan_key.clear();   // a captured graph holds the previous draw kernel
+        drop_graph(c);
         return EPT_OK;
     case EPT_OPT_SERVE_LANES:
     case EPT_OPT_SERVE_SLOTS:

@@ -188,6 +188,67 @@ __global__ void __launch_bounds__(128) k_masks(const Batch bt) {
     }
 }
 
+// One thread per relabeling column (used when the batch has enough columns to fill
+// the GPU this way, and no caller relabelings): the thread runs Algorithm S over
+// its column's slots one at a time, from the same Philox words as draw_column, so
+// the two kernels write identical bits.  Without the warp's ballots, shuffles and
+// fixed-point rounds a slot costs about half the instructions, and the 32 lanes of
+// a warp write 32 neighbouring columns of a word with one coalesced store.
+__global__ void __launch_bounds__(256) k_masks_lanes(const Batch bt) {
+    const int64_t gc = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gc >= bt.ncols_total) return;
+    const int t = find_test(bt.pre.cols, bt.n_tests, gc);
+    const TestDesc &d = bt.desc[t];
+    const int64_t c = gc - bt.pre.cols[t];
+    const int n = (int)d.n, nw = (int)d.nw, nx = (int)d.nx;
+    const int64_t Bp = d.Bp;
+    const bool comp = d.comp != 0;
+    uint32_t *col = bt.maskT + d.mask0 + c;
+    if (c >= d.ncols) {
+        for (int w = 0; w < nw; ++w) col[(int64_t)w * Bp] = 0u;
+        return;
+    }
+    if (c == 0) {
+        for (int w = 0; w < nw; ++w) {
+            const uint32_t v = valid_bits(w, nx);
+            col[(int64_t)w * Bp] = comp ? (~v & valid_bits(w, n)) : v;
+        }
+        return;
+    }
+    const uint64_t seed = d.seed;
+    uint32_t kx[10], ky[10];
+    kx[0] = (uint32_t)seed;
+    ky[0] = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        kx[r] = kx[r - 1] + 0x9E3779B9u;
+        ky[r] = ky[r - 1] + 0xBB67AE85u;
+    }
+    const uint32_t blo = (uint32_t)(uint64_t)c, bhi = (uint32_t)((uint64_t)c >> 32);
+    int need = nx;
+    for (int w = 0; w < nw; ++w) {
+        uint32_t bits = 0;
+        const int t0 = w * 32;
+        if (need > 0 && t0 < n) {
+#pragma unroll 2
+            for (int j = 0; j < 16; ++j) {
+                const int tp = t0 + 2 * j;
+                uint64_t u0, u1;
+                philox_words((uint32_t)(tp >> 1), blo, bhi, kx, ky, u0, u1);
+                if (tp < n && (int)mulhi_64x32(u0, (uint32_t)(n - tp)) < need) {
+                    bits |= 1u << (2 * j);
+                    --need;
+                }
+                if (tp + 1 < n && (int)mulhi_64x32(u1, (uint32_t)(n - tp - 1)) < need) {
+                    bits |= 2u << (2 * j);
+                    --need;
+                }
+            }
+        }
+        col[(int64_t)w * Bp] = comp ? (~bits & valid_bits(w, n)) : bits;
+    }
+}
+
 // Blocks per SM of the draw kernel: MASK_CTAS_PER_SM, or the environment's
 // EPT_MASK_BLOCKS_PER_SM (0: one warp per column, no cap).
 static int mask_blocks_per_sm() {
@@ -200,8 +261,12 @@ static int mask_blocks_per_sm() {
     return v;
 }
 
-void launch_masks(const Batch &b, int num_sms, cudaStream_t s) {
+void launch_masks(const Batch &b, int num_sms, int mode, cudaStream_t s) {
     if (b.ncols_total <= 0) return;
+    if (mode == DRAW_LANES) {
+        k_masks_lanes<<<(unsigned)((b.ncols_total + 255) / 256), 256, 0, s>>>(b);
+        return;
+    }
     int64_t blocks = (b.ncols_total + 3) / 4;
     const int per_sm = mask_blocks_per_sm();
     if (per_sm > 0) {

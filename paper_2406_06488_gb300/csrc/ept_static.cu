@@ -268,7 +268,7 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     launch_rowsum_reduce(b, s);
     launch_center(b, s);
     launch_pack(b, true, s);
-    launch_masks(b, sd->num_sms, s);
+    launch_masks(b, sd->num_sms, DRAW_WARPS, s);
     SCK(cudaGetLastError());
     alignas(64) CUtensorMap th, tl;
     char emsg[160];

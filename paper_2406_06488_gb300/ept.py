@@ -145,7 +145,7 @@ def estimate_bytes(nx: int, ny: int, p: int, B: int, prec="split_bf16") -> int:
     return int(load().ept_estimate_bytes(nx, ny, p, B, _prec(prec)))
 
 
-OPTION = {"graphs": 1, "autotune": 2, "serve_lanes": 3, "serve_slots": 4}
+OPTION = {"graphs": 1, "autotune": 2, "serve_lanes": 3, "serve_slots": 4, "draw_mode": 5}
 
 
 class Context:
