@@ -349,6 +349,14 @@ struct ept_ctx {
     Plan *plan = nullptr;
     std::vector<int64_t> plan_key;
     bool tables_staged = false;
+    // host-to-device copies of this run's inputs: from the caller's buffers when they
+    // are page-locked, else from the pinned staging area
+    struct InputCopy {
+        size_t dst;          // byte offset in the arena
+        const void *src;
+        size_t bytes;
+    };
+    std::vector<InputCopy> in_copies;
     std::string tune_file;
 };
 
@@ -434,13 +442,35 @@ Staging staging_layout(const Plan &P) {
     return S;
 }
 
-// Host-side staging of one run: device pointers into the descriptors, tables and
-// (host inputs) the input rows into the pinned area.  Everything the device work
-// reads from the host goes through this area, so a captured graph can be replayed
-// after re-staging.
+bool page_locked(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// Host-side staging of one run: device pointers into the descriptors and the tables
+// into the pinned area (everything a captured graph reads from the host goes through
+// it, so the graph can be replayed after re-staging), and the list of input copies:
+// host inputs in page-locked memory are copied to the device directly, others are
+// first gathered into the pinned area.
 void stage_host(ept_ctx *c, Plan &P, const std::vector<TestSpec> &specs, bool on_device, bool tables = true) {
     const Staging S = staging_layout(P);
     uint8_t *A = c->arena, *pin = c->pinned;
+    c->in_copies.clear();
+    bool all_staged = true;
+    auto input = [&](size_t off, const void *src, size_t bytes) {
+        if (bytes == 0) return;
+        if (page_locked(src)) {
+            c->in_copies.push_back({P.off_in + off, src, bytes});
+            all_staged = false;
+        } else {
+            memcpy(pin + S.inputs + off, src, bytes);
+            c->in_copies.push_back({P.off_in + off, pin + S.inputs + off, bytes});
+        }
+    };
     for (int t = 0; t < P.n_tests; ++t) {
         TestDesc &d = P.desc[t];
         const TestSpec &s = specs[t];
@@ -452,18 +482,23 @@ void stage_host(ept_ctx *c, Plan &P, const std::vector<TestSpec> &specs, bool on
         } else {
             const size_t xo = P.in_off[t], yo = xo + align_up((size_t)d.nx * d.p * 4, 256);
             const size_t mo = yo + align_up((size_t)d.ny * d.p * 4, 256);
-            memcpy(pin + S.inputs + xo, s.X, (size_t)d.nx * d.p * 4);
-            memcpy(pin + S.inputs + yo, s.Y, (size_t)d.ny * d.p * 4);
+            input(xo, s.X, (size_t)d.nx * d.p * 4);
+            input(yo, s.Y, (size_t)d.ny * d.p * 4);
             d.X = (const float *)(A + P.off_in + xo);
             d.Y = (const float *)(A + P.off_in + yo);
             if (s.user_masks) {
-                memcpy(pin + S.inputs + mo, s.user_masks, (size_t)s.B * d.nwu * 4);
+                input(mo, s.user_masks, (size_t)s.B * d.nwu * 4);
                 d.user_masks = (const uint32_t *)(A + P.off_in + mo);
             } else {
                 d.user_masks = nullptr;
             }
             d.out_stats = nullptr;   // copied back to the host and scattered there
         }
+    }
+    if (!on_device && all_staged && P.in_bytes) {
+        // everything went through the staging area: one copy of the whole input region
+        c->in_copies.clear();
+        c->in_copies.push_back({P.off_in, pin + S.inputs, P.in_bytes});
     }
     uint8_t *tab = pin + S.tables;
     memcpy(tab + P.off_desc, P.desc.data(), sizeof(TestDesc) * P.n_tests);
@@ -532,15 +567,23 @@ Batch device_view(ept_ctx *c, const Plan &P) {
 
 // The device work of one run, enqueued on s (and the side stream).  With `timed`,
 // events mark the phases (not used while capturing a graph).
-ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed) {
+ept_status enqueue_inputs(ept_ctx *c, cudaStream_t s) {
+    for (const ept_ctx::InputCopy &k : c->in_copies)
+        CK(cudaMemcpyAsync(c->arena + k.dst, k.src, k.bytes, cudaMemcpyHostToDevice, s));
+    return EPT_OK;
+}
+
+// with_inputs: also copy the host inputs (a captured graph leaves them out: they are
+// copied before each replay, from wherever the caller's buffers are)
+ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed, bool with_inputs = true) {
+    ept_status st = EPT_OK;
     const Staging S = staging_layout(P);
     uint8_t *A = c->arena, *pin = c->pinned;
     const Batch b = device_view(c, P);
     const bool tc = P.prec == EPT_PREC_SPLIT_BF16;
     if (timed) CK(cudaEventRecord(c->ev[0], s));
     CK(cudaMemcpyAsync(A, pin + S.tables, P.tab_bytes, cudaMemcpyHostToDevice, s));
-    if (P.host_in && P.in_bytes)
-        CK(cudaMemcpyAsync(A + P.off_in, pin + S.inputs, P.in_bytes, cudaMemcpyHostToDevice, s));
+    if (with_inputs && (st = enqueue_inputs(c, s)) != EPT_OK) return st;
     CK(cudaMemsetAsync(b.ctr, 0, sizeof(Counters) * P.n_tests, s));
     CK(cudaEventRecord(c->ev[1], s));
 
@@ -756,7 +799,7 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
             drop_graph(c);
             cudaGraph_t g = nullptr;
             CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            st = enqueue_device(c, P, s, false);
+            st = enqueue_device(c, P, s, false, false);
             const cudaError_t e_end = cudaStreamEndCapture(s, &g);
             if (st != EPT_OK) {
                 if (g) cudaGraphDestroy(g);
@@ -772,6 +815,7 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
             c->graph.arena = c->arena;
         }
         CK(cudaEventRecord(c->ev[0], s));
+        if ((st = enqueue_inputs(c, s)) != EPT_OK) return st;
         CK(cudaGraphLaunch(c->graph.exec, s));
         CK(cudaEventRecord(c->ev[4], s));
         CK(cudaStreamSynchronize(s));
@@ -1264,8 +1308,7 @@ ept_status ept_build_blocks(ept_ctx *c, const float *X, int64_t nx, const float 
     uint8_t *A = c->arena;
     const Batch b = device_view(c, P);
     CK(cudaMemcpyAsync(A, c->pinned + S.tables, P.tab_bytes, cudaMemcpyHostToDevice, s));
-    if (P.host_in && P.in_bytes)
-        CK(cudaMemcpyAsync(A + P.off_in, c->pinned + S.inputs, P.in_bytes, cudaMemcpyHostToDevice, s));
+    if ((st = enqueue_inputs(c, s)) != EPT_OK) return st;
     CK(cudaMemsetAsync(b.ctr, 0, sizeof(Counters), s));
     if (prec == EPT_PREC_SPLIT_BF16) {
         launch_split_rows(b, s);

@@ -178,3 +178,24 @@ def test_draw_modes_agree_and_match_oracle(ctx, prec):
         assert abs(r.observed - ref["observed"]) <= REL_TOL * abs(ref["observed"])
         if t["B"] > 0:
             assert _close(r.stats, ref["stats"])
+
+
+def test_page_locked_host_inputs(ctx):
+    # page-locked host buffers are copied to the device directly, pageable ones through
+    # the staging area; a batch may mix both
+    import torch
+    tests = _uneven(6, seed=10)
+    pinned = [dict(t, X=torch.from_numpy(t["X"]).pin_memory().numpy(),
+                   Y=torch.from_numpy(t["Y"]).pin_memory().numpy()) for t in tests]
+    mixed = [p if k % 2 else t for k, (p, t) in enumerate(zip(pinned, tests))]
+    a = ctx.test_batch(tests)
+    b = ctx.test_batch(pinned)
+    m = ctx.test_batch(mixed)
+    for x, y, z, t in zip(a, b, m, tests):
+        assert x.observed == y.observed == z.observed and x.n_ge == y.n_ge == z.n_ge
+        if t["B"] > 0:
+            assert np.array_equal(np.asarray(x.stats), np.asarray(y.stats))
+    t = tests[1]
+    s1 = ctx.test(t["X"], t["Y"], B=t["B"], seed=t["seed"], stat=t["stat"], sigma=t["sigma"])
+    s2 = ctx.test(pinned[1]["X"], pinned[1]["Y"], B=t["B"], seed=t["seed"], stat=t["stat"], sigma=t["sigma"])
+    assert s1.observed == s2.observed and s1.n_ge == s2.n_ge
