@@ -60,6 +60,24 @@ def _args():
     return ap.parse_args()
 
 
+def _max_over_ranks(value: float, device="cuda") -> float:
+    """The largest of the ranks' values (the slowest rank's time); the value itself
+    without a process group or with one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _weak_value(units_per_rank: float, world_size: int, steps: int, slowest_ms: float) -> float:
+    """Whole-job throughput of independent replicas: every rank's units over the
+    slowest rank's time."""
+    return units_per_rank * world_size * steps / (slowest_ms / 1000.0)
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -268,12 +286,8 @@ def run_ours(args):
         build_ms.append(r.ms_build)
     ctx.set_option("graphs", 1)
     tot_ms = sum(step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = spec.B * ws * args.steps / (tot_ms / 1000.0)
+    tot_ms = _max_over_ranks(tot_ms)
+    value = _weak_value(spec.B, ws, args.steps, tot_ms)
 
     # ---- plain FP32 path (the comparison side of the metric)
     plain_ms = []
@@ -418,12 +432,8 @@ def run_batched(args):
     torch.cuda.synchronize()
     clocks = sampler.stop()
     tot_ms = sum(step_ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = total_B * ws * args.steps / (tot_ms / 1000.0)
+    tot_ms = _max_over_ranks(tot_ms)
+    value = _weak_value(total_B, ws, args.steps, tot_ms)
 
     # per-phase times: the same batch launched directly (no graph), phases event-timed
     ctx.set_option("graphs", 0)
