@@ -36,8 +36,9 @@ METRIC = "permuted stats/s & p99 test latency, tuned vs plain FP32 GPU at rel er
 UNIT = "permuted stats/s"
 KERNELS_PER_STEP = 11  # libept kernels launched by one ept_test / ept_test_batch run (split path)
 # dram read + write bytes of one k_contract_tc launch on the highdim workload, from the ncu
-# capture summarised in profiles/k_contract_tc_highdim_ed.md (None once the kernel changes)
-CONTRACT_TRAFFIC = {}
+# capture summarised in profiles/k_contract_tc_highdim_ed.md (to be reset to {} whenever the
+# kernel changes, until it is captured again)
+CONTRACT_TRAFFIC = {"highdim": 63.68e6}
 
 
 def _args():
