@@ -68,7 +68,10 @@ __device__ __forceinline__ const float *row_ptr(const TestDesc &d, int64_t i) {
 
 // Pooled row i of a test -> FP16 hi / lo parts of c_i z_i (zero padding up to the
 // test's p_pad), the inverse scale 1/c_i, and the squared norm of the unscaled row
-// (exact products accumulated in FP64, rounded once).  c_i = 2^k with
+// (each product split exactly into p + e by an FMA, the p summed with TwoSum and
+// every rounding error carried in a second FP32 sum: about FP64 accuracy without
+// FP64 arithmetic per element; the lanes' pairs are added in FP64 and rounded once).
+// c_i = 2^k with
 // max |c_i z_i| < 2^14, k clamped to [-60, 60] so that 1/c_i 1/c_j stays a normal
 // FP32 number (rows above 2^74 would overflow the FP32 norms in any case).
 // Non-finite inputs are counted.  One warp per row of the batch.
@@ -77,9 +80,9 @@ __global__ void __launch_bounds__(256) k_split_rows(const Batch bt) {
     const int64_t gr = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (gr >= bt.nrows_total) return;
     const int t = find_test(bt.pre.rows, bt.n_tests, gr);
-    const TestDesc d = bt.desc[t];
+    const TestDesc &d = bt.desc[t];
     const int64_t i = gr - d.row0;
-    const int64_t p = d.p;
+    const int64_t p = d.p, p_pad = d.p_pad;
     const float *z = (i < d.n) ? row_ptr(d, i) : nullptr;
     uint32_t mx = 0;
     bool bad = false;
@@ -103,15 +106,24 @@ __global__ void __launch_bounds__(256) k_split_rows(const Batch bt) {
     }
     const float c = ldexpf(1.f, k2);
     __half *zh = (__half *)bt.Zh + gr * bt.p_stride, *zl = (__half *)bt.Zl + gr * bt.p_stride;
-    double acc = 0.0;
-    for (int64_t k = 2 * lane; k < d.p_pad; k += 64) {
+    float sh = 0.f, sl = 0.f;
+    for (int64_t k = 2 * lane; k < p_pad; k += 64) {
         float v0 = 0.f, v1 = 0.f;
         if (z && k < p) v0 = z[k];
         if (z && k + 1 < p) v1 = z[k + 1];
         if (!isfinite(v0)) v0 = 0.f;
         if (!isfinite(v1)) v1 = 0.f;
-        acc = fma((double)v0, (double)v0, acc);
-        acc = fma((double)v1, (double)v1, acc);
+        {
+            const float p0 = v0 * v0, e0 = fmaf(v0, v0, -p0);
+            const float p1 = v1 * v1, e1 = fmaf(v1, v1, -p1);
+            float s2, f;
+            two_sum(sh, p0, s2, f);
+            sh = s2;
+            sl += f + e0;
+            two_sum(sh, p1, s2, f);
+            sh = s2;
+            sl += f + e1;
+        }
         const float w0 = v0 * c, w1 = v1 * c;
         const __half h0 = __float2half_rn(w0), h1 = __float2half_rn(w1);
         const __half l0 = __float2half_rn(w0 - __half2float(h0));
@@ -119,6 +131,7 @@ __global__ void __launch_bounds__(256) k_split_rows(const Batch bt) {
         *reinterpret_cast<__half2 *>(zh + k) = __halves2half2(h0, h1);
         *reinterpret_cast<__half2 *>(zl + k) = __halves2half2(l0, l1);
     }
+    double acc = (double)sh + (double)sl;
     for (int off = 16; off; off >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, off);
     if (lane == 0) {
         bt.norms[gr] = (float)acc;

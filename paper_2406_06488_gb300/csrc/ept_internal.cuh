@@ -140,6 +140,13 @@ struct Batch {
 // tensor-core contraction work units of a test: chunk x relabeling tile x row half
 __host__ __device__ inline int64_t tc_units(const TestDesc &d) { return d.nchunks * d.MT * 2; }
 
+// Knuth's TwoSum: s = fl(a + b) and the exact rounding error e, a + b = s + e.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
 __device__ __forceinline__ int find_test(const int64_t *pre, int nt, int64_t g) {
     int lo = 0, hi = nt - 1;
     while (lo < hi) {

@@ -230,18 +230,22 @@ __global__ void __launch_bounds__(256) k_masks_lanes(const Batch bt) {
         uint32_t bits = 0;
         const int t0 = w * 32;
         if (need > 0 && t0 < n) {
+            // two Philox calls per step (slots tp .. tp + 3): independent chains for the
+            // scheduler to interleave
 #pragma unroll 2
-            for (int j = 0; j < 16; ++j) {
+            for (int j = 0; j < 16; j += 2) {
                 const int tp = t0 + 2 * j;
-                uint64_t u0, u1;
+                uint64_t u0, u1, u2, u3;
                 philox_words((uint32_t)(tp >> 1), blo, bhi, kx, ky, u0, u1);
-                if (tp < n && (int)mulhi_64x32(u0, (uint32_t)(n - tp)) < need) {
-                    bits |= 1u << (2 * j);
-                    --need;
-                }
-                if (tp + 1 < n && (int)mulhi_64x32(u1, (uint32_t)(n - tp - 1)) < need) {
-                    bits |= 2u << (2 * j);
-                    --need;
+                philox_words((uint32_t)(tp >> 1) + 1u, blo, bhi, kx, ky, u2, u3);
+                const uint64_t uu[4] = {u0, u1, u2, u3};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int ts = tp + q;
+                    if (ts < n && (int)mulhi_64x32(uu[q], (uint32_t)(n - ts)) < need) {
+                        bits |= 1u << (2 * j + q);
+                        --need;
+                    }
                 }
             }
         }
@@ -264,7 +268,9 @@ static int mask_blocks_per_sm() {
 void launch_masks(const Batch &b, int num_sms, int mode, cudaStream_t s) {
     if (b.ncols_total <= 0) return;
     if (mode == DRAW_LANES) {
-        k_masks_lanes<<<(unsigned)((b.ncols_total + 255) / 256), 256, 0, s>>>(b);
+        // few columns: small blocks, so that they spread over the SMs beside the build
+        const int threads = (b.ncols_total >= 1024 * (int64_t)(num_sms > 0 ? num_sms : 1)) ? 256 : 64;
+        k_masks_lanes<<<(unsigned)((b.ncols_total + threads - 1) / threads), threads, 0, s>>>(b);
         return;
     }
     int64_t blocks = (b.ncols_total + 3) / 4;
@@ -451,12 +457,6 @@ void launch_build_simt(const Batch &b, cudaStream_t s) {
 // (hi, lo) with Knuth's TwoSum, an error-free transformation (the rounding error of
 // every addition is carried in lo), then widened to FP64: about twice the FP32
 // precision at FP32 cost.  One CTA per stored block of the batch.
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
 __global__ void __launch_bounds__(256) k_blocksums(const Batch bt) {
     __shared__ double cs[8][64];
     const int64_t gb = blockIdx.x;
@@ -795,32 +795,38 @@ void launch_contract_simt(const Batch &b, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // Final combination (Algorithm 1, statistic and p-value lines): per relabeling
-// column b, Q_b = sum of its partials (four threads per column, every fourth
-// partial each, then a fixed shuffle tree: deterministic), stat_b =
-// sign * (cT Q_b + S~/o^2).  Then, against stat_0 (the identity, evaluated by the
-// same kernels), count stat_b >= stat_0 and near-ties |stat_b - stat_0| <= 1e-5 |stat_0|.
-// A CTA covers 64 columns of one test (the column padding is a multiple of 256).
+// column b, Q_b = sum of its partials, stat_b = sign * (cT Q_b + S~/o^2).  A CTA
+// covers 32 columns of one test (the column padding is a multiple of 256): lane l of
+// each of its 8 warps reads column l of every eighth partial (one coalesced 128-byte
+// row per load), and the 8 warp sums are added in a fixed order (deterministic).
+// Then k_combine_count compares against stat_0 (the identity, evaluated by the same
+// kernels): stat_b >= stat_0 and near-ties |stat_b - stat_0| <= 1e-5 |stat_0|.
 __global__ void __launch_bounds__(256) k_combine_stats(const Batch bt) {
     __shared__ double bSt;
-    const int64_t gc0 = (int64_t)blockIdx.x * 64;
+    __shared__ double ws[8][32];
+    const int64_t gc0 = (int64_t)blockIdx.x * 32;
     const int t = find_test(bt.pre.cols, bt.n_tests, gc0);
-    const TestDesc d = bt.desc[t];
-    if (threadIdx.x < 32) {
+    const TestDesc &d = bt.desc[t];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp == 0) {
         const double St = warp_ordered_sum(bt.Stpart + d.pan0, d.NP);
-        if (threadIdx.x == 0) bSt = St;
+        if (lane == 0) bSt = St;
     }
-    __syncthreads();
-    const int q = threadIdx.x & 3;
-    const int64_t c = gc0 + (threadIdx.x >> 2) - bt.pre.cols[t];
-    const float *part = bt.partial + d.part0;
+    const int64_t c = gc0 + lane - bt.pre.cols[t];
+    const int64_t Bp = d.Bp, nparts = d.nparts;
+    const float *part = bt.partial + d.part0 + c;
     double acc = 0.0;
-    if (c < d.ncols)
-        for (int64_t k = q; k < d.nparts; k += 4) acc += (double)part[k * d.Bp + c];
-    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 2);
-    acc += __shfl_xor_sync(0xFFFFFFFFu, acc, 1);
-    // the tensor-core path accumulates c Q (packed operand scaled by c); 1/c is exact
-    const double inv_c = d.scaled ? 1.0 / (double)packed_scale(bt.ctr[t]) : 1.0;
-    if (c < d.ncols && q == 0) bt.stats[d.col0 + c] = d.sign * (d.cT * (acc * inv_c) + bSt * d.inv_o2);
+    for (int64_t k = warp; k < nparts; k += 8) acc += (double)part[k * Bp];
+    ws[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0) {
+        double q = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) q += ws[w][lane];
+        // the tensor-core path accumulates c Q (packed operand scaled by c); 1/c is exact
+        const double inv_c = d.scaled ? 1.0 / (double)packed_scale(bt.ctr[t]) : 1.0;
+        if (c < d.ncols) bt.stats[d.col0 + c] = d.sign * (d.cT * (q * inv_c) + bSt * d.inv_o2);
+    }
 }
 
 // Counting and outputs: a CTA covers 256 columns of one test.
@@ -848,7 +854,7 @@ __global__ void __launch_bounds__(256) k_combine_count(const Batch bt) {
 
 void launch_combine(const Batch &b, cudaStream_t s) {
     if (b.ncols_total <= 0) return;
-    k_combine_stats<<<(unsigned)(b.ncols_total / 64), 256, 0, s>>>(b);
+    k_combine_stats<<<(unsigned)(b.ncols_total / 32), 256, 0, s>>>(b);
     k_combine_count<<<(unsigned)(b.ncols_total / 256), 256, 0, s>>>(b);
 }
 
