@@ -9,7 +9,10 @@ compiles it with gcc and marshals numpy arrays.  Every function names the passag
 of the paper it follows:
 
 * Eq. 1 (energy distance V-statistic) and Eq. 2 (biased MMD^2), pairwise distances
-  as in Algorithm 3 (Appendix A.1), Gaussian kernel exp(-||x-y||^2 / (2 sigma^2));
+  as in Algorithm 3 (Appendix A.1), Gaussian kernel exp(-||x-y||^2 / (2 sigma^2))
+  or Laplacian kernel exp(-||x-y|| / sigma);
+* the median-heuristic bandwidth (lower median of the pooled pairwise distances)
+  -- ``median_pairs``;
 * Algorithm 4 (standard permutation test: statistics recomputed from permuted
   raw rows) -- ``test_direct``;
 * Algorithm 5 (pre-computed pooled matrix) -- ``test_pooled``;
@@ -36,6 +39,7 @@ _LIB_PATH = os.path.join(_OUT_DIR, "libept_oracle.so")
 
 STAT_ED = 0
 STAT_MMD = 1
+STAT_MMD_LAPLACE = 2
 
 _lib = None
 
@@ -116,6 +120,8 @@ def _load(path=None):
     lib.eo_stat_select_mt.restype = ctypes.c_double
     lib.eo_pooled_moments.argtypes = [f32p, i64, f32p, i64, i64, ctypes.c_int, ctypes.c_double, f64p, f64p]
     lib.eo_pooled_moments.restype = None
+    lib.eo_median_pairs.argtypes = [f32p, i64, f32p, i64, i64]
+    lib.eo_median_pairs.restype = ctypes.c_double
     lib.eo_num_threads.argtypes = []
     lib.eo_num_threads.restype = ctypes.c_int
     _lib = lib
@@ -135,7 +141,9 @@ def _stat_code(stat) -> int:
         return STAT_ED
     if stat in (STAT_MMD, "mmd", "MMD"):
         return STAT_MMD
-    raise ValueError("stat must be 'ed' or 'mmd'")
+    if stat in (STAT_MMD_LAPLACE, "mmd_laplace"):
+        return STAT_MMD_LAPLACE
+    raise ValueError("stat must be 'ed', 'mmd' or 'mmd_laplace'")
 
 
 def num_threads() -> int:
@@ -333,3 +341,14 @@ def exhaustive(X, Y, stat="ed", sigma: float = 1.0, max_count: int = 1_000_000):
     if got != count:
         raise RuntimeError("exhaustive enumeration failed")
     return sel.astype(bool), stats
+
+
+def median_pairs(X, Y) -> float:
+    """Median-heuristic bandwidth: the lower median of the distances between distinct
+    pooled rows (C, FP64)."""
+    lib = _load()
+    X, Y = _f32(X), _f32(Y)
+    v = lib.eo_median_pairs(_ptr(X, ctypes.c_float), X.shape[0], _ptr(Y, ctypes.c_float), Y.shape[0], X.shape[1])
+    if v < 0:
+        raise ValueError("median of pairwise distances needs at least two rows")
+    return float(v)

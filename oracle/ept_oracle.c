@@ -12,7 +12,11 @@
  * What it computes, each function citing the passage it follows:
  *   - the energy-distance V-statistic of Eq. 1 and the biased MMD^2 of Eq. 2,
  *     with Euclidean distances computed pair by pair as in Algorithm 3
- *     (Appendix A.1) and the Gaussian kernel exp(-||x-y||^2 / (2 sigma^2));
+ *     (Appendix A.1) and the Gaussian kernel exp(-||x-y||^2 / (2 sigma^2)), or the
+ *     Laplacian kernel exp(-||x-y|| / sigma) (the other reading of Appendix A.1's
+ *     "exponential of the negative scaled Euclidean distance");
+ *   - the median heuristic for the bandwidth: the lower median of the distances
+ *     between the distinct pairs of the pooled sample;
  *   - the standard permutation test (Algorithm 4, Appendix A.2): every permuted
  *     statistic recomputed from the permuted raw rows;
  *   - the pre-computation test (Algorithm 5, Appendix A.2): one pooled matrix,
@@ -39,7 +43,8 @@
 #endif
 
 #define EO_STAT_ED 0
-#define EO_STAT_MMD 1
+#define EO_STAT_MMD 1          /* Gaussian kernel */
+#define EO_STAT_MMD_LAPLACE 2  /* Laplacian kernel */
 
 /* Test-only mutation switch.  The default build (EO_MUTANT undefined or 0) is the
  * oracle.  The pin tests compile copies with EO_MUTANT = 1..7, each planting one
@@ -195,7 +200,8 @@ int eo_alg2_indices(int64_t nx, int64_t ny, const int64_t *idx_p1, int64_t *out,
 
 /* ------------------------------------------------------------------------- */
 /* Algorithm 3 (Appendix A.1): D = (sum_k (a_k - b_k)^2)^(1/2).  The Gaussian
- * kernel of Appendix A.1 (and Eq. 2) is exp(-(sum_k (a_k - b_k)^2) / (2 sigma^2)). */
+ * kernel of Appendix A.1 (and Eq. 2) is exp(-(sum_k (a_k - b_k)^2) / (2 sigma^2));
+ * the Laplacian kernel is exp(-D / sigma). */
 static double eo_sqdist(const double *a, const double *b, int64_t p)
 {
     double s = 0.0;
@@ -210,6 +216,7 @@ static double eo_entry(const double *a, const double *b, int64_t p, int stat, do
 {
     const double s = eo_sqdist(a, b, p);
     if (stat == EO_STAT_ED) return sqrt(s);
+    if (stat == EO_STAT_MMD_LAPLACE) return exp(-(EO_MUTANT == 8 ? s : sqrt(s)) / sigma);
     return exp(-s / ((EO_MUTANT == 3 ? 1.0 : 2.0) * sigma * sigma));
 }
 
@@ -631,4 +638,39 @@ int eo_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------- */
+/* Median heuristic for the kernel bandwidth (a reading: the paper leaves sigma to
+ * the user): the lower median -- element floor((N - 1) / 2) of the sorted list --
+ * of the N = n (n - 1) / 2 Euclidean distances between distinct pooled rows
+ * (Algorithm 3 entries).  Taken over the pooled sample it does not depend on the
+ * split into x and y, so every relabeling sees the same bandwidth.  Returns -1 when
+ * n < 2 or on allocation failure. */
+static int eo_cmp_double(const void *a, const void *b)
+{
+    const double x = *(const double *)a, y = *(const double *)b;
+    return (x > y) - (x < y);
+}
+
+double eo_median_pairs(const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p)
+{
+    const int64_t n = nx + ny;
+    if (n < 2) return -1.0;
+    double *w = eo_pool(X, nx, Y, ny, p);
+    const int64_t N = n * (n - 1) / 2;
+    double *d = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!w || !d) {
+        free(w);
+        free(d);
+        return -1.0;
+    }
+    int64_t k = 0;
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = i + 1; j < n; ++j) d[k++] = sqrt(eo_sqdist(w + i * p, w + j * p, p));
+    qsort(d, (size_t)N, sizeof(double), eo_cmp_double);
+    const double med = d[(N - 1) / 2];
+    free(w);
+    free(d);
+    return med;
 }

@@ -18,6 +18,7 @@ MUTANTS = {
     6: ("block swap reads D_XY untransposed",
         [lambda: pins.test_block_swap_equals_recomputation_on_worked_example("ed")]),
     7: ("p-value without the +1 terms", [pins.test_pvalue_definition]),
+    8: ("Laplacian kernel exp(-d^2/sigma)", [pins.test_laplace_kernel_matches_library_routine]),
 }
 
 

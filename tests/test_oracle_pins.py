@@ -258,3 +258,58 @@ def test_permutation_mean_closed_form():
     res = oracle.permutation_test(X, Y, B=B, seed=9, stat="ed", method="blocks")
     st = res["stats"]
     assert abs(st.mean() - want) <= 5 * st.std() / math.sqrt(B)
+
+
+# ------------------------------------------- Laplacian kernel and median bandwidth
+def test_laplace_kernel_matches_library_routine():
+    # exp(-||x - y|| / sigma) against scipy's distances
+    X, Y = _rand_pair(30, 20, 7, seed=13)
+    ref = cdist(X.astype(np.float64), Y.astype(np.float64))
+    sig = 1.7
+    assert np.allclose(oracle.block_matrix(X, Y, "mmd_laplace", sig), np.exp(-ref / sig), rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("nx,ny,p", [(7, 11, 3), (40, 25, 6), (1, 5, 4)])
+def test_laplace_three_implementations_agree(nx, ny, p):
+    X, Y = _rand_pair(nx, ny, p, seed=nx * 100 + ny, shift=0.3)
+    sel = oracle.perm_select(9, nx, ny, 0, 30)
+    a = oracle.test_direct(X, Y, sel, "mmd_laplace", 1.5)
+    b = oracle.test_pooled(X, Y, sel, "mmd_laplace", 1.5)
+    c = oracle.test_blocks(X, Y, sel, "mmd_laplace", 1.5)
+    scale = np.abs(a).max() + 1e-300
+    assert np.abs(a - b).max() <= 1e-12 * scale and np.abs(a - c).max() <= 1e-12 * scale
+
+
+def test_laplace_mmd_properties():
+    # the Laplacian kernel is positive definite: MMD^2 >= 0, symmetric, zero for
+    # identical samples; invariant to translations and rotations; (cX, cY, c sigma)
+    # gives the same value
+    X, Y = _rand_pair(25, 31, 5, seed=18, shift=0.5)
+    X64, Y64 = X.astype(np.float64), Y.astype(np.float64)
+    m = oracle.stat_direct(X64, Y64, "mmd_laplace", 2.0)
+    assert m > 0
+    assert abs(oracle.stat_direct(Y64, X64, "mmd_laplace", 2.0) - m) <= 1e-12 * m
+    assert abs(oracle.stat_direct(X64, X64, "mmd_laplace", 2.0)) <= 1e-13
+    q, _ = np.linalg.qr(np.random.default_rng(2).standard_normal((5, 5)))
+    assert abs(oracle.stat_direct(X64 @ q + 1.0, Y64 @ q + 1.0, "mmd_laplace", 2.0) - m) <= 1e-11 * m
+    assert abs(oracle.stat_direct(3 * X64, 3 * Y64, "mmd_laplace", 6.0) - m) <= 1e-12 * m
+
+
+def test_median_pairs_hand_examples():
+    # pooled points 0, 1, 3, 7 on a line: distances 1, 3, 7, 2, 6, 4 -> sorted
+    # 1 2 3 4 6 7, lower median 3; points 0, 1, 3: distances 1, 3, 2 -> median 2
+    assert oracle.median_pairs(np.array([[0.0], [1.0]]), np.array([[3.0], [7.0]])) == 3.0
+    assert oracle.median_pairs(np.array([[0.0], [1.0]]), np.array([[3.0]])) == 2.0
+
+
+def test_median_pairs_matches_library_routine_and_ignores_the_split():
+    from scipy.spatial.distance import pdist
+    X, Y = _rand_pair(23, 18, 4, seed=21, shift=0.4)
+    d = np.sort(pdist(np.concatenate([X, Y]).astype(np.float64)))
+    want = d[(d.size - 1) // 2]
+    assert abs(oracle.median_pairs(X, Y) - want) <= 1e-14 * want
+    W = np.concatenate([X, Y])
+    perm = np.random.default_rng(3).permutation(W.shape[0])
+    W = W[perm]
+    assert oracle.median_pairs(W[:10], W[10:]) == oracle.median_pairs(X, Y)
+    assert oracle.median_pairs(Y, X) == oracle.median_pairs(X, Y)
