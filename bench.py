@@ -47,7 +47,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="highdim", choices=["highdim", "mmd", "small", "batched", "serving"])
+    ap.add_argument("--workload", default="highdim", choices=["highdim", "mmd", "mmd_laplace", "mmd_median", "small",
+                                                                "batched", "serving"])
     ap.add_argument("--tests", type=int, default=512, help="batched: tests per step")
     ap.add_argument("--rates", default="10,100,1000", help="serving: request rates (1/s) swept")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests per rate (at most)")
@@ -158,18 +159,27 @@ def _spec(name):
     return workloads.NAMED[name]
 
 
-def _cpu_baseline(spec, X, Y, budget_s=20.0):
+def _oracle_sigma(spec, gpu_sigma=None):
+    """Bandwidth for the oracle's timing runs: the workload's, or for the median
+    heuristic the value the GPU selected (else sqrt(p))."""
+    if spec.sigma > 0:
+        return spec.sigma
+    return gpu_sigma if gpu_sigma else float(np.sqrt(spec.p))
+
+
+def _cpu_baseline(spec, X, Y, budget_s=20.0, sigma=None):
     """The FP64 oracle (direct recomputation of each permuted statistic from the
     permuted raw rows, Algorithm 4), timed on a bounded sample of relabelings."""
     import oracle
     oracle.build()
+    sigma = _oracle_sigma(spec, sigma)
     cores = oracle.num_threads()
     sel = oracle.perm_select(spec.seed, spec.nx, spec.ny, 1, 64)
     t0 = time.perf_counter()
     done = 0
     vals = []
     while done < 64:
-        vals.append(oracle.stat_select(X, Y, sel[done], spec.stat, spec.sigma))
+        vals.append(oracle.stat_select(X, Y, sel[done], spec.stat, sigma))
         done += 1
         if time.perf_counter() - t0 > budget_s:
             break
@@ -177,7 +187,7 @@ def _cpu_baseline(spec, X, Y, budget_s=20.0):
     return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": "%d relabelings (draws 1..%d) of the %s workload, each statistic recomputed in FP64 from "
                       "the permuted raw rows (Algorithm 4), threads splitting the rows; %.1f s"
-                      % (done, done, "ED nx=%d ny=%d p=%d" % (spec.nx, spec.ny, spec.p), dt)}, vals
+                      % (done, done, "%s nx=%d ny=%d p=%d" % (spec.stat.upper(), spec.nx, spec.ny, spec.p), dt)}, vals
 
 
 def run_reference(args):
@@ -194,12 +204,13 @@ def run_reference(args):
     oracle.build()
     cores = oracle.num_threads()
     sel = oracle.perm_select(spec.seed, spec.nx, spec.ny, 1, args.warmup + args.steps)
+    sigma = _oracle_sigma(spec)
     for k in range(args.warmup):
-        oracle.stat_select(X, Y, sel[k], spec.stat, spec.sigma)
+        oracle.stat_select(X, Y, sel[k], spec.stat, sigma)
     times = []
     for k in range(args.steps):
         t0 = time.perf_counter()
-        oracle.stat_select(X, Y, sel[args.warmup + k], spec.stat, spec.sigma)
+        oracle.stat_select(X, Y, sel[args.warmup + k], spec.stat, sigma)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
     value = args.steps / tot
@@ -336,7 +347,7 @@ def run_ours(args):
     mma_flops = 2.0 * 2.0 * stored * cols
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
-        cpu, _ = _cpu_baseline(spec, X, Y)
+        cpu, _ = _cpu_baseline(spec, X, Y, sigma=last.sigma)
     sorted_ms = sorted(step_ms)
     p99 = sorted_ms[min(len(sorted_ms) - 1, int(np.ceil(0.99 * len(sorted_ms))) - 1)]
     psorted = sorted(plain_ms)
@@ -346,7 +357,8 @@ def run_ours(args):
         "dtype": "f16", "data": "synthetic",
         "config": {"workload": "highdim ED test: nx=%d ny=%d p=%d B=%d, X~N(0,I), Y~N(mu,I) mu=0.05 on first 50 "
                                "coords" % (spec.nx, spec.ny, spec.p, spec.B) if args.workload == "highdim"
-                   else "%s: %s nx=%d ny=%d p=%d B=%d" % (args.workload, spec.stat, spec.nx, spec.ny, spec.p, spec.B),
+                   else "%s: %s nx=%d ny=%d p=%d B=%d sigma=%s" % (args.workload, spec.stat, spec.nx, spec.ny, spec.p,
+                                                                 spec.B, "median" if spec.sigma < 0 else spec.sigma),
                    "precision": "blocks FP32, contraction FP16 hi+lo split on tcgen05, FP32 accumulate, FP64 "
                                 "combine", "l2": "flushed between steps (256 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -367,7 +379,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": int((spec.B + 1) * 8 + 48), "steps": args.e2e_steps},
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clocks,
-        "result": {"observed": last.observed, "p_value": last.p_value, "n_near_tie": last.n_near_tie},
+        "result": {"observed": last.observed, "p_value": last.p_value, "n_near_tie": last.n_near_tie,
+                   "sigma": last.sigma},
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu

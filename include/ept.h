@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define EPT_ABI_VERSION 1
+#define EPT_ABI_VERSION 2
 
 typedef enum {
     EPT_OK = 0,
@@ -56,16 +56,28 @@ typedef enum {
 } ept_status;
 
 typedef enum {
-    EPT_STAT_ED = 0,         /* energy distance V-statistic, Eq. 1 */
-    EPT_STAT_MMD_GAUSS = 1   /* biased MMD^2, Eq. 2, k(x,y) = exp(-||x-y||^2 / (2 sigma^2)) */
+    EPT_STAT_ED = 0,           /* energy distance V-statistic, Eq. 1 */
+    EPT_STAT_MMD_GAUSS = 1,    /* biased MMD^2, Eq. 2, k(x,y) = exp(-||x-y||^2 / (2 sigma^2)) */
+    EPT_STAT_MMD_LAPLACE = 2   /* biased MMD^2, Eq. 2, k(x,y) = exp(-||x-y|| / sigma): the other
+                                  reading of Appendix A.1's "exponential of the negative scaled
+                                  Euclidean distance" */
 } ept_stat;
+
+/* sigma value selecting the median heuristic (MMD statistics): the bandwidth is the
+   lower median (element floor((N-1)/2) in sorted order) of the N = n(n-1)/2
+   distances between distinct pooled rows, found on the device by an exact radix
+   selection; it does not depend on the split into x and y, so every relabeling
+   sees the same kernel.  Returned in ept_result.sigma. */
+#define EPT_SIGMA_MEDIAN (-1.0)
 
 typedef enum {
     /* plain path: FP32 SIMT block build and FP32 SIMT permutation contraction,
        one launch per phase, no CUDA graph: the comparison baseline */
     EPT_PREC_PLAIN_FP32 = 0,
-    /* tuned path: blocks stored FP32, the contraction s' C s on tcgen05 tensor cores
-       with C split into BF16 hi + lo parts accumulated in FP32 in tensor memory */
+    /* tuned path: blocks built on tcgen05 tensor cores (split-FP16 Gram) and stored
+       FP32; the contraction s' C s on tcgen05 with C scaled by a power of two and
+       split into FP16 hi + lo parts accumulated in FP32 in tensor memory (the name
+       is kept from the first version, which split into BF16) */
     EPT_PREC_SPLIT_BF16 = 1
 } ept_precision;
 
@@ -83,6 +95,8 @@ typedef struct {
     double ms_masks;      /* device time of the relabeling draws alone */
     double ms_contract;   /* device time of the contraction kernel alone (CUDA events
                              recorded on the stream it is launched on) */
+    double sigma;         /* kernel bandwidth used (the median heuristic's value when
+                             EPT_SIGMA_MEDIAN was given); 0 for ED */
 } ept_result;
 
 /* Library ABI version (EPT_ABI_VERSION of the build). */
@@ -104,12 +118,14 @@ ept_status ept_destroy(ept_ctx *ctx);
 size_t ept_estimate_bytes(int64_t nx, int64_t ny, int64_t p, int64_t B, int prec);
 
 /* One permutation test (Algorithm 1).
-   X: nx*p floats, Y: ny*p floats (row-major).  stat: ept_stat.  sigma: Gaussian
-   bandwidth, > 0 for MMD, ignored for ED.  B >= 0 permutations; draw b (1..B) of the
+   X: nx*p floats, Y: ny*p floats (row-major).  stat: ept_stat.  sigma: kernel
+   bandwidth for the MMD statistics, > 0 or EPT_SIGMA_MEDIAN; ignored for ED.
+   B >= 0 permutations; draw b (1..B) of the
    permutation stream of `seed` (ept_perm_masks) is relabeling b.
    perm_stats: B doubles (may be NULL), perm_stats[b-1] = statistic of draw b.
    out: host struct, required.  Errors: EPT_EINVAL for nx < 1, ny < 1, p < 1, B < 0,
-   sigma <= 0 with MMD, non-finite data; EPT_ENOMEM over budget.
+   any other sigma <= 0 with MMD, non-finite data, a median bandwidth of 0 (more than
+   half of the pooled pairs coincide); EPT_ENOMEM over budget.
    A repeated call with the same shapes replays the CUDA graph captured by the
    first (EPT_OPT_GRAPHS); then only out->ms_total is timed (the per-phase times
    are filled in when graphs are off). */
@@ -134,7 +150,7 @@ typedef struct {
     const float *Y;        /* ny * p floats, row-major */
     int64_t nx, ny, p;
     int stat;              /* ept_stat */
-    double sigma;          /* Gaussian bandwidth (MMD) */
+    double sigma;          /* kernel bandwidth (MMD): > 0 or EPT_SIGMA_MEDIAN */
     int64_t B;             /* permutations */
     uint64_t seed;         /* permutation-stream seed */
     double *perm_stats;    /* B doubles or NULL */

@@ -71,9 +71,10 @@ ept_status validate(int64_t nx, int64_t ny, int64_t p, int stat, double sigma, i
     if (nx < 1 || ny < 1) return fail(EPT_EINVAL, "nx and ny must be >= 1 (got %lld, %lld)", (long long)nx, (long long)ny);
     if (p < 1) return fail(EPT_EINVAL, "p must be >= 1 (got %lld)", (long long)p);
     if (nx + ny > (int64_t)1 << 22) return fail(EPT_EINVAL, "nx + ny = %lld exceeds 2^22", (long long)(nx + ny));
-    if (stat != EPT_STAT_ED && stat != EPT_STAT_MMD_GAUSS) return fail(EPT_EINVAL, "unknown statistic %d", stat);
-    if (stat == EPT_STAT_MMD_GAUSS && !(sigma > 0.0 && std::isfinite(sigma)))
-        return fail(EPT_EINVAL, "MMD needs a finite bandwidth sigma > 0");
+    if (stat != EPT_STAT_ED && stat != EPT_STAT_MMD_GAUSS && stat != EPT_STAT_MMD_LAPLACE)
+        return fail(EPT_EINVAL, "unknown statistic %d", stat);
+    if (stat != EPT_STAT_ED && sigma != EPT_SIGMA_MEDIAN && !(sigma > 0.0 && std::isfinite(sigma)))
+        return fail(EPT_EINVAL, "MMD needs a finite bandwidth sigma > 0 or EPT_SIGMA_MEDIAN");
     if (prec != EPT_PREC_PLAIN_FP32 && prec != EPT_PREC_SPLIT_BF16) return fail(EPT_EINVAL, "unknown precision %d", prec);
     return EPT_OK;
 }
@@ -90,6 +91,8 @@ struct Plan {
     std::vector<Chunk> chunks;
     std::vector<int64_t> sched, sched_off;   // contraction schedule: units of CTA c = sched[sched_off[c] ..)
     bool user_masks = false;                 // some test brings its own relabelings
+    bool any_median = false;                 // some test takes its bandwidth from the median heuristic
+    size_t off_sel_hist = 0;
     int tc_grid = 0;                         // contraction CTAs
     std::vector<size_t> in_off;       // per test: byte offset of its X (then Y, then masks) in the input region
     int64_t nrows = 0, npan = 0, ncols_pad = 0, nunits = 0, nsimt = 0, nblk = 0, nmask = 0, nchunk = 0, npart = 0,
@@ -108,7 +111,11 @@ struct Plan {
 void set_test_params(TestDesc &d, const TestSpec &s) {
     d.stat = s.stat;
     d.seed = s.seed;
-    d.neg_inv_2s2 = (s.stat == EPT_STAT_ED) ? 0.f : (float)(-1.0 / (2.0 * s.sigma * s.sigma));
+    d.median = (s.stat != EPT_STAT_ED && s.sigma == EPT_SIGMA_MEDIAN) ? 1 : 0;
+    // the build writes kernel values directly unless the bandwidth is still unknown
+    d.kern = (s.stat == EPT_STAT_ED || d.median) ? 0 : s.stat;
+    d.neg_inv_2s2 = (d.kern == EPT_STAT_MMD_GAUSS) ? (float)(-1.0 / (2.0 * s.sigma * s.sigma)) : 0.f;
+    d.inv_sigma = (d.kern == EPT_STAT_MMD_LAPLACE) ? (float)(1.0 / s.sigma) : 0.f;
     d.sign = (s.stat == EPT_STAT_ED) ? -1.0 : 1.0;
 }
 
@@ -229,6 +236,7 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
         push_pre(P.pre_units, tc_units(d));
         push_pre(P.pre_simt, d.nchunks * 2 * (d.Bp / 64));
         P.user_masks |= s.user_masks != nullptr;
+        P.any_median |= d.median != 0;
         P.in_off.push_back(in_bytes);
         if (host_in) {
             in_bytes += align_up((size_t)d.nx * d.p * 4, 256) + align_up((size_t)d.ny * d.p * 4, 256);
@@ -284,6 +292,7 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
     P.off_stats = take((size_t)P.nstats * 8);
     P.off_observed = take((size_t)P.n_tests * 8);
     P.off_ctr = take(sizeof(Counters) * P.n_tests);
+    P.off_sel_hist = P.any_median ? take((size_t)P.n_tests * 2048 * 4) : 0;
     P.total = o;
 }
 
@@ -562,6 +571,7 @@ Batch device_view(ept_ctx *c, const Plan &P) {
     b.observed = (double *)(A + P.off_observed);
     b.maskT = (uint32_t *)(A + P.off_maskT);
     b.ctr = (Counters *)(A + P.off_ctr);
+    b.sel_hist = P.any_median ? (uint32_t *)(A + P.off_sel_hist) : nullptr;
     return b;
 }
 
@@ -585,6 +595,7 @@ ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed,
     CK(cudaMemcpyAsync(A, pin + S.tables, P.tab_bytes, cudaMemcpyHostToDevice, s));
     if (with_inputs && (st = enqueue_inputs(c, s)) != EPT_OK) return st;
     CK(cudaMemsetAsync(b.ctr, 0, sizeof(Counters) * P.n_tests, s));
+    if (P.any_median) CK(cudaMemsetAsync(b.sel_hist, 0, (size_t)P.n_tests * 2048 * 4, s));
     CK(cudaEventRecord(c->ev[1], s));
 
     // relabelings on the side stream, beside the block build
@@ -612,6 +623,7 @@ ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed,
         launch_norms(b, s);
         launch_build_simt(b, s);
     }
+    launch_median_select(b, s);
     launch_blocksums(b, s);
     launch_rowsum_reduce(b, s);
     launch_center(b, s);
@@ -652,8 +664,20 @@ struct TestError {
     std::string msg;
 };
 
+float median_sigma(const Counters &k) {
+    float v;
+    memcpy(&v, &k.sel_prefix, 4);
+    return v;
+}
+
 ept_status test_error(const Plan &P, const Counters *ctr, int t) {
     if (ctr[t].nonfinite) return fail(EPT_EINVAL, "test %d: X or Y holds NaN or Inf", t);
+    if (P.desc[t].median) {
+        const float sg = median_sigma(ctr[t]);
+        if (!(sg > 0.f) || !std::isfinite(sg))
+            return fail(EPT_EINVAL, "test %d: the median-heuristic bandwidth is %g (more than half of the pooled "
+                                    "pairs coincide)", t, (double)sg);
+    }
     if (ctr[t].bad_mask)
         return fail(EPT_EINVAL, "test %d: %llu relabeling(s) do not have exactly nx = %lld members among the n rows", t,
                     (unsigned long long)ctr[t].bad_mask, (long long)P.desc[t].nx);
@@ -691,6 +715,7 @@ ept_status collect(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &specs
         r.n_near_tie = (int64_t)ctr[t].n_near;
         r.n_fixup = (int64_t)ctr[t].n_fixup;
         r.p_value = (1.0 + (double)r.n_ge) / (1.0 + (double)d.B);
+        r.sigma = d.median ? (double)median_sigma(ctr[t]) : (d.stat == EPT_STAT_ED ? 0.0 : specs[t].sigma);
         r.ms_build = ms_build;
         r.ms_perm = ms_perm;
         r.ms_total = ms_total;
@@ -713,6 +738,7 @@ std::vector<int64_t> shape_key(const std::vector<TestSpec> &specs, int prec, boo
         k.push_back(s.B);
         k.push_back(s.user_masks ? 1 : 0);
         k.push_back(s.perm_stats ? 1 : 0);
+        k.push_back(s.stat != EPT_STAT_ED && s.sigma == EPT_SIGMA_MEDIAN ? 1 : 0);   // selection buffers
     }
     return k;
 }
@@ -1319,6 +1345,12 @@ ept_status ept_build_blocks(ept_ctx *c, const float *X, int64_t nx, const float 
     } else {
         launch_norms(b, s);
         launch_build_simt(b, s);
+    }
+    if (P.any_median) {
+        // median bandwidth: select it, then the block-sum pass turns distances into kernel values
+        CK(cudaMemsetAsync(b.sel_hist, 0, (size_t)2048 * 4, s));
+        launch_median_select(b, s);
+        launch_blocksums(b, s);
     }
     float *dout = on_device ? D_out : (float *)(A + P.total);
     launch_expand_blocks(b.D, nx + ny, P.desc[0].NKB, dout, s);

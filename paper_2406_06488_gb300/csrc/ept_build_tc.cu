@@ -12,8 +12,9 @@
 // the entries are about as accurate as an FP32 Gram), and the epilogue multiplies
 // by 1/c_i and 1/c_j (exact).
 // The epilogue forms d^2, recomputes cancellation-prone near-duplicate pairs
-// (d^2 < tau (||z_i||^2 + ||z_j||^2)) directly in FP64, applies sqrt (ED) or
-// exp(-d^2 / (2 sigma^2)) (MMD), forces the diagonal to 0 / 1, zeroes padding, and
+// (d^2 < tau (||z_i||^2 + ||z_j||^2)) directly in FP64, applies sqrt (distances),
+// exp(-d^2 / (2 sigma^2)) (Gaussian) or exp(-d / sigma) (Laplacian), forces the
+// diagonal to 0 / 1, zeroes padding, and
 // writes the FP32 entries into the packed upper blocks.
 //
 // Tile = 128 rows (half of a 256-row panel I) x 256 columns (panel J >= I, four
@@ -137,6 +138,33 @@ __global__ void __launch_bounds__(256) k_split_rows(const Batch bt) {
         bt.norms[gr] = (float)acc;
         bt.iscale[gr] = ldexpf(1.f, -k2);
     }
+}
+
+// One row's 32 entries of a column group from the Gram accumulator v (scaled by
+// c_i c_j): d^2 = n_i + n_j - 2 G_ij, the entry for kernel kind KERN (0 distance,
+// 1 Gaussian, 2 Laplacian; the approximate square root is within 2^-22 of the
+// exact one, below the split Gram's own error), and the bit mask of the entries
+// that need the FP64 recomputation (d^2 < tau (n_i + n_j)).
+template <int KERN>
+__device__ __forceinline__ uint32_t group_entries(const uint32_t (&v)[32], const float2 *cg, float ni, float si,
+                                                  float tau, float neg_inv_2s2, float inv_sigma, float (&out)[32]) {
+    uint32_t fix = 0;
+#pragma unroll
+    for (int e = 0; e < 32; ++e) {
+        const float2 cj = cg[e];
+        const float gij = (__uint_as_float(v[e]) * si) * cj.y;   // exact rescaling
+        const float sn = ni + cj.x;
+        const float d2 = fmaxf(0.f, sn - 2.f * gij);
+        fix |= (d2 < tau * sn) ? (1u << e) : 0u;
+        if (KERN == 1) {
+            out[e] = expf(d2 * neg_inv_2s2);
+        } else {
+            float dist;
+            asm("sqrt.approx.f32 %0, %1;" : "=f"(dist) : "f"(d2));
+            out[e] = (KERN == 0) ? dist : expf(-dist * inv_sigma);
+        }
+    }
+    return fix;
 }
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
@@ -286,9 +314,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const TestDesc &d = bt.desc[tile.t];
             const int64_t n = d.n, p = d.p, NKB = d.NKB, nx = d.nx;
             const float *X = d.X, *Y = d.Y;
-            const int stat = d.stat;
-            const float neg_inv_2s2 = d.neg_inv_2s2, tau = d.tau;
-            const float diag_val = (stat == 0) ? 0.f : 1.f;
+            const int kern = d.kern;
+            const float neg_inv_2s2 = d.neg_inv_2s2, inv_sigma = d.inv_sigma, tau = d.tau;
+            const float diag_val = (kern == 0) ? 0.f : 1.f;
             const float *norms = bt.norms + d.row0, *inv_scale = bt.iscale + d.row0;
             float *Dblk = bt.D + (d.blk0 + blk_index(tile.I, (int64_t)tile.J * KB_PER_PANEL, NKB)) * PANEL * KB;
             unsigned fixups = 0;
@@ -312,19 +340,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 tmem_ld32(tbase + (uint32_t)(g * 32), v);
                 const int64_t j0 = (int64_t)tile.J * PANEL + g * 32;
                 float out[32];
-                uint32_t fix = 0;
-#pragma unroll
-                for (int e = 0; e < 32; ++e) {
-                    const float2 cj = colv[g * 32 + e];
-                    const float gij = (__uint_as_float(v[e]) * si) * cj.y;   // exact rescaling
-                    const float sn = ni + cj.x;
-                    const float d2 = fmaxf(0.f, sn - 2.f * gij);
-                    fix |= (d2 < tau * sn) ? (1u << e) : 0u;
-                    float val;
-                    if (stat == 0) asm("sqrt.approx.f32 %0, %1;" : "=f"(val) : "f"(d2));
-                    else val = expf(d2 * neg_inv_2s2);
-                    out[e] = val;
-                }
+                const float2 *cg = colv + g * 32;
+                uint32_t fix = (kern == 0)   ? group_entries<0>(v, cg, ni, si, tau, neg_inv_2s2, inv_sigma, out)
+                               : (kern == 1) ? group_entries<1>(v, cg, ni, si, tau, neg_inv_2s2, inv_sigma, out)
+                                             : group_entries<2>(v, cg, ni, si, tau, neg_inv_2s2, inv_sigma, out);
                 // padding rows / columns hold 0; the diagonal is exactly 0 (ED) / 1 (MMD)
                 const uint32_t jvalid =
                     (j0 >= n) ? 0u : ((j0 + 32 <= n) ? 0xFFFFFFFFu : ((1u << (uint32_t)(n - j0)) - 1u));
@@ -356,7 +375,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                         sq = fma(df, df, sq);
                     }
                     ++fixups;
-                    dst[e] = (stat == 0) ? (float)sqrt(sq) : (float)exp(sq * (double)neg_inv_2s2);
+                    dst[e] = (float)entry_from_d2(sq, kern, neg_inv_2s2, inv_sigma);
                 }
             }
             fence_before();

@@ -61,7 +61,8 @@ struct Counters {
     unsigned int max_d_bits;         // max |D_ij| over the stored blocks (FP32 bits; non-negative values
     unsigned int max_u_bits;         //   order like their bit patterns), max |u_i|,
     unsigned int max_dc_bits;        //   max |dcorr_i|: they bound |C| for the FP16 scale of the packing
-    unsigned int pad_;
+    unsigned int sel_prefix;         // median heuristic: radix-selection prefix, then the median's bits
+    unsigned long long sel_k;        //   rank still to find within the prefix
 };
 
 // Power-of-two scale c of a test's packed contraction operand, from the bound
@@ -105,6 +106,10 @@ struct TestDesc {
     int32_t stat, comp, kblocks, nwu;
     int32_t scaled, pad_;            // scaled: the partials carry the packing scale (tensor-core path)
     float neg_inv_2s2, tau;
+    float inv_sigma;                 // Laplacian kernel: 1 / sigma
+    int32_t kern;                    // entries the build writes: 0 distance, 1 Gaussian, 2 Laplacian kernel
+    int32_t median;                  // bandwidth from the median heuristic (build distances, select, transform)
+    int32_t pad2_;
     double cT, inv_o2, sign, kappa, inv_n, inv_2n2;
 };
 
@@ -135,10 +140,20 @@ struct Batch {
     double *rowpart, *colpart, *r, *Spart, *dcorr, *Upart, *Stpart, *stats, *observed;
     uint32_t *maskT;
     Counters *ctr;
+    uint32_t *sel_hist;                  // median heuristic: 2048 bins per test (null if no test needs it)
 };
 
 // tensor-core contraction work units of a test: chunk x relabeling tile x row half
 __host__ __device__ inline int64_t tc_units(const TestDesc &d) { return d.nchunks * d.MT * 2; }
+
+// Entry of the pooled matrix from a squared distance d2 (FP32 or, for the fix-up of
+// cancellation-prone pairs, FP64): the distance (Algorithm 3), the Gaussian kernel
+// exp(-d2 / (2 sigma^2)) or the Laplacian kernel exp(-sqrt(d2) / sigma) (Appendix A.1).
+__device__ __forceinline__ double entry_from_d2(double d2, int kern, float neg_inv_2s2, float inv_sigma) {
+    if (kern == 0) return sqrt(d2);
+    if (kern == 1) return exp(d2 * (double)neg_inv_2s2);
+    return exp(-sqrt(d2) * (double)inv_sigma);
+}
 
 // Knuth's TwoSum: s = fl(a + b) and the exact rounding error e, a + b = s + e.
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
@@ -160,7 +175,8 @@ __device__ __forceinline__ int find_test(const int64_t *pre, int nt, int64_t g) 
 // ---- launchers (ept_kernels.cu) ----
 void launch_norms(const Batch &b, cudaStream_t s);                       // plain path: norms + finite check
 void launch_build_simt(const Batch &b, cudaStream_t s);
-void launch_blocksums(const Batch &b, cudaStream_t s);
+void launch_blocksums(const Batch &b, cudaStream_t s);   // median-heuristic tests: kernel transform first
+void launch_median_select(const Batch &b, cudaStream_t s);   // exact radix selection of the median distance
 void launch_rowsum_reduce(const Batch &b, cudaStream_t s);
 void launch_center(const Batch &b, cudaStream_t s);
 void launch_pack(const Batch &b, bool split, cudaStream_t s);   // split: FP16 hi/lo (tensor-core path)

@@ -355,8 +355,9 @@ void launch_norms(const Batch &b, cudaStream_t s) {
 // K-loop over p in steps of 16 staged through shared memory.
 // Epilogue: d2 = max(0, n_i + n_j - 2 g_ij); a pair with d2 < tau (n_i + n_j)
 // (cancellation-prone near-duplicate) is recomputed directly as sum (x - y)^2 in
-// FP64; then sqrt (ED) or exp(-d2 / (2 sigma^2)) (MMD); the diagonal is exactly 0
-// (ED) or 1 (MMD); padded rows and columns are 0.
+// FP64; then the distance, exp(-d2 / (2 sigma^2)) (Gaussian) or exp(-d / sigma)
+// (Laplacian); the diagonal is exactly 0 (distances) or 1 (kernels); padded rows and
+// columns are 0.
 __global__ void __launch_bounds__(256) k_build_simt(const Batch bt) {
     __shared__ float As[16][128 + 4];
     __shared__ float Bs[16][64 + 4];
@@ -406,8 +407,8 @@ __global__ void __launch_bounds__(256) k_build_simt(const Batch bt) {
         }
         __syncthreads();
     }
-    const float neg = d.neg_inv_2s2, tau = d.tau;
-    const int stat = d.stat;
+    const float neg = d.neg_inv_2s2, inv_sigma = d.inv_sigma, tau = d.tau;
+    const int kern = d.kern;
     unsigned fixups = 0;
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
@@ -419,7 +420,7 @@ __global__ void __launch_bounds__(256) k_build_simt(const Batch bt) {
             float v = 0.f;
             if (i < n && j < n) {
                 if (i == j) {
-                    v = (stat == 0) ? 0.f : 1.f;
+                    v = (kern == 0) ? 0.f : 1.f;
                 } else {
                     const float ni = __ldg(bt.norms + d.row0 + i), nj = __ldg(bt.norms + d.row0 + j);
                     const float d2 = fmaxf(0.f, ni + nj - 2.f * acc[a][c]);
@@ -431,9 +432,9 @@ __global__ void __launch_bounds__(256) k_build_simt(const Batch bt) {
                             s = fma(df, df, s);
                         }
                         ++fixups;
-                        v = (stat == 0) ? (float)sqrt(s) : (float)exp(s * (double)neg);
+                        v = (float)entry_from_d2(s, kern, neg, inv_sigma);
                     } else {
-                        v = (stat == 0) ? sqrtf(d2) : expf(d2 * neg);
+                        v = (kern == 0) ? sqrtf(d2) : (kern == 1) ? expf(d2 * neg) : expf(-sqrtf(d2) * inv_sigma);
                     }
                 }
             }
@@ -461,7 +462,32 @@ __global__ void __launch_bounds__(256) k_blocksums(const Batch bt) {
     __shared__ double cs[8][64];
     const int64_t gb = blockIdx.x;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const float *base = bt.D + gb * (int64_t)(PANEL * KB);
+    float *base = bt.D + gb * (int64_t)(PANEL * KB);
+    {
+        // median-heuristic tests: the build wrote distances; now that the bandwidth is
+        // known, turn them into kernel values in place (padding stays 0)
+        const BlkInfo bi = bt.blk[gb];
+        const TestDesc &d = bt.desc[bi.t];
+        if (d.median) {
+            const float sigma = __uint_as_float(bt.ctr[bi.t].sel_prefix);
+            const float neg = -1.f / (2.f * sigma * sigma), inv = 1.f / sigma;
+            const int64_t i = (int64_t)bi.I * PANEL + t, n = d.n;
+            const bool gauss = d.stat == 1;
+            float4 *row = reinterpret_cast<float4 *>(base + (int64_t)t * KB);
+#pragma unroll 4
+            for (int q = 0; q < 16; ++q) {
+                float4 v = row[q];
+                float e4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int64_t j = (int64_t)bi.kb * KB + 4 * q + k;
+                    if (i < n && j < n) e4[k] = gauss ? expf(e4[k] * e4[k] * neg) : expf(-e4[k] * inv);
+                }
+                row[q] = make_float4(e4[0], e4[1], e4[2], e4[3]);
+            }
+            __syncthreads();
+        }
+    }
     // row sums: thread t owns row t (64 contiguous values, no cross-thread traffic)
     {
         const float4 *row = reinterpret_cast<const float4 *>(base + (int64_t)t * KB);
@@ -522,6 +548,108 @@ __global__ void __launch_bounds__(256) k_blocksums(const Batch bt) {
 void launch_blocksums(const Batch &b, cudaStream_t s) {
     if (b.nblk_total <= 0) return;
     k_blocksums<<<(unsigned)b.nblk_total, 256, 0, s>>>(b);
+}
+
+// ---------------------------------------------------------------------------
+// Median heuristic (bandwidth of the MMD kernels): the lower median, rank
+// k = floor((N - 1) / 2) in ascending order, of the N = n (n - 1) / 2 distances
+// between distinct pooled rows (the strictly upper entries of the stored blocks).
+// Exact radix selection on the FP32 bit patterns (non-negative floats order like
+// their bits): three passes over digits of 11, 11 and 10 bits, most significant
+// first; each pass histograms the digit of the entries whose higher bits match the
+// prefix found so far (k_median_hist, one CTA per stored block, lanes with equal
+// digits aggregated before the shared-memory atomics) and then finds the bin that
+// holds rank k (k_median_pick, one CTA per test), which extends the prefix.  After
+// the last pass the prefix is the median's bit pattern (Counters::sel_prefix).
+__device__ __forceinline__ void sel_digit(int pass, uint32_t &mask, int &shift, uint32_t &dmask) {
+    mask = pass == 0 ? 0u : (pass == 1 ? 0xFFE00000u : 0xFFFFFC00u);
+    shift = pass == 0 ? 21 : (pass == 1 ? 10 : 0);
+    dmask = pass == 2 ? 0x3FFu : 0x7FFu;
+}
+
+__global__ void __launch_bounds__(256) k_median_hist(const Batch bt, int pass) {
+    __shared__ uint32_t hist[2048];
+    const int64_t gb = blockIdx.x;
+    const BlkInfo bi = bt.blk[gb];
+    const TestDesc &d = bt.desc[bi.t];
+    if (!d.median) return;
+    for (int k = threadIdx.x; k < 2048; k += 256) hist[k] = 0u;
+    __syncthreads();
+    uint32_t mask, dmask;
+    int shift;
+    sel_digit(pass, mask, shift, dmask);
+    const uint32_t prefix = bt.ctr[bi.t].sel_prefix;
+    const int64_t n = d.n;
+    const float *base = bt.D + gb * (int64_t)(PANEL * KB);
+    for (int e = threadIdx.x; e < PANEL * KB; e += 256) {
+        const int64_t i = (int64_t)bi.I * PANEL + (e >> 6), j = (int64_t)bi.kb * KB + (e & 63);
+        const uint32_t v = __float_as_uint(base[e]);
+        const bool take = i < n && j < n && j > i && (v & mask) == prefix;
+        const uint32_t bin = take ? ((v >> shift) & dmask) : 0xFFFFFFFFu;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin);
+        if (take && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&hist[bin], (uint32_t)__popc(peers));
+    }
+    __syncthreads();
+    uint32_t *gh = bt.sel_hist + (int64_t)bi.t * 2048;
+    for (int k = threadIdx.x; k < 2048; k += 256)
+        if (hist[k]) atomicAdd(&gh[k], hist[k]);
+}
+
+__global__ void __launch_bounds__(256) k_median_pick(const Batch bt, int pass) {
+    __shared__ unsigned long long part[256];
+    __shared__ int owner;
+    __shared__ unsigned long long before;
+    const int t = blockIdx.x;
+    const TestDesc &d = bt.desc[t];
+    if (!d.median) return;
+    uint32_t mask, dmask;
+    int shift;
+    sel_digit(pass, mask, shift, dmask);
+    const int nbins = (int)dmask + 1, per = nbins / 256;
+    uint32_t *gh = bt.sel_hist + (int64_t)t * 2048;
+    Counters *c = bt.ctr + t;
+    const unsigned long long npairs = (unsigned long long)d.n * (unsigned long long)(d.n - 1) / 2ull;
+    const unsigned long long k = pass == 0 ? (npairs - 1ull) / 2ull : c->sel_k;
+    unsigned long long mine = 0;
+    for (int q = 0; q < per; ++q) mine += gh[threadIdx.x * per + q];
+    part[threadIdx.x] = mine;
+    if (threadIdx.x == 0) owner = -1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long cum = 0;
+        for (int q = 0; q < 256; ++q) {
+            if (k < cum + part[q]) {
+                owner = q;
+                before = cum;
+                break;
+            }
+            cum += part[q];
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x == owner) {
+        unsigned long long cum = before;
+        for (int q = 0; q < per; ++q) {
+            const unsigned long long h = gh[threadIdx.x * per + q];
+            if (k < cum + h) {
+                c->sel_prefix |= (uint32_t)(threadIdx.x * per + q) << shift;
+                c->sel_k = k - cum;
+                break;
+            }
+            cum += h;
+        }
+    }
+    if (owner < 0 && threadIdx.x == 0) c->sel_prefix = 0u;   // counts do not add up: reported as a zero bandwidth
+    __syncthreads();
+    for (int q = 0; q < per; ++q) gh[threadIdx.x * per + q] = 0u;   // ready for the next pass
+}
+
+void launch_median_select(const Batch &b, cudaStream_t s) {
+    if (!b.sel_hist || b.nblk_total <= 0) return;
+    for (int pass = 0; pass < 3; ++pass) {
+        k_median_hist<<<(unsigned)b.nblk_total, 256, 0, s>>>(b, pass);
+        k_median_pick<<<(unsigned)b.n_tests, 256, 0, s>>>(b, pass);
+    }
 }
 
 // r_i = sum over the stored blocks of row i's panel (its own row segments) + sum

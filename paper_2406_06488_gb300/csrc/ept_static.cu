@@ -165,9 +165,10 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     if (nx < 1 || ny < 1 || p < 1) return err(EPT_EINVAL, "nx, ny and p must be >= 1");
     if (B < 0 || B > ((int64_t)1 << 31)) return err(EPT_EINVAL, "B must be in [0, 2^31]");
     if (nx + ny > ((int64_t)1 << 22)) return err(EPT_EINVAL, "nx + ny exceeds 2^22");
-    if (stat != EPT_STAT_ED && stat != EPT_STAT_MMD_GAUSS) return err(EPT_EINVAL, "unknown statistic %d", stat);
-    if (stat == EPT_STAT_MMD_GAUSS && !(sigma > 0.0 && sigma < 1e300))
-        return err(EPT_EINVAL, "MMD needs a finite bandwidth sigma > 0");
+    if (stat != EPT_STAT_ED && stat != EPT_STAT_MMD_GAUSS && stat != EPT_STAT_MMD_LAPLACE)
+        return err(EPT_EINVAL, "unknown statistic %d", stat);
+    if (stat != EPT_STAT_ED && !(sigma > 0.0 && sigma < 1e300))
+        return err(EPT_EINVAL, "MMD needs a finite bandwidth sigma > 0 (ept_test_static has no median heuristic)");
     // the test, described as a batch of one (same layout rules as ept_test)
     TestDesc d;
     memset(&d, 0, sizeof(d));
@@ -198,7 +199,9 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     d.other = d.comp ? nx : ny;
     d.stat = stat;
     d.seed = seed;
-    d.neg_inv_2s2 = (stat == EPT_STAT_ED) ? 0.f : (float)(-1.0 / (2.0 * sigma * sigma));
+    d.kern = stat;
+    d.neg_inv_2s2 = (stat == EPT_STAT_MMD_GAUSS) ? (float)(-1.0 / (2.0 * sigma * sigma)) : 0.f;
+    d.inv_sigma = (stat == EPT_STAT_MMD_LAPLACE) ? (float)(1.0 / sigma) : 0.f;
     d.tau = 1.f / 4.f;
     const double fn = (double)d.n, q = fn / ((double)nx * (double)ny);
     d.cT = q * q;
@@ -290,6 +293,7 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     out->n_fixup = (int64_t)h.n_fixup;
     out->p_value = (1.0 + (double)out->n_ge) / (1.0 + (double)B);
     out->ms_build = out->ms_perm = out->ms_masks = out->ms_contract = 0.0;
+    out->sigma = (stat == EPT_STAT_ED) ? 0.0 : sigma;
     out->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     return EPT_OK;
 }

@@ -20,7 +20,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libept.so")
 
-STAT = {"ed": 0, "mmd": 1}
+STAT = {"ed": 0, "mmd": 1, "mmd_gauss": 1, "mmd_laplace": 2}
+SIGMA_MEDIAN = -1.0   # EPT_SIGMA_MEDIAN: bandwidth from the median heuristic
+ABI_VERSION = 2       # EPT_ABI_VERSION this binding's structures follow
 PREC = {"plain_fp32": 0, "split_bf16": 1}
 STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT_ECUDA", 5: "EPT_ETIMEOUT",
           6: "EPT_ECANCELLED", 7: "EPT_ENOTFOUND", 8: "EPT_EUNSUPPORTED"}
@@ -47,7 +49,7 @@ class _Result(ctypes.Structure):
     _fields_ = [("observed", ctypes.c_double), ("p_value", ctypes.c_double), ("n_ge", ctypes.c_int64),
                 ("n_near_tie", ctypes.c_int64), ("n_fixup", ctypes.c_int64), ("ms_build", ctypes.c_double),
                 ("ms_perm", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_masks", ctypes.c_double),
-                ("ms_contract", ctypes.c_double)]
+                ("ms_contract", ctypes.c_double), ("sigma", ctypes.c_double)]
 
 
 @dataclass
@@ -62,12 +64,13 @@ class Result:
     ms_total: float
     ms_masks: float
     ms_contract: float
+    sigma: float
     stats: Optional[object] = field(default=None, repr=False)
 
 
 def _result(r, buf) -> "Result":
     return Result(r.observed, r.p_value, r.n_ge, r.n_near_tie, r.n_fixup, r.ms_build, r.ms_perm, r.ms_total,
-                  r.ms_masks, r.ms_contract, buf)
+                  r.ms_masks, r.ms_contract, r.sigma, buf)
 
 
 _lib = None
@@ -85,6 +88,9 @@ def load():
     vp, i64, u64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, ctypes.c_double
     lib.ept_abi_version.argtypes = []
     lib.ept_abi_version.restype = i32
+    if lib.ept_abi_version() != ABI_VERSION:
+        raise RuntimeError("libept ABI version %d, binding expects %d: rebuild the library"
+                           % (lib.ept_abi_version(), ABI_VERSION))
     lib.ept_last_error.argtypes = []
     lib.ept_last_error.restype = ctypes.c_char_p
     lib.ept_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_size_t]
@@ -133,6 +139,15 @@ def _stat(stat) -> int:
     if isinstance(stat, str):
         return STAT[stat.lower()]
     return int(stat)
+
+
+def _sigma(sigma) -> float:
+    """Kernel bandwidth: a number, or "median" for the median heuristic."""
+    if isinstance(sigma, str):
+        if sigma.lower() != "median":
+            raise ValueError("sigma must be a number or 'median'")
+        return SIGMA_MEDIAN
+    return float(sigma)
 
 
 def _prec(prec) -> int:
@@ -215,7 +230,7 @@ class Context:
         buf, pbuf = self._stats_buffer(X, B if want_stats else 0, on_dev)
         r = _Result()
         _check(load().ept_test(self._h, px, X.shape[0], py, Y.shape[0], X.shape[1], on_dev, _stat(stat),
-                               float(sigma), int(B), ctypes.c_uint64(seed), _prec(prec), pbuf, ctypes.byref(r),
+                               _sigma(sigma), int(B), ctypes.c_uint64(seed), _prec(prec), pbuf, ctypes.byref(r),
                                stream))
         return _result(r, buf)
 
@@ -242,7 +257,7 @@ class Context:
         buf, pbuf = self._stats_buffer(X, count, on_dev)
         r = _Result()
         _check(load().ept_test_masks(self._h, px, X.shape[0], py, Y.shape[0], X.shape[1], on_dev, _stat(stat),
-                                     float(sigma), pm, int(count), _prec(prec), pbuf, ctypes.byref(r), stream))
+                                     _sigma(sigma), pm, int(count), _prec(prec), pbuf, ctypes.byref(r), stream))
         return _result(r, buf)
 
     def test_batch(self, tests, prec="split_bf16", want_stats: bool = True):
@@ -264,7 +279,7 @@ class Context:
         """Queue one test (host arrays, copied before returning); returns a ticket."""
         X = np.ascontiguousarray(X, dtype=np.float32)
         Y = np.ascontiguousarray(Y, dtype=np.float32)
-        d = _TestDesc(X.ctypes.data, Y.ctypes.data, X.shape[0], Y.shape[0], X.shape[1], _stat(stat), float(sigma),
+        d = _TestDesc(X.ctypes.data, Y.ctypes.data, X.shape[0], Y.shape[0], X.shape[1], _stat(stat), _sigma(sigma),
                       int(B), int(seed), None)
         t = ctypes.c_uint64(0)
         _check(load().ept_submit(self._h, ctypes.byref(d), _prec(prec), ctypes.byref(t)))
@@ -312,7 +327,7 @@ class Context:
             out = np.empty((n, n), dtype=np.float32)
             pout = out.ctypes.data
         _check(load().ept_build_blocks(self._h, px, X.shape[0], py, Y.shape[0], X.shape[1], on_dev, _stat(stat),
-                                       float(sigma), _prec(prec), pout, stream))
+                                       _sigma(sigma), _prec(prec), pout, stream))
         return out
 
 
@@ -338,7 +353,7 @@ class PreparedBatch:
             self.keep.append((X, Y))
             self.bufs.append(buf)
             self.descs[k] = _TestDesc(px, py, X.shape[0], Y.shape[0], X.shape[1], _stat(t.get("stat", "ed")),
-                                      float(t.get("sigma", 1.0)), B, int(t.get("seed", 0)), pbuf)
+                                      _sigma(t.get("sigma", 1.0)), B, int(t.get("seed", 0)), pbuf)
 
     def run(self):
         if self.n == 0:

@@ -14,6 +14,8 @@ Workloads (the paper draws X ~ N_p(0, I) and Y ~ N_p(mu, I), Section 5.2):
                  coordinates
 * ``mmd``        Gaussian MMD, nx = ny = 10000, p = 100, Y ~ N(0, 1.1 I),
                  bandwidth sigma = sqrt(p)
+* ``mmd_laplace`` the same shape with the Laplacian kernel exp(-d / sigma), sigma = sqrt(p)
+* ``mmd_median`` the same shape, Gaussian kernel, bandwidth from the median heuristic
 * ``batched``    512 independent ED tests, nx, ny uniform on {50..2000}, p uniform on
                  {20..500}, half null, half with Y mean 0.1 on every coordinate
 * ``serving``    Poisson request stream (see ``serving_requests``)
@@ -62,7 +64,15 @@ HIGHDIM = TwoSampleSpec(nx=2000, ny=3000, p=1000, y_mean=0.05, y_mean_coords=50,
 MMD = TwoSampleSpec(nx=10000, ny=10000, p=100, stat="mmd", sigma=10.0, y_var=1.1, B=10000,
                     seed=0, data_seed=0)
 
-NAMED = {"small": SMALL, "tiny": TINY, "highdim": HIGHDIM, "mmd": MMD}
+# the MMD shape with the Laplacian kernel exp(-d / sigma), and with the Gaussian kernel
+# whose bandwidth comes from the median heuristic (sigma = -1 selects it)
+MMD_LAPLACE = TwoSampleSpec(nx=10000, ny=10000, p=100, stat="mmd_laplace", sigma=10.0, y_var=1.1, B=10000,
+                            seed=0, data_seed=0)
+MMD_MEDIAN = TwoSampleSpec(nx=10000, ny=10000, p=100, stat="mmd", sigma=-1.0, y_var=1.1, B=10000,
+                           seed=0, data_seed=0)
+
+NAMED = {"small": SMALL, "tiny": TINY, "highdim": HIGHDIM, "mmd": MMD, "mmd_laplace": MMD_LAPLACE,
+         "mmd_median": MMD_MEDIAN}
 
 
 def batched_specs(n_tests: int = 512, B: int = 5000, master_seed: int = 0):

@@ -36,7 +36,11 @@ def test_library_exports_every_declared_symbol(lib_path):
 def test_abi_version_and_errors_without_gpu(lib_path):
     from paper_2406_06488_gb300 import ept
     lib = ept.load()
-    assert lib.ept_abi_version() == 1
+    import re
+    hdr = open(os.path.join(ROOT, "include", "ept.h")).read()
+    want = int(re.search(r"#define EPT_ABI_VERSION (\d+)", hdr).group(1))
+    from paper_2406_06488_gb300 import ept
+    assert lib.ept_abi_version() == want == ept.ABI_VERSION
     # creating a context without a GPU fails cleanly with a status, not a crash
     h = ctypes.c_void_p()
     st = lib.ept_create(ctypes.byref(h), 0, 0)
