@@ -48,7 +48,7 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="highdim", choices=["highdim", "mmd", "mmd_laplace", "mmd_median", "small",
-                                                                "batched", "serving"])
+                                                                "batched", "serving", "validation"])
     ap.add_argument("--tests", type=int, default=512, help="batched: tests per step")
     ap.add_argument("--rates", default="10,100,1000", help="serving: request rates (1/s) swept")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests per rate (at most)")
@@ -626,6 +626,67 @@ def run_serving(args):
     return 0
 
 
+def run_validation(args):
+    """The paper's statistical experiments (Section 5) as batched runs: null
+    replications (nx = ny = 200, p = 100 and 1000, 2000 each: p-value histogram,
+    chi-square uniformity p-value, rejection rate at 0.05) and the three power
+    settings (500 replications per point, B = 200: rejection rate at 0.05)."""
+    import torch
+    from scipy.stats import chisquare
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_06488_gb300 import ept, workloads
+    ctx = ept.Context(local)
+    n_tests = [0]
+    n_stats = [0]
+    gpu_s = [0.0]
+
+    def pvalues(specs, chunk=500):
+        out = []
+        for k in range(0, len(specs), chunk):
+            tests = []
+            for sp in specs[k:k + chunk]:
+                X, Y = workloads.gaussian_pair(sp)
+                tests.append(dict(X=X, Y=Y, B=sp.B, seed=sp.seed, stat=sp.stat, sigma=sp.sigma))
+            t0 = time.perf_counter()
+            res = ctx.test_batch(tests, want_stats=False)
+            gpu_s[0] += time.perf_counter() - t0
+            n_tests[0] += len(tests)
+            n_stats[0] += sum(t["B"] for t in tests)
+            out += [r.p_value for r in res]
+        return np.asarray(out)
+
+    B = 200
+    null = {}
+    for p in (100, 1000):
+        pv = pvalues(workloads.null_specs(reps=2000, n=200, p=p, B=B))
+        atoms = np.arange(1, B + 2) / (B + 1)
+        edges = np.linspace(0, 1, 11)
+        expect = np.bincount(np.clip(np.searchsorted(edges, atoms) - 1, 0, 9), minlength=10) / atoms.size * pv.size
+        got = np.bincount(np.clip(np.searchsorted(edges, pv) - 1, 0, 9), minlength=10)
+        null["p=%d" % p] = {"reps": int(pv.size), "histogram_deciles": got.tolist(),
+                            "chisquare_pvalue": float(chisquare(got, expect).pvalue),
+                            "rejection_rate_0.05": float(np.mean(pv <= 0.05)), "expected_rate": 10 / (B + 1)}
+    power = {}
+    for setting in (1, 2, 3):
+        pts = {}
+        for x, specs in workloads.power_specs(setting, reps=500, B=B):
+            pts[str(x)] = float(np.mean(pvalues(specs) <= 0.05))
+        power["setting %d" % setting] = pts
+    line = {"metric": METRIC, "value": n_stats[0] / gpu_s[0], "unit": UNIT, "n_gpus": 1, "steps": n_tests[0],
+            "warmup": 0, "ms_per_step": 1000 * gpu_s[0] / n_tests[0], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+            "config": {"workload": "validation: Section 5 null (nx = ny = 200, p = 100 / 1000, 2000 reps) and power "
+                                   "settings 1-3 (500 reps per point), ED, B = 200, in batches of 500 tests; a step "
+                                   "is one test, timed on the host around each batched call (inputs from host)"},
+            "null": null, "power": power}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -634,6 +695,8 @@ def main():
         return run_batched(args)
     if args.workload == "serving":
         return run_serving(args)
+    if args.workload == "validation":
+        return run_validation(args)
     return run_ours(args)
 
 

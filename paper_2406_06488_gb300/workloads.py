@@ -19,6 +19,9 @@ Workloads (the paper draws X ~ N_p(0, I) and Y ~ N_p(mu, I), Section 5.2):
 * ``batched``    512 independent ED tests, nx, ny uniform on {50..2000}, p uniform on
                  {20..500}, half null, half with Y mean 0.1 on every coordinate
 * ``serving``    Poisson request stream (see ``serving_requests``)
+* ``null_specs`` / ``power_specs``  the paper's statistical experiments (Section 5):
+                 null replications (X, Y ~ N_p(0, I), nx = ny = 200, p = 100 or 1000) and
+                 the three power settings (Y mean eps on the first j coordinates)
 """
 from __future__ import annotations
 
@@ -111,4 +114,41 @@ def serving_requests(rate_per_s: float, n_requests: int, master_seed: int = 0,
         out.append((float(t[k]), TwoSampleSpec(nx=int(nx[k]), ny=int(ny[k]), p=int(p[k]), stat=stat,
                                                sigma=math.sqrt(float(p[k])), B=int(Bs[k]), seed=k,
                                                data_seed=master_seed * 7_000_003 + k + 1)))
+    return out
+
+
+def null_specs(reps: int = 2000, n: int = 200, p: int = 100, B: int = 200, stat: str = "ed",
+               master_seed: int = 0):
+    """Null replications of Section 5: X and Y both N_p(0, I), nx = ny = n (the paper's
+    "n = 200" read as the size of each sample), B permutations; replication r has
+    permutation seed r and its own data seed."""
+    return [TwoSampleSpec(nx=n, ny=n, p=p, stat=stat, sigma=math.sqrt(p), B=B, seed=r,
+                          data_seed=master_seed * 10_000_019 + 7 * p + 100_003 * r + 1)
+            for r in range(reps)]
+
+
+def power_specs(setting: int, reps: int = 500, B: int = 200, points=None, master_seed: int = 0):
+    """The power experiments of Section 5 (Y ~ N_p(mu, I), mu = eps on the first j
+    coordinates, B = 200 permutations, 500 replications per point):
+    setting 1: nx = ny in 60..360 step 20, p = 50, j = 5, eps = 0.25;
+    setting 2: nx = ny = 200, p in 200..2000 step 100, j = 50, eps = 0.1;
+    setting 3: as setting 2 with j = p / 10.
+    Returns [(x value of the point, [TwoSampleSpec] * reps)]; `points` restricts the
+    x values."""
+    if setting == 1:
+        xs = list(range(60, 361, 20))
+        make = lambda x: dict(nx=x, ny=x, p=50, y_mean=0.25, y_mean_coords=5)
+    elif setting in (2, 3):
+        xs = list(range(200, 2001, 100))
+        make = lambda x: dict(nx=200, ny=200, p=x, y_mean=0.1,
+                              y_mean_coords=50 if setting == 2 else x // 10)
+    else:
+        raise ValueError("setting must be 1, 2 or 3")
+    if points is not None:
+        xs = [x for x in xs if x in set(points)]
+    out = []
+    for x in xs:
+        kw = make(x)
+        out.append((x, [TwoSampleSpec(B=B, seed=r, data_seed=master_seed * 10_000_019 + 1_000_003 * setting
+                                      + 1009 * x + 100_003 * r + 2, **kw) for r in range(reps)]))
     return out

@@ -95,3 +95,24 @@ def test_mixed_batch(ctx):
         assert r.sigma == alone.sigma
         assert abs(r.observed - alone.observed) <= REL_TOL * abs(alone.observed)
         assert np.max(np.abs(np.asarray(r.stats) - np.asarray(alone.stats)) / np.abs(np.asarray(alone.stats))) <= REL_TOL
+
+
+def test_full_size_mmd_median_sampled(ctx):
+    # the MMD shape (nx = ny = 10000, p = 100) with the median-heuristic bandwidth:
+    # sampled draws against the oracle at the bandwidth the GPU selected, and the
+    # bandwidth against the median of a random sample of pooled pairs
+    spec = workloads.MMD_MEDIAN
+    X, Y = workloads.gaussian_pair(spec)
+    res = ctx.test(X, Y, B=2000, seed=spec.seed, stat=spec.stat, sigma="median")
+    st = np.asarray(res.stats)
+    for b in (1, 2000):
+        sel = oracle.perm_select(spec.seed, spec.nx, spec.ny, b, 1)[0]
+        v = oracle.stat_select(X, Y, sel, spec.stat, res.sigma)
+        assert abs(st[b - 1] - v) <= REL_TOL * abs(v)
+    W = np.concatenate([X, Y]).astype(np.float64)
+    r = np.random.default_rng(0)
+    i, j = r.integers(0, W.shape[0], 200000), r.integers(0, W.shape[0], 200000)
+    keep = i != j
+    d = np.sqrt(((W[i[keep]] - W[j[keep]]) ** 2).sum(axis=1))
+    # the sample median of 2e5 pairs is within a few 1e-3 of the population median
+    assert abs(np.median(d) - res.sigma) <= 0.01 * res.sigma
