@@ -353,6 +353,8 @@ struct ept_ctx {
     int serve_lanes = 3;                // serving: batches in flight at once
     int serve_slots = 256;              // serving: requests in flight at once
     cudaEvent_t ev_user = nullptr;      // orders the context's stream after a caller's stream
+    cudaStream_t copy = nullptr;        // host-to-device input copies, beside the relabeling draws
+    cudaEvent_t ev_in = nullptr;        // the run's inputs are on the device
     // plan of the last run, reused while the batch shape repeats; tables_staged: the
     // pinned staging area still holds its constant tables
     Plan *plan = nullptr;
@@ -577,23 +579,37 @@ Batch device_view(ept_ctx *c, const Plan &P) {
 
 // The device work of one run, enqueued on s (and the side stream).  With `timed`,
 // events mark the phases (not used while capturing a graph).
-ept_status enqueue_inputs(ept_ctx *c, cudaStream_t s) {
+// The run's input copies on the copy stream (after `after`'s prior work), then ev_in:
+// the relabeling draws, which do not read the inputs, start while the copies run.
+ept_status enqueue_inputs(ept_ctx *c, cudaStream_t after) {
+    CK(cudaEventRecord(c->ev_user, after));
+    CK(cudaStreamWaitEvent(c->copy, c->ev_user, 0));
     for (const ept_ctx::InputCopy &k : c->in_copies)
-        CK(cudaMemcpyAsync(c->arena + k.dst, k.src, k.bytes, cudaMemcpyHostToDevice, s));
+        CK(cudaMemcpyAsync(c->arena + k.dst, k.src, k.bytes, cudaMemcpyHostToDevice, c->copy));
+    CK(cudaEventRecord(c->ev_in, c->copy));
     return EPT_OK;
 }
 
-// with_inputs: also copy the host inputs (a captured graph leaves them out: they are
-// copied before each replay, from wherever the caller's buffers are)
+// The run's host-to-device traffic: the tables on s first (the copy engine takes
+// copies in order, so the small upload that the draws wait for goes ahead), then the
+// inputs on the copy stream.
+ept_status enqueue_uploads(ept_ctx *c, const Plan &P, cudaStream_t s) {
+    const Staging S = staging_layout(P);
+    CK(cudaMemcpyAsync(c->arena, c->pinned + S.tables, P.tab_bytes, cudaMemcpyHostToDevice, s));
+    return enqueue_inputs(c, s);
+}
+
+// with_inputs: also issue the uploads; a captured graph leaves them out (they are
+// issued before each replay, the inputs from wherever the caller's buffers are) and
+// waits for the inputs through ev_in as an external event.
 ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed, bool with_inputs = true) {
     ept_status st = EPT_OK;
     const Staging S = staging_layout(P);
-    uint8_t *A = c->arena, *pin = c->pinned;
+    uint8_t *pin = c->pinned;
     const Batch b = device_view(c, P);
     const bool tc = P.prec == EPT_PREC_SPLIT_BF16;
     if (timed) CK(cudaEventRecord(c->ev[0], s));
-    CK(cudaMemcpyAsync(A, pin + S.tables, P.tab_bytes, cudaMemcpyHostToDevice, s));
-    if (with_inputs && (st = enqueue_inputs(c, s)) != EPT_OK) return st;
+    if (with_inputs && (st = enqueue_uploads(c, P, s)) != EPT_OK) return st;
     CK(cudaMemsetAsync(b.ctr, 0, sizeof(Counters) * P.n_tests, s));
     if (P.any_median) CK(cudaMemsetAsync(b.sel_hist, 0, (size_t)P.n_tests * 2048 * 4, s));
     CK(cudaEventRecord(c->ev[1], s));
@@ -611,7 +627,8 @@ ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed,
     CK(cudaGetLastError());
     CK(cudaEventRecord(c->ev_side[2], s2));
 
-    // phase 1: blocks, centring, packing
+    // phase 1: blocks, centring, packing (after the inputs have arrived)
+    CK(cudaStreamWaitEvent(s, c->ev_in, with_inputs ? cudaEventWaitDefault : cudaEventWaitExternal));
     if (tc) {
         launch_split_rows(b, s);
         alignas(64) CUtensorMap tm[4];
@@ -841,7 +858,7 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
             c->graph.arena = c->arena;
         }
         CK(cudaEventRecord(c->ev[0], s));
-        if ((st = enqueue_inputs(c, s)) != EPT_OK) return st;
+        if ((st = enqueue_uploads(c, P, s)) != EPT_OK) return st;   // the graph waits for ev_in
         CK(cudaGraphLaunch(c->graph.exec, s));
         CK(cudaEventRecord(c->ev[4], s));
         CK(cudaStreamSynchronize(s));
@@ -1196,6 +1213,8 @@ ept_status ept_create(ept_ctx **out, int device, size_t mem_budget_bytes) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking);
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) e = cudaEventCreate(&c->ev_side[k]);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_user, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         ept_destroy(c);
         return fail(EPT_ECUDA, "stream/event creation failed: %s", cudaGetErrorString(e));
@@ -1220,6 +1239,11 @@ ept_status ept_destroy(ept_ctx *c) {
         for (int k = 0; k < 3; ++k)
             if (c->ev_side[k]) cudaEventDestroy(c->ev_side[k]);
         if (c->ev_user) cudaEventDestroy(c->ev_user);
+        if (c->ev_in) cudaEventDestroy(c->ev_in);
+        if (c->copy) {
+            cudaStreamSynchronize(c->copy);
+            cudaStreamDestroy(c->copy);
+        }
         if (c->side) cudaStreamDestroy(c->side);
         if (c->stream) cudaStreamDestroy(c->stream);
     }
@@ -1335,6 +1359,7 @@ ept_status ept_build_blocks(ept_ctx *c, const float *X, int64_t nx, const float 
     const Batch b = device_view(c, P);
     CK(cudaMemcpyAsync(A, c->pinned + S.tables, P.tab_bytes, cudaMemcpyHostToDevice, s));
     if ((st = enqueue_inputs(c, s)) != EPT_OK) return st;
+    CK(cudaStreamWaitEvent(s, c->ev_in, 0));
     CK(cudaMemsetAsync(b.ctr, 0, sizeof(Counters), s));
     if (prec == EPT_PREC_SPLIT_BF16) {
         launch_split_rows(b, s);
