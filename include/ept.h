@@ -133,6 +133,19 @@ ept_status ept_test(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, in
                     int64_t p, int on_device, int stat, double sigma, int64_t B, uint64_t seed,
                     int prec, double *perm_stats, ept_result *out, void *stream);
 
+/* A range of the permutation stream: the observed statistic and draws b_first ..
+   b_first + count - 1 of the stream of `seed` (b_first >= 1), everything else as in
+   ept_test; out->n_ge counts the range's draws and out->p_value is
+   (1 + n_ge) / (1 + count).  Because the stream is counter-based, a test with B
+   permutations can be split into ranges (checkpoint and resume, or one range per
+   GPU): the ranges' statistics are those of ept_test for the same draws, and the
+   test's p-value is (1 + the sum of the ranges' n_ge) / (1 + B).  The paper has no
+   counterpart (its permutations come from an unspecified R generator). */
+ept_status ept_test_range(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, int64_t ny,
+                          int64_t p, int on_device, int stat, double sigma, int64_t b_first,
+                          int64_t count, uint64_t seed, int prec, double *perm_stats,
+                          ept_result *out, void *stream);
+
 /* The same test on caller-given relabelings (testing, exhaustive enumeration).
    masks: n_masks * ceil((nx+ny)/32) uint32 words, row-major by relabeling; pooled
    row t (x rows first, then y rows) is bit t%32 of word t/32; a set bit sends the

@@ -63,6 +63,7 @@ struct TestSpec {
     int stat;
     double sigma;
     uint64_t seed;
+    int64_t b0 = 1;               // first draw of the stream (column 1)
     const uint32_t *user_masks;   // B relabelings (ept_test_masks), same memory space as X
     double *perm_stats;           // B doubles or null, same memory space as X
 };
@@ -111,6 +112,7 @@ struct Plan {
 void set_test_params(TestDesc &d, const TestSpec &s) {
     d.stat = s.stat;
     d.seed = s.seed;
+    d.b0 = s.b0;
     d.median = (s.stat != EPT_STAT_ED && s.sigma == EPT_SIGMA_MEDIAN) ? 1 : 0;
     // the build writes kernel values directly unless the bandwidth is still unknown
     d.kern = (s.stat == EPT_STAT_ED || d.median) ? 0 : s.stat;
@@ -1271,6 +1273,22 @@ ept_status ept_test(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, in
     DeviceGuard dg(ctx->device);
     return run_tuned(ctx, one_test(X, nx, Y, ny, p, stat, sigma, B, seed, nullptr, perm_stats), prec, on_device != 0,
                      true, out, stream);
+}
+
+ept_status ept_test_range(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p,
+                          int on_device, int stat, double sigma, int64_t b_first, int64_t count, uint64_t seed,
+                          int prec, double *perm_stats, ept_result *out, void *stream) {
+    if (!ctx || !out) return fail(EPT_EINVAL, "null context or result");
+    if (!X || !Y) return fail(EPT_EINVAL, "null X or Y");
+    if (count < 0 || count > ((int64_t)1 << 31)) return fail(EPT_EINVAL, "count must be in [0, 2^31]");
+    if (b_first < 1 || b_first > ((int64_t)1 << 62)) return fail(EPT_EINVAL, "b_first must be >= 1");
+    ept_status st = validate(nx, ny, p, stat, sigma, prec);
+    if (st != EPT_OK) return st;
+    std::vector<TestSpec> specs = one_test(X, nx, Y, ny, p, stat, sigma, count, seed, nullptr, perm_stats);
+    specs[0].b0 = b_first;
+    std::lock_guard<std::mutex> lock(ctx->mu);
+    DeviceGuard dg(ctx->device);
+    return run_tuned(ctx, specs, prec, on_device != 0, true, out, stream);
 }
 
 ept_status ept_test_masks(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p,

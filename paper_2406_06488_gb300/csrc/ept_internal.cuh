@@ -15,7 +15,8 @@
 // Relabeling masks are stored transposed, maskT[w][c] (word w of column c), so
 // that the 32 lanes of a warp read 32 consecutive relabelings of one word.
 // Column 0 is always the identity relabeling (the observed statistic); columns
-// 1..B are the permuted ones; padding columns are all-zero.
+// 1..B are the permuted ones (draws b0 .. b0+B-1 of the stream, b0 = 1 unless a
+// range of the stream is asked for); padding columns are all-zero.
 //
 // Contracted group.  Eq. 1 and Eq. 2 are symmetric in x and y, so a relabeling can
 // be described by either of its two groups.  The quadratic form is taken over the
@@ -103,6 +104,7 @@ struct TestDesc {
     int64_t part0;    // partials (nparts * Bp)
     int64_t col0;     // statistics (ncols)
     uint64_t seed;
+    int64_t b0;                      // relabeling column c >= 1 is draw b0 + c - 1 of the stream
     int32_t stat, comp, kblocks, nwu;
     int32_t scaled, pad_;            // scaled: the partials carry the packing scale (tensor-core path)
     float neg_inv_2s2, tau;

@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(128) k_masks(const Batch bt) {
             if (lane == 0 && (bad || cnt != nx)) atomicAdd(&bt.ctr[t].bad_mask, 1ull);
             continue;
         }
-        draw_column(d.seed, (int)d.nx, n, c, nw, d.comp != 0, col, Bp);
+        draw_column(d.seed, (int)d.nx, n, d.b0 + c - 1, nw, d.comp != 0, col, Bp);   // column c >= 1: draw b0 + c - 1
     }
 }
 
@@ -224,7 +224,8 @@ __global__ void __launch_bounds__(256) k_masks_lanes(const Batch bt) {
         kx[r] = kx[r - 1] + 0x9E3779B9u;
         ky[r] = ky[r - 1] + 0xBB67AE85u;
     }
-    const uint32_t blo = (uint32_t)(uint64_t)c, bhi = (uint32_t)((uint64_t)c >> 32);
+    const uint64_t bdraw = (uint64_t)(d.b0 + c - 1);   // column c >= 1 holds draw b0 + c - 1
+    const uint32_t blo = (uint32_t)bdraw, bhi = (uint32_t)(bdraw >> 32);
     int need = nx;
     for (int w = 0; w < nw; ++w) {
         uint32_t bits = 0;

@@ -199,6 +199,7 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     d.other = d.comp ? nx : ny;
     d.stat = stat;
     d.seed = seed;
+    d.b0 = 1;
     d.kern = stat;
     d.neg_inv_2s2 = (stat == EPT_STAT_MMD_GAUSS) ? (float)(-1.0 / (2.0 * sigma * sigma)) : 0.f;
     d.inv_sigma = (stat == EPT_STAT_MMD_LAPLACE) ? (float)(1.0 / sigma) : 0.f;

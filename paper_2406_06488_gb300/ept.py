@@ -30,7 +30,7 @@ STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT
 # every entry point declared in include/ept.h
 EXPORTS = ["ept_abi_version", "ept_last_error", "ept_create", "ept_destroy", "ept_estimate_bytes", "ept_test",
            "ept_test_masks", "ept_perm_masks", "ept_build_blocks", "ept_test_static", "ept_test_batch",
-           "ept_set_option", "ept_submit", "ept_poll", "ept_wait", "ept_cancel"]
+           "ept_set_option", "ept_submit", "ept_poll", "ept_wait", "ept_cancel", "ept_test_range"]
 
 
 class EptError(RuntimeError):
@@ -101,6 +101,9 @@ def load():
     lib.ept_estimate_bytes.restype = ctypes.c_size_t
     lib.ept_test.argtypes = [vp, vp, i64, vp, i64, i64, i32, i32, f64, i64, u64, i32, vp, ctypes.POINTER(_Result), vp]
     lib.ept_test.restype = i32
+    lib.ept_test_range.argtypes = [vp, vp, i64, vp, i64, i64, i32, i32, f64, i64, i64, u64, i32, vp,
+                                   ctypes.POINTER(_Result), vp]
+    lib.ept_test_range.restype = i32
     lib.ept_test_masks.argtypes = [vp, vp, i64, vp, i64, i64, i32, i32, f64, vp, i64, i32, vp,
                                    ctypes.POINTER(_Result), vp]
     lib.ept_test_masks.restype = i32
@@ -232,6 +235,18 @@ class Context:
         _check(load().ept_test(self._h, px, X.shape[0], py, Y.shape[0], X.shape[1], on_dev, _stat(stat),
                                _sigma(sigma), int(B), ctypes.c_uint64(seed), _prec(prec), pbuf, ctypes.byref(r),
                                stream))
+        return _result(r, buf)
+
+    def test_range(self, X, Y, b_first: int, count: int, seed: int = 0, stat="ed", sigma: float = 1.0,
+                   prec="split_bf16", want_stats: bool = True) -> Result:
+        """The observed statistic and draws b_first .. b_first + count - 1 of the stream
+        of `seed` (a range of ept_test's relabelings; p_value is the range's own)."""
+        X, Y, px, py, on_dev, stream = self._arrays(X, Y)
+        buf, pbuf = self._stats_buffer(X, count if want_stats else 0, on_dev)
+        r = _Result()
+        _check(load().ept_test_range(self._h, px, X.shape[0], py, Y.shape[0], X.shape[1], on_dev, _stat(stat),
+                                     _sigma(sigma), int(b_first), int(count), ctypes.c_uint64(seed), _prec(prec),
+                                     pbuf, ctypes.byref(r), stream))
         return _result(r, buf)
 
     def test_masks(self, X, Y, masks, stat="ed", sigma: float = 1.0, prec="split_bf16") -> Result:

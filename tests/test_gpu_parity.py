@@ -233,3 +233,23 @@ def test_full_size_highdim_ed(ctx):
 def test_full_size_mmd(ctx):
     # Gaussian MMD, nx = ny = 10000, p = 100, Y ~ N(0, 1.1 I), sigma = 10, B = 10000
     _full_size_check(ctx, workloads.MMD, [1, 10000])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_stream_ranges_combine(ctx, prec):
+    # a test split into ranges of the counter-based stream (checkpoint / resume, or
+    # one range per GPU) gives the same statistics and count as the whole test
+    X, Y = _pair(150, 170, 9, seed=31)
+    full = ctx.test(X, Y, B=1000, seed=4, prec=prec)
+    a = ctx.test_range(X, Y, b_first=1, count=400, seed=4, prec=prec)
+    b = ctx.test_range(X, Y, b_first=401, count=600, seed=4, prec=prec)
+    got = np.concatenate([np.asarray(a.stats), np.asarray(b.stats)])
+    want = np.asarray(full.stats)
+    assert np.max(np.abs(got - want) / np.abs(want)) <= 1e-9
+    assert a.observed == full.observed == b.observed
+    assert abs((a.n_ge + b.n_ge) - full.n_ge) <= full.n_near_tie
+    assert a.p_value == (1.0 + a.n_ge) / 401.0
+    # and the range really is draws 401..1000 of the oracle's stream
+    ref = oracle.permutation_test(X, Y, B=1000, seed=4, stat="ed")
+    rel = np.abs(np.asarray(b.stats) - ref["stats"][400:]) / np.abs(ref["stats"][400:])
+    assert rel.max() <= REL_TOL
