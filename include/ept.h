@@ -193,6 +193,9 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    per column when the batch has at least 1024 columns per SM, else a warp per
    column), 1 = a warp per column, 2 = a thread per column; the draws are
    identical in every mode.
+   EPT_OPT_FAULT_INJECT_ALLOC (test hook, default 0): the next `value` acquisitions
+   of device scratch (a run's arena, a serving batch's pool allocation) fail with
+   EPT_ENOMEM on the host, without touching the GPU, to exercise error paths.
    EPT_OPT_SERVE_LANES (default 3, 1..16): serving batches in flight at once;
    EPT_OPT_SERVE_SLOTS (default 256): serving requests in flight at once; both
    before the first ept_submit.  EPT_EINVAL for an unknown option or value. */
@@ -201,7 +204,8 @@ enum {
     EPT_OPT_AUTOTUNE = 2,
     EPT_OPT_SERVE_LANES = 3,
     EPT_OPT_SERVE_SLOTS = 4,
-    EPT_OPT_DRAW_MODE = 5
+    EPT_OPT_DRAW_MODE = 5,
+    EPT_OPT_FAULT_INJECT_ALLOC = 6
 };
 ept_status ept_set_option(ept_ctx *ctx, int option, int64_t value);
 
@@ -231,6 +235,12 @@ ept_status ept_wait(ept_ctx *ctx, uint64_t ticket, double *perm_stats, ept_resul
 /* Cancels a request: removed if still queued; if already running, its result is
    discarded when its batch finishes.  The ticket must still be waited on. */
 ept_status ept_cancel(ept_ctx *ctx, uint64_t ticket);
+
+/* Serving state (any pointer may be NULL): device scratch held by running batches,
+   requests running, requests queued, finished requests not yet waited on.  All
+   zero before the first ept_submit. */
+ept_status ept_serving_stats(ept_ctx *ctx, size_t *bytes_in_use, int64_t *running, int64_t *queued,
+                             int64_t *finished);
 
 /* Draws b0 .. b0+count-1 of the permutation stream of `seed` (Algorithm 2's
    SampleWithoutReplacement, fixed as Philox4x32-10 + Knuth's selection sampling;

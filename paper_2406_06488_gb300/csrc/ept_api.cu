@@ -12,6 +12,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <atomic>
+#include <nvtx3/nvToolsExt.h>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -352,6 +353,7 @@ struct ept_ctx {
     bool autotune = true;
     bool graphs = true;                 // replay captured graphs of repeated batches
     int draw_mode = 0;                  // relabeling draws: 0 automatic, DRAW_WARPS, DRAW_LANES
+    std::atomic<int> inject_alloc{0};   // test hook: the next N scratch acquisitions fail (host side)
     int serve_lanes = 3;                // serving: batches in flight at once
     int serve_slots = 256;              // serving: requests in flight at once
     cudaEvent_t ev_user = nullptr;      // orders the context's stream after a caller's stream
@@ -385,6 +387,20 @@ struct DeviceGuard {
         if (prev >= 0) cudaSetDevice(prev);
     }
 };
+
+// NVTX range on the host timeline (shown by Nsight tools; no cost without them)
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+};
+
+// fault-injection hook (EPT_OPT_FAULT_INJECT_ALLOC): consume one injected failure
+bool injected_failure(ept_ctx *c) {
+    int v = c->inject_alloc.load();
+    while (v > 0)
+        if (c->inject_alloc.compare_exchange_weak(v, v - 1)) return true;
+    return false;
+}
 
 void drop_graph(ept_ctx *c) {
     if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
@@ -824,6 +840,8 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
     }
     Plan &P = *c->plan;
     for (int t = 0; t < P.n_tests; ++t) set_test_params(P.desc[t], specs[t]);
+    NvtxRange range(use_graph && c->graphs ? "ept.run (graph)" : "ept.run");
+    if (injected_failure(c)) return fail(EPT_ENOMEM, "device scratch not available (injected failure)");
     ept_status st = ensure_arena(c, P.total, s);
     if (st != EPT_OK) return st;
     const Staging S = staging_layout(P);
@@ -946,6 +964,7 @@ struct Lane {
 };
 
 struct Server {
+    ept_ctx *owner = nullptr;
     std::thread th;
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
@@ -973,6 +992,8 @@ ept_status lane_enqueue(Server *S, Lane &L) {
     const Staging SL = staging_layout(L.plan);
     ept_status st = ensure_pinned(c, SL.total);
     if (st != EPT_OK) return st;
+    NvtxRange range("ept.serve.batch");
+    if (injected_failure(S->owner)) return fail(EPT_ENOMEM, "device scratch not available (injected failure)");
     void *mem = nullptr;
     cudaError_t e = cudaMallocFromPoolAsync(&mem, L.plan.total, S->pool, s);
     if (e != cudaSuccess) {
@@ -1117,6 +1138,7 @@ ept_status serve_start(ept_ctx *c) {
         cudaGetLastError();
         free_b = 0;
     }
+    S->owner = c;
     S->budget = c->budget ? c->budget : (size_t)(0.8 * (double)free_b);
     cudaMemPoolProps props;
     memset(&props, 0, sizeof(props));
@@ -1420,6 +1442,10 @@ ept_status ept_set_option(ept_ctx *c, int option, int64_t value) {
     case EPT_OPT_AUTOTUNE:
         c->autotune = value != 0;
         return EPT_OK;
+    case EPT_OPT_FAULT_INJECT_ALLOC:
+        if (value < 0 || value > (1 << 20)) return fail(EPT_EINVAL, "injected failure count must be in [0, 2^20]");
+        c->inject_alloc.store((int)value);
+        return EPT_OK;
     case EPT_OPT_DRAW_MODE:
         if (value < 0 || value > 2) return fail(EPT_EINVAL, "draw mode must be 0, 1 or 2");
         c->draw_mode = (int)value;
@@ -1519,6 +1545,25 @@ ept_status ept_wait(ept_ctx *c, uint64_t ticket, double *perm_stats, ept_result 
     delete r;
     if (state == REQ_CANCELLED) return fail(EPT_ECANCELLED, "request %llu was cancelled", (unsigned long long)ticket);
     if (st != EPT_OK) return fail(st, "%s", msg.c_str());
+    return EPT_OK;
+}
+
+ept_status ept_serving_stats(ept_ctx *c, size_t *bytes_in_use, int64_t *running, int64_t *queued,
+                             int64_t *finished) {
+    if (!c) return fail(EPT_EINVAL, "null context");
+    size_t b = 0;
+    int64_t run = 0, q = 0, fin = 0;
+    if (Server *S = c->server) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        b = S->in_use;
+        run = S->slots;
+        q = (int64_t)S->pending.size();
+        for (auto &kv : S->reqs) fin += kv.second->state >= REQ_DONE;
+    }
+    if (bytes_in_use) *bytes_in_use = b;
+    if (running) *running = run;
+    if (queued) *queued = q;
+    if (finished) *finished = fin;
     return EPT_OK;
 }
 

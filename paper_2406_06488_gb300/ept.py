@@ -30,7 +30,8 @@ STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT
 # every entry point declared in include/ept.h
 EXPORTS = ["ept_abi_version", "ept_last_error", "ept_create", "ept_destroy", "ept_estimate_bytes", "ept_test",
            "ept_test_masks", "ept_perm_masks", "ept_build_blocks", "ept_test_static", "ept_test_batch",
-           "ept_set_option", "ept_submit", "ept_poll", "ept_wait", "ept_cancel", "ept_test_range"]
+           "ept_set_option", "ept_submit", "ept_poll", "ept_wait", "ept_cancel", "ept_test_range",
+           "ept_serving_stats"]
 
 
 class EptError(RuntimeError):
@@ -123,6 +124,9 @@ def load():
     lib.ept_poll.restype = i32
     lib.ept_wait.argtypes = [vp, u64, vp, ctypes.POINTER(_Result), i64]
     lib.ept_wait.restype = i32
+    lib.ept_serving_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i64),
+                                      ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.ept_serving_stats.restype = i32
     lib.ept_cancel.argtypes = [vp, u64]
     lib.ept_cancel.restype = i32
     _lib = lib
@@ -163,7 +167,8 @@ def estimate_bytes(nx: int, ny: int, p: int, B: int, prec="split_bf16") -> int:
     return int(load().ept_estimate_bytes(nx, ny, p, B, _prec(prec)))
 
 
-OPTION = {"graphs": 1, "autotune": 2, "serve_lanes": 3, "serve_slots": 4, "draw_mode": 5}
+OPTION = {"graphs": 1, "autotune": 2, "serve_lanes": 3, "serve_slots": 4, "draw_mode": 5,
+          "fault_inject_alloc": 6}
 
 
 class Context:
@@ -317,6 +322,13 @@ class Context:
             self._pending_B.pop(ticket, None)
         _check(st)
         return _result(r, buf)
+
+    def serving_stats(self) -> dict:
+        b = ctypes.c_size_t(0)
+        run, q, fin = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(load().ept_serving_stats(self._h, ctypes.byref(b), ctypes.byref(run), ctypes.byref(q),
+                                        ctypes.byref(fin)))
+        return {"bytes_in_use": b.value, "running": run.value, "queued": q.value, "finished": fin.value}
 
     def cancel(self, ticket: int) -> None:
         _check(load().ept_cancel(self._h, ctypes.c_uint64(ticket)))

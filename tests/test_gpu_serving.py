@@ -148,3 +148,40 @@ def test_destroy_with_requests_in_flight(ept):
     for k in range(20):
         c.submit(X, Y, B=2000, seed=k)
     c.close()                            # stops the scheduler, drains running batches, frees everything
+
+
+def test_injected_allocation_failures_leave_no_leaks(ept):
+    # host-side fault injection: the next scratch acquisitions fail with EPT_ENOMEM;
+    # the context keeps working and the serving state drains back to zero
+    c = ept.Context(0)
+    try:
+        X, Y = workloads.gaussian_pair(workloads.SMALL)
+        c.set_option("fault_inject_alloc", 1)
+        with pytest.raises(ept.EptError) as e:
+            c.test(X, Y, B=100, seed=1)
+        assert e.value.status == 2
+        alone = c.test(X, Y, B=100, seed=1)
+        c.set_option("serve_lanes", 1)
+        c.set_option("fault_inject_alloc", 1)
+        t1 = c.submit(X, Y, B=100, seed=1)
+        with pytest.raises(ept.EptError) as e:
+            c.wait(t1)
+        assert e.value.status == 2
+        t2 = c.submit(X, Y, B=100, seed=1)
+        r2 = c.wait(t2)
+        assert r2.observed == alone.observed and r2.n_ge == alone.n_ge
+        assert np.array_equal(np.asarray(r2.stats), np.asarray(alone.stats))
+        assert c.serving_stats() == {"bytes_in_use": 0, "running": 0, "queued": 0, "finished": 0}
+    finally:
+        c.close()
+
+
+def test_serving_stats_while_busy(ctx):
+    X, Y = workloads.gaussian_pair(workloads.HIGHDIM)
+    tickets = [ctx.submit(X, Y, B=10000, seed=k) for k in range(6)]
+    st = ctx.serving_stats()
+    assert st["running"] + st["queued"] + st["finished"] >= 1
+    for t in tickets:
+        ctx.wait(t)
+    st = ctx.serving_stats()
+    assert st["running"] == 0 and st["queued"] == 0 and st["bytes_in_use"] == 0
