@@ -196,6 +196,11 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    EPT_OPT_FAULT_INJECT_ALLOC (test hook, default 0): the next `value` acquisitions
    of device scratch (a run's arena, a serving batch's pool allocation) fail with
    EPT_ENOMEM on the host, without touching the GPU, to exercise error paths.
+   EPT_OPT_FAULT_INJECT_STALL (test hook, default 0): in the next run (tensor-core
+   path, launched directly) the contraction's MMA issuer waits on a device flag that
+   nothing sets; its bounded wait expires after 2 s, every role of the kernel takes
+   the abort path (drain copies, free tensor memory, return) and the call returns
+   EPT_ETIMEOUT; the context stays usable.  One-shot.
    EPT_OPT_SERVE_LANES (default 3, 1..16): serving batches in flight at once;
    EPT_OPT_SERVE_SLOTS (default 256): serving requests in flight at once; both
    before the first ept_submit.  EPT_EINVAL for an unknown option or value. */
@@ -205,7 +210,8 @@ enum {
     EPT_OPT_SERVE_LANES = 3,
     EPT_OPT_SERVE_SLOTS = 4,
     EPT_OPT_DRAW_MODE = 5,
-    EPT_OPT_FAULT_INJECT_ALLOC = 6
+    EPT_OPT_FAULT_INJECT_ALLOC = 6,
+    EPT_OPT_FAULT_INJECT_STALL = 7
 };
 ept_status ept_set_option(ept_ctx *ctx, int option, int64_t value);
 

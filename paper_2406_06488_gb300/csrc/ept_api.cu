@@ -354,6 +354,7 @@ struct ept_ctx {
     bool graphs = true;                 // replay captured graphs of repeated batches
     int draw_mode = 0;                  // relabeling draws: 0 automatic, DRAW_WARPS, DRAW_LANES
     std::atomic<int> inject_alloc{0};   // test hook: the next N scratch acquisitions fail (host side)
+    bool inject_stall = false;          // test hook: the next run's contraction waits out its limit
     int serve_lanes = 3;                // serving: batches in flight at once
     int serve_slots = 256;              // serving: requests in flight at once
     cudaEvent_t ev_user = nullptr;      // orders the context's stream after a caller's stream
@@ -592,6 +593,7 @@ Batch device_view(ept_ctx *c, const Plan &P) {
     b.maskT = (uint32_t *)(A + P.off_maskT);
     b.ctr = (Counters *)(A + P.off_ctr);
     b.sel_hist = P.any_median ? (uint32_t *)(A + P.off_sel_hist) : nullptr;
+    b.inject_stall = c->inject_stall ? 1 : 0;
     return b;
 }
 
@@ -849,6 +851,7 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
     if (s != c->stream) CK(cudaStreamSynchronize(c->stream));
     stage_host(c, P, specs, on_device, !c->tables_staged);
     c->tables_staged = true;
+    if (c->inject_stall) use_graph = false;   // one direct run with the hook, never captured
     if (use_graph && c->graphs) {
         // the graph runs on the context's stream, after the caller's stream's prior work
         if (s != c->stream) {
@@ -889,7 +892,9 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
         if (device_ms) *device_ms = ms;
         return EPT_OK;
     }
-    if ((st = enqueue_device(c, P, s, true)) != EPT_OK) return st;
+    st = enqueue_device(c, P, s, true);
+    c->inject_stall = false;   // the hook is one-shot
+    if (st != EPT_OK) return st;
     CK(cudaStreamSynchronize(s));
     if ((st = collect(c, P, specs, out, true)) != EPT_OK) return st;
     if (device_ms) cudaEventElapsedTime(device_ms, c->ev[5], c->ev[6]);
@@ -1445,6 +1450,9 @@ ept_status ept_set_option(ept_ctx *c, int option, int64_t value) {
     case EPT_OPT_FAULT_INJECT_ALLOC:
         if (value < 0 || value > (1 << 20)) return fail(EPT_EINVAL, "injected failure count must be in [0, 2^20]");
         c->inject_alloc.store((int)value);
+        return EPT_OK;
+    case EPT_OPT_FAULT_INJECT_STALL:
+        c->inject_stall = value != 0;
         return EPT_OK;
     case EPT_OPT_DRAW_MODE:
         if (value < 0 || value > 2) return fail(EPT_EINVAL, "draw mode must be 0, 1 or 2");

@@ -62,7 +62,7 @@ constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 /*barriers*/ + RED_BYTES 
 
 // error codes recorded in Counters::err_code
 constexpr unsigned long long ERR_WAIT_TMA = 0x101, ERR_WAIT_MMA = 0x102, ERR_WAIT_EPI = 0x103,
-                             ERR_WAIT_MASK = 0x104, ERR_DRAIN = 0x105;
+                             ERR_WAIT_MASK = 0x104, ERR_DRAIN = 0x105, ERR_INJECTED = 0x1FF;
 
 constexpr uint32_t IDESC = idesc_f16_f32(TC_M, TC_N);
 
@@ -209,6 +209,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             int stage = 0, acc = 0;
             uint32_t phase = 0, acc_phase = 0;
             bool ok = true;
+            // failure-path test hook: wait (bounded) on a flag that nothing sets; the
+            // expiry takes the same abort path as any other expired wait
+            if (bt.inject_stall && !flag_wait(&ctr->never_set, abort_flag, ctr, ERR_INJECTED)) ok = false;
             for (int64_t k = k_first; k < k_end && ok; k += k_step) {
                 const int64_t u = unit_at(k);
                 const Chunk ch = decode_unit(bt, u).ch;

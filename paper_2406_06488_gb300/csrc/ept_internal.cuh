@@ -63,6 +63,7 @@ struct Counters {
     unsigned int max_u_bits;         //   order like their bit patterns), max |u_i|,
     unsigned int max_dc_bits;        //   max |dcorr_i|: they bound |C| for the FP16 scale of the packing
     unsigned int sel_prefix;         // median heuristic: radix-selection prefix, then the median's bits
+    unsigned int never_set;          // stays 0: the failure-path test hook waits for it
     unsigned long long sel_k;        //   rank still to find within the prefix
 };
 
@@ -143,6 +144,8 @@ struct Batch {
     uint32_t *maskT;
     Counters *ctr;
     uint32_t *sel_hist;                  // median heuristic: 2048 bins per test (null if no test needs it)
+    int inject_stall;                    // failure-path test hook: the contraction's MMA issuer waits on a
+                                         //   flag that nothing sets until its bounded wait expires
 };
 
 // tensor-core contraction work units of a test: chunk x relabeling tile x row half

@@ -68,6 +68,23 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
+// Bounded wait on a device word becoming non-zero (the same limit and abort
+// protocol as mbar_wait).
+__device__ __forceinline__ bool flag_wait(const volatile unsigned int *flag, volatile int *abort_flag, Counters *ctr,
+                                          unsigned long long code) {
+    const unsigned long long t0 = gtimer();
+    for (;;) {
+        if (*flag) return true;
+        if (*abort_flag) return false;
+        if (gtimer() - t0 > WAIT_NS) {
+            *abort_flag = 1;
+            atomicCAS(&ctr->err_code, 0ull, code);
+            return false;
+        }
+        __nanosleep(1000);
+    }
+}
+
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const void *tmap, int c0, int c1, uint32_t bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"

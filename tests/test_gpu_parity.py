@@ -253,3 +253,19 @@ def test_stream_ranges_combine(ctx, prec):
     ref = oracle.permutation_test(X, Y, B=1000, seed=4, stat="ed")
     rel = np.abs(np.asarray(b.stats) - ref["stats"][400:]) / np.abs(ref["stats"][400:])
     assert rel.max() <= REL_TOL
+
+
+def test_expired_device_wait_returns_timeout_and_context_recovers(ctx):
+    # failure path of the tcgen05 contraction, driven without a fault: the MMA issuer
+    # waits on a device flag that nothing sets; the bounded wait expires (2 s), the
+    # kernel aborts cleanly and the call reports EPT_ETIMEOUT
+    from paper_2406_06488_gb300 import ept
+    X, Y = _pair(200, 230, 8, seed=41)
+    ctx.set_option("fault_inject_stall", 1)
+    with pytest.raises(ept.EptError) as e:
+        ctx.test(X, Y, B=500, seed=2, prec="split_bf16")
+    assert e.value.status == 5
+    # one-shot, and the context (tensor memory, streams, graphs) still works
+    res = ctx.test(X, Y, B=500, seed=2, prec="split_bf16")
+    ref = oracle.permutation_test(X, Y, B=500, seed=2, stat="ed")
+    _check(res, ref["stats"], ref["observed"], 500)
