@@ -332,7 +332,88 @@ struct GraphCache {
 
 namespace {
 struct Server;
-}
+
+// Host memory copies spread over a small pool of worker threads (the caller works
+// too), used to gather pageable inputs into the pinned staging area at several times
+// the bandwidth of one core.  run() returns when every byte is copied.
+class HostCopier {
+public:
+    struct Job {
+        void *dst;
+        const void *src;
+        size_t bytes;
+    };
+    explicit HostCopier(int workers) {
+        for (int k = 0; k < workers; ++k) th_.emplace_back([this] { worker(); });
+    }
+    ~HostCopier() {
+        {
+            std::lock_guard<std::mutex> lk(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (std::thread &t : th_) t.join();
+    }
+    void run(const std::vector<Job> &jobs) {
+        constexpr size_t PIECE = 1 << 20;
+        {
+            std::unique_lock<std::mutex> lk(mu_);
+            cv_done_.wait(lk, [this] { return active_ == 0; });   // a late worker of the last run has left
+            pieces_.clear();
+            for (const Job &j : jobs)
+                for (size_t o = 0; o < j.bytes; o += PIECE)
+                    pieces_.push_back({(uint8_t *)j.dst + o, (const uint8_t *)j.src + o, std::min(PIECE, j.bytes - o)});
+            next_.store(0);
+            remaining_.store(pieces_.size());
+            ++gen_;
+        }
+        cv_.notify_all();
+        work();
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_done_.wait(lk, [this] { return remaining_.load() == 0 && active_ == 0; });
+    }
+
+private:
+    void work() {
+        const size_t n = pieces_.size();
+        for (;;) {
+            const size_t k = next_.fetch_add(1);
+            if (k >= n) break;
+            memcpy(pieces_[k].dst, pieces_[k].src, pieces_[k].bytes);
+            if (remaining_.fetch_sub(1) == 1) {
+                std::lock_guard<std::mutex> lk(mu_);
+                cv_done_.notify_all();
+            }
+        }
+    }
+    void worker() {
+        uint64_t seen = 0;
+        for (;;) {
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return stop_ || gen_ != seen; });
+                if (stop_) return;
+                seen = gen_;
+                ++active_;
+            }
+            work();
+            {
+                std::lock_guard<std::mutex> lk(mu_);
+                --active_;
+            }
+            cv_done_.notify_all();
+        }
+    }
+    std::vector<std::thread> th_;
+    std::mutex mu_;
+    std::condition_variable cv_, cv_done_;
+    std::vector<Job> pieces_;
+    std::atomic<size_t> next_{0}, remaining_{0};
+    int active_ = 0;
+    uint64_t gen_ = 0;
+    bool stop_ = false;
+};
+}  // namespace
 
 struct ept_ctx {
     Server *server = nullptr;           // serving scheduler, started by the first ept_submit
@@ -373,6 +454,7 @@ struct ept_ctx {
         size_t bytes;
     };
     std::vector<InputCopy> in_copies;
+    std::unique_ptr<HostCopier> copier;   // started by the first large pageable input
     std::string tune_file;
 };
 
@@ -491,13 +573,16 @@ void stage_host(ept_ctx *c, Plan &P, const std::vector<TestSpec> &specs, bool on
     uint8_t *A = c->arena, *pin = c->pinned;
     c->in_copies.clear();
     bool all_staged = true;
+    std::vector<HostCopier::Job> gather;
+    size_t gather_bytes = 0;
     auto input = [&](size_t off, const void *src, size_t bytes) {
         if (bytes == 0) return;
         if (page_locked(src)) {
             c->in_copies.push_back({P.off_in + off, src, bytes});
             all_staged = false;
         } else {
-            memcpy(pin + S.inputs + off, src, bytes);
+            gather.push_back({pin + S.inputs + off, src, bytes});
+            gather_bytes += bytes;
             c->in_copies.push_back({P.off_in + off, pin + S.inputs + off, bytes});
         }
     };
@@ -524,6 +609,15 @@ void stage_host(ept_ctx *c, Plan &P, const std::vector<TestSpec> &specs, bool on
             }
             d.out_stats = nullptr;   // copied back to the host and scattered there
         }
+    }
+    if (gather_bytes >= ((size_t)4 << 20)) {
+        if (!c->copier) {
+            const unsigned hw = std::thread::hardware_concurrency();
+            c->copier.reset(new HostCopier((int)std::max(1u, std::min(8u, hw / 2))));
+        }
+        c->copier->run(gather);
+    } else {
+        for (const HostCopier::Job &j : gather) memcpy(j.dst, j.src, j.bytes);
     }
     if (!on_device && all_staged && P.in_bytes) {
         // everything went through the staging area: one copy of the whole input region
