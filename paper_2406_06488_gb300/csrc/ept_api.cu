@@ -141,7 +141,8 @@ void plan_schedule(Plan &P, int num_sms) {
         const int64_t u0 = P.pre_units[t], nu = P.pre_units[t + 1] - u0;
         for (int64_t lu = 0; lu < nu; ++lu) {
             const Chunk &ch = P.chunks[(size_t)(d.chunk0 + (lu >> 1) / d.MT)];
-            const int l = ch.kb1 - ch.kb0;
+            int l = ch.kb1 - ch.kb0;
+            if ((lu & 1) && ch.kb0 == KB_PER_PANEL * ch.I && l > 2) l -= 2;   // zero blocks the kernel skips
             len[(size_t)(u0 + lu)] = l;
             maxlen = std::max(maxlen, l);
         }

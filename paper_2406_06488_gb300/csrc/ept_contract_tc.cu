@@ -86,6 +86,7 @@ static_assert(sizeof(Bars) <= 512, "barriers overlap the nibble table");
 struct Unit {
     Chunk ch;
     int64_t q, m, h, Bp, mask0, part0, blk0, NKB;
+    int ncols;   // relabeling columns of the tile that exist, rounded up to 16 (the MMA's N)
 };
 
 __device__ __forceinline__ Unit decode_unit(const Batch &bt, int64_t u) {
@@ -103,6 +104,12 @@ __device__ __forceinline__ Unit decode_unit(const Batch &bt, int64_t u) {
     x.blk0 = d->blk0;
     x.NKB = d->NKB;
     x.ch = bt.chunks[d->chunk0 + x.q];
+    // the first two K-blocks of a panel's diagonal square lie below the diagonal for
+    // the second row half: all zero in C, skipped
+    if (x.h == 1 && x.ch.kb0 == KB_PER_PANEL * x.ch.I && x.ch.kb1 - x.ch.kb0 > 2) x.ch.kb0 += 2;
+    // the last relabeling tile of a test is partial: the MMA's N covers its columns only
+    const int64_t left = d->ncols - x.m * TC_N;
+    x.ncols = left >= TC_N ? TC_N : (int)((left + 15) / 16 * 16);
     return x;
 }
 
@@ -214,7 +221,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             if (bt.inject_stall && !flag_wait(&ctr->never_set, abort_flag, ctr, ERR_INJECTED)) ok = false;
             for (int64_t k = k_first; k < k_end && ok; k += k_step) {
                 const int64_t u = unit_at(k);
-                const Chunk ch = decode_unit(bt, u).ch;
+                const Unit x = decode_unit(bt, u);
+                const Chunk ch = x.ch;
+                const uint32_t idesc = (x.ncols == TC_N) ? IDESC : idesc_f16_f32(TC_M, x.ncols);
                 if (!mbar_wait(su32(&bars->acc_empty[acc]), acc_phase ^ 1u, abort_flag, ctr, ERR_WAIT_MMA)) {
                     ok = false;
                     break;
@@ -235,9 +244,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     const uint64_t db = desc_sw128(sa + 2 * A_BYTES);
 #pragma unroll
                     for (int k = 0; k < KB / 16; ++k)
-                        mma_f16(d_tmem, dhi + 2 * k, db + 2 * k, IDESC, (first && k == 0) ? 0u : 1u);
+                        mma_f16(d_tmem, dhi + 2 * k, db + 2 * k, idesc, (first && k == 0) ? 0u : 1u);
 #pragma unroll
-                    for (int k = 0; k < KB / 16; ++k) mma_f16(d_tmem, dlo + 2 * k, db + 2 * k, IDESC, 1u);
+                    for (int k = 0; k < KB / 16; ++k) mma_f16(d_tmem, dlo + 2 * k, db + 2 * k, idesc, 1u);
                     mma_commit(su32(&bars->empty[stage]));
                     first = false;
                     if (++stage == STAGES) {
@@ -359,15 +368,17 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     break;
                 }
                 uint8_t *brow = smem + stage * STAGE_BYTES + 2 * A_BYTES + r * 128;
+                if (r < x.ncols) {   // rows past the tile's columns are not read by the MMA
 #pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const uint32_t w = c < 4 ? cur.x : cur.y;
-                    const uint2 lo = lut[(w >> (8 * (c & 3))) & 15u];
-                    const uint2 hi = lut[(w >> (8 * (c & 3) + 4)) & 15u];
-                    const uint32_t dst = su32(brow + ((c ^ (r & 7)) << 4));
-                    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(lo.x), "r"(lo.y),
-                                 "r"(hi.x), "r"(hi.y)
-                                 : "memory");
+                    for (int c = 0; c < 8; ++c) {
+                        const uint32_t w = c < 4 ? cur.x : cur.y;
+                        const uint2 lo = lut[(w >> (8 * (c & 3))) & 15u];
+                        const uint2 hi = lut[(w >> (8 * (c & 3) + 4)) & 15u];
+                        const uint32_t dst = su32(brow + ((c ^ (r & 7)) << 4));
+                        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(dst), "r"(lo.x), "r"(lo.y),
+                                     "r"(hi.x), "r"(hi.y)
+                                     : "memory");
+                    }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(su32(&bars->b_full[stage]));
