@@ -342,10 +342,12 @@ def run_ours(args):
     peak = float(peaks.get("bf16_tflops", 1900.0))
     n_pad = (n + 255) // 256 * 256
     npan = n_pad // 256
-    # issued MMA work: hi and lo passes over the stored upper panels, less the two
-    # all-zero K-blocks of each diagonal square's second row half, over the relabeling
+    # issued MMA work: hi and lo passes over the stored upper panels up to the last
+    # K-block with real columns, less the two all-zero K-blocks of each diagonal
+    # square's second row half, over the relabeling
     # tiles (the last one sized to its columns, rounded up to 16)
-    stored = sum((n_pad - 256 * I) * 256 for I in range(npan)) - npan * 128 * 128
+    nkb = (n + 63) // 64   # K-blocks holding real columns (the contraction stops there)
+    stored = sum((nkb - 4 * I) * 64 * 256 for I in range(npan)) - npan * 128 * 128
     ncols = spec.B + 1
     cols = (ncols // 256) * 256 + ((ncols % 256 + 15) // 16 * 16 if ncols % 256 else 0)
     mma_flops = 2.0 * 2.0 * stored * cols

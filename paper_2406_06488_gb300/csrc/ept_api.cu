@@ -216,8 +216,11 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
         d.col0 = P.nstats;
         for (int64_t I = 0; I < d.NP; ++I) {
             for (int64_t kb = KB_PER_PANEL * I; kb < d.NKB; ++kb) P.blk.push_back(BlkInfo{t, (int)I, (int)kb, 0});
-            for (int64_t kb = KB_PER_PANEL * I; kb < d.NKB; kb += chunk_kb)
-                P.chunks.push_back(Chunk{(int)I, (int)kb, (int)std::min<int64_t>(kb + chunk_kb, d.NKB), 0});
+            // contraction chunks stop at the last K-block holding real columns (the
+            // padding columns of C are zero)
+            const int64_t NKBc = (d.n + KB - 1) / KB;
+            for (int64_t kb = KB_PER_PANEL * I; kb < NKBc; kb += chunk_kb)
+                P.chunks.push_back(Chunk{(int)I, (int)kb, (int)std::min<int64_t>(kb + chunk_kb, NKBc), 0});
             if (tc)
                 for (int64_t J = I; J < d.NP; ++J)
                     for (int h = 0; h < 2; ++h) P.tiles.push_back(Tile{t, (int)I, (int)J, h});
