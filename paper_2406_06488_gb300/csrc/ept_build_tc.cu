@@ -20,9 +20,10 @@
 // Tile = 128 rows (half of a 256-row panel I) x 256 columns (panel J >= I, four
 // K-blocks); K loop over p in steps of 64 with TMA loads of the four operand tiles
 // (A hi/lo 128 x 64, B hi/lo 256 x 64, 128-byte swizzle); two TMEM accumulators so
-// the epilogue of one tile overlaps the main loop of the next.  Roles (192
-// threads): warp 0 TMA, warp 1 MMA + TMEM owner, warps 2-5 epilogue.  All waits
-// are bounded as in the contraction kernel.
+// the epilogue of one tile overlaps the main loop of the next.  Roles (320
+// threads): warp 0 TMA, warp 1 MMA + TMEM owner, warps 2-9 epilogue (two per TMEM
+// lane quarter, each taking half of the tile's columns).  All waits are bounded as
+// in the contraction kernel.
 #include <cuda.h>
 #include <cuda_fp16.h>
 
@@ -45,9 +46,10 @@ constexpr int STAGES = 2;
 constexpr int A_BYTES = BM * BK * 2;                  // 16 KB
 constexpr int B_BYTES = BN * BK * 2;                  // 32 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 96 KB: A hi, A lo, B hi, B lo
-constexpr int NUM_THREADS = 192;
-// stages | barriers (1 KB) | per-epilogue-warp column norms and scales (4 x 2 KB) | alignment slack
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 4 * PANEL * 8 + 1024;
+constexpr int NUM_THREADS = 320;   // TMA warp, MMA warp, 8 epilogue warps
+constexpr int EPI_THREADS = 256;
+// stages | barriers (1 KB) | per-epilogue-warp column norms and scales (8 x 1 KB) | alignment slack
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 8 * (PANEL / 2) * 8 + 1024;
 // kind::f16 instruction descriptor with A = B = FP16 (format 0), D = FP32, K-major
 constexpr uint32_t IDESC = idesc_f16_f32(BM, BN);
 
@@ -185,7 +187,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(su32(&bars->acc_full[a]), 1);
-            mbar_init(su32(&bars->acc_empty[a]), 128);
+            mbar_init(su32(&bars->acc_empty[a]), EPI_THREADS);
         }
         mbar_init(su32(&bars->drain), 1);
         bars->abort_flag = 0;
@@ -304,9 +306,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         // entries without branches, patches padding and the diagonal with selects, and
         // recomputes the rare cancellation-prone entries afterwards (same thread, so
         // its later store wins).
+        // two warps per TMEM lane quarter: each takes one half (128 columns) of the tile
         const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int rt = quarter * 32 + lane;   // row within the 128-row tile
-        float2 *colv = reinterpret_cast<float2 *>(smem + STAGES * STAGE_BYTES + 1024) + (warp - 2) * PANEL;
+        float2 *colv = reinterpret_cast<float2 *>(smem + STAGES * STAGE_BYTES + 1024) + (warp - 2) * (PANEL / 2);
         int acc = 0;
         uint32_t acc_phase = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -326,8 +330,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             const float si = (i < n) ? inv_scale[i] : 0.f;
             __syncwarp();
 #pragma unroll
-            for (int c = lane; c < PANEL; c += 32) {
-                const int64_t j = (int64_t)tile.J * PANEL + c;
+            for (int c = lane; c < PANEL / 2; c += 32) {
+                const int64_t j = (int64_t)tile.J * PANEL + half * (PANEL / 2) + c;
                 colv[c] = (j < n) ? make_float2(norms[j], inv_scale[j]) : make_float2(0.f, 0.f);
             }
             __syncwarp();
@@ -335,12 +339,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             fence_after();
             const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1
-            for (int g = 0; g < BN / 32; ++g) {
+            for (int gl = 0; gl < BN / 64; ++gl) {
+                const int g = half * (BN / 64) + gl;   // column group of the tile
                 uint32_t v[32];
                 tmem_ld32(tbase + (uint32_t)(g * 32), v);
                 const int64_t j0 = (int64_t)tile.J * PANEL + g * 32;
                 float out[32];
-                const float2 *cg = colv + g * 32;
+                const float2 *cg = colv + gl * 32;
                 uint32_t fix = (kern == 0)   ? group_entries<0>(v, cg, ni, si, tau, neg_inv_2s2, inv_sigma, out)
                                : (kern == 1) ? group_entries<1>(v, cg, ni, si, tau, neg_inv_2s2, inv_sigma, out)
                                              : group_entries<2>(v, cg, ni, si, tau, neg_inv_2s2, inv_sigma, out);
