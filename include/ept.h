@@ -52,7 +52,8 @@ typedef enum {
     EPT_ETIMEOUT = 5,     /* a device-side bounded wait gave up, or ept_wait timed out */
     EPT_ECANCELLED = 6,   /* serving: the request was cancelled */
     EPT_ENOTFOUND = 7,    /* serving: unknown ticket */
-    EPT_EUNSUPPORTED = 8  /* the device is not an sm_103 GPU, or a mode is unavailable */
+    EPT_EUNSUPPORTED = 8, /* the device is not an sm_103 GPU, or a mode is unavailable */
+    EPT_EINTERNAL = 9     /* debug checks found a broken invariant (EPT_OPT_DEBUG_CHECKS) */
 } ept_status;
 
 typedef enum {
@@ -201,6 +202,11 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    nothing sets; its bounded wait expires after 2 s, every role of the kernel takes
    the abort path (drain copies, free tensor memory, return) and the call returns
    EPT_ETIMEOUT; the context stays usable.  One-shot.
+   EPT_OPT_DEBUG_CHECKS (default 0): a stand-in for a memory checker -- every scratch
+   region of a run is followed by a 256-byte guard band filled with a pattern before
+   the run and checked after it, and the host checks the plan's invariants (tables,
+   chunk ranges, the contraction schedule covering every unit once); a violation
+   returns EPT_EINTERNAL.
    EPT_OPT_SERVE_LANES (default 3, 1..16): serving batches in flight at once;
    EPT_OPT_SERVE_SLOTS (default 256): serving requests in flight at once; both
    before the first ept_submit.  EPT_EINVAL for an unknown option or value. */
@@ -211,7 +217,8 @@ enum {
     EPT_OPT_SERVE_SLOTS = 4,
     EPT_OPT_DRAW_MODE = 5,
     EPT_OPT_FAULT_INJECT_ALLOC = 6,
-    EPT_OPT_FAULT_INJECT_STALL = 7
+    EPT_OPT_FAULT_INJECT_STALL = 7,
+    EPT_OPT_DEBUG_CHECKS = 8
 };
 ept_status ept_set_option(ept_ctx *ctx, int option, int64_t value);
 

@@ -94,6 +94,8 @@ struct Plan {
     std::vector<int64_t> sched, sched_off;   // contraction schedule: units of CTA c = sched[sched_off[c] ..)
     bool user_masks = false;                 // some test brings its own relabelings
     bool any_median = false;                 // some test takes its bandwidth from the median heuristic
+    bool debug = false;                      // guard bands around the scratch regions
+    GuardList guards{};
     size_t off_sel_hist = 0;
     int tc_grid = 0;                         // contraction CTAs
     std::vector<size_t> in_off;       // per test: byte offset of its X (then Y, then masks) in the input region
@@ -167,8 +169,9 @@ void plan_schedule(Plan &P, int num_sms) {
 }
 
 void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host_in, int chunk_kb,
-                int num_sms = 160) {
+                int num_sms = 160, bool debug = false) {
     P = Plan();
+    P.debug = debug;
     P.n_tests = (int)specs.size();
     P.prec = prec;
     P.host_in = host_in;
@@ -258,9 +261,14 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
     P.in_bytes = in_bytes;
 
     size_t o = 0;
+    bool in_data = false;   // guard bands follow the data regions (the tables are uploaded whole)
     auto take = [&](size_t bytes) {
         const size_t at = o;
         o = align_up(o + std::max<size_t>(bytes, 1), 256);
+        if (P.debug && in_data && P.guards.n < MAX_GUARDS) {
+            P.guards.off[P.guards.n++] = o;
+            o += GUARD_BYTES;
+        }
         return at;
     };
     const size_t nt1 = (size_t)P.n_tests + 1;
@@ -277,6 +285,11 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
     P.off_sched_off = take(8 * P.sched_off.size());
     P.tab_bytes = o;
     o = align_up(o, 1024);
+    in_data = true;
+    if (P.debug) {   // a band right after the tables as well
+        P.guards.off[P.guards.n++] = o;
+        o += GUARD_BYTES;
+    }
     const size_t elems = (size_t)P.nblk * PANEL * KB;
     P.off_in = take(P.in_bytes);
     P.off_norms = take((size_t)P.nrows * 4);
@@ -301,6 +314,35 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
     P.off_ctr = take(sizeof(Counters) * P.n_tests);
     P.off_sel_hist = P.any_median ? take((size_t)P.n_tests * 2048 * 4) : 0;
     P.total = o;
+}
+
+// Debug checks on the host: invariants of a plan that the kernels rely on.
+ept_status check_plan(const Plan &P) {
+    auto bad = [](const char *what) { return fail(EPT_EINTERNAL, "debug checks: plan invariant broken: %s", what); };
+    for (int t = 0; t < P.n_tests; ++t) {
+        const TestDesc &d = P.desc[t];
+        if (d.n != d.nx + d.ny || d.n_pad < d.n || d.n_pad % PANEL) return bad("row padding");
+        if (d.Bp < d.ncols || d.Bp % COL_PAD || d.MT * TC_TILE_N != d.Bp) return bad("column padding");
+        if (P.pre_rows[t + 1] - P.pre_rows[t] != d.n_pad || d.row0 != P.pre_rows[t]) return bad("row prefix");
+        if (P.pre_cols[t + 1] - P.pre_cols[t] != d.Bp) return bad("column prefix");
+        for (int64_t q = 0; q < d.nchunks; ++q) {
+            const Chunk &ch = P.chunks[(size_t)(d.chunk0 + q)];
+            if (ch.I < 0 || ch.I >= d.NP || ch.kb0 < KB_PER_PANEL * ch.I || ch.kb1 <= ch.kb0 || ch.kb1 > d.NKB)
+                return bad("chunk range");
+        }
+        if (d.nparts != 2 * d.nchunks) return bad("partials");
+    }
+    if (!P.sched.empty()) {
+        std::vector<char> seen((size_t)P.nunits, 0);
+        if ((int64_t)P.sched.size() != P.nunits || P.sched_off.back() != P.nunits) return bad("schedule size");
+        for (int64_t u : P.sched) {
+            if (u < 0 || u >= P.nunits || seen[(size_t)u]) return bad("schedule covers every unit once");
+            seen[(size_t)u] = 1;
+        }
+    }
+    for (int k = 0; k < P.guards.n; ++k)
+        if (P.guards.off[k] + GUARD_BYTES > P.total || P.guards.off[k] % 256) return bad("guard band");
+    return EPT_OK;
 }
 
 std::vector<TestSpec> one_test(const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p, int stat,
@@ -437,6 +479,7 @@ struct ept_ctx {
     std::map<std::vector<int64_t>, int> tuned_chunk;   // autotuner cache: batch shape -> chunk length
     bool autotune = true;
     bool graphs = true;                 // replay captured graphs of repeated batches
+    bool debug = false;                 // guard bands around scratch regions, plan invariants checked
     int draw_mode = 0;                  // relabeling draws: 0 automatic, DRAW_WARPS, DRAW_LANES
     std::atomic<int> inject_alloc{0};   // test hook: the next N scratch acquisitions fail (host side)
     bool inject_stall = false;          // test hook: the next run's contraction waits out its limit
@@ -730,6 +773,7 @@ ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed,
     if (with_inputs && (st = enqueue_uploads(c, P, s)) != EPT_OK) return st;
     CK(cudaMemsetAsync(b.ctr, 0, sizeof(Counters) * P.n_tests, s));
     if (P.any_median) CK(cudaMemsetAsync(b.sel_hist, 0, (size_t)P.n_tests * 2048 * 4, s));
+    if (P.debug) launch_guards(c->arena, P.guards, false, b.ctr, s);
     CK(cudaEventRecord(c->ev[1], s));
 
     // relabelings on the side stream, beside the block build
@@ -781,6 +825,7 @@ ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed,
     if (timed) CK(cudaEventRecord(c->ev[6], s));
     launch_combine(b, s);
     CK(cudaGetLastError());
+    if (P.debug) launch_guards(c->arena, P.guards, true, b.ctr, s);   // after every write of the run
     if (timed) CK(cudaEventRecord(c->ev[3], s));
 
     CK(cudaMemcpyAsync(pin + S.res_ctr, b.ctr, sizeof(Counters) * P.n_tests, cudaMemcpyDeviceToHost, s));
@@ -827,6 +872,9 @@ ept_status collect(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &specs
     const double *stats = (const double *)(c->pinned + S.res_stats);
     if (P.n_tests > 0 && ctr[0].err_code)
         return fail(EPT_ETIMEOUT, "device-side bounded wait gave up (code 0x%llx)", (unsigned long long)ctr[0].err_code);
+    if (P.debug && P.n_tests > 0 && ctr[0].guard_bad)
+        return fail(EPT_EINTERNAL, "debug checks: %llu words of the scratch guard bands were overwritten",
+                    (unsigned long long)ctr[0].guard_bad);
     if (per_test) per_test->assign(P.n_tests, TestError{EPT_OK, std::string()});
     for (int t = 0; t < P.n_tests; ++t) {
         const ept_status st = test_error(P, ctr, t);
@@ -927,16 +975,22 @@ void load_tune_file(ept_ctx *c) {
 ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bool on_device, int chunk_kb,
                     bool use_graph, ept_result *out, void *stream, float *device_ms) {
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    ept_status st0 = EPT_OK;
     std::vector<int64_t> pkey = shape_key(specs, prec, on_device);
     pkey.push_back(chunk_kb);
+    pkey.push_back(c->debug ? 1 : 0);
     if (!c->plan) {
         c->plan = new (std::nothrow) Plan();
         if (!c->plan) return fail(EPT_ENOMEM, "host allocation failed");
     }
     if (c->plan_key != pkey) {
-        plan_batch(*c->plan, specs, prec, !on_device, chunk_kb, c->num_sms);
+        plan_batch(*c->plan, specs, prec, !on_device, chunk_kb, c->num_sms, c->debug);
         c->plan_key = pkey;
         c->tables_staged = false;
+        if (c->debug && (st0 = check_plan(*c->plan)) != EPT_OK) {
+            c->plan_key.clear();
+            return st0;
+        }
     }
     Plan &P = *c->plan;
     for (int t = 0; t < P.n_tests; ++t) set_test_params(P.desc[t], specs[t]);
@@ -959,6 +1013,7 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
         }
         std::vector<int64_t> key = shape_key(specs, prec, on_device);
         key.push_back(chunk_kb);
+        key.push_back(c->debug ? 1 : 0);
         if (!(c->graph.exec && c->graph.key == key && c->graph.arena == c->arena)) {
             drop_graph(c);
             cudaGraph_t g = nullptr;
@@ -1551,6 +1606,11 @@ ept_status ept_set_option(ept_ctx *c, int option, int64_t value) {
         return EPT_OK;
     case EPT_OPT_FAULT_INJECT_STALL:
         c->inject_stall = value != 0;
+        return EPT_OK;
+    case EPT_OPT_DEBUG_CHECKS:
+        c->debug = value != 0;
+        c->plan_key.clear();
+        drop_graph(c);
         return EPT_OK;
     case EPT_OPT_DRAW_MODE:
         if (value < 0 || value > 2) return fail(EPT_EINVAL, "draw mode must be 0, 1 or 2");

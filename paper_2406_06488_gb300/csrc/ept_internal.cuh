@@ -65,7 +65,18 @@ struct Counters {
     unsigned int sel_prefix;         // median heuristic: radix-selection prefix, then the median's bits
     unsigned int never_set;          // stays 0: the failure-path test hook waits for it
     unsigned long long sel_k;        //   rank still to find within the prefix
+    unsigned long long guard_bad;    // debug checks: words of the guard bands found overwritten
 };
+
+// Debug checks: guard bands of GUARD_BYTES after every scratch region, filled with a
+// per-band pattern before a run and checked after it.
+constexpr int GUARD_BYTES = 256;
+constexpr int MAX_GUARDS = 48;
+struct GuardList {
+    int n;
+    uint64_t off[MAX_GUARDS];
+};
+void launch_guards(uint8_t *arena, const GuardList &g, bool check, Counters *ctr, cudaStream_t s);
 
 // Power-of-two scale c of a test's packed contraction operand, from the bound
 // |C_ij| <= 2 (max|D| + 2 max|u|) + max|dcorr|: c |C| < 2^14, inside FP16's range.

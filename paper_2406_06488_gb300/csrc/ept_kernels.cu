@@ -1010,4 +1010,28 @@ void launch_expand_blocks(const float *D, int64_t n, int64_t NKB, float *out, cu
     k_expand<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(D, n, NKB, out);
 }
 
+// ---------------------------------------------------------------------------
+// Debug checks: one CTA per guard band fills it with a pattern that depends on the
+// band's index, or counts the words that no longer hold it.
+__global__ void k_guards(uint8_t *arena, GuardList g, int check, Counters *ctr) {
+    const int k = blockIdx.x;
+    if (k >= g.n) return;
+    uint32_t *w = reinterpret_cast<uint32_t *>(arena + g.off[k]);
+    const uint32_t pat = 0xA5C3E1F0u ^ (uint32_t)(k * 0x9E3779B9u);
+    unsigned bad = 0;
+    for (int i = threadIdx.x; i < GUARD_BYTES / 4; i += blockDim.x) {
+        if (check) bad += (w[i] != (pat ^ (uint32_t)i));
+        else w[i] = pat ^ (uint32_t)i;
+    }
+    if (check) {
+        for (int off = 16; off; off >>= 1) bad += __shfl_xor_sync(0xFFFFFFFFu, bad, off);
+        if ((threadIdx.x & 31) == 0 && bad) atomicAdd(&ctr->guard_bad, (unsigned long long)bad);
+    }
+}
+
+void launch_guards(uint8_t *arena, const GuardList &g, bool check, Counters *ctr, cudaStream_t s) {
+    if (g.n <= 0) return;
+    k_guards<<<(unsigned)g.n, 32, 0, s>>>(arena, g, check ? 1 : 0, ctr);
+}
+
 }  // namespace ept

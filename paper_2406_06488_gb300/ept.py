@@ -25,7 +25,7 @@ SIGMA_MEDIAN = -1.0   # EPT_SIGMA_MEDIAN: bandwidth from the median heuristic
 ABI_VERSION = 2       # EPT_ABI_VERSION this binding's structures follow
 PREC = {"plain_fp32": 0, "split_bf16": 1}
 STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT_ECUDA", 5: "EPT_ETIMEOUT",
-          6: "EPT_ECANCELLED", 7: "EPT_ENOTFOUND", 8: "EPT_EUNSUPPORTED"}
+          6: "EPT_ECANCELLED", 7: "EPT_ENOTFOUND", 8: "EPT_EUNSUPPORTED", 9: "EPT_EINTERNAL"}
 
 # every entry point declared in include/ept.h
 EXPORTS = ["ept_abi_version", "ept_last_error", "ept_create", "ept_destroy", "ept_estimate_bytes", "ept_test",
@@ -168,7 +168,7 @@ def estimate_bytes(nx: int, ny: int, p: int, B: int, prec="split_bf16") -> int:
 
 
 OPTION = {"graphs": 1, "autotune": 2, "serve_lanes": 3, "serve_slots": 4, "draw_mode": 5,
-          "fault_inject_alloc": 6, "fault_inject_stall": 7}
+          "fault_inject_alloc": 6, "fault_inject_stall": 7, "debug_checks": 8}
 
 
 class Context:
