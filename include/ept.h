@@ -281,7 +281,7 @@ ept_status ept_build_blocks(ept_ctx *ctx, const float *X, int64_t nx, const floa
    of the GPU's memory, or a latency-critical loop in which an allocation (which
    can synchronise the whole device) is not acceptable.
    All scratch lives in one file-scope device array of EPT_STATIC_SCRATCH_BYTES; a
-   test whose scratch does not fit (roughly nx + ny above ~1500 at B = 10^4, or more
+   test whose scratch does not fit (roughly nx + ny above ~2300 at B = 10^4, or more
    permutations for smaller n) is rejected with EPT_EINVAL and a message giving the
    bytes it needs.  The call runs on the calling thread's current device and on
    `stream` (NULL = the legacy default stream); its first call on a device looks up

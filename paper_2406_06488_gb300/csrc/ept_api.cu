@@ -105,7 +105,7 @@ struct Plan {
     // byte offsets in the arena; the first tab_bytes are the uploaded tables
     size_t off_desc, off_pre_rows, off_pre_panels, off_pre_cols, off_pre_units, off_pre_simt, off_blk, off_tiles,
         off_chunks, off_sched, off_sched_off, tab_bytes;
-    size_t off_in, off_norms, off_iscale, off_u, off_Zh, off_Zl, off_D, off_Chi, off_Clo, off_rowpart, off_colpart,
+    size_t off_in, off_norms, off_iscale, off_u, off_Zh, off_Zl, off_D, off_Chi, off_rowpart, off_colpart,
         off_r, off_Spart, off_dcorr, off_Upart, off_Stpart, off_maskT, off_partial, off_stats, off_observed, off_ctr,
         total;
 };
@@ -298,8 +298,7 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
     P.off_Zh = tc ? take((size_t)P.nrows * P.p_stride * 2) : 0;
     P.off_Zl = tc ? take((size_t)P.nrows * P.p_stride * 2) : 0;
     P.off_D = take(elems * 4);
-    P.off_Chi = tc ? take(elems * 2) : 0;
-    P.off_Clo = tc ? take(elems * 2) : 0;
+    P.off_Chi = P.off_D;   // the split parts are written over the blocks' FP32 storage
     P.off_rowpart = take((size_t)P.nblk * PANEL * 8);
     P.off_colpart = take((size_t)P.nblk * KB * 8);
     P.off_r = take((size_t)P.nrows * 8);
@@ -718,8 +717,9 @@ Batch device_view(ept_ctx *c, const Plan &P) {
     b.u = (float *)(A + P.off_u);
     b.Zh = (uint16_t *)(A + P.off_Zh);
     b.Zl = (uint16_t *)(A + P.off_Zl);
-    b.Chi = (uint16_t *)(A + P.off_Chi);
-    b.Clo = (uint16_t *)(A + P.off_Clo);
+    b.Chi = (uint16_t *)(A + P.off_D);            // block b: hi at its first 32 KB,
+    b.Clo = b.Chi + (size_t)PANEL * KB;           //          lo at its second 32 KB
+    b.c_stride = 2 * (int64_t)PANEL * KB;
     b.D = (float *)(A + P.off_D);
     b.partial = (float *)(A + P.off_partial);
     b.rowpart = (double *)(A + P.off_rowpart);
@@ -816,7 +816,8 @@ ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed,
     if (tc) {
         alignas(64) CUtensorMap th, tl;
         char emsg[160];
-        if (!encode_block_tmaps(&th, &tl, b.Chi, b.Clo, P.nblk, emsg, sizeof(emsg))) return fail(EPT_ECUDA, "%s", emsg);
+        if (!encode_block_tmaps(&th, &tl, b.Chi, b.Clo, P.nblk, b.c_stride, emsg, sizeof(emsg)))
+            return fail(EPT_ECUDA, "%s", emsg);
         CK(launch_contract_tc(b, &th, &tl, c->num_sms, s));
     } else {
         launch_contract_simt(b, s);

@@ -463,11 +463,11 @@ bool encode_rows_tmaps(void *tmaps4, const uint16_t *Zh, const uint16_t *Zl, int
 }
 
 bool encode_block_tmaps(void *tmap_hi, void *tmap_lo, const uint16_t *Chi, const uint16_t *Clo, int64_t nblk,
-                        char *err, size_t errlen) {
+                        int64_t c_stride, char *err, size_t errlen) {
     EncodeTiledFn enc = encode_fn(err, errlen);
     if (!enc) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)KB, (cuuint64_t)PANEL, (cuuint64_t)nblk};
-    const cuuint64_t strides[2] = {(cuuint64_t)KB * 2, (cuuint64_t)KB * 2 * PANEL};
+    const cuuint64_t strides[2] = {(cuuint64_t)KB * 2, (cuuint64_t)c_stride * 2};
     const cuuint32_t box[3] = {(cuuint32_t)KB, (cuuint32_t)TC_M, 1};   // 128 rows of a block per copy
     const cuuint32_t estr[3] = {1, 1, 1};
     void *ptrs[2] = {(void *)Chi, (void *)Clo};

@@ -149,7 +149,8 @@ struct Batch {
     int64_t nblk_total, ntiles, nrows_total, npan_total, ncols_total, nunits_total, nsimt_total;
     int64_t p_stride;                    // row stride of the FP16 rows (max p_pad)
     float *norms, *iscale, *u;
-    uint16_t *Zh, *Zl, *Chi, *Clo;
+    uint16_t *Zh, *Zl, *Chi, *Clo;       // Chi / Clo: the split parts of block b start at b * c_stride
+    int64_t c_stride;
     float *D, *partial;
     double *rowpart, *colpart, *r, *Spart, *dcorr, *Upart, *Stpart, *stats, *observed;
     uint32_t *maskT;
@@ -216,10 +217,11 @@ void launch_split_rows(const Batch &b, cudaStream_t s);                  // FP16
 cudaError_t launch_build_tc(const Batch &b, const void *tmaps4, int num_sms, cudaStream_t s);
 cudaError_t launch_contract_tc(const Batch &b, const void *tmap_hi, const void *tmap_lo, int num_sms,
                                cudaStream_t s);
-// TMA descriptors: the packed hi/lo blocks [nblk_total x 256 x 64] and the FP16
+// TMA descriptors: the packed hi/lo blocks [nblk_total x 256 x 64], block stride
+// c_stride halves, and the FP16
 // rows [nrows x p_stride] (hi, lo with 64 x 128 boxes, then hi, lo with 64 x 256 boxes)
 bool encode_block_tmaps(void *tmap_hi, void *tmap_lo, const uint16_t *Chi, const uint16_t *Clo, int64_t nblk,
-                        char *err, size_t errlen);
+                        int64_t c_stride, char *err, size_t errlen);
 bool encode_rows_tmaps(void *tmaps4, const uint16_t *Zh, const uint16_t *Zl, int64_t nrows, int64_t p_stride,
                        char *err, size_t errlen);
 

@@ -786,9 +786,11 @@ void launch_center(const Batch &b, cudaStream_t s) {
 //   j < i or padding: 0
 // FP32 in place (plain path), or (tuned path) c C split into FP16 hi + lo parts,
 // hi = fp16(c C), lo = fp16(c C - hi), with the test's power-of-two scale c
-// (packed_scale): |c C - hi - lo| <= 2^-22 |c C|.  One CTA per block.
+// (packed_scale): |c C - hi - lo| <= 2^-22 |c C|, written over the block's own FP32
+// storage (Batch::Chi / Clo with block stride c_stride), so the packed operand needs
+// no memory of its own.  One CTA per block.
 template <bool SPLIT>
-__global__ void __launch_bounds__(256) k_pack(const Batch bt) {
+__global__ void __launch_bounds__(512) k_pack(const Batch bt) {
     const int64_t gb = blockIdx.x;
     const BlkInfo bi = bt.blk[gb];
     const TestDesc d = bt.desc[bi.t];
@@ -798,54 +800,52 @@ __global__ void __launch_bounds__(256) k_pack(const Batch bt) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t j0 = (int64_t)bi.kb * KB + 2 * lane;
     const float uj[2] = {(j0 < n) ? u[j0] : 0.f, (j0 + 1 < n) ? u[j0 + 1] : 0.f};
-    const int64_t row0 = (int64_t)bi.I * PANEL + warp * 32;
+    const int64_t row0 = (int64_t)bi.I * PANEL + warp * 16;   // 16 warps x 16 rows
     const float cs = SPLIT ? packed_scale(bt.ctr[bi.t]) : 1.f;
-#pragma unroll 1
-    for (int r0 = 0; r0 < 32; r0 += 8) {
-        float2 dv8[8];
-        float ui[8];
+    // the whole block is read before any of it is rewritten: the split parts are
+    // written over the block's own FP32 storage (hi in its first half, lo in its second)
+    float2 dv[16];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            dv8[q] = *reinterpret_cast<const float2 *>(bt.D + (gb * PANEL + warp * 32 + r0 + q) * KB + 2 * lane);
-            const int64_t i = row0 + r0 + q;
-            ui[q] = (i < n) ? u[i] : 0.f;
+    for (int q = 0; q < 16; ++q)
+        dv[q] = *reinterpret_cast<const float2 *>(bt.D + (gb * PANEL + warp * 16 + q) * KB + 2 * lane);
+    if (SPLIT) __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int64_t i = row0 + q;
+        const float ui = (i < n) ? u[i] : 0.f;
+        const float dq[2] = {dv[q].x, dv[q].y};
+        float w[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int64_t j = j0 + e;
+            float v = 0.f;
+            if (i < n && j < n && j >= i) {
+                if (j == i) v = (float)((double)dq[e] - 2.0 * (double)ui - dcorr[i]);
+                else v = 2.f * ((dq[e] - ui) - uj[e]);
+            }
+            w[e] = v;
         }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int64_t i = row0 + r0 + q;
-            const int64_t off = (gb * PANEL + warp * 32 + r0 + q) * KB + 2 * lane;
-            const float dv[2] = {dv8[q].x, dv8[q].y};
-            float w[2];
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const int64_t j = j0 + e;
-                float v = 0.f;
-                if (i < n && j < n && j >= i) {
-                    if (j == i) v = (float)((double)dv[e] - 2.0 * (double)ui[q] - dcorr[i]);
-                    else v = 2.f * ((dv[e] - ui[q]) - uj[e]);
-                }
-                w[e] = v;
-            }
-            if (SPLIT) {
-                const float a0 = w[0] * cs, a1 = w[1] * cs;   // exact: cs is a power of two
-                const __half h0 = __float2half_rn(a0), h1 = __float2half_rn(a1);
-                const __half l0 = __float2half_rn(a0 - __half2float(h0));
-                const __half l1 = __float2half_rn(a1 - __half2float(h1));
-                const uint32_t hv = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
-                const uint32_t lv = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
-                *reinterpret_cast<uint32_t *>(bt.Chi + off) = hv;
-                *reinterpret_cast<uint32_t *>(bt.Clo + off) = lv;
-            } else {
-                *reinterpret_cast<float2 *>(bt.D + off) = make_float2(w[0], w[1]);
-            }
+        const int64_t r = warp * 16 + q;
+        if (SPLIT) {
+            const float a0 = w[0] * cs, a1 = w[1] * cs;   // exact: cs is a power of two
+            const __half h0 = __float2half_rn(a0), h1 = __float2half_rn(a1);
+            const __half l0 = __float2half_rn(a0 - __half2float(h0));
+            const __half l1 = __float2half_rn(a1 - __half2float(h1));
+            const uint32_t hv = (uint32_t)__half_as_ushort(h0) | ((uint32_t)__half_as_ushort(h1) << 16);
+            const uint32_t lv = (uint32_t)__half_as_ushort(l0) | ((uint32_t)__half_as_ushort(l1) << 16);
+            const int64_t off = gb * bt.c_stride + r * KB + 2 * lane;
+            *reinterpret_cast<uint32_t *>(bt.Chi + off) = hv;
+            *reinterpret_cast<uint32_t *>(bt.Clo + off) = lv;
+        } else {
+            *reinterpret_cast<float2 *>(bt.D + (gb * PANEL + r) * KB + 2 * lane) = make_float2(w[0], w[1]);
         }
     }
 }
 
 void launch_pack(const Batch &b, bool split, cudaStream_t s) {
     if (b.nblk_total <= 0) return;
-    if (split) k_pack<true><<<(unsigned)b.nblk_total, 256, 0, s>>>(b);
-    else k_pack<false><<<(unsigned)b.nblk_total, 256, 0, s>>>(b);
+    if (split) k_pack<true><<<(unsigned)b.nblk_total, 512, 0, s>>>(b);
+    else k_pack<false><<<(unsigned)b.nblk_total, 512, 0, s>>>(b);
 }
 
 // ---------------------------------------------------------------------------

@@ -51,7 +51,7 @@ inline size_t up(size_t v) { return (v + 255) / 256 * 256; }
 
 // Layout of one test's scratch inside the static array (byte offsets).
 struct StaticPlan {
-    size_t desc, pre, blk, chunks, norms, iscale, u, D, hi, lo, rowpart, colpart, r, Spart, dcorr, Upart, Stpart,
+    size_t desc, pre, blk, chunks, norms, iscale, u, D, rowpart, colpart, r, Spart, dcorr, Upart, Stpart,
         maskT, partial, stats, observed, ctr, total;
 };
 
@@ -72,8 +72,6 @@ StaticPlan static_plan(const TestDesc &d) {
     P.iscale = take((size_t)d.n_pad * 4);
     P.u = take((size_t)d.n_pad * 4);
     P.D = take(elems * 4);
-    P.hi = take(elems * 2);
-    P.lo = take(elems * 2);
     P.rowpart = take((size_t)d.nblk * PANEL * 8);
     P.colpart = take((size_t)d.nblk * KB * 8);
     P.r = take((size_t)d.n_pad * 8);
@@ -248,8 +246,9 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     b.iscale = (float *)(A + P.iscale);
     b.u = (float *)(A + P.u);
     b.D = (float *)(A + P.D);
-    b.Chi = (uint16_t *)(A + P.hi);
-    b.Clo = (uint16_t *)(A + P.lo);
+    b.Chi = (uint16_t *)(A + P.D);   // the split parts are written over the blocks' FP32 storage
+    b.Clo = b.Chi + (size_t)PANEL * KB;
+    b.c_stride = 2 * (int64_t)PANEL * KB;
     b.rowpart = (double *)(A + P.rowpart);
     b.colpart = (double *)(A + P.colpart);
     b.r = (double *)(A + P.r);
@@ -276,7 +275,8 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     SCK(cudaGetLastError());
     alignas(64) CUtensorMap th, tl;
     char emsg[160];
-    if (!encode_block_tmaps(&th, &tl, b.Chi, b.Clo, d.nblk, emsg, sizeof(emsg))) return err(EPT_ECUDA, "%s", emsg);
+    if (!encode_block_tmaps(&th, &tl, b.Chi, b.Clo, d.nblk, b.c_stride, emsg, sizeof(emsg)))
+        return err(EPT_ECUDA, "%s", emsg);
     SCK(launch_contract_tc(b, &th, &tl, sd->num_sms, s));
     launch_combine(b, s);
     SCK(cudaGetLastError());
