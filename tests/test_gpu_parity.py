@@ -269,3 +269,20 @@ def test_expired_device_wait_returns_timeout_and_context_recovers(ctx):
     res = ctx.test(X, Y, B=500, seed=2, prec="split_bf16")
     ref = oracle.permutation_test(X, Y, B=500, seed=2, stat="ed")
     _check(res, ref["stats"], ref["observed"], 500)
+
+
+def test_large_n_sampled(ctx):
+    # n = 60000 pooled rows (7.2 GB of packed blocks): sampled draws against the
+    # oracle's direct recomputation, and the closed-form permutation mean
+    spec = workloads.TwoSampleSpec(nx=30000, ny=30000, p=8, y_mean=0.02, B=400, seed=6, data_seed=12)
+    X, Y = workloads.gaussian_pair(spec)
+    res = ctx.test(X, Y, B=spec.B, seed=spec.seed)
+    st = np.asarray(res.stats)
+    obs = oracle.stat_select(X, Y, oracle.perm_select(spec.seed, spec.nx, spec.ny, 0, 1)[0], "ed", 1.0)
+    assert abs(res.observed - obs) <= REL_TOL * abs(obs)
+    for b in (1, 400):
+        v = oracle.stat_select(X, Y, oracle.perm_select(spec.seed, spec.nx, spec.ny, b, 1)[0], "ed", 1.0)
+        assert abs(st[b - 1] - v) <= REL_TOL * abs(v), (b, st[b - 1], v)
+    S, tr = oracle.pooled_moments(X, Y, "ed", 1.0)
+    mean_ref = oracle.permutation_mean(S, tr, spec.nx, spec.ny, "ed")
+    assert abs(st.mean() - mean_ref) <= 5 * st.std() / np.sqrt(spec.B)
