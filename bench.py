@@ -38,7 +38,7 @@ KERNELS_PER_STEP = 11  # libept kernels launched by one ept_test / ept_test_batc
 # dram read + write bytes of one k_contract_tc launch on the highdim workload, from the ncu
 # capture summarised in profiles/k_contract_tc_highdim_ed.md (to be reset to {} whenever the
 # kernel changes, until it is captured again)
-CONTRACT_TRAFFIC = {"highdim": 60.71e6}
+CONTRACT_TRAFFIC = {"highdim": 60.73e6}
 
 
 def _args():
