@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define EPT_ABI_VERSION 2
+#define EPT_ABI_VERSION 3
 
 typedef enum {
     EPT_OK = 0,
@@ -98,6 +98,9 @@ typedef struct {
                              recorded on the stream it is launched on) */
     double sigma;         /* kernel bandwidth used (the median heuristic's value when
                              EPT_SIGMA_MEDIAN was given); 0 for ED */
+    int64_t n_windows;    /* 0: the packed blocks were resident; k > 0: the test ran in
+                             the streaming mode, in k windows of row panels
+                             (EPT_OPT_STREAM_BLOCKS) */
 } ept_result;
 
 /* Library ABI version (EPT_ABI_VERSION of the build). */
@@ -207,6 +210,21 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    the run and checked after it, and the host checks the plan's invariants (tables,
    chunk ranges, the contraction schedule covering every unit once); a violation
    returns EPT_EINTERNAL.
+   EPT_OPT_STREAM_BLOCKS (default 0): the streaming mode for tests whose packed
+   blocks do not fit in device memory (single tests: ept_test, ept_test_range,
+   ept_test_masks; split precision; a given sigma).  The row panels are taken in
+   windows, in two passes: the first builds each window's blocks for the exact row
+   sums of the pooled matrix (the centring needs them before any block is packed);
+   the second builds each window again, packs it and contracts it against every
+   relabeling, and the next window reuses the memory.  The blocks then need one
+   window of memory instead of about 2 n^2 bytes, at the price of a second build.
+   0 = automatic: a test streams when its resident scratch would not fit (the
+   context budget, else the device's free memory), with the largest window that
+   fits; k > 0 = every single test streams, with windows of at most k stored
+   blocks of 256 x 64 entries (at least one panel); -1 = never (a test that does
+   not fit fails with EPT_ENOMEM).  Streaming with the plain precision or the
+   median bandwidth gives EPT_EUNSUPPORTED.  The arithmetic is the resident path's;
+   only the order in which the windows' FP64 partial sums are added differs.
    EPT_OPT_SERVE_LANES (default 3, 1..16): serving batches in flight at once;
    EPT_OPT_SERVE_SLOTS (default 256): serving requests in flight at once; both
    before the first ept_submit.  EPT_EINVAL for an unknown option or value. */
@@ -218,7 +236,8 @@ enum {
     EPT_OPT_DRAW_MODE = 5,
     EPT_OPT_FAULT_INJECT_ALLOC = 6,
     EPT_OPT_FAULT_INJECT_STALL = 7,
-    EPT_OPT_DEBUG_CHECKS = 8
+    EPT_OPT_DEBUG_CHECKS = 8,
+    EPT_OPT_STREAM_BLOCKS = 9
 };
 ept_status ept_set_option(ept_ctx *ctx, int option, int64_t value);
 

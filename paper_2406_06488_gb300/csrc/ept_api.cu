@@ -108,6 +108,15 @@ struct Plan {
     size_t off_in, off_norms, off_iscale, off_u, off_Zh, off_Zl, off_D, off_Chi, off_rowpart, off_colpart,
         off_r, off_Spart, off_dcorr, off_Upart, off_Stpart, off_maskT, off_partial, off_stats, off_observed, off_ctr,
         total;
+    // streaming mode (one test, windows of row panels): per window its panels
+    // [I0, I1), its first stored block and block count, its build tiles, the test's
+    // descriptor seen through the window and its contraction units; the window's
+    // capacity in blocks and partial floats
+    bool stream = false;
+    std::vector<TestDesc> gdesc;
+    std::vector<int64_t> gI0, gI1, gblk0, gnblk, gtile0, gntile, gpre;
+    int64_t win_blk = 0, win_part = 0;
+    size_t off_gdesc = 0, off_gpre = 0, off_sacc = 0;
 };
 
 // The fields of a test's descriptor that do not depend on its shape (statistic,
@@ -169,7 +178,7 @@ void plan_schedule(Plan &P, int num_sms) {
 }
 
 void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host_in, int chunk_kb,
-                int num_sms = 160, bool debug = false) {
+                int num_sms = 160, bool debug = false, bool schedule = true) {
     P = Plan();
     P.debug = debug;
     P.n_tests = (int)specs.size();
@@ -256,7 +265,7 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
     }
     P.ncols_pad = P.pre_cols.back();
     P.nunits = P.pre_units.back();
-    if (tc) plan_schedule(P, num_sms);
+    if (tc && schedule) plan_schedule(P, num_sms);
     P.nsimt = P.pre_simt.back();
     P.in_bytes = in_bytes;
 
@@ -480,6 +489,7 @@ struct ept_ctx {
     bool graphs = true;                 // replay captured graphs of repeated batches
     bool debug = false;                 // guard bands around scratch regions, plan invariants checked
     int draw_mode = 0;                  // relabeling draws: 0 automatic, DRAW_WARPS, DRAW_LANES
+    int64_t stream_blocks = 0;          // streaming mode: 0 automatic, k > 0 windows of <= k blocks, -1 never
     std::atomic<int> inject_alloc{0};   // test hook: the next N scratch acquisitions fail (host side)
     bool inject_stall = false;          // test hook: the next run's contraction waits out its limit
     int serve_lanes = 3;                // serving: batches in flight at once
@@ -536,7 +546,9 @@ void drop_graph(ept_ctx *c) {
     c->graph = GraphCache();
 }
 
-ept_status ensure_arena(ept_ctx *c, size_t bytes, cudaStream_t s) {
+// exact: allocate just `bytes` (the streaming mode sizes its window to the memory
+// there is), else 1/8 more, so that slightly larger runs reuse the arena
+ept_status ensure_arena(ept_ctx *c, size_t bytes, cudaStream_t s, bool exact = false) {
     if (c->budget && bytes > c->budget)
         return fail(EPT_ENOMEM, "this run needs %zu bytes of device scratch, over the context budget of %zu", bytes,
                     c->budget);
@@ -549,7 +561,7 @@ ept_status ensure_arena(ept_ctx *c, size_t bytes, cudaStream_t s) {
         c->arena = nullptr;
         c->arena_cap = 0;
     }
-    const size_t cap = align_up(bytes + bytes / 8, 1 << 20);
+    const size_t cap = align_up(exact ? bytes : bytes + bytes / 8, 1 << 20);
     cudaError_t e = cudaMalloc(&c->arena, cap);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -734,6 +746,7 @@ Batch device_view(ept_ctx *c, const Plan &P) {
     b.maskT = (uint32_t *)(A + P.off_maskT);
     b.ctr = (Counters *)(A + P.off_ctr);
     b.sel_hist = P.any_median ? (uint32_t *)(A + P.off_sel_hist) : nullptr;
+    b.sacc = nullptr;
     b.inject_stall = c->inject_stall ? 1 : 0;
     return b;
 }
@@ -905,6 +918,7 @@ ept_status collect(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &specs
         r.ms_total = ms_total;
         r.ms_masks = ms_masks;
         r.ms_contract = ms_contract;
+        r.n_windows = P.stream ? (int64_t)P.gI0.size() : 0;
         if (P.host_in && specs[t].perm_stats && d.B > 0)
             memcpy(specs[t].perm_stats, stats + d.col0 + 1, (size_t)d.B * 8);
     }
@@ -1079,6 +1093,335 @@ ept_status run_tuned(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, b
     c->tuned_chunk[key] = best;
     save_tune_file(c);
     return run_once(c, specs, prec, on_device, best, use_graph, out, stream, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Streaming mode (EPT_OPT_STREAM_BLOCKS): one test whose packed blocks do not fit
+// in device memory runs one window of row panels at a time, in two passes (the
+// first for the exact row sums; ept_stream.cu).  The test's tables are those of a
+// resident run (plan_batch, without the contraction schedule: a window's units are
+// strided over the grid); each window sees the test through its own descriptor,
+// whose block offset maps the window's blocks to the start of the window's memory.
+
+// device bytes of one stored block in a window: its FP32 entries (the FP16 parts
+// are written over them) and its row and column sums
+constexpr size_t STREAM_BLK_BYTES = (size_t)PANEL * KB * 4 + (size_t)PANEL * 8 + (size_t)KB * 8;
+
+// device bytes of a resident run of one test, without building its tables (the
+// dominant terms of plan_batch's layout, rounded up)
+size_t resident_bytes(const TestSpec &s, int prec) {
+    const int64_t n = s.nx + s.ny, n_pad = (n + PANEL - 1) / PANEL * PANEL, NP = n_pad / PANEL, NKB = n_pad / KB;
+    const int64_t nblk = blk_off(NP, NKB), Bp = (s.B + 1 + COL_PAD - 1) / COL_PAD * COL_PAD;
+    const int64_t p_pad = (s.p + BUILD_KB - 1) / BUILD_KB * BUILD_KB;
+    const int64_t nchunks = nblk / 8 + NP;   // chunks of 8 K-blocks or more, one partial one per panel
+    const bool tc = prec == EPT_PREC_SPLIT_BF16;
+    size_t b = (size_t)nblk * (STREAM_BLK_BYTES + sizeof(BlkInfo) + sizeof(Tile));
+    b += (size_t)nchunks * (sizeof(Chunk) + 2 * (size_t)Bp * 4 + 2 * (size_t)(Bp / TC_TILE_N) * 8);
+    b += (size_t)n_pad * (4 * 3 + 8 * 4 + (tc ? 4 * (size_t)p_pad : 0));
+    b += (size_t)(n_pad / 32) * Bp * 4 + (size_t)Bp * 8;
+    b += (size_t)n * s.p * 4 + (s.user_masks ? (size_t)s.B * ((n + 31) / 32) * 4 : 0);
+    return b + ((size_t)1 << 20);
+}
+
+// device memory a run may take: the context budget, else what is free plus the
+// context's own arena, less a margin (2 %, at least 1 GiB) for everything else
+size_t available_bytes(ept_ctx *c) {
+    if (c->budget) return c->budget;
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    const size_t have = fr + c->arena_cap;
+    const size_t margin = std::max<size_t>((size_t)1 << 30, have / 50);
+    return have > margin ? have - margin : 0;
+}
+
+// whether a single test runs in the streaming mode
+bool use_stream(ept_ctx *c, const TestSpec &s, int prec) {
+    if (c->stream_blocks < 0) return false;
+    if (c->stream_blocks > 0) return true;
+    if (prec != EPT_PREC_SPLIT_BF16 || (s.stat != EPT_STAT_ED && s.sigma == EPT_SIGMA_MEDIAN)) return false;
+    const size_t need = resident_bytes(s, prec);
+    if (need <= c->arena_cap) return false;   // the arena already holds it
+    return need > available_bytes(c);
+}
+
+// Windows of consecutive row panels: a panel joins the current window while the
+// window stays within limit_blk stored blocks and limit_bytes of device memory (a
+// window holds at least one panel).  Fills the per-window fields of P.
+void stream_partition(Plan &P, int64_t limit_blk, size_t limit_bytes) {
+    const TestDesc &d = P.desc[0];
+    const int64_t NP = d.NP;
+    std::vector<int64_t> cfirst((size_t)NP + 1, 0), tfirst((size_t)NP + 1, 0);
+    int64_t q = 0;
+    for (int64_t I = 0; I < NP; ++I) {
+        cfirst[(size_t)I] = q;
+        while (q < (int64_t)P.chunks.size() && P.chunks[(size_t)q].I == I) ++q;
+        tfirst[(size_t)I + 1] = tfirst[(size_t)I] + 2 * (NP - I);
+    }
+    cfirst[(size_t)NP] = q;
+    P.gdesc.clear();
+    P.gI0.clear();
+    P.gI1.clear();
+    P.gblk0.clear();
+    P.gnblk.clear();
+    P.gtile0.clear();
+    P.gntile.clear();
+    P.gpre.clear();
+    P.win_blk = P.win_part = 0;
+    int64_t I = 0;
+    while (I < NP) {
+        const int64_t I0 = I;
+        int64_t blocks = 0;
+        size_t bytes = 0;
+        while (I < NP) {
+            const int64_t nb = d.NKB - KB_PER_PANEL * I, nc = cfirst[(size_t)I + 1] - cfirst[(size_t)I];
+            const size_t add = (size_t)nb * STREAM_BLK_BYTES + (size_t)(2 * nc * d.Bp) * 4;
+            if (I > I0 && (blocks + nb > limit_blk || bytes + add > limit_bytes)) break;
+            blocks += nb;
+            bytes += add;
+            ++I;
+        }
+        TestDesc g = d;
+        g.blk0 = -blk_off(I0, d.NKB);
+        g.chunk0 = cfirst[(size_t)I0];
+        g.nchunks = cfirst[(size_t)I] - cfirst[(size_t)I0];
+        g.nparts = 2 * g.nchunks;
+        g.part0 = 0;
+        P.gdesc.push_back(g);
+        P.gI0.push_back(I0);
+        P.gI1.push_back(I);
+        P.gblk0.push_back(blk_off(I0, d.NKB));
+        P.gnblk.push_back(blocks);
+        P.gtile0.push_back(tfirst[(size_t)I0]);
+        P.gntile.push_back(tfirst[(size_t)I] - tfirst[(size_t)I0]);
+        P.gpre.push_back(0);
+        P.gpre.push_back(tc_units(g));
+        P.win_blk = std::max(P.win_blk, blocks);
+        P.win_part = std::max(P.win_part, g.nparts * d.Bp);
+    }
+}
+
+// Arena layout of a streaming run: the test's tables as plan_batch laid them out,
+// the windows' descriptors and unit prefixes, the per-row and per-relabeling arrays
+// of the whole test, then the window (blocks, their sums, the partials).
+void stream_layout(Plan &P, size_t tab_bytes_resident) {
+    const TestDesc &d = P.desc[0];
+    size_t o = tab_bytes_resident;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + std::max<size_t>(bytes, 1), 256);
+        return at;
+    };
+    P.off_gdesc = take(sizeof(TestDesc) * P.gdesc.size());
+    P.off_gpre = take(8 * P.gpre.size());
+    P.tab_bytes = o;
+    o = align_up(o, 1024);
+    P.off_in = take(P.in_bytes);
+    P.off_norms = take((size_t)P.nrows * 4);
+    P.off_iscale = take((size_t)P.nrows * 4);
+    P.off_u = take((size_t)P.nrows * 4);
+    P.off_Zh = take((size_t)P.nrows * P.p_stride * 2);
+    P.off_Zl = take((size_t)P.nrows * P.p_stride * 2);
+    P.off_r = take((size_t)P.nrows * 8);
+    P.off_Spart = take((size_t)(P.nrows / 32) * 8);
+    P.off_dcorr = take((size_t)P.nrows * 8);
+    P.off_Upart = take((size_t)P.npan * 8);
+    P.off_Stpart = take((size_t)P.npan * 8);
+    P.off_maskT = take((size_t)P.nmask * 4);
+    P.off_sacc = take((size_t)d.Bp * 8);
+    P.off_stats = take((size_t)P.nstats * 8);
+    P.off_observed = take(8);
+    P.off_ctr = take(sizeof(Counters));
+    P.off_D = take((size_t)P.win_blk * PANEL * KB * 4);
+    P.off_Chi = P.off_D;
+    P.off_rowpart = take((size_t)P.win_blk * PANEL * 8);
+    P.off_colpart = take((size_t)P.win_blk * KB * 8);
+    P.off_partial = take((size_t)P.win_part * 4);
+    P.total = o;
+}
+
+// device view of a streaming run: the whole test (g < 0) or window g
+Batch stream_view(ept_ctx *c, const Plan &P, int g) {
+    uint8_t *A = c->arena;
+    Batch b;
+    memset(&b, 0, sizeof(b));
+    b.n_tests = 1;
+    b.desc = g < 0 ? (const TestDesc *)(A + P.off_desc) : (const TestDesc *)(A + P.off_gdesc) + g;
+    b.pre.rows = (const int64_t *)(A + P.off_pre_rows);
+    b.pre.panels = (const int64_t *)(A + P.off_pre_panels);
+    b.pre.cols = (const int64_t *)(A + P.off_pre_cols);
+    b.pre.units = g < 0 ? (const int64_t *)(A + P.off_pre_units) : (const int64_t *)(A + P.off_gpre) + 2 * g;
+    b.pre.simt = (const int64_t *)(A + P.off_pre_simt);
+    b.blk = (const BlkInfo *)(A + P.off_blk) + (g < 0 ? 0 : P.gblk0[(size_t)g]);
+    b.tiles = (const Tile *)(A + P.off_tiles) + (g < 0 ? 0 : P.gtile0[(size_t)g]);
+    b.chunks = (const Chunk *)(A + P.off_chunks);
+    b.nblk_total = g < 0 ? 0 : P.gnblk[(size_t)g];
+    b.ntiles = g < 0 ? 0 : P.gntile[(size_t)g];
+    b.nrows_total = P.nrows;
+    b.npan_total = P.npan;
+    b.ncols_total = P.ncols_pad;
+    b.nunits_total = g < 0 ? 0 : P.gpre[2 * (size_t)g + 1];
+    b.p_stride = P.p_stride;
+    b.norms = (float *)(A + P.off_norms);
+    b.iscale = (float *)(A + P.off_iscale);
+    b.u = (float *)(A + P.off_u);
+    b.Zh = (uint16_t *)(A + P.off_Zh);
+    b.Zl = (uint16_t *)(A + P.off_Zl);
+    b.Chi = (uint16_t *)(A + P.off_D);
+    b.Clo = b.Chi + (size_t)PANEL * KB;
+    b.c_stride = 2 * (int64_t)PANEL * KB;
+    b.D = (float *)(A + P.off_D);
+    b.partial = (float *)(A + P.off_partial);
+    b.rowpart = (double *)(A + P.off_rowpart);
+    b.colpart = (double *)(A + P.off_colpart);
+    b.r = (double *)(A + P.off_r);
+    b.Spart = (double *)(A + P.off_Spart);
+    b.dcorr = (double *)(A + P.off_dcorr);
+    b.Upart = (double *)(A + P.off_Upart);
+    b.Stpart = (double *)(A + P.off_Stpart);
+    b.stats = (double *)(A + P.off_stats);
+    b.observed = (double *)(A + P.off_observed);
+    b.maskT = (uint32_t *)(A + P.off_maskT);
+    b.ctr = (Counters *)(A + P.off_ctr);
+    b.sacc = (double *)(A + P.off_sacc);
+    b.inject_stall = (g == 0 && c->inject_stall) ? 1 : 0;
+    return b;
+}
+
+ept_status run_stream(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bool on_device, ept_result *out,
+                      void *stream) {
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    const TestSpec &sp = specs[0];
+    if (prec != EPT_PREC_SPLIT_BF16) return fail(EPT_EUNSUPPORTED, "the streaming mode runs the split precision only");
+    if (sp.stat != EPT_STAT_ED && sp.sigma == EPT_SIGMA_MEDIAN)
+        return fail(EPT_EUNSUPPORTED, "the streaming mode needs a given sigma (the median heuristic selects over "
+                                      "every pooled distance before the first window)");
+    NvtxRange range("ept.run (streaming)");
+    std::unique_ptr<Plan> hold(new (std::nothrow) Plan());
+    if (!hold) return fail(EPT_ENOMEM, "host allocation failed");
+    Plan &P = *hold;
+    plan_batch(P, specs, prec, !on_device, CHUNK_KB_DEFAULT, c->num_sms, false, false);
+    P.stream = true;
+    const size_t tab0 = P.tab_bytes;
+    const TestDesc &d = P.desc[0];
+    const size_t panel0 = (size_t)d.NKB * STREAM_BLK_BYTES;
+    if (c->stream_blocks > 0) {
+        stream_partition(P, c->stream_blocks, SIZE_MAX);
+        stream_layout(P, tab0);
+    } else {
+        const size_t avail = available_bytes(c);
+        stream_partition(P, INT64_MAX, panel0);   // the smallest windows: the fixed part of the layout
+        stream_layout(P, tab0);
+        const size_t win0 = (size_t)P.win_blk * STREAM_BLK_BYTES + (size_t)P.win_part * 4;
+        const size_t fixed = P.total - std::min(P.total, win0);
+        if (fixed + win0 > avail)
+            return fail(EPT_ENOMEM, "the streaming mode needs %zu bytes of device memory for one panel, %zu are "
+                                    "available", fixed + win0, avail);
+        size_t wb = avail - fixed;
+        for (;;) {
+            stream_partition(P, INT64_MAX, wb);
+            stream_layout(P, tab0);
+            if (P.total <= avail || wb <= win0) break;
+            wb = std::max(win0, wb / 10 * 9);
+        }
+        if (P.total > avail)
+            return fail(EPT_ENOMEM, "the streaming mode needs %zu bytes of device memory, %zu are available", P.total,
+                        avail);
+    }
+    if (injected_failure(c)) return fail(EPT_ENOMEM, "device scratch not available (injected failure)");
+    ept_status st = ensure_arena(c, P.total, s, true);
+    if (st != EPT_OK) return st;
+    const Staging S = staging_layout(P);
+    if ((st = ensure_pinned(c, S.total)) != EPT_OK) return st;
+    if (s != c->stream) CK(cudaStreamSynchronize(c->stream));
+    stage_host(c, P, specs, on_device, true);
+    c->tables_staged = false;   // the pinned tables now hold this run's; the cached plan's are staged again
+    for (TestDesc &g : P.gdesc) {   // the device addresses of the inputs, as staged
+        g.X = P.desc[0].X;
+        g.Y = P.desc[0].Y;
+        g.user_masks = P.desc[0].user_masks;
+        g.out_stats = P.desc[0].out_stats;
+    }
+    uint8_t *tab = c->pinned + S.tables;
+    memcpy(tab + P.off_gdesc, P.gdesc.data(), sizeof(TestDesc) * P.gdesc.size());
+    memcpy(tab + P.off_gpre, P.gpre.data(), 8 * P.gpre.size());
+
+    const Batch bf = stream_view(c, P, -1);
+    CK(cudaEventRecord(c->ev[0], s));
+    if ((st = enqueue_uploads(c, P, s)) != EPT_OK) return st;
+    CK(cudaMemsetAsync(bf.ctr, 0, sizeof(Counters), s));
+    CK(cudaMemsetAsync(bf.r, 0, (size_t)P.nrows * 8, s));
+    CK(cudaMemsetAsync(bf.sacc, 0, (size_t)d.Bp * 8, s));
+    CK(cudaEventRecord(c->ev[1], s));
+    // relabeling draws on the side stream, beside the first pass
+    CK(cudaStreamWaitEvent(c->side, c->ev[1], 0));
+    int mode = c->draw_mode;
+    if (mode == 0)
+        mode = (!P.user_masks && P.ncols_pad >= DRAW_LANES_MIN_COLS_PER_SM * (int64_t)c->num_sms) ? DRAW_LANES
+                                                                                                  : DRAW_WARPS;
+    if (P.user_masks) mode = DRAW_WARPS;
+    launch_masks(bf, c->num_sms, mode, c->side);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(c->ev_side[2], c->side));
+    CK(cudaStreamWaitEvent(s, c->ev_in, 0));
+    launch_split_rows(bf, s);
+    CK(cudaGetLastError());
+    alignas(64) CUtensorMap tm[4];
+    alignas(64) CUtensorMap th, tl;
+    char emsg[160];
+    if (!encode_rows_tmaps(tm, bf.Zh, bf.Zl, P.nrows, P.p_stride, emsg, sizeof(emsg)))
+        return fail(EPT_ECUDA, "%s", emsg);
+    if (!encode_block_tmaps(&th, &tl, bf.Chi, bf.Clo, P.win_blk, bf.c_stride, emsg, sizeof(emsg)))
+        return fail(EPT_ECUDA, "%s", emsg);
+    const int nwin = (int)P.gI0.size();
+    // pass 1: the row sums r (and max |D| for the FP16 scale)
+    for (int g = 0; g < nwin; ++g) {
+        const Batch gv = stream_view(c, P, g);
+        CK(launch_build_tc(gv, tm, c->num_sms, s));
+        launch_blocksums(gv, s);
+        launch_stream_rowsums(gv, P.gI0[(size_t)g], P.gI1[(size_t)g], d.n_pad, s);
+        CK(cudaGetLastError());
+    }
+    // the resident path's centring: u, r~, the diagonal fold, S~
+    launch_stream_spart(bf, s);
+    launch_center(bf, s);
+    CK(cudaGetLastError());
+    CK(cudaStreamWaitEvent(s, c->ev_side[2], 0));
+    // pass 2: build again, pack, contract, fold the partials
+    for (int g = 0; g < nwin; ++g) {
+        const Batch gv = stream_view(c, P, g);
+        CK(launch_build_tc(gv, tm, c->num_sms, s));
+        launch_pack(gv, true, s);
+        CK(cudaGetLastError());
+        CK(launch_contract_tc(gv, &th, &tl, c->num_sms, s));
+        launch_stream_accum(gv, s);
+        CK(cudaGetLastError());
+    }
+    launch_stream_stats(bf, s);
+    launch_combine_count(bf, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->pinned + S.res_ctr, bf.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->pinned + S.res_obs, bf.observed, 8, cudaMemcpyDeviceToHost, s));
+    if (P.host_in) CK(cudaMemcpyAsync(c->pinned + S.res_stats, bf.stats, 8 * (size_t)P.nstats, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(c->ev[4], s));
+    c->inject_stall = false;   // the hook is one-shot
+    CK(cudaStreamSynchronize(s));
+    if ((st = collect(c, P, specs, out, false)) != EPT_OK) return st;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev[0], c->ev[4]);
+    out[0].ms_total = ms;
+    return EPT_OK;
+}
+
+// a single test: streamed when its blocks do not fit (or the option asks for it),
+// else the resident path
+ept_status run_single(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bool on_device, bool tuned,
+                      ept_result *out, void *stream) {
+    if (use_stream(c, specs[0], prec)) return run_stream(c, specs, prec, on_device, out, stream);
+    if (tuned) return run_tuned(c, specs, prec, on_device, true, out, stream);
+    return run_once(c, specs, prec, on_device, CHUNK_KB_DEFAULT, false, out, stream, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1452,8 +1795,8 @@ ept_status ept_test(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, in
     if (st != EPT_OK) return st;
     std::lock_guard<std::mutex> lock(ctx->mu);
     DeviceGuard dg(ctx->device);
-    return run_tuned(ctx, one_test(X, nx, Y, ny, p, stat, sigma, B, seed, nullptr, perm_stats), prec, on_device != 0,
-                     true, out, stream);
+    return run_single(ctx, one_test(X, nx, Y, ny, p, stat, sigma, B, seed, nullptr, perm_stats), prec, on_device != 0,
+                      true, out, stream);
 }
 
 ept_status ept_test_range(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p,
@@ -1469,7 +1812,7 @@ ept_status ept_test_range(ept_ctx *ctx, const float *X, int64_t nx, const float 
     specs[0].b0 = b_first;
     std::lock_guard<std::mutex> lock(ctx->mu);
     DeviceGuard dg(ctx->device);
-    return run_tuned(ctx, specs, prec, on_device != 0, true, out, stream);
+    return run_single(ctx, specs, prec, on_device != 0, true, out, stream);
 }
 
 ept_status ept_test_masks(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p,
@@ -1483,8 +1826,9 @@ ept_status ept_test_masks(ept_ctx *ctx, const float *X, int64_t nx, const float 
     if (st != EPT_OK) return st;
     std::lock_guard<std::mutex> lock(ctx->mu);
     DeviceGuard dg(ctx->device);
-    return run_once(ctx, one_test(X, nx, Y, ny, p, stat, sigma, n_masks, 0, n_masks > 0 ? masks : nullptr, perm_stats),
-                    prec, on_device != 0, CHUNK_KB_DEFAULT, false, out, stream, nullptr);
+    return run_single(ctx,
+                      one_test(X, nx, Y, ny, p, stat, sigma, n_masks, 0, n_masks > 0 ? masks : nullptr, perm_stats),
+                      prec, on_device != 0, false, out, stream);
 }
 
 ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_tests, int on_device, int prec,
@@ -1618,6 +1962,10 @@ ept_status ept_set_option(ept_ctx *c, int option, int64_t value) {
         c->draw_mode = (int)value;
         c->plan_key.clear();   // a captured graph holds the previous draw kernel
         drop_graph(c);
+        return EPT_OK;
+    case EPT_OPT_STREAM_BLOCKS:
+        if (value < -1) return fail(EPT_EINVAL, "stream blocks must be -1, 0 or a block count");
+        c->stream_blocks = value;
         return EPT_OK;
     case EPT_OPT_SERVE_LANES:
     case EPT_OPT_SERVE_SLOTS:

@@ -156,6 +156,7 @@ struct Batch {
     uint32_t *maskT;
     Counters *ctr;
     uint32_t *sel_hist;                  // median heuristic: 2048 bins per test (null if no test needs it)
+    double *sacc;                        // streaming mode: FP64 sums of the windows' partials (Bp)
     int inject_stall;                    // failure-path test hook: the contraction's MMA issuer waits on a
                                          //   flag that nothing sets until its bounded wait expires
 };
@@ -204,6 +205,7 @@ constexpr int64_t DRAW_LANES_MIN_COLS_PER_SM = 32 * 32;
 void launch_masks(const Batch &b, int num_sms, int mode, cudaStream_t s);   // draws or caller masks
 void launch_contract_simt(const Batch &b, cudaStream_t s);
 void launch_combine(const Batch &b, cudaStream_t s);                     // statistics, counts, outputs
+void launch_combine_count(const Batch &b, cudaStream_t s);               // counts and outputs alone
 
 // single-draw-stream export (ept_perm_masks): columns 0..count-1 = draws b0..b0+count-1
 void launch_perm_masks_plain(uint64_t seed, int nx, int ny, int64_t b0, int64_t count, int nw, uint32_t *maskT,
@@ -224,6 +226,16 @@ bool encode_block_tmaps(void *tmap_hi, void *tmap_lo, const uint16_t *Chi, const
                         int64_t c_stride, char *err, size_t errlen);
 bool encode_rows_tmaps(void *tmaps4, const uint16_t *Zh, const uint16_t *Zl, int64_t nrows, int64_t p_stride,
                        char *err, size_t errlen);
+
+// ---- streaming mode (ept_stream.cu): one test, windows of row panels ----
+// r += the row and column sums of the window [I0, I1) (its stored blocks' parts)
+void launch_stream_rowsums(const Batch &g, int64_t I0, int64_t I1, int64_t n_pad, cudaStream_t s);
+// Spart from the complete r (then the resident path's launch_center)
+void launch_stream_spart(const Batch &b, cudaStream_t s);
+// sacc += the window's contraction partials
+void launch_stream_accum(const Batch &g, cudaStream_t s);
+// the statistics from sacc (after the last window)
+void launch_stream_stats(const Batch &b, cudaStream_t s);
 
 void set_last_error(const char *msg);   // ept_api.cu
 

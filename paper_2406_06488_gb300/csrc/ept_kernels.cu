@@ -988,6 +988,11 @@ void launch_combine(const Batch &b, cudaStream_t s) {
     k_combine_count<<<(unsigned)(b.ncols_total / 256), 256, 0, s>>>(b);
 }
 
+void launch_combine_count(const Batch &b, cudaStream_t s) {
+    if (b.ncols_total <= 0) return;
+    k_combine_count<<<(unsigned)(b.ncols_total / 256), 256, 0, s>>>(b);
+}
+
 // ---------------------------------------------------------------------------
 // Expand one test's packed upper storage into a full row-major n x n matrix
 // (checking aid).

@@ -295,6 +295,7 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     out->p_value = (1.0 + (double)out->n_ge) / (1.0 + (double)B);
     out->ms_build = out->ms_perm = out->ms_masks = out->ms_contract = 0.0;
     out->sigma = (stat == EPT_STAT_ED) ? 0.0 : sigma;
+    out->n_windows = 0;
     out->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     return EPT_OK;
 }
