@@ -100,7 +100,10 @@ typedef struct {
                              EPT_SIGMA_MEDIAN was given); 0 for ED */
     int64_t n_windows;    /* 0: the packed blocks were resident; k > 0: the test ran in
                              the streaming mode, in k windows of row panels
-                             (EPT_OPT_STREAM_BLOCKS) */
+                             (EPT_OPT_STREAM_BLOCKS); there ms_build covers the row split,
+                             the first pass and the centring, ms_perm the second pass and
+                             the combination, ms_contract the contraction launches summed
+                             (0 beyond 64 windows) */
 } ept_result;
 
 /* Library ABI version (EPT_ABI_VERSION of the build). */

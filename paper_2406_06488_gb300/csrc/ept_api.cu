@@ -497,6 +497,7 @@ struct ept_ctx {
     cudaEvent_t ev_user = nullptr;      // orders the context's stream after a caller's stream
     cudaStream_t copy = nullptr;        // host-to-device input copies, beside the relabeling draws
     cudaEvent_t ev_in = nullptr;        // the run's inputs are on the device
+    std::vector<cudaEvent_t> ev_win;    // streaming mode: around each window's contraction (first 64 windows)
     // plan of the last run, reused while the batch shape repeats; tables_staged: the
     // pinned staging area still holds its constant tables
     Plan *plan = nullptr;
@@ -1124,7 +1125,7 @@ size_t resident_bytes(const TestSpec &s, int prec) {
 }
 
 // device memory a run may take: the context budget, else what is free plus the
-// context's own arena, less a margin (2 %, at least 1 GiB) for everything else
+// context's own arena, less a margin (3 %, at least 2 GiB) for everything else
 size_t available_bytes(ept_ctx *c) {
     if (c->budget) return c->budget;
     size_t fr = 0, tot = 0;
@@ -1133,7 +1134,7 @@ size_t available_bytes(ept_ctx *c) {
         return 0;
     }
     const size_t have = fr + c->arena_cap;
-    const size_t margin = std::max<size_t>((size_t)1 << 30, have / 50);
+    const size_t margin = std::max<size_t>((size_t)2 << 30, have / 33);
     return have > margin ? have - margin : 0;
 }
 
@@ -1357,6 +1358,7 @@ ept_status run_stream(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, 
     CK(cudaEventRecord(c->ev[1], s));
     // relabeling draws on the side stream, beside the first pass
     CK(cudaStreamWaitEvent(c->side, c->ev[1], 0));
+    CK(cudaEventRecord(c->ev_side[1], c->side));
     int mode = c->draw_mode;
     if (mode == 0)
         mode = (!P.user_masks && P.ncols_pad >= DRAW_LANES_MIN_COLS_PER_SM * (int64_t)c->num_sms) ? DRAW_LANES
@@ -1376,6 +1378,12 @@ ept_status run_stream(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, 
     if (!encode_block_tmaps(&th, &tl, bf.Chi, bf.Clo, P.win_blk, bf.c_stride, emsg, sizeof(emsg)))
         return fail(EPT_ECUDA, "%s", emsg);
     const int nwin = (int)P.gI0.size();
+    const int ntimed = std::min(nwin, 64);
+    while ((int)c->ev_win.size() < 2 * ntimed) {
+        cudaEvent_t e = nullptr;
+        CK(cudaEventCreate(&e));
+        c->ev_win.push_back(e);
+    }
     // pass 1: the row sums r (and max |D| for the FP16 scale)
     for (int g = 0; g < nwin; ++g) {
         const Batch gv = stream_view(c, P, g);
@@ -1389,19 +1397,23 @@ ept_status run_stream(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, 
     launch_center(bf, s);
     CK(cudaGetLastError());
     CK(cudaStreamWaitEvent(s, c->ev_side[2], 0));
+    CK(cudaEventRecord(c->ev[2], s));
     // pass 2: build again, pack, contract, fold the partials
     for (int g = 0; g < nwin; ++g) {
         const Batch gv = stream_view(c, P, g);
         CK(launch_build_tc(gv, tm, c->num_sms, s));
         launch_pack(gv, true, s);
         CK(cudaGetLastError());
+        if (g < ntimed) CK(cudaEventRecord(c->ev_win[2 * (size_t)g], s));
         CK(launch_contract_tc(gv, &th, &tl, c->num_sms, s));
+        if (g < ntimed) CK(cudaEventRecord(c->ev_win[2 * (size_t)g + 1], s));
         launch_stream_accum(gv, s);
         CK(cudaGetLastError());
     }
     launch_stream_stats(bf, s);
     launch_combine_count(bf, s);
     CK(cudaGetLastError());
+    CK(cudaEventRecord(c->ev[3], s));
     CK(cudaMemcpyAsync(c->pinned + S.res_ctr, bf.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->pinned + S.res_obs, bf.observed, 8, cudaMemcpyDeviceToHost, s));
     if (P.host_in) CK(cudaMemcpyAsync(c->pinned + S.res_stats, bf.stats, 8 * (size_t)P.nstats, cudaMemcpyDeviceToHost, s));
@@ -1412,6 +1424,20 @@ ept_status run_stream(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, 
     float ms = 0.f;
     cudaEventElapsedTime(&ms, c->ev[0], c->ev[4]);
     out[0].ms_total = ms;
+    // phases: row split + pass 1 + centring (build), pass 2 + combination (perm), the
+    // draws, and the contraction launches (summed; 0 beyond 64 windows)
+    cudaEventElapsedTime(&ms, c->ev[1], c->ev[2]);
+    out[0].ms_build = ms;
+    cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
+    out[0].ms_perm = ms;
+    cudaEventElapsedTime(&ms, c->ev_side[1], c->ev_side[2]);
+    out[0].ms_masks = ms;
+    double con = 0.0;
+    for (int g = 0; g < ntimed; ++g) {
+        cudaEventElapsedTime(&ms, c->ev_win[2 * (size_t)g], c->ev_win[2 * (size_t)g + 1]);
+        con += ms;
+    }
+    out[0].ms_contract = nwin <= 64 ? con : 0.0;
     return EPT_OK;
 }
 
@@ -1766,6 +1792,7 @@ ept_status ept_destroy(ept_ctx *c) {
             if (c->ev_side[k]) cudaEventDestroy(c->ev_side[k]);
         if (c->ev_user) cudaEventDestroy(c->ev_user);
         if (c->ev_in) cudaEventDestroy(c->ev_in);
+        for (cudaEvent_t e : c->ev_win) cudaEventDestroy(e);
         if (c->copy) {
             cudaStreamSynchronize(c->copy);
             cudaStreamDestroy(c->copy);

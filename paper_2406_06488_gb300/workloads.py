@@ -74,8 +74,12 @@ MMD_LAPLACE = TwoSampleSpec(nx=10000, ny=10000, p=100, stat="mmd_laplace", sigma
 MMD_MEDIAN = TwoSampleSpec(nx=10000, ny=10000, p=100, stat="mmd", sigma=-1.0, y_var=1.1, B=10000,
                            seed=0, data_seed=0)
 
+# a test beyond device memory: n = 400,000 pooled rows, whose packed upper blocks
+# (about 2 n^2 = 320 GB) exceed the GPU's memory; it runs in the streaming mode
+STREAM = TwoSampleSpec(nx=200000, ny=200000, p=64, y_mean=0.01, B=10000, seed=0, data_seed=0)
+
 NAMED = {"small": SMALL, "tiny": TINY, "highdim": HIGHDIM, "mmd": MMD, "mmd_laplace": MMD_LAPLACE,
-         "mmd_median": MMD_MEDIAN}
+         "mmd_median": MMD_MEDIAN, "stream": STREAM}
 
 
 def batched_specs(n_tests: int = 512, B: int = 5000, master_seed: int = 0):

@@ -35,7 +35,7 @@ def _rank_main(rank, world, port, out):
 def test_max_over_ranks_and_weak_value_gloo():
     import torch.multiprocessing as mp
     port = _free_port()
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.spawn(_rank_main, args=(2, port, out), nprocs=2, join=True)
         res = dict(out)
