@@ -48,12 +48,17 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="highdim", choices=["highdim", "mmd", "mmd_laplace", "mmd_median", "small",
-                                                                "batched", "serving", "validation", "stream"])
+                                                                "batched", "serving", "validation", "stream",
+                                                                "pooled"])
     ap.add_argument("--tests", type=int, default=512, help="batched: tests per step")
     ap.add_argument("--rates", default="10,100,1000", help="serving: request rates (1/s) swept")
     ap.add_argument("--requests", type=int, default=200, help="serving: requests per rate (at most)")
     ap.add_argument("--serve-plain-rate", type=float, default=10.0,
                     help="serving: rate at which the plain FP32 path is also served (0: skip)")
+    ap.add_argument("--stream-rows", type=int, default=0,
+                    help="stream: pooled rows of the test (0: the 400,000-row workload)")
+    ap.add_argument("--stream-blocks", type=int, default=0,
+                    help="stream: windows of at most this many stored blocks (0: sized to free memory)")
     ap.add_argument("--plain-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -703,10 +708,15 @@ def run_stream(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_2406_06488_gb300 import ept, workloads
+    import dataclasses
     spec = workloads.NAMED["stream"]
+    if args.stream_rows > 0:
+        spec = dataclasses.replace(spec, nx=args.stream_rows // 2, ny=args.stream_rows - args.stream_rows // 2)
     steps = min(args.steps, 5)
     X, Y = workloads.gaussian_pair(spec)
     ctx = ept.Context(local)
+    if args.stream_blocks > 0:
+        ctx.set_option("stream_blocks", args.stream_blocks)
     Xd = torch.from_numpy(X).cuda()
     Yd = torch.from_numpy(Y).cuda()
     stream = torch.cuda.current_stream()
@@ -755,8 +765,9 @@ def run_stream(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps, "warmup": args.warmup,
         "ms_per_step": tot_ms / steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f16", "data": "synthetic",
-        "config": {"workload": "stream: ED nx=%d ny=%d p=%d B=%d (packed blocks ~%.0f GB, beyond device memory)"
-                               % (spec.nx, spec.ny, spec.p, spec.B, 2.0 * n * n / 1e9),
+        "config": {"workload": "stream: ED nx=%d ny=%d p=%d B=%d (packed blocks ~%.0f GB%s)"
+                               % (spec.nx, spec.ny, spec.p, spec.B, 2.0 * n * n / 1e9,
+                                  ", beyond device memory" if args.stream_rows <= 0 else ""),
                    "mode": "streaming: %d windows of row panels, two passes (row sums; build, pack, contract)" % nwin,
                    "precision": "blocks FP32, contraction FP16 hi+lo split on tcgen05, FP32 accumulate, FP64 "
                                 "combine", "l2": "inputs larger than L2 (hundreds of GB per step)",
@@ -785,6 +796,75 @@ def run_stream(args):
     return 0
 
 
+def run_pooled_comparison(args):
+    """The paper's timing experiments (Section 5.1) on the GPU: the efficient test
+    (tuned path), the plain FP32 path and the pre-computation strategy (Algorithm 5,
+    EPT_PREC_POOLED_FP32) on the same tests.  Experiment 1: p = 500, nx = ny = 100 ..
+    1000; experiment 2: nx = ny = 200, p = 200 .. 2000; B = 200 permutations; X ~ N(0, I),
+    Y ~ N(0, I) as in the paper.  Per shape and method: the median over --steps (at most
+    20) timed calls, CUDA events around each call with the inputs on the device."""
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_06488_gb300 import ept, workloads
+    steps = max(1, min(args.steps, 20))
+    ctx = ept.Context(local)
+    stream = torch.cuda.current_stream()
+    methods = ("split_bf16", "plain_fp32", "pooled_fp32")
+
+    def time_shape(nx, p):
+        spec = workloads.TwoSampleSpec(nx=nx, ny=nx, p=p, B=200, seed=1, data_seed=nx + p)
+        X, Y = workloads.gaussian_pair(spec)
+        Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+        row = {"nx": nx, "ny": nx, "p": p, "B": 200}
+        pv = {}
+        for m in methods:
+            for _ in range(args.warmup):
+                ctx.test(Xd, Yd, B=200, seed=1, prec=m)
+            ms = []
+            for _ in range(steps):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = ctx.test(Xd, Yd, B=200, seed=1, prec=m)
+                e1.record(stream)
+                e1.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            row[m + "_ms"] = statistics.median(ms)
+            pv[m] = r.p_value
+        row["pooled_over_efficient"] = row["pooled_fp32_ms"] / row["split_bf16_ms"]
+        row["p_values_equal"] = len(set(pv.values())) == 1
+        return row
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    e1 = [time_shape(n, 500) for n in range(100, 1001, 100)]
+    e2 = [time_shape(200, p) for p in range(200, 2001, 200)]
+    clocks = sampler.stop()
+    if rank != 0:
+        ctx.close()
+        return 0
+    last = e1[-1]
+    line = {
+        "metric": METRIC, "value": 200.0 / (last["split_bf16_ms"] / 1000.0), "unit": UNIT, "n_gpus": ws,
+        "steps": steps, "warmup": args.warmup, "ms_per_step": last["split_bf16_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+        "config": {"workload": "pooled: the paper's timing experiments (Section 5.1), efficient vs pre-computed "
+                               "(Algorithm 5) vs plain FP32; value = efficient path at nx = ny = 1000, p = 500, "
+                               "B = 200",
+                   "timing": "CUDA events around each whole call (planning and launches included), inputs on "
+                             "the device, median of the steps",
+                   "l2": "not flushed (tests of a few MB, as in the paper's repeated runs)"},
+        "experiment1_p500": e1, "experiment2_n200": e2,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     args = _args()
     if args.impl == "reference":
@@ -797,6 +877,8 @@ def main():
         return run_validation(args)
     if args.workload == "stream":
         return run_stream(args)
+    if args.workload == "pooled":
+        return run_pooled_comparison(args)
     return run_ours(args)
 
 

@@ -79,7 +79,14 @@ typedef enum {
        FP32; the contraction s' C s on tcgen05 with C scaled by a power of two and
        split into FP16 hi + lo parts accumulated in FP32 in tensor memory (the name
        is kept from the first version, which split into BF16) */
-    EPT_PREC_SPLIT_BF16 = 1
+    EPT_PREC_SPLIT_BF16 = 1,
+    /* the pre-computation strategy of Algorithm 5, the comparison the paper times
+       the efficient test against (Section 5.1): the full n x n FP32 matrix of the
+       pooled data computed once, each relabeling's three sub-matrices extracted by
+       index and summed (TwoSum-compensated FP32 pairs, FP64 combination).  Single
+       tests only (ept_test, ept_test_range, ept_test_masks; a given sigma); it needs
+       4 n^2 bytes for the matrix.  Elsewhere EPT_EUNSUPPORTED. */
+    EPT_PREC_POOLED_FP32 = 2
 } ept_precision;
 
 typedef struct ept_ctx ept_ctx;

@@ -69,7 +69,7 @@ struct TestSpec {
     double *perm_stats;           // B doubles or null, same memory space as X
 };
 
-ept_status validate(int64_t nx, int64_t ny, int64_t p, int stat, double sigma, int prec) {
+ept_status validate(int64_t nx, int64_t ny, int64_t p, int stat, double sigma, int prec, bool single = false) {
     if (nx < 1 || ny < 1) return fail(EPT_EINVAL, "nx and ny must be >= 1 (got %lld, %lld)", (long long)nx, (long long)ny);
     if (p < 1) return fail(EPT_EINVAL, "p must be >= 1 (got %lld)", (long long)p);
     if (nx + ny > (int64_t)1 << 22) return fail(EPT_EINVAL, "nx + ny = %lld exceeds 2^22", (long long)(nx + ny));
@@ -77,6 +77,12 @@ ept_status validate(int64_t nx, int64_t ny, int64_t p, int stat, double sigma, i
         return fail(EPT_EINVAL, "unknown statistic %d", stat);
     if (stat != EPT_STAT_ED && sigma != EPT_SIGMA_MEDIAN && !(sigma > 0.0 && std::isfinite(sigma)))
         return fail(EPT_EINVAL, "MMD needs a finite bandwidth sigma > 0 or EPT_SIGMA_MEDIAN");
+    if (prec == EPT_PREC_POOLED_FP32) {
+        if (!single) return fail(EPT_EUNSUPPORTED, "the pre-computation baseline runs single tests only");
+        if (stat != EPT_STAT_ED && sigma == EPT_SIGMA_MEDIAN)
+            return fail(EPT_EUNSUPPORTED, "the pre-computation baseline needs a given sigma");
+        return EPT_OK;
+    }
     if (prec != EPT_PREC_PLAIN_FP32 && prec != EPT_PREC_SPLIT_BF16) return fail(EPT_EINVAL, "unknown precision %d", prec);
     return EPT_OK;
 }
@@ -752,6 +758,17 @@ Batch device_view(ept_ctx *c, const Plan &P) {
     return b;
 }
 
+// relabeling-draw kernel of a run: the context's choice, else a thread per column
+// when there are at least 1024 columns per SM; caller relabelings always take the
+// warp kernel (it validates them)
+int draw_mode_for(const ept_ctx *c, const Plan &P) {
+    int mode = c->draw_mode;
+    if (mode == 0)
+        mode = (!P.user_masks && P.ncols_pad >= DRAW_LANES_MIN_COLS_PER_SM * (int64_t)c->num_sms) ? DRAW_LANES
+                                                                                                  : DRAW_WARPS;
+    return P.user_masks ? DRAW_WARPS : mode;
+}
+
 // The device work of one run, enqueued on s (and the side stream).  With `timed`,
 // events mark the phases (not used while capturing a graph).
 // The run's input copies on the copy stream (after `after`'s prior work), then ev_in:
@@ -794,12 +811,7 @@ ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed,
     cudaStream_t s2 = c->side;
     CK(cudaStreamWaitEvent(s2, c->ev[1], 0));
     if (timed) CK(cudaEventRecord(c->ev_side[1], s2));
-    int mode = c->draw_mode;
-    if (mode == 0)
-        mode = (!P.user_masks && P.ncols_pad >= DRAW_LANES_MIN_COLS_PER_SM * (int64_t)c->num_sms) ? DRAW_LANES
-                                                                                                  : DRAW_WARPS;
-    if (P.user_masks) mode = DRAW_WARPS;   // caller relabelings are validated by the warp kernel
-    launch_masks(b, c->num_sms, mode, s2);
+    launch_masks(b, c->num_sms, draw_mode_for(c, P), s2);
     CK(cudaGetLastError());
     CK(cudaEventRecord(c->ev_side[2], s2));
 
@@ -1359,12 +1371,7 @@ ept_status run_stream(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, 
     // relabeling draws on the side stream, beside the first pass
     CK(cudaStreamWaitEvent(c->side, c->ev[1], 0));
     CK(cudaEventRecord(c->ev_side[1], c->side));
-    int mode = c->draw_mode;
-    if (mode == 0)
-        mode = (!P.user_masks && P.ncols_pad >= DRAW_LANES_MIN_COLS_PER_SM * (int64_t)c->num_sms) ? DRAW_LANES
-                                                                                                  : DRAW_WARPS;
-    if (P.user_masks) mode = DRAW_WARPS;
-    launch_masks(bf, c->num_sms, mode, c->side);
+    launch_masks(bf, c->num_sms, draw_mode_for(c, P), c->side);
     CK(cudaGetLastError());
     CK(cudaEventRecord(c->ev_side[2], c->side));
     CK(cudaStreamWaitEvent(s, c->ev_in, 0));
@@ -1441,10 +1448,112 @@ ept_status run_stream(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, 
     return EPT_OK;
 }
 
-// a single test: streamed when its blocks do not fit (or the option asks for it),
-// else the resident path
+// ---------------------------------------------------------------------------
+// Pre-computation baseline (EPT_PREC_POOLED_FP32, Algorithm 5; kernels in
+// ept_pooled.cu).  The test's descriptor comes from plan_batch (its tables are not
+// used); the relabelings mark x* (no complement).  Arena: the tables, the inputs,
+// W (n_pad x n_pad FP32), the masks, the per-chunk sums, the statistics.
+void pooled_layout(Plan &P, int num_sms) {
+    const TestDesc &d = P.desc[0];
+    size_t o = P.tab_bytes;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + std::max<size_t>(bytes, 1), 256);
+        return at;
+    };
+    o = align_up(o, 1024);
+    P.off_in = take(P.in_bytes);
+    P.off_D = take((size_t)d.n_pad * d.n_pad * 4);
+    P.off_maskT = take((size_t)P.nmask * 4);
+    P.win_part = pooled_row_chunks(d.n, d.ncols, num_sms);   // row chunks of the sums
+    P.off_partial = take((size_t)P.win_part * 3 * d.ncols * 8);
+    P.off_stats = take((size_t)P.nstats * 8);
+    P.off_observed = take(8);
+    P.off_ctr = take(sizeof(Counters));
+    P.total = o;
+}
+
+void plan_pooled(Plan &P, const std::vector<TestSpec> &specs, bool host_in, int num_sms) {
+    plan_batch(P, specs, EPT_PREC_PLAIN_FP32, host_in, CHUNK_KB_DEFAULT, num_sms, false, false);
+    TestDesc &d = P.desc[0];
+    d.comp = 0;   // the relabelings mark x*
+    d.m = d.nx;
+    d.other = d.ny;
+    pooled_layout(P, num_sms);
+}
+
+ept_status run_pooled(ept_ctx *c, const std::vector<TestSpec> &specs, bool on_device, ept_result *out, void *stream) {
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    NvtxRange range("ept.run (pooled baseline)");
+    std::unique_ptr<Plan> hold(new (std::nothrow) Plan());
+    if (!hold) return fail(EPT_ENOMEM, "host allocation failed");
+    Plan &P = *hold;
+    plan_pooled(P, specs, !on_device, c->num_sms);
+    if (injected_failure(c)) return fail(EPT_ENOMEM, "device scratch not available (injected failure)");
+    ept_status st = ensure_arena(c, P.total, s);
+    if (st != EPT_OK) return st;
+    const Staging S = staging_layout(P);
+    if ((st = ensure_pinned(c, S.total)) != EPT_OK) return st;
+    if (s != c->stream) CK(cudaStreamSynchronize(c->stream));
+    stage_host(c, P, specs, on_device, true);
+    c->tables_staged = false;   // the pinned tables now hold this run's
+    const TestDesc &d = P.desc[0];
+    uint8_t *A = c->arena;
+    Batch b;
+    memset(&b, 0, sizeof(b));
+    b.n_tests = 1;
+    b.desc = (const TestDesc *)(A + P.off_desc);
+    b.pre.rows = (const int64_t *)(A + P.off_pre_rows);
+    b.pre.panels = (const int64_t *)(A + P.off_pre_panels);
+    b.pre.cols = (const int64_t *)(A + P.off_pre_cols);
+    b.ncols_total = P.ncols_pad;
+    b.nrows_total = P.nrows;
+    b.D = (float *)(A + P.off_D);
+    b.maskT = (uint32_t *)(A + P.off_maskT);
+    b.stats = (double *)(A + P.off_stats);
+    b.observed = (double *)(A + P.off_observed);
+    b.ctr = (Counters *)(A + P.off_ctr);
+    double *part = (double *)(A + P.off_partial);
+
+    CK(cudaEventRecord(c->ev[0], s));
+    if ((st = enqueue_uploads(c, P, s)) != EPT_OK) return st;
+    CK(cudaMemsetAsync(b.ctr, 0, sizeof(Counters), s));
+    CK(cudaEventRecord(c->ev[1], s));
+    // the relabelings (Algorithm 5's SampleWithoutReplacement, the library's stream)
+    // on the side stream, beside the matrix
+    CK(cudaStreamWaitEvent(c->side, c->ev[1], 0));
+    CK(cudaEventRecord(c->ev_side[1], c->side));
+    launch_masks(b, c->num_sms, draw_mode_for(c, P), c->side);
+    CK(cudaGetLastError());
+    CK(cudaEventRecord(c->ev_side[2], c->side));
+    CK(cudaStreamWaitEvent(s, c->ev_in, 0));
+    CK(cudaStreamWaitEvent(s, c->ev_side[2], 0));
+    CK(cudaEventRecord(c->ev[2], s));
+    CK(launch_pooled(b, d.n, d.n_pad, d.ncols, part, P.win_part, d.nw, s));
+    CK(cudaEventRecord(c->ev[3], s));
+    launch_combine_count(b, s);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(c->pinned + S.res_ctr, b.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(c->pinned + S.res_obs, b.observed, 8, cudaMemcpyDeviceToHost, s));
+    if (P.host_in) CK(cudaMemcpyAsync(c->pinned + S.res_stats, b.stats, 8 * (size_t)P.nstats, cudaMemcpyDeviceToHost, s));
+    CK(cudaEventRecord(c->ev[4], s));
+    CK(cudaStreamSynchronize(s));
+    if ((st = collect(c, P, specs, out, false)) != EPT_OK) return st;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, c->ev[0], c->ev[4]);
+    out[0].ms_total = ms;
+    cudaEventElapsedTime(&ms, c->ev_side[1], c->ev_side[2]);
+    out[0].ms_masks = ms;
+    cudaEventElapsedTime(&ms, c->ev[2], c->ev[3]);
+    out[0].ms_perm = ms;   // matrix and sums (the matrix and the extraction are one launch sequence)
+    return EPT_OK;
+}
+
+// a single test: the pre-computation baseline when asked for; streamed when its
+// blocks do not fit (or the option asks for it); else the resident path
 ept_status run_single(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bool on_device, bool tuned,
                       ept_result *out, void *stream) {
+    if (prec == EPT_PREC_POOLED_FP32) return run_pooled(c, specs, on_device, out, stream);
     if (use_stream(c, specs[0], prec)) return run_stream(c, specs, prec, on_device, out, stream);
     if (tuned) return run_tuned(c, specs, prec, on_device, true, out, stream);
     return run_once(c, specs, prec, on_device, CHUNK_KB_DEFAULT, false, out, stream, nullptr);
@@ -1806,6 +1915,11 @@ ept_status ept_destroy(ept_ctx *c) {
 
 size_t ept_estimate_bytes(int64_t nx, int64_t ny, int64_t p, int64_t B, int prec) {
     if (nx < 1 || ny < 1 || p < 1 || B < 0 || nx + ny > ((int64_t)1 << 22)) return 0;
+    if (prec == EPT_PREC_POOLED_FP32) {
+        Plan P;
+        plan_pooled(P, one_test(nullptr, nx, nullptr, ny, p, 0, 1.0, B, 0, nullptr, nullptr), true, 148);
+        return P.total;
+    }
     if (prec != EPT_PREC_PLAIN_FP32 && prec != EPT_PREC_SPLIT_BF16) return 0;
     Plan P;
     plan_batch(P, one_test(nullptr, nx, nullptr, ny, p, 0, 1.0, B, 0, nullptr, nullptr), prec, true, 8);
@@ -1818,7 +1932,7 @@ ept_status ept_test(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, in
     if (!ctx) return fail(EPT_EINVAL, "null context");
     if (!X || !Y || !out) return fail(EPT_EINVAL, "null X, Y or result pointer");
     if (B < 0 || B > ((int64_t)1 << 31)) return fail(EPT_EINVAL, "B must be in [0, 2^31]");
-    ept_status st = validate(nx, ny, p, stat, sigma, prec);
+    ept_status st = validate(nx, ny, p, stat, sigma, prec, true);
     if (st != EPT_OK) return st;
     std::lock_guard<std::mutex> lock(ctx->mu);
     DeviceGuard dg(ctx->device);
@@ -1833,7 +1947,7 @@ ept_status ept_test_range(ept_ctx *ctx, const float *X, int64_t nx, const float 
     if (!X || !Y) return fail(EPT_EINVAL, "null X or Y");
     if (count < 0 || count > ((int64_t)1 << 31)) return fail(EPT_EINVAL, "count must be in [0, 2^31]");
     if (b_first < 1 || b_first > ((int64_t)1 << 62)) return fail(EPT_EINVAL, "b_first must be >= 1");
-    ept_status st = validate(nx, ny, p, stat, sigma, prec);
+    ept_status st = validate(nx, ny, p, stat, sigma, prec, true);
     if (st != EPT_OK) return st;
     std::vector<TestSpec> specs = one_test(X, nx, Y, ny, p, stat, sigma, count, seed, nullptr, perm_stats);
     specs[0].b0 = b_first;
@@ -1849,7 +1963,7 @@ ept_status ept_test_masks(ept_ctx *ctx, const float *X, int64_t nx, const float 
     if (!X || !Y || !out) return fail(EPT_EINVAL, "null X, Y or result pointer");
     if (n_masks < 0 || n_masks > ((int64_t)1 << 31)) return fail(EPT_EINVAL, "n_masks must be in [0, 2^31]");
     if (n_masks > 0 && !masks) return fail(EPT_EINVAL, "null masks");
-    ept_status st = validate(nx, ny, p, stat, sigma, prec);
+    ept_status st = validate(nx, ny, p, stat, sigma, prec, true);
     if (st != EPT_OK) return st;
     std::lock_guard<std::mutex> lock(ctx->mu);
     DeviceGuard dg(ctx->device);

@@ -237,6 +237,14 @@ void launch_stream_accum(const Batch &g, cudaStream_t s);
 // the statistics from sacc (after the last window)
 void launch_stream_stats(const Batch &b, cudaStream_t s);
 
+// ---- pre-computation baseline (ept_pooled.cu): one test, Algorithm 5 ----
+// row chunks of the per-relabeling sums (about four CTAs per SM in all)
+int64_t pooled_row_chunks(int64_t n, int64_t ncols, int num_sms);
+// W (into b.D, row stride ld), the per-chunk sums (part: nchunks x 3 x ncols doubles)
+// and the statistics (b.stats); the relabelings must be in b.maskT (marking x*)
+cudaError_t launch_pooled(const Batch &b, int64_t n, int64_t ld, int64_t ncols, double *part, int64_t nchunks,
+                          int64_t nw, cudaStream_t s);
+
 void set_last_error(const char *msg);   // ept_api.cu
 
 }  // namespace ept

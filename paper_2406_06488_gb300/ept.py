@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libept.so")
 STAT = {"ed": 0, "mmd": 1, "mmd_gauss": 1, "mmd_laplace": 2}
 SIGMA_MEDIAN = -1.0   # EPT_SIGMA_MEDIAN: bandwidth from the median heuristic
 ABI_VERSION = 3       # EPT_ABI_VERSION this binding's structures follow
-PREC = {"plain_fp32": 0, "split_bf16": 1}
+PREC = {"plain_fp32": 0, "split_bf16": 1, "pooled_fp32": 2}   # pooled_fp32: Algorithm 5 baseline
 STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT_ECUDA", 5: "EPT_ETIMEOUT",
           6: "EPT_ECANCELLED", 7: "EPT_ENOTFOUND", 8: "EPT_EUNSUPPORTED", 9: "EPT_EINTERNAL"}
 
