@@ -1219,18 +1219,39 @@ void stream_partition(Plan &P, int64_t limit_blk, size_t limit_bytes) {
 // Arena layout of a streaming run: the test's tables as plan_batch laid them out,
 // the windows' descriptors and unit prefixes, the per-row and per-relabeling arrays
 // of the whole test, then the window (blocks, their sums, the partials).
-void stream_layout(Plan &P, size_t tab_bytes_resident) {
-    const TestDesc &d = P.desc[0];
-    size_t o = tab_bytes_resident;
-    auto take = [&](size_t bytes) {
+// Debug checks: a guard band after every data region (the tables are uploaded whole).
+struct LayoutCursor {
+    Plan &P;
+    size_t o;
+    bool in_data = false;
+    size_t take(size_t bytes) {
         const size_t at = o;
         o = align_up(o + std::max<size_t>(bytes, 1), 256);
+        if (P.debug && in_data && P.guards.n < MAX_GUARDS) {
+            P.guards.off[P.guards.n++] = o;
+            o += GUARD_BYTES;
+        }
         return at;
-    };
+    }
+    void start_data() {   // after the tables: a band right away, then one after each region
+        o = align_up(o, 1024);
+        in_data = true;
+        if (P.debug && P.guards.n < MAX_GUARDS) {
+            P.guards.off[P.guards.n++] = o;
+            o += GUARD_BYTES;
+        }
+    }
+};
+
+void stream_layout(Plan &P, size_t tab_bytes_resident) {
+    const TestDesc &d = P.desc[0];
+    P.guards.n = 0;
+    LayoutCursor L{P, tab_bytes_resident};
+    auto take = [&](size_t bytes) { return L.take(bytes); };
     P.off_gdesc = take(sizeof(TestDesc) * P.gdesc.size());
     P.off_gpre = take(8 * P.gpre.size());
-    P.tab_bytes = o;
-    o = align_up(o, 1024);
+    P.tab_bytes = L.o;
+    L.start_data();
     P.off_in = take(P.in_bytes);
     P.off_norms = take((size_t)P.nrows * 4);
     P.off_iscale = take((size_t)P.nrows * 4);
@@ -1252,7 +1273,33 @@ void stream_layout(Plan &P, size_t tab_bytes_resident) {
     P.off_rowpart = take((size_t)P.win_blk * PANEL * 8);
     P.off_colpart = take((size_t)P.win_blk * KB * 8);
     P.off_partial = take((size_t)P.win_part * 4);
-    P.total = o;
+    P.total = L.o;
+}
+
+// Debug checks on the host: the windows of a streaming plan cover the panels in
+// order, once, within the window's capacity.
+ept_status check_stream_plan(const Plan &P) {
+    auto bad = [](const char *what) { return fail(EPT_EINTERNAL, "debug checks: streaming plan broken: %s", what); };
+    const TestDesc &d = P.desc[0];
+    int64_t next = 0, tiles = 0;
+    for (size_t g = 0; g < P.gI0.size(); ++g) {
+        if (P.gI0[g] != next || P.gI1[g] <= P.gI0[g] || P.gI1[g] > d.NP) return bad("panel ranges");
+        next = P.gI1[g];
+        if (P.gblk0[g] != blk_off(P.gI0[g], d.NKB) || P.gnblk[g] != blk_off(P.gI1[g], d.NKB) - P.gblk0[g])
+            return bad("block ranges");
+        if (P.gnblk[g] > P.win_blk || P.gdesc[g].nparts * d.Bp > P.win_part) return bad("window capacity");
+        if (P.gdesc[g].blk0 != -P.gblk0[g] || P.gdesc[g].part0 != 0) return bad("window offsets");
+        if (P.gtile0[g] != tiles) return bad("tile ranges");
+        tiles += P.gntile[g];
+        for (int64_t q = 0; q < P.gdesc[g].nchunks; ++q) {
+            const Chunk &ch = P.chunks[(size_t)(P.gdesc[g].chunk0 + q)];
+            if (ch.I < P.gI0[g] || ch.I >= P.gI1[g]) return bad("chunks outside their window");
+        }
+    }
+    if (next != d.NP || tiles != (int64_t)P.tiles.size()) return bad("coverage");
+    for (int k = 0; k < P.guards.n; ++k)
+        if (P.guards.off[k] + GUARD_BYTES > P.total || P.guards.off[k] % 256) return bad("guard band");
+    return EPT_OK;
 }
 
 // device view of a streaming run: the whole test (g < 0) or window g
@@ -1315,7 +1362,7 @@ ept_status run_stream(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, 
     std::unique_ptr<Plan> hold(new (std::nothrow) Plan());
     if (!hold) return fail(EPT_ENOMEM, "host allocation failed");
     Plan &P = *hold;
-    plan_batch(P, specs, prec, !on_device, CHUNK_KB_DEFAULT, c->num_sms, false, false);
+    plan_batch(P, specs, prec, !on_device, CHUNK_KB_DEFAULT, c->num_sms, c->debug, false);
     P.stream = true;
     const size_t tab0 = P.tab_bytes;
     const TestDesc &d = P.desc[0];
@@ -1343,6 +1390,11 @@ ept_status run_stream(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, 
             return fail(EPT_ENOMEM, "the streaming mode needs %zu bytes of device memory, %zu are available", P.total,
                         avail);
     }
+    if (c->debug) {
+        ept_status st0 = check_plan(P);
+        if (st0 == EPT_OK) st0 = check_stream_plan(P);
+        if (st0 != EPT_OK) return st0;
+    }
     if (injected_failure(c)) return fail(EPT_ENOMEM, "device scratch not available (injected failure)");
     ept_status st = ensure_arena(c, P.total, s, true);
     if (st != EPT_OK) return st;
@@ -1365,6 +1417,7 @@ ept_status run_stream(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, 
     CK(cudaEventRecord(c->ev[0], s));
     if ((st = enqueue_uploads(c, P, s)) != EPT_OK) return st;
     CK(cudaMemsetAsync(bf.ctr, 0, sizeof(Counters), s));
+    if (P.debug) launch_guards(c->arena, P.guards, false, bf.ctr, s);
     CK(cudaMemsetAsync(bf.r, 0, (size_t)P.nrows * 8, s));
     CK(cudaMemsetAsync(bf.sacc, 0, (size_t)d.Bp * 8, s));
     CK(cudaEventRecord(c->ev[1], s));
@@ -1420,6 +1473,7 @@ ept_status run_stream(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, 
     launch_stream_stats(bf, s);
     launch_combine_count(bf, s);
     CK(cudaGetLastError());
+    if (P.debug) launch_guards(c->arena, P.guards, true, bf.ctr, s);
     CK(cudaEventRecord(c->ev[3], s));
     CK(cudaMemcpyAsync(c->pinned + S.res_ctr, bf.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->pinned + S.res_obs, bf.observed, 8, cudaMemcpyDeviceToHost, s));
@@ -1455,13 +1509,10 @@ ept_status run_stream(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, 
 // W (n_pad x n_pad FP32), the masks, the per-chunk sums, the statistics.
 void pooled_layout(Plan &P, int num_sms) {
     const TestDesc &d = P.desc[0];
-    size_t o = P.tab_bytes;
-    auto take = [&](size_t bytes) {
-        const size_t at = o;
-        o = align_up(o + std::max<size_t>(bytes, 1), 256);
-        return at;
-    };
-    o = align_up(o, 1024);
+    P.guards.n = 0;
+    LayoutCursor L{P, P.tab_bytes};
+    auto take = [&](size_t bytes) { return L.take(bytes); };
+    L.start_data();
     P.off_in = take(P.in_bytes);
     P.off_D = take((size_t)d.n_pad * d.n_pad * 4);
     P.off_maskT = take((size_t)P.nmask * 4);
@@ -1470,11 +1521,11 @@ void pooled_layout(Plan &P, int num_sms) {
     P.off_stats = take((size_t)P.nstats * 8);
     P.off_observed = take(8);
     P.off_ctr = take(sizeof(Counters));
-    P.total = o;
+    P.total = L.o;
 }
 
-void plan_pooled(Plan &P, const std::vector<TestSpec> &specs, bool host_in, int num_sms) {
-    plan_batch(P, specs, EPT_PREC_PLAIN_FP32, host_in, CHUNK_KB_DEFAULT, num_sms, false, false);
+void plan_pooled(Plan &P, const std::vector<TestSpec> &specs, bool host_in, int num_sms, bool debug = false) {
+    plan_batch(P, specs, EPT_PREC_PLAIN_FP32, host_in, CHUNK_KB_DEFAULT, num_sms, debug, false);
     TestDesc &d = P.desc[0];
     d.comp = 0;   // the relabelings mark x*
     d.m = d.nx;
@@ -1488,7 +1539,7 @@ ept_status run_pooled(ept_ctx *c, const std::vector<TestSpec> &specs, bool on_de
     std::unique_ptr<Plan> hold(new (std::nothrow) Plan());
     if (!hold) return fail(EPT_ENOMEM, "host allocation failed");
     Plan &P = *hold;
-    plan_pooled(P, specs, !on_device, c->num_sms);
+    plan_pooled(P, specs, !on_device, c->num_sms, c->debug);
     if (injected_failure(c)) return fail(EPT_ENOMEM, "device scratch not available (injected failure)");
     ept_status st = ensure_arena(c, P.total, s);
     if (st != EPT_OK) return st;
@@ -1518,6 +1569,7 @@ ept_status run_pooled(ept_ctx *c, const std::vector<TestSpec> &specs, bool on_de
     CK(cudaEventRecord(c->ev[0], s));
     if ((st = enqueue_uploads(c, P, s)) != EPT_OK) return st;
     CK(cudaMemsetAsync(b.ctr, 0, sizeof(Counters), s));
+    if (P.debug) launch_guards(c->arena, P.guards, false, b.ctr, s);
     CK(cudaEventRecord(c->ev[1], s));
     // the relabelings (Algorithm 5's SampleWithoutReplacement, the library's stream)
     // on the side stream, beside the matrix
@@ -1533,6 +1585,7 @@ ept_status run_pooled(ept_ctx *c, const std::vector<TestSpec> &specs, bool on_de
     CK(cudaEventRecord(c->ev[3], s));
     launch_combine_count(b, s);
     CK(cudaGetLastError());
+    if (P.debug) launch_guards(c->arena, P.guards, true, b.ctr, s);
     CK(cudaMemcpyAsync(c->pinned + S.res_ctr, b.ctr, sizeof(Counters), cudaMemcpyDeviceToHost, s));
     CK(cudaMemcpyAsync(c->pinned + S.res_obs, b.observed, 8, cudaMemcpyDeviceToHost, s));
     if (P.host_in) CK(cudaMemcpyAsync(c->pinned + S.res_stats, b.stats, 8 * (size_t)P.nstats, cudaMemcpyDeviceToHost, s));

@@ -58,3 +58,33 @@ def test_guards_hold_for_batches_masks_and_ranges(ctxs):
     assert dbg.test_masks(X, Y, masks).observed == ref.test_masks(X, Y, masks).observed
     assert dbg.test_range(X, Y, b_first=17, count=99, seed=2).n_ge == ref.test_range(X, Y, b_first=17, count=99,
                                                                                     seed=2).n_ge
+
+
+@pytest.mark.parametrize("nx,ny,p,B,stat", [(9, 1, 3, 40, "ed"), (300, 420, 70, 700, "mmd"),
+                                            (700, 900, 37, 300, "mmd_laplace")])
+def test_guards_hold_in_streaming_mode(ctxs, nx, ny, p, B, stat):
+    # windows of one panel each: every window's blocks, sums and partials reuse the
+    # same guarded regions
+    dbg, ref = ctxs
+    X, Y = _pair(nx, ny, p, seed=nx + 2 * ny)
+    try:
+        for c in (dbg, ref):
+            c.set_option("stream_blocks", 1)
+        a = dbg.test(X, Y, B=B, seed=4, stat=stat, sigma=2.0)
+        b = ref.test(X, Y, B=B, seed=4, stat=stat, sigma=2.0)
+    finally:
+        for c in (dbg, ref):
+            c.set_option("stream_blocks", 0)
+    assert a.n_windows == (nx + ny + 255) // 256
+    assert a.observed == b.observed and a.n_ge == b.n_ge
+    assert np.array_equal(np.asarray(a.stats), np.asarray(b.stats))
+
+
+@pytest.mark.parametrize("nx,ny,p,B", [(1, 1, 1, 5), (255, 2, 5, 300), (600, 500, 40, 257)])
+def test_guards_hold_for_the_precomputation_baseline(ctxs, nx, ny, p, B):
+    dbg, ref = ctxs
+    X, Y = _pair(nx, ny, p, seed=nx + 3 * ny)
+    a = dbg.test(X, Y, B=B, seed=6, prec="pooled_fp32")
+    b = ref.test(X, Y, B=B, seed=6, prec="pooled_fp32")
+    assert a.observed == b.observed and a.n_ge == b.n_ge
+    assert np.array_equal(np.asarray(a.stats), np.asarray(b.stats))
