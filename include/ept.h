@@ -125,6 +125,29 @@ const char *ept_last_error(void);
    device is not compute capability 10.3.  *out receives the context. */
 ept_status ept_create(ept_ctx **out, int device, size_t mem_budget_bytes);
 
+/* Caller-supplied device memory for a context's scratch (ept_create_ex).
+   alloc(bytes, stream, user): device memory of at least `bytes` bytes on the
+   context's device, aligned to 256 bytes, usable by work enqueued on `stream` (a
+   cudaStream_t) from now on; NULL if it cannot be had (the call then fails with
+   EPT_ENOMEM).  free(ptr, stream, user): gives back memory from alloc; the
+   memory's last use is the work already enqueued on `stream`, so a stream-ordered
+   allocator (like cudaFreeAsync) may reuse it once that work is done, and any
+   other allocator must synchronise `stream` before reusing it.  The callbacks may
+   be called from the calling thread and from the serving scheduler's thread (one at
+   a time per context), never from inside a CUDA callback.  The pinned host staging
+   memory stays the library's own. */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *stream, void *user);
+    void (*free)(void *ptr, void *stream, void *user);
+    void *user;
+} ept_allocator;
+
+/* ept_create with a caller-supplied allocator for all device scratch of the
+   context (the run arena, streaming windows, serving batches); alloc = NULL
+   behaves as ept_create (cudaMalloc for runs, a stream-ordered memory pool for
+   serving).  The struct is copied. */
+ept_status ept_create_ex(ept_ctx **out, int device, size_t mem_budget_bytes, const ept_allocator *alloc);
+
 /* Destroy a context and free its device and pinned memory.  NULL is accepted. */
 ept_status ept_destroy(ept_ctx *ctx);
 

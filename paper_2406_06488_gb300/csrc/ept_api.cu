@@ -496,6 +496,7 @@ struct ept_ctx {
     bool debug = false;                 // guard bands around scratch regions, plan invariants checked
     int draw_mode = 0;                  // relabeling draws: 0 automatic, DRAW_WARPS, DRAW_LANES
     int64_t stream_blocks = 0;          // streaming mode: 0 automatic, k > 0 windows of <= k blocks, -1 never
+    ept_allocator alloc{};              // caller-supplied device memory (alloc.alloc == nullptr: cudaMalloc)
     std::atomic<int> inject_alloc{0};   // test hook: the next N scratch acquisitions fail (host side)
     bool inject_stall = false;          // test hook: the next run's contraction waits out its limit
     int serve_lanes = 3;                // serving: batches in flight at once
@@ -553,6 +554,36 @@ void drop_graph(ept_ctx *c) {
     c->graph = GraphCache();
 }
 
+// device memory through the context's allocator (or cudaMalloc / cudaFree); memory
+// from a caller's allocator must be 256-byte aligned (the tensor maps and the
+// arena's own alignment rely on it)
+ept_status device_alloc(ept_ctx *c, size_t bytes, cudaStream_t s, void **out) {
+    *out = nullptr;
+    if (c->alloc.alloc) {
+        void *p = c->alloc.alloc(bytes, (void *)s, c->alloc.user);
+        if (!p) return fail(EPT_ENOMEM, "the caller's allocator returned no memory for %zu bytes", bytes);
+        if ((uintptr_t)p % 256) {
+            c->alloc.free(p, (void *)s, c->alloc.user);
+            return fail(EPT_EINVAL, "the caller's allocator returned an address not aligned to 256 bytes");
+        }
+        *out = p;
+        return EPT_OK;
+    }
+    cudaError_t e = cudaMalloc(out, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *out = nullptr;
+        return fail(EPT_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return EPT_OK;
+}
+
+void device_free(ept_ctx *c, void *p, cudaStream_t s) {
+    if (!p) return;
+    if (c->alloc.alloc) c->alloc.free(p, (void *)s, c->alloc.user);
+    else cudaFree(p);
+}
+
 // exact: allocate just `bytes` (the streaming mode sizes its window to the memory
 // there is), else 1/8 more, so that slightly larger runs reuse the arena
 ept_status ensure_arena(ept_ctx *c, size_t bytes, cudaStream_t s, bool exact = false) {
@@ -564,17 +595,15 @@ ept_status ensure_arena(ept_ctx *c, size_t bytes, cudaStream_t s, bool exact = f
     CK(cudaStreamSynchronize(c->stream));
     drop_graph(c);
     if (c->arena) {
-        cudaFree(c->arena);
+        device_free(c, c->arena, c->stream);
         c->arena = nullptr;
         c->arena_cap = 0;
     }
     const size_t cap = align_up(exact ? bytes : bytes + bytes / 8, 1 << 20);
-    cudaError_t e = cudaMalloc(&c->arena, cap);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        c->arena = nullptr;
-        return fail(EPT_ENOMEM, "cudaMalloc(%zu bytes) failed: %s", cap, cudaGetErrorString(e));
-    }
+    void *p = nullptr;
+    ept_status st = device_alloc(c, cap, c->stream, &p);
+    if (st != EPT_OK) return st;
+    c->arena = (uint8_t *)p;
     c->arena_cap = cap;
     return EPT_OK;
 }
@@ -1685,11 +1714,16 @@ ept_status lane_enqueue(Server *S, Lane &L) {
     NvtxRange range("ept.serve.batch");
     if (injected_failure(S->owner)) return fail(EPT_ENOMEM, "device scratch not available (injected failure)");
     void *mem = nullptr;
-    cudaError_t e = cudaMallocFromPoolAsync(&mem, L.plan.total, S->pool, s);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(EPT_ENOMEM, "device scratch of %zu bytes not available: %s", (size_t)L.plan.total,
-                    cudaGetErrorString(e));
+    ept_allocator &ua = S->owner->alloc;
+    if (ua.alloc) {
+        if ((st = device_alloc(S->owner, L.plan.total, s, &mem)) != EPT_OK) return st;
+    } else {
+        cudaError_t e = cudaMallocFromPoolAsync(&mem, L.plan.total, S->pool, s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(EPT_ENOMEM, "device scratch of %zu bytes not available: %s", (size_t)L.plan.total,
+                        cudaGetErrorString(e));
+        }
     }
     L.arena = (uint8_t *)mem;
     c->arena = L.arena;   // the kernels and staging address the lane's scratch through the context
@@ -1698,7 +1732,10 @@ ept_status lane_enqueue(Server *S, Lane &L) {
     st = enqueue_device(c, L.plan, s, false);
     c->arena = nullptr;
     c->arena_cap = 0;
-    e = cudaFreeAsync(L.arena, s);   // returns to the pool once the run's work is done
+    // back to the pool (or the caller's allocator) once the run's work is done
+    cudaError_t e = cudaSuccess;
+    if (ua.alloc) ua.free(L.arena, (void *)s, ua.user);
+    else e = cudaFreeAsync(L.arena, s);
     L.arena = nullptr;
     if (st != EPT_OK) return st;
     if (e != cudaSuccess) return fail(EPT_ECUDA, "cudaFreeAsync: %s", cudaGetErrorString(e));
@@ -1898,7 +1935,13 @@ int ept_abi_version(void) { return EPT_ABI_VERSION; }
 const char *ept_last_error(void) { return g_err.c_str(); }
 
 ept_status ept_create(ept_ctx **out, int device, size_t mem_budget_bytes) {
+    return ept_create_ex(out, device, mem_budget_bytes, nullptr);
+}
+
+ept_status ept_create_ex(ept_ctx **out, int device, size_t mem_budget_bytes, const ept_allocator *alloc) {
     if (!out) return fail(EPT_EINVAL, "null output pointer");
+    if (alloc && (!alloc->alloc != !alloc->free))
+        return fail(EPT_EINVAL, "an allocator needs both alloc and free (or neither)");
     *out = nullptr;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
@@ -1916,6 +1959,7 @@ ept_status ept_create(ept_ctx **out, int device, size_t mem_budget_bytes) {
     c->device = device;
     c->num_sms = prop.multiProcessorCount;
     c->budget = mem_budget_bytes;
+    if (alloc) c->alloc = *alloc;
     const char *at = getenv("EPT_AUTOTUNE");
     c->autotune = !(at && at[0] == '0');
     const char *tf = getenv("EPT_AUTOTUNE_CACHE");
@@ -1945,7 +1989,7 @@ ept_status ept_destroy(ept_ctx *c) {
         if (c->stream) cudaStreamSynchronize(c->stream);
         if (c->side) cudaStreamSynchronize(c->side);
         drop_graph(c);
-        if (c->arena) cudaFree(c->arena);
+        if (c->arena) device_free(c, c->arena, c->stream);
         if (c->pinned) cudaFreeHost(c->pinned);
         delete c->plan;
         for (int k = 0; k < 7; ++k)

@@ -31,7 +31,7 @@ STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT
 EXPORTS = ["ept_abi_version", "ept_last_error", "ept_create", "ept_destroy", "ept_estimate_bytes", "ept_test",
            "ept_test_masks", "ept_perm_masks", "ept_build_blocks", "ept_test_static", "ept_test_batch",
            "ept_set_option", "ept_submit", "ept_poll", "ept_wait", "ept_cancel", "ept_test_range",
-           "ept_serving_stats"]
+           "ept_serving_stats", "ept_create_ex"]
 
 
 class EptError(RuntimeError):
@@ -51,6 +51,15 @@ class _Result(ctypes.Structure):
                 ("n_near_tie", ctypes.c_int64), ("n_fixup", ctypes.c_int64), ("ms_build", ctypes.c_double),
                 ("ms_perm", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_masks", ctypes.c_double),
                 ("ms_contract", ctypes.c_double), ("sigma", ctypes.c_double), ("n_windows", ctypes.c_int64)]
+
+
+# ept_allocator: device memory from the caller (ept_create_ex)
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", ctypes.c_void_p)]
 
 
 @dataclass
@@ -97,6 +106,8 @@ def load():
     lib.ept_last_error.restype = ctypes.c_char_p
     lib.ept_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_size_t]
     lib.ept_create.restype = i32
+    lib.ept_create_ex.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_size_t, ctypes.POINTER(_Allocator)]
+    lib.ept_create_ex.restype = i32
     lib.ept_destroy.argtypes = [vp]
     lib.ept_destroy.restype = i32
     lib.ept_estimate_bytes.argtypes = [i64, i64, i64, i64, i32]
@@ -175,10 +186,28 @@ OPTION = {"graphs": 1, "autotune": 2, "serve_lanes": 3, "serve_slots": 4, "draw_
 class Context:
     """One libept context on one CUDA device (owns its scratch memory and stream)."""
 
-    def __init__(self, device: int = 0, budget_bytes: int = 0):
+    def __init__(self, device: int = 0, budget_bytes: int = 0, allocator=None):
+        """allocator: optional (alloc, free) pair of callables for the context's device
+        scratch -- alloc(nbytes, stream) -> device address (int, 256-byte aligned; 0 on
+        failure), free(address, stream); `stream` is the cudaStream_t (int) whose work
+        uses the memory (ept_allocator in ept.h)."""
         lib = load()
         h = ctypes.c_void_p()
-        _check(lib.ept_create(ctypes.byref(h), int(device), int(budget_bytes)))
+        self._alloc_keep = None
+        if allocator is None:
+            _check(lib.ept_create(ctypes.byref(h), int(device), int(budget_bytes)))
+        else:
+            a_fn, f_fn = allocator
+
+            def _a(nbytes, stream, user):
+                return int(a_fn(int(nbytes), int(stream or 0))) or None
+
+            def _f(ptr, stream, user):
+                f_fn(int(ptr or 0), int(stream or 0))
+
+            st = _Allocator(_ALLOC_FN(_a), _FREE_FN(_f), None)
+            self._alloc_keep = st   # the callbacks must outlive the context
+            _check(lib.ept_create_ex(ctypes.byref(h), int(device), int(budget_bytes), ctypes.byref(st)))
         self._h = h
         self.device = int(device)
 
