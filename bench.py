@@ -34,7 +34,8 @@ if ROOT not in sys.path:
 
 METRIC = "permuted stats/s & p99 test latency, tuned vs plain FP32 GPU at rel err ≤1e-5"
 UNIT = "permuted stats/s"
-KERNELS_PER_STEP = 11  # libept kernels launched by one ept_test / ept_test_batch run (split path)
+KERNELS_PER_STEP = 11  # libept kernels launched by one ept_test run (split path)
+BATCH_KERNELS_PER_STEP = 12  # ept_test_batch: the same and the batch's error status
 # dram read + write bytes of one k_contract_tc launch on the highdim workload, from the ncu
 # capture summarised in profiles/k_contract_tc_highdim_ed.md (to be reset to {} whenever the
 # kernel changes, until it is captured again)
@@ -522,7 +523,7 @@ def run_batched(args):
                      "peak_kind": "%s bf16 dense burst" % peak_kind, "algorithmic_flops_per_launch": alg_flops},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(in_bytes),
                 "d2h_bytes_per_step": int(sum((sp.B + 1) * 8 + 48 for sp in specs)), "steps": args.e2e_steps},
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "gpu_launches": BATCH_KERNELS_PER_STEP * args.steps,
         "clocks": clocks,
     }
     if cpu is not None:

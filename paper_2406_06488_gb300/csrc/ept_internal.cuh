@@ -66,6 +66,8 @@ struct Counters {
     unsigned int never_set;          // stays 0: the failure-path test hook waits for it
     unsigned long long sel_k;        //   rank still to find within the prefix
     unsigned long long guard_bad;    // debug checks: words of the guard bands found overwritten
+    unsigned long long batch_failed; // (test 0) some test of a batched call has an error: device outputs
+                                     //   of the call are then left unwritten
 };
 
 // Debug checks: guard bands of GUARD_BYTES after every scratch region, filled with a

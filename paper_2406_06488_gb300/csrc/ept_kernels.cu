@@ -959,7 +959,31 @@ __global__ void __launch_bounds__(256) k_combine_stats(const Batch bt) {
     }
 }
 
-// Counting and outputs: a CTA covers 256 columns of one test.
+// Errors of test t that the host will report: non-finite data, malformed
+// relabelings, a median bandwidth that is not positive and finite.
+__device__ __forceinline__ bool test_failed(const Batch &bt, int t) {
+    const Counters &k = bt.ctr[t];
+    bool f = k.nonfinite || k.bad_mask;
+    if (bt.desc[t].median) {
+        const float sg = __uint_as_float(k.sel_prefix);
+        f = f || !(sg > 0.f) || !isfinite(sg);
+    }
+    return f;
+}
+
+// Whether any test of a batch failed (one CTA): a batched call that returns an
+// error writes none of its device outputs.
+__global__ void __launch_bounds__(256) k_batch_status(const Batch bt) {
+    int bad = 0;
+    for (int t = threadIdx.x; t < bt.n_tests; t += blockDim.x) bad |= test_failed(bt, t) ? 1 : 0;
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x == 0 && bad) bt.ctr[0].batch_failed = 1ull;
+}
+
+// Counting and outputs: a CTA covers 256 columns of one test.  A caller's device
+// buffer of permuted statistics is written only when the call will succeed (no
+// error in any test of the call, no expired wait), so that output buffers are
+// written only on success.
 __global__ void __launch_bounds__(256) k_combine_count(const Batch bt) {
     const int64_t gc = (int64_t)blockIdx.x * 256 + threadIdx.x;
     const int t = find_test(bt.pre.cols, bt.n_tests, (int64_t)blockIdx.x * 256);
@@ -971,7 +995,9 @@ __global__ void __launch_bounds__(256) k_combine_count(const Batch bt) {
         const double v = bt.stats[d.col0 + c];
         ge = v >= obs;
         near = fabs(v - obs) <= 1e-5 * fabs(obs);
-        if (d.out_stats) d.out_stats[c - 1] = v;
+        if (d.out_stats) {
+            if (!test_failed(bt, t) && !bt.ctr[0].err_code && !bt.ctr[0].batch_failed) d.out_stats[c - 1] = v;
+        }
     }
     if (c == 0) bt.observed[t] = obs;
     ge = __syncthreads_count(ge);
@@ -984,6 +1010,7 @@ __global__ void __launch_bounds__(256) k_combine_count(const Batch bt) {
 
 void launch_combine(const Batch &b, cudaStream_t s) {
     if (b.ncols_total <= 0) return;
+    if (b.n_tests > 1) k_batch_status<<<1, 256, 0, s>>>(b);
     k_combine_stats<<<(unsigned)(b.ncols_total / 32), 256, 0, s>>>(b);
     k_combine_count<<<(unsigned)(b.ncols_total / 256), 256, 0, s>>>(b);
 }

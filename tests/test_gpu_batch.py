@@ -199,3 +199,38 @@ def test_page_locked_host_inputs(ctx):
     s1 = ctx.test(t["X"], t["Y"], B=t["B"], seed=t["seed"], stat=t["stat"], sigma=t["sigma"])
     s2 = ctx.test(pinned[1]["X"], pinned[1]["Y"], B=t["B"], seed=t["seed"], stat=t["stat"], sigma=t["sigma"])
     assert s1.observed == s2.observed and s1.n_ge == s2.n_ge
+
+
+def test_device_outputs_untouched_on_error(ctx):
+    # "on an error the outputs are left unwritten": a single test and a batched call
+    # with NaN in one test leave every caller-owned device buffer as it was
+    import ctypes
+    torch = pytest.importorskip("torch")
+    from paper_2406_06488_gb300 import ept
+    lib = ept.load()
+    good = [workloads.gaussian_pair(workloads.TwoSampleSpec(nx=60, ny=70, p=5, data_seed=k)) for k in range(3)]
+    X, Y = (a.copy() for a in good[1])
+    X[3, 2] = np.nan
+    dev = [(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()) for a, b in (good[0], (X, Y), good[2])]
+    bufs = [torch.full((40,), -7.0, dtype=torch.float64, device="cuda") for _ in dev]
+    stream = torch.cuda.current_stream().cuda_stream
+    r = ept._Result()
+    st = lib.ept_test(ctx._h, dev[1][0].data_ptr(), 60, dev[1][1].data_ptr(), 70, 5, 1, 0, 1.0, 40,
+                      ctypes.c_uint64(0), 1, bufs[1].data_ptr(), ctypes.byref(r), stream)
+    assert st == 1   # EPT_EINVAL
+    descs = (ept._TestDesc * 3)()
+    for k, (Xd, Yd) in enumerate(dev):
+        descs[k] = ept._TestDesc(Xd.data_ptr(), Yd.data_ptr(), 60, 70, 5, 0, 1.0, 40, k, bufs[k].data_ptr())
+    res = (ept._Result * 3)()
+    st = lib.ept_test_batch(ctx._h, descs, 3, 1, 1, res, stream)
+    assert st == 1
+    torch.cuda.synchronize()
+    for b in bufs:
+        assert torch.all(b == -7.0)
+    # the same batch without the NaN writes every buffer
+    dev[1] = (torch.from_numpy(good[1][0]).cuda(), torch.from_numpy(good[1][1]).cuda())
+    descs[1] = ept._TestDesc(dev[1][0].data_ptr(), dev[1][1].data_ptr(), 60, 70, 5, 0, 1.0, 40, 1, bufs[1].data_ptr())
+    assert lib.ept_test_batch(ctx._h, descs, 3, 1, 1, res, stream) == 0
+    torch.cuda.synchronize()
+    for b in bufs:
+        assert not torch.any(b == -7.0)
