@@ -54,3 +54,23 @@ def test_abi_version_and_errors_without_gpu(lib_path):
 def test_destroy_null_is_ok(lib_path):
     from paper_2406_06488_gb300 import ept
     assert ept.load().ept_destroy(None) == 0
+
+
+def test_host_side_argument_checks(lib_path):
+    # checks that run before any device call, so they hold on a machine without a GPU
+    from paper_2406_06488_gb300 import ept
+    lib = ept.load()
+    h = ctypes.c_void_p()
+    half = ept._Allocator(ept._ALLOC_FN(lambda n, s, u: None), ept._FREE_FN(), None)
+    assert lib.ept_create_ex(ctypes.byref(h), 0, 0, ctypes.byref(half)) == 1   # alloc without free: EPT_EINVAL
+    assert b"alloc and free" in lib.ept_last_error()
+    assert lib.ept_create_ex(None, 0, 0, None) == 1
+    assert lib.ept_set_option(None, 9, 1) == 1
+    r = ept._Result()
+    assert lib.ept_test(None, None, 1, None, 1, 1, 0, 0, 1.0, 1, ctypes.c_uint64(0), 1, None, ctypes.byref(r),
+                        None) == 1
+    # the pre-computation baseline: estimate = the full n x n matrix and the rest
+    n = 3000
+    est = ept.estimate_bytes(1500, 1500, 64, 200, prec="pooled_fp32")
+    assert est >= ((n + 255) // 256 * 256) ** 2 * 4
+    assert ept.estimate_bytes(1500, 1500, 64, 200, prec=7) == 0
