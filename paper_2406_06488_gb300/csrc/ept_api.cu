@@ -479,6 +479,7 @@ struct ept_ctx {
     Server *server = nullptr;           // serving scheduler, started by the first ept_submit
     int device = 0;
     int num_sms = 0;
+    size_t total_mem = 0;               // the device's memory (cudaDeviceProp::totalGlobalMem)
     size_t budget = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t side = nullptr;        // relabeling draws run here, beside the block build
@@ -1179,13 +1180,16 @@ size_t available_bytes(ept_ctx *c) {
     return have > margin ? have - margin : 0;
 }
 
-// whether a single test runs in the streaming mode
+// whether a single test runs in the streaming mode.  The free memory is asked of
+// the driver only for tests near the device's size: the query costs tens of
+// microseconds, and most tests need a small fraction of the memory.
 bool use_stream(ept_ctx *c, const TestSpec &s, int prec) {
     if (c->stream_blocks < 0) return false;
     if (c->stream_blocks > 0) return true;
     if (prec != EPT_PREC_SPLIT_BF16 || (s.stat != EPT_STAT_ED && s.sigma == EPT_SIGMA_MEDIAN)) return false;
     const size_t need = resident_bytes(s, prec);
-    if (need <= c->arena_cap) return false;   // the arena already holds it
+    if (c->budget) return need > c->budget;
+    if (need <= c->arena_cap || need <= c->total_mem / 4) return false;
     return need > available_bytes(c);
 }
 
@@ -1958,6 +1962,7 @@ ept_status ept_create_ex(ept_ctx **out, int device, size_t mem_budget_bytes, con
     if (!c) return fail(EPT_ENOMEM, "host allocation failed");
     c->device = device;
     c->num_sms = prop.multiProcessorCount;
+    c->total_mem = prop.totalGlobalMem;
     c->budget = mem_budget_bytes;
     if (alloc) c->alloc = *alloc;
     const char *at = getenv("EPT_AUTOTUNE");
