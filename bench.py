@@ -39,7 +39,10 @@ BATCH_KERNELS_PER_STEP = 12  # ept_test_batch: the same and the batch's error st
 # dram read + write bytes of one k_contract_tc launch on the highdim workload, from the ncu
 # capture summarised in profiles/k_contract_tc_highdim_ed.md (to be reset to {} whenever the
 # kernel changes, until it is captured again)
-CONTRACT_TRAFFIC = {"highdim": 60.73e6}
+CONTRACT_TRAFFIC = {"highdim": 60.73e6, "mmd": 947.8e6, "mmd_laplace": 947.8e6, "mmd_median": 947.8e6}
+# streaming mode: DRAM bytes per stored block of the contraction, from the n = 60,000 capture summarised in
+# profiles/k_contract_tc_stream_60k.md (scaled to a launch by its window's blocks)
+STREAM_TRAFFIC_PER_BLOCK = 8656e6 / 110920
 
 
 def _args():
@@ -761,6 +764,8 @@ def run_stream(args):
     alg_flops = 2.0 * (n * (n + 1) // 2) * (spec.B + 1)
     t_contract = statistics.mean(x.ms_contract for x in results) / 1000.0
     nwin = last.n_windows
+    npan = (n + 255) // 256
+    nblk = npan * (4 * npan) - 2 * npan * (npan - 1)   # stored blocks of 256 x 64 entries
     achieved = alg_flops / t_contract / 1e12 if t_contract > 0 else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": steps, "warmup": args.warmup,
@@ -779,7 +784,10 @@ def run_stream(args):
                      "masks": statistics.mean(x.ms_masks for x in results),
                      "contract_all_windows": t_contract * 1000.0},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak if achieved else None, "traffic": None, "kernel": "k_contract_tc",
+                     "frac": achieved / peak if achieved else None,
+                     "traffic": STREAM_TRAFFIC_PER_BLOCK * nblk / max(nwin, 1),
+                     "traffic_note": "scaled from an ncu capture of the same path at n = 60,000 by stored blocks",
+                     "kernel": "k_contract_tc",
                      "peak_kind": "%s bf16 dense sustained (seconds-long step)" % peak_kind,
                      "algorithmic_flops_per_test": alg_flops, "launches_per_test": nwin},
         "e2e": {"value": spec.B * ws / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(n * spec.p * 4),
