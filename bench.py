@@ -62,7 +62,8 @@ def _args():
     ap.add_argument("--stream-rows", type=int, default=0,
                     help="stream: pooled rows of the test (0: the 400,000-row workload)")
     ap.add_argument("--stream-blocks", type=int, default=0,
-                    help="stream: windows of at most this many stored blocks (0: sized to free memory)")
+                    help="stream: windows of at most this many stored blocks (0: sized to free memory, "
+                         "-1: resident)")
     ap.add_argument("--plain-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -719,8 +720,8 @@ def run_stream(args):
     steps = min(args.steps, 5)
     X, Y = workloads.gaussian_pair(spec)
     ctx = ept.Context(local)
-    if args.stream_blocks > 0:
-        ctx.set_option("stream_blocks", args.stream_blocks)
+    if args.stream_blocks != 0:
+        ctx.set_option("stream_blocks", args.stream_blocks)   # -1: resident (for comparisons)
     Xd = torch.from_numpy(X).cuda()
     Yd = torch.from_numpy(Y).cuda()
     stream = torch.cuda.current_stream()
