@@ -95,3 +95,11 @@ def test_pooled_unsupported(ctx, ept_mod):
     assert e.value.status == 8
     ref = oracle.permutation_test(X, Y, B=10, seed=0, stat="ed")
     _check(ctx.test(X, Y, B=10, prec="pooled_fp32"), ref["stats"], ref["observed"], 10)
+
+
+def test_pooled_zero_permutations(ctx):
+    X, Y = _pair(300, 200, 6, seed=14)
+    res = ctx.test(X, Y, B=0, seed=0, prec="pooled_fp32")
+    assert res.p_value == 1.0 and res.n_ge == 0
+    ref = oracle.stat_direct(X, Y, "ed")
+    assert abs(res.observed - ref) <= REL_TOL * ref

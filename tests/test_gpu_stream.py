@@ -180,3 +180,11 @@ def test_stream_large_n_sampled(ept_mod):
     S, tr = oracle.pooled_moments(X, Y, "ed", 1.0)
     mean_ref = oracle.permutation_mean(S, tr, spec.nx, spec.ny, "ed")
     assert abs(st.mean() - mean_ref) <= 5 * st.std() / np.sqrt(spec.B)
+
+
+def test_stream_zero_permutations(ctx):
+    X, Y = _pair(300, 200, 6, seed=14)
+    res = ctx.test(X, Y, B=0, seed=0)
+    assert res.p_value == 1.0 and res.n_ge == 0 and res.n_windows == 2
+    ref = oracle.stat_direct(X, Y, "ed")
+    assert abs(res.observed - ref) <= REL_TOL * ref
