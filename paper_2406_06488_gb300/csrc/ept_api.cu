@@ -1204,7 +1204,7 @@ size_t available_bytes(ept_ctx *c) {
 }
 
 // whether a single test runs in the streaming mode.  The free memory is asked of
-// the driver only for tests near the device's size: the query costs tens of
+// the CUDA driver only for tests near the device's size: the query costs tens of
 // microseconds, and most tests need a small fraction of the memory.
 bool use_stream(ept_ctx *c, const TestSpec &s, int prec) {
     if (c->stream_blocks < 0) return false;
