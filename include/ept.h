@@ -258,9 +258,18 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    not fit fails with EPT_ENOMEM).  Streaming with the plain precision or the
    median bandwidth gives EPT_EUNSUPPORTED.  The arithmetic is the resident path's;
    only the order in which the windows' FP64 partial sums are added differs.
+   EPT_OPT_WAIT_LIMIT_MS (default 2000, 10..600000): the limit of every bounded wait
+   inside the tensor-core kernels (a pipeline barrier or flag that does not arrive
+   within it makes the kernel record an error, drain and return; the call returns
+   EPT_ETIMEOUT).
    EPT_OPT_SERVE_LANES (default 3, 1..16): serving batches in flight at once;
    EPT_OPT_SERVE_SLOTS (default 256): serving requests in flight at once; both
-   before the first ept_submit.  EPT_EINVAL for an unknown option or value. */
+   before the first ept_submit.  EPT_EINVAL for an unknown option or value.
+   Environment: EPT_GRAPHS, EPT_AUTOTUNE, EPT_DRAW_MODE, EPT_DEBUG_CHECKS,
+   EPT_STREAM_BLOCKS, EPT_WAIT_LIMIT_MS, EPT_SERVE_LANES and EPT_SERVE_SLOTS set the
+   starting value of the option of that name in every new context (an invalid value
+   makes ept_create fail with EPT_EINVAL); EPT_AUTOTUNE_CACHE names a file in which
+   the autotuner keeps its choices across processes. */
 enum {
     EPT_OPT_GRAPHS = 1,
     EPT_OPT_AUTOTUNE = 2,
@@ -270,7 +279,8 @@ enum {
     EPT_OPT_FAULT_INJECT_ALLOC = 6,
     EPT_OPT_FAULT_INJECT_STALL = 7,
     EPT_OPT_DEBUG_CHECKS = 8,
-    EPT_OPT_STREAM_BLOCKS = 9
+    EPT_OPT_STREAM_BLOCKS = 9,
+    EPT_OPT_WAIT_LIMIT_MS = 10
 };
 ept_status ept_set_option(ept_ctx *ctx, int option, int64_t value);
 

@@ -520,6 +520,7 @@ struct ept_ctx {
     bool debug = false;                 // guard bands around scratch regions, plan invariants checked
     int draw_mode = 0;                  // relabeling draws: 0 automatic, DRAW_WARPS, DRAW_LANES
     int64_t stream_blocks = 0;          // streaming mode: 0 automatic, k > 0 windows of <= k blocks, -1 never
+    unsigned long long wait_ns = 0;     // limit of the kernels' bounded waits (0: their default, 2 s)
     ept_allocator alloc{};              // caller-supplied device memory (alloc.alloc == nullptr: cudaMalloc)
     std::atomic<int> inject_alloc{0};   // test hook: the next N scratch acquisitions fail (host side)
     bool inject_stall = false;          // test hook: the next run's contraction waits out its limit
@@ -808,6 +809,7 @@ Batch device_view(ept_ctx *c, const Plan &P) {
     b.sel_hist = P.any_median ? (uint32_t *)(A + P.off_sel_hist) : nullptr;
     b.sacc = nullptr;
     b.inject_stall = c->inject_stall ? 1 : 0;
+    b.wait_ns = c->wait_ns;
     return b;
 }
 
@@ -1403,6 +1405,7 @@ Batch stream_view(ept_ctx *c, const Plan &P, int g) {
     b.ctr = (Counters *)(A + P.off_ctr);
     b.sacc = (double *)(A + P.off_sacc);
     b.inject_stall = (g == 0 && c->inject_stall) ? 1 : 0;
+    b.wait_ns = c->wait_ns;
     return b;
 }
 
@@ -1999,8 +2002,7 @@ ept_status ept_create_ex(ept_ctx **out, int device, size_t mem_budget_bytes, con
     c->total_mem = prop.totalGlobalMem;
     c->budget = mem_budget_bytes;
     if (alloc) c->alloc = *alloc;
-    const char *at = getenv("EPT_AUTOTUNE");
-    c->autotune = !(at && at[0] == '0');
+    c->autotune = true;
     const char *tf = getenv("EPT_AUTOTUNE_CACHE");
     if (tf) c->tune_file = tf;
     load_tune_file(c);
@@ -2015,6 +2017,26 @@ ept_status ept_create_ex(ept_ctx **out, int device, size_t mem_budget_bytes, con
     if (e != cudaSuccess) {
         ept_destroy(c);
         return fail(EPT_ECUDA, "stream/event creation failed: %s", cudaGetErrorString(e));
+    }
+    // EPT_<OPTION> environment variables give the options' starting values
+    static const struct {
+        const char *env;
+        int option;
+    } env_opts[] = {{"EPT_GRAPHS", EPT_OPT_GRAPHS},           {"EPT_AUTOTUNE", EPT_OPT_AUTOTUNE},
+                    {"EPT_DRAW_MODE", EPT_OPT_DRAW_MODE},     {"EPT_DEBUG_CHECKS", EPT_OPT_DEBUG_CHECKS},
+                    {"EPT_STREAM_BLOCKS", EPT_OPT_STREAM_BLOCKS}, {"EPT_WAIT_LIMIT_MS", EPT_OPT_WAIT_LIMIT_MS},
+                    {"EPT_SERVE_LANES", EPT_OPT_SERVE_LANES}, {"EPT_SERVE_SLOTS", EPT_OPT_SERVE_SLOTS}};
+    for (const auto &eo : env_opts) {
+        const char *v = getenv(eo.env);
+        if (!v || !*v) continue;
+        char *end = nullptr;
+        const long long x = strtoll(v, &end, 10);
+        if (end == v || *end || ept_set_option(c, eo.option, (int64_t)x) != EPT_OK) {
+            const std::string msg = g_err;
+            ept_destroy(c);
+            return fail(EPT_EINVAL, "environment %s=%s: %s", eo.env, v,
+                        end == v || *end ? "not an integer" : msg.c_str());
+        }
     }
     *out = c;
     return EPT_OK;
@@ -2243,6 +2265,12 @@ ept_status ept_set_option(ept_ctx *c, int option, int64_t value) {
     case EPT_OPT_STREAM_BLOCKS:
         if (value < -1) return fail(EPT_EINVAL, "stream blocks must be -1, 0 or a block count");
         c->stream_blocks = value;
+        return EPT_OK;
+    case EPT_OPT_WAIT_LIMIT_MS:
+        if (value < 10 || value > 600000) return fail(EPT_EINVAL, "the wait limit must be in [10, 600000] ms");
+        c->wait_ns = (unsigned long long)value * 1000000ull;
+        c->plan_key.clear();   // a captured graph holds the previous limit
+        drop_graph(c);
         return EPT_OK;
     case EPT_OPT_SERVE_LANES:
     case EPT_OPT_SERVE_SLOTS:

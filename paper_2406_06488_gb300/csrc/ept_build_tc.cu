@@ -173,6 +173,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_build_tc(const __grid_constant__ CUtensorMap tm_ah, const __grid_constant__ CUtensorMap tm_al,
                const __grid_constant__ CUtensorMap tm_bh, const __grid_constant__ CUtensorMap tm_bl, const Batch bt) {
     Counters *ctr = bt.ctr;   // bounded-wait errors are recorded in test 0's counters
+    const unsigned long long wait_ns = bt.wait_ns ? bt.wait_ns : WAIT_NS;   // limit of every bounded wait
     const int ntiles = (int)bt.ntiles;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -218,7 +219,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const int rowB = (int)row0 + tile.J * PANEL;
                 const int kblocks = bt.desc[tile.t].kblocks;
                 for (int kk = 0; kk < kblocks; ++kk) {
-                    if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_TMA)) {
+                    if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_TMA, wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     if (armed[s2] < 0) continue;
                     const unsigned long long t0 = gtimer();
                     while (!mbar_try(su32(&bars->full[s2]), (uint32_t)armed[s2])) {
-                        if (gtimer() - t0 > WAIT_NS) {
+                        if (gtimer() - t0 > wait_ns) {
                             atomicCAS(&ctr->err_code, 0ull, ERR_DRAIN);
                             break;
                         }
@@ -256,14 +257,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 const int kblocks = bt.desc[bt.tiles[t].t].kblocks;
-                if (!mbar_wait(su32(&bars->acc_empty[acc]), acc_phase ^ 1u, abort_flag, ctr, ERR_WAIT_MMA)) {
+                if (!mbar_wait(su32(&bars->acc_empty[acc]), acc_phase ^ 1u, abort_flag, ctr, ERR_WAIT_MMA, wait_ns)) {
                     ok = false;
                     break;
                 }
                 fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(acc * BN);
                 for (int kk = 0; kk < kblocks; ++kk) {
-                    if (!mbar_wait(su32(&bars->full[stage]), phase, abort_flag, ctr, ERR_WAIT_MMA)) {
+                    if (!mbar_wait(su32(&bars->full[stage]), phase, abort_flag, ctr, ERR_WAIT_MMA, wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             mma_commit(su32(&bars->drain));
             const unsigned long long t0 = gtimer();
             while (!mbar_try(su32(&bars->drain), 0)) {
-                if (gtimer() - t0 > WAIT_NS) {
+                if (gtimer() - t0 > wait_ns) {
                     atomicCAS(&ctr->err_code, 0ull, ERR_DRAIN);
                     break;
                 }
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 colv[c] = (j < n) ? make_float2(norms[j], inv_scale[j]) : make_float2(0.f, 0.f);
             }
             __syncwarp();
-            if (!mbar_wait(su32(&bars->acc_full[acc]), acc_phase, abort_flag, ctr, ERR_WAIT_EPI)) break;
+            if (!mbar_wait(su32(&bars->acc_full[acc]), acc_phase, abort_flag, ctr, ERR_WAIT_EPI, wait_ns)) break;
             fence_after();
             const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * BN);
 #pragma unroll 1

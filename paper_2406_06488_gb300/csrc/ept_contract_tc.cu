@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_contract_tc(const __grid_constant__ CUtensorMap tmap_hi, const __grid_constant__ CUtensorMap tmap_lo,
                   const Batch bt) {
     Counters *ctr = bt.ctr;   // bounded-wait errors are recorded in test 0's counters
+    const unsigned long long wait_ns = bt.wait_ns ? bt.wait_ns : WAIT_NS;   // limit of every bounded wait
     const int64_t nunits = bt.nunits_total;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const Chunk ch = x.ch;
                 const int row = (int)x.h * TC_M;
                 for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
-                    if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_TMA)) {
+                    if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_TMA, wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                     if (armed[s2] < 0) continue;
                     const unsigned long long t0 = gtimer();
                     while (!mbar_try(su32(&bars->a_full[s2]), (uint32_t)armed[s2])) {
-                        if (gtimer() - t0 > WAIT_NS) {
+                        if (gtimer() - t0 > wait_ns) {
                             atomicCAS(&ctr->err_code, 0ull, ERR_DRAIN);
                             break;
                         }
@@ -218,13 +219,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             bool ok = true;
             // failure-path test hook: wait (bounded) on a flag that nothing sets; the
             // expiry takes the same abort path as any other expired wait
-            if (bt.inject_stall && !flag_wait(&ctr->never_set, abort_flag, ctr, ERR_INJECTED)) ok = false;
+            if (bt.inject_stall && !flag_wait(&ctr->never_set, abort_flag, ctr, ERR_INJECTED, wait_ns)) ok = false;
             for (int64_t k = k_first; k < k_end && ok; k += k_step) {
                 const int64_t u = unit_at(k);
                 const Unit x = decode_unit(bt, u);
                 const Chunk ch = x.ch;
                 const uint32_t idesc = (x.ncols == TC_N) ? IDESC : idesc_f16_f32(TC_M, x.ncols);
-                if (!mbar_wait(su32(&bars->acc_empty[acc]), acc_phase ^ 1u, abort_flag, ctr, ERR_WAIT_MMA)) {
+                if (!mbar_wait(su32(&bars->acc_empty[acc]), acc_phase ^ 1u, abort_flag, ctr, ERR_WAIT_MMA, wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -232,8 +233,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 const uint32_t d_tmem = tmem_base + (uint32_t)(acc * TC_N);
                 bool first = true;
                 for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
-                    if (!mbar_wait(su32(&bars->a_full[stage]), phase, abort_flag, ctr, ERR_WAIT_MMA) ||
-                        !mbar_wait(su32(&bars->b_full[stage]), phase, abort_flag, ctr, ERR_WAIT_MMA)) {
+                    if (!mbar_wait(su32(&bars->a_full[stage]), phase, abort_flag, ctr, ERR_WAIT_MMA, wait_ns) ||
+                        !mbar_wait(su32(&bars->b_full[stage]), phase, abort_flag, ctr, ERR_WAIT_MMA, wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             mma_commit(su32(&bars->drain));
             unsigned long long t0 = gtimer();
             while (!mbar_try(su32(&bars->drain), 0)) {
-                if (gtimer() - t0 > WAIT_NS) {
+                if (gtimer() - t0 > wait_ns) {
                     atomicCAS(&ctr->err_code, 0ull, ERR_DRAIN);
                     break;
                 }
@@ -290,7 +291,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             uint32_t words[4];
 #pragma unroll
             for (int g = 0; g < 4; ++g) words[g] = wrow[g * 32 + lane];
-            if (!mbar_wait(su32(&bars->acc_full[acc]), acc_phase, abort_flag, ctr, ERR_WAIT_EPI)) break;
+            if (!mbar_wait(su32(&bars->acc_full[acc]), acc_phase, abort_flag, ctr, ERR_WAIT_EPI, wait_ns)) break;
             fence_after();
             const uint32_t tbase =
                 tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * TC_N) + (uint32_t)(g0 * 32);
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             mbar_arrive(su32(&bars->acc_empty[acc]));
             // the four row quarters' sums, added in a fixed order
             mbar_arrive(su32(&bars->red));
-            if (!mbar_wait(su32(&bars->red), red_phase, abort_flag, ctr, ERR_WAIT_EPI)) break;
+            if (!mbar_wait(su32(&bars->red), red_phase, abort_flag, ctr, ERR_WAIT_EPI, wait_ns)) break;
             const float *rb = red + rbuf * 4 * TC_N;
             float *out = bt.partial + x.part0 + (2 * x.q + x.h) * Bp + x.m * TC_N;
             out[et] = (rb[et] + rb[TC_N + et]) + (rb[2 * TC_N + et] + rb[3 * TC_N + et]);
@@ -363,7 +364,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
                 uint2 nn = make_uint2(0, 0);
                 if (kb + 2 < ch.kb1) load2(kb + 2, nn);
-                if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_MASK)) {
+                if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_MASK, wait_ns)) {
                     ok = false;
                     break;
                 }

@@ -161,6 +161,7 @@ struct Batch {
     double *sacc;                        // streaming mode: FP64 sums of the windows' partials (Bp)
     int inject_stall;                    // failure-path test hook: the contraction's MMA issuer waits on a
                                          //   flag that nothing sets until its bounded wait expires
+    unsigned long long wait_ns;          // limit of the tensor-core kernels' bounded waits (0: 2 s)
 };
 
 // tensor-core contraction work units of a test: chunk x relabeling tile x row half

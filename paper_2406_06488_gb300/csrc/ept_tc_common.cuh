@@ -13,7 +13,7 @@ namespace tc {
 
 // every mbarrier wait gives up after this long (then the kernel records an error
 // code, raises its CTA abort flag, drains its own asynchronous work and returns)
-constexpr unsigned long long WAIT_NS = 2000000000ull;
+constexpr unsigned long long WAIT_NS = 2000000000ull;   // default limit of a bounded wait (Batch::wait_ns)
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -50,7 +50,7 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
 // Bounded wait: true when the phase completed; false when the CTA is aborting or
 // the wait expired (then the abort flag is raised and the error recorded).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
-                                          Counters *ctr, unsigned long long code) {
+                                          Counters *ctr, unsigned long long code, unsigned long long limit) {
     unsigned long long t0 = 0;
     for (uint32_t it = 0;; ++it) {
         if (mbar_try(bar, parity)) return true;
@@ -59,7 +59,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
             const unsigned long long now = gtimer();
             if (t0 == 0) {
                 t0 = now;
-            } else if (now - t0 > WAIT_NS) {
+            } else if (now - t0 > limit) {
                 *abort_flag = 1;
                 atomicCAS(&ctr->err_code, 0ull, code);
                 return false;
@@ -71,12 +71,12 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 // Bounded wait on a device word becoming non-zero (the same limit and abort
 // protocol as mbar_wait).
 __device__ __forceinline__ bool flag_wait(const volatile unsigned int *flag, volatile int *abort_flag, Counters *ctr,
-                                          unsigned long long code) {
+                                          unsigned long long code, unsigned long long limit) {
     const unsigned long long t0 = gtimer();
     for (;;) {
         if (*flag) return true;
         if (*abort_flag) return false;
-        if (gtimer() - t0 > WAIT_NS) {
+        if (gtimer() - t0 > limit) {
             *abort_flag = 1;
             atomicCAS(&ctr->err_code, 0ull, code);
             return false;

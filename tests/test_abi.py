@@ -74,3 +74,12 @@ def test_host_side_argument_checks(lib_path):
     est = ept.estimate_bytes(1500, 1500, 64, 200, prec="pooled_fp32")
     assert est >= ((n + 255) // 256 * 256) ** 2 * 4
     assert ept.estimate_bytes(1500, 1500, 64, 200, prec=7) == 0
+
+
+def test_environment_options_are_checked(lib_path, monkeypatch):
+    # EPT_<OPTION> values are parsed at ept_create; without a GPU the call fails earlier
+    # (no device), so here only the library's acceptance of the names is exercised
+    from paper_2406_06488_gb300 import ept
+    monkeypatch.setenv("EPT_WAIT_LIMIT_MS", "250")
+    h = ctypes.c_void_p()
+    assert ept.load().ept_create(ctypes.byref(h), 0, 0) != 0   # no device here

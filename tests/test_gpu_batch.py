@@ -234,3 +234,19 @@ def test_device_outputs_untouched_on_error(ctx):
     torch.cuda.synchronize()
     for b in bufs:
         assert not torch.any(b == -7.0)
+
+
+def test_environment_sets_option_defaults(monkeypatch):
+    from paper_2406_06488_gb300 import ept
+    monkeypatch.setenv("EPT_DRAW_MODE", "7")
+    with pytest.raises(ept.EptError) as e:
+        ept.Context(0)
+    assert e.value.status == 1 and "EPT_DRAW_MODE" in str(e.value)
+    monkeypatch.setenv("EPT_DRAW_MODE", "2")
+    monkeypatch.setenv("EPT_STREAM_BLOCKS", "1")
+    X, Y = workloads.gaussian_pair(workloads.TwoSampleSpec(nx=300, ny=250, p=7, y_mean=0.1, data_seed=5))
+    with ept.Context(0) as c:
+        r = c.test(X, Y, B=300, seed=1)
+    assert r.n_windows == 3   # streamed, one panel per window, by the environment
+    ref = oracle.permutation_test(X, Y, B=300, seed=1, stat="ed")
+    assert np.max(np.abs(np.asarray(r.stats) - ref["stats"]) / np.abs(ref["stats"])) <= REL_TOL

@@ -271,6 +271,29 @@ def test_expired_device_wait_returns_timeout_and_context_recovers(ctx):
     _check(res, ref["stats"], ref["observed"], 500)
 
 
+def test_wait_limit_option(ctx):
+    # the limit of the bounded waits is a context option: with 100 ms the stalled
+    # contraction gives up well before the 2 s default; out-of-range limits are refused
+    import time
+    from paper_2406_06488_gb300 import ept
+    X, Y = _pair(150, 170, 6, seed=43)
+    with pytest.raises(ept.EptError):
+        ctx.set_option("wait_limit_ms", 5)
+    try:
+        ctx.set_option("wait_limit_ms", 100)
+        ctx.test(X, Y, B=200, seed=3)   # a normal run with the short limit
+        ctx.set_option("fault_inject_stall", 1)
+        t0 = time.perf_counter()
+        with pytest.raises(ept.EptError) as e:
+            ctx.test(X, Y, B=200, seed=3)
+        assert e.value.status == 5
+        assert time.perf_counter() - t0 < 1.5
+    finally:
+        ctx.set_option("wait_limit_ms", 2000)
+    ref = oracle.permutation_test(X, Y, B=200, seed=3, stat="ed")
+    _check(ctx.test(X, Y, B=200, seed=3), ref["stats"], ref["observed"], 200)
+
+
 def test_large_n_sampled(ctx):
     # n = 60000 pooled rows (7.2 GB of packed blocks): sampled draws against the
     # oracle's direct recomputation, and the closed-form permutation mean
