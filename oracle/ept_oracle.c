@@ -47,7 +47,7 @@
 #define EO_STAT_MMD_LAPLACE 2  /* Laplacian kernel */
 
 /* Test-only mutation switch.  The default build (EO_MUTANT undefined or 0) is the
- * oracle.  The pin tests compile copies with EO_MUTANT = 1..7, each planting one
+ * oracle.  The pin tests compile copies with EO_MUTANT = 1..8, each planting one
  * plausible mistake, and check that at least one pin fails for every mutant. */
 #ifndef EO_MUTANT
 #define EO_MUTANT 0
