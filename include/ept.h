@@ -262,11 +262,18 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    inside the tensor-core kernels (a pipeline barrier or flag that does not arrive
    within it makes the kernel record an error, drain and return; the call returns
    EPT_ETIMEOUT).
+   EPT_OPT_MAX_CHUNK (default 8; 8, 16 or 32): the longest contraction work unit, in
+   K-blocks of 64 pooled columns.  The tensor cores accumulate each unit in FP32, and
+   the error grows with the unit's length: 8 keeps the statistics within 1e-5 of the
+   FP64 oracle even when the permuted statistics are far smaller than the spread of
+   the pooled matrix's entries (a wide-kernel MMD on strongly separated samples, for
+   instance); 16 or 32 let the autotuner pick longer units, about 12 % faster on large
+   tests, with about three times the error in that case.
    EPT_OPT_SERVE_LANES (default 3, 1..16): serving batches in flight at once;
    EPT_OPT_SERVE_SLOTS (default 256): serving requests in flight at once; both
    before the first ept_submit.  EPT_EINVAL for an unknown option or value.
    Environment: EPT_GRAPHS, EPT_AUTOTUNE, EPT_DRAW_MODE, EPT_DEBUG_CHECKS,
-   EPT_STREAM_BLOCKS, EPT_WAIT_LIMIT_MS, EPT_SERVE_LANES and EPT_SERVE_SLOTS set the
+   EPT_STREAM_BLOCKS, EPT_WAIT_LIMIT_MS, EPT_MAX_CHUNK, EPT_SERVE_LANES and EPT_SERVE_SLOTS set the
    starting value of the option of that name in every new context (an invalid value
    makes ept_create fail with EPT_EINVAL); EPT_AUTOTUNE_CACHE names a file in which
    the autotuner keeps its choices across processes. */
@@ -280,7 +287,8 @@ enum {
     EPT_OPT_FAULT_INJECT_STALL = 7,
     EPT_OPT_DEBUG_CHECKS = 8,
     EPT_OPT_STREAM_BLOCKS = 9,
-    EPT_OPT_WAIT_LIMIT_MS = 10
+    EPT_OPT_WAIT_LIMIT_MS = 10,
+    EPT_OPT_MAX_CHUNK = 11
 };
 ept_status ept_set_option(ept_ctx *ctx, int option, int64_t value);
 

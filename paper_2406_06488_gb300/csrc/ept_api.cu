@@ -521,6 +521,7 @@ struct ept_ctx {
     int draw_mode = 0;                  // relabeling draws: 0 automatic, DRAW_WARPS, DRAW_LANES
     int64_t stream_blocks = 0;          // streaming mode: 0 automatic, k > 0 windows of <= k blocks, -1 never
     unsigned long long wait_ns = 0;     // limit of the kernels' bounded waits (0: their default, 2 s)
+    int max_chunk = CHUNK_KB_DEFAULT;   // longest contraction unit the autotuner may pick (precision)
     ept_allocator alloc{};              // caller-supplied device memory (alloc.alloc == nullptr: cudaMalloc)
     std::atomic<int> inject_alloc{0};   // test hook: the next N scratch acquisitions fail (host side)
     bool inject_stall = false;          // test hook: the next run's contraction waits out its limit
@@ -1010,9 +1011,11 @@ std::vector<int64_t> shape_key(const std::vector<TestSpec> &specs, int prec, boo
 }
 
 // key of the autotuner: the batch's padded shapes (what the unit decomposition sees)
-std::vector<int64_t> tune_key(const std::vector<TestSpec> &specs, int prec) {
+// and the longest unit allowed
+std::vector<int64_t> tune_key(const std::vector<TestSpec> &specs, int prec, int max_chunk) {
     std::vector<int64_t> k;
     k.push_back(prec);
+    k.push_back(max_chunk);
     for (const TestSpec &s : specs) {
         k.push_back((s.nx + s.ny + PANEL - 1) / PANEL);
         k.push_back((s.B + 1 + COL_PAD - 1) / COL_PAD);
@@ -1143,13 +1146,17 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
 // is the one chosen.
 ept_status run_tuned(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bool on_device, bool use_graph,
                      ept_result *out, void *stream) {
-    if (!c->autotune) return run_once(c, specs, prec, on_device, CHUNK_KB_DEFAULT, use_graph, out, stream, nullptr);
-    const std::vector<int64_t> key = tune_key(specs, prec);
+    // candidates up to the precision limit (one candidate: nothing to tune)
+    int ncand = 0;
+    while (ncand < 3 && CHUNK_CANDIDATES[ncand] <= c->max_chunk) ++ncand;
+    if (!c->autotune || ncand <= 1)
+        return run_once(c, specs, prec, on_device, CHUNK_KB_DEFAULT, use_graph, out, stream, nullptr);
+    const std::vector<int64_t> key = tune_key(specs, prec, c->max_chunk);
     auto it = c->tuned_chunk.find(key);
     if (it != c->tuned_chunk.end()) return run_once(c, specs, prec, on_device, it->second, use_graph, out, stream, nullptr);
     int best = CHUNK_KB_DEFAULT;
     float best_ms = 1e30f;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < ncand; ++k) {
         float ms = 0.f;
         ept_status st = run_once(c, specs, prec, on_device, CHUNK_CANDIDATES[k], false, out, stream, &ms);
         if (st != EPT_OK) return st;
@@ -2025,6 +2032,7 @@ ept_status ept_create_ex(ept_ctx **out, int device, size_t mem_budget_bytes, con
     } env_opts[] = {{"EPT_GRAPHS", EPT_OPT_GRAPHS},           {"EPT_AUTOTUNE", EPT_OPT_AUTOTUNE},
                     {"EPT_DRAW_MODE", EPT_OPT_DRAW_MODE},     {"EPT_DEBUG_CHECKS", EPT_OPT_DEBUG_CHECKS},
                     {"EPT_STREAM_BLOCKS", EPT_OPT_STREAM_BLOCKS}, {"EPT_WAIT_LIMIT_MS", EPT_OPT_WAIT_LIMIT_MS},
+                    {"EPT_MAX_CHUNK", EPT_OPT_MAX_CHUNK},
                     {"EPT_SERVE_LANES", EPT_OPT_SERVE_LANES}, {"EPT_SERVE_SLOTS", EPT_OPT_SERVE_SLOTS}};
     for (const auto &eo : env_opts) {
         const char *v = getenv(eo.env);
@@ -2265,6 +2273,10 @@ ept_status ept_set_option(ept_ctx *c, int option, int64_t value) {
     case EPT_OPT_STREAM_BLOCKS:
         if (value < -1) return fail(EPT_EINVAL, "stream blocks must be -1, 0 or a block count");
         c->stream_blocks = value;
+        return EPT_OK;
+    case EPT_OPT_MAX_CHUNK:
+        if (value != 8 && value != 16 && value != 32) return fail(EPT_EINVAL, "the longest unit must be 8, 16 or 32");
+        c->max_chunk = (int)value;
         return EPT_OK;
     case EPT_OPT_WAIT_LIMIT_MS:
         if (value < 10 || value > 600000) return fail(EPT_EINVAL, "the wait limit must be in [10, 600000] ms");

@@ -300,12 +300,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             for (int g = 0; g < 4; ++g) {
                 uint32_t v[32];
                 tmem_ld32(tbase + (uint32_t)(g * 32), v);
-                // bit e of `mine` = s_{b_e}[row of this lane], b_e = relabeling 32 (g0 + g) + e
-                uint32_t mine = 0;
+                // bit e of `mine` = s_{b_e}[row of this lane], b_e = relabeling 32 (g0 + g) + e:
+                // the 32 x 32 bit matrix (lane = relabeling, bit = row) transposed in five
+                // butterfly stages, each swapping the off-diagonal halves of 2j x 2j blocks
+                uint32_t mine = words[g];
 #pragma unroll
-                for (int l = 0; l < 32; ++l) {
-                    const uint32_t col = __ballot_sync(0xFFFFFFFFu, (words[g] >> l) & 1u);
-                    mine = (lane == l) ? col : mine;
+                for (int j = 16; j >= 1; j >>= 1) {
+                    const uint32_t m = j == 16 ? 0x0000FFFFu
+                                     : j == 8  ? 0x00FF00FFu
+                                     : j == 4  ? 0x0F0F0F0Fu
+                                     : j == 2  ? 0x33333333u
+                                               : 0x55555555u;
+                    const uint32_t y = __shfl_xor_sync(0xFFFFFFFFu, mine, j);
+                    mine = (lane & j) ? ((mine & ~m) | ((y & ~m) >> j)) : ((mine & m) | ((y & m) << j));
                 }
                 float xv[32];
 #pragma unroll

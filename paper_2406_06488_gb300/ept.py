@@ -181,7 +181,7 @@ def estimate_bytes(nx: int, ny: int, p: int, B: int, prec="split_bf16") -> int:
 
 OPTION = {"graphs": 1, "autotune": 2, "serve_lanes": 3, "serve_slots": 4, "draw_mode": 5,
           "fault_inject_alloc": 6, "fault_inject_stall": 7, "debug_checks": 8, "stream_blocks": 9,
-          "wait_limit_ms": 10}
+          "wait_limit_ms": 10, "max_chunk": 11}
 
 
 class Context:
