@@ -250,3 +250,18 @@ def test_environment_sets_option_defaults(monkeypatch):
     assert r.n_windows == 3   # streamed, one panel per window, by the environment
     ref = oracle.permutation_test(X, Y, B=300, seed=1, stat="ed")
     assert np.max(np.abs(np.asarray(r.stats) - ref["stats"]) / np.abs(ref["stats"])) <= REL_TOL
+
+
+def test_max_chunk_option(ctx):
+    from paper_2406_06488_gb300 import ept
+    with pytest.raises(ept.EptError):
+        ctx.set_option("max_chunk", 12)
+    X, Y = workloads.gaussian_pair(workloads.TwoSampleSpec(nx=900, ny=1100, p=40, y_mean=0.05, data_seed=7))
+    ref = oracle.permutation_test(X, Y, B=600, seed=3, stat="ed")
+    try:
+        for mc in (32, 16, 8):
+            ctx.set_option("max_chunk", mc)
+            r = ctx.test(X, Y, B=600, seed=3)
+            assert _close(r.stats, ref["stats"])
+    finally:
+        ctx.set_option("max_chunk", 8)
