@@ -200,6 +200,51 @@ def _cpu_baseline(spec, X, Y, budget_s=20.0, sigma=None):
                       % (done, done, "%s nx=%d ny=%d p=%d" % (spec.stat.upper(), spec.nx, spec.ny, spec.p), dt)}, vals
 
 
+PAPER_METHOD_MAX_N = 8000   # per-thread buffers of n^2 doubles (0.5 GB at this n)
+
+
+def _cpu_paper_method(spec, X, Y, sigma=None, budget_s=15.0):
+    """The paper's efficient test itself on the host cores: the oracle's FP64 Algorithm 1
+    (three blocks built once, each relabeling assembled from them by the block swaps of
+    Algorithm 2).  The block build is timed alone (no relabelings), then a bounded
+    number of relabelings; the whole test of B relabelings is extrapolated from the two."""
+    import oracle
+    oracle.build()
+    n = spec.nx + spec.ny
+    if n > PAPER_METHOD_MAX_N:
+        return {"value": None, "unit": UNIT, "kind": "oracle Algorithm 1 (FP64)",
+                "sample": "not timed: n = %d needs %d MB of buffers per thread" % (n, 8 * n * n >> 20)}
+    sigma = _oracle_sigma(spec, sigma)
+    cores = oracle.num_threads()
+    # warm the thread pool on a tiny case before the timed calls
+    oracle.test_blocks(X[:8], Y[:8], oracle.perm_select(1, 8, 8, 1, 2 * cores), spec.stat, sigma)
+    t_build, spent = float("inf"), 0.0
+    while spent < 1.0:   # short builds: the least of a few
+        t0 = time.perf_counter()
+        oracle.test_blocks(X, Y, np.zeros((0, n), np.uint8), spec.stat, sigma)
+        dt = time.perf_counter() - t0
+        t_build, spent = min(t_build, dt), spent + dt
+    count = cores
+    while True:
+        sel = oracle.perm_select(spec.seed, spec.nx, spec.ny, 1, min(count, spec.B))
+        t0 = time.perf_counter()
+        oracle.test_blocks(X, Y, sel, spec.stat, sigma)
+        t = time.perf_counter() - t0
+        if t > budget_s / 4 or count >= spec.B:
+            break
+        count *= 4
+    if sel.shape[0] == spec.B:
+        return {"value": spec.B / t, "unit": UNIT, "cores": cores, "kind": "oracle Algorithm 1 (FP64)",
+                "build_s": t_build, "test_s": t,
+                "sample": "the whole test (block build and B = %d relabelings) timed once" % spec.B}
+    per_relabeling = max(t - t_build, 1e-9) / sel.shape[0]
+    test_s = t_build + spec.B * per_relabeling
+    return {"value": spec.B / test_s, "unit": UNIT, "cores": cores, "kind": "oracle Algorithm 1 (FP64)",
+            "build_s": t_build, "ms_per_relabeling": 1000.0 * per_relabeling, "test_s": test_s,
+            "sample": "block build timed alone, then %d relabelings (draws 1..%d) with the build; a whole test of "
+                      "B = %d extrapolated as build + B x per-relabeling time" % (sel.shape[0], sel.shape[0], spec.B)}
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -361,9 +406,10 @@ def run_ours(args):
     ncols = spec.B + 1
     cols = (ncols // 256) * 256 + ((ncols % 256 + 15) // 16 * 16 if ncols % 256 else 0)
     mma_flops = 2.0 * 2.0 * stored * cols
-    cpu = None
+    cpu = paper_cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu, _ = _cpu_baseline(spec, X, Y, sigma=last.sigma)
+        paper_cpu = _cpu_paper_method(spec, X, Y, sigma=last.sigma)
     sorted_ms = sorted(step_ms)
     p99 = sorted_ms[min(len(sorted_ms) - 1, int(np.ceil(0.99 * len(sorted_ms))) - 1)]
     psorted = sorted(plain_ms)
@@ -400,6 +446,8 @@ def run_ours(args):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if paper_cpu is not None:
+        line["cpu_paper_method"] = paper_cpu
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
@@ -504,9 +552,11 @@ def run_batched(args):
     t_contract = ph.ms_contract / 1000.0
     achieved = alg_flops / t_contract / 1e12
     peak = float(peaks.get("bf16_tflops", 1900.0))
-    cpu = None
+    cpu = paper_cpu = None
     if not args.no_cpu_baseline and ws == 1:
         cpu, _ = _cpu_baseline(specs[0], tests[0]["X"], tests[0]["Y"], budget_s=15.0)
+        paper_cpu = _cpu_paper_method(specs[0], tests[0]["X"], tests[0]["Y"], budget_s=10.0)
+        paper_cpu["sample"] = "first test of the batch: " + paper_cpu["sample"]
     in_bytes = sum((sp.nx + sp.ny) * sp.p * 4 for sp in specs)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -532,6 +582,8 @@ def run_batched(args):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if paper_cpu is not None:
+        line["cpu_paper_method"] = paper_cpu
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
