@@ -1144,17 +1144,21 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
 // by timing the contraction with each candidate on this very batch.  Each tuning
 // run is a complete, correct test, so the last one's results are returned when it
 // is the one chosen.
+// Contraction unit length (K-blocks) of a context's untuned runs: the default, or the
+// context's precision limit when that is shorter.
+int unit_kb(const ept_ctx *c) { return std::min(CHUNK_KB_DEFAULT, c->max_chunk); }
+
 ept_status run_tuned(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bool on_device, bool use_graph,
                      ept_result *out, void *stream) {
     // candidates up to the precision limit (one candidate: nothing to tune)
     int ncand = 0;
     while (ncand < 3 && CHUNK_CANDIDATES[ncand] <= c->max_chunk) ++ncand;
     if (!c->autotune || ncand <= 1)
-        return run_once(c, specs, prec, on_device, CHUNK_KB_DEFAULT, use_graph, out, stream, nullptr);
+        return run_once(c, specs, prec, on_device, unit_kb(c), use_graph, out, stream, nullptr);
     const std::vector<int64_t> key = tune_key(specs, prec, c->max_chunk);
     auto it = c->tuned_chunk.find(key);
     if (it != c->tuned_chunk.end()) return run_once(c, specs, prec, on_device, it->second, use_graph, out, stream, nullptr);
-    int best = CHUNK_KB_DEFAULT;
+    int best = unit_kb(c);
     float best_ms = 1e30f;
     for (int k = 0; k < ncand; ++k) {
         float ms = 0.f;
@@ -1428,7 +1432,7 @@ ept_status run_stream(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, 
     std::unique_ptr<Plan> hold(new (std::nothrow) Plan());
     if (!hold) return fail(EPT_ENOMEM, "host allocation failed");
     Plan &P = *hold;
-    plan_batch(P, specs, prec, !on_device, CHUNK_KB_DEFAULT, c->num_sms, c->debug, false);
+    plan_batch(P, specs, prec, !on_device, unit_kb(c), c->num_sms, c->debug, false);
     P.stream = true;
     const size_t tab0 = P.tab_bytes;
     const TestDesc &d = P.desc[0];
@@ -1686,7 +1690,7 @@ ept_status run_single(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, 
     if (prec == EPT_PREC_POOLED_FP32) return run_pooled(c, specs, on_device, out, stream);
     if (use_stream(c, specs[0], prec)) return run_stream(c, specs, prec, on_device, out, stream);
     if (tuned) return run_tuned(c, specs, prec, on_device, true, out, stream);
-    return run_once(c, specs, prec, on_device, CHUNK_KB_DEFAULT, false, out, stream, nullptr);
+    return run_once(c, specs, prec, on_device, unit_kb(c), false, out, stream, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1843,7 +1847,7 @@ bool form_batch(Server *S, Lane &L) {
     std::vector<TestSpec> specs;
     for (Request *r : batch) specs.push_back(r->spec);
     while (!batch.empty()) {
-        plan_batch(L.plan, specs, prec, true, CHUNK_KB_DEFAULT, L.ctx->num_sms);
+        plan_batch(L.plan, specs, prec, true, unit_kb(L.ctx), L.ctx->num_sms);
         if (S->in_use + L.plan.total <= S->budget) break;
         // hand the last one back, at its place in arrival order
         Request *r = batch.back();
@@ -2275,7 +2279,8 @@ ept_status ept_set_option(ept_ctx *c, int option, int64_t value) {
         c->stream_blocks = value;
         return EPT_OK;
     case EPT_OPT_MAX_CHUNK:
-        if (value != 8 && value != 16 && value != 32) return fail(EPT_EINVAL, "the longest unit must be 8, 16 or 32");
+        if (value != 4 && value != 8 && value != 16 && value != 32)
+            return fail(EPT_EINVAL, "the longest unit must be 4, 8, 16 or 32");
         c->max_chunk = (int)value;
         return EPT_OK;
     case EPT_OPT_WAIT_LIMIT_MS:
@@ -2320,7 +2325,7 @@ ept_status ept_submit(ept_ctx *c, const ept_test_desc *q, int prec, uint64_t *ti
                        q->B > 0 ? r->stats.data() : nullptr)[0];
     r->prec = prec;
     Plan P;
-    plan_batch(P, std::vector<TestSpec>(1, r->spec), prec, true, CHUNK_KB_DEFAULT);
+    plan_batch(P, std::vector<TestSpec>(1, r->spec), prec, true, unit_kb(c));
     r->bytes = P.total;
     std::lock_guard<std::mutex> lk(S->mu);
     if (r->bytes > S->budget) {

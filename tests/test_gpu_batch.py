@@ -259,7 +259,7 @@ def test_max_chunk_option(ctx):
     X, Y = workloads.gaussian_pair(workloads.TwoSampleSpec(nx=900, ny=1100, p=40, y_mean=0.05, data_seed=7))
     ref = oracle.permutation_test(X, Y, B=600, seed=3, stat="ed")
     try:
-        for mc in (32, 16, 8):
+        for mc in (32, 16, 8, 4):
             ctx.set_option("max_chunk", mc)
             r = ctx.test(X, Y, B=600, seed=3)
             assert _close(r.stats, ref["stats"])
