@@ -35,14 +35,18 @@ __device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
+// One test of a phase: the thread may sleep in the wait until the phase completes
+// or TRY_WAIT_NS pass (then false), so that waiting warps leave the issue slots to
+// the others.  Every 256 tests of mbar_wait below are then at most about 8 ms.
+constexpr uint32_t TRY_WAIT_NS = 32768;
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "n"(TRY_WAIT_NS)
         : "memory");
     return ok != 0;
 }
