@@ -39,10 +39,10 @@ BATCH_KERNELS_PER_STEP = 12  # ept_test_batch: the same and the batch's error st
 # dram read + write bytes of one k_contract_tc launch on the highdim workload, from the ncu
 # capture summarised in profiles/k_contract_tc_highdim_ed.md (to be reset to {} whenever the
 # kernel changes, until it is captured again)
-CONTRACT_TRAFFIC = {"highdim": 60.84e6, "mmd": 1033.7e6, "mmd_laplace": 1033.7e6, "mmd_median": 1033.7e6}
+CONTRACT_TRAFFIC = {"highdim": 61.58e6, "mmd": 1044.8e6, "mmd_laplace": 1044.8e6, "mmd_median": 1044.8e6}
 # streaming mode: DRAM bytes per stored block of the contraction, from the n = 60,000 capture summarised in
 # profiles/k_contract_tc_stream_60k.md (scaled to a launch by its window's blocks)
-STREAM_TRAFFIC_PER_BLOCK = 9105.1e6 / 110920
+STREAM_TRAFFIC_PER_BLOCK = 9119.0e6 / 110920
 
 
 def _args():
