@@ -15,14 +15,14 @@
 //   A (128 x 64): the packed C half-block, the test's C scaled by a power of two and
 //     split hi + lo in FP16, loaded by TMA (two 16 KB boxes, 128-byte swizzle);
 //   B (256 x 64): 0/1 relabeling values, exact in FP16, expanded from the bit masks
-//     by four producer warps straight into the 128-byte-swizzled K-major layout;
+//     by eight producer warps straight into the 128-byte-swizzled K-major layout;
 //   D (128 x 256 FP32) in tensor memory: D += A_hi * B, then D += A_lo * B.
 //   With the relabelings as N, one stage moves 32 KB through TMA for 2 x 128 x 256 x
 //   64 multiply-adds (half of what the relabelings-as-M mapping needs), and three
 //   64 KB stages fit in shared memory.  Two accumulators (512 TMEM columns) let the
 //   epilogue of one unit overlap the main loop of the next.
 //   Epilogue: TMEM lane = row i; a warp reads 32 relabelings at a time, takes the
-//   mask bits of its 32 rows for them with a 32 x 32 bit transpose (ballots), masks
+//   mask bits of its 32 rows for them with a 32 x 32 bit transpose (shuffles), masks
 //   its values, and sums over its 32 rows with a butterfly transpose-reduce (lane e
 //   ends with relabeling e's sum).  The four warps' sums meet in shared memory and
 //   are added in a fixed order.
@@ -31,10 +31,11 @@
 // owner), warps 2-9 = epilogue (two warps per TMEM lane quarter, each taking half
 // of the relabelings), warps 10-17 = relabeling-tile producers (one B row each).
 // Two epilogue and two producer warps per SM sub-partition hide each other's
-// shared-memory and L2 latencies.  Every
-// wait on an mbarrier is bounded (2 s); on expiry the kernel records an error
-// code, raises a CTA-wide abort flag, drains its own copies and MMAs (bounded
-// again), frees its tensor memory and returns.
+// shared-memory and L2 latencies.  Every wait on an mbarrier is bounded (2 s unless
+// the context sets another limit), and a waiting thread sleeps in the wait until its
+// phase completes; on expiry the kernel records an error code, raises a CTA-wide
+// abort flag, drains its own copies and MMAs (bounded again), frees its tensor
+// memory and returns.
 #include <cuda.h>
 #include <cstdio>
 #include <cstring>
