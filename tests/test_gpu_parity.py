@@ -230,6 +230,18 @@ def test_full_size_highdim_ed(ctx):
     _full_size_check(ctx, workloads.HIGHDIM, [1, 2, 4999, 10000])
 
 
+def test_full_size_highdim_every_statistic(ctx):
+    # the same configuration against the oracle's FP64 Algorithm 1 (three blocks built
+    # once, each relabeling assembled by the block swaps; pinned against the direct
+    # recomputation on the CPU): all 10,000 permuted statistics and the count
+    spec = workloads.HIGHDIM
+    X, Y = workloads.gaussian_pair(spec)
+    ref = oracle.permutation_test(X, Y, B=spec.B, seed=spec.seed, stat="ed", method="blocks")
+    for prec in PRECS:
+        res = ctx.test(X, Y, B=spec.B, seed=spec.seed, prec=prec)
+        _check(res, ref["stats"], ref["observed"], spec.B)
+
+
 def test_full_size_mmd(ctx):
     # Gaussian MMD, nx = ny = 10000, p = 100, Y ~ N(0, 1.1 I), sigma = 10, B = 10000
     _full_size_check(ctx, workloads.MMD, [1, 10000])
