@@ -161,7 +161,7 @@ size_t ept_estimate_bytes(int64_t nx, int64_t ny, int64_t p, int64_t B, int prec
    permutation stream of `seed` (ept_perm_masks) is relabeling b.
    perm_stats: B doubles (may be NULL), perm_stats[b-1] = statistic of draw b.
    out: host struct, required.  Errors: EPT_EINVAL for nx < 1, ny < 1, p < 1, B < 0,
-   any other sigma <= 0 with MMD, non-finite data, a median bandwidth of 0 (more than
+   nx + ny > 2^22, p > 2^30, B > 2^31, any other sigma <= 0 with MMD, non-finite data, a median bandwidth of 0 (more than
    half of the pooled pairs coincide); EPT_ENOMEM over budget.
    A repeated call with the same shapes replays the CUDA graph captured by the
    first (EPT_OPT_GRAPHS); then only out->ms_total is timed (the per-phase times

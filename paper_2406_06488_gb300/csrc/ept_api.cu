@@ -73,7 +73,7 @@ struct TestSpec {
 
 ept_status validate(int64_t nx, int64_t ny, int64_t p, int stat, double sigma, int prec, bool single = false) {
     if (nx < 1 || ny < 1) return fail(EPT_EINVAL, "nx and ny must be >= 1 (got %lld, %lld)", (long long)nx, (long long)ny);
-    if (p < 1) return fail(EPT_EINVAL, "p must be >= 1 (got %lld)", (long long)p);
+    if (p < 1 || p > ((int64_t)1 << 30)) return fail(EPT_EINVAL, "p must be in [1, 2^30] (got %lld)", (long long)p);
     if (nx + ny > (int64_t)1 << 22) return fail(EPT_EINVAL, "nx + ny = %lld exceeds 2^22", (long long)(nx + ny));
     if (stat != EPT_STAT_ED && stat != EPT_STAT_MMD_GAUSS && stat != EPT_STAT_MMD_LAPLACE)
         return fail(EPT_EINVAL, "unknown statistic %d", stat);
@@ -2084,7 +2084,7 @@ ept_status ept_destroy(ept_ctx *c) {
 }
 
 size_t ept_estimate_bytes(int64_t nx, int64_t ny, int64_t p, int64_t B, int prec) {
-    if (nx < 1 || ny < 1 || p < 1 || B < 0 || nx + ny > ((int64_t)1 << 22)) return 0;
+    if (nx < 1 || ny < 1 || p < 1 || p > ((int64_t)1 << 30) || B < 0 || nx + ny > ((int64_t)1 << 22)) return 0;
     if (prec == EPT_PREC_POOLED_FP32) {
         Plan P;
         plan_pooled(P, one_test(nullptr, nx, nullptr, ny, p, 0, 1.0, B, 0, nullptr, nullptr), true, 148);

@@ -161,6 +161,7 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     const auto t_start = std::chrono::steady_clock::now();
     if (!X || !Y || !out) return err(EPT_EINVAL, "null X, Y or result pointer");
     if (nx < 1 || ny < 1 || p < 1) return err(EPT_EINVAL, "nx, ny and p must be >= 1");
+    if (p > ((int64_t)1 << 30)) return err(EPT_EINVAL, "p exceeds 2^30");
     if (B < 0 || B > ((int64_t)1 << 31)) return err(EPT_EINVAL, "B must be in [0, 2^31]");
     if (nx + ny > ((int64_t)1 << 22)) return err(EPT_EINVAL, "nx + ny exceeds 2^22");
     if (stat != EPT_STAT_ED && stat != EPT_STAT_MMD_GAUSS && stat != EPT_STAT_MMD_LAPLACE)

@@ -49,6 +49,9 @@ def test_abi_version_and_errors_without_gpu(lib_path):
     # size estimates are pure host arithmetic
     assert ept.estimate_bytes(2000, 3000, 1000, 10000) > 0
     assert ept.estimate_bytes(0, 3, 1, 1) == 0
+    assert ept.estimate_bytes(2, 3, (1 << 30) + 1, 1) == 0       # p beyond 2^30
+    assert ept.estimate_bytes(2, 3, 1 << 30, 1) > 0
+    assert ept.estimate_bytes(1 << 21, (1 << 21) + 1, 1, 1) == 0  # nx + ny beyond 2^22
 
 
 def test_destroy_null_is_ok(lib_path):
