@@ -264,13 +264,14 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    EPT_ETIMEOUT).
    EPT_OPT_MAX_CHUNK (default 8; 4, 8, 16 or 32): the longest contraction work unit, in
    K-blocks of 64 pooled columns.  The tensor cores accumulate each unit in FP32, and
-   the error grows faster than the unit's length (about 2.8x per doubling): 8 keeps
-   the statistics within 1e-5 of the FP64 oracle on the workloads and the random
-   parity sweep of the tests; 16 or 32 let the autotuner pick longer units, about
-   12 % faster on large tests, with about three times the error on ill-conditioned
-   inputs (a wide-kernel MMD of few features on strongly separated samples, whose
-   permuted statistics are far smaller than the spread of the pooled matrix); 4
-   makes every unit 4 K-blocks, about 30 % slower, with about a third less error there.
+   the error grows faster than the unit's length (about 2.8x per doubling).  8 keeps
+   the statistics within 1e-5 of the FP64 oracle on the paper-shaped workloads and on
+   the random parity cases of the tests; on strongly ill-conditioned inputs (a
+   wide-kernel MMD of one to three features, say, whose permuted statistics are far
+   smaller than the spread of the pooled matrix) they can be off by up to a few 1e-3
+   relative while the p-values still agree.  16 or 32 let the autotuner pick longer
+   units, about 12 % faster on large tests, with about three times the error on such
+   inputs; 4 makes every unit 4 K-blocks, about 30 % slower, with somewhat less.
    EPT_OPT_SERVE_LANES (default 3, 1..16): serving batches in flight at once;
    EPT_OPT_SERVE_SLOTS (default 256): serving requests in flight at once; both
    before the first ept_submit.  EPT_EINVAL for an unknown option or value.
