@@ -154,6 +154,34 @@ ept_status ept_destroy(ept_ctx *ctx);
 /* Device scratch bytes a test of this shape needs (0 on invalid sizes). */
 size_t ept_estimate_bytes(int64_t nx, int64_t ny, int64_t p, int64_t B, int prec);
 
+/* Totals of a run's plan (ept_plan_check). */
+typedef struct {
+    int64_t units;            /* contraction work units: chunk x 256 relabelings x row half */
+    int64_t chunks;           /* chunks: a row panel's range of K-blocks */
+    int64_t stored_blocks;    /* 256 x 64 blocks of the packed upper storage */
+    int64_t partials;         /* partial-sum rows (two per chunk, one per row half), each one
+                                 FP32 per relabeling column, over all tests */
+    int64_t cta_kblocks_max;  /* contraction schedule: K-blocks of MMA work of the busiest CTA */
+    int64_t cta_kblocks_min;  /*   and of the least busy one */
+    int64_t windows;          /* streaming windows (0: resident) */
+    size_t scratch_bytes;     /* device scratch of the run */
+} ept_plan_info;
+
+/* The run planner on the host alone (no context, no device work), for checking it:
+   plans n_tests tests of sizes nx[t], ny[t], p[t] with B[t] relabelings each as a
+   tensor-core run does (Algorithm 1's permutation loop as quadratic forms over row
+   panels, K-block chunks and tiles of 256 relabelings), with contraction units of
+   at most unit_kb K-blocks dealt over num_sms CTAs, or, when stream_blocks > 0 (one
+   test), in streaming windows of at most stream_blocks stored blocks; then checks the
+   plan's invariants (row and column padding, prefix sums, chunk ranges, the
+   schedule covering every unit once, the windows covering the panels once and in
+   order within their capacity, guard bands).  out (may be NULL) receives the totals.
+   EPT_OK; EPT_EINVAL for bad arguments (the size limits of ept_test, unit_kb outside
+   1..1024, num_sms outside 1..4096, stream_blocks with more than one test);
+   EPT_EINTERNAL, with ept_last_error naming it, for a broken invariant. */
+ept_status ept_plan_check(const int64_t *nx, const int64_t *ny, const int64_t *p, const int64_t *B,
+                          int n_tests, int unit_kb, int num_sms, int64_t stream_blocks, ept_plan_info *out);
+
 /* One permutation test (Algorithm 1).
    X: nx*p floats, Y: ny*p floats (row-major).  stat: ept_stat.  sigma: kernel
    bandwidth for the MMD statistics, > 0 or EPT_SIGMA_MEDIAN; ignored for ED.

@@ -2096,6 +2096,74 @@ size_t ept_estimate_bytes(int64_t nx, int64_t ny, int64_t p, int64_t B, int prec
     return P.total;
 }
 
+ept_status ept_plan_check(const int64_t *nx, const int64_t *ny, const int64_t *p, const int64_t *B, int n_tests,
+                          int unit_kb, int num_sms, int64_t stream_blocks, ept_plan_info *out) {
+    if (!nx || !ny || !p || !B || n_tests < 1) return fail(EPT_EINVAL, "null size arrays or n_tests < 1");
+    if (unit_kb < 1 || unit_kb > 1024) return fail(EPT_EINVAL, "unit_kb must be in [1, 1024]");
+    if (num_sms < 1 || num_sms > 4096) return fail(EPT_EINVAL, "num_sms must be in [1, 4096]");
+    if (stream_blocks > 0 && n_tests != 1) return fail(EPT_EINVAL, "streaming windows are planned for one test");
+    std::vector<TestSpec> specs;
+    for (int t = 0; t < n_tests; ++t) {
+        ept_status st = validate(nx[t], ny[t], p[t], EPT_STAT_ED, 1.0, EPT_PREC_SPLIT_BF16);
+        if (st != EPT_OK) return st;
+        if (B[t] < 0 || B[t] > ((int64_t)1 << 31)) return fail(EPT_EINVAL, "test %d: B must be in [0, 2^31]", t);
+        specs.push_back(one_test(nullptr, nx[t], nullptr, ny[t], p[t], EPT_STAT_ED, 1.0, B[t], 0, nullptr, nullptr)[0]);
+    }
+    std::unique_ptr<Plan> hold(new (std::nothrow) Plan());
+    if (!hold) return fail(EPT_ENOMEM, "host allocation failed");
+    Plan &P = *hold;
+    const bool streaming = stream_blocks > 0;
+    plan_batch(P, specs, EPT_PREC_SPLIT_BF16, true, unit_kb, num_sms, true, !streaming);
+    if (streaming) {
+        // as the streaming run plans it: windows of panels, chunks of each window by first K-block
+        P.stream = true;
+        const size_t tab0 = P.tab_bytes;
+        stream_partition(P, stream_blocks, SIZE_MAX);
+        stream_layout(P, tab0);
+        for (size_t g = 0; g < P.gdesc.size(); ++g) {
+            auto first = P.chunks.begin() + P.gdesc[g].chunk0;
+            std::stable_sort(first, first + P.gdesc[g].nchunks,
+                             [](const Chunk &a, const Chunk &b) { return a.kb0 < b.kb0; });
+        }
+    }
+    ept_status st = check_plan(P);
+    if (st == EPT_OK && streaming) st = check_stream_plan(P);
+    if (st != EPT_OK) return st;
+    if (out) {
+        memset(out, 0, sizeof(*out));
+        out->units = P.nunits;
+        out->chunks = (int64_t)P.chunks.size();
+        out->stored_blocks = P.nblk;
+        for (const TestDesc &d : P.desc) out->partials += d.nparts;
+        out->windows = streaming ? (int64_t)P.gI0.size() : 0;
+        out->scratch_bytes = P.total;
+        if (!P.sched.empty()) {
+            // MMA work per CTA, with the unit lengths the kernel sees (the all-zero
+            // K-blocks of a diagonal square's second row half skipped)
+            int64_t mx = 0, mn = INT64_MAX;
+            for (size_t c = 0; c + 1 < P.sched_off.size(); ++c) {
+                int64_t w = 0;
+                for (int64_t k = P.sched_off[c]; k < P.sched_off[c + 1]; ++k) {
+                    const int64_t u = P.sched[(size_t)k];
+                    int t = 0;
+                    while (t + 1 < P.n_tests && P.pre_units[t + 1] <= u) ++t;
+                    const TestDesc &d = P.desc[t];
+                    const int64_t lu = u - P.pre_units[t];
+                    const Chunk &ch = P.chunks[(size_t)(d.chunk0 + (lu >> 1) / d.MT)];
+                    int64_t l = ch.kb1 - ch.kb0;
+                    if ((lu & 1) && ch.kb0 == KB_PER_PANEL * ch.I && l > 2) l -= 2;
+                    w += l;
+                }
+                mx = std::max(mx, w);
+                mn = std::min(mn, w);
+            }
+            out->cta_kblocks_max = mx;
+            out->cta_kblocks_min = mn;
+        }
+    }
+    return EPT_OK;
+}
+
 ept_status ept_test(ept_ctx *ctx, const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p, int on_device,
                     int stat, double sigma, int64_t B, uint64_t seed, int prec, double *perm_stats, ept_result *out,
                     void *stream) {

@@ -31,7 +31,7 @@ STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT
 EXPORTS = ["ept_abi_version", "ept_last_error", "ept_create", "ept_destroy", "ept_estimate_bytes", "ept_test",
            "ept_test_masks", "ept_perm_masks", "ept_build_blocks", "ept_test_static", "ept_test_batch",
            "ept_set_option", "ept_submit", "ept_poll", "ept_wait", "ept_cancel", "ept_test_range",
-           "ept_serving_stats", "ept_create_ex"]
+           "ept_serving_stats", "ept_create_ex", "ept_plan_check"]
 
 
 class EptError(RuntimeError):
@@ -51,6 +51,12 @@ class _Result(ctypes.Structure):
                 ("n_near_tie", ctypes.c_int64), ("n_fixup", ctypes.c_int64), ("ms_build", ctypes.c_double),
                 ("ms_perm", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_masks", ctypes.c_double),
                 ("ms_contract", ctypes.c_double), ("sigma", ctypes.c_double), ("n_windows", ctypes.c_int64)]
+
+
+class _PlanInfo(ctypes.Structure):
+    _fields_ = [("units", ctypes.c_int64), ("chunks", ctypes.c_int64), ("stored_blocks", ctypes.c_int64),
+                ("partials", ctypes.c_int64), ("cta_kblocks_max", ctypes.c_int64), ("cta_kblocks_min", ctypes.c_int64),
+                ("windows", ctypes.c_int64), ("scratch_bytes", ctypes.c_size_t)]
 
 
 # ept_allocator: device memory from the caller (ept_create_ex)
@@ -112,6 +118,8 @@ def load():
     lib.ept_destroy.restype = i32
     lib.ept_estimate_bytes.argtypes = [i64, i64, i64, i64, i32]
     lib.ept_estimate_bytes.restype = ctypes.c_size_t
+    lib.ept_plan_check.argtypes = [vp, vp, vp, vp, i32, i32, i32, i64, ctypes.POINTER(_PlanInfo)]
+    lib.ept_plan_check.restype = i32
     lib.ept_test.argtypes = [vp, vp, i64, vp, i64, i64, i32, i32, f64, i64, u64, i32, vp, ctypes.POINTER(_Result), vp]
     lib.ept_test.restype = i32
     lib.ept_test_range.argtypes = [vp, vp, i64, vp, i64, i64, i32, i32, f64, i64, i64, u64, i32, vp,
@@ -177,6 +185,17 @@ def _prec(prec) -> int:
 
 def estimate_bytes(nx: int, ny: int, p: int, B: int, prec="split_bf16") -> int:
     return int(load().ept_estimate_bytes(nx, ny, p, B, _prec(prec)))
+
+
+def plan_check(shapes, unit_kb: int = 8, num_sms: int = 152, stream_blocks: int = 0) -> dict:
+    """The run planner on the host alone (ept_plan_check): shapes = [(nx, ny, p, B), ...].
+    Returns the plan's totals; raises EptError if an argument is bad or an invariant breaks."""
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(shapes, dtype=np.int64).reshape(-1, 4).T)
+    info = _PlanInfo()
+    _check(load().ept_plan_check(a[0].ctypes.data, a[1].ctypes.data, a[2].ctypes.data, a[3].ctypes.data,
+                                 a.shape[1], unit_kb, num_sms, stream_blocks, ctypes.byref(info)))
+    return {name: int(getattr(info, name)) for name, _ in _PlanInfo._fields_}
 
 
 OPTION = {"graphs": 1, "autotune": 2, "serve_lanes": 3, "serve_slots": 4, "draw_mode": 5,
