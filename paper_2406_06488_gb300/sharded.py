@@ -1,0 +1,85 @@
+"""One permutation test across several processes (one GPU each): the relabelings
+1..B of the test's counter-based stream are split into contiguous ranges, each
+process evaluates its range (the observed statistic is relabeling 0 in every range),
+and a single exchange at the end gathers the permuted statistics and sum-reduces the
+counts; the p-value (1 + #{stat* >= observed}) / (1 + B) (Section 3.1) is then that
+of the whole test.  Relabeling b is draw b of the stream whatever the number of
+processes, so the result does not depend on it.  No collective runs inside a kernel.
+
+The exchange uses torch.distributed on the process group given (tensors on the
+current CUDA device for NCCL, on the CPU otherwise)."""
+from __future__ import annotations
+
+import numpy as np
+
+
+def permutation_ranges(B: int, world: int):
+    """Contiguous ranges (b_first, count) of relabelings 1..B for ranks 0..world-1,
+    sizes differing by at most one (a rank may get none when world > B)."""
+    if B < 0 or world < 1:
+        raise ValueError("B must be >= 0 and world >= 1")
+    base, extra = divmod(B, world)
+    out, b = [], 1
+    for r in range(world):
+        c = base + (1 if r < extra else 0)
+        out.append((b, c))
+        b += c
+    return out
+
+
+def combine(observed: float, stats_parts, n_ge_parts, n_near_parts, B: int):
+    """The whole test from its ranges: (observed, stats[B] in relabeling order, n_ge,
+    n_near_tie, p_value)."""
+    stats = np.concatenate([np.asarray(s, dtype=np.float64) for s in stats_parts]) if B else np.zeros(0)
+    if stats.shape[0] != B:
+        raise ValueError("the ranges hold %d statistics, the test has %d" % (stats.shape[0], B))
+    n_ge = int(sum(n_ge_parts))
+    return observed, stats, n_ge, int(sum(n_near_parts)), (1.0 + n_ge) / (1.0 + B)
+
+
+def sharded_test(run_range, B: int, group=None):
+    """Run this rank's range with run_range(b_first, count) -> (observed, stats[count],
+    n_ge, n_near_tie), then exchange once; every rank returns the whole test's
+    (observed, stats[B], n_ge, n_near_tie, p_value)."""
+    import torch
+    import torch.distributed as dist
+
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    ranges = permutation_ranges(B, world)
+    b_first, count = ranges[rank]
+    observed, stats, n_ge, n_near = run_range(b_first, count)
+    stats = np.asarray(stats, dtype=np.float64).reshape(-1)
+    if stats.shape[0] != count:
+        raise ValueError("run_range returned %d statistics for a range of %d" % (stats.shape[0], count))
+    device = (torch.device("cuda", torch.cuda.current_device())
+              if dist.get_backend(group) == "nccl" else torch.device("cpu"))
+    width = max(c for _, c in ranges) if ranges else 0
+    # one gather of the padded ranges (and of each rank's observed statistic, which
+    # is the same relabeling 0 everywhere), one sum of the counts
+    mine = torch.zeros(width + 1, dtype=torch.float64, device=device)
+    mine[0] = float(observed)
+    if count:
+        mine[1:count + 1] = torch.from_numpy(stats).to(device)
+    parts = [torch.empty_like(mine) for _ in range(world)]
+    dist.all_gather(parts, mine, group=group)
+    counts = torch.tensor([int(n_ge), int(n_near)], dtype=torch.int64, device=device)
+    dist.all_reduce(counts, group=group)
+    parts = [p.cpu().numpy() for p in parts]
+    stats_parts = [parts[r][1:c + 1] for r, (_, c) in enumerate(ranges)]
+    counts = counts.cpu().numpy()
+    return combine(float(parts[0][0]), stats_parts, [int(counts[0])], [int(counts[1])], B)
+
+
+def run_across_ranks(ctx, X, Y, B: int, seed: int = 0, stat="ed", sigma: float = 1.0, prec="split_bf16",
+                      group=None):
+    """sharded_test with this rank's range evaluated by ctx.test_range (the library)."""
+    def run_range(b_first, count):
+        if count == 0:   # no relabelings here: the observed statistic alone
+            r = ctx.test(X, Y, B=0, seed=seed, stat=stat, sigma=sigma, prec=prec)
+            return r.observed, np.zeros(0), 0, 0
+        r = ctx.test_range(X, Y, b_first=b_first, count=count, seed=seed, stat=stat, sigma=sigma, prec=prec)
+        st = r.stats.cpu().numpy() if hasattr(r.stats, "cpu") else r.stats
+        return r.observed, st, r.n_ge, r.n_near_tie
+
+    return sharded_test(run_range, B, group)
