@@ -164,7 +164,8 @@ typedef struct {
     int64_t cta_kblocks_max;  /* contraction schedule: K-blocks of MMA work of the busiest CTA */
     int64_t cta_kblocks_min;  /*   and of the least busy one */
     int64_t windows;          /* streaming windows (0: resident) */
-    size_t scratch_bytes;     /* device scratch of the run */
+    size_t scratch_bytes;     /* device scratch of the run, with the 256-byte guard bands of
+                                 EPT_OPT_DEBUG_CHECKS (whose placement is checked too) */
 } ept_plan_info;
 
 /* The run planner on the host alone (no context, no device work), for checking it:
