@@ -265,3 +265,33 @@ def test_max_chunk_option(ctx):
             assert _close(r.stats, ref["stats"])
     finally:
         ctx.set_option("max_chunk", 8)
+
+
+def test_full_batched_configuration_sampled(ctx):
+    # the benchmark's batched configuration as it runs: 512 uneven ED tests (nx, ny in
+    # 50..2000, p in 20..500, B = 5000) in one batched run on device inputs; eight of
+    # them, spread over the sizes, against the oracle's FP64 Algorithm 1 on every
+    # statistic, and every test's count and p-value consistent
+    torch = pytest.importorskip("torch")
+    specs = workloads.batched_specs(512, B=5000)
+    tests = []
+    for sp in specs:
+        X, Y = workloads.gaussian_pair(sp)
+        tests.append(dict(X=torch.from_numpy(X).cuda(), Y=torch.from_numpy(Y).cuda(), B=sp.B, seed=sp.seed,
+                          stat=sp.stat, sigma=sp.sigma))
+    res = ctx.test_batch(tests)
+    assert len(res) == 512
+    for r, sp in zip(res, specs):
+        assert r.p_value == (1.0 + r.n_ge) / (1.0 + sp.B) and 0 <= r.n_ge <= sp.B
+    order = sorted(range(512), key=lambda t: specs[t].nx + specs[t].ny)
+    for t in [order[0], order[1], order[170], order[255], order[340], order[-2], order[-1], 511]:
+        sp = specs[t]
+        X, Y = workloads.gaussian_pair(sp)
+        ref = oracle.permutation_test(X, Y, B=sp.B, seed=sp.seed, stat="ed", method="blocks")
+        r = res[t]
+        assert abs(r.observed - ref["observed"]) <= REL_TOL * abs(ref["observed"]), t
+        got = r.stats.cpu().numpy() if hasattr(r.stats, "cpu") else np.asarray(r.stats)
+        rel = np.abs(got - ref["stats"]) / np.abs(ref["stats"])
+        assert rel.max() <= REL_TOL, (t, float(rel.max()))
+        near = np.abs(ref["stats"] - ref["observed"]) <= 1e-5 * abs(ref["observed"])
+        assert abs(r.n_ge - ref["n_ge"]) <= int(near.sum()), t
