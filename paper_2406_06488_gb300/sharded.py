@@ -7,7 +7,11 @@ of the whole test.  Relabeling b is draw b of the stream whatever the number of
 processes, so the result does not depend on it.  No collective runs inside a kernel.
 
 The exchange uses torch.distributed on the process group given (tensors on the
-current CUDA device for NCCL, on the CPU otherwise)."""
+current CUDA device for NCCL, on the CPU otherwise).  Failures: a rank whose range
+raises reports it in a status reduction before the exchange and re-raises; the other
+ranks then raise RangeFailed at once instead of waiting in the gather.  A rank that
+dies outright is noticed by the process group (its timeout, or the broken
+connection) in that same reduction."""
 from __future__ import annotations
 
 import numpy as np
@@ -37,6 +41,10 @@ def combine(observed: float, stats_parts, n_ge_parts, n_near_parts, B: int):
     return observed, stats, n_ge, int(sum(n_near_parts)), (1.0 + n_ge) / (1.0 + B)
 
 
+class RangeFailed(RuntimeError):
+    """Another rank's range failed, so the test has no result."""
+
+
 def sharded_test(run_range, B: int, group=None):
     """Run this rank's range with run_range(b_first, count) -> (observed, stats[count],
     n_ge, n_near_tie), then exchange once; every rank returns the whole test's
@@ -48,12 +56,23 @@ def sharded_test(run_range, B: int, group=None):
     rank = dist.get_rank(group)
     ranges = permutation_ranges(B, world)
     b_first, count = ranges[rank]
-    observed, stats, n_ge, n_near = run_range(b_first, count)
-    stats = np.asarray(stats, dtype=np.float64).reshape(-1)
-    if stats.shape[0] != count:
-        raise ValueError("run_range returned %d statistics for a range of %d" % (stats.shape[0], count))
     device = (torch.device("cuda", torch.cuda.current_device())
               if dist.get_backend(group) == "nccl" else torch.device("cpu"))
+    error = None
+    try:
+        observed, stats, n_ge, n_near = run_range(b_first, count)
+        stats = np.asarray(stats, dtype=np.float64).reshape(-1)
+        if stats.shape[0] != count:
+            raise ValueError("run_range returned %d statistics for a range of %d" % (stats.shape[0], count))
+    except Exception as e:   # reported to the other ranks below, then re-raised here
+        error = e
+    # every rank's status before the exchange: a failed range ends the test everywhere
+    failed = torch.tensor([0 if error is None else 1], dtype=torch.int64, device=device)
+    dist.all_reduce(failed, group=group)
+    if error is not None:
+        raise error
+    if int(failed.item()):
+        raise RangeFailed("%d rank(s) failed to evaluate their range of relabelings" % int(failed.item()))
     width = max(c for _, c in ranges) if ranges else 0
     # one gather of the padded ranges (and of each rank's observed statistic, which
     # is the same relabeling 0 everywhere), one sum of the counts

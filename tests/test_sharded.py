@@ -96,3 +96,55 @@ def test_ranks_reproduce_the_whole_test(world):
         assert obs == whole["observed"]
         assert np.array_equal(np.asarray(stats), whole["stats"])
         assert nge == whole["n_ge"] and p == whole["p_value"]
+
+
+def _failing_rank_main(rank, world, port, mode, out):
+    import datetime
+    import torch.distributed as dist
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), OMP_NUM_THREADS="1")
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    from paper_2406_06488_gb300 import sharded as sh
+
+    def run_range(b_first, count):
+        if rank == 1:
+            if mode == "raise":
+                raise ValueError("range evaluation failed")
+            os._exit(3)                     # the process dies without a word
+        return _oracle_range(b_first, count)
+
+    import time
+    t0 = time.time()
+    try:
+        sh.sharded_test(run_range, B)
+        out[rank] = ("ok", time.time() - t0)
+    except Exception as e:                  # noqa: BLE001 - the type is what the test checks
+        out[rank] = (type(e).__name__, time.time() - t0)
+    finally:
+        try:
+            dist.destroy_process_group()
+        except Exception:                   # noqa: BLE001 - the group may be broken by a dead peer
+            pass
+
+
+@pytest.mark.parametrize("mode", ["raise", "exit"])
+def test_a_failed_rank_ends_the_test_everywhere(mode):
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    with ctx.Manager() as m:
+        out = m.dict()
+        procs = [ctx.Process(target=_failing_rank_main, args=(r, 2, port, mode, out)) for r in range(2)]
+        for pr in procs:
+            pr.start()
+        for pr in procs:
+            pr.join(timeout=120)
+        res = dict(out)
+        codes = [pr.exitcode for pr in procs]
+    # rank 0 learns of the failure in the status reduction (no result, no wait in the gather)
+    assert res[0][0] == "RangeFailed" if mode == "raise" else res[0][0] != "ok", res
+    assert res[0][1] < 30.0
+    if mode == "raise":
+        assert res[1][0] == "ValueError" and codes == [0, 0]
+    else:
+        assert 1 not in res and codes[1] == 3
