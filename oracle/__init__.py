@@ -21,7 +21,12 @@ of the paper it follows:
 * the p-value of Section 3.1 -- ``pvalue``;
 * the permutation stream (Philox4x32-10 + Knuth's Algorithm S, the library's
   reading of SampleWithoutReplacement) -- ``perm_select``;
-* exhaustive enumeration of all relabelings -- ``exhaustive``.
+* exhaustive enumeration of all relabelings -- ``exhaustive``;
+* the statistic of one relabeling recomputed from permuted raw rows with threads
+  over rows (Algorithm 4, for sampled checks at full size) -- ``stat_select``;
+* the sum and trace of the pooled matrix and the closed-form mean of the
+  permutation distribution (Section 3.1's null) -- ``pooled_moments``,
+  ``permutation_mean``.
 """
 from __future__ import annotations
 
@@ -122,6 +127,8 @@ def _load(path=None):
     lib.eo_pooled_moments.restype = None
     lib.eo_median_pairs.argtypes = [f32p, i64, f32p, i64, i64]
     lib.eo_median_pairs.restype = ctypes.c_double
+    lib.eo_permutation_mean.argtypes = [ctypes.c_double, ctypes.c_double, i64, i64, ctypes.c_int]
+    lib.eo_permutation_mean.restype = ctypes.c_double
     lib.eo_num_threads.argtypes = []
     lib.eo_num_threads.restype = ctypes.c_int
     _lib = lib
@@ -313,15 +320,10 @@ def pooled_moments(X, Y, stat="ed", sigma: float = 1.0):
 
 def permutation_mean(S: float, trace: float, nx: int, ny: int, stat="ed") -> float:
     """Closed-form mean of the permutation distribution of Eq. 1 / Eq. 2 under a uniform
-    random nx-subset s of the pooled rows: with E[s_i] = nx/n and
-    E[s_i s_j] = nx(nx-1)/(n(n-1)), E[T] = nx/n tr + nx(nx-1)/(n(n-1)) (S - tr) for
-    T = s'Ws, E[L] = nx/n S for L = s'W1, and the statistic is linear in (T, L):
-    ED = 2(L - T)/(nx ny) - T/nx^2 - (S - 2L + T)/ny^2, MMD = -(that expression)."""
-    n = nx + ny
-    ET = nx / n * trace + nx * (nx - 1) / (n * (n - 1)) * (S - trace)
-    EL = nx / n * S
-    ed = 2 * (EL - ET) / (nx * ny) - ET / nx ** 2 - (S - 2 * EL + ET) / ny ** 2
-    return ed if _stat_code(stat) == STAT_ED else -ed
+    random nx-subset of the pooled rows, from S = 1'W1 and tr W of the pooled matrix
+    (E[s_i] = nx/n, E[s_i s_j] = nx(nx-1)/(n(n-1)); the statistic is linear in
+    T = s'Ws and L = s'W1)."""
+    return float(_load().eo_permutation_mean(float(S), float(trace), int(nx), int(ny), _stat_code(stat)))
 
 
 def exhaustive(X, Y, stat="ed", sigma: float = 1.0, max_count: int = 1_000_000):

@@ -47,7 +47,7 @@
 #define EO_STAT_MMD_LAPLACE 2  /* Laplacian kernel */
 
 /* Test-only mutation switch.  The default build (EO_MUTANT undefined or 0) is the
- * oracle.  The pin tests compile copies with EO_MUTANT = 1..8, each planting one
+ * oracle.  The pin tests compile copies with EO_MUTANT = 1..12, each planting one
  * plausible mistake, and check that at least one pin fails for every mutant. */
 #ifndef EO_MUTANT
 #define EO_MUTANT 0
@@ -536,7 +536,7 @@ int64_t eo_exhaustive(const float *X, int64_t nx, const float *Y, int64_t ny, in
     for (int64_t k = 0; k < nx; ++k) comb[k] = k;
     for (int64_t c = 0; c < count; ++c) {
         uint8_t *s = all + c * n;
-        for (int64_t k = 0; k < nx; ++k) s[comb[k]] = 1;
+        for (int64_t k = 0; k < nx; ++k) s[EO_MUTANT == 11 ? n - 1 - comb[k] : comb[k]] = 1;
         uint8_t *q = canon + c * n;
         const int flip = (nx == ny) && !s[0];
         for (int64_t t = 0; t < n; ++t) q[t] = flip ? (uint8_t)!s[t] : s[t];
@@ -582,7 +582,7 @@ double eo_stat_select_mt(const float *X, int64_t nx, const float *Y, int64_t ny,
 #pragma omp parallel for schedule(dynamic, 8)
         for (int64_t k = 0; k < nx; ++k) {
             double s1 = 0.0, s2 = 0.0;
-            for (int64_t l = 0; l < ny; ++l) s1 += eo_entry(w + ix[k] * p, w + iy[l] * p, p, stat, sigma);
+            for (int64_t l = (EO_MUTANT == 9); l < ny; ++l) s1 += eo_entry(w + ix[k] * p, w + iy[l] * p, p, stat, sigma);
             for (int64_t l = 0; l < nx; ++l) s2 += eo_entry(w + ix[k] * p, w + ix[l] * p, p, stat, sigma);
             rxy[k] = s1;
             rxx[k] = s2;
@@ -622,13 +622,32 @@ void eo_pooled_moments(const float *X, int64_t nx, const float *Y, int64_t ny, i
         double s = 0.0;
         for (int64_t j = 0; j < n; ++j) s += eo_entry(w + i * p, w + j * p, p, stat, sigma);
         rs[i] = s;
-        dg[i] = eo_entry(w + i * p, w + i * p, p, stat, sigma);
+        dg[i] = eo_entry(w + i * p, w + (EO_MUTANT == 10 ? (i + 1) % n : i) * p, p, stat, sigma);
     }
     double S = 0.0, tr = 0.0;
     for (int64_t i = 0; i < n; ++i) { S += rs[i]; tr += dg[i]; }
     *S_out = S;
     *trace_out = tr;
     free(w); free(rs); free(dg);
+}
+
+/* Closed-form mean of the permutation distribution of Eq. 1 / Eq. 2 when the
+ * relabeling s is a uniform random nx-subset of the n pooled rows (Section 3.1's
+ * null distribution).  Inclusion probabilities: E[s_i] = nx/n and, for i != j,
+ * E[s_i s_j] = nx(nx-1)/(n(n-1)).  With T = s'Ws, L = s'W1 and S = 1'W1 the three
+ * block sums of the relabeled data are T (x*x*), L - T (x*y*) and S - 2L + T
+ * (y*y*), so E[T] = nx/n tr W + nx(nx-1)/(n(n-1)) (S - tr W), E[L] = nx/n S and,
+ * the statistic being linear in (T, L),
+ *   E[ED*] = 2(E[L] - E[T])/(nx ny) - E[T]/nx^2 - (S - 2E[L] + E[T])/ny^2;
+ * E[MMD*] is the same expression with the opposite sign. */
+double eo_permutation_mean(double S, double trace, int64_t nx, int64_t ny, int stat)
+{
+    const double fx = (double)nx, fy = (double)ny, fn = (double)(nx + ny);
+    const double pair = (EO_MUTANT == 12) ? (fx / fn) * (fx / fn) : fx * (fx - 1.0) / (fn * (fn - 1.0));
+    const double ET = fx / fn * trace + pair * (S - trace);
+    const double EL = fx / fn * S;
+    const double ed = 2.0 * (EL - ET) / (fx * fy) - ET / (fx * fx) - (S - 2.0 * EL + ET) / (fy * fy);
+    return stat == EO_STAT_ED ? ed : -ed;
 }
 
 int eo_num_threads(void)

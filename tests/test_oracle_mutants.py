@@ -19,6 +19,14 @@ MUTANTS = {
         [lambda: pins.test_block_swap_equals_recomputation_on_worked_example("ed")]),
     7: ("p-value without the +1 terms", [pins.test_pvalue_definition]),
     8: ("Laplacian kernel exp(-d^2/sigma)", [pins.test_laplace_kernel_matches_library_routine]),
+    9: ("single-relabeling statistic skips the first y* row in the cross sum",
+        [lambda: pins.test_stat_select_matches_recomputation("ed", 7, 11, 1)]),
+    10: ("pooled trace taken along the first super-diagonal",
+         [lambda: pins.test_pooled_moments_match_library_routine("mmd")]),
+    11: ("exhaustive enumeration writes each index set mirrored",
+         [lambda: pins.test_exhaustive_order_is_lexicographic(3, 5)]),
+    12: ("permutation mean with pair inclusion (nx/n)^2",
+         [lambda: pins.test_permutation_mean_equals_exhaustive_mean("ed")]),
 }
 
 

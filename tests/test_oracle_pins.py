@@ -241,23 +241,90 @@ def test_exhaustive_70(stat, shift):
     assert abs(p_mc - p_exact) <= 4 * se + 2.0 / B
 
 
-def test_permutation_mean_closed_form():
-    # Under a uniform random nx-subset s: E[s_i] = nx/n, E[s_i s_j] = nx(nx-1)/(n(n-1)).
-    # With W the pooled distance matrix, T = s'Ws, L = s'W1, S = 1'W1:
-    #   ED* = 2(L - T)/(nx ny) - T/nx^2 - (S - 2L + T)/ny^2.
+def _brute_stat(Z, sel, stat, sigma):
+    """Eq. 1 / Eq. 2 of one relabeling by scipy's distances (independent of the oracle)."""
+    xs, ys = Z[sel].astype(np.float64), Z[~sel].astype(np.float64)
+
+    def blk(a, b):
+        d = cdist(a, b)
+        if stat == "ed":
+            return d
+        if stat == "mmd":
+            return np.exp(-d ** 2 / (2 * sigma * sigma))
+        return np.exp(-d / sigma)
+    nx, ny = len(xs), len(ys)
+    ed = 2 * blk(xs, ys).sum() / (nx * ny) - blk(xs, xs).sum() / nx ** 2 - blk(ys, ys).sum() / ny ** 2
+    return ed if stat == "ed" else -ed
+
+
+@pytest.mark.parametrize("stat", ["ed", "mmd", "mmd_laplace"])
+@pytest.mark.parametrize("nx,ny,p", [(1, 1, 1), (1, 9, 1), (9, 1, 3), (7, 11, 1), (33, 20, 5), (3, 64, 2)])
+def test_stat_select_matches_recomputation(stat, nx, ny, p):
+    # the threaded single-relabeling statistic (the checker of every full-size sampled
+    # test) against scipy's distances and against the pinned Algorithm 4 routine
+    X, Y = _rand_pair(nx, ny, p, seed=31 * nx + ny, shift=0.4)
+    Z = np.vstack([X, Y])
+    sel = oracle.perm_select(17, nx, ny, 0, 6)
+    direct = oracle.test_direct(X, Y, sel, stat, 1.3)
+    for k, s in enumerate(sel):
+        got = oracle.stat_select(X, Y, s, stat, 1.3)
+        want = _brute_stat(Z, s, stat, 1.3)
+        tol = 1e-13 * max(abs(want), 1e-300) + 1e-15
+        assert abs(got - want) <= max(tol, 1e-12 * abs(want)), (k, got, want)
+        assert abs(got - direct[k]) <= 1e-13 * max(abs(direct[k]), 1e-300) + 1e-16, (k, got, direct[k])
+
+
+@pytest.mark.parametrize("stat", ["ed", "mmd", "mmd_laplace"])
+def test_pooled_moments_match_library_routine(stat):
+    X, Y = _rand_pair(23, 31, 4, seed=41, shift=0.3)
+    Z = np.vstack([X, Y]).astype(np.float64)
+    D = cdist(Z, Z)
+    W = D if stat == "ed" else (np.exp(-D ** 2 / (2 * 1.7 ** 2)) if stat == "mmd" else np.exp(-D / 1.7))
+    S, tr = oracle.pooled_moments(X, Y, stat, 1.7)
+    assert abs(S - W.sum()) <= 1e-13 * abs(W.sum())
+    assert abs(tr - np.trace(W)) <= 1e-13 * max(1.0, abs(np.trace(W)))
+    # distances vanish on the diagonal, kernels are 1 there
+    assert tr == (0.0 if stat == "ed" else float(len(Z)))
+
+
+@pytest.mark.parametrize("stat", ["ed", "mmd"])
+def test_permutation_mean_equals_exhaustive_mean(stat):
+    # the closed form E[stat*] over a uniform nx-subset equals the plain average over
+    # all C(n, nx) subsets (brute force, exact up to rounding)
+    nx, ny, p = 5, 7, 3
+    X, Y = _rand_pair(nx, ny, p, seed=43, shift=0.5)
+    Z = np.vstack([X, Y])
+    vals = []
+    for c in combinations(range(nx + ny), nx):
+        s = np.zeros(nx + ny, dtype=bool)
+        s[list(c)] = True
+        vals.append(_brute_stat(Z, s, stat, 1.9))
+    want = float(np.mean(vals))
+    S, tr = oracle.pooled_moments(X, Y, stat, 1.9)
+    got = oracle.permutation_mean(S, tr, nx, ny, stat)
+    assert abs(got - want) <= 1e-12 * abs(want)
+
+
+@pytest.mark.parametrize("stat", ["ed", "mmd"])
+def test_permutation_mean_matches_the_stream(stat):
+    # at a size beyond enumeration: the sample mean of B draws of the stream (the
+    # statistics by Algorithm 1) lies within a CLT bound of the closed form
     nx, ny, p = 30, 45, 6
-    n = nx + ny
     X, Y = _rand_pair(nx, ny, p, seed=13, shift=0.3)
-    Wm = cdist(np.vstack([X, Y]).astype(np.float64), np.vstack([X, Y]).astype(np.float64))
-    S = Wm.sum()
-    tr = np.trace(Wm)
-    ET = nx / n * tr + nx * (nx - 1) / (n * (n - 1)) * (S - tr)
-    EL = nx / n * S
-    want = 2 * (EL - ET) / (nx * ny) - ET / nx ** 2 - (S - 2 * EL + ET) / ny ** 2
+    S, tr = oracle.pooled_moments(X, Y, stat, 2.2)
+    want = oracle.permutation_mean(S, tr, nx, ny, stat)
     B = 4000
-    res = oracle.permutation_test(X, Y, B=B, seed=9, stat="ed", method="blocks")
-    st = res["stats"]
+    st = oracle.permutation_test(X, Y, B=B, seed=9, stat=stat, sigma=2.2, method="blocks")["stats"]
     assert abs(st.mean() - want) <= 5 * st.std() / math.sqrt(B)
+
+
+@pytest.mark.parametrize("nx,ny", [(4, 4), (3, 5), (5, 2), (1, 4), (4, 1), (2, 2)])
+def test_exhaustive_order_is_lexicographic(nx, ny):
+    X, Y = _rand_pair(nx, ny, 2, seed=nx * 10 + ny)
+    sel, stats = oracle.exhaustive(X, Y, "ed")
+    got = [tuple(int(t) for t in np.flatnonzero(r)) for r in sel]
+    assert got == list(combinations(range(nx + ny), nx))
+    assert stats.shape == (len(got),)
 
 
 # ------------------------------------------- Laplacian kernel and median bandwidth
