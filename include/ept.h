@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define EPT_ABI_VERSION 3
+#define EPT_ABI_VERSION 4
 
 typedef enum {
     EPT_OK = 0,
@@ -111,6 +111,10 @@ typedef struct {
                              the first pass and the centring, ms_perm the second pass and
                              the combination, ms_contract the contraction launches summed
                              (0 beyond 64 windows) */
+    int64_t n_refined;    /* statistics (the observed one included) whose a-posteriori
+                             error estimate exceeded 1e-5 of their value and that were
+                             recomputed in FP64 from the raw rows (EPT_OPT_REFINE); with
+                             EPT_OPT_REFINE = 0, the number that would have been */
 } ept_result;
 
 /* Library ABI version (EPT_ABI_VERSION of the build). */
@@ -301,11 +305,27 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    relative while the p-values still agree.  16 or 32 let the autotuner pick longer
    units, about 12 % faster on large tests, with about three times the error on such
    inputs; 4 makes every unit 4 K-blocks, about 30 % slower, with somewhat less.
+   EPT_OPT_REFINE (default 1; 0 or 1): FP64 recomputation of flagged statistics
+   (Section 3.1's statistics, Eq. 1 / Eq. 2, evaluated from the raw rows).  Every
+   statistic of the split and plain precisions carries an a-posteriori estimate of
+   its error, E_b = 12 u cT A_b + 4 u Wbar g_b: u = 2^-24, cT = (n/(nx ny))^2, A_b the
+   sum of the absolute values of its contraction partial sums (the magnitudes its
+   FP32 accumulations carried), Wbar the mean entry of the pooled matrix, g_b = 1/m
+   for a relabeling and 1/sqrt(m) for the observed statistic and every statistic
+   within 1e-5 |observed| + 2 E_0 of it (m = min(nx, ny)).  A statistic with
+   E_b > 1e-5 |stat_b| is recomputed from W built in FP64 by direct differences of the
+   widened inputs (Algorithm 3) and its three block sums in FP64; the counts are then
+   taken again.  The run needs extra device memory for it (8 n bytes per row of a
+   window of at most 2 GiB, 16 bytes per 64 rows and flagged statistic).  Flagged
+   statistics arise on ill-conditioned inputs, such as a wide-kernel MMD of a few
+   features whose permuted statistics are far below the FP32 resolution of the
+   kernel values; ept_result.n_refined counts them.  Not applied in the streaming
+   mode, by the pre-computation baseline or by ept_test_static.
    EPT_OPT_SERVE_LANES (default 3, 1..16): serving batches in flight at once;
    EPT_OPT_SERVE_SLOTS (default 256): serving requests in flight at once; both
    before the first ept_submit.  EPT_EINVAL for an unknown option or value.
    Environment: EPT_GRAPHS, EPT_AUTOTUNE, EPT_DRAW_MODE, EPT_DEBUG_CHECKS,
-   EPT_STREAM_BLOCKS, EPT_WAIT_LIMIT_MS, EPT_MAX_CHUNK, EPT_SERVE_LANES and EPT_SERVE_SLOTS set the
+   EPT_STREAM_BLOCKS, EPT_WAIT_LIMIT_MS, EPT_MAX_CHUNK, EPT_REFINE, EPT_SERVE_LANES and EPT_SERVE_SLOTS set the
    starting value of the option of that name in every new context (an invalid value
    makes ept_create fail with EPT_EINVAL); EPT_AUTOTUNE_CACHE names a file in which
    the autotuner keeps its choices across processes. */
@@ -320,7 +340,8 @@ enum {
     EPT_OPT_DEBUG_CHECKS = 8,
     EPT_OPT_STREAM_BLOCKS = 9,
     EPT_OPT_WAIT_LIMIT_MS = 10,
-    EPT_OPT_MAX_CHUNK = 11
+    EPT_OPT_MAX_CHUNK = 11,
+    EPT_OPT_REFINE = 12
 };
 ept_status ept_set_option(ept_ctx *ctx, int option, int64_t value);
 
@@ -387,13 +408,19 @@ ept_status ept_build_blocks(ept_ctx *ctx, const float *X, int64_t nx, const floa
    permutations for smaller n) is rejected with EPT_EINVAL and a message giving the
    bytes it needs.  The call runs on the calling thread's current device and on
    `stream` (NULL = the legacy default stream); its first call on a device looks up
-   the array's device address (cudaGetSymbolAddress) and caches it, so make that
-   first call before any stream capture.  X, Y and perm_stats (B doubles, may be
-   NULL) are DEVICE pointers; out is a host struct (ms_total is host wall time, the
-   other timing fields are 0).  Every call reuses the same array: each call clears
-   what must start at zero, calls from one process are serialised, and calls that
-   overlap on the GPU (e.g. from several processes) race on the array.  It calls no
-   cudaMalloc, cudaFree or other allocating routine. */
+   the array's device address (cudaGetSymbolAddress) and caches it.  The call is
+   synchronous: it reads its counters back to the host and waits for `stream`
+   before returning.  X, Y and perm_stats (B doubles, may be NULL) are DEVICE
+   pointers; out is a host struct (ms_total is host wall time, the other timing
+   fields are 0); on any error perm_stats is left unwritten.  The test is planned
+   by ept_test's planner (same descriptor and contraction chunks, units of 8
+   K-blocks); its blocks are built by the plain FP32 SIMT kernel (the tensor-core
+   build needs FP16 copies of the rows that the array has no room for), its
+   relabelings are contracted on the tensor cores as in ept_test.  Every call
+   reuses the same array: each call clears what must start at zero, calls from one
+   process are serialised, and calls that overlap on the GPU (e.g. from several
+   processes) race on the array.  It calls no cudaMalloc, cudaFree or other
+   allocating routine. */
 ept_status ept_test_static(const float *X, int64_t nx, const float *Y, int64_t ny, int64_t p,
                            int stat, double sigma, int64_t B, uint64_t seed, double *perm_stats,
                            ept_result *out, void *stream);

@@ -116,6 +116,7 @@ struct Plan {
     size_t off_in, off_norms, off_iscale, off_u, off_Zh, off_Zl, off_D, off_Chi, off_rowpart, off_colpart,
         off_r, off_Spart, off_dcorr, off_Upart, off_Stpart, off_maskT, off_partial, off_stats, off_observed, off_ctr,
         total;
+    size_t off_errest = 0, off_flags = 0;   // error estimates and refinement flags (0: none)
     // streaming mode (one test, windows of row panels): per window its panels
     // [I0, I1), its first stored block and block count, its build tiles, the test's
     // descriptor seen through the window and its contraction units; the window's
@@ -129,16 +130,21 @@ struct Plan {
 
 // The fields of a test's descriptor that do not depend on its shape (statistic,
 // bandwidth, seed); a cached plan is refreshed with them on every run.
-void set_test_params(TestDesc &d, const TestSpec &s) {
-    d.stat = s.stat;
-    d.seed = s.seed;
-    d.b0 = s.b0;
-    d.median = (s.stat != EPT_STAT_ED && s.sigma == EPT_SIGMA_MEDIAN) ? 1 : 0;
+void set_params(TestDesc &d, int stat, double sigma, uint64_t seed) {
+    d.stat = stat;
+    d.seed = seed;
+    d.median = (stat != EPT_STAT_ED && sigma == EPT_SIGMA_MEDIAN) ? 1 : 0;
     // the build writes kernel values directly unless the bandwidth is still unknown
-    d.kern = (s.stat == EPT_STAT_ED || d.median) ? 0 : s.stat;
-    d.neg_inv_2s2 = (d.kern == EPT_STAT_MMD_GAUSS) ? (float)(-1.0 / (2.0 * s.sigma * s.sigma)) : 0.f;
-    d.inv_sigma = (d.kern == EPT_STAT_MMD_LAPLACE) ? (float)(1.0 / s.sigma) : 0.f;
-    d.sign = (s.stat == EPT_STAT_ED) ? -1.0 : 1.0;
+    d.kern = (stat == EPT_STAT_ED || d.median) ? 0 : stat;
+    d.neg_inv_2s2 = (d.kern == EPT_STAT_MMD_GAUSS) ? (float)(-1.0 / (2.0 * sigma * sigma)) : 0.f;
+    d.inv_sigma = (d.kern == EPT_STAT_MMD_LAPLACE) ? (float)(1.0 / sigma) : 0.f;
+    d.sign = (stat == EPT_STAT_ED) ? -1.0 : 1.0;
+    d.sigma64 = (stat != EPT_STAT_ED && !d.median) ? sigma : 0.0;
+}
+
+void set_test_params(TestDesc &d, const TestSpec &s) {
+    set_params(d, s.stat, s.sigma, s.seed);
+    d.b0 = s.b0;
 }
 
 // Static schedule of the tensor-core contraction: units sorted by length (K-blocks,
@@ -220,34 +226,8 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
     for (int t = 0; t < P.n_tests; ++t) {
         const TestSpec &s = specs[t];
         TestDesc d;
-        memset(&d, 0, sizeof(d));
-        d.nx = s.nx;
-        d.ny = s.ny;
-        d.n = s.nx + s.ny;
-        d.p = s.p;
-        d.B = s.B;
-        d.n_pad = (d.n + PANEL - 1) / PANEL * PANEL;
-        d.NP = d.n_pad / PANEL;
-        d.NKB = d.n_pad / KB;
-        d.nblk = blk_off(d.NP, d.NKB);
-        d.nw = d.n_pad / 32;
-        d.nwu = (int)((d.n + 31) / 32);
-        d.ncols = s.B + 1;
-        d.Bp = (d.ncols + COL_PAD - 1) / COL_PAD * COL_PAD;
-        d.MT = d.Bp / TC_TILE_N;
-        d.p_pad = (d.p + BUILD_KB - 1) / BUILD_KB * BUILD_KB;
-        d.kblocks = (int)(d.p_pad / BUILD_KB);
-        d.comp = d.ny < d.nx;
-        d.m = d.comp ? d.ny : d.nx;
-        d.other = d.comp ? d.nx : d.ny;
-        set_test_params(d, s);
-        d.tau = (float)NEAR_DUP_TAU;
-        const double fn = (double)d.n, q = fn / ((double)d.nx * (double)d.ny);
-        d.cT = q * q;
-        d.inv_o2 = 1.0 / ((double)d.other * (double)d.other);
-        d.kappa = 2.0 * (double)d.m / fn;
-        d.inv_n = 1.0 / fn;
-        d.inv_2n2 = 1.0 / (2.0 * fn * fn);
+        describe_test(d, s.nx, s.ny, s.p, s.B, s.stat, s.sigma, s.seed, tc);
+        d.b0 = s.b0;
         d.row0 = P.nrows;
         d.blk0 = P.nblk;
         d.pan0 = P.npan;
@@ -257,18 +237,14 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
         d.col0 = P.nstats;
         for (int64_t I = 0; I < d.NP; ++I) {
             for (int64_t kb = KB_PER_PANEL * I; kb < d.NKB; ++kb) P.blk.push_back(BlkInfo{t, (int)I, (int)kb, 0});
-            // contraction chunks stop at the last K-block holding real columns (the
-            // padding columns of C are zero)
-            const int64_t NKBc = (d.n + KB - 1) / KB;
-            for (int64_t kb = KB_PER_PANEL * I; kb < NKBc; kb += chunk_kb)
-                P.chunks.push_back(Chunk{(int)I, (int)kb, (int)std::min<int64_t>(kb + chunk_kb, NKBc), 0});
+            const int64_t nq = panel_chunks(d, I, chunk_kb);
+            for (int64_t q = 0; q < nq; ++q) P.chunks.push_back(panel_chunk(d, I, q, chunk_kb));
             if (tc)
                 for (int64_t J = I; J < d.NP; ++J)
                     for (int h = 0; h < 2; ++h) P.tiles.push_back(Tile{t, (int)I, (int)J, h});
         }
         d.nchunks = (int64_t)P.chunks.size() - d.chunk0;
         d.nparts = 2 * d.nchunks;   // (chunk, row half)
-        d.scaled = tc ? 1 : 0;
         d.part0 = P.npart;
         P.nrows += d.n_pad;
         P.nblk += d.nblk;
@@ -347,6 +323,8 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
     P.off_maskT = take((size_t)P.nmask * 4);
     P.off_partial = take((size_t)P.npart * 4);
     P.off_stats = take((size_t)P.nstats * 8);
+    P.off_errest = take((size_t)P.nstats * 8);
+    P.off_flags = take((size_t)P.nstats);
     P.off_observed = take((size_t)P.n_tests * 8);
     P.off_ctr = take(sizeof(Counters) * P.n_tests);
     P.off_sel_hist = P.any_median ? take((size_t)P.n_tests * 2048 * 4) : 0;
@@ -404,6 +382,51 @@ std::vector<TestSpec> one_test(const float *X, int64_t nx, const float *Y, int64
 namespace ept {
 // lets other translation units of the library report an error message
 void set_last_error(const char *msg) { g_err = msg; }
+
+void describe_test(TestDesc &d, int64_t nx, int64_t ny, int64_t p, int64_t B, int stat, double sigma,
+                   uint64_t seed, bool split) {
+    memset(&d, 0, sizeof(d));
+    d.nx = nx;
+    d.ny = ny;
+    d.n = nx + ny;
+    d.p = p;
+    d.B = B;
+    d.n_pad = (d.n + PANEL - 1) / PANEL * PANEL;
+    d.NP = d.n_pad / PANEL;
+    d.NKB = d.n_pad / KB;
+    d.nblk = blk_off(d.NP, d.NKB);
+    d.nw = d.n_pad / 32;
+    d.nwu = (int)((d.n + 31) / 32);
+    d.ncols = B + 1;
+    d.Bp = (d.ncols + COL_PAD - 1) / COL_PAD * COL_PAD;
+    d.MT = d.Bp / TC_TILE_N;
+    d.p_pad = (d.p + BUILD_KB - 1) / BUILD_KB * BUILD_KB;
+    d.kblocks = (int)(d.p_pad / BUILD_KB);
+    d.comp = d.ny < d.nx;
+    d.m = d.comp ? d.ny : d.nx;
+    d.other = d.comp ? d.nx : d.ny;
+    set_params(d, stat, sigma, seed);
+    d.b0 = 1;
+    d.tau = (float)NEAR_DUP_TAU;
+    const double fn = (double)d.n, q = fn / ((double)d.nx * (double)d.ny);
+    d.cT = q * q;
+    d.inv_o2 = 1.0 / ((double)d.other * (double)d.other);
+    d.kappa = 2.0 * (double)d.m / fn;
+    d.inv_n = 1.0 / fn;
+    d.inv_2n2 = 1.0 / (2.0 * fn * fn);
+    d.scaled = split ? 1 : 0;
+}
+
+cudaError_t smem_limit_once(const void *func, int bytes, unsigned long long *done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (__atomic_load_n(done, __ATOMIC_ACQUIRE) & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) __atomic_fetch_or(done, bit, __ATOMIC_RELEASE);
+    return e;
+}
 }  // namespace ept
 
 struct GraphCache {
@@ -522,6 +545,7 @@ struct ept_ctx {
     int64_t stream_blocks = 0;          // streaming mode: 0 automatic, k > 0 windows of <= k blocks, -1 never
     unsigned long long wait_ns = 0;     // limit of the kernels' bounded waits (0: their default, 2 s)
     int max_chunk = CHUNK_KB_DEFAULT;   // longest contraction unit the autotuner may pick (precision)
+    bool refine = true;                 // recompute flagged statistics in FP64 (EPT_OPT_REFINE)
     ept_allocator alloc{};              // caller-supplied device memory (alloc.alloc == nullptr: cudaMalloc)
     std::atomic<int> inject_alloc{0};   // test hook: the next N scratch acquisitions fail (host side)
     bool inject_stall = false;          // test hook: the next run's contraction waits out its limit
@@ -804,6 +828,8 @@ Batch device_view(ept_ctx *c, const Plan &P) {
     b.Upart = (double *)(A + P.off_Upart);
     b.Stpart = (double *)(A + P.off_Stpart);
     b.stats = (double *)(A + P.off_stats);
+    b.errest = P.off_errest ? (double *)(A + P.off_errest) : nullptr;
+    b.flags = P.off_flags ? (uint8_t *)(A + P.off_flags) : nullptr;
     b.observed = (double *)(A + P.off_observed);
     b.maskT = (uint32_t *)(A + P.off_maskT);
     b.ctr = (Counters *)(A + P.off_ctr);
@@ -988,6 +1014,7 @@ ept_status collect(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &specs
         r.ms_masks = ms_masks;
         r.ms_contract = ms_contract;
         r.n_windows = P.stream ? (int64_t)P.gI0.size() : 0;
+        r.n_refined = (int64_t)ctr[t].n_flag;
         if (P.host_in && specs[t].perm_stats && d.B > 0)
             memcpy(specs[t].perm_stats, stats + d.col0 + 1, (size_t)d.B * 8);
     }
@@ -1055,6 +1082,78 @@ void load_tune_file(ept_ctx *c) {
         if (chunk == 8 || chunk == 16 || chunk == 32) c->tuned_chunk[key] = (int)chunk;
     }
     fclose(f);
+}
+
+// FP64 recomputation of the statistics the error criterion flagged (ept_refine.cu),
+// after a finished run whose scratch is still in place: per test with flagged
+// columns, the list of its flagged columns, W64 in row windows of at most
+// REFINE_W64_BYTES, the statistics; then the counts again and the results read
+// back as the run itself does.  Statistics that were not flagged keep their values.
+const size_t REFINE_W64_BYTES = (size_t)2 << 30;
+
+ept_status refine_after(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &specs, ept_result *out, bool timed,
+                        cudaStream_t s, std::vector<TestError> *per_test = nullptr) {
+    if (!c->refine || P.off_flags == 0) return EPT_OK;
+    const Staging S = staging_layout(P);
+    const Counters *ctr = (const Counters *)(c->pinned + S.res_ctr);
+    bool any = false;
+    for (int t = 0; t < P.n_tests; ++t)
+        any |= ctr[t].n_flag > 0 && test_error(P, ctr, t) == EPT_OK && !(per_test && (*per_test)[t].st != EPT_OK);
+    if (!any) return EPT_OK;
+    NvtxRange range("ept.refine");
+    const Batch b = device_view(c, P);
+    std::vector<uint8_t> fl;
+    std::vector<int32_t> list;
+    for (int t = 0; t < P.n_tests; ++t) {
+        if (ctr[t].n_flag == 0 || test_error(P, ctr, t) != EPT_OK) continue;
+        if (per_test && (*per_test)[t].st != EPT_OK) continue;
+        const TestDesc &d = P.desc[t];
+        fl.resize((size_t)d.ncols);
+        CK(cudaMemcpyAsync(fl.data(), b.flags + d.col0, (size_t)d.ncols, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        list.clear();
+        for (int64_t k = 0; k < d.ncols; ++k)
+            if (fl[(size_t)k]) list.push_back((int32_t)k);
+        const int64_t nflag = (int64_t)list.size();
+        if (nflag == 0) continue;
+        const double sigma = d.stat == EPT_STAT_ED ? 0.0 : (d.median ? (double)median_sigma(ctr[t]) : d.sigma64);
+        const int64_t ntiles = (d.n + 63) / 64;
+        int64_t rows_w = (int64_t)(REFINE_W64_BYTES / (8 * (size_t)d.n)) / 64 * 64;
+        rows_w = std::max<int64_t>(64, std::min<int64_t>(rows_w, ntiles * 64));
+        const size_t b_list = align_up(4 * (size_t)nflag, 256), b_part = align_up(16 * (size_t)ntiles * nflag, 256),
+                     b_spart = align_up(8 * (size_t)ntiles, 256), b_w = 8 * (size_t)rows_w * (size_t)d.n;
+        void *mem = nullptr;
+        ept_status st = device_alloc(c, b_list + b_part + b_spart + b_w, s, &mem);
+        if (st != EPT_OK) return st;
+        uint8_t *m8 = (uint8_t *)mem;
+        int32_t *dlist = (int32_t *)m8;
+        double *part = (double *)(m8 + b_list), *spart = (double *)(m8 + b_list + b_part);
+        double *W64 = (double *)(m8 + b_list + b_part + b_spart);
+        cudaError_t e = cudaMemcpyAsync(dlist, list.data(), 4 * (size_t)nflag, cudaMemcpyHostToDevice, s);
+        for (int64_t r0 = 0; r0 < d.n && e == cudaSuccess; r0 += rows_w) {
+            const int64_t r1 = std::min<int64_t>(d.n, r0 + rows_w);
+            launch_refine_w(b, t, d.n, sigma, r0, r1, W64, s);
+            launch_refine_rows(b, t, r0, r1, W64, dlist, nflag, part, spart, s);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            launch_refine_finish(b, t, dlist, nflag, part, spart, ntiles, s);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the list's host copy stays valid until here
+        device_free(c, mem, s);
+        if (e != cudaSuccess) return fail(EPT_ECUDA, "FP64 refinement failed: %s", cudaGetErrorString(e));
+    }
+    // counts and outputs again, read back as in the run
+    launch_reset_counts(b, s);
+    launch_combine_count(b, s);
+    CK(cudaGetLastError());
+    uint8_t *pin = c->pinned;
+    CK(cudaMemcpyAsync(pin + S.res_ctr, b.ctr, sizeof(Counters) * P.n_tests, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(pin + S.res_obs, b.observed, 8 * (size_t)P.n_tests, cudaMemcpyDeviceToHost, s));
+    if (P.host_in) CK(cudaMemcpyAsync(pin + S.res_stats, b.stats, 8 * (size_t)P.nstats, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return collect(c, P, specs, out, timed, per_test);
 }
 
 // One run of a batch: plan, stage, enqueue (or replay a captured graph), wait, collect.
@@ -1125,6 +1224,7 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
         CK(cudaEventRecord(c->ev[4], s));
         CK(cudaStreamSynchronize(s));
         if ((st = collect(c, P, specs, out, false)) != EPT_OK) return st;
+        if ((st = refine_after(c, P, specs, out, false, s)) != EPT_OK) return st;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, c->ev[0], c->ev[4]);
         for (int t = 0; t < P.n_tests; ++t) out[t].ms_total = ms;
@@ -1136,6 +1236,7 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
     if (st != EPT_OK) return st;
     CK(cudaStreamSynchronize(s));
     if ((st = collect(c, P, specs, out, true)) != EPT_OK) return st;
+    if ((st = refine_after(c, P, specs, out, true, s)) != EPT_OK) return st;
     if (device_ms) cudaEventElapsedTime(device_ms, c->ev[5], c->ev[6]);
     return EPT_OK;
 }
@@ -1315,6 +1416,7 @@ struct LayoutCursor {
 void stream_layout(Plan &P, size_t tab_bytes_resident) {
     const TestDesc &d = P.desc[0];
     P.guards.n = 0;
+    P.off_errest = P.off_flags = 0;   // no FP64 refinement in the streaming mode
     LayoutCursor L{P, tab_bytes_resident};
     auto take = [&](size_t bytes) { return L.take(bytes); };
     P.off_gdesc = take(sizeof(TestDesc) * P.gdesc.size());
@@ -1591,6 +1693,7 @@ ept_status run_stream(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, 
 void pooled_layout(Plan &P, int num_sms) {
     const TestDesc &d = P.desc[0];
     P.guards.n = 0;
+    P.off_errest = P.off_flags = 0;   // the baseline has no error estimate
     LayoutCursor L{P, P.tab_bytes};
     auto take = [&](size_t bytes) { return L.take(bytes); };
     L.start_data();
@@ -1757,6 +1860,20 @@ void CUDART_CB lane_finished(void *arg) {
     S->cv_work.notify_all();   // no lock: the scheduler also wakes on a short timeout
 }
 
+// the lane's scratch back to the pool (or the caller's allocator), stream-ordered
+// after the lane's work
+ept_status lane_release(Server *S, Lane &L) {
+    if (!L.arena) return EPT_OK;
+    cudaStream_t s = L.ctx->stream;
+    const ept_allocator &ua = S->owner->alloc;
+    cudaError_t e = cudaSuccess;
+    if (ua.alloc) ua.free(L.arena, (void *)s, ua.user);
+    else e = cudaFreeAsync(L.arena, s);
+    L.arena = nullptr;
+    if (e != cudaSuccess) return fail(EPT_ECUDA, "cudaFreeAsync: %s", cudaGetErrorString(e));
+    return EPT_OK;
+}
+
 ept_status lane_enqueue(Server *S, Lane &L) {
     ept_ctx *c = L.ctx;
     cudaStream_t s = c->stream;
@@ -1780,17 +1897,17 @@ ept_status lane_enqueue(Server *S, Lane &L) {
     L.arena = (uint8_t *)mem;
     c->arena = L.arena;   // the kernels and staging address the lane's scratch through the context
     c->arena_cap = L.plan.total;
+    c->refine = S->owner->refine;
     stage_host(c, L.plan, L.specs, false);
     st = enqueue_device(c, L.plan, s, false);
     c->arena = nullptr;
     c->arena_cap = 0;
-    // back to the pool (or the caller's allocator) once the run's work is done
-    cudaError_t e = cudaSuccess;
-    if (ua.alloc) ua.free(L.arena, (void *)s, ua.user);
-    else e = cudaFreeAsync(L.arena, s);
-    L.arena = nullptr;
-    if (st != EPT_OK) return st;
-    if (e != cudaSuccess) return fail(EPT_ECUDA, "cudaFreeAsync: %s", cudaGetErrorString(e));
+    if (st != EPT_OK) {
+        lane_release(S, L);
+        return st;
+    }
+    // the scratch stays with the lane until its results (and any FP64 refinement)
+    // have been collected
     CK(cudaEventRecord(L.done, s));
     CK(cudaLaunchHostFunc(s, lane_finished, S));
     return EPT_OK;
@@ -1883,7 +2000,18 @@ void serve_loop(Server *S, int device) {
             ept_status st = EPT_OK;
             if (q != cudaSuccess) st = fail(EPT_ECUDA, "serving run failed: %s", cudaGetErrorString(q));
             else st = collect(L.ctx, L.plan, L.specs, out.data(), false, &per_test);
-            finish_requests(S, L, st, st == EPT_OK ? std::string() : g_err, out.data(), &per_test);
+            if (st == EPT_OK) {
+                // FP64 recomputation of flagged statistics, on the lane's scratch
+                L.ctx->arena = L.arena;
+                L.ctx->arena_cap = L.plan.total;
+                st = refine_after(L.ctx, L.plan, L.specs, out.data(), false, L.ctx->stream, &per_test);
+                L.ctx->arena = nullptr;
+                L.ctx->arena_cap = 0;
+            }
+            const std::string msg = st == EPT_OK ? std::string() : g_err;
+            const ept_status rst = lane_release(S, L);
+            if (st == EPT_OK && rst != EPT_OK) st = rst;
+            finish_requests(S, L, st, st == EPT_OK ? msg : (msg.empty() ? g_err : msg), out.data(), &per_test);
             progressed = true;
         }
         bool any_busy = false;
@@ -1934,6 +2062,7 @@ ept_status serve_start(ept_ctx *c) {
         Lane L;
         if ((st = ept_create(&L.ctx, c->device, 0)) != EPT_OK) break;
         L.ctx->autotune = false;
+        L.ctx->alloc = c->alloc;   // the FP64 refinement's scratch comes from the caller's allocator too
         if (cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             ept_destroy(L.ctx);
@@ -2036,7 +2165,7 @@ ept_status ept_create_ex(ept_ctx **out, int device, size_t mem_budget_bytes, con
     } env_opts[] = {{"EPT_GRAPHS", EPT_OPT_GRAPHS},           {"EPT_AUTOTUNE", EPT_OPT_AUTOTUNE},
                     {"EPT_DRAW_MODE", EPT_OPT_DRAW_MODE},     {"EPT_DEBUG_CHECKS", EPT_OPT_DEBUG_CHECKS},
                     {"EPT_STREAM_BLOCKS", EPT_OPT_STREAM_BLOCKS}, {"EPT_WAIT_LIMIT_MS", EPT_OPT_WAIT_LIMIT_MS},
-                    {"EPT_MAX_CHUNK", EPT_OPT_MAX_CHUNK},
+                    {"EPT_MAX_CHUNK", EPT_OPT_MAX_CHUNK},     {"EPT_REFINE", EPT_OPT_REFINE},
                     {"EPT_SERVE_LANES", EPT_OPT_SERVE_LANES}, {"EPT_SERVE_SLOTS", EPT_OPT_SERVE_SLOTS}};
     for (const auto &eo : env_opts) {
         const char *v = getenv(eo.env);
@@ -2345,6 +2474,10 @@ ept_status ept_set_option(ept_ctx *c, int option, int64_t value) {
     case EPT_OPT_STREAM_BLOCKS:
         if (value < -1) return fail(EPT_EINVAL, "stream blocks must be -1, 0 or a block count");
         c->stream_blocks = value;
+        return EPT_OK;
+    case EPT_OPT_REFINE:
+        if (value != 0 && value != 1) return fail(EPT_EINVAL, "refine must be 0 or 1");
+        c->refine = value != 0;
         return EPT_OK;
     case EPT_OPT_MAX_CHUNK:
         if (value != 4 && value != 8 && value != 16 && value != 32)

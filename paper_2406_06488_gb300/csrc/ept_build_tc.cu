@@ -410,12 +410,9 @@ void launch_split_rows(const Batch &b, cudaStream_t s) {
 }
 
 cudaError_t launch_build_tc(const Batch &b, const void *tmaps, int num_sms, cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_build_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static unsigned long long smem_set = 0;   // one bit per device
+    cudaError_t e = smem_limit_once((const void *)k_build_tc, SMEM_BYTES, &smem_set);
+    if (e != cudaSuccess) return e;
     if (b.ntiles < 1) return cudaSuccess;
     const CUtensorMap *tm = (const CUtensorMap *)tmaps;
     const int grid = b.ntiles < num_sms ? (int)b.ntiles : num_sms;

@@ -413,13 +413,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
 cudaError_t launch_contract_tc(const Batch &b, const void *tmap_hi, const void *tmap_lo, int num_sms,
                                cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_contract_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr_set = true;
-    }
+    static unsigned long long smem_set = 0;   // one bit per device
+    cudaError_t e = smem_limit_once((const void *)k_contract_tc, SMEM_BYTES, &smem_set);
+    if (e != cudaSuccess) return e;
     int64_t grid = b.sched ? (int64_t)b.tc_grid : (int64_t)num_sms;
     if (grid > b.nunits_total) grid = b.nunits_total;
     if (grid < 1) return cudaSuccess;

@@ -73,7 +73,27 @@ struct Counters {
     unsigned long long guard_bad;    // debug checks: words of the guard bands found overwritten
     unsigned long long batch_failed; // (test 0) some test of a batched call has an error: device outputs
                                      //   of the call are then left unwritten
+    unsigned long long n_flag;       // statistics whose error estimate exceeds the tolerance (refined in FP64)
 };
+
+// A-posteriori error estimate of a statistic computed by the contraction, and the
+// statistics that are recomputed in FP64 (ept_refine.cu).  For relabeling column b:
+//     E_b = REFINE_KA u cT A_b + REFINE_KR u Wbar g_b,
+// u = 2^-24 (the FP32 unit roundoff), cT the statistic's factor on s'Cs, A_b the sum
+// over the contraction's work units of |partial sum| (the magnitudes the FP32
+// accumulations of column b carried), Wbar = 1'W1 / n^2 the mean entry of the
+// pooled matrix (the FP32 representation of its entries), g_b = 1/m for a
+// relabeling (the representation errors of its m^2 entries average out) and
+// 1/sqrt(m) for the observed statistic and every statistic within 1e-5 |stat_0| +
+// 2 E_0 of it (relabelings aligned with the samples keep value-dependent biases of
+// the entries, such as those of the kernel evaluation, which differ between the
+// blocks).  m is the contracted group's size.  Statistics with E_b > REFINE_TOL
+// |stat_b| are flagged.  The constants were fitted to measured GPU errors (a sweep
+// of 200 ill-conditioned problems against the FP64 oracle, both precisions).
+constexpr double REFINE_KA = 12.0;
+constexpr double REFINE_KR = 4.0;
+constexpr double REFINE_TOL = 1e-5;
+constexpr double REFINE_U = 5.9604644775390625e-08;   // 2^-24
 
 // Debug checks: guard bands of GUARD_BYTES after every scratch region, filled with a
 // per-band pattern before a run and checked after it.
@@ -132,6 +152,7 @@ struct TestDesc {
     int32_t median;                  // bandwidth from the median heuristic (build distances, select, transform)
     int32_t pad2_;
     double cT, inv_o2, sign, kappa, inv_n, inv_2n2;
+    double sigma64;                  // the given bandwidth in FP64 (FP64 refinement; 0 for ED and median)
 };
 
 // Prefix sums over the tests (n_tests + 1 entries each) of the work dimensions.
@@ -160,6 +181,8 @@ struct Batch {
     int64_t c_stride;
     float *D, *partial;
     double *rowpart, *colpart, *r, *Spart, *dcorr, *Upart, *Stpart, *stats, *observed;
+    double *errest;                      // per relabeling column: the accumulation part of E_b
+    uint8_t *flags;                      // per relabeling column: 1 = recompute in FP64
     uint32_t *maskT;
     Counters *ctr;
     uint32_t *sel_hist;                  // median heuristic: 2048 bins per test (null if no test needs it)
@@ -171,6 +194,32 @@ struct Batch {
 
 // tensor-core contraction work units of a test: chunk x relabeling tile x row half
 __host__ __device__ inline int64_t tc_units(const TestDesc &d) { return d.nchunks * d.MT * 2; }
+
+// Contraction chunks of a test: panel I covers K-blocks 4I .. NKBc-1 in chunks of
+// chunk_kb, where NKBc = ceil(n / KB) is the last K-block holding real columns (the
+// padding columns of C are zero, so the contraction stops there).
+__host__ __device__ inline int64_t contract_nkb(const TestDesc &d) { return (d.n + KB - 1) / KB; }
+__host__ __device__ inline int64_t panel_chunks(const TestDesc &d, int64_t I, int chunk_kb) {
+    const int64_t len = contract_nkb(d) - KB_PER_PANEL * I;
+    return len > 0 ? (len + chunk_kb - 1) / chunk_kb : 0;
+}
+__host__ __device__ inline Chunk panel_chunk(const TestDesc &d, int64_t I, int64_t q, int chunk_kb) {
+    const int64_t kb0 = KB_PER_PANEL * I + q * chunk_kb, end = contract_nkb(d);
+    return Chunk{(int)I, (int)kb0, (int)(kb0 + chunk_kb < end ? kb0 + chunk_kb : end), 0};
+}
+
+// The planner's description of one test (ept_api.cu; every entry point plans its
+// tests with it): padding, panels, K-blocks, relabeling columns, the contracted
+// group, the statistic's parameters and the combination constants.  The batch
+// offsets (row0, blk0, ...) and the chunk count are left at zero.  sigma is a
+// bandwidth > 0 or EPT_SIGMA_MEDIAN (MMD); split selects the tensor-core path.
+void describe_test(TestDesc &d, int64_t nx, int64_t ny, int64_t p, int64_t B, int stat, double sigma,
+                   uint64_t seed, bool split);
+
+// Raises a kernel's dynamic shared-memory limit on the calling thread's current
+// device, once per device (the attribute is per device; `done` holds one bit per
+// device and concurrent first calls both set the same value).
+cudaError_t smem_limit_once(const void *func, int bytes, unsigned long long *done);
 
 // Entry of the pooled matrix from a squared distance d2 (FP32 or, for the fix-up of
 // cancellation-prone pairs, FP64): the distance (Algorithm 3), the Gaussian kernel
@@ -212,8 +261,23 @@ enum { DRAW_WARPS = 1, DRAW_LANES = 2 };
 constexpr int64_t DRAW_LANES_MIN_COLS_PER_SM = 32 * 32;
 void launch_masks(const Batch &b, int num_sms, int mode, cudaStream_t s);   // draws or caller masks
 void launch_contract_simt(const Batch &b, cudaStream_t s);
-void launch_combine(const Batch &b, cudaStream_t s);                     // statistics, counts, outputs
-void launch_combine_count(const Batch &b, cudaStream_t s);               // counts and outputs alone
+void launch_combine(const Batch &b, cudaStream_t s);                     // statistics, flags, counts, outputs
+void launch_combine_count(const Batch &b, cudaStream_t s);               // counts and outputs alone (recount)
+
+// ---- FP64 refinement of flagged statistics (ept_refine.cu): one test ----
+// W64 rows [r0, r1) of test t (n pooled rows; all n columns, FP64, row stride n) from
+// the raw rows; r0 is a multiple of 64
+void launch_refine_w(const Batch &b, int t, int64_t n, double sigma, int64_t r0, int64_t r1, double *W64,
+                     cudaStream_t s);
+// for the nflag listed columns (test-local indexes): per 64-row tile of [r0, r1)
+// the sums T = s'W s and L = s'W 1 over those rows (part[tile][k][2]) and
+// spart[tile] = the rows' total
+void launch_refine_rows(const Batch &b, int t, int64_t r0, int64_t r1, const double *W64, const int32_t *list,
+                        int64_t nflag, double *part, double *spart, cudaStream_t s);
+// the statistics of the listed columns from the partial sums of all ntiles row tiles
+void launch_refine_finish(const Batch &b, int t, const int32_t *list, int64_t nflag, const double *part,
+                          const double *spart, int64_t ntiles, cudaStream_t s);
+void launch_reset_counts(const Batch &b, cudaStream_t s);   // n_ge = n_near = 0 before a recount
 
 // single-draw-stream export (ept_perm_masks): columns 0..count-1 = draws b0..b0+count-1
 void launch_perm_masks_plain(uint64_t seed, int nx, int ny, int64_t b0, int64_t count, int nw, uint32_t *maskT,

@@ -933,7 +933,7 @@ void launch_contract_simt(const Batch &b, cudaStream_t s) {
 // kernels): stat_b >= stat_0 and near-ties |stat_b - stat_0| <= 1e-5 |stat_0|.
 __global__ void __launch_bounds__(256) k_combine_stats(const Batch bt) {
     __shared__ double bSt;
-    __shared__ double ws[8][32];
+    __shared__ double ws[8][32], wa[8][32];
     const int64_t gc0 = (int64_t)blockIdx.x * 32;
     const int t = find_test(bt.pre.cols, bt.n_tests, gc0);
     const TestDesc &d = bt.desc[t];
@@ -945,17 +945,29 @@ __global__ void __launch_bounds__(256) k_combine_stats(const Batch bt) {
     const int64_t c = gc0 + lane - bt.pre.cols[t];
     const int64_t Bp = d.Bp, nparts = d.nparts;
     const float *part = bt.partial + d.part0 + c;
-    double acc = 0.0;
-    for (int64_t k = warp; k < nparts; k += 8) acc += (double)part[k * Bp];
+    double acc = 0.0, aabs = 0.0;
+    for (int64_t k = warp; k < nparts; k += 8) {
+        const double v = (double)part[k * Bp];
+        acc += v;
+        aabs += fabs(v);
+    }
     ws[warp][lane] = acc;
+    wa[warp][lane] = aabs;
     __syncthreads();
     if (warp == 0) {
-        double q = 0.0;
+        double q = 0.0, a = 0.0;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) q += ws[w][lane];
+        for (int w = 0; w < 8; ++w) {
+            q += ws[w][lane];
+            a += wa[w][lane];
+        }
         // the tensor-core path accumulates c Q (packed operand scaled by c); 1/c is exact
         const double inv_c = d.scaled ? 1.0 / (double)packed_scale(bt.ctr[t]) : 1.0;
-        if (c < d.ncols) bt.stats[d.col0 + c] = d.sign * (d.cT * (q * inv_c) + bSt * d.inv_o2);
+        if (c < d.ncols) {
+            bt.stats[d.col0 + c] = d.sign * (d.cT * (q * inv_c) + bSt * d.inv_o2);
+            // accumulation part of the error estimate (ept_internal.cuh, REFINE_KA)
+            if (bt.errest) bt.errest[d.col0 + c] = REFINE_KA * REFINE_U * d.cT * (a * inv_c);
+        }
     }
 }
 
@@ -984,12 +996,35 @@ __global__ void __launch_bounds__(256) k_batch_status(const Batch bt) {
 // buffer of permuted statistics is written only when the call will succeed (no
 // error in any test of the call, no expired wait), so that output buffers are
 // written only on success.
-__global__ void __launch_bounds__(256) k_combine_count(const Batch bt) {
+// With `flag` (the first count of a run), also the error criterion: statistic c is
+// flagged for FP64 recomputation when E_c > REFINE_TOL |stat_c| (ept_internal.cuh).
+__global__ void __launch_bounds__(256) k_combine_count(const Batch bt, int flag) {
+    __shared__ double bW;
     const int64_t gc = (int64_t)blockIdx.x * 256 + threadIdx.x;
     const int t = find_test(bt.pre.cols, bt.n_tests, (int64_t)blockIdx.x * 256);
     const TestDesc d = bt.desc[t];
     const int64_t c = gc - bt.pre.cols[t];
     const double obs = bt.stats[d.col0];
+    if (flag && bt.flags) {
+        if (threadIdx.x < 32) {
+            const double S = warp_ordered_sum(bt.Spart + d.sp0, d.n_pad / 32);
+            if (threadIdx.x == 0) bW = S * d.inv_n * d.inv_n;
+        }
+        __syncthreads();
+        int fl = 0;
+        if (c < d.ncols) {
+            const double v = bt.stats[d.col0 + c];
+            const double m = (double)d.m;
+            const double rep_obs = REFINE_KR * REFINE_U * fabs(bW) / sqrt(m);
+            const double e0 = bt.errest[d.col0] + rep_obs;
+            const bool aligned = c == 0 || fabs(v - obs) <= REFINE_TOL * fabs(obs) + 2.0 * e0;
+            const double e = bt.errest[d.col0 + c] + (aligned ? rep_obs : REFINE_KR * REFINE_U * fabs(bW) / m);
+            fl = !(e <= REFINE_TOL * fabs(v));   // NaN-safe: a non-finite estimate flags
+            bt.flags[d.col0 + c] = (uint8_t)fl;
+        }
+        fl = __syncthreads_count(fl);
+        if (threadIdx.x == 0 && fl) atomicAdd(&bt.ctr[t].n_flag, (unsigned long long)fl);
+    }
     int ge = 0, near = 0;
     if (c >= 1 && c < d.ncols) {
         const double v = bt.stats[d.col0 + c];
@@ -1012,12 +1047,25 @@ void launch_combine(const Batch &b, cudaStream_t s) {
     if (b.ncols_total <= 0) return;
     if (b.n_tests > 1) k_batch_status<<<1, 256, 0, s>>>(b);
     k_combine_stats<<<(unsigned)(b.ncols_total / 32), 256, 0, s>>>(b);
-    k_combine_count<<<(unsigned)(b.ncols_total / 256), 256, 0, s>>>(b);
+    k_combine_count<<<(unsigned)(b.ncols_total / 256), 256, 0, s>>>(b, 1);
 }
 
 void launch_combine_count(const Batch &b, cudaStream_t s) {
     if (b.ncols_total <= 0) return;
-    k_combine_count<<<(unsigned)(b.ncols_total / 256), 256, 0, s>>>(b);
+    k_combine_count<<<(unsigned)(b.ncols_total / 256), 256, 0, s>>>(b, 0);
+}
+
+__global__ void k_reset_counts(Counters *ctr, int n_tests) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n_tests) {
+        ctr[t].n_ge = 0;
+        ctr[t].n_near = 0;
+    }
+}
+
+void launch_reset_counts(const Batch &b, cudaStream_t s) {
+    if (b.n_tests <= 0) return;
+    k_reset_counts<<<(unsigned)((b.n_tests + 255) / 256), 256, 0, s>>>(b.ctr, b.n_tests);
 }
 
 // ---------------------------------------------------------------------------

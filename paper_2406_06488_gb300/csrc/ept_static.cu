@@ -104,10 +104,13 @@ __global__ void k_static_tables(const TestDesc d, TestDesc *desc, int64_t *pre, 
             pre[2 * k] = 0;
             pre[2 * k + 1] = tot[k];
         }
-        int q = 0;
-        for (int I = 0; I < d.NP; ++I)
-            for (int kb = KB_PER_PANEL * I; kb < d.NKB; kb += CHUNK_KB_DEFAULT)
-                chunks[q++] = Chunk{I, kb, (kb + CHUNK_KB_DEFAULT < d.NKB) ? kb + CHUNK_KB_DEFAULT : (int)d.NKB, 0};
+        // the chunk table of ept_test's planner (chunks end at the last K-block with real
+        // columns), at the default unit length
+        int64_t q = 0;
+        for (int64_t I = 0; I < d.NP; ++I) {
+            const int64_t nq = panel_chunks(d, I, CHUNK_KB_DEFAULT);
+            for (int64_t k = 0; k < nq; ++k) chunks[q++] = panel_chunk(d, I, k, CHUNK_KB_DEFAULT);
+        }
     }
 }
 
@@ -168,48 +171,14 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
         return err(EPT_EINVAL, "unknown statistic %d", stat);
     if (stat != EPT_STAT_ED && !(sigma > 0.0 && sigma < 1e300))
         return err(EPT_EINVAL, "MMD needs a finite bandwidth sigma > 0 (ept_test_static has no median heuristic)");
-    // the test, described as a batch of one (same layout rules as ept_test)
+    // the test, described by ept_test's planner as a batch of one
     TestDesc d;
-    memset(&d, 0, sizeof(d));
+    describe_test(d, nx, ny, p, B, stat, sigma, seed, true);
     d.X = X;
     d.Y = Y;
     d.out_stats = perm_stats;
-    d.nx = nx;
-    d.ny = ny;
-    d.n = nx + ny;
-    d.p = p;
-    d.B = B;
-    d.n_pad = (d.n + PANEL - 1) / PANEL * PANEL;
-    d.NP = d.n_pad / PANEL;
-    d.NKB = d.n_pad / KB;
-    d.nblk = blk_off(d.NP, d.NKB);
-    d.nw = d.n_pad / 32;
-    d.nwu = (int)((d.n + 31) / 32);
-    d.ncols = B + 1;
-    d.Bp = (d.ncols + COL_PAD - 1) / COL_PAD * COL_PAD;
-    d.MT = d.Bp / TC_TILE_N;
-    for (int64_t I = 0; I < d.NP; ++I) d.nchunks += (d.NKB - KB_PER_PANEL * I + CHUNK_KB_DEFAULT - 1) / CHUNK_KB_DEFAULT;
+    for (int64_t I = 0; I < d.NP; ++I) d.nchunks += panel_chunks(d, I, CHUNK_KB_DEFAULT);
     d.nparts = 2 * d.nchunks;
-    d.scaled = 1;
-    d.p_pad = (p + BUILD_KB - 1) / BUILD_KB * BUILD_KB;
-    d.kblocks = (int)(d.p_pad / BUILD_KB);
-    d.comp = ny < nx;
-    d.m = d.comp ? ny : nx;
-    d.other = d.comp ? nx : ny;
-    d.stat = stat;
-    d.seed = seed;
-    d.b0 = 1;
-    d.kern = stat;
-    d.neg_inv_2s2 = (stat == EPT_STAT_MMD_GAUSS) ? (float)(-1.0 / (2.0 * sigma * sigma)) : 0.f;
-    d.inv_sigma = (stat == EPT_STAT_MMD_LAPLACE) ? (float)(1.0 / sigma) : 0.f;
-    d.tau = 1.f / 4.f;
-    const double fn = (double)d.n, q = fn / ((double)nx * (double)ny);
-    d.cT = q * q;
-    d.inv_o2 = 1.0 / ((double)d.other * (double)d.other);
-    d.sign = (stat == EPT_STAT_ED) ? -1.0 : 1.0;
-    d.kappa = 2.0 * (double)d.m / fn;
-    d.inv_n = 1.0 / fn;
-    d.inv_2n2 = 1.0 / (2.0 * fn * fn);
     const StaticPlan P = static_plan(d);
     if (P.total > (size_t)EPT_STATIC_SCRATCH_BYTES)
         return err(EPT_EINVAL,
@@ -297,6 +266,7 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     out->ms_build = out->ms_perm = out->ms_masks = out->ms_contract = 0.0;
     out->sigma = (stat == EPT_STAT_ED) ? 0.0 : sigma;
     out->n_windows = 0;
+    out->n_refined = 0;   // no FP64 refinement here (it needs scratch beyond the array)
     out->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     return EPT_OK;
 }

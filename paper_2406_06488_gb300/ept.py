@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libept.so")
 
 STAT = {"ed": 0, "mmd": 1, "mmd_gauss": 1, "mmd_laplace": 2}
 SIGMA_MEDIAN = -1.0   # EPT_SIGMA_MEDIAN: bandwidth from the median heuristic
-ABI_VERSION = 3       # EPT_ABI_VERSION this binding's structures follow
+ABI_VERSION = 4       # EPT_ABI_VERSION this binding's structures follow
 PREC = {"plain_fp32": 0, "split_bf16": 1, "pooled_fp32": 2}   # pooled_fp32: Algorithm 5 baseline
 STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT_ECUDA", 5: "EPT_ETIMEOUT",
           6: "EPT_ECANCELLED", 7: "EPT_ENOTFOUND", 8: "EPT_EUNSUPPORTED", 9: "EPT_EINTERNAL"}
@@ -50,7 +50,8 @@ class _Result(ctypes.Structure):
     _fields_ = [("observed", ctypes.c_double), ("p_value", ctypes.c_double), ("n_ge", ctypes.c_int64),
                 ("n_near_tie", ctypes.c_int64), ("n_fixup", ctypes.c_int64), ("ms_build", ctypes.c_double),
                 ("ms_perm", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_masks", ctypes.c_double),
-                ("ms_contract", ctypes.c_double), ("sigma", ctypes.c_double), ("n_windows", ctypes.c_int64)]
+                ("ms_contract", ctypes.c_double), ("sigma", ctypes.c_double), ("n_windows", ctypes.c_int64),
+                ("n_refined", ctypes.c_int64)]
 
 
 class _PlanInfo(ctypes.Structure):
@@ -82,12 +83,13 @@ class Result:
     ms_contract: float
     sigma: float
     n_windows: int = 0
+    n_refined: int = 0
     stats: Optional[object] = field(default=None, repr=False)
 
 
 def _result(r, buf) -> "Result":
     return Result(r.observed, r.p_value, r.n_ge, r.n_near_tie, r.n_fixup, r.ms_build, r.ms_perm, r.ms_total,
-                  r.ms_masks, r.ms_contract, r.sigma, r.n_windows, buf)
+                  r.ms_masks, r.ms_contract, r.sigma, r.n_windows, r.n_refined, buf)
 
 
 _lib = None
@@ -200,7 +202,7 @@ def plan_check(shapes, unit_kb: int = 8, num_sms: int = 152, stream_blocks: int 
 
 OPTION = {"graphs": 1, "autotune": 2, "serve_lanes": 3, "serve_slots": 4, "draw_mode": 5,
           "fault_inject_alloc": 6, "fault_inject_stall": 7, "debug_checks": 8, "stream_blocks": 9,
-          "wait_limit_ms": 10, "max_chunk": 11}
+          "wait_limit_ms": 10, "max_chunk": 11, "refine": 12}
 
 
 class Context:

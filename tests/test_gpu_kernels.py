@@ -105,10 +105,12 @@ def test_full_size_mmd_median_sampled(ctx):
     X, Y = workloads.gaussian_pair(spec)
     res = ctx.test(X, Y, B=2000, seed=spec.seed, stat=spec.stat, sigma="median")
     st = np.asarray(res.stats)
-    for b in (1, 2000):
+    obs = oracle.stat_select(X, Y, oracle.perm_select(spec.seed, spec.nx, spec.ny, 0, 1)[0], spec.stat, res.sigma)
+    assert abs(res.observed - obs) <= REL_TOL * abs(obs)
+    for b in list(range(1, 16)) + [2000]:
         sel = oracle.perm_select(spec.seed, spec.nx, spec.ny, b, 1)[0]
         v = oracle.stat_select(X, Y, sel, spec.stat, res.sigma)
-        assert abs(st[b - 1] - v) <= REL_TOL * abs(v)
+        assert abs(st[b - 1] - v) <= REL_TOL * abs(v), (b, st[b - 1], v)
     W = np.concatenate([X, Y]).astype(np.float64)
     r = np.random.default_rng(0)
     i, j = r.integers(0, W.shape[0], 200000), r.integers(0, W.shape[0], 200000)

@@ -217,6 +217,11 @@ def _full_size_check(ctx, spec, sample_draws):
     for prec in PRECS:
         res = ctx.test(X, Y, B=spec.B, seed=spec.seed, stat=spec.stat, sigma=spec.sigma, prec=prec)
         st = np.asarray(res.stats)
+        worst = abs(res.observed - obs_ref) / abs(obs_ref)
+        for b, v in sampled.items():
+            worst = max(worst, abs(st[b - 1] - v) / abs(v))
+        print("%s %s: largest relative error over the observed and %d sampled statistics %.3g"
+              % (spec.stat, prec, len(sampled), worst))
         assert abs(res.observed - obs_ref) <= REL_TOL * abs(obs_ref), (prec, res.observed, obs_ref)
         for b, v in sampled.items():
             assert abs(st[b - 1] - v) <= REL_TOL * abs(v), (prec, b, st[b - 1], v)
@@ -243,8 +248,10 @@ def test_full_size_highdim_every_statistic(ctx):
 
 
 def test_full_size_mmd(ctx):
-    # Gaussian MMD, nx = ny = 10000, p = 100, Y ~ N(0, 1.1 I), sigma = 10, B = 10000
-    _full_size_check(ctx, workloads.MMD, [1, 10000])
+    # Gaussian MMD, nx = ny = 10000, p = 100, Y ~ N(0, 1.1 I), sigma = 10, B = 10000:
+    # the observed statistic and draws 1..64 against the direct recomputation, plus
+    # the last draw, on both precisions
+    _full_size_check(ctx, workloads.MMD, list(range(1, 65)) + [10000])
 
 
 @pytest.mark.parametrize("prec", PRECS)

@@ -3,14 +3,19 @@ fixed device array inside the library), for callers that cannot call cudaMalloc 
 for example an application whose own memory pool owns the whole GPU, or a
 latency-critical loop that must not enter the allocator.
 
-Called through the C ABI with device buffers, it must give the statistics of the
-allocating entry point (ept_test, split-BF16 path) within the tolerance of the
-other parity tests, on two calls in a row (the second call reuses the array the
-first one left behind), and reject tests too large for its array."""
+Called through the C ABI with device buffers, on two calls in a row (the second
+call reuses the array the first one left behind), its statistics must match the
+FP64 oracle (Algorithm 1 on the three blocks, Section 3.1 p-value) within the
+tolerance of the other parity tests and the allocating entry point's own results;
+a warmed call must leave the device's free memory unchanged; a failing call (NaN
+input) must leave the output buffer untouched; a test too large for the array is
+rejected."""
 import ctypes
 
 import numpy as np
 import pytest
+
+import oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -26,7 +31,7 @@ def _call_static(lib, ept, Xd, Yd, B, seed, stat, sigma, out):
     return st, r
 
 
-def test_static_entry_point_matches_allocating_one():
+def test_static_entry_point_matches_the_oracle():
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -39,22 +44,46 @@ def test_static_entry_point_matches_allocating_one():
     ]
     with ept.Context(0) as ctx:
         for spec, stat, sigma in cases:   # two calls in a row, different shapes
+            name = ["ed", "mmd"][stat]
             X, Y = workloads.gaussian_pair(spec)
+            ref = oracle.permutation_test(X, Y, B=spec.B, seed=spec.seed, stat=name, sigma=sigma, method="blocks")
             Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
-            ref = ctx.test(Xd, Yd, B=spec.B, seed=spec.seed, stat=["ed", "mmd"][stat], sigma=sigma,
-                           prec="split_bf16")
-            ref_stats = ref.stats.cpu().numpy()
             out = torch.full((spec.B,), float("nan"), dtype=torch.float64, device="cuda")
             st, r = _call_static(lib, ept, Xd, Yd, spec.B, spec.seed, stat, sigma, out)
             assert st == 0, lib.ept_last_error()
             torch.cuda.synchronize()
             got = out.cpu().numpy()
-            rel = np.abs(got - ref_stats) / np.abs(ref_stats)
-            assert rel.max() <= REL_TOL
-            assert abs(r.observed - ref.observed) <= REL_TOL * abs(ref.observed)
-            near = int(np.count_nonzero(np.abs(ref_stats - ref.observed) <= 1e-5 * abs(ref.observed)))
-            assert abs(r.n_ge - ref.n_ge) <= near
+            rel = np.abs(got - ref["stats"]) / np.abs(ref["stats"])
+            assert rel.max() <= REL_TOL, rel.max()
+            assert abs(r.observed - ref["observed"]) <= REL_TOL * abs(ref["observed"])
+            near = int(np.count_nonzero(np.abs(ref["stats"] - ref["observed"]) <= 1e-5 * abs(ref["observed"])))
+            assert abs(r.n_ge - ref["n_ge"]) <= near
             assert r.p_value == (1.0 + r.n_ge) / (1.0 + spec.B)
+            # the allocating entry point on the same device inputs agrees as well
+            alloc = ctx.test(Xd, Yd, B=spec.B, seed=spec.seed, stat=name, sigma=sigma, prec="split_bf16")
+            a = alloc.stats.cpu().numpy()
+            assert (np.abs(got - a) / np.abs(a)).max() <= REL_TOL
+
+        # a warmed call allocates nothing: the device's free memory is the same after it
+        spec, stat, sigma = cases[0]
+        X, Y = workloads.gaussian_pair(spec)
+        Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+        out = torch.empty(spec.B, dtype=torch.float64, device="cuda")
+        assert _call_static(lib, ept, Xd, Yd, spec.B, spec.seed, stat, sigma, out)[0] == 0
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        assert _call_static(lib, ept, Xd, Yd, spec.B, spec.seed, stat, sigma, out)[0] == 0
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+
+        # a failing call leaves the output untouched
+        Xbad = Xd.clone()
+        Xbad[3, 1] = float("nan")
+        keep = torch.full((spec.B,), float("nan"), dtype=torch.float64, device="cuda")
+        st, _ = _call_static(lib, ept, Xbad, Yd, spec.B, spec.seed, stat, sigma, keep)
+        assert st == 1
+        torch.cuda.synchronize()
+        assert torch.isnan(keep).all()
 
     # a test whose scratch does not fit in the fixed array is refused, not truncated
     X, Y = workloads.gaussian_pair(workloads.TwoSampleSpec(nx=3000, ny=3000, p=8))
