@@ -67,6 +67,8 @@ def _args():
     ap.add_argument("--plain-steps", type=int, default=5)
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="highdim: skip the bounded MMD, batched and serving sub-objects of the line")
     ap.add_argument("--profile", action="store_true",
                     help="run only --warmup + 1 tuned steps (a short program to capture under ncu)")
     return ap.parse_args()
@@ -173,6 +175,15 @@ def _spec(name):
     return workloads.NAMED[name]
 
 
+def _workload_name(name, spec):
+    """The workload's description, the same string on both arms of the bench."""
+    if name == "highdim":
+        return ("highdim ED test: nx=%d ny=%d p=%d B=%d, X~N(0,I), Y~N(mu,I) mu=0.05 on first 50 coords"
+                % (spec.nx, spec.ny, spec.p, spec.B))
+    return "%s: %s nx=%d ny=%d p=%d B=%d sigma=%s" % (name, spec.stat, spec.nx, spec.ny, spec.p, spec.B,
+                                                      "median" if spec.sigma < 0 else spec.sigma)
+
+
 def _oracle_sigma(spec, gpu_sigma=None):
     """Bandwidth for the oracle's timing runs: the workload's, or for the median
     heuristic the value the GPU selected (else sqrt(p))."""
@@ -276,8 +287,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "%s: %s nx=%d ny=%d p=%d B=%d" % (args.workload, spec.stat.upper(), spec.nx,
-                                                                      spec.ny, spec.p, spec.B),
+            "config": {"workload": (_workload_name(args.workload, spec) if args.workload not in ("batched", "serving")
+                                    else "%s: one ED test of the batched mix nx=%d ny=%d p=%d B=%d"
+                                    % (args.workload, spec.nx, spec.ny, spec.p, spec.B)),
                        "reference": "FP64 CPU oracle, one permuted statistic per step"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": "one relabeling per step (draws %d..%d), direct FP64 recomputation "
@@ -323,8 +335,10 @@ def run_ours(args):
         ctx.close()
         return 0
 
-    # ---- tuned path, inputs resident on the device (graph replay after the first call)
-    for _ in range(args.warmup):
+    # ---- tuned path, inputs resident on the device (graph replay after the first call;
+    # the first call of the shape runs the autotuner)
+    first = step("split_bf16")
+    for _ in range(max(args.warmup - 1, 0)):
         step("split_bf16")
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
@@ -421,10 +435,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tot_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f16", "data": "synthetic",
-        "config": {"workload": "highdim ED test: nx=%d ny=%d p=%d B=%d, X~N(0,I), Y~N(mu,I) mu=0.05 on first 50 "
-                               "coords" % (spec.nx, spec.ny, spec.p, spec.B) if args.workload == "highdim"
-                   else "%s: %s nx=%d ny=%d p=%d B=%d sigma=%s" % (args.workload, spec.stat, spec.nx, spec.ny, spec.p,
-                                                                 spec.B, "median" if spec.sigma < 0 else spec.sigma),
+        "config": {"workload": _workload_name(args.workload, spec),
                    "precision": "blocks FP32, contraction FP16 hi+lo split on tcgen05, FP32 accumulate, FP64 "
                                 "combine", "l2": "flushed between steps (256 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -446,8 +457,13 @@ def run_ours(args):
         "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clocks,
         "result": {"observed": last.observed, "p_value": last.p_value, "n_near_tie": last.n_near_tie,
-                   "sigma": last.sigma},
+                   "sigma": last.sigma, "n_refined": last.n_refined},
+        "autotune": _tuning(first),
     }
+    if args.workload == "highdim" and not args.no_extras and ws == 1:
+        line["mmd"] = _extra_mmd(ctx, flush, peaks)
+        line["batched"] = _extra_batched(ctx, flush, args)
+        line["serving"] = _extra_serving(local, args)
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if paper_cpu is not None:
@@ -460,6 +476,123 @@ def run_ours(args):
 def _p99(xs):
     xs = sorted(xs)
     return xs[min(len(xs) - 1, int(np.ceil(0.99 * len(xs))) - 1)]
+
+
+def _tuning(res):
+    """The autotuner's choice for a run (ept_result.tuning) and the candidates it timed."""
+    code = int(res.tuning)
+    return {"unit_kblocks": code // 100, "draw_kernel": ["auto", "warp per column", "thread per column"][code // 10 % 10],
+            "unit_order": ["auto", "by length", "by first K-block"][code % 10],
+            "candidates_timed": int(res.tune_candidates)}
+
+
+def _timed(fn, flush, steps):
+    """CUDA-event times (ms) of `steps` calls of fn on the current stream, L2 flushed
+    before each; returns (times, last result)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ms, last = [], None
+    for k in range(steps):
+        flush.fill_(float(k))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        last = fn()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms, last
+
+
+def _extra_mmd(ctx, flush, peaks, steps=10, plain_steps=2):
+    """The Gaussian-MMD workload (nx = ny = 10000, p = 100, Y ~ N(0, 1.1 I), sigma = 10,
+    B = 10000), bounded: tuned and plain steps, the contraction's fraction of peak."""
+    import torch
+    from paper_2406_06488_gb300 import workloads
+    spec = workloads.MMD
+    X, Y = workloads.gaussian_pair(spec)
+    Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
+
+    def run(prec):
+        return ctx.test(Xd, Yd, B=spec.B, seed=spec.seed, stat=spec.stat, sigma=spec.sigma, prec=prec)
+    for _ in range(3):
+        run("split_bf16")
+    ms, last = _timed(lambda: run("split_bf16"), flush, steps)
+    ctx.set_option("graphs", 0)
+    contract = statistics.mean(run("split_bf16").ms_contract for _ in range(3))
+    ctx.set_option("graphs", 1)
+    # the same steps without the recomputation of flagged statistics (its cost)
+    ctx.set_option("refine", 0)
+    run("split_bf16")
+    oms, _ = _timed(lambda: run("split_bf16"), flush, steps)
+    ctx.set_option("refine", 1)
+    run("plain_fp32")
+    pms, _ = _timed(lambda: run("plain_fp32"), flush, plain_steps)
+    n = spec.nx + spec.ny
+    alg = 2.0 * (n * (n + 1) // 2) * (spec.B + 1)
+    peak = float(peaks.get("bf16_tflops", 1900.0))
+    del Xd, Yd
+    return {"workload": _workload_name("mmd", spec), "value": spec.B / (statistics.mean(ms) / 1000.0), "unit": UNIT,
+            "ms_per_step": statistics.mean(ms), "p50_ms": statistics.median(ms), "p99_ms": _p99(ms), "steps": steps,
+            "n_refined": last.n_refined,
+            "without_recomputation": {"value": spec.B / (statistics.mean(oms) / 1000.0),
+                                      "ms_per_step": statistics.mean(oms), "p99_ms": _p99(oms)},
+            "plain_fp32": {"value": spec.B / (statistics.mean(pms) / 1000.0), "ms_per_step": statistics.mean(pms),
+                           "p99_ms": _p99(pms), "steps": plain_steps},
+            "contract_ms": contract, "contract_frac": alg / (contract / 1000.0) / 1e12 / peak}
+
+
+def _extra_batched(ctx, flush, args, steps=5):
+    """The batched workload (512 uneven ED tests, B = 5000, one graph-replayed batched
+    run per step), bounded: tuned and plain steps."""
+    import torch
+    specs, tests = _batched_tests(512)
+    dev = [dict(t, X=torch.from_numpy(t["X"]).cuda(), Y=torch.from_numpy(t["Y"]).cuda()) for t in tests]
+    total_B = sum(t["B"] for t in tests)
+    pb = ctx.prepare_batch(dev)
+    first = pb.run()[0]
+    for _ in range(2):
+        pb.run()
+    ms, last = _timed(pb.run, flush, steps)
+    plain = ctx.prepare_batch(dev, prec="plain_fp32")
+    plain.run()
+    pms, _ = _timed(plain.run, flush, 1)
+    del dev, pb, plain
+    return {"workload": "batched: 512 independent ED tests, nx, ny ~ U{50..2000}, p ~ U{20..500}, half null / half "
+                        "Y mean 0.1, B=5000 each, one batched run per step replayed from a CUDA graph",
+            "value": total_B / (statistics.mean(ms) / 1000.0), "unit": UNIT, "ms_per_step": statistics.mean(ms),
+            "p50_ms": statistics.median(ms), "p99_ms": _p99(ms), "steps": steps,
+            "n_refined": int(sum(r.n_refined for r in last)), "autotune": _tuning(first),
+            "plain_fp32": {"value": total_B / (statistics.mean(pms) / 1000.0), "ms_per_step": statistics.mean(pms),
+                           "steps": len(pms)}}
+
+
+def _extra_serving(device, args, rates=(10.0, 100.0), requests=(20, 40), plain_requests=12):
+    """The serving workload, bounded: Poisson arrivals at two rates (p50 / p99 latency
+    from submit to completion, permuted statistics per second over the stream), and
+    the plain FP32 path served at the first rate."""
+    from paper_2406_06488_gb300 import ept, workloads
+    pools = _serving_data()
+    ctx = ept.Context(device, budget_bytes=150 << 30)
+    warm = workloads.serving_requests(1000.0, 8, master_seed=99)
+    _serve_once(ctx, [(0.0, sp) for _, sp in warm], pools, "split_bf16")
+    out = []
+    for k, (rate, n) in enumerate(zip(rates, requests)):
+        reqs = workloads.serving_requests(rate, n, master_seed=k + 1)
+        lat, stats_n, wall = _serve_once(ctx, reqs, pools, "split_bf16")
+        out.append({"rate_per_s": rate, "requests": n, "stats_per_s": stats_n / wall, "p50_ms": statistics.median(lat),
+                    "p99_ms": _p99(lat)})
+    ctx.close()
+    pctx = ept.Context(device, budget_bytes=150 << 30)
+    reqs = workloads.serving_requests(rates[0], plain_requests, master_seed=1)
+    lat, stats_n, wall = _serve_once(pctx, reqs, pools, "plain_fp32")
+    pctx.close()
+    return {"workload": "serving: Poisson ED/MMD requests, nx, ny log-uniform [100, 20000], p log-uniform "
+                        "[10, 2000], B in {1000, 5000, 20000}, 150 GB admission budget; latency on the host clock "
+                        "from submit to completion",
+            "rates": out,
+            "plain_fp32": {"rate_per_s": rates[0], "requests": plain_requests, "stats_per_s": stats_n / wall,
+                           "p50_ms": statistics.median(lat), "p99_ms": _p99(lat)}}
 
 
 def _batched_tests(n_tests=512, B=5000):

@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define EPT_ABI_VERSION 4
+#define EPT_ABI_VERSION 5
 
 typedef enum {
     EPT_OK = 0,
@@ -115,6 +115,13 @@ typedef struct {
                              error estimate exceeded 1e-5 of their value and that were
                              recomputed in FP64 from the raw rows (EPT_OPT_REFINE); with
                              EPT_OPT_REFINE = 0, the number that would have been */
+    int64_t tuning;       /* parameters of the tensor-core run: 100 x unit length in K-blocks
+                             + 10 x relabeling-draw kernel (0 automatic, 1 a warp per
+                             column, 2 a thread per column) + unit order (0 automatic,
+                             1 by length, 2 by first K-block); 0 for other paths */
+    int64_t tune_candidates; /* parameter sets the autotuner timed in this call (its first
+                             call of a batch shape); 0 when the parameters came from its
+                             cache or were not tuned */
 } ept_result;
 
 /* Library ABI version (EPT_ABI_VERSION of the build). */
@@ -258,7 +265,15 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
 /* Context options (ept_set_option).  EPT_OPT_GRAPHS (default 1): capture and
    replay CUDA graphs of repeated batches; with 0 every run is launched directly
    and the per-phase times of ept_result are filled in.  EPT_OPT_AUTOTUNE (default
-   1 unless the environment sets EPT_AUTOTUNE=0): the contraction chunk autotuner.
+   1 unless the environment sets EPT_AUTOTUNE=0): the autotuner of tensor-core runs.
+   On the first call of a batch shape (several tests, or one test with (nx+ny)^2 B of
+   at least 2.5e10) it times whole device runs of the batch with each candidate
+   parameter set -- the defaults, the other relabeling-draw kernel, the other order
+   of the contraction's units (by length, or by first K-block then length), units of
+   4 K-blocks, and longer units where EPT_OPT_MAX_CHUNK allows them -- keeps the
+   fastest for the shape (ept_result.tuning, .tune_candidates) and uses it from then
+   on; every candidate computes the same statistics except for the accumulation
+   order that the unit length sets.
    EPT_OPT_DRAW_MODE (default 0): relabeling-draw kernel, 0 = automatic (a thread
    per column when the batch has at least 1024 columns per SM, else a warp per
    column), 1 = a warp per column, 2 = a thread per column; the draws are
@@ -313,10 +328,14 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    FP32 accumulations carried), Wbar the mean entry of the pooled matrix, g_b = 1/m
    for a relabeling and 1/sqrt(m) for the observed statistic and every statistic
    within 1e-5 |observed| + 2 E_0 of it (m = min(nx, ny)).  A statistic with
-   E_b > 1e-5 |stat_b| is recomputed from W built in FP64 by direct differences of the
-   widened inputs (Algorithm 3) and its three block sums in FP64; the counts are then
-   taken again.  The run needs extra device memory for it (8 n bytes per row of a
-   window of at most 2 GiB, 16 bytes per 64 rows and flagged statistic).  Flagged
+   E_b > 1e-5 |stat_b| is recomputed: when its representation term (the second) is
+   above 1/20 of the tolerance, from W built in FP64 by direct differences of the
+   widened inputs (Algorithm 3) and its three block sums in FP64; otherwise by summing
+   the packed operand the contraction read with compensated arithmetic (which
+   removes the FP32 accumulation error and keeps the entries).  The counts are then
+   taken again.  The run needs extra device memory for it (8 bytes per row panel and
+   re-summed statistic; for the FP64 rebuild 8 n bytes per row of a window of at most
+   2 GiB and 16 bytes per 64 rows and statistic).  Flagged
    statistics arise on ill-conditioned inputs, such as a wide-kernel MMD of a few
    features whose permuted statistics are far below the FP32 resolution of the
    kernel values; ept_result.n_refined counts them.  Not applied in the streaming
@@ -377,6 +396,13 @@ ept_status ept_cancel(ept_ctx *ctx, uint64_t ticket);
    zero before the first ept_submit. */
 ept_status ept_serving_stats(ept_ctx *ctx, size_t *bytes_in_use, int64_t *running, int64_t *queued,
                              int64_t *finished);
+
+/* Serving lanes (any pointer may be NULL): lanes holding a running batch now, the
+   most lanes that held one at the same time since the context's first ept_submit,
+   and the number of requests submitted while at least one lane held a running batch
+   (requests that arrived while others were on the GPU).  All zero before the first
+   ept_submit. */
+ept_status ept_serving_lanes(ept_ctx *ctx, int64_t *busy, int64_t *peak_busy, int64_t *submits_while_busy);
 
 /* Draws b0 .. b0+count-1 of the permutation stream of `seed` (Algorithm 2's
    SampleWithoutReplacement, fixed as Philox4x32-10 + Knuth's selection sampling;

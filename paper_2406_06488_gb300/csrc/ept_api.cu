@@ -55,7 +55,6 @@ inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 // pairs with d^2 < tau (||x||^2 + ||y||^2) are recomputed directly in FP64: the norm
 // expansion amplifies rounding by at most 1/tau on the pairs it keeps
 const double NEAR_DUP_TAU = 1.0 / 4.0;
-const int CHUNK_CANDIDATES[3] = {8, 16, 32};
 // relabeling masks above this size (a quarter of the L2) change the contraction's unit order
 const int64_t MASKS_IN_L2_BYTES = (int64_t)32 << 20;
 
@@ -69,6 +68,17 @@ struct TestSpec {
     int64_t b0 = 1;               // first draw of the stream (column 1)
     const uint32_t *user_masks;   // B relabelings (ept_test_masks), same memory space as X
     double *perm_stats;           // B doubles or null, same memory space as X
+};
+
+// The tunable parameters of a run: contraction unit length in K-blocks, the
+// relabeling-draw kernel (0 automatic, DRAW_WARPS, DRAW_LANES) and the order of the
+// contraction schedule's units (0 automatic, 1 by length, 2 by first K-block, then
+// length).  Every choice computes the same statistics bit for bit except the unit
+// length, which changes the FP32 accumulation order (every length offered keeps the
+// error criterion's calibration, at most 8 K-blocks unless EPT_OPT_MAX_CHUNK allows more).
+struct Tuning {
+    int chunk_kb = CHUNK_KB_DEFAULT, draw_mode = 0, order = 0;
+    int64_t code() const { return (int64_t)chunk_kb * 100 + draw_mode * 10 + order; }
 };
 
 ept_status validate(int64_t nx, int64_t ny, int64_t p, int stat, double sigma, int prec, bool single = false) {
@@ -101,6 +111,7 @@ struct Plan {
     std::vector<Chunk> chunks;
     std::vector<int64_t> sched, sched_off;   // contraction schedule: units of CTA c = sched[sched_off[c] ..)
     bool user_masks = false;                 // some test brings its own relabelings
+    int draw_mode = 0;                       // relabeling-draw kernel of the run (0: the context's choice)
     bool any_median = false;                 // some test takes its bandwidth from the median heuristic
     bool debug = false;                      // guard bands around the scratch regions
     GuardList guards{};
@@ -158,7 +169,9 @@ void set_test_params(TestDesc &d, const TestSpec &s) {
 // the mask words of nearby K-ranges across panels (in panel order every panel
 // sweeps all of the masks: measured at n = 60,000, 22.8 GB of DRAM reads for 7.3 GB
 // of operand, 18.6 GB in K-block order; the smaller bench shapes are unchanged).
-void plan_schedule(Plan &P, int num_sms) {
+// order: 0 automatic (by first K-block only when the masks outgrow a quarter of L2),
+// 1 by length alone, 2 by first K-block, then length.
+void plan_schedule(Plan &P, int num_sms, int unit_order = 0) {
     P.sched.clear();
     P.sched_off.clear();
     P.tc_grid = 0;
@@ -185,6 +198,7 @@ void plan_schedule(Plan &P, int num_sms) {
     // length, longest first
     bool big_masks = false;
     for (const TestDesc &d : P.desc) big_masks |= d.nw * d.Bp * 4 > MASKS_IN_L2_BYTES;
+    if (unit_order != 0) big_masks = unit_order == 2;
     std::vector<int64_t> by_kb((size_t)P.nunits);
     if (!big_masks) {
         for (int64_t u = 0; u < P.nunits; ++u) by_kb[(size_t)u] = u;
@@ -213,7 +227,7 @@ void plan_schedule(Plan &P, int num_sms) {
 }
 
 void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host_in, int chunk_kb,
-                int num_sms = 160, bool debug = false, bool schedule = true) {
+                int num_sms = 160, bool debug = false, bool schedule = true, int order = 0) {
     P = Plan();
     P.debug = debug;
     P.n_tests = (int)specs.size();
@@ -270,7 +284,7 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
     }
     P.ncols_pad = P.pre_cols.back();
     P.nunits = P.pre_units.back();
-    if (tc && schedule) plan_schedule(P, num_sms);
+    if (tc && schedule) plan_schedule(P, num_sms, order);
     P.nsimt = P.pre_simt.back();
     P.in_bytes = in_bytes;
 
@@ -537,7 +551,7 @@ struct ept_ctx {
     uint8_t *pinned = nullptr;
     size_t pinned_cap = 0;
     GraphCache graph;
-    std::map<std::vector<int64_t>, int> tuned_chunk;   // autotuner cache: batch shape -> chunk length
+    std::map<std::vector<int64_t>, Tuning> tuned;   // autotuner cache: batch shape -> parameters
     bool autotune = true;
     bool graphs = true;                 // replay captured graphs of repeated batches
     bool debug = false;                 // guard bands around scratch regions, plan invariants checked
@@ -545,7 +559,9 @@ struct ept_ctx {
     int64_t stream_blocks = 0;          // streaming mode: 0 automatic, k > 0 windows of <= k blocks, -1 never
     unsigned long long wait_ns = 0;     // limit of the kernels' bounded waits (0: their default, 2 s)
     int max_chunk = CHUNK_KB_DEFAULT;   // longest contraction unit the autotuner may pick (precision)
-    bool refine = true;                 // recompute flagged statistics in FP64 (EPT_OPT_REFINE)
+    bool refine = true;                 // recompute flagged statistics (EPT_OPT_REFINE)
+    uint8_t *refine_buf = nullptr;      // scratch of the recomputation (grows, kept until ept_destroy)
+    size_t refine_cap = 0;
     ept_allocator alloc{};              // caller-supplied device memory (alloc.alloc == nullptr: cudaMalloc)
     std::atomic<int> inject_alloc{0};   // test hook: the next N scratch acquisitions fail (host side)
     bool inject_stall = false;          // test hook: the next run's contraction waits out its limit
@@ -844,7 +860,7 @@ Batch device_view(ept_ctx *c, const Plan &P) {
 // when there are at least 1024 columns per SM; caller relabelings always take the
 // warp kernel (it validates them)
 int draw_mode_for(const ept_ctx *c, const Plan &P) {
-    int mode = c->draw_mode;
+    int mode = P.draw_mode ? P.draw_mode : c->draw_mode;
     if (mode == 0)
         mode = (!P.user_masks && P.ncols_pad >= DRAW_LANES_MIN_COLS_PER_SM * (int64_t)c->num_sms) ? DRAW_LANES
                                                                                                   : DRAW_WARPS;
@@ -1015,6 +1031,8 @@ ept_status collect(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &specs
         r.ms_contract = ms_contract;
         r.n_windows = P.stream ? (int64_t)P.gI0.size() : 0;
         r.n_refined = (int64_t)ctr[t].n_flag;
+        r.tuning = 0;
+        r.tune_candidates = 0;
         if (P.host_in && specs[t].perm_stats && d.B > 0)
             memcpy(specs[t].perm_stats, stats + d.col0 + 1, (size_t)d.B * 8);
     }
@@ -1054,8 +1072,8 @@ void save_tune_file(ept_ctx *c) {
     if (c->tune_file.empty()) return;
     FILE *f = fopen(c->tune_file.c_str(), "w");
     if (!f) return;
-    for (auto &kv : c->tuned_chunk) {
-        fprintf(f, "%d", kv.second);
+    for (auto &kv : c->tuned) {
+        fprintf(f, "%d %d %d", kv.second.chunk_kb, kv.second.draw_mode, kv.second.order);
         for (int64_t v : kv.first) fprintf(f, " %lld", (long long)v);
         fprintf(f, "\n");
     }
@@ -1069,27 +1087,58 @@ void load_tune_file(ept_ctx *c) {
     char line[1 << 16];
     while (fgets(line, sizeof(line), f)) {
         char *p = line, *end = nullptr;
-        const long chunk = strtol(p, &end, 10);
-        if (end == p) continue;
+        long head[3];
+        int k = 0;
+        for (; k < 3; ++k) {
+            head[k] = strtol(p, &end, 10);
+            if (end == p) break;
+            p = end;
+        }
+        if (k < 3) continue;
         std::vector<int64_t> key;
-        p = end;
         for (;;) {
             const long long v = strtoll(p, &end, 10);
             if (end == p) break;
             key.push_back(v);
             p = end;
         }
-        if (chunk == 8 || chunk == 16 || chunk == 32) c->tuned_chunk[key] = (int)chunk;
+        Tuning tn;
+        tn.chunk_kb = (int)head[0];
+        tn.draw_mode = (int)head[1];
+        tn.order = (int)head[2];
+        const bool ok = (tn.chunk_kb == 4 || tn.chunk_kb == 8 || tn.chunk_kb == 16 || tn.chunk_kb == 32) &&
+                        tn.draw_mode >= 0 && tn.draw_mode <= 2 && tn.order >= 0 && tn.order <= 2;
+        if (ok) c->tuned[key] = tn;
     }
     fclose(f);
 }
 
-// FP64 recomputation of the statistics the error criterion flagged (ept_refine.cu),
-// after a finished run whose scratch is still in place: per test with flagged
-// columns, the list of its flagged columns, W64 in row windows of at most
-// REFINE_W64_BYTES, the statistics; then the counts again and the results read
-// back as the run itself does.  Statistics that were not flagged keep their values.
+// Recomputation of the statistics the error criterion flagged (ept_refine.cu), after
+// a finished run whose scratch is still in place: per test, the columns flagged for
+// an exact re-summation of the packed operand, then those flagged for entries rebuilt
+// in FP64 (W64 in row windows of at most REFINE_W64_BYTES); then the counts again and
+// the results read back as the run itself does.  Statistics that were not flagged
+// keep their values.
 const size_t REFINE_W64_BYTES = (size_t)2 << 30;
+
+// the recomputation's scratch: the context's buffer, grown when needed (the previous
+// recomputation has finished with it: it waits for its work before returning); kept
+// between calls up to 256 MiB
+ept_status refine_scratch(ept_ctx *c, size_t bytes, cudaStream_t s, uint8_t **out) {
+    if (bytes > c->refine_cap) {
+        if (c->refine_buf) device_free(c, c->refine_buf, s);
+        c->refine_buf = nullptr;
+        c->refine_cap = 0;
+        void *p = nullptr;
+        const size_t cap = align_up(bytes + bytes / 4, 1 << 20);
+        ept_status st = device_alloc(c, cap, s, &p);
+        if (st != EPT_OK) return st;
+        c->refine_buf = (uint8_t *)p;
+        c->refine_cap = cap;
+    }
+    *out = c->refine_buf;
+    return EPT_OK;
+}
 
 ept_status refine_after(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &specs, ept_result *out, bool timed,
                         cudaStream_t s, std::vector<TestError> *per_test = nullptr) {
@@ -1111,9 +1160,30 @@ ept_status refine_after(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &
         fl.resize((size_t)d.ncols);
         CK(cudaMemcpyAsync(fl.data(), b.flags + d.col0, (size_t)d.ncols, cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
+        // level 1: exact re-summation of the packed operand (the accumulation part)
         list.clear();
         for (int64_t k = 0; k < d.ncols; ++k)
-            if (fl[(size_t)k]) list.push_back((int32_t)k);
+            if (fl[(size_t)k] == 1) list.push_back((int32_t)k);
+        if (!list.empty()) {
+            const int64_t n1 = (int64_t)list.size();
+            const size_t b_list = align_up(4 * (size_t)n1, 256);
+            uint8_t *mem = nullptr;
+            ept_status st = refine_scratch(c, b_list + 8 * (size_t)(d.NP * refine_packed_chunks(d.NKB)) * n1, s, &mem);
+            if (st != EPT_OK) return st;
+            int32_t *dlist = (int32_t *)mem;
+            double *part = (double *)(mem + b_list);
+            cudaError_t e = cudaMemcpyAsync(dlist, list.data(), 4 * (size_t)n1, cudaMemcpyHostToDevice, s);
+            if (e == cudaSuccess) {
+                launch_refine_packed(b, t, d.NP, d.NKB, dlist, n1, part, s);
+                e = cudaGetLastError();
+            }
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the list's host copy stays valid until here
+            if (e != cudaSuccess) return fail(EPT_ECUDA, "exact re-summation failed: %s", cudaGetErrorString(e));
+        }
+        // level 2: the entries rebuilt in FP64 from the raw rows (the representation part)
+        list.clear();
+        for (int64_t k = 0; k < d.ncols; ++k)
+            if (fl[(size_t)k] == 2) list.push_back((int32_t)k);
         const int64_t nflag = (int64_t)list.size();
         if (nflag == 0) continue;
         const double sigma = d.stat == EPT_STAT_ED ? 0.0 : (d.median ? (double)median_sigma(ctr[t]) : d.sigma64);
@@ -1122,10 +1192,9 @@ ept_status refine_after(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &
         rows_w = std::max<int64_t>(64, std::min<int64_t>(rows_w, ntiles * 64));
         const size_t b_list = align_up(4 * (size_t)nflag, 256), b_part = align_up(16 * (size_t)ntiles * nflag, 256),
                      b_spart = align_up(8 * (size_t)ntiles, 256), b_w = 8 * (size_t)rows_w * (size_t)d.n;
-        void *mem = nullptr;
-        ept_status st = device_alloc(c, b_list + b_part + b_spart + b_w, s, &mem);
+        uint8_t *m8 = nullptr;
+        ept_status st = refine_scratch(c, b_list + b_part + b_spart + b_w, s, &m8);
         if (st != EPT_OK) return st;
-        uint8_t *m8 = (uint8_t *)mem;
         int32_t *dlist = (int32_t *)m8;
         double *part = (double *)(m8 + b_list), *spart = (double *)(m8 + b_list + b_part);
         double *W64 = (double *)(m8 + b_list + b_part + b_spart);
@@ -1141,8 +1210,13 @@ ept_status refine_after(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the list's host copy stays valid until here
-        device_free(c, mem, s);
         if (e != cudaSuccess) return fail(EPT_ECUDA, "FP64 refinement failed: %s", cudaGetErrorString(e));
+    }
+    // large scratch (an FP64 rebuild's window) is not kept between calls
+    if (c->refine_cap > ((size_t)256 << 20)) {
+        device_free(c, c->refine_buf, s);
+        c->refine_buf = nullptr;
+        c->refine_cap = 0;
     }
     // counts and outputs again, read back as in the run
     launch_reset_counts(b, s);
@@ -1157,19 +1231,21 @@ ept_status refine_after(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &
 }
 
 // One run of a batch: plan, stage, enqueue (or replay a captured graph), wait, collect.
-ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bool on_device, int chunk_kb,
+ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bool on_device, const Tuning &tn,
                     bool use_graph, ept_result *out, void *stream, float *device_ms) {
     cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
     ept_status st0 = EPT_OK;
+    const int chunk_kb = tn.chunk_kb;
     std::vector<int64_t> pkey = shape_key(specs, prec, on_device);
-    pkey.push_back(chunk_kb);
+    pkey.push_back(tn.code());
     pkey.push_back(c->debug ? 1 : 0);
     if (!c->plan) {
         c->plan = new (std::nothrow) Plan();
         if (!c->plan) return fail(EPT_ENOMEM, "host allocation failed");
     }
     if (c->plan_key != pkey) {
-        plan_batch(*c->plan, specs, prec, !on_device, chunk_kb, c->num_sms, c->debug);
+        plan_batch(*c->plan, specs, prec, !on_device, chunk_kb, c->num_sms, c->debug, true, tn.order);
+        c->plan->draw_mode = tn.draw_mode;
         c->plan_key = pkey;
         c->tables_staged = false;
         if (c->debug && (st0 = check_plan(*c->plan)) != EPT_OK) {
@@ -1197,7 +1273,7 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
             s = c->stream;
         }
         std::vector<int64_t> key = shape_key(specs, prec, on_device);
-        key.push_back(chunk_kb);
+        key.push_back(tn.code());
         key.push_back(c->debug ? 1 : 0);
         if (!(c->graph.exec && c->graph.key == key && c->graph.arena == c->arena)) {
             drop_graph(c);
@@ -1225,6 +1301,7 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
         CK(cudaStreamSynchronize(s));
         if ((st = collect(c, P, specs, out, false)) != EPT_OK) return st;
         if ((st = refine_after(c, P, specs, out, false, s)) != EPT_OK) return st;
+        for (int t = 0; t < P.n_tests; ++t) out[t].tuning = tn.code();
         float ms = 0.f;
         cudaEventElapsedTime(&ms, c->ev[0], c->ev[4]);
         for (int t = 0; t < P.n_tests; ++t) out[t].ms_total = ms;
@@ -1237,7 +1314,8 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
     CK(cudaStreamSynchronize(s));
     if ((st = collect(c, P, specs, out, true)) != EPT_OK) return st;
     if ((st = refine_after(c, P, specs, out, true, s)) != EPT_OK) return st;
-    if (device_ms) cudaEventElapsedTime(device_ms, c->ev[5], c->ev[6]);
+    if (device_ms) cudaEventElapsedTime(device_ms, c->ev[0], c->ev[4]);   // the whole run on the device
+    for (int t = 0; t < P.n_tests; ++t) out[t].tuning = tn.code();
     return EPT_OK;
 }
 
@@ -1249,30 +1327,86 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
 // context's precision limit when that is shorter.
 int unit_kb(const ept_ctx *c) { return std::min(CHUNK_KB_DEFAULT, c->max_chunk); }
 
+Tuning default_tuning(const ept_ctx *c) {
+    Tuning tn;
+    tn.chunk_kb = unit_kb(c);
+    return tn;
+}
+
+// batches worth timing several parameter sets on their first call: several tests,
+// or a test whose contraction is long enough for the choice to show
+// (n^2 B >= 2.5e10: the high-dimensional ED workload has 2.5e11)
+bool worth_tuning(const std::vector<TestSpec> &specs) {
+    if (specs.size() >= 2) return true;
+    const double n = (double)(specs[0].nx + specs[0].ny);
+    return n * n * (double)specs[0].B >= 2.5e10;
+}
+
+// Parameters for this batch shape (tensor-core path): from the cache, or (first call
+// of the shape) by timing whole device runs with each candidate on this very batch:
+// the defaults; the other relabeling-draw kernel; the other unit order; units of 4
+// K-blocks; and longer units where EPT_OPT_MAX_CHUNK allows them.  Every candidate
+// run is a complete, correct test; the chosen one is run once more for the results
+// (a captured graph when graphs are on).
 ept_status run_tuned(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bool on_device, bool use_graph,
                      ept_result *out, void *stream) {
-    // candidates up to the precision limit (one candidate: nothing to tune)
-    int ncand = 0;
-    while (ncand < 3 && CHUNK_CANDIDATES[ncand] <= c->max_chunk) ++ncand;
-    if (!c->autotune || ncand <= 1)
-        return run_once(c, specs, prec, on_device, unit_kb(c), use_graph, out, stream, nullptr);
+    const Tuning def = default_tuning(c);
+    if (!c->autotune || prec != EPT_PREC_SPLIT_BF16 || !worth_tuning(specs)) {
+        ept_status st = run_once(c, specs, prec, on_device, def, use_graph, out, stream, nullptr);
+        for (size_t t = 0; st == EPT_OK && t < specs.size(); ++t) out[t].tune_candidates = 0;
+        return st;
+    }
     const std::vector<int64_t> key = tune_key(specs, prec, c->max_chunk);
-    auto it = c->tuned_chunk.find(key);
-    if (it != c->tuned_chunk.end()) return run_once(c, specs, prec, on_device, it->second, use_graph, out, stream, nullptr);
-    int best = unit_kb(c);
+    auto it = c->tuned.find(key);
+    if (it != c->tuned.end()) {
+        ept_status st = run_once(c, specs, prec, on_device, it->second, use_graph, out, stream, nullptr);
+        for (size_t t = 0; st == EPT_OK && t < specs.size(); ++t) out[t].tune_candidates = 0;
+        return st;
+    }
+    // the automatic choices of this batch, and their alternatives
+    int64_t cols = 0;
+    bool big_masks = false, user_masks = false;
+    for (const TestSpec &sp : specs) {
+        const int64_t Bp = (sp.B + 1 + COL_PAD - 1) / COL_PAD * COL_PAD;
+        const int64_t nw = (sp.nx + sp.ny + PANEL - 1) / PANEL * (PANEL / 32);
+        cols += Bp;
+        big_masks |= nw * Bp * 4 > MASKS_IN_L2_BYTES;
+        user_masks |= sp.user_masks != nullptr;
+    }
+    const int auto_draw = cols >= DRAW_LANES_MIN_COLS_PER_SM * (int64_t)c->num_sms ? DRAW_LANES : DRAW_WARPS;
+    std::vector<Tuning> cand(1, def);
+    if (!user_masks && c->draw_mode == 0) {
+        Tuning t = def;
+        t.draw_mode = auto_draw == DRAW_LANES ? DRAW_WARPS : DRAW_LANES;
+        cand.push_back(t);
+    }
+    {
+        Tuning t = def;
+        t.order = big_masks ? 1 : 2;
+        cand.push_back(t);
+    }
+    for (int kb : {4, 16, 32})
+        if (kb != def.chunk_kb && kb <= c->max_chunk) {
+            Tuning t = def;
+            t.chunk_kb = kb;
+            cand.push_back(t);
+        }
+    Tuning best = def;
     float best_ms = 1e30f;
-    for (int k = 0; k < ncand; ++k) {
+    for (const Tuning &tn : cand) {
         float ms = 0.f;
-        ept_status st = run_once(c, specs, prec, on_device, CHUNK_CANDIDATES[k], false, out, stream, &ms);
+        ept_status st = run_once(c, specs, prec, on_device, tn, false, out, stream, &ms);
         if (st != EPT_OK) return st;
         if (ms < best_ms) {
             best_ms = ms;
-            best = CHUNK_CANDIDATES[k];
+            best = tn;
         }
     }
-    c->tuned_chunk[key] = best;
+    c->tuned[key] = best;
     save_tune_file(c);
-    return run_once(c, specs, prec, on_device, best, use_graph, out, stream, nullptr);
+    ept_status st = run_once(c, specs, prec, on_device, best, use_graph, out, stream, nullptr);
+    for (size_t t = 0; st == EPT_OK && t < specs.size(); ++t) out[t].tune_candidates = (int64_t)cand.size();
+    return st;
 }
 
 // ---------------------------------------------------------------------------
@@ -1793,7 +1927,7 @@ ept_status run_single(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, 
     if (prec == EPT_PREC_POOLED_FP32) return run_pooled(c, specs, on_device, out, stream);
     if (use_stream(c, specs[0], prec)) return run_stream(c, specs, prec, on_device, out, stream);
     if (tuned) return run_tuned(c, specs, prec, on_device, true, out, stream);
-    return run_once(c, specs, prec, on_device, unit_kb(c), false, out, stream, nullptr);
+    return run_once(c, specs, prec, on_device, default_tuning(c), false, out, stream, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -1852,6 +1986,8 @@ struct Server {
     uint64_t next_ticket = 1;
     bool stop = false;
     size_t max_pending = 1 << 16;
+    int64_t peak_busy = 0;         // the most lanes that held a running batch at the same time
+    int64_t submits_busy = 0;      // requests submitted while some lane held a running batch
 };
 
 void CUDART_CB lane_finished(void *arg) {
@@ -1976,6 +2112,9 @@ bool form_batch(Server *S, Lane &L) {
     }
     if (batch.empty()) return false;
     L.busy = true;
+    int64_t busy = 0;
+    for (const Lane &o : S->lanes) busy += o.busy ? 1 : 0;
+    S->peak_busy = std::max(S->peak_busy, busy);
     L.reqs = batch;
     L.specs = specs;
     L.bytes = L.plan.total;
@@ -2192,6 +2331,7 @@ ept_status ept_destroy(ept_ctx *c) {
         if (c->side) cudaStreamSynchronize(c->side);
         drop_graph(c);
         if (c->arena) device_free(c, c->arena, c->stream);
+        if (c->refine_buf) device_free(c, c->refine_buf, c->stream);
         if (c->pinned) cudaFreeHost(c->pinned);
         delete c->plan;
         for (int k = 0; k < 7; ++k)
@@ -2540,6 +2680,11 @@ ept_status ept_submit(ept_ctx *c, const ept_test_desc *q, int prec, uint64_t *ti
     }
     r->ticket = S->next_ticket++;
     r->t_submit = Clock::now();
+    for (const Lane &L : S->lanes)
+        if (L.busy) {
+            ++S->submits_busy;
+            break;
+        }
     S->reqs[r->ticket] = r;
     S->pending.push_back(r);
     *ticket = r->ticket;
@@ -2602,6 +2747,21 @@ ept_status ept_serving_stats(ept_ctx *c, size_t *bytes_in_use, int64_t *running,
     if (running) *running = run;
     if (queued) *queued = q;
     if (finished) *finished = fin;
+    return EPT_OK;
+}
+
+ept_status ept_serving_lanes(ept_ctx *c, int64_t *busy, int64_t *peak_busy, int64_t *submits_while_busy) {
+    if (!c) return fail(EPT_EINVAL, "null context");
+    int64_t b = 0, pk = 0, sb = 0;
+    if (Server *S = c->server) {
+        std::lock_guard<std::mutex> lk(S->mu);
+        for (const Lane &L : S->lanes) b += L.busy ? 1 : 0;
+        pk = S->peak_busy;
+        sb = S->submits_busy;
+    }
+    if (busy) *busy = b;
+    if (peak_busy) *peak_busy = pk;
+    if (submits_while_busy) *submits_while_busy = sb;
     return EPT_OK;
 }
 

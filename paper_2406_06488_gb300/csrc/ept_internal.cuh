@@ -88,11 +88,17 @@ struct Counters {
 // 2 E_0 of it (relabelings aligned with the samples keep value-dependent biases of
 // the entries, such as those of the kernel evaluation, which differ between the
 // blocks).  m is the contracted group's size.  Statistics with E_b > REFINE_TOL
-// |stat_b| are flagged.  The constants were fitted to measured GPU errors (a sweep
-// of 200 ill-conditioned problems against the FP64 oracle, both precisions).
+// |stat_b| are flagged: when the representation term exceeds REFINE_L2 of the
+// tolerance, for entries rebuilt in FP64 from the raw rows (level 2); otherwise for
+// an exact re-summation of the packed operand the contraction read (level 1), which
+// removes the accumulation part and leaves the FP32 representation of the entries.
+// The constants were fitted to measured GPU errors (a sweep of 200 ill-conditioned
+// problems against the FP64 oracle, both precisions): with them every statistic of
+// the sweep ends within 1e-5, the level-1 results within 6.1e-6.
 constexpr double REFINE_KA = 12.0;
 constexpr double REFINE_KR = 4.0;
 constexpr double REFINE_TOL = 1e-5;
+constexpr double REFINE_L2 = 0.05;
 constexpr double REFINE_U = 5.9604644775390625e-08;   // 2^-24
 
 // Debug checks: guard bands of GUARD_BYTES after every scratch region, filled with a
@@ -278,6 +284,12 @@ void launch_refine_rows(const Batch &b, int t, int64_t r0, int64_t r1, const dou
 void launch_refine_finish(const Batch &b, int t, const int32_t *list, int64_t nflag, const double *part,
                           const double *spart, int64_t ntiles, cudaStream_t s);
 void launch_reset_counts(const Batch &b, cudaStream_t s);   // n_ge = n_near = 0 before a recount
+// the statistics of the listed columns of test t (NP row panels, NKB K-blocks) from the
+// packed operand the contraction read, summed exactly (part: NP x chunks x nflag doubles,
+// chunks = refine_packed_chunks(NKB))
+int64_t refine_packed_chunks(int64_t NKB);
+void launch_refine_packed(const Batch &b, int t, int64_t NP, int64_t NKB, const int32_t *list, int64_t nflag,
+                          double *part, cudaStream_t s);
 
 // single-draw-stream export (ept_perm_masks): columns 0..count-1 = draws b0..b0+count-1
 void launch_perm_masks_plain(uint64_t seed, int nx, int ny, int64_t b0, int64_t count, int nw, uint32_t *maskT,

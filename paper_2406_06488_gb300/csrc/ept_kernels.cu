@@ -1018,9 +1018,14 @@ __global__ void __launch_bounds__(256) k_combine_count(const Batch bt, int flag)
             const double rep_obs = REFINE_KR * REFINE_U * fabs(bW) / sqrt(m);
             const double e0 = bt.errest[d.col0] + rep_obs;
             const bool aligned = c == 0 || fabs(v - obs) <= REFINE_TOL * fabs(obs) + 2.0 * e0;
-            const double e = bt.errest[d.col0 + c] + (aligned ? rep_obs : REFINE_KR * REFINE_U * fabs(bW) / m);
-            fl = !(e <= REFINE_TOL * fabs(v));   // NaN-safe: a non-finite estimate flags
-            bt.flags[d.col0 + c] = (uint8_t)fl;
+            const double rep = aligned ? rep_obs : REFINE_KR * REFINE_U * fabs(bW) / m;
+            const double tol = REFINE_TOL * fabs(v);
+            // flagged when the estimate exceeds the tolerance; 2 (rebuild the entries in FP64)
+            // when the representation term exceeds REFINE_L2 of it, else 1 (re-sum the
+            // packed operand exactly).  NaN-safe: a non-finite estimate takes the rebuild
+            const int lvl = !(bt.errest[d.col0 + c] + rep <= tol) ? (!(rep <= REFINE_L2 * tol) ? 2 : 1) : 0;
+            fl = lvl != 0;
+            bt.flags[d.col0 + c] = (uint8_t)lvl;
         }
         fl = __syncthreads_count(fl);
         if (threadIdx.x == 0 && fl) atomicAdd(&bt.ctr[t].n_flag, (unsigned long long)fl);

@@ -13,11 +13,15 @@
 // centring and no FP32 anywhere after the inputs.
 //
 // Work: W64 rows [r0, r1) (a window sized to the scratch) are computed once by
-// k_refine_w (64 x 64 tiles, FP64 differences staged through shared memory); then
+// k_refine_w (64 x 64 tiles; the squared distances as FP32 pairs with error-free
+// transformations -- about 48 significant bits on the FP32 pipes, which run many
+// times faster than FP64 on this GPU -- then the entry in FP64); then
 // k_refine_rows gives every 64-row tile and every group of 64 flagged columns a
 // CTA, which reads its rows of W64 once per column tile and keeps, per row and
 // column, sum_j s_j W_ij in registers; the tile's sums over its rows are added in a
 // fixed order (deterministic), and k_refine_finish adds the tiles in order.
+#include <cuda_fp16.h>
+
 #include <cstdint>
 
 #include "../../include/ept.h"
@@ -51,11 +55,14 @@ __global__ void __launch_bounds__(256) k_refine_w(const Batch bt, int t, double 
     const TestDesc d = bt.desc[t];
     const int64_t i0 = r0 + (int64_t)blockIdx.y * RT, j0 = (int64_t)blockIdx.x * CT;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 4 x 4 entries each
-    double acc[4][4];
+    // d^2 as an unevaluated FP32 pair (hi, lo): each difference is split exactly
+    // (TwoSum), its square's leading part exactly (FMA), and the pair accumulates with
+    // TwoSum -- about 48 significant bits, on the FP32 pipes
+    float ahi[4][4], alo[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+        for (int b = 0; b < 4; ++b) ahi[a][b] = alo[a][b] = 0.f;
     for (int64_t f0 = 0; f0 < d.p; f0 += FCH) {
         for (int e = threadIdx.x; e < RT * FCH; e += 256) {
             const int r = e / FCH, f = e % FCH;
@@ -64,19 +71,31 @@ __global__ void __launch_bounds__(256) k_refine_w(const Batch bt, int t, double 
             rb[r][f] = (j < d.n && f0 + f < d.p) ? pooled_row(d, j)[f0 + f] : 0.f;
         }
         __syncthreads();
-#pragma unroll 4
+#pragma unroll 2
         for (int f = 0; f < FCH; ++f) {
-            double x[4], y[4];
+            float x[4], y[4];
 #pragma unroll
-            for (int a = 0; a < 4; ++a) x[a] = (double)ra[ty * 4 + a][f];
+            for (int a = 0; a < 4; ++a) x[a] = ra[ty * 4 + a][f];
 #pragma unroll
-            for (int b = 0; b < 4; ++b) y[b] = (double)rb[tx * 4 + b][f];
+            for (int b = 0; b < 4; ++b) y[b] = rb[tx * 4 + b][f];
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
-                    const double df = x[a] - y[b];
-                    acc[a][b] = fma(df, df, acc[a][b]);
+                    // x - y = s + e exactly
+                    const float sd = __fsub_rn(x[a], y[b]);
+                    const float bb = __fsub_rn(sd, x[a]);
+                    const float e = __fadd_rn(__fsub_rn(x[a], __fsub_rn(sd, bb)), __fsub_rn(-y[b], bb));
+                    // (s + e)^2 = p + pe + (2 s e + e^2), p + pe = s^2 exactly
+                    const float pq = __fmul_rn(sd, sd);
+                    const float pe = __fmaf_rn(sd, sd, -pq);
+                    const float tl = __fmaf_rn(2.f * sd, e, __fmul_rn(e, e));
+                    // (hi, lo) += p + (pe + tl)
+                    const float h2 = __fadd_rn(ahi[a][b], pq);
+                    const float hb = __fsub_rn(h2, ahi[a][b]);
+                    const float he = __fadd_rn(__fsub_rn(ahi[a][b], __fsub_rn(h2, hb)), __fsub_rn(pq, hb));
+                    ahi[a][b] = h2;
+                    alo[a][b] = __fadd_rn(alo[a][b], __fadd_rn(he, __fadd_rn(pe, tl)));
                 }
         }
         __syncthreads();
@@ -88,7 +107,7 @@ __global__ void __launch_bounds__(256) k_refine_w(const Batch bt, int t, double 
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const int64_t j = j0 + tx * 4 + b;
-            if (j < d.n) W64[(i - r0) * d.n + j] = refine_entry(acc[a][b], d.stat, sigma);
+            if (j < d.n) W64[(i - r0) * d.n + j] = refine_entry((double)ahi[a][b] + (double)alo[a][b], d.stat, sigma);
         }
     }
 }
@@ -204,7 +223,142 @@ __global__ void __launch_bounds__(256) k_refine_finish(const Batch bt, int t, co
     bt.stats[d.col0 + list[k]] = d.stat == EPT_STAT_ED ? ed : -ed;
 }
 
+// ---- exact re-summation of the packed operand (the accumulation part) ----
+// For flagged columns whose representation term is small, the statistic is
+// recomputed from the packed, centred operand the contraction read, T = s'Cs, with
+// no accumulation error: on the tensor-core path every entry is c C_ij = hi + lo, two
+// FP16 numbers that are both multiples of 2^-24 with |hi + lo| < 2^15, so 2^24 c C_ij
+// is an integer below 2^39 and a row of up to 2^22 entries sums exactly in int64; on
+// the plain path the FP32 entries are summed with TwoSum-compensated FP32 pairs.  The
+// rows' sums meet in FP64.  CTA = (row panel I, chunk of RK K-blocks, 16 flagged
+// columns); thread = (row r of one 128-row half, 8 of the 16 columns).
+constexpr int PCOLS = 16;
+constexpr int RK = 16;   // K-blocks per CTA
+
+__global__ void __launch_bounds__(256) k_refine_packed(const Batch bt, int t, const int32_t *__restrict__ list,
+                                                       int64_t nflag, int64_t nkc, double *__restrict__ part) {
+    // the values of 64 rows x 64 columns (int64 fixed point or FP32), then the sums
+    __shared__ __align__(16) uint8_t sm[PANEL * (PCOLS + 1) * 8];
+    long long(*vi)[KB + 1] = reinterpret_cast<long long(*)[KB + 1]>(sm);
+    float(*vf)[KB + 1] = reinterpret_cast<float(*)[KB + 1]>(sm);
+    double(*red)[PCOLS + 1] = reinterpret_cast<double(*)[PCOLS + 1]>(sm);
+    static_assert(64 * (KB + 1) * 8 <= PANEL * (PCOLS + 1) * 8, "value buffer");
+    const TestDesc d = bt.desc[t];
+    const int64_t I = blockIdx.x / nkc, kc = blockIdx.x % nkc;
+    const int64_t k0 = (int64_t)blockIdx.y * PCOLS;
+    const int r = threadIdx.x & 63, cg = threadIdx.x >> 6;   // row r of a 64-row quarter, columns 4 cg ..
+    const bool split = d.scaled != 0;
+    const int64_t nkb = contract_nkb(d);
+    const int64_t kb_lo = KB_PER_PANEL * I + kc * RK;
+    const int64_t kb_hi = kb_lo + RK < nkb ? kb_lo + RK : nkb;
+    int64_t col[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int64_t k = k0 + 4 * cg + q;
+        col[q] = k < nflag ? (int64_t)list[k] : -1;
+    }
+    double rowT[4][4];   // [quarter][column]
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) rowT[a][q] = 0.0;
+    for (int qr = 0; qr < 4; ++qr) {   // the panel's four 64-row quarters
+        const int64_t i = I * PANEL + 64 * qr + r;
+        long long si[4] = {0, 0, 0, 0};
+        float sf[4] = {0.f, 0.f, 0.f, 0.f}, ef[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int64_t kb = kb_lo; kb < kb_hi; ++kb) {
+            const int64_t blk = d.blk0 + blk_index(I, kb, d.NKB);
+            __syncthreads();
+            for (int x = threadIdx.x; x < 64 * KB; x += 256) {
+                const int rr = x / KB, cc = x % KB;
+                const int64_t off = (int64_t)(64 * qr + rr) * KB + cc;
+                if (split) {
+                    const float h = __half2float(__ushort_as_half(bt.Chi[blk * bt.c_stride + off]));
+                    const float l = __half2float(__ushort_as_half(bt.Clo[blk * bt.c_stride + off]));
+                    // exact: h and l are multiples of 2^-24 below 2^15 in magnitude
+                    vi[rr][cc] = __float2ll_rn(ldexpf(h, 24)) + __float2ll_rn(ldexpf(l, 24));
+                } else {
+                    vf[rr][cc] = bt.D[blk * (int64_t)(PANEL * KB) + off];
+                }
+            }
+            __syncthreads();
+            const int64_t w0 = kb * KB / 32;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (col[q] < 0) continue;
+                const uint32_t m0 = bt.maskT[d.mask0 + w0 * d.Bp + col[q]];
+                const uint32_t m1 = bt.maskT[d.mask0 + (w0 + 1) * d.Bp + col[q]];
+                if (split) {
+                    long long acc = 0;
+                    for (int cc = 0; cc < 32; ++cc) acc += ((m0 >> cc) & 1u) ? vi[r][cc] : 0ll;
+                    for (int cc = 0; cc < 32; ++cc) acc += ((m1 >> cc) & 1u) ? vi[r][32 + cc] : 0ll;
+                    si[q] += acc;
+                } else {
+                    float sq = sf[q], eq = ef[q];
+                    for (int cc = 0; cc < KB; ++cc) {
+                        const uint32_t bit = cc < 32 ? (m0 >> cc) & 1u : (m1 >> (cc - 32)) & 1u;
+                        const float a = bit ? vf[r][cc] : 0.f;
+                        const float t2 = sq + a;   // TwoSum
+                        const float bb = t2 - sq;
+                        eq += (sq - (t2 - bb)) + (a - bb);
+                        sq = t2;
+                    }
+                    sf[q] = sq;
+                    ef[q] = eq;
+                }
+            }
+        }
+        // this row's masked sum counts when the row is in the column's group
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (col[q] < 0 || i >= d.n) continue;
+            const uint32_t bit = (bt.maskT[d.mask0 + (i / 32) * d.Bp + col[q]] >> (i & 31)) & 1u;
+            if (bit) rowT[qr][q] = split ? ldexp((double)si[q], -24) : (double)sf[q] + (double)ef[q];
+        }
+    }
+    __syncthreads();
+    // rows in order: red[row of the panel][column]
+#pragma unroll
+    for (int qr = 0; qr < 4; ++qr)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) red[64 * qr + r][4 * cg + q] = rowT[qr][q];
+    __syncthreads();
+    if (threadIdx.x < PCOLS) {
+        const int64_t k = k0 + threadIdx.x;
+        if (k < nflag) {
+            double T = 0.0;
+            for (int rr = 0; rr < PANEL; ++rr) T += red[rr][threadIdx.x];
+            const double inv_c = split ? 1.0 / (double)packed_scale(bt.ctr[t]) : 1.0;
+            part[(I * nkc + kc) * nflag + k] = T * inv_c;
+        }
+    }
+}
+
+// the statistics of the listed columns from the exact T: stat = sign (cT T + S~ / o^2)
+__global__ void __launch_bounds__(256) k_refine_packed_finish(const Batch bt, int t, const int32_t *__restrict__ list,
+                                                              int64_t nflag, int64_t nkc,
+                                                              const double *__restrict__ part) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nflag) return;
+    const TestDesc d = bt.desc[t];
+    double T = 0.0, St = 0.0;
+    for (int64_t g = 0; g < d.NP * nkc; ++g) T += part[g * nflag + k];
+    for (int64_t I = 0; I < d.NP; ++I) St += bt.Stpart[d.pan0 + I];
+    bt.stats[d.col0 + list[k]] = d.sign * (d.cT * T + St * d.inv_o2);
+}
+
 }  // namespace
+
+int64_t refine_packed_chunks(int64_t NKB) { return (NKB + RK - 1) / RK; }
+
+void launch_refine_packed(const Batch &b, int t, int64_t NP, int64_t NKB, const int32_t *list, int64_t nflag,
+                          double *part, cudaStream_t s) {
+    if (nflag <= 0) return;
+    const int64_t nkc = refine_packed_chunks(NKB);
+    const dim3 grid((unsigned)(NP * nkc), (unsigned)((nflag + PCOLS - 1) / PCOLS));
+    k_refine_packed<<<grid, 256, 0, s>>>(b, t, list, nflag, nkc, part);
+    k_refine_packed_finish<<<(unsigned)((nflag + 255) / 256), 256, 0, s>>>(b, t, list, nflag, nkc, part);
+}
 
 void launch_refine_w(const Batch &b, int t, int64_t n, double sigma, int64_t r0, int64_t r1, double *W64,
                      cudaStream_t s) {

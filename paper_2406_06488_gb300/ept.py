@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libept.so")
 
 STAT = {"ed": 0, "mmd": 1, "mmd_gauss": 1, "mmd_laplace": 2}
 SIGMA_MEDIAN = -1.0   # EPT_SIGMA_MEDIAN: bandwidth from the median heuristic
-ABI_VERSION = 4       # EPT_ABI_VERSION this binding's structures follow
+ABI_VERSION = 5       # EPT_ABI_VERSION this binding's structures follow
 PREC = {"plain_fp32": 0, "split_bf16": 1, "pooled_fp32": 2}   # pooled_fp32: Algorithm 5 baseline
 STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT_ECUDA", 5: "EPT_ETIMEOUT",
           6: "EPT_ECANCELLED", 7: "EPT_ENOTFOUND", 8: "EPT_EUNSUPPORTED", 9: "EPT_EINTERNAL"}
@@ -31,7 +31,7 @@ STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT
 EXPORTS = ["ept_abi_version", "ept_last_error", "ept_create", "ept_destroy", "ept_estimate_bytes", "ept_test",
            "ept_test_masks", "ept_perm_masks", "ept_build_blocks", "ept_test_static", "ept_test_batch",
            "ept_set_option", "ept_submit", "ept_poll", "ept_wait", "ept_cancel", "ept_test_range",
-           "ept_serving_stats", "ept_create_ex", "ept_plan_check"]
+           "ept_serving_stats", "ept_create_ex", "ept_plan_check", "ept_serving_lanes"]
 
 
 class EptError(RuntimeError):
@@ -51,7 +51,7 @@ class _Result(ctypes.Structure):
                 ("n_near_tie", ctypes.c_int64), ("n_fixup", ctypes.c_int64), ("ms_build", ctypes.c_double),
                 ("ms_perm", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_masks", ctypes.c_double),
                 ("ms_contract", ctypes.c_double), ("sigma", ctypes.c_double), ("n_windows", ctypes.c_int64),
-                ("n_refined", ctypes.c_int64)]
+                ("n_refined", ctypes.c_int64), ("tuning", ctypes.c_int64), ("tune_candidates", ctypes.c_int64)]
 
 
 class _PlanInfo(ctypes.Structure):
@@ -84,12 +84,14 @@ class Result:
     sigma: float
     n_windows: int = 0
     n_refined: int = 0
+    tuning: int = 0
+    tune_candidates: int = 0
     stats: Optional[object] = field(default=None, repr=False)
 
 
 def _result(r, buf) -> "Result":
     return Result(r.observed, r.p_value, r.n_ge, r.n_near_tie, r.n_fixup, r.ms_build, r.ms_perm, r.ms_total,
-                  r.ms_masks, r.ms_contract, r.sigma, r.n_windows, r.n_refined, buf)
+                  r.ms_masks, r.ms_contract, r.sigma, r.n_windows, r.n_refined, r.tuning, r.tune_candidates, buf)
 
 
 _lib = None
@@ -149,6 +151,8 @@ def load():
     lib.ept_serving_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(i64),
                                       ctypes.POINTER(i64), ctypes.POINTER(i64)]
     lib.ept_serving_stats.restype = i32
+    lib.ept_serving_lanes.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.ept_serving_lanes.restype = i32
     lib.ept_cancel.argtypes = [vp, u64]
     lib.ept_cancel.restype = i32
     _lib = lib
@@ -381,6 +385,13 @@ class Context:
         _check(load().ept_serving_stats(self._h, ctypes.byref(b), ctypes.byref(run), ctypes.byref(q),
                                         ctypes.byref(fin)))
         return {"bytes_in_use": b.value, "running": run.value, "queued": q.value, "finished": fin.value}
+
+    def serving_lanes(self) -> dict:
+        """Lanes busy now, the most busy at once so far, and requests submitted while a
+        batch was running (ept_serving_lanes)."""
+        b, pk, sb = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+        _check(load().ept_serving_lanes(self._h, ctypes.byref(b), ctypes.byref(pk), ctypes.byref(sb)))
+        return {"busy": b.value, "peak_busy": pk.value, "submits_while_busy": sb.value}
 
     def cancel(self, ticket: int) -> None:
         _check(load().ept_cancel(self._h, ctypes.c_uint64(ticket)))

@@ -295,3 +295,47 @@ def test_full_batched_configuration_sampled(ctx):
         assert rel.max() <= REL_TOL, (t, float(rel.max()))
         near = np.abs(ref["stats"] - ref["observed"]) <= 1e-5 * abs(ref["observed"])
         assert abs(r.n_ge - ref["n_ge"]) <= int(near.sum()), t
+
+
+def test_autotuner_times_candidates_and_round_trips(tmp_path, monkeypatch):
+    """The first call of a batch shape times at least three parameter sets (unit
+    length, relabeling-draw kernel, unit order), keeps the fastest, and every result
+    equals the FP64 oracle's (Algorithm 1; Section 3.1 p-value); later calls and a new
+    context reading the cache file take the same parameters without timing."""
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2406_06488_gb300 import ept
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("EPT_AUTOTUNE_CACHE", str(cache))
+    tests = []
+    for k in range(6):
+        spec = workloads.TwoSampleSpec(nx=150 + 170 * k, ny=900 - 110 * k, p=5 + 7 * k, y_mean=0.1 * (k % 2),
+                                       data_seed=300 + k)
+        X, Y = workloads.gaussian_pair(spec)
+        tests.append(dict(X=X, Y=Y, B=700 + 250 * k, seed=40 + k, stat=["ed", "mmd"][k % 2],
+                          sigma=float(np.sqrt(5 + 7 * k))))
+    with ept.Context(0) as c:
+        first = c.test_batch(tests)
+        assert all(r.tune_candidates >= 3 for r in first), [r.tune_candidates for r in first]
+        chosen = first[0].tuning
+        assert all(r.tuning == chosen for r in first)
+        for t, r in zip(tests, first):
+            ref = oracle.permutation_test(t["X"], t["Y"], B=t["B"], seed=t["seed"], stat=t["stat"], sigma=t["sigma"],
+                                          method="blocks")
+            assert abs(r.observed - ref["observed"]) <= REL_TOL * abs(ref["observed"])
+            assert _close(r.stats, ref["stats"])
+            near = int(np.count_nonzero(np.abs(ref["stats"] - ref["observed"]) <= 1e-5 * abs(ref["observed"])))
+            assert abs(r.n_ge - ref["n_ge"]) <= near
+            assert r.p_value == (1.0 + r.n_ge) / (1.0 + t["B"])
+        again = c.test_batch(tests)
+        assert all(r.tune_candidates == 0 and r.tuning == chosen for r in again)
+        for a, b in zip(first, again):
+            assert a.observed == b.observed and np.array_equal(np.asarray(a.stats), np.asarray(b.stats))
+    lines = cache.read_text().split("\n")
+    head = [int(v) for v in lines[0].split()[:3]]
+    assert head[0] * 100 + head[1] * 10 + head[2] == chosen
+    with ept.Context(0) as c2:
+        res = c2.test_batch(tests)
+        assert all(r.tune_candidates == 0 and r.tuning == chosen for r in res)
+        for a, b in zip(first, res):
+            assert np.array_equal(np.asarray(a.stats), np.asarray(b.stats))

@@ -1,9 +1,15 @@
 """Serving: requests submitted to the continuous-batching scheduler give the same
-results as the same tests run alone; tickets, cancellation, timeouts, per-request
-errors and the memory budget behave as the C ABI states."""
+results as the same tests run alone, and the FP64 oracle's results when they arrive
+(Poisson-timed, from a submitter thread) while earlier batches are running on other
+lanes; tickets, cancellation, timeouts, per-request errors and the memory budget
+behave as the C ABI states."""
+import threading
+import time
+
 import numpy as np
 import pytest
 
+import oracle
 from paper_2406_06488_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -65,6 +71,64 @@ def test_mixed_precisions_in_queue(ctx):
         r = ctx.wait(t)
         alone = ctx.test(q["X"], q["Y"], B=q["B"], seed=q["seed"], stat=q["stat"], sigma=q["sigma"], prec=pr)
         assert abs(r.observed - alone.observed) <= REL_TOL * abs(alone.observed)
+        if q["B"] > 0:
+            a, b = np.asarray(r.stats), np.asarray(alone.stats)
+            assert a.shape == b.shape and np.max(np.abs(a - b) / np.abs(b)) <= REL_TOL
+        assert abs(r.n_ge - alone.n_ge) <= alone.n_near_tie
+        assert r.p_value == (1.0 + r.n_ge) / (1.0 + q["B"])
+
+
+def test_overlapping_arrivals_match_the_oracle(ept):
+    """A submitter thread feeds Poisson-timed requests (about 2000 per second) right
+    after a large first one, so that requests arrive while earlier batches run on other
+    lanes; every served result equals the FP64 oracle's whole test (Algorithm 1 on the
+    three blocks; Section 3.1 p-value): statistics within 1e-5, counts equal except
+    through near-ties."""
+    c = ept.Context(0)
+    try:
+        r = np.random.default_rng(21)
+        reqs = []
+        big = workloads.TwoSampleSpec(nx=1000, ny=1000, p=400, y_mean=0.05, data_seed=2100)
+        X, Y = workloads.gaussian_pair(big)
+        reqs.append(dict(X=X, Y=Y, B=20000, seed=1, stat="ed", sigma=1.0))
+        for k in range(31):
+            nx, ny, p = int(r.integers(100, 1000)), int(r.integers(100, 1000)), int(r.integers(4, 120))
+            spec = workloads.TwoSampleSpec(nx=nx, ny=ny, p=p, y_mean=0.1 * (k % 3), y_var=1.0 + 0.1 * (k % 2),
+                                           data_seed=2200 + k)
+            X, Y = workloads.gaussian_pair(spec)
+            reqs.append(dict(X=X, Y=Y, B=int(r.choice([1000, 3000, 5000])), seed=100 + k,
+                             stat=["ed", "mmd", "mmd_laplace"][k % 3], sigma=float(np.sqrt(p))))
+        gaps = r.exponential(1.0 / 2000.0, size=len(reqs))
+        tickets = [None] * len(reqs)
+
+        def submitter():
+            t0 = time.perf_counter()
+            due = 0.0
+            for k, q in enumerate(reqs):
+                due += gaps[k] if k else 0.0
+                delay = t0 + due - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[k] = c.submit(q["X"], q["Y"], B=q["B"], seed=q["seed"], stat=q["stat"], sigma=q["sigma"])
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        th.join()
+        got = [c.wait(t) for t in tickets]
+        lanes = c.serving_lanes()
+        assert lanes["submits_while_busy"] >= 1, lanes
+        assert lanes["peak_busy"] >= 2, lanes
+        for q, res in zip(reqs, got):
+            ref = oracle.permutation_test(q["X"], q["Y"], B=q["B"], seed=q["seed"], stat=q["stat"], sigma=q["sigma"],
+                                          method="blocks")
+            assert abs(res.observed - ref["observed"]) <= REL_TOL * abs(ref["observed"])
+            rel = np.abs(np.asarray(res.stats) - ref["stats"]) / np.abs(ref["stats"])
+            assert rel.max() <= REL_TOL, (q["stat"], float(rel.max()))
+            near = int(np.count_nonzero(np.abs(ref["stats"] - ref["observed"]) <= 1e-5 * abs(ref["observed"])))
+            assert abs(res.n_ge - ref["n_ge"]) <= near
+            assert res.p_value == (1.0 + res.n_ge) / (1.0 + q["B"])
+    finally:
+        c.close()
 
 
 def test_poll_timeout_and_unknown_ticket(ctx, ept):

@@ -81,10 +81,13 @@ def test_stream_matches_resident(ept_mod):
     # the same test resident and streamed, with the same contraction chunks: the same
     # blocks, partials and scale; the FP64 row sums and partial sums are added in
     # another order (which can move the FP32 rounding of a centring constant), so
-    # the statistics agree to far below the parity tolerance, not bitwise
+    # the statistics agree to far below the parity tolerance, not bitwise.  The
+    # resident run's FP64 recomputation of flagged statistics is off here (the
+    # streaming mode has none), so that the two compute the same thing.
     X, Y = _pair(9000, 11000, 50, seed=8, shift=0.02)
     with ept_mod.Context(0) as c:
         c.set_option("autotune", 0)
+        c.set_option("refine", 0)
         c.set_option("stream_blocks", -1)
         a = c.test(X, Y, B=2000, seed=3, stat="mmd", sigma=9.0)
         c.set_option("stream_blocks", 3000)
