@@ -1,9 +1,9 @@
 """One permutation test across several processes (one GPU each): the relabelings
 1..B of the test's counter-based stream are split into contiguous ranges, each
 process evaluates its range (the observed statistic is relabeling 0 in every range),
-and a single exchange at the end gathers the permuted statistics and sum-reduces the
-counts; the p-value (1 + #{stat* >= observed}) / (1 + B) (Section 3.1) is then that
-of the whole test.  Relabeling b is draw b of the stream whatever the number of
+and a single exchange at the end gathers the permuted statistics, which every
+process then counts against rank 0's observed statistic; the p-value
+(1 + #{stat* >= observed}) / (1 + B) (Section 3.1) is then that of the whole test.  Relabeling b is draw b of the stream whatever the number of
 processes, so the result does not depend on it.  No collective runs inside a kernel.
 
 The exchange uses torch.distributed on the process group given (tensors on the
@@ -31,14 +31,18 @@ def permutation_ranges(B: int, world: int):
     return out
 
 
-def combine(observed: float, stats_parts, n_ge_parts, n_near_parts, B: int):
+def combine(observed: float, stats_parts, B: int):
     """The whole test from its ranges: (observed, stats[B] in relabeling order, n_ge,
-    n_near_tie, p_value)."""
+    n_near_tie, p_value).  The counts are taken here, against the one observed
+    statistic given (Section 3.1: #{stat* >= observed}; near-ties within 1e-5 of it),
+    so that every rank compares every statistic with the same threshold even where
+    the ranks' own evaluations of the observed statistic differ in the last bits."""
     stats = np.concatenate([np.asarray(s, dtype=np.float64) for s in stats_parts]) if B else np.zeros(0)
     if stats.shape[0] != B:
         raise ValueError("the ranges hold %d statistics, the test has %d" % (stats.shape[0], B))
-    n_ge = int(sum(n_ge_parts))
-    return observed, stats, n_ge, int(sum(n_near_parts)), (1.0 + n_ge) / (1.0 + B)
+    n_ge = int(np.count_nonzero(stats >= observed))
+    n_near = int(np.count_nonzero(np.abs(stats - observed) <= 1e-5 * abs(observed)))
+    return observed, stats, n_ge, n_near, (1.0 + n_ge) / (1.0 + B)
 
 
 class RangeFailed(RuntimeError):
@@ -75,19 +79,17 @@ def sharded_test(run_range, B: int, group=None):
         raise RangeFailed("%d rank(s) failed to evaluate their range of relabelings" % int(failed.item()))
     width = max(c for _, c in ranges) if ranges else 0
     # one gather of the padded ranges (and of each rank's observed statistic, which
-    # is the same relabeling 0 everywhere), one sum of the counts
+    # is the same relabeling 0 everywhere); every rank then counts the whole test's
+    # statistics against rank 0's observed statistic
     mine = torch.zeros(width + 1, dtype=torch.float64, device=device)
     mine[0] = float(observed)
     if count:
         mine[1:count + 1] = torch.from_numpy(stats).to(device)
     parts = [torch.empty_like(mine) for _ in range(world)]
     dist.all_gather(parts, mine, group=group)
-    counts = torch.tensor([int(n_ge), int(n_near)], dtype=torch.int64, device=device)
-    dist.all_reduce(counts, group=group)
     parts = [p.cpu().numpy() for p in parts]
     stats_parts = [parts[r][1:c + 1] for r, (_, c) in enumerate(ranges)]
-    counts = counts.cpu().numpy()
-    return combine(float(parts[0][0]), stats_parts, [int(counts[0])], [int(counts[1])], B)
+    return combine(float(parts[0][0]), stats_parts, B)
 
 
 def run_across_ranks(ctx, X, Y, B: int, seed: int = 0, stat="ed", sigma: float = 1.0, prec="split_bf16",

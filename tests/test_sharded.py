@@ -44,10 +44,19 @@ def test_range_arguments():
 
 
 def test_combine():
-    obs, st, nge, near, p = sharded.combine(2.0, [[1.0, 3.0], [], [2.0]], [1, 0, 1], [0, 0, 1], 3)
+    obs, st, nge, near, p = sharded.combine(2.0, [[1.0, 3.0], [], [2.0]], 3)
     assert obs == 2.0 and list(st) == [1.0, 3.0, 2.0] and nge == 2 and near == 1 and p == 3.0 / 4.0
     with pytest.raises(ValueError):
-        sharded.combine(2.0, [[1.0]], [0], [0], 2)
+        sharded.combine(2.0, [[1.0]], 2)
+
+
+def test_combine_counts_against_one_observed():
+    # the counts come from the gathered statistics and the observed statistic given,
+    # not from per-range counts taken against slightly different observed values
+    obs = 1.0
+    parts = [[1.0 - 1e-16, 0.5], [1.0 + 1e-16, 2.0]]
+    _, _, nge, near, p = sharded.combine(obs, parts, 4)
+    assert nge == 2 and near == 2 and p == 3.0 / 5.0
 
 
 def _inputs():
