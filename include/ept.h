@@ -323,11 +323,11 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    EPT_OPT_REFINE (default 1; 0 or 1): FP64 recomputation of flagged statistics
    (Section 3.1's statistics, Eq. 1 / Eq. 2, evaluated from the raw rows).  Every
    statistic of the split and plain precisions carries an a-posteriori estimate of
-   its error, E_b = 12 u cT A_b + 4 u Wbar g_b: u = 2^-24, cT = (n/(nx ny))^2, A_b the
-   sum of the absolute values of its contraction partial sums (the magnitudes its
-   FP32 accumulations carried), Wbar the mean entry of the pooled matrix, g_b = 1/m
-   for a relabeling and 1/sqrt(m) for the observed statistic and every statistic
-   within 1e-5 |observed| + 2 E_0 of it (m = min(nx, ny)).  A statistic with
+   its error, E_b = k_b u cT A_b + 20 u Wbar / m: u = 2^-24, cT = (n/(nx ny))^2, A_b
+   the sum of the absolute values of its contraction partial sums (the magnitudes its
+   FP32 accumulations carried), Wbar the mean entry of the pooled matrix, m =
+   min(nx, ny), k_b = 12 for a relabeling and 64 for the observed statistic and every
+   statistic within 1e-5 |observed| + 2 E_0 of it.  A statistic with
    E_b > 1e-5 |stat_b| is recomputed: when its representation term (the second) is
    above 1/20 of the tolerance, from W built in FP64 by direct differences of the
    widened inputs (Algorithm 3) and its three block sums in FP64; otherwise by summing
@@ -340,6 +340,12 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    features whose permuted statistics are far below the FP32 resolution of the
    kernel values; ept_result.n_refined counts them.  Not applied in the streaming
    mode, by the pre-computation baseline or by ept_test_static.
+   EPT_OPT_PAIR (default 0; 0 or 1): the tensor-core contraction on pairs of SMs
+   (clusters of two CTAs, tcgen05 cta_group::2): a work unit covers a whole 256-row
+   panel, each CTA of the pair loads its 128 rows of the operand and expands its half
+   of the 256 relabelings, one CTA issues the MMAs for both (less shared-memory
+   traffic and relabeling expansion per multiply-add).  Same statistics as the
+   single-SM kernel up to the accumulation order.
    EPT_OPT_SERVE_LANES (default 3, 1..16): serving batches in flight at once;
    EPT_OPT_SERVE_SLOTS (default 256): serving requests in flight at once; both
    before the first ept_submit.  EPT_EINVAL for an unknown option or value.
@@ -360,7 +366,8 @@ enum {
     EPT_OPT_STREAM_BLOCKS = 9,
     EPT_OPT_WAIT_LIMIT_MS = 10,
     EPT_OPT_MAX_CHUNK = 11,
-    EPT_OPT_REFINE = 12
+    EPT_OPT_REFINE = 12,
+    EPT_OPT_PAIR = 13
 };
 ept_status ept_set_option(ept_ctx *ctx, int option, int64_t value);
 

@@ -560,6 +560,7 @@ struct ept_ctx {
     unsigned long long wait_ns = 0;     // limit of the kernels' bounded waits (0: their default, 2 s)
     int max_chunk = CHUNK_KB_DEFAULT;   // longest contraction unit the autotuner may pick (precision)
     bool refine = true;                 // recompute flagged statistics (EPT_OPT_REFINE)
+    bool pair = false;                  // contraction on pairs of SMs (EPT_OPT_PAIR)
     uint8_t *refine_buf = nullptr;      // scratch of the recomputation (grows, kept until ept_destroy)
     size_t refine_cap = 0;
     ept_allocator alloc{};              // caller-supplied device memory (alloc.alloc == nullptr: cudaMalloc)
@@ -942,7 +943,8 @@ ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed,
         char emsg[160];
         if (!encode_block_tmaps(&th, &tl, b.Chi, b.Clo, P.nblk, b.c_stride, emsg, sizeof(emsg)))
             return fail(EPT_ECUDA, "%s", emsg);
-        CK(launch_contract_tc(b, &th, &tl, c->num_sms, s));
+        if (c->pair) CK(launch_contract_tc2(b, &th, &tl, c->num_sms, s));
+        else CK(launch_contract_tc(b, &th, &tl, c->num_sms, s));
     } else {
         launch_contract_simt(b, s);
         CK(cudaGetLastError());
@@ -2137,10 +2139,13 @@ void serve_loop(Server *S, int device) {
             std::vector<ept_result> out(L.reqs.size());
             std::vector<TestError> per_test;
             ept_status st = EPT_OK;
+            // the lane stays busy (no other thread uses its state) while its results are
+            // collected and its flagged statistics recomputed, without the server lock,
+            // so that submissions and waits go on meanwhile
+            lk.unlock();
             if (q != cudaSuccess) st = fail(EPT_ECUDA, "serving run failed: %s", cudaGetErrorString(q));
             else st = collect(L.ctx, L.plan, L.specs, out.data(), false, &per_test);
             if (st == EPT_OK) {
-                // FP64 recomputation of flagged statistics, on the lane's scratch
                 L.ctx->arena = L.arena;
                 L.ctx->arena_cap = L.plan.total;
                 st = refine_after(L.ctx, L.plan, L.specs, out.data(), false, L.ctx->stream, &per_test);
@@ -2150,6 +2155,7 @@ void serve_loop(Server *S, int device) {
             const std::string msg = st == EPT_OK ? std::string() : g_err;
             const ept_status rst = lane_release(S, L);
             if (st == EPT_OK && rst != EPT_OK) st = rst;
+            lk.lock();
             finish_requests(S, L, st, st == EPT_OK ? msg : (msg.empty() ? g_err : msg), out.data(), &per_test);
             progressed = true;
         }
@@ -2305,6 +2311,7 @@ ept_status ept_create_ex(ept_ctx **out, int device, size_t mem_budget_bytes, con
                     {"EPT_DRAW_MODE", EPT_OPT_DRAW_MODE},     {"EPT_DEBUG_CHECKS", EPT_OPT_DEBUG_CHECKS},
                     {"EPT_STREAM_BLOCKS", EPT_OPT_STREAM_BLOCKS}, {"EPT_WAIT_LIMIT_MS", EPT_OPT_WAIT_LIMIT_MS},
                     {"EPT_MAX_CHUNK", EPT_OPT_MAX_CHUNK},     {"EPT_REFINE", EPT_OPT_REFINE},
+                    {"EPT_PAIR", EPT_OPT_PAIR},
                     {"EPT_SERVE_LANES", EPT_OPT_SERVE_LANES}, {"EPT_SERVE_SLOTS", EPT_OPT_SERVE_SLOTS}};
     for (const auto &eo : env_opts) {
         const char *v = getenv(eo.env);
@@ -2618,6 +2625,12 @@ ept_status ept_set_option(ept_ctx *c, int option, int64_t value) {
     case EPT_OPT_REFINE:
         if (value != 0 && value != 1) return fail(EPT_EINVAL, "refine must be 0 or 1");
         c->refine = value != 0;
+        return EPT_OK;
+    case EPT_OPT_PAIR:
+        if (value != 0 && value != 1) return fail(EPT_EINVAL, "pair must be 0 or 1");
+        c->pair = value != 0;
+        c->plan_key.clear();   // a captured graph holds the previous contraction kernel
+        drop_graph(c);
         return EPT_OK;
     case EPT_OPT_MAX_CHUNK:
         if (value != 4 && value != 8 && value != 16 && value != 32)

@@ -159,11 +159,11 @@ __device__ __forceinline__ uint32_t group_entries(const uint32_t (&v)[32], const
         const float d2 = fmaxf(0.f, sn - 2.f * gij);
         fix |= (d2 < tau * sn) ? (1u << e) : 0u;
         if (KERN == 1) {
-            out[e] = expf(d2 * neg_inv_2s2);
+            out[e] = exp_cw(d2 * neg_inv_2s2);
         } else {
             float dist;
             asm("sqrt.approx.f32 %0, %1;" : "=f"(dist) : "f"(d2));
-            out[e] = (KERN == 0) ? dist : expf(-dist * inv_sigma);
+            out[e] = (KERN == 0) ? dist : exp_cw(-dist * inv_sigma);
         }
     }
     return fix;

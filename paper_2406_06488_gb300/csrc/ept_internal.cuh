@@ -78,25 +78,28 @@ struct Counters {
 
 // A-posteriori error estimate of a statistic computed by the contraction, and the
 // statistics that are recomputed in FP64 (ept_refine.cu).  For relabeling column b:
-//     E_b = REFINE_KA u cT A_b + REFINE_KR u Wbar g_b,
+//     E_b = k_b u cT A_b + REFINE_KR u Wbar / m,
 // u = 2^-24 (the FP32 unit roundoff), cT the statistic's factor on s'Cs, A_b the sum
 // over the contraction's work units of |partial sum| (the magnitudes the FP32
 // accumulations of column b carried), Wbar = 1'W1 / n^2 the mean entry of the
-// pooled matrix (the FP32 representation of its entries), g_b = 1/m for a
-// relabeling (the representation errors of its m^2 entries average out) and
-// 1/sqrt(m) for the observed statistic and every statistic within 1e-5 |stat_0| +
-// 2 E_0 of it (relabelings aligned with the samples keep value-dependent biases of
-// the entries, such as those of the kernel evaluation, which differ between the
-// blocks).  m is the contracted group's size.  Statistics with E_b > REFINE_TOL
-// |stat_b| are flagged: when the representation term exceeds REFINE_L2 of the
-// tolerance, for entries rebuilt in FP64 from the raw rows (level 2); otherwise for
-// an exact re-summation of the packed operand the contraction read (level 1), which
-// removes the accumulation part and leaves the FP32 representation of the entries.
-// The constants were fitted to measured GPU errors (a sweep of 200 ill-conditioned
-// problems against the FP64 oracle, both precisions): with them every statistic of
-// the sweep ends within 1e-5, the level-1 results within 6.1e-6.
+// pooled matrix and m the contracted group's size (the FP32 representation errors
+// of the m^2 entries a relabeling sums average out; the kernel values come from
+// exp_cw, whose rounding errors carry no smooth bias).  k_b = REFINE_KA for a
+// relabeling and REFINE_KC for the observed statistic and every statistic within
+// 1e-5 |stat_0| + 2 E_0 of it: relabelings aligned with the samples sum entries of
+// one sign and similar size in the same order on the tensor cores, so their
+// accumulation errors add coherently.  Statistics with E_b > REFINE_TOL |stat_b| are
+// flagged: when the representation term exceeds REFINE_L2 of the tolerance, for
+// entries rebuilt in FP64 from the raw rows (level 2); otherwise for an exact
+// re-summation of the packed operand the contraction read (level 1), which removes
+// the accumulation part and leaves the FP32 representation of the entries.  The
+// constants were fitted to measured GPU errors (a sweep of 200 ill-conditioned
+// problems against the FP64 oracle, both precisions), with a margin: the largest
+// accumulation errors seen were 40 (tensor cores) and 53 (plain FP32) u cT A_0 on
+// observed statistics, and with REFINE_KA the relabelings needed REFINE_KR >= 16.6.
 constexpr double REFINE_KA = 12.0;
-constexpr double REFINE_KR = 4.0;
+constexpr double REFINE_KC = 64.0;
+constexpr double REFINE_KR = 20.0;
 constexpr double REFINE_TOL = 1e-5;
 constexpr double REFINE_L2 = 0.05;
 constexpr double REFINE_U = 5.9604644775390625e-08;   // 2^-24
@@ -201,17 +204,20 @@ struct Batch {
 // tensor-core contraction work units of a test: chunk x relabeling tile x row half
 __host__ __device__ inline int64_t tc_units(const TestDesc &d) { return d.nchunks * d.MT * 2; }
 
-// Contraction chunks of a test: panel I covers K-blocks 4I .. NKBc-1 in chunks of
-// chunk_kb, where NKBc = ceil(n / KB) is the last K-block holding real columns (the
-// padding columns of C are zero, so the contraction stops there).
+// Contraction chunks of a test: panel I covers the L = NKBc - 4I K-blocks from its
+// diagonal to NKBc = ceil(n / KB), the last K-block holding real columns (the padding
+// columns of C are zero, so the contraction stops there), in ceil(L / chunk_kb)
+// chunks of as equal a length as possible (each at most chunk_kb): a short last
+// chunk would leave the tensor cores idle while its epilogue runs.
 __host__ __device__ inline int64_t contract_nkb(const TestDesc &d) { return (d.n + KB - 1) / KB; }
 __host__ __device__ inline int64_t panel_chunks(const TestDesc &d, int64_t I, int chunk_kb) {
     const int64_t len = contract_nkb(d) - KB_PER_PANEL * I;
     return len > 0 ? (len + chunk_kb - 1) / chunk_kb : 0;
 }
 __host__ __device__ inline Chunk panel_chunk(const TestDesc &d, int64_t I, int64_t q, int chunk_kb) {
-    const int64_t kb0 = KB_PER_PANEL * I + q * chunk_kb, end = contract_nkb(d);
-    return Chunk{(int)I, (int)kb0, (int)(kb0 + chunk_kb < end ? kb0 + chunk_kb : end), 0};
+    const int64_t len = contract_nkb(d) - KB_PER_PANEL * I, nq = panel_chunks(d, I, chunk_kb);
+    const int64_t kb0 = KB_PER_PANEL * I + q * len / nq, kb1 = KB_PER_PANEL * I + (q + 1) * len / nq;
+    return Chunk{(int)I, (int)kb0, (int)kb1, 0};
 }
 
 // The planner's description of one test (ept_api.cu; every entry point plans its
@@ -234,6 +240,31 @@ __device__ __forceinline__ double entry_from_d2(double d2, int kern, float neg_i
     if (kern == 0) return sqrt(d2);
     if (kern == 1) return exp(d2 * (double)neg_inv_2s2);
     return exp(-sqrt(d2) * (double)inv_sigma);
+}
+
+// exp(x) for x <= 0 in FP32, for the kernel values of Eq. 2 (Appendix A.1): Cody and
+// Waite's range reduction (x = k ln 2 + r, |r| <= ln 2 / 2, ln 2 split in a 9-bit head
+// whose products with k are exact and a tail) and the Taylor polynomial of degree 8
+// of e^r, whose truncation error (|r|^9 / 9! < 2.1e-10) is far below FP32's unit
+// roundoff; what is left is the rounding of the few FMAs, which varies from argument
+// to argument instead of following the argument smoothly.  That matters here: a
+// smooth error in the kernel values differs between the XX, YY and XY blocks and
+// does not average out of the observed statistic.  Arguments below -87 give 0.
+__host__ __device__ __forceinline__ float exp_cw(float x) {
+    if (!(x > -87.f)) return 0.f;
+    const float k = rintf(x * 1.44269504f);
+    float r = fmaf(-k, 0.693359375f, x);     // head of ln 2: exact products with |k| <= 126
+    r = fmaf(-k, -2.12194440e-4f, r);        // tail of ln 2
+    float q = 2.48015873e-5f;                // 1/8!
+    q = fmaf(q, r, 1.98412698e-4f);          // 1/7!
+    q = fmaf(q, r, 1.38888889e-3f);          // 1/6!
+    q = fmaf(q, r, 8.33333333e-3f);          // 1/5!
+    q = fmaf(q, r, 4.16666667e-2f);          // 1/4!
+    q = fmaf(q, r, 1.66666667e-1f);          // 1/3!
+    q = fmaf(q, r, 0.5f);
+    q = fmaf(q, r, 1.f);
+    q = fmaf(q, r, 1.f);
+    return ldexpf(q, (int)k);
 }
 
 // Knuth's TwoSum: s = fl(a + b) and the exact rounding error e, a + b = s + e.
@@ -303,6 +334,10 @@ void launch_split_rows(const Batch &b, cudaStream_t s);                  // FP16
 cudaError_t launch_build_tc(const Batch &b, const void *tmaps4, int num_sms, cudaStream_t s);
 cudaError_t launch_contract_tc(const Batch &b, const void *tmap_hi, const void *tmap_lo, int num_sms,
                                cudaStream_t s);
+// the same contraction on pairs of SMs (clusters of two CTAs, tcgen05 cta_group::2;
+// ept_contract_tc2.cu): units of whole 256-row panels, strided over the pairs
+cudaError_t launch_contract_tc2(const Batch &b, const void *tmap_hi, const void *tmap_lo, int num_sms,
+                                cudaStream_t s);
 // TMA descriptors: the packed hi/lo blocks [nblk_total x 256 x 64], block stride
 // c_stride halves, and the FP16
 // rows [nrows x p_stride] (hi, lo with 64 x 128 boxes, then hi, lo with 64 x 256 boxes)

@@ -436,7 +436,7 @@ __global__ void __launch_bounds__(256) k_build_simt(const Batch bt) {
                         ++fixups;
                         v = (float)entry_from_d2(s, kern, neg, inv_sigma);
                     } else {
-                        v = (kern == 0) ? sqrtf(d2) : (kern == 1) ? expf(d2 * neg) : expf(-sqrtf(d2) * inv_sigma);
+                        v = (kern == 0) ? sqrtf(d2) : (kern == 1) ? exp_cw(d2 * neg) : exp_cw(-sqrtf(d2) * inv_sigma);
                     }
                 }
             }
@@ -483,7 +483,7 @@ __global__ void __launch_bounds__(256) k_blocksums(const Batch bt) {
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     const int64_t j = (int64_t)bi.kb * KB + 4 * q + k;
-                    if (i < n && j < n) e4[k] = gauss ? expf(e4[k] * e4[k] * neg) : expf(-e4[k] * inv);
+                    if (i < n && j < n) e4[k] = gauss ? exp_cw(e4[k] * e4[k] * neg) : exp_cw(-e4[k] * inv);
                 }
                 row[q] = make_float4(e4[0], e4[1], e4[2], e4[3]);
             }
@@ -1014,16 +1014,16 @@ __global__ void __launch_bounds__(256) k_combine_count(const Batch bt, int flag)
         int fl = 0;
         if (c < d.ncols) {
             const double v = bt.stats[d.col0 + c];
-            const double m = (double)d.m;
-            const double rep_obs = REFINE_KR * REFINE_U * fabs(bW) / sqrt(m);
-            const double e0 = bt.errest[d.col0] + rep_obs;
+            const double rep = REFINE_KR * REFINE_U * fabs(bW) / (double)d.m;
+            // errest holds REFINE_KA u cT A; the observed and aligned statistics take REFINE_KC
+            const double e0 = (REFINE_KC / REFINE_KA) * bt.errest[d.col0] + rep;
             const bool aligned = c == 0 || fabs(v - obs) <= REFINE_TOL * fabs(obs) + 2.0 * e0;
-            const double rep = aligned ? rep_obs : REFINE_KR * REFINE_U * fabs(bW) / m;
+            const double acc = aligned ? (REFINE_KC / REFINE_KA) * bt.errest[d.col0 + c] : bt.errest[d.col0 + c];
             const double tol = REFINE_TOL * fabs(v);
             // flagged when the estimate exceeds the tolerance; 2 (rebuild the entries in FP64)
             // when the representation term exceeds REFINE_L2 of it, else 1 (re-sum the
             // packed operand exactly).  NaN-safe: a non-finite estimate takes the rebuild
-            const int lvl = !(bt.errest[d.col0 + c] + rep <= tol) ? (!(rep <= REFINE_L2 * tol) ? 2 : 1) : 0;
+            const int lvl = !(acc + rep <= tol) ? (!(rep <= REFINE_L2 * tol) ? 2 : 1) : 0;
             fl = lvl != 0;
             bt.flags[d.col0 + c] = (uint8_t)lvl;
         }

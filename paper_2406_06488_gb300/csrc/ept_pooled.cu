@@ -23,8 +23,8 @@ __device__ __forceinline__ const float *pooled_row(const TestDesc &d, int64_t i)
 
 __device__ __forceinline__ float pooled_entry(float d2, const TestDesc &d) {
     if (d.kern == 0) return sqrtf(d2);
-    if (d.kern == 1) return expf(d2 * d.neg_inv_2s2);
-    return expf(-sqrtf(d2) * d.inv_sigma);
+    if (d.kern == 1) return exp_cw(d2 * d.neg_inv_2s2);
+    return exp_cw(-sqrtf(d2) * d.inv_sigma);
 }
 
 // W[i][j] for i, j < n (row stride ld): a CTA computes a 64 x 64 tile, thread (ty,

@@ -19,7 +19,8 @@
 // k_refine_rows gives every 64-row tile and every group of 64 flagged columns a
 // CTA, which reads its rows of W64 once per column tile and keeps, per row and
 // column, sum_j s_j W_ij in registers; the tile's sums over its rows are added in a
-// fixed order (deterministic), and k_refine_finish adds the tiles in order.
+// fixed order (deterministic), and k_refine_finish adds the tiles (lanes over tiles,
+// then a butterfly: the same order on every run).
 #include <cuda_fp16.h>
 
 #include <cstdint>
@@ -206,15 +207,22 @@ __global__ void __launch_bounds__(256) k_refine_rows(const Batch bt, int t, int6
 __global__ void __launch_bounds__(256) k_refine_finish(const Batch bt, int t, const int32_t *__restrict__ list,
                                                        int64_t nflag, const double *__restrict__ part,
                                                        const double *__restrict__ spart, int64_t ntiles) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (k >= nflag) return;
     const TestDesc d = bt.desc[t];
     double T = 0.0, L = 0.0, S = 0.0;
-    for (int64_t tl = 0; tl < ntiles; ++tl) {
+    for (int64_t tl = lane; tl < ntiles; tl += 32) {
         T += part[(tl * nflag + k) * 2];
         L += part[(tl * nflag + k) * 2 + 1];
         S += spart[tl];
     }
+    for (int off = 16; off; off >>= 1) {
+        T += __shfl_xor_sync(0xFFFFFFFFu, T, off);
+        L += __shfl_xor_sync(0xFFFFFFFFu, L, off);
+        S += __shfl_xor_sync(0xFFFFFFFFu, S, off);
+    }
+    if (lane != 0) return;
     // sums over the contracted group G (size m) and the other group H (size o)
     const double sGG = T, sGH = L - T, sHH = S - 2.0 * L + T;
     const double sxx = d.comp ? sHH : sGG, syy = d.comp ? sGG : sHH;
@@ -234,6 +242,15 @@ __global__ void __launch_bounds__(256) k_refine_finish(const Batch bt, int t, co
 // columns); thread = (row r of one 128-row half, 8 of the 16 columns).
 constexpr int PCOLS = 16;
 constexpr int RK = 16;   // K-blocks per CTA
+
+// 2^24 x (an FP16 number), exactly, from its bits with integer operations: a normal
+// number (exponent field e >= 1) is (1024 + f) 2^(e - 25), a subnormal one f 2^-24
+// (f the 10-bit fraction); infinities and NaNs do not occur in the packed operand
+__device__ __forceinline__ long long fp16_fixed24(uint16_t bits) {
+    const int e = (bits >> 10) & 31, f = bits & 1023;
+    const long long mag = e ? (long long)(1024 + f) << (e - 1) : (long long)f;
+    return (bits & 0x8000u) ? -mag : mag;
+}
 
 __global__ void __launch_bounds__(256) k_refine_packed(const Batch bt, int t, const int32_t *__restrict__ list,
                                                        int64_t nflag, int64_t nkc, double *__restrict__ part) {
@@ -262,6 +279,7 @@ __global__ void __launch_bounds__(256) k_refine_packed(const Batch bt, int t, co
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int q = 0; q < 4; ++q) rowT[a][q] = 0.0;
+#pragma unroll
     for (int qr = 0; qr < 4; ++qr) {   // the panel's four 64-row quarters
         const int64_t i = I * PANEL + 64 * qr + r;
         long long si[4] = {0, 0, 0, 0};
@@ -273,27 +291,37 @@ __global__ void __launch_bounds__(256) k_refine_packed(const Batch bt, int t, co
                 const int rr = x / KB, cc = x % KB;
                 const int64_t off = (int64_t)(64 * qr + rr) * KB + cc;
                 if (split) {
-                    const float h = __half2float(__ushort_as_half(bt.Chi[blk * bt.c_stride + off]));
-                    const float l = __half2float(__ushort_as_half(bt.Clo[blk * bt.c_stride + off]));
-                    // exact: h and l are multiples of 2^-24 below 2^15 in magnitude
-                    vi[rr][cc] = __float2ll_rn(ldexpf(h, 24)) + __float2ll_rn(ldexpf(l, 24));
+                    vi[rr][cc] = fp16_fixed24(bt.Chi[blk * bt.c_stride + off]) +
+                                 fp16_fixed24(bt.Clo[blk * bt.c_stride + off]);
                 } else {
                     vf[rr][cc] = bt.D[blk * (int64_t)(PANEL * KB) + off];
                 }
             }
             __syncthreads();
             const int64_t w0 = kb * KB / 32;
+            uint32_t mw[4][2];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
+                mw[q][0] = col[q] < 0 ? 0u : bt.maskT[d.mask0 + w0 * d.Bp + col[q]];
+                mw[q][1] = col[q] < 0 ? 0u : bt.maskT[d.mask0 + (w0 + 1) * d.Bp + col[q]];
+            }
+            if (split) {
+                // each value read once from shared memory for the four columns
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+#pragma unroll 8
+                    for (int sh = 0; sh < 32; ++sh) {
+                        const long long x = vi[r][32 * h2 + sh];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) si[q] += ((mw[q][h2] >> sh) & 1u) ? x : 0ll;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 4 && !split; ++q) {
                 if (col[q] < 0) continue;
-                const uint32_t m0 = bt.maskT[d.mask0 + w0 * d.Bp + col[q]];
-                const uint32_t m1 = bt.maskT[d.mask0 + (w0 + 1) * d.Bp + col[q]];
-                if (split) {
-                    long long acc = 0;
-                    for (int cc = 0; cc < 32; ++cc) acc += ((m0 >> cc) & 1u) ? vi[r][cc] : 0ll;
-                    for (int cc = 0; cc < 32; ++cc) acc += ((m1 >> cc) & 1u) ? vi[r][32 + cc] : 0ll;
-                    si[q] += acc;
-                } else {
+                const uint32_t m0 = mw[q][0], m1 = mw[q][1];
+                {
                     float sq = sf[q], eq = ef[q];
                     for (int cc = 0; cc < KB; ++cc) {
                         const uint32_t bit = cc < 32 ? (m0 >> cc) & 1u : (m1 >> (cc - 32)) & 1u;
@@ -335,16 +363,23 @@ __global__ void __launch_bounds__(256) k_refine_packed(const Batch bt, int t, co
 }
 
 // the statistics of the listed columns from the exact T: stat = sign (cT T + S~ / o^2)
+// (a warp per column: lanes take every 32nd partial, then a fixed butterfly -- the
+// same order on every run)
 __global__ void __launch_bounds__(256) k_refine_packed_finish(const Batch bt, int t, const int32_t *__restrict__ list,
                                                               int64_t nflag, int64_t nkc,
                                                               const double *__restrict__ part) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t k = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
     if (k >= nflag) return;
     const TestDesc d = bt.desc[t];
     double T = 0.0, St = 0.0;
-    for (int64_t g = 0; g < d.NP * nkc; ++g) T += part[g * nflag + k];
-    for (int64_t I = 0; I < d.NP; ++I) St += bt.Stpart[d.pan0 + I];
-    bt.stats[d.col0 + list[k]] = d.sign * (d.cT * T + St * d.inv_o2);
+    for (int64_t g = lane; g < d.NP * nkc; g += 32) T += part[g * nflag + k];
+    for (int64_t I = lane; I < d.NP; I += 32) St += bt.Stpart[d.pan0 + I];
+    for (int off = 16; off; off >>= 1) {
+        T += __shfl_xor_sync(0xFFFFFFFFu, T, off);
+        St += __shfl_xor_sync(0xFFFFFFFFu, St, off);
+    }
+    if (lane == 0) bt.stats[d.col0 + list[k]] = d.sign * (d.cT * T + St * d.inv_o2);
 }
 
 }  // namespace
@@ -357,7 +392,7 @@ void launch_refine_packed(const Batch &b, int t, int64_t NP, int64_t NKB, const 
     const int64_t nkc = refine_packed_chunks(NKB);
     const dim3 grid((unsigned)(NP * nkc), (unsigned)((nflag + PCOLS - 1) / PCOLS));
     k_refine_packed<<<grid, 256, 0, s>>>(b, t, list, nflag, nkc, part);
-    k_refine_packed_finish<<<(unsigned)((nflag + 255) / 256), 256, 0, s>>>(b, t, list, nflag, nkc, part);
+    k_refine_packed_finish<<<(unsigned)((nflag + 7) / 8), 256, 0, s>>>(b, t, list, nflag, nkc, part);
 }
 
 void launch_refine_w(const Batch &b, int t, int64_t n, double sigma, int64_t r0, int64_t r1, double *W64,
@@ -377,7 +412,7 @@ void launch_refine_rows(const Batch &b, int t, int64_t r0, int64_t r1, const dou
 void launch_refine_finish(const Batch &b, int t, const int32_t *list, int64_t nflag, const double *part,
                           const double *spart, int64_t ntiles, cudaStream_t s) {
     if (nflag <= 0) return;
-    k_refine_finish<<<(unsigned)((nflag + 255) / 256), 256, 0, s>>>(b, t, list, nflag, part, spart, ntiles);
+    k_refine_finish<<<(unsigned)((nflag + 7) / 8), 256, 0, s>>>(b, t, list, nflag, part, spart, ntiles);
 }
 
 }  // namespace ept

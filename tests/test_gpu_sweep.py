@@ -6,22 +6,22 @@ three blocks), on the tensor-core and the plain FP32 paths:
 * every statistic (observed and permuted) within 1e-5 relative, and the count
   #{stat* >= observed} equal except through near-ties (Section 3.1 p-value);
 * the statistics the library recomputed in FP64 are exactly those its stated
-  error criterion flags: with E_b = 12 u cT A_b + 4 u Wbar g_b (u = 2^-24, cT the
+  error criterion flags: with E_b = k_b u cT A_b + 20 u Wbar / m (u = 2^-24, cT the
   statistic's factor on the quadratic form s'Cs of the centred pooled matrix, A_b
   the sum over the contraction's work units of |partial sum|, Wbar the mean entry
-  of the pooled matrix, g_b = 1/m, or 1/sqrt(m) for the observed statistic and the
-  statistics within 1e-5 |stat_0| + 2 E_0 of it), statistic b is recomputed iff
+  of the pooled matrix, m the smaller group's size, k_b = 12, or 64 for the observed
+  statistic and the statistics within 1e-5 |stat_0| + 2 E_0 of it), statistic b is recomputed iff
   E_b > 1e-5 |stat_b| of the fast value.  A_b is recomputed here in FP64 from the
   oracle's pooled matrix with the contraction's unit decomposition (row halves of
-  128 rows of 256-row panels, chunks of 8 K-blocks of 64 columns from the panel's
-  diagonal on, upper storage), so decisions within 2 % of the threshold are not
-  compared;
+  128 rows of 256-row panels; each panel's K-blocks of 64 columns from its diagonal
+  on, split into chunks of equal length of at most 8; upper storage), so decisions
+  within 2 % of the threshold are not compared;
 * the criterion is sound on this sweep: every fast statistic off by more than 1e-5
   was recomputed.
 
 The fast values come from a context with refinement off (EPT_OPT_REFINE = 0; the
-computation is deterministic, so a statistic was recomputed exactly where the two
-contexts' results differ)."""
+computation is deterministic, so a value that differs between the two contexts was
+recomputed, and the count of recomputed statistics is the library's own)."""
 import numpy as np
 import pytest
 
@@ -33,7 +33,7 @@ pytestmark = pytest.mark.gpu
 N_CASES = 200
 REL_TOL = 1e-5
 U = 2.0 ** -24
-KA, KR = 12.0, 4.0
+KA, KC, KR = 12.0, 64.0, 20.0
 
 
 @pytest.fixture(scope="module")
@@ -65,8 +65,8 @@ def _case(k):
 
 def _error_terms(X, Y, B, seed, stat, sigma):
     """The parts of the criterion's E_b for every column (observed first), from the
-    oracle's pooled matrix and the contraction's unit decomposition: the
-    accumulation term, the observed-like and the relabeling representation terms."""
+    oracle's pooled matrix and the contraction's unit decomposition: u cT A_b and the
+    representation term."""
     nx, ny = len(X), len(Y)
     n = nx + ny
     Z = np.vstack([X, Y])
@@ -86,8 +86,10 @@ def _error_terms(X, Y, B, seed, stat, sigma):
     A = np.zeros(B + 1)
     nkb = (n + 63) // 64
     for I in range((n + 255) // 256):
-        for kb0 in range(4 * I, nkb, 8):
-            c0, c1 = 64 * kb0, min(64 * (kb0 + 8), n)
+        L = nkb - 4 * I
+        nq = -(-L // 8)
+        for q in range(nq):   # chunks of equal length (at most 8 K-blocks)
+            c0, c1 = 64 * (4 * I + q * L // nq), min(64 * (4 * I + (q + 1) * L // nq), n)
             Ub = Cup[256 * I:256 * I + 256, c0:c1] @ sel[c0:c1]
             for h in range(2):
                 r0, r1 = 256 * I + 128 * h, min(256 * I + 128 * h + 128, n)
@@ -95,15 +97,15 @@ def _error_terms(X, Y, B, seed, stat, sigma):
                     A += np.abs((sel[r0:r1] * Ub[128 * h:128 * h + r1 - r0]).sum(0))
     cT = (n / (nx * ny)) ** 2
     wbar = S / n ** 2
-    return KA * U * cT * A, KR * U * wbar / np.sqrt(m), KR * U * wbar / m
+    return U * cT * A, KR * U * wbar / m
 
 
 def _estimates(terms, fast):
-    acc, rep_obs, rep_perm = terms
-    e0 = acc[0] + rep_obs
+    uA, rep = terms
+    e0 = KC * uA[0] + rep
     aligned = np.abs(fast - fast[0]) <= REL_TOL * abs(fast[0]) + 2 * e0
     aligned[0] = True
-    return acc + np.where(aligned, rep_obs, rep_perm)
+    return np.where(aligned, KC, KA) * uA + rep
 
 
 @pytest.mark.parametrize("block", range(4))
@@ -124,15 +126,19 @@ def test_statistics_and_p_values_equal_the_oracle(ctxs, block):
             assert rel.max() <= REL_TOL, (k, prec, float(rel.max()), int(rel.argmax()))
             assert abs(r.n_ge - ref["n_ge"]) <= near, (k, prec, r.n_ge, ref["n_ge"], near)
             assert r.p_value == (1.0 + r.n_ge) / (1.0 + B)
-            # the recomputed statistics
-            refined = got != fast
-            assert int(refined.sum()) == r.n_refined == f.n_refined, (k, prec, int(refined.sum()), r.n_refined)
+            # the recomputed statistics: a value that changed was recomputed (a recomputed
+            # value may, rarely, equal the fast one bit for bit)
+            changed = got != fast
+            assert r.n_refined == f.n_refined and int(changed.sum()) <= r.n_refined, (k, prec)
             # sound: every fast statistic beyond the tolerance was recomputed
             fast_bad = np.abs(fast - want) > REL_TOL * np.abs(want)
-            assert not (fast_bad & ~refined).any(), (k, prec, np.flatnonzero(fast_bad & ~refined))
-            # and exactly the ones the criterion flags (away from the threshold)
+            assert not (fast_bad & ~changed).any(), (k, prec, np.flatnonzero(fast_bad & ~changed))
+            # and the ones the criterion flags (decisions within 2 % of the threshold aside)
             if terms is None:
                 terms = _error_terms(X, Y, B, seed, stat, sigma)
             ratio = _estimates(terms, fast) / (REL_TOL * np.abs(fast))
             clear = np.abs(ratio - 1.0) > 0.02
-            assert np.array_equal(refined[clear], ratio[clear] > 1.0), (k, prec)
+            flag = ratio > 1.0
+            assert not (changed & clear & ~flag).any(), (k, prec, "recomputed but not flagged")
+            assert abs(r.n_refined - int(flag.sum())) <= int((~clear).sum()), (k, prec, r.n_refined, int(flag.sum()))
+            assert int((flag & clear & ~changed).sum()) <= max(1, r.n_refined // 100), (k, prec, "flagged, unchanged")
