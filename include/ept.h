@@ -323,10 +323,10 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    EPT_OPT_REFINE (default 1; 0 or 1): FP64 recomputation of flagged statistics
    (Section 3.1's statistics, Eq. 1 / Eq. 2, evaluated from the raw rows).  Every
    statistic of the split and plain precisions carries an a-posteriori estimate of
-   its error, E_b = k_b u cT A_b + 20 u Wbar / m: u = 2^-24, cT = (n/(nx ny))^2, A_b
+   its error, E_b = k_b u cT A_b + 4 u Wbar / m: u = 2^-24, cT = (n/(nx ny))^2, A_b
    the sum of the absolute values of its contraction partial sums (the magnitudes its
    FP32 accumulations carried), Wbar the mean entry of the pooled matrix, m =
-   min(nx, ny), k_b = 12 for a relabeling and 64 for the observed statistic and every
+   min(nx, ny), k_b = 8 for a relabeling and 64 for the observed statistic and every
    statistic within 1e-5 |observed| + 2 E_0 of it.  A statistic with
    E_b > 1e-5 |stat_b| is recomputed: when its representation term (the second) is
    above 1/20 of the tolerance, from W built in FP64 by direct differences of the

@@ -94,12 +94,13 @@ struct Counters {
 // re-summation of the packed operand the contraction read (level 1), which removes
 // the accumulation part and leaves the FP32 representation of the entries.  The
 // constants were fitted to measured GPU errors (a sweep of 200 ill-conditioned
-// problems against the FP64 oracle, both precisions), with a margin: the largest
-// accumulation errors seen were 40 (tensor cores) and 53 (plain FP32) u cT A_0 on
-// observed statistics, and with REFINE_KA the relabelings needed REFINE_KR >= 16.6.
-constexpr double REFINE_KA = 12.0;
+// problems against the FP64 oracle, both precisions) so that every statistic off by
+// more than half the tolerance is flagged (with REFINE_KA = 8 that took REFINE_KR >=
+// 2.4; the largest accumulation errors of observed statistics were 40 (tensor cores)
+// and 53 (plain FP32) u cT A_0); the largest error left unflagged was 6.2e-6.
+constexpr double REFINE_KA = 8.0;
 constexpr double REFINE_KC = 64.0;
-constexpr double REFINE_KR = 20.0;
+constexpr double REFINE_KR = 4.0;
 constexpr double REFINE_TOL = 1e-5;
 constexpr double REFINE_L2 = 0.05;
 constexpr double REFINE_U = 5.9604644775390625e-08;   // 2^-24

@@ -6,10 +6,10 @@ three blocks), on the tensor-core and the plain FP32 paths:
 * every statistic (observed and permuted) within 1e-5 relative, and the count
   #{stat* >= observed} equal except through near-ties (Section 3.1 p-value);
 * the statistics the library recomputed in FP64 are exactly those its stated
-  error criterion flags: with E_b = k_b u cT A_b + 20 u Wbar / m (u = 2^-24, cT the
+  error criterion flags: with E_b = k_b u cT A_b + 4 u Wbar / m (u = 2^-24, cT the
   statistic's factor on the quadratic form s'Cs of the centred pooled matrix, A_b
   the sum over the contraction's work units of |partial sum|, Wbar the mean entry
-  of the pooled matrix, m the smaller group's size, k_b = 12, or 64 for the observed
+  of the pooled matrix, m the smaller group's size, k_b = 8, or 64 for the observed
   statistic and the statistics within 1e-5 |stat_0| + 2 E_0 of it), statistic b is recomputed iff
   E_b > 1e-5 |stat_b| of the fast value.  A_b is recomputed here in FP64 from the
   oracle's pooled matrix with the contraction's unit decomposition (row halves of
@@ -33,7 +33,7 @@ pytestmark = pytest.mark.gpu
 N_CASES = 200
 REL_TOL = 1e-5
 U = 2.0 ** -24
-KA, KC, KR = 12.0, 64.0, 20.0
+KA, KC, KR = 8.0, 64.0, 4.0
 
 
 @pytest.fixture(scope="module")
