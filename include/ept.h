@@ -41,7 +41,7 @@
 extern "C" {
 #endif
 
-#define EPT_ABI_VERSION 5
+#define EPT_ABI_VERSION 6
 
 typedef enum {
     EPT_OK = 0,
@@ -340,12 +340,18 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    features whose permuted statistics are far below the FP32 resolution of the
    kernel values; ept_result.n_refined counts them.  Not applied in the streaming
    mode, by the pre-computation baseline or by ept_test_static.
-   EPT_OPT_PAIR (default 0; 0 or 1): the tensor-core contraction on pairs of SMs
-   (clusters of two CTAs, tcgen05 cta_group::2): a work unit covers a whole 256-row
-   panel, each CTA of the pair loads its 128 rows of the operand and expands its half
-   of the 256 relabelings, one CTA issues the MMAs for both (less shared-memory
-   traffic and relabeling expansion per multiply-add).  Same statistics as the
-   single-SM kernel up to the accumulation order.
+   EPT_OPT_CONTRACTION (default 0; 0..3): the tensor-core contraction kernel.  1:
+   relabelings as the MMA's shared-memory operand (N = 256 relabelings, M = 128 rows
+   of C; producer warps expand the mask bits into shared memory).  2: the same on
+   pairs of SMs (clusters of two CTAs, tcgen05 cta_group::2; a work unit covers a
+   whole 256-row panel, each CTA loads its 128 rows of the operand and expands its
+   half of the relabelings, one CTA issues the MMAs for both).  3: relabelings as the
+   tensor-memory operand (M = 128 relabelings stored from registers with tcgen05.st,
+   N = 128 rows of C from shared memory; each epilogue thread sums its own
+   relabeling's row values, no transposes).  0: the library's choice (1).  Measured
+   on a GB300 (n = 5000, B = 10^4 contraction): 1 319 us, 2 324 us, 3 451 us (the
+   MMA pipe alone, with N = 128, needs 366 us for the work that N = 256 does in 254
+   us).  The statistics agree to the accumulation order.
    EPT_OPT_SERVE_LANES (default 3, 1..16): serving batches in flight at once;
    EPT_OPT_SERVE_SLOTS (default 256): serving requests in flight at once; both
    before the first ept_submit.  EPT_EINVAL for an unknown option or value.
@@ -367,7 +373,7 @@ enum {
     EPT_OPT_WAIT_LIMIT_MS = 10,
     EPT_OPT_MAX_CHUNK = 11,
     EPT_OPT_REFINE = 12,
-    EPT_OPT_PAIR = 13
+    EPT_OPT_CONTRACTION = 13
 };
 ept_status ept_set_option(ept_ctx *ctx, int option, int64_t value);
 

@@ -560,7 +560,7 @@ struct ept_ctx {
     unsigned long long wait_ns = 0;     // limit of the kernels' bounded waits (0: their default, 2 s)
     int max_chunk = CHUNK_KB_DEFAULT;   // longest contraction unit the autotuner may pick (precision)
     bool refine = true;                 // recompute flagged statistics (EPT_OPT_REFINE)
-    bool pair = false;                  // contraction on pairs of SMs (EPT_OPT_PAIR)
+    int contraction = 0;                // tensor-core contraction kernel (EPT_OPT_CONTRACTION; 0: default)
     uint8_t *refine_buf = nullptr;      // scratch of the recomputation (grows, kept until ept_destroy)
     size_t refine_cap = 0;
     ept_allocator alloc{};              // caller-supplied device memory (alloc.alloc == nullptr: cudaMalloc)
@@ -588,6 +588,10 @@ struct ept_ctx {
     std::unique_ptr<HostCopier> copier;   // started by the first large pageable input
     std::string tune_file;
 };
+
+// the tensor-core contraction kernel of a run: 1 relabelings in shared memory (the
+// default: measured fastest), 2 the same on pairs of SMs, 3 relabelings in tensor memory
+static int contraction_kernel(const ept_ctx *c) { return c->contraction ? c->contraction : 1; }
 
 namespace {
 
@@ -943,8 +947,11 @@ ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed,
         char emsg[160];
         if (!encode_block_tmaps(&th, &tl, b.Chi, b.Clo, P.nblk, b.c_stride, emsg, sizeof(emsg)))
             return fail(EPT_ECUDA, "%s", emsg);
-        if (c->pair) CK(launch_contract_tc2(b, &th, &tl, c->num_sms, s));
-        else CK(launch_contract_tc(b, &th, &tl, c->num_sms, s));
+        switch (contraction_kernel(c)) {
+        case 2: CK(launch_contract_tc2(b, &th, &tl, c->num_sms, s)); break;
+        case 3: CK(launch_contract_tm(b, &th, &tl, c->num_sms, s)); break;
+        default: CK(launch_contract_tc(b, &th, &tl, c->num_sms, s)); break;
+        }
     } else {
         launch_contract_simt(b, s);
         CK(cudaGetLastError());
@@ -2036,6 +2043,7 @@ ept_status lane_enqueue(Server *S, Lane &L) {
     c->arena = L.arena;   // the kernels and staging address the lane's scratch through the context
     c->arena_cap = L.plan.total;
     c->refine = S->owner->refine;
+    c->contraction = S->owner->contraction;
     stage_host(c, L.plan, L.specs, false);
     st = enqueue_device(c, L.plan, s, false);
     c->arena = nullptr;
@@ -2311,7 +2319,7 @@ ept_status ept_create_ex(ept_ctx **out, int device, size_t mem_budget_bytes, con
                     {"EPT_DRAW_MODE", EPT_OPT_DRAW_MODE},     {"EPT_DEBUG_CHECKS", EPT_OPT_DEBUG_CHECKS},
                     {"EPT_STREAM_BLOCKS", EPT_OPT_STREAM_BLOCKS}, {"EPT_WAIT_LIMIT_MS", EPT_OPT_WAIT_LIMIT_MS},
                     {"EPT_MAX_CHUNK", EPT_OPT_MAX_CHUNK},     {"EPT_REFINE", EPT_OPT_REFINE},
-                    {"EPT_PAIR", EPT_OPT_PAIR},
+                    {"EPT_CONTRACTION", EPT_OPT_CONTRACTION},
                     {"EPT_SERVE_LANES", EPT_OPT_SERVE_LANES}, {"EPT_SERVE_SLOTS", EPT_OPT_SERVE_SLOTS}};
     for (const auto &eo : env_opts) {
         const char *v = getenv(eo.env);
@@ -2626,9 +2634,9 @@ ept_status ept_set_option(ept_ctx *c, int option, int64_t value) {
         if (value != 0 && value != 1) return fail(EPT_EINVAL, "refine must be 0 or 1");
         c->refine = value != 0;
         return EPT_OK;
-    case EPT_OPT_PAIR:
-        if (value != 0 && value != 1) return fail(EPT_EINVAL, "pair must be 0 or 1");
-        c->pair = value != 0;
+    case EPT_OPT_CONTRACTION:
+        if (value < 0 || value > 3) return fail(EPT_EINVAL, "contraction must be 0, 1, 2 or 3");
+        c->contraction = (int)value;
         c->plan_key.clear();   // a captured graph holds the previous contraction kernel
         drop_graph(c);
         return EPT_OK;

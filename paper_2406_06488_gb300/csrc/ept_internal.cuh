@@ -339,6 +339,11 @@ cudaError_t launch_contract_tc(const Batch &b, const void *tmap_hi, const void *
 // ept_contract_tc2.cu): units of whole 256-row panels, strided over the pairs
 cudaError_t launch_contract_tc2(const Batch &b, const void *tmap_hi, const void *tmap_lo, int num_sms,
                                 cudaStream_t s);
+// the same contraction with the relabeling tile as the tensor-memory operand
+// (ept_contract_tm.cu): M = 128 relabelings, N = 128 rows of C; the same units and
+// partial sums as launch_contract_tc
+cudaError_t launch_contract_tm(const Batch &b, const void *tmap_hi, const void *tmap_lo, int num_sms,
+                               cudaStream_t s);
 // TMA descriptors: the packed hi/lo blocks [nblk_total x 256 x 64], block stride
 // c_stride halves, and the FP16
 // rows [nrows x p_stride] (hi, lo with 64 x 128 boxes, then hi, lo with 64 x 256 boxes)

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libept.so")
 
 STAT = {"ed": 0, "mmd": 1, "mmd_gauss": 1, "mmd_laplace": 2}
 SIGMA_MEDIAN = -1.0   # EPT_SIGMA_MEDIAN: bandwidth from the median heuristic
-ABI_VERSION = 5       # EPT_ABI_VERSION this binding's structures follow
+ABI_VERSION = 6       # EPT_ABI_VERSION this binding's structures follow
 PREC = {"plain_fp32": 0, "split_bf16": 1, "pooled_fp32": 2}   # pooled_fp32: Algorithm 5 baseline
 STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT_ECUDA", 5: "EPT_ETIMEOUT",
           6: "EPT_ECANCELLED", 7: "EPT_ENOTFOUND", 8: "EPT_EUNSUPPORTED", 9: "EPT_EINTERNAL"}
@@ -206,7 +206,7 @@ def plan_check(shapes, unit_kb: int = 8, num_sms: int = 152, stream_blocks: int 
 
 OPTION = {"graphs": 1, "autotune": 2, "serve_lanes": 3, "serve_slots": 4, "draw_mode": 5,
           "fault_inject_alloc": 6, "fault_inject_stall": 7, "debug_checks": 8, "stream_blocks": 9,
-          "wait_limit_ms": 10, "max_chunk": 11, "refine": 12, "pair": 13}
+          "wait_limit_ms": 10, "max_chunk": 11, "refine": 12, "contraction": 13}
 
 
 class Context:
