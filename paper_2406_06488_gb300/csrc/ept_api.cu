@@ -1154,60 +1154,103 @@ ept_status refine_after(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &
     if (!c->refine || P.off_flags == 0) return EPT_OK;
     const Staging S = staging_layout(P);
     const Counters *ctr = (const Counters *)(c->pinned + S.res_ctr);
-    bool any = false;
-    for (int t = 0; t < P.n_tests; ++t)
-        any |= ctr[t].n_flag > 0 && test_error(P, ctr, t) == EPT_OK && !(per_test && (*per_test)[t].st != EPT_OK);
-    if (!any) return EPT_OK;
-    NvtxRange range("ept.refine");
-    const Batch b = device_view(c, P);
-    std::vector<uint8_t> fl;
-    std::vector<int32_t> list;
+    std::vector<int> tl;   // tests with flagged statistics
+    size_t nfl = 0;
     for (int t = 0; t < P.n_tests; ++t) {
         if (ctr[t].n_flag == 0 || test_error(P, ctr, t) != EPT_OK) continue;
         if (per_test && (*per_test)[t].st != EPT_OK) continue;
+        tl.push_back(t);
+        nfl += (size_t)P.desc[t].ncols;
+    }
+    if (tl.empty()) return EPT_OK;
+    NvtxRange range("ept.refine");
+    const Batch b = device_view(c, P);
+    // the flags of those tests, read back together
+    std::vector<uint8_t> fl(nfl);
+    std::vector<size_t> fl_off;
+    for (size_t k = 0, o = 0; k < tl.size(); ++k) {
+        const TestDesc &d = P.desc[tl[k]];
+        fl_off.push_back(o);
+        CK(cudaMemcpyAsync(fl.data() + o, b.flags + d.col0, (size_t)d.ncols, cudaMemcpyDeviceToHost, s));
+        o += (size_t)d.ncols;
+    }
+    CK(cudaStreamSynchronize(s));
+    // level 1: exact re-summation of the packed operand (the accumulation part), every
+    // test's groups of flagged columns in one launch; level 2: the entries rebuilt in
+    // FP64 from the raw rows (the representation part), test by test.  The host lists
+    // live until the final synchronisation.
+    std::vector<int32_t> list1, list2;
+    std::vector<RefineJob> jobs;
+    std::vector<int64_t> l2_first(tl.size() + 1, 0);
+    int64_t part1 = 0, max_ctas = 0;
+    size_t l2_bytes = 0;
+    for (size_t k = 0; k < tl.size(); ++k) {
+        const int t = tl[k];
         const TestDesc &d = P.desc[t];
-        fl.resize((size_t)d.ncols);
-        CK(cudaMemcpyAsync(fl.data(), b.flags + d.col0, (size_t)d.ncols, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
-        // level 1: exact re-summation of the packed operand (the accumulation part)
-        list.clear();
-        for (int64_t k = 0; k < d.ncols; ++k)
-            if (fl[(size_t)k] == 1) list.push_back((int32_t)k);
-        if (!list.empty()) {
-            const int64_t n1 = (int64_t)list.size();
-            const size_t b_list = align_up(4 * (size_t)n1, 256);
-            uint8_t *mem = nullptr;
-            ept_status st = refine_scratch(c, b_list + 8 * (size_t)(d.NP * refine_packed_chunks(d.NKB)) * n1, s, &mem);
-            if (st != EPT_OK) return st;
-            int32_t *dlist = (int32_t *)mem;
-            double *part = (double *)(mem + b_list);
-            cudaError_t e = cudaMemcpyAsync(dlist, list.data(), 4 * (size_t)n1, cudaMemcpyHostToDevice, s);
-            if (e == cudaSuccess) {
-                launch_refine_packed(b, t, d.NP, d.NKB, dlist, n1, part, s);
-                e = cudaGetLastError();
-            }
-            if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the list's host copy stays valid until here
-            if (e != cudaSuccess) return fail(EPT_ECUDA, "exact re-summation failed: %s", cudaGetErrorString(e));
+        const uint8_t *f = fl.data() + fl_off[k];
+        const int64_t first1 = (int64_t)list1.size();
+        for (int64_t j = 0; j < d.ncols; ++j) {
+            if (f[j] == 1) list1.push_back((int32_t)j);
+            if (f[j] == 2) list2.push_back((int32_t)j);
         }
-        // level 2: the entries rebuilt in FP64 from the raw rows (the representation part)
-        list.clear();
-        for (int64_t k = 0; k < d.ncols; ++k)
-            if (fl[(size_t)k] == 2) list.push_back((int32_t)k);
-        const int64_t nflag = (int64_t)list.size();
+        const int32_t nkc = (int32_t)refine_packed_chunks(d.NKB);
+        for (int64_t j = first1; j < (int64_t)list1.size(); j += REFINE_JOB_COLS) {
+            RefineJob J;
+            J.t = t;
+            J.ncol = (int32_t)std::min<int64_t>(REFINE_JOB_COLS, (int64_t)list1.size() - j);
+            J.np = (int32_t)d.NP;
+            J.nkc = nkc;
+            J.list0 = j;
+            J.part0 = part1;
+            part1 += (int64_t)J.np * J.nkc * J.ncol;
+            max_ctas = std::max<int64_t>(max_ctas, (int64_t)J.np * J.nkc);
+            jobs.push_back(J);
+        }
+        l2_first[k + 1] = (int64_t)list2.size();
+        const int64_t n2 = l2_first[k + 1] - l2_first[k];
+        if (n2 > 0) {
+            const int64_t ntiles = (d.n + 63) / 64;
+            int64_t rows_w = (int64_t)(REFINE_W64_BYTES / (8 * (size_t)d.n)) / 64 * 64;
+            rows_w = std::max<int64_t>(64, std::min<int64_t>(rows_w, ntiles * 64));
+            l2_bytes = std::max(l2_bytes, align_up(16 * (size_t)ntiles * n2, 256) + align_up(8 * (size_t)ntiles, 256) +
+                                              8 * (size_t)rows_w * (size_t)d.n);
+        }
+    }
+    const size_t b_list1 = align_up(4 * list1.size() + 4, 256), b_list2 = align_up(4 * list2.size() + 4, 256),
+                 b_jobs = align_up(sizeof(RefineJob) * jobs.size() + 16, 256), b_part1 = align_up(8 * (size_t)part1 + 8, 256);
+    uint8_t *mem = nullptr;
+    ept_status st = refine_scratch(c, b_list1 + b_list2 + b_jobs + b_part1 + l2_bytes, s, &mem);
+    if (st != EPT_OK) return st;
+    int32_t *dlist1 = (int32_t *)mem, *dlist2 = (int32_t *)(mem + b_list1);
+    RefineJob *djobs = (RefineJob *)(mem + b_list1 + b_list2);
+    double *dpart1 = (double *)(mem + b_list1 + b_list2 + b_jobs);
+    uint8_t *l2mem = mem + b_list1 + b_list2 + b_jobs + b_part1;
+    cudaError_t e = cudaSuccess;
+    if (!jobs.empty()) {
+        e = cudaMemcpyAsync(dlist1, list1.data(), 4 * list1.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(djobs, jobs.data(), sizeof(RefineJob) * jobs.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) {
+            launch_refine_packed(b, djobs, (int64_t)jobs.size(), max_ctas, dlist1, dpart1, s);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess && !list2.empty())
+        e = cudaMemcpyAsync(dlist2, list2.data(), 4 * list2.size(), cudaMemcpyHostToDevice, s);
+    for (size_t k = 0; k < tl.size() && e == cudaSuccess; ++k) {
+        const int64_t nflag = l2_first[k + 1] - l2_first[k];
         if (nflag == 0) continue;
+        const int t = tl[k];
+        const TestDesc &d = P.desc[t];
         const double sigma = d.stat == EPT_STAT_ED ? 0.0 : (d.median ? (double)median_sigma(ctr[t]) : d.sigma64);
         const int64_t ntiles = (d.n + 63) / 64;
         int64_t rows_w = (int64_t)(REFINE_W64_BYTES / (8 * (size_t)d.n)) / 64 * 64;
         rows_w = std::max<int64_t>(64, std::min<int64_t>(rows_w, ntiles * 64));
-        const size_t b_list = align_up(4 * (size_t)nflag, 256), b_part = align_up(16 * (size_t)ntiles * nflag, 256),
-                     b_spart = align_up(8 * (size_t)ntiles, 256), b_w = 8 * (size_t)rows_w * (size_t)d.n;
-        uint8_t *m8 = nullptr;
-        ept_status st = refine_scratch(c, b_list + b_part + b_spart + b_w, s, &m8);
-        if (st != EPT_OK) return st;
-        int32_t *dlist = (int32_t *)m8;
-        double *part = (double *)(m8 + b_list), *spart = (double *)(m8 + b_list + b_part);
-        double *W64 = (double *)(m8 + b_list + b_part + b_spart);
-        cudaError_t e = cudaMemcpyAsync(dlist, list.data(), 4 * (size_t)nflag, cudaMemcpyHostToDevice, s);
+        const size_t b_part = align_up(16 * (size_t)ntiles * nflag, 256), b_spart = align_up(8 * (size_t)ntiles, 256);
+        // the tests' rebuilds reuse one region in stream order
+        const int32_t *dlist = dlist2 + l2_first[k];
+        double *part = (double *)l2mem, *spart = (double *)(l2mem + b_part);
+        double *W64 = (double *)(l2mem + b_part + b_spart);
         for (int64_t r0 = 0; r0 < d.n && e == cudaSuccess; r0 += rows_w) {
             const int64_t r1 = std::min<int64_t>(d.n, r0 + rows_w);
             launch_refine_w(b, t, d.n, sigma, r0, r1, W64, s);
@@ -1218,9 +1261,9 @@ ept_status refine_after(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &
             launch_refine_finish(b, t, dlist, nflag, part, spart, ntiles, s);
             e = cudaGetLastError();
         }
-        if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the list's host copy stays valid until here
-        if (e != cudaSuccess) return fail(EPT_ECUDA, "FP64 refinement failed: %s", cudaGetErrorString(e));
     }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // the host lists stay valid until here
+    if (e != cudaSuccess) return fail(EPT_ECUDA, "recomputation of flagged statistics failed: %s", cudaGetErrorString(e));
     // large scratch (an FP64 rebuild's window) is not kept between calls
     if (c->refine_cap > ((size_t)256 << 20)) {
         device_free(c, c->refine_buf, s);

@@ -316,12 +316,20 @@ void launch_refine_rows(const Batch &b, int t, int64_t r0, int64_t r1, const dou
 void launch_refine_finish(const Batch &b, int t, const int32_t *list, int64_t nflag, const double *part,
                           const double *spart, int64_t ntiles, cudaStream_t s);
 void launch_reset_counts(const Batch &b, cudaStream_t s);   // n_ge = n_near = 0 before a recount
-// the statistics of the listed columns of test t (NP row panels, NKB K-blocks) from the
-// packed operand the contraction read, summed exactly (part: NP x chunks x nflag doubles,
-// chunks = refine_packed_chunks(NKB))
+// The statistics of flagged columns from the packed operand the contraction read,
+// summed exactly: one job per group of up to REFINE_JOB_COLS columns of one test
+// (list[list0 ..] test-local column indexes; part[part0 + g * ncol + k] for the
+// test's np x nkc (panel, chunk) pairs g, nkc = refine_packed_chunks(NKB)); every job
+// of a run in one launch (max_ctas = the largest np x nkc).
+constexpr int REFINE_JOB_COLS = 16;
+struct RefineJob {
+    int32_t t, ncol;
+    int32_t np, nkc;
+    int64_t list0, part0;
+};
 int64_t refine_packed_chunks(int64_t NKB);
-void launch_refine_packed(const Batch &b, int t, int64_t NP, int64_t NKB, const int32_t *list, int64_t nflag,
-                          double *part, cudaStream_t s);
+void launch_refine_packed(const Batch &b, const RefineJob *jobs, int64_t njobs, int64_t max_ctas,
+                          const int32_t *list, double *part, cudaStream_t s);
 
 // single-draw-stream export (ept_perm_masks): columns 0..count-1 = draws b0..b0+count-1
 void launch_perm_masks_plain(uint64_t seed, int nx, int ny, int64_t b0, int64_t count, int nw, uint32_t *maskT,

@@ -238,10 +238,11 @@ __global__ void __launch_bounds__(256) k_refine_finish(const Batch bt, int t, co
 // FP16 numbers that are both multiples of 2^-24 with |hi + lo| < 2^15, so 2^24 c C_ij
 // is an integer below 2^39 and a row of up to 2^22 entries sums exactly in int64; on
 // the plain path the FP32 entries are summed with TwoSum-compensated FP32 pairs.  The
-// rows' sums meet in FP64.  CTA = (row panel I, chunk of RK K-blocks, 16 flagged
-// columns); thread = (row r of one 128-row half, 8 of the 16 columns).
-constexpr int PCOLS = 16;
-constexpr int RK = 16;   // K-blocks per CTA
+// rows' sums meet in FP64.  One launch serves every flagged test of a run: a job is
+// a group of up to 16 flagged columns of one test; CTA = (row panel I, chunk of RK
+// K-blocks) x job; thread = (row r of a 64-row quarter, 4 of the 16 columns).
+constexpr int PCOLS = REFINE_JOB_COLS;
+constexpr int RK = 8;   // K-blocks per CTA
 
 // 2^24 x (an FP16 number), exactly, from its bits with integer operations: a normal
 // number (exponent field e >= 1) is (1024 + f) 2^(e - 25), a subnormal one f 2^-24
@@ -252,17 +253,20 @@ __device__ __forceinline__ long long fp16_fixed24(uint16_t bits) {
     return (bits & 0x8000u) ? -mag : mag;
 }
 
-__global__ void __launch_bounds__(256) k_refine_packed(const Batch bt, int t, const int32_t *__restrict__ list,
-                                                       int64_t nflag, int64_t nkc, double *__restrict__ part) {
+__global__ void __launch_bounds__(256) k_refine_packed(const Batch bt, const RefineJob *__restrict__ jobs,
+                                                       const int32_t *__restrict__ list, double *__restrict__ part) {
     // the values of 64 rows x 64 columns (int64 fixed point or FP32), then the sums
     __shared__ __align__(16) uint8_t sm[PANEL * (PCOLS + 1) * 8];
     long long(*vi)[KB + 1] = reinterpret_cast<long long(*)[KB + 1]>(sm);
     float(*vf)[KB + 1] = reinterpret_cast<float(*)[KB + 1]>(sm);
     double(*red)[PCOLS + 1] = reinterpret_cast<double(*)[PCOLS + 1]>(sm);
     static_assert(64 * (KB + 1) * 8 <= PANEL * (PCOLS + 1) * 8, "value buffer");
+    const RefineJob J = jobs[blockIdx.y];
+    if ((int64_t)blockIdx.x >= (int64_t)J.np * J.nkc) return;
+    const int t = J.t;
     const TestDesc d = bt.desc[t];
+    const int64_t nkc = J.nkc;
     const int64_t I = blockIdx.x / nkc, kc = blockIdx.x % nkc;
-    const int64_t k0 = (int64_t)blockIdx.y * PCOLS;
     const int r = threadIdx.x & 63, cg = threadIdx.x >> 6;   // row r of a 64-row quarter, columns 4 cg ..
     const bool split = d.scaled != 0;
     const int64_t nkb = contract_nkb(d);
@@ -271,8 +275,8 @@ __global__ void __launch_bounds__(256) k_refine_packed(const Batch bt, int t, co
     int64_t col[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const int64_t k = k0 + 4 * cg + q;
-        col[q] = k < nflag ? (int64_t)list[k] : -1;
+        const int k = 4 * cg + q;
+        col[q] = k < J.ncol ? (int64_t)list[J.list0 + k] : -1;
     }
     double rowT[4][4];   // [quarter][column]
 #pragma unroll
@@ -351,48 +355,46 @@ __global__ void __launch_bounds__(256) k_refine_packed(const Batch bt, int t, co
 #pragma unroll
         for (int q = 0; q < 4; ++q) red[64 * qr + r][4 * cg + q] = rowT[qr][q];
     __syncthreads();
-    if (threadIdx.x < PCOLS) {
-        const int64_t k = k0 + threadIdx.x;
-        if (k < nflag) {
-            double T = 0.0;
-            for (int rr = 0; rr < PANEL; ++rr) T += red[rr][threadIdx.x];
-            const double inv_c = split ? 1.0 / (double)packed_scale(bt.ctr[t]) : 1.0;
-            part[(I * nkc + kc) * nflag + k] = T * inv_c;
-        }
+    if (threadIdx.x < J.ncol) {
+        double T = 0.0;
+        for (int rr = 0; rr < PANEL; ++rr) T += red[rr][threadIdx.x];
+        const double inv_c = split ? 1.0 / (double)packed_scale(bt.ctr[t]) : 1.0;
+        part[J.part0 + (I * nkc + kc) * J.ncol + threadIdx.x] = T * inv_c;
     }
 }
 
 // the statistics of the listed columns from the exact T: stat = sign (cT T + S~ / o^2)
-// (a warp per column: lanes take every 32nd partial, then a fixed butterfly -- the
-// same order on every run)
-__global__ void __launch_bounds__(256) k_refine_packed_finish(const Batch bt, int t, const int32_t *__restrict__ list,
-                                                              int64_t nflag, int64_t nkc,
-                                                              const double *__restrict__ part) {
-    const int64_t k = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (k >= nflag) return;
-    const TestDesc d = bt.desc[t];
+// (CTA = job, a warp per column of the job: lanes take every 32nd partial, then a
+// fixed butterfly -- the same order on every run)
+__global__ void __launch_bounds__(32 * REFINE_JOB_COLS) k_refine_packed_finish(const Batch bt,
+                                                                             const RefineJob *__restrict__ jobs,
+                                                                             const int32_t *__restrict__ list,
+                                                                             const double *__restrict__ part) {
+    const RefineJob J = jobs[blockIdx.x];
+    const int k = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (k >= J.ncol) return;
+    const TestDesc d = bt.desc[J.t];
     double T = 0.0, St = 0.0;
-    for (int64_t g = lane; g < d.NP * nkc; g += 32) T += part[g * nflag + k];
+    for (int64_t g = lane; g < (int64_t)J.np * J.nkc; g += 32) T += part[J.part0 + g * J.ncol + k];
     for (int64_t I = lane; I < d.NP; I += 32) St += bt.Stpart[d.pan0 + I];
     for (int off = 16; off; off >>= 1) {
         T += __shfl_xor_sync(0xFFFFFFFFu, T, off);
         St += __shfl_xor_sync(0xFFFFFFFFu, St, off);
     }
-    if (lane == 0) bt.stats[d.col0 + list[k]] = d.sign * (d.cT * T + St * d.inv_o2);
+    if (lane == 0) bt.stats[d.col0 + list[J.list0 + k]] = d.sign * (d.cT * T + St * d.inv_o2);
 }
 
 }  // namespace
 
 int64_t refine_packed_chunks(int64_t NKB) { return (NKB + RK - 1) / RK; }
 
-void launch_refine_packed(const Batch &b, int t, int64_t NP, int64_t NKB, const int32_t *list, int64_t nflag,
-                          double *part, cudaStream_t s) {
-    if (nflag <= 0) return;
-    const int64_t nkc = refine_packed_chunks(NKB);
-    const dim3 grid((unsigned)(NP * nkc), (unsigned)((nflag + PCOLS - 1) / PCOLS));
-    k_refine_packed<<<grid, 256, 0, s>>>(b, t, list, nflag, nkc, part);
-    k_refine_packed_finish<<<(unsigned)((nflag + 7) / 8), 256, 0, s>>>(b, t, list, nflag, nkc, part);
+void launch_refine_packed(const Batch &b, const RefineJob *jobs, int64_t njobs, int64_t max_ctas,
+                          const int32_t *list, double *part, cudaStream_t s) {
+    for (int64_t j0 = 0; j0 < njobs; j0 += 65535) {   // grid.y holds at most 65535 jobs
+        const int64_t nj = njobs - j0 < 65535 ? njobs - j0 : 65535;
+        k_refine_packed<<<dim3((unsigned)max_ctas, (unsigned)nj), 256, 0, s>>>(b, jobs + j0, list, part);
+        k_refine_packed_finish<<<(unsigned)nj, 32 * REFINE_JOB_COLS, 0, s>>>(b, jobs + j0, list, part);
+    }
 }
 
 void launch_refine_w(const Batch &b, int t, int64_t n, double sigma, int64_t r0, int64_t r1, double *W64,
