@@ -31,6 +31,7 @@
 // by binary search in a prefix-sum array over the tests (BatchPrefix).
 #pragma once
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 namespace ept {
@@ -250,9 +251,12 @@ __device__ __forceinline__ double entry_from_d2(double d2, int kern, float neg_i
 // roundoff; what is left is the rounding of the few FMAs, which varies from argument
 // to argument instead of following the argument smoothly.  That matters here: a
 // smooth error in the kernel values differs between the XX, YY and XY blocks and
-// does not average out of the observed statistic.  Arguments below -87 give 0.
+// does not average out of the observed statistic.  Arguments below -87 give 0 and
+// arguments above 0 are taken as 0 (the kernels' arguments are never positive); the
+// scaling by 2^k (-126 < k <= 0) is a multiplication by a normal power of two.
 __host__ __device__ __forceinline__ float exp_cw(float x) {
     if (!(x > -87.f)) return 0.f;
+    x = x < 0.f ? x : 0.f;
     const float k = rintf(x * 1.44269504f);
     float r = fmaf(-k, 0.693359375f, x);     // head of ln 2: exact products with |k| <= 126
     r = fmaf(-k, -2.12194440e-4f, r);        // tail of ln 2
@@ -265,7 +269,14 @@ __host__ __device__ __forceinline__ float exp_cw(float x) {
     q = fmaf(q, r, 0.5f);
     q = fmaf(q, r, 1.f);
     q = fmaf(q, r, 1.f);
-    return ldexpf(q, (int)k);
+    const uint32_t bits = (uint32_t)((int)k + 127) << 23;
+#ifdef __CUDA_ARCH__
+    return q * __uint_as_float(bits);
+#else
+    float scale;
+    memcpy(&scale, &bits, sizeof(scale));
+    return q * scale;
+#endif
 }
 
 // Knuth's TwoSum: s = fl(a + b) and the exact rounding error e, a + b = s + e.
