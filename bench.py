@@ -34,12 +34,13 @@ if ROOT not in sys.path:
 
 METRIC = "permuted stats/s & p99 test latency, tuned vs plain FP32 GPU at rel err ≤1e-5"
 UNIT = "permuted stats/s"
-KERNELS_PER_STEP = 11  # libept kernels launched by one ept_test run (split path)
+KERNELS_PER_STEP = 11  # libept kernels launched by one ept_test run (split path), before any recomputation
 BATCH_KERNELS_PER_STEP = 12  # ept_test_batch: the same and the batch's error status
+# (the recomputation of flagged statistics adds Result.refine_launches launches to a step)
 # dram read + write bytes of one k_contract_tc launch on the highdim workload, from the ncu
 # capture summarised in profiles/k_contract_tc_highdim_ed.md (to be reset to {} whenever the
 # kernel changes, until it is captured again)
-CONTRACT_TRAFFIC = {"highdim": 61.58e6, "mmd": 1044.8e6, "mmd_laplace": 1044.8e6, "mmd_median": 1044.8e6}
+CONTRACT_TRAFFIC = {"highdim": 61.16e6}
 # streaming mode: DRAM bytes per stored block of the contraction, from the n = 60,000 capture summarised in
 # profiles/k_contract_tc_stream_60k.md (scaled to a launch by its window's blocks)
 STREAM_TRAFFIC_PER_BLOCK = 9119.0e6 / 110920
@@ -454,7 +455,7 @@ def run_ours(args):
                      "mma_frac": mma_flops / t_contract / 1e12 / peak},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int((spec.nx + spec.ny) * spec.p * 4),
                 "d2h_bytes_per_step": int((spec.B + 1) * 8 + 48), "steps": args.e2e_steps},
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "gpu_launches": (KERNELS_PER_STEP + last.refine_launches) * args.steps,
         "clocks": clocks,
         "result": {"observed": last.observed, "p_value": last.p_value, "n_near_tie": last.n_near_tie,
                    "sigma": last.sigma, "n_refined": last.n_refined},
@@ -714,7 +715,7 @@ def run_batched(args):
                      "peak_kind": "%s bf16 dense burst" % peak_kind, "algorithmic_flops_per_launch": alg_flops},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(in_bytes),
                 "d2h_bytes_per_step": int(sum((sp.B + 1) * 8 + 48 for sp in specs)), "steps": args.e2e_steps},
-        "gpu_launches": BATCH_KERNELS_PER_STEP * args.steps,
+        "gpu_launches": (BATCH_KERNELS_PER_STEP + last[0].refine_launches) * args.steps,
         "clocks": clocks,
     }
     if cpu is not None:

@@ -122,6 +122,9 @@ typedef struct {
     int64_t tune_candidates; /* parameter sets the autotuner timed in this call (its first
                              call of a batch shape); 0 when the parameters came from its
                              cache or were not tuned */
+    int64_t refine_launches; /* kernel launches of the call's recomputation of flagged
+                             statistics (all tests of a batched call together; 0 when
+                             nothing was recomputed) */
 } ept_result;
 
 /* Library ABI version (EPT_ABI_VERSION of the build). */

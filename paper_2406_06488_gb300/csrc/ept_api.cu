@@ -1042,6 +1042,7 @@ ept_status collect(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &specs
         r.n_refined = (int64_t)ctr[t].n_flag;
         r.tuning = 0;
         r.tune_candidates = 0;
+        r.refine_launches = 0;
         if (P.host_in && specs[t].perm_stats && d.B > 0)
             memcpy(specs[t].perm_stats, stats + d.col0 + 1, (size_t)d.B * 8);
     }
@@ -1226,7 +1227,9 @@ ept_status refine_after(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &
     double *dpart1 = (double *)(mem + b_list1 + b_list2 + b_jobs);
     uint8_t *l2mem = mem + b_list1 + b_list2 + b_jobs + b_part1;
     cudaError_t e = cudaSuccess;
+    int64_t launches = 2;   // the counts reset and taken again
     if (!jobs.empty()) {
+        launches += 2 * (((int64_t)jobs.size() + 65534) / 65535);
         e = cudaMemcpyAsync(dlist1, list1.data(), 4 * list1.size(), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(djobs, jobs.data(), sizeof(RefineJob) * jobs.size(), cudaMemcpyHostToDevice, s);
@@ -1255,10 +1258,12 @@ ept_status refine_after(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &
             const int64_t r1 = std::min<int64_t>(d.n, r0 + rows_w);
             launch_refine_w(b, t, d.n, sigma, r0, r1, W64, s);
             launch_refine_rows(b, t, r0, r1, W64, dlist, nflag, part, spart, s);
+            launches += 2;
             e = cudaGetLastError();
         }
         if (e == cudaSuccess) {
             launch_refine_finish(b, t, dlist, nflag, part, spart, ntiles, s);
+            launches += 1;
             e = cudaGetLastError();
         }
     }
@@ -1279,7 +1284,9 @@ ept_status refine_after(ept_ctx *c, const Plan &P, const std::vector<TestSpec> &
     CK(cudaMemcpyAsync(pin + S.res_obs, b.observed, 8 * (size_t)P.n_tests, cudaMemcpyDeviceToHost, s));
     if (P.host_in) CK(cudaMemcpyAsync(pin + S.res_stats, b.stats, 8 * (size_t)P.nstats, cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    return collect(c, P, specs, out, timed, per_test);
+    const ept_status st2 = collect(c, P, specs, out, timed, per_test);
+    for (int t = 0; st2 == EPT_OK && t < P.n_tests; ++t) out[t].refine_launches = launches;
+    return st2;
 }
 
 // One run of a batch: plan, stage, enqueue (or replay a captured graph), wait, collect.

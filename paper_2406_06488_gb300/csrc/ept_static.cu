@@ -269,6 +269,7 @@ extern "C" ept_status ept_test_static(const float *X, int64_t nx, const float *Y
     out->n_refined = 0;   // no FP64 refinement here (it needs scratch beyond the array)
     out->tuning = 0;
     out->tune_candidates = 0;
+    out->refine_launches = 0;
     out->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
     return EPT_OK;
 }

@@ -51,7 +51,8 @@ class _Result(ctypes.Structure):
                 ("n_near_tie", ctypes.c_int64), ("n_fixup", ctypes.c_int64), ("ms_build", ctypes.c_double),
                 ("ms_perm", ctypes.c_double), ("ms_total", ctypes.c_double), ("ms_masks", ctypes.c_double),
                 ("ms_contract", ctypes.c_double), ("sigma", ctypes.c_double), ("n_windows", ctypes.c_int64),
-                ("n_refined", ctypes.c_int64), ("tuning", ctypes.c_int64), ("tune_candidates", ctypes.c_int64)]
+                ("n_refined", ctypes.c_int64), ("tuning", ctypes.c_int64), ("tune_candidates", ctypes.c_int64),
+                ("refine_launches", ctypes.c_int64)]
 
 
 class _PlanInfo(ctypes.Structure):
@@ -86,12 +87,14 @@ class Result:
     n_refined: int = 0
     tuning: int = 0
     tune_candidates: int = 0
+    refine_launches: int = 0
     stats: Optional[object] = field(default=None, repr=False)
 
 
 def _result(r, buf) -> "Result":
     return Result(r.observed, r.p_value, r.n_ge, r.n_near_tie, r.n_fixup, r.ms_build, r.ms_perm, r.ms_total,
-                  r.ms_masks, r.ms_contract, r.sigma, r.n_windows, r.n_refined, r.tuning, r.tune_candidates, buf)
+                  r.ms_masks, r.ms_contract, r.sigma, r.n_windows, r.n_refined, r.tuning, r.tune_candidates,
+                  r.refine_launches, buf)
 
 
 _lib = None

@@ -6,11 +6,15 @@ the form in which kernel measurements are kept next to the code.
             serialised, so the shares are what compare with a timed run);
   metrics   per kernel: the mean per launch of every captured metric and, where the
             DRAM byte counters were captured, the traffic per launch and (with the
-            duration) its rate against the measured HBM copy bandwidth.
+            duration) its rate against the measured HBM copy bandwidth;
+  phases    one tuned step of the library from a launch list: the per-launch mean of
+            each of its kernels, grouped by the phase of the hot path they belong to,
+            and each phase's share of the step's serialised kernel time.
 
 Usage:
     python -m paper_2406_06488_gb300.ncu_summary launches FILE.csv
     python -m paper_2406_06488_gb300.ncu_summary metrics FILE.csv [--peaks MEASURED_PEAKS.json]
+    python -m paper_2406_06488_gb300.ncu_summary phases FILE.csv
 
 Reads only the CSV (and the peaks file); it runs nothing on a GPU.
 """
@@ -138,19 +142,61 @@ def metrics_markdown(table):
     return "\n".join(lines).rstrip()
 
 
+# the tuned path's kernels by phase (the plain path's k_contract_simt, k_build_simt,
+# k_norms and k_pack<0>, and the bench's own kernels, are not part of a tuned step)
+PHASES = [
+    ("contraction", ["k_contract_tc", "k_contract_tc2", "k_contract_tm"]),
+    ("relabeling draws (side stream)", ["k_masks", "k_masks_lanes"]),
+    ("block build", ["k_split_rows", "k_build_tc"]),
+    ("centring / packing", ["k_blocksums", "k_rowsum_reduce", "k_center_u", "k_center_r", "k_pack<1>"]),
+    ("combination", ["k_combine_stats", "k_combine_count", "k_batch_status", "k_reset_counts"]),
+    ("recomputation of flagged statistics", ["k_refine_packed", "k_refine_packed_finish", "k_refine_w",
+                                             "k_refine_rows", "k_refine_finish"]),
+]
+
+
+def _short(kernel):
+    """A kernel name without its namespaces ('ept::<unnamed>::k_pack<1>' -> 'k_pack<1>')."""
+    name = kernel.replace("<unnamed>::", "").replace("unnamed>::", "")
+    cut = name.split("<")[0].rfind("::")
+    return name[cut + 2:] if cut >= 0 else name
+
+
+def phase_table(rows):
+    """[(phase, kernels, us, share)]: per phase the sum of its kernels' per-launch means."""
+    means = {_short(k): mean for k, n, t, mean, share in launch_table(rows)}
+    out = []
+    for phase, kernels in PHASES:
+        present = [k for k in kernels if k in means]
+        if present:
+            out.append((phase, present, sum(means[k] for k in present)))
+    total = sum(us for _, _, us in out) or 1.0
+    return [(ph, ks, us, us / total) for ph, ks, us in out]
+
+
+def phases_markdown(table):
+    lines = ["| phase | kernels | us | share of the serialised step |", "|---|---|---:|---:|"]
+    for ph, ks, us, share in table:
+        lines.append("| %s | %s | %.1f | %.1f %% |" % (ph, ", ".join(ks), us, 100.0 * share))
+    lines.append("| total | | %.1f | |" % sum(us for _, _, us, _ in table))
+    return "\n".join(lines)
+
+
 def summarise(mode, text, hbm_gbs=None):
-    """The markdown summary of ncu CSV text: mode 'launches' or 'metrics'."""
+    """The markdown summary of ncu CSV text: mode 'launches', 'metrics' or 'phases'."""
     rows = read_rows(text)
     if mode == "launches":
         return launches_markdown(launch_table(rows))
     if mode == "metrics":
         return metrics_markdown(metric_table(rows, hbm_gbs))
-    raise ValueError("mode must be 'launches' or 'metrics'")
+    if mode == "phases":
+        return phases_markdown(phase_table(rows))
+    raise ValueError("mode must be 'launches', 'metrics' or 'phases'")
 
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    ap.add_argument("mode", choices=["launches", "metrics"])
+    ap.add_argument("mode", choices=["launches", "metrics", "phases"])
     ap.add_argument("csv")
     ap.add_argument("--peaks", default=None, help="MEASURED_PEAKS.json (hbm_gbs) for the DRAM fraction")
     args = ap.parse_args(argv)

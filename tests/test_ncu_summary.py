@@ -82,3 +82,15 @@ def test_summarise_modes():
     assert "dram_frac" in ns.summarise("metrics", METRICS, hbm_gbs=6766.0)
     with pytest.raises(ValueError):
         ns.summarise("sections", LAUNCHES)
+
+
+def test_phases_group_the_tuned_step():
+    # per-launch means: contraction 310, draws 120, packing 25 (of 455 us)
+    table = ns.phase_table(ns.read_rows(LAUNCHES))
+    assert [(ph, ks) for ph, ks, _, _ in table] == [("contraction", ["k_contract_tc"]),
+                                                    ("relabeling draws (side stream)", ["k_masks"]),
+                                                    ("centring / packing", ["k_pack<1>"])]
+    assert [round(us, 6) for _, _, us, _ in table] == [310.0, 120.0, 25.0]
+    assert table[0][3] == pytest.approx(310.0 / 455.0)
+    md = ns.summarise("phases", LAUNCHES)
+    assert "| contraction | k_contract_tc | 310.0 | 68.1 % |" in md and md.splitlines()[-1] == "| total | | 455.0 | |"
