@@ -313,24 +313,25 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    inside the tensor-core kernels (a pipeline barrier or flag that does not arrive
    within it makes the kernel record an error, drain and return; the call returns
    EPT_ETIMEOUT).
-   EPT_OPT_MAX_CHUNK (default 8; 4, 8, 16 or 32): the longest contraction work unit, in
-   K-blocks of 64 pooled columns.  The tensor cores accumulate each unit in FP32, and
-   the error grows faster than the unit's length (about 2.8x per doubling).  8 keeps
-   the statistics within 1e-5 of the FP64 oracle on the paper-shaped workloads and on
-   the random parity cases of the tests; on strongly ill-conditioned inputs (a
-   wide-kernel MMD of one to three features, say, whose permuted statistics are far
-   smaller than the spread of the pooled matrix) they can be off by up to a few 1e-3
-   relative while the p-values still agree.  16 or 32 let the autotuner pick longer
-   units, about 12 % faster on large tests, with about three times the error on such
-   inputs; 4 makes every unit 4 K-blocks, about 30 % slower, with somewhat less.
+   EPT_OPT_MAX_CHUNK (default 32; 4, 8, 16 or 32): the longest contraction work unit,
+   in K-blocks of 64 pooled columns, that the autotuner may pick (untuned runs use 8).
+   The tensor cores accumulate each unit in FP32, and the error grows faster than the
+   unit's length (measured: the accumulation coefficient of the error estimate below
+   has to be 6.8, 15.4 and 51.4 for units of 8, 16 and 32 K-blocks); the estimate takes
+   8, 20 and 64, so every length keeps the returned statistics within 1e-5 of the FP64
+   oracle through the recomputation of the flagged ones, and the autotuner, which
+   times whole runs with their recomputation, picks a longer unit only where it is
+   faster all included.  With EPT_OPT_REFINE = 0 the fast values of longer units can
+   be off by up to a few 1e-3 relative on strongly ill-conditioned inputs.
    EPT_OPT_REFINE (default 1; 0 or 1): FP64 recomputation of flagged statistics
    (Section 3.1's statistics, Eq. 1 / Eq. 2, evaluated from the raw rows).  Every
    statistic of the split and plain precisions carries an a-posteriori estimate of
    its error, E_b = k_b u cT A_b + 4 u Wbar / m: u = 2^-24, cT = (n/(nx ny))^2, A_b
    the sum of the absolute values of its contraction partial sums (the magnitudes its
    FP32 accumulations carried), Wbar the mean entry of the pooled matrix, m =
-   min(nx, ny), k_b = 8 for a relabeling and 64 for the observed statistic and every
-   statistic within 1e-5 |observed| + 2 E_0 of it.  A statistic with
+   min(nx, ny), k_b = 8 for a relabeling (20 with units of 16 K-blocks, 64 with units
+   of 32) and 8 times that for the observed statistic and every statistic within
+   1e-5 |observed| + 2 E_0 of it.  A statistic with
    E_b > 1e-5 |stat_b| is recomputed: when its representation term (the second) is
    above 1/20 of the tolerance, from W built in FP64 by direct differences of the
    widened inputs (Algorithm 3) and its three block sums in FP64; otherwise by summing
@@ -343,6 +344,9 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    features whose permuted statistics are far below the FP32 resolution of the
    kernel values; ept_result.n_refined counts them.  Not applied in the streaming
    mode, by the pre-computation baseline or by ept_test_static.
+   EPT_OPT_UNIT_KB (default 0; 0, 4, 8, 16 or 32): the contraction unit length of
+   every run, in K-blocks (0: 8, or the autotuner's choice); the autotuner then tries
+   no other length.
    EPT_OPT_CONTRACTION (default 0; 0..3): the tensor-core contraction kernel.  1:
    relabelings as the MMA's shared-memory operand (N = 256 relabelings, M = 128 rows
    of C; producer warps expand the mask bits into shared memory).  2: the same on
@@ -359,7 +363,8 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    EPT_OPT_SERVE_SLOTS (default 256): serving requests in flight at once; both
    before the first ept_submit.  EPT_EINVAL for an unknown option or value.
    Environment: EPT_GRAPHS, EPT_AUTOTUNE, EPT_DRAW_MODE, EPT_DEBUG_CHECKS,
-   EPT_STREAM_BLOCKS, EPT_WAIT_LIMIT_MS, EPT_MAX_CHUNK, EPT_REFINE, EPT_SERVE_LANES and EPT_SERVE_SLOTS set the
+   EPT_STREAM_BLOCKS, EPT_WAIT_LIMIT_MS, EPT_MAX_CHUNK, EPT_REFINE, EPT_CONTRACTION, EPT_UNIT_KB,
+   EPT_SERVE_LANES and EPT_SERVE_SLOTS set the
    starting value of the option of that name in every new context (an invalid value
    makes ept_create fail with EPT_EINVAL); EPT_AUTOTUNE_CACHE names a file in which
    the autotuner keeps its choices across processes. */
@@ -376,7 +381,8 @@ enum {
     EPT_OPT_WAIT_LIMIT_MS = 10,
     EPT_OPT_MAX_CHUNK = 11,
     EPT_OPT_REFINE = 12,
-    EPT_OPT_CONTRACTION = 13
+    EPT_OPT_CONTRACTION = 13,
+    EPT_OPT_UNIT_KB = 14
 };
 ept_status ept_set_option(ept_ctx *ctx, int option, int64_t value);
 

@@ -242,6 +242,7 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
         TestDesc d;
         describe_test(d, s.nx, s.ny, s.p, s.B, s.stat, s.sigma, s.seed, tc);
         d.b0 = s.b0;
+        d.ka = refine_ka(chunk_kb);
         d.row0 = P.nrows;
         d.blk0 = P.nblk;
         d.pan0 = P.npan;
@@ -429,6 +430,7 @@ void describe_test(TestDesc &d, int64_t nx, int64_t ny, int64_t p, int64_t B, in
     d.inv_n = 1.0 / fn;
     d.inv_2n2 = 1.0 / (2.0 * fn * fn);
     d.scaled = split ? 1 : 0;
+    d.ka = refine_ka(CHUNK_KB_DEFAULT);
 }
 
 cudaError_t smem_limit_once(const void *func, int bytes, unsigned long long *done) {
@@ -558,7 +560,8 @@ struct ept_ctx {
     int draw_mode = 0;                  // relabeling draws: 0 automatic, DRAW_WARPS, DRAW_LANES
     int64_t stream_blocks = 0;          // streaming mode: 0 automatic, k > 0 windows of <= k blocks, -1 never
     unsigned long long wait_ns = 0;     // limit of the kernels' bounded waits (0: their default, 2 s)
-    int max_chunk = CHUNK_KB_DEFAULT;   // longest contraction unit the autotuner may pick (precision)
+    int max_chunk = 32;                 // longest contraction unit the autotuner may pick
+    int unit_kb = 0;                    // unit length of every run (EPT_OPT_UNIT_KB; 0: the default / autotuner)
     bool refine = true;                 // recompute flagged statistics (EPT_OPT_REFINE)
     int contraction = 0;                // tensor-core contraction kernel (EPT_OPT_CONTRACTION; 0: default)
     uint8_t *refine_buf = nullptr;      // scratch of the recomputation (grows, kept until ept_destroy)
@@ -1372,8 +1375,14 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
     if (st != EPT_OK) return st;
     CK(cudaStreamSynchronize(s));
     if ((st = collect(c, P, specs, out, true)) != EPT_OK) return st;
+    const auto r0 = std::chrono::steady_clock::now();
     if ((st = refine_after(c, P, specs, out, true, s)) != EPT_OK) return st;
-    if (device_ms) cudaEventElapsedTime(device_ms, c->ev[0], c->ev[4]);   // the whole run on the device
+    if (device_ms) {
+        // the whole run on the device, and the recomputation of flagged statistics (its
+        // wall time: it waits for its own work)
+        cudaEventElapsedTime(device_ms, c->ev[0], c->ev[4]);
+        *device_ms += std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - r0).count();
+    }
     for (int t = 0; t < P.n_tests; ++t) out[t].tuning = tn.code();
     return EPT_OK;
 }
@@ -1384,7 +1393,7 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
 // is the one chosen.
 // Contraction unit length (K-blocks) of a context's untuned runs: the default, or the
 // context's precision limit when that is shorter.
-int unit_kb(const ept_ctx *c) { return std::min(CHUNK_KB_DEFAULT, c->max_chunk); }
+int unit_kb(const ept_ctx *c) { return c->unit_kb ? c->unit_kb : std::min(CHUNK_KB_DEFAULT, c->max_chunk); }
 
 Tuning default_tuning(const ept_ctx *c) {
     Tuning tn;
@@ -1415,7 +1424,7 @@ ept_status run_tuned(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, b
         for (size_t t = 0; st == EPT_OK && t < specs.size(); ++t) out[t].tune_candidates = 0;
         return st;
     }
-    const std::vector<int64_t> key = tune_key(specs, prec, c->max_chunk);
+    const std::vector<int64_t> key = tune_key(specs, prec, 64 * c->max_chunk + c->unit_kb);
     auto it = c->tuned.find(key);
     if (it != c->tuned.end()) {
         ept_status st = run_once(c, specs, prec, on_device, it->second, use_graph, out, stream, nullptr);
@@ -1445,7 +1454,7 @@ ept_status run_tuned(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, b
         cand.push_back(t);
     }
     for (int kb : {4, 16, 32})
-        if (kb != def.chunk_kb && kb <= c->max_chunk) {
+        if (kb != def.chunk_kb && kb <= c->max_chunk && c->unit_kb == 0) {
             Tuning t = def;
             t.chunk_kb = kb;
             cand.push_back(t);
@@ -2369,7 +2378,7 @@ ept_status ept_create_ex(ept_ctx **out, int device, size_t mem_budget_bytes, con
                     {"EPT_DRAW_MODE", EPT_OPT_DRAW_MODE},     {"EPT_DEBUG_CHECKS", EPT_OPT_DEBUG_CHECKS},
                     {"EPT_STREAM_BLOCKS", EPT_OPT_STREAM_BLOCKS}, {"EPT_WAIT_LIMIT_MS", EPT_OPT_WAIT_LIMIT_MS},
                     {"EPT_MAX_CHUNK", EPT_OPT_MAX_CHUNK},     {"EPT_REFINE", EPT_OPT_REFINE},
-                    {"EPT_CONTRACTION", EPT_OPT_CONTRACTION},
+                    {"EPT_CONTRACTION", EPT_OPT_CONTRACTION}, {"EPT_UNIT_KB", EPT_OPT_UNIT_KB},
                     {"EPT_SERVE_LANES", EPT_OPT_SERVE_LANES}, {"EPT_SERVE_SLOTS", EPT_OPT_SERVE_SLOTS}};
     for (const auto &eo : env_opts) {
         const char *v = getenv(eo.env);
@@ -2689,6 +2698,11 @@ ept_status ept_set_option(ept_ctx *c, int option, int64_t value) {
         c->contraction = (int)value;
         c->plan_key.clear();   // a captured graph holds the previous contraction kernel
         drop_graph(c);
+        return EPT_OK;
+    case EPT_OPT_UNIT_KB:
+        if (value != 0 && value != 4 && value != 8 && value != 16 && value != 32)
+            return fail(EPT_EINVAL, "the unit length must be 0, 4, 8, 16 or 32");
+        c->unit_kb = (int)value;
         return EPT_OK;
     case EPT_OPT_MAX_CHUNK:
         if (value != 4 && value != 8 && value != 16 && value != 32)

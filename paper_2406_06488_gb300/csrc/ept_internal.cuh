@@ -85,22 +85,25 @@ struct Counters {
 // accumulations of column b carried), Wbar = 1'W1 / n^2 the mean entry of the
 // pooled matrix and m the contracted group's size (the FP32 representation errors
 // of the m^2 entries a relabeling sums average out; the kernel values come from
-// exp_cw, whose rounding errors carry no smooth bias).  k_b = REFINE_KA for a
-// relabeling and REFINE_KC for the observed statistic and every statistic within
-// 1e-5 |stat_0| + 2 E_0 of it: relabelings aligned with the samples sum entries of
-// one sign and similar size in the same order on the tensor cores, so their
-// accumulation errors add coherently.  Statistics with E_b > REFINE_TOL |stat_b| are
-// flagged: when the representation term exceeds REFINE_L2 of the tolerance, for
-// entries rebuilt in FP64 from the raw rows (level 2); otherwise for an exact
-// re-summation of the packed operand the contraction read (level 1), which removes
-// the accumulation part and leaves the FP32 representation of the entries.  The
-// constants were fitted to measured GPU errors (a sweep of 200 ill-conditioned
-// problems against the FP64 oracle, both precisions) so that every statistic off by
-// more than half the tolerance is flagged (with REFINE_KA = 8 that took REFINE_KR >=
-// 2.4; the largest accumulation errors of observed statistics were 40 (tensor cores)
-// and 53 (plain FP32) u cT A_0); the largest error left unflagged was 6.2e-6.
-constexpr double REFINE_KA = 8.0;
-constexpr double REFINE_KC = 64.0;
+// exp_cw, whose rounding errors carry no smooth bias).  k_b = refine_ka(L) for a
+// relabeling (L the run's unit length in K-blocks: the accumulation error of a unit
+// grows faster than its length) and REFINE_KC_RATIO times that for the observed
+// statistic and every statistic within 1e-5 |stat_0| + 2 E_0 of it: relabelings
+// aligned with the samples sum entries of one sign and similar size in the same
+// order on the tensor cores, so their accumulation errors add coherently.
+// Statistics with E_b > REFINE_TOL |stat_b| are flagged: when the representation term
+// exceeds REFINE_L2 of the tolerance, for entries rebuilt in FP64 from the raw rows
+// (level 2); otherwise for an exact re-summation of the packed operand the
+// contraction read (level 1), which removes the accumulation part and leaves the
+// FP32 representation of the entries.  The constants were fitted to measured GPU
+// errors (a sweep of 200 ill-conditioned problems against the FP64 oracle, both
+// precisions, units of 8, 16 and 32 K-blocks) so that every statistic off by more
+// than half the tolerance is flagged: the relabelings needed k = 6.8, 15.4 and 51.4
+// (tensor cores; 2.2, 2.5 and 6.8 on the plain path) with REFINE_KR = 4; the largest
+// accumulation errors of observed statistics were 40 (tensor cores) and 53 (plain
+// FP32) u cT A_0 with units of 8.
+__host__ __device__ constexpr double refine_ka(int unit_kb) { return unit_kb <= 8 ? 8.0 : unit_kb <= 16 ? 20.0 : 64.0; }
+constexpr double REFINE_KC_RATIO = 8.0;
 constexpr double REFINE_KR = 4.0;
 constexpr double REFINE_TOL = 1e-5;
 constexpr double REFINE_L2 = 0.05;
@@ -164,6 +167,7 @@ struct TestDesc {
     int32_t pad2_;
     double cT, inv_o2, sign, kappa, inv_n, inv_2n2;
     double sigma64;                  // the given bandwidth in FP64 (FP64 refinement; 0 for ED and median)
+    double ka;                       // accumulation coefficient of the error estimate (refine_ka of the unit length)
 };
 
 // Prefix sums over the tests (n_tests + 1 entries each) of the work dimensions.

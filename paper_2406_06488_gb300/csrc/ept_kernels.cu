@@ -965,8 +965,8 @@ __global__ void __launch_bounds__(256) k_combine_stats(const Batch bt) {
         const double inv_c = d.scaled ? 1.0 / (double)packed_scale(bt.ctr[t]) : 1.0;
         if (c < d.ncols) {
             bt.stats[d.col0 + c] = d.sign * (d.cT * (q * inv_c) + bSt * d.inv_o2);
-            // accumulation part of the error estimate (ept_internal.cuh, REFINE_KA)
-            if (bt.errest) bt.errest[d.col0 + c] = REFINE_KA * REFINE_U * d.cT * (a * inv_c);
+            // accumulation part of the error estimate (ept_internal.cuh, refine_ka)
+            if (bt.errest) bt.errest[d.col0 + c] = d.ka * REFINE_U * d.cT * (a * inv_c);
         }
     }
 }
@@ -1015,10 +1015,10 @@ __global__ void __launch_bounds__(256) k_combine_count(const Batch bt, int flag)
         if (c < d.ncols) {
             const double v = bt.stats[d.col0 + c];
             const double rep = REFINE_KR * REFINE_U * fabs(bW) / (double)d.m;
-            // errest holds REFINE_KA u cT A; the observed and aligned statistics take REFINE_KC
-            const double e0 = (REFINE_KC / REFINE_KA) * bt.errest[d.col0] + rep;
+            // errest holds refine_ka u cT A; the observed and aligned statistics take REFINE_KC_RATIO times it
+            const double e0 = REFINE_KC_RATIO * bt.errest[d.col0] + rep;
             const bool aligned = c == 0 || fabs(v - obs) <= REFINE_TOL * fabs(obs) + 2.0 * e0;
-            const double acc = aligned ? (REFINE_KC / REFINE_KA) * bt.errest[d.col0 + c] : bt.errest[d.col0 + c];
+            const double acc = aligned ? REFINE_KC_RATIO * bt.errest[d.col0 + c] : bt.errest[d.col0 + c];
             const double tol = REFINE_TOL * fabs(v);
             // flagged when the estimate exceeds the tolerance; 2 (rebuild the entries in FP64)
             // when the representation term exceeds REFINE_L2 of it, else 1 (re-sum the

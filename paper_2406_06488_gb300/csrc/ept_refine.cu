@@ -1,5 +1,5 @@
 // ept_refine.cu -- FP64 recomputation of the statistics whose error estimate
-// exceeds the tolerance (the criterion is in ept_internal.cuh, REFINE_KA/KR/TOL;
+// exceeds the tolerance (the criterion is in ept_internal.cuh, refine_ka, REFINE_KR, REFINE_TOL;
 // k_combine_count sets the flags).
 //
 // What it computes: for a flagged relabeling column with indicator s of the

@@ -209,7 +209,7 @@ def plan_check(shapes, unit_kb: int = 8, num_sms: int = 152, stream_blocks: int 
 
 OPTION = {"graphs": 1, "autotune": 2, "serve_lanes": 3, "serve_slots": 4, "draw_mode": 5,
           "fault_inject_alloc": 6, "fault_inject_stall": 7, "debug_checks": 8, "stream_blocks": 9,
-          "wait_limit_ms": 10, "max_chunk": 11, "refine": 12, "contraction": 13}
+          "wait_limit_ms": 10, "max_chunk": 11, "refine": 12, "contraction": 13, "unit_kb": 14}
 
 
 class Context:

@@ -252,19 +252,26 @@ def test_environment_sets_option_defaults(monkeypatch):
     assert np.max(np.abs(np.asarray(r.stats) - ref["stats"]) / np.abs(ref["stats"])) <= REL_TOL
 
 
-def test_max_chunk_option(ctx):
+def test_unit_length_options(ctx):
+    # every unit length, forced, returns statistics within the tolerance of the oracle
+    # (the error estimate's coefficient follows the length; flagged statistics are
+    # recomputed); invalid lengths are refused
     from paper_2406_06488_gb300 import ept
     with pytest.raises(ept.EptError):
         ctx.set_option("max_chunk", 12)
+    with pytest.raises(ept.EptError):
+        ctx.set_option("unit_kb", 24)
     X, Y = workloads.gaussian_pair(workloads.TwoSampleSpec(nx=900, ny=1100, p=40, y_mean=0.05, data_seed=7))
     ref = oracle.permutation_test(X, Y, B=600, seed=3, stat="ed")
     try:
-        for mc in (32, 16, 8, 4):
-            ctx.set_option("max_chunk", mc)
+        for L in (32, 16, 8, 4):
+            ctx.set_option("unit_kb", L)
             r = ctx.test(X, Y, B=600, seed=3)
+            assert r.tuning // 100 == L
             assert _close(r.stats, ref["stats"])
     finally:
-        ctx.set_option("max_chunk", 8)
+        ctx.set_option("unit_kb", 0)
+        ctx.set_option("max_chunk", 32)
 
 
 def test_full_batched_configuration_sampled(ctx):

@@ -1,7 +1,8 @@
 """Seeded sweep of 200 random two-sample problems, drawn towards ill-conditioned ones:
 kernel bandwidths from 0.3 to 12 times sqrt(p) (log-uniform), down to one feature,
 shifted and rescaled second samples.  Against the FP64 oracle (Algorithm 1 on the
-three blocks), on the tensor-core and the plain FP32 paths:
+three blocks), on the tensor-core and the plain FP32 paths, with contraction units
+of 8, 16 and 32 K-blocks:
 
 * every statistic (observed and permuted) within 1e-5 relative, and the count
   #{stat* >= observed} equal except through near-ties (Section 3.1 p-value);
@@ -9,12 +10,13 @@ three blocks), on the tensor-core and the plain FP32 paths:
   error criterion flags: with E_b = k_b u cT A_b + 4 u Wbar / m (u = 2^-24, cT the
   statistic's factor on the quadratic form s'Cs of the centred pooled matrix, A_b
   the sum over the contraction's work units of |partial sum|, Wbar the mean entry
-  of the pooled matrix, m the smaller group's size, k_b = 8, or 64 for the observed
-  statistic and the statistics within 1e-5 |stat_0| + 2 E_0 of it), statistic b is recomputed iff
+  of the pooled matrix, m the smaller group's size, k_b = 8, 20 or 64 for units of
+  8, 16 or 32 K-blocks, eight times that for the observed statistic and the
+  statistics within 1e-5 |stat_0| + 2 E_0 of it), statistic b is recomputed iff
   E_b > 1e-5 |stat_b| of the fast value.  A_b is recomputed here in FP64 from the
   oracle's pooled matrix with the contraction's unit decomposition (row halves of
   128 rows of 256-row panels; each panel's K-blocks of 64 columns from its diagonal
-  on, split into chunks of equal length of at most 8; upper storage), so decisions
+  on, split into chunks of equal length of at most the unit length; upper storage), so decisions
   within 2 % of the threshold are not compared;
 * the criterion is sound on this sweep: every fast statistic off by more than 1e-5
   was recomputed.
@@ -22,6 +24,8 @@ three blocks), on the tensor-core and the plain FP32 paths:
 The fast values come from a context with refinement off (EPT_OPT_REFINE = 0; the
 computation is deterministic, so a value that differs between the two contexts was
 recomputed, and the count of recomputed statistics is the library's own)."""
+import functools
+
 import numpy as np
 import pytest
 
@@ -33,7 +37,9 @@ pytestmark = pytest.mark.gpu
 N_CASES = 200
 REL_TOL = 1e-5
 U = 2.0 ** -24
-KA, KC, KR = 8.0, 64.0, 4.0
+KA = {8: 8.0, 16: 20.0, 32: 64.0}   # accumulation coefficient by unit length (K-blocks)
+KC_RATIO, KR = 8.0, 4.0
+UNITS = (8, 16, 32)
 
 
 @pytest.fixture(scope="module")
@@ -41,12 +47,18 @@ def ctxs():
     import __graft_entry__
     __graft_entry__.build()
     from paper_2406_06488_gb300 import ept
-    on = ept.Context(0)
-    off = ept.Context(0)
-    off.set_option("refine", 0)
-    yield on, off
-    on.close()
-    off.close()
+    out = {}
+    for L in UNITS:
+        on = ept.Context(0)
+        off = ept.Context(0)
+        off.set_option("refine", 0)
+        for c in (on, off):
+            c.set_option("unit_kb", L)
+        out[L] = (on, off)
+    yield out
+    for on, off in out.values():
+        on.close()
+        off.close()
 
 
 def _case(k):
@@ -63,10 +75,16 @@ def _case(k):
     return X, Y, B, int(r.integers(0, 2**40)), stat, sigma
 
 
-def _error_terms(X, Y, B, seed, stat, sigma):
+@functools.lru_cache(maxsize=None)
+def _oracle(k):
+    X, Y, B, seed, stat, sigma = _case(k)
+    return oracle.permutation_test(X, Y, B=B, seed=seed, stat=stat, sigma=sigma, method="blocks")
+
+
+def _error_terms(X, Y, B, seed, stat, sigma, L):
     """The parts of the criterion's E_b for every column (observed first), from the
-    oracle's pooled matrix and the contraction's unit decomposition: u cT A_b and the
-    representation term."""
+    oracle's pooled matrix and the contraction's unit decomposition (units of at most
+    L K-blocks): u cT A_b and the representation term."""
     nx, ny = len(X), len(Y)
     n = nx + ny
     Z = np.vstack([X, Y])
@@ -86,10 +104,10 @@ def _error_terms(X, Y, B, seed, stat, sigma):
     A = np.zeros(B + 1)
     nkb = (n + 63) // 64
     for I in range((n + 255) // 256):
-        L = nkb - 4 * I
-        nq = -(-L // 8)
-        for q in range(nq):   # chunks of equal length (at most 8 K-blocks)
-            c0, c1 = 64 * (4 * I + q * L // nq), min(64 * (4 * I + (q + 1) * L // nq), n)
+        Lp = nkb - 4 * I
+        nq = -(-Lp // L)
+        for q in range(nq):   # chunks of equal length (at most L K-blocks)
+            c0, c1 = 64 * (4 * I + q * Lp // nq), min(64 * (4 * I + (q + 1) * Lp // nq), n)
             Ub = Cup[256 * I:256 * I + 256, c0:c1] @ sel[c0:c1]
             for h in range(2):
                 r0, r1 = 256 * I + 128 * h, min(256 * I + 128 * h + 128, n)
@@ -100,20 +118,22 @@ def _error_terms(X, Y, B, seed, stat, sigma):
     return U * cT * A, KR * U * wbar / m
 
 
-def _estimates(terms, fast):
+def _estimates(terms, fast, L):
     uA, rep = terms
-    e0 = KC * uA[0] + rep
+    ka = KA[L]
+    e0 = KC_RATIO * ka * uA[0] + rep
     aligned = np.abs(fast - fast[0]) <= REL_TOL * abs(fast[0]) + 2 * e0
     aligned[0] = True
-    return np.where(aligned, KC, KA) * uA + rep
+    return np.where(aligned, KC_RATIO * ka, ka) * uA + rep
 
 
 @pytest.mark.parametrize("block", range(4))
-def test_statistics_and_p_values_equal_the_oracle(ctxs, block):
-    on, off = ctxs
+@pytest.mark.parametrize("L", UNITS)
+def test_statistics_and_p_values_equal_the_oracle(ctxs, L, block):
+    on, off = ctxs[L]
     for k in range(block * N_CASES // 4, (block + 1) * N_CASES // 4):
         X, Y, B, seed, stat, sigma = _case(k)
-        ref = oracle.permutation_test(X, Y, B=B, seed=seed, stat=stat, sigma=sigma, method="blocks")
+        ref = _oracle(k)
         want = np.concatenate([[ref["observed"]], ref["stats"]])
         near = int(np.count_nonzero(np.abs(ref["stats"] - ref["observed"]) <= 1e-5 * abs(ref["observed"])))
         terms = None
@@ -123,7 +143,7 @@ def test_statistics_and_p_values_equal_the_oracle(ctxs, block):
             got = np.concatenate([[r.observed], r.stats])
             fast = np.concatenate([[f.observed], f.stats])
             rel = np.abs(got - want) / np.abs(want)
-            assert rel.max() <= REL_TOL, (k, prec, float(rel.max()), int(rel.argmax()))
+            assert rel.max() <= REL_TOL, (L, k, prec, float(rel.max()), int(rel.argmax()))
             assert abs(r.n_ge - ref["n_ge"]) <= near, (k, prec, r.n_ge, ref["n_ge"], near)
             assert r.p_value == (1.0 + r.n_ge) / (1.0 + B)
             # the recomputed statistics: a value that changed was recomputed (a recomputed
@@ -135,8 +155,8 @@ def test_statistics_and_p_values_equal_the_oracle(ctxs, block):
             assert not (fast_bad & ~changed).any(), (k, prec, np.flatnonzero(fast_bad & ~changed))
             # and the ones the criterion flags (decisions within 2 % of the threshold aside)
             if terms is None:
-                terms = _error_terms(X, Y, B, seed, stat, sigma)
-            ratio = _estimates(terms, fast) / (REL_TOL * np.abs(fast))
+                terms = _error_terms(X, Y, B, seed, stat, sigma, L)
+            ratio = _estimates(terms, fast, L) / (REL_TOL * np.abs(fast))
             clear = np.abs(ratio - 1.0) > 0.02
             flag = ratio > 1.0
             assert not (changed & clear & ~flag).any(), (k, prec, "recomputed but not flagged")
