@@ -482,7 +482,9 @@ def _p99(xs):
 def _tuning(res):
     """The autotuner's choice for a run (ept_result.tuning) and the candidates it timed."""
     code = int(res.tuning)
-    return {"unit_kblocks": code // 100, "draw_kernel": ["auto", "warp per column", "thread per column"][code // 10 % 10],
+    return {"contraction": ["default", "relabelings in shared memory (N = 256)", "pairs of SMs (M = 256)",
+                            "relabelings in tensor memory (N = 128)"][code // 10000],
+            "unit_kblocks": code // 100 % 100, "draw_kernel": ["auto", "warp per column", "thread per column"][code // 10 % 10],
             "unit_order": ["auto", "by length", "by first K-block"][code % 10],
             "candidates_timed": int(res.tune_candidates)}
 

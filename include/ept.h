@@ -115,10 +115,11 @@ typedef struct {
                              error estimate exceeded 1e-5 of their value and that were
                              recomputed in FP64 from the raw rows (EPT_OPT_REFINE); with
                              EPT_OPT_REFINE = 0, the number that would have been */
-    int64_t tuning;       /* parameters of the tensor-core run: 100 x unit length in K-blocks
-                             + 10 x relabeling-draw kernel (0 automatic, 1 a warp per
-                             column, 2 a thread per column) + unit order (0 automatic,
-                             1 by length, 2 by first K-block); 0 for other paths */
+    int64_t tuning;       /* parameters of the tensor-core run: 10000 x contraction kernel
+                             (0 the context's, 1..3 as EPT_OPT_CONTRACTION) + 100 x unit
+                             length in K-blocks + 10 x relabeling-draw kernel (0 automatic,
+                             1 a warp per column, 2 a thread per column) + unit order (0
+                             automatic, 1 by length, 2 by first K-block); 0 for other paths */
     int64_t tune_candidates; /* parameter sets the autotuner timed in this call (its first
                              call of a batch shape); 0 when the parameters came from its
                              cache or were not tuned */
@@ -273,10 +274,12 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    at least 2.5e10) it times whole device runs of the batch with each candidate
    parameter set -- the defaults, the other relabeling-draw kernel, the other order
    of the contraction's units (by length, or by first K-block then length), units of
-   4 K-blocks, and longer units where EPT_OPT_MAX_CHUNK allows them -- keeps the
-   fastest for the shape (ept_result.tuning, .tune_candidates) and uses it from then
-   on; every candidate computes the same statistics except for the accumulation
-   order that the unit length sets.
+   4 K-blocks, longer units where EPT_OPT_MAX_CHUNK allows them, and (unless
+   EPT_OPT_CONTRACTION fixes it) the other two contraction kernels, i.e. the MMA
+   shapes M = 256 across a pair of SMs and N = 128 -- each with its recomputation of
+   flagged statistics, keeps the fastest for the shape (ept_result.tuning,
+   .tune_candidates) and uses it from then on; every candidate computes the same
+   statistics except for the accumulation order.
    EPT_OPT_DRAW_MODE (default 0): relabeling-draw kernel, 0 = automatic (a thread
    per column when the batch has at least 1024 columns per SM, else a warp per
    column), 1 = a warp per column, 2 = a thread per column; the draws are

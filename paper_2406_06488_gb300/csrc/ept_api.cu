@@ -78,7 +78,8 @@ struct TestSpec {
 // error criterion's calibration, at most 8 K-blocks unless EPT_OPT_MAX_CHUNK allows more).
 struct Tuning {
     int chunk_kb = CHUNK_KB_DEFAULT, draw_mode = 0, order = 0;
-    int64_t code() const { return (int64_t)chunk_kb * 100 + draw_mode * 10 + order; }
+    int kernel = 0;   // tensor-core contraction kernel (1..3; 0: the context's choice)
+    int64_t code() const { return (int64_t)kernel * 10000 + (int64_t)chunk_kb * 100 + draw_mode * 10 + order; }
 };
 
 ept_status validate(int64_t nx, int64_t ny, int64_t p, int stat, double sigma, int prec, bool single = false) {
@@ -112,6 +113,7 @@ struct Plan {
     std::vector<int64_t> sched, sched_off;   // contraction schedule: units of CTA c = sched[sched_off[c] ..)
     bool user_masks = false;                 // some test brings its own relabelings
     int draw_mode = 0;                       // relabeling-draw kernel of the run (0: the context's choice)
+    int contraction = 0;                     // tensor-core contraction kernel of the run (0: the context's choice)
     bool any_median = false;                 // some test takes its bandwidth from the median heuristic
     bool debug = false;                      // guard bands around the scratch regions
     GuardList guards{};
@@ -950,7 +952,7 @@ ept_status enqueue_device(ept_ctx *c, const Plan &P, cudaStream_t s, bool timed,
         char emsg[160];
         if (!encode_block_tmaps(&th, &tl, b.Chi, b.Clo, P.nblk, b.c_stride, emsg, sizeof(emsg)))
             return fail(EPT_ECUDA, "%s", emsg);
-        switch (contraction_kernel(c)) {
+        switch (P.contraction ? P.contraction : contraction_kernel(c)) {
         case 2: CK(launch_contract_tc2(b, &th, &tl, c->num_sms, s)); break;
         case 3: CK(launch_contract_tm(b, &th, &tl, c->num_sms, s)); break;
         default: CK(launch_contract_tc(b, &th, &tl, c->num_sms, s)); break;
@@ -1086,7 +1088,7 @@ void save_tune_file(ept_ctx *c) {
     FILE *f = fopen(c->tune_file.c_str(), "w");
     if (!f) return;
     for (auto &kv : c->tuned) {
-        fprintf(f, "%d %d %d", kv.second.chunk_kb, kv.second.draw_mode, kv.second.order);
+        fprintf(f, "%d %d %d %d", kv.second.chunk_kb, kv.second.draw_mode, kv.second.order, kv.second.kernel);
         for (int64_t v : kv.first) fprintf(f, " %lld", (long long)v);
         fprintf(f, "\n");
     }
@@ -1100,14 +1102,14 @@ void load_tune_file(ept_ctx *c) {
     char line[1 << 16];
     while (fgets(line, sizeof(line), f)) {
         char *p = line, *end = nullptr;
-        long head[3];
+        long head[4];
         int k = 0;
-        for (; k < 3; ++k) {
+        for (; k < 4; ++k) {
             head[k] = strtol(p, &end, 10);
             if (end == p) break;
             p = end;
         }
-        if (k < 3) continue;
+        if (k < 4) continue;
         std::vector<int64_t> key;
         for (;;) {
             const long long v = strtoll(p, &end, 10);
@@ -1119,8 +1121,10 @@ void load_tune_file(ept_ctx *c) {
         tn.chunk_kb = (int)head[0];
         tn.draw_mode = (int)head[1];
         tn.order = (int)head[2];
+        tn.kernel = (int)head[3];
         const bool ok = (tn.chunk_kb == 4 || tn.chunk_kb == 8 || tn.chunk_kb == 16 || tn.chunk_kb == 32) &&
-                        tn.draw_mode >= 0 && tn.draw_mode <= 2 && tn.order >= 0 && tn.order <= 2;
+                        tn.draw_mode >= 0 && tn.draw_mode <= 2 && tn.order >= 0 && tn.order <= 2 &&
+                        tn.kernel >= 0 && tn.kernel <= 3;
         if (ok) c->tuned[key] = tn;
     }
     fclose(f);
@@ -1308,6 +1312,7 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
     if (c->plan_key != pkey) {
         plan_batch(*c->plan, specs, prec, !on_device, chunk_kb, c->num_sms, c->debug, true, tn.order);
         c->plan->draw_mode = tn.draw_mode;
+        c->plan->contraction = tn.kernel;
         c->plan_key = pkey;
         c->tables_staged = false;
         if (c->debug && (st0 = check_plan(*c->plan)) != EPT_OK) {
@@ -1457,6 +1462,14 @@ ept_status run_tuned(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, b
         if (kb != def.chunk_kb && kb <= c->max_chunk && c->unit_kb == 0) {
             Tuning t = def;
             t.chunk_kb = kb;
+            cand.push_back(t);
+        }
+    // the MMA shape: pairs of SMs (M = 256 across a cluster) and relabelings as the
+    // tensor-memory operand (N = 128), unless the context fixes the kernel
+    if (c->contraction == 0)
+        for (int k : {2, 3}) {
+            Tuning t = def;
+            t.kernel = k;
             cand.push_back(t);
         }
     Tuning best = def;

@@ -267,7 +267,7 @@ def test_unit_length_options(ctx):
         for L in (32, 16, 8, 4):
             ctx.set_option("unit_kb", L)
             r = ctx.test(X, Y, B=600, seed=3)
-            assert r.tuning // 100 == L
+            assert r.tuning // 100 % 100 == L
             assert _close(r.stats, ref["stats"])
     finally:
         ctx.set_option("unit_kb", 0)
@@ -306,7 +306,7 @@ def test_full_batched_configuration_sampled(ctx):
 
 def test_autotuner_times_candidates_and_round_trips(tmp_path, monkeypatch):
     """The first call of a batch shape times at least three parameter sets (unit
-    length, relabeling-draw kernel, unit order), keeps the fastest, and every result
+    length, relabeling-draw kernel, unit order, contraction kernel), keeps the fastest, and every result
     equals the FP64 oracle's (Algorithm 1; Section 3.1 p-value); later calls and a new
     context reading the cache file take the same parameters without timing."""
     import __graft_entry__
@@ -339,8 +339,8 @@ def test_autotuner_times_candidates_and_round_trips(tmp_path, monkeypatch):
         for a, b in zip(first, again):
             assert a.observed == b.observed and np.array_equal(np.asarray(a.stats), np.asarray(b.stats))
     lines = cache.read_text().split("\n")
-    head = [int(v) for v in lines[0].split()[:3]]
-    assert head[0] * 100 + head[1] * 10 + head[2] == chosen
+    head = [int(v) for v in lines[0].split()[:4]]
+    assert head[3] * 10000 + head[0] * 100 + head[1] * 10 + head[2] == chosen
     with ept.Context(0) as c2:
         res = c2.test_batch(tests)
         assert all(r.tune_candidates == 0 and r.tuning == chosen for r in res)
