@@ -111,6 +111,8 @@ struct Plan {
     std::vector<Tile> tiles;
     std::vector<Chunk> chunks;
     std::vector<int64_t> sched, sched_off;   // contraction schedule: units of CTA c = sched[sched_off[c] ..)
+    std::vector<UnitRec> urec;               // the scheduled units' records, in schedule order
+    uint64_t serial = 0;                     // distinct for every plan_batch (the records are uploaded once per plan)
     bool user_masks = false;                 // some test brings its own relabelings
     int draw_mode = 0;                       // relabeling-draw kernel of the run (0: the context's choice)
     int contraction = 0;                     // tensor-core contraction kernel of the run (0: the context's choice)
@@ -125,7 +127,7 @@ struct Plan {
     size_t in_bytes = 0;              // host inputs copied into the arena
     // byte offsets in the arena; the first tab_bytes are the uploaded tables
     size_t off_desc, off_pre_rows, off_pre_panels, off_pre_cols, off_pre_units, off_pre_simt, off_blk, off_tiles,
-        off_chunks, off_sched, off_sched_off, tab_bytes;
+        off_chunks, off_sched, off_sched_off, off_urec, tab_bytes;
     size_t off_in, off_norms, off_iscale, off_u, off_Zh, off_Zl, off_D, off_Chi, off_rowpart, off_colpart,
         off_r, off_Spart, off_dcorr, off_Upart, off_Stpart, off_maskT, off_partial, off_stats, off_observed, off_ctr,
         total;
@@ -176,6 +178,7 @@ void set_test_params(TestDesc &d, const TestSpec &s) {
 void plan_schedule(Plan &P, int num_sms, int unit_order = 0) {
     P.sched.clear();
     P.sched_off.clear();
+    P.urec.clear();
     P.tc_grid = 0;
     if (P.nunits <= 0) return;
     const int64_t G = std::min<int64_t>(std::max(num_sms, 1), P.nunits);
@@ -226,11 +229,22 @@ void plan_schedule(Plan &P, int num_sms, int unit_order = 0) {
     std::vector<int64_t> fill(P.sched_off.begin(), P.sched_off.end() - 1);
     P.sched.resize((size_t)P.nunits);
     for (int64_t k = 0; k < P.nunits; ++k) P.sched[(size_t)fill[(size_t)cta_of(k)]++] = order[(size_t)k];
+    // the records of the scheduled units, in schedule order
+    P.urec.resize((size_t)P.nunits);
+    for (int64_t k = 0; k < P.nunits; ++k) {
+        const int64_t u = P.sched[(size_t)k];
+        const int t = (int)(std::upper_bound(P.pre_units.begin(), P.pre_units.end(), u) - P.pre_units.begin()) - 1;
+        const TestDesc &d = P.desc[t];
+        const int64_t lu = u - P.pre_units[t];
+        P.urec[(size_t)k] = unit_record(d, lu, P.chunks[(size_t)(d.chunk0 + (lu >> 1) / d.MT)]);
+    }
 }
 
 void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host_in, int chunk_kb,
                 int num_sms = 160, bool debug = false, bool schedule = true, int order = 0) {
     P = Plan();
+    static std::atomic<uint64_t> plans{0};
+    P.serial = ++plans;
     P.debug = debug;
     P.n_tests = (int)specs.size();
     P.prec = prec;
@@ -317,6 +331,8 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
     P.tab_bytes = o;
     o = align_up(o, 1024);
     in_data = true;
+    // the unit records: uploaded with the first run of the plan, not with every run
+    P.off_urec = take(sizeof(UnitRec) * P.urec.size());
     if (P.debug) {   // a band right after the tables as well
         P.guards.off[P.guards.n++] = o;
         o += GUARD_BYTES;
@@ -582,6 +598,8 @@ struct ept_ctx {
     Plan *plan = nullptr;
     std::vector<int64_t> plan_key;
     bool tables_staged = false;
+    uint64_t urec_serial = 0;           // plan whose unit records the arena holds (0: none)
+    uint8_t *urec_arena = nullptr;      // the arena they were uploaded to
     // host-to-device copies of this run's inputs: from the caller's buffers when they
     // are page-locked, else from the pinned staging area
     struct InputCopy {
@@ -681,6 +699,7 @@ ept_status ensure_arena(ept_ctx *c, size_t bytes, cudaStream_t s, bool exact = f
     if (st != EPT_OK) return st;
     c->arena = (uint8_t *)p;
     c->arena_cap = cap;
+    c->urec_serial = 0;   // a new arena holds no unit records
     return EPT_OK;
 }
 
@@ -827,6 +846,7 @@ Batch device_view(ept_ctx *c, const Plan &P) {
     b.chunks = (const Chunk *)(A + P.off_chunks);
     b.sched = P.sched.empty() ? nullptr : (const int64_t *)(A + P.off_sched);
     b.sched_off = P.sched.empty() ? nullptr : (const int64_t *)(A + P.off_sched_off);
+    b.urec = P.urec.empty() ? nullptr : (const UnitRec *)(A + P.off_urec);
     b.tc_grid = P.tc_grid;
     b.nblk_total = P.nblk;
     b.ntiles = (int64_t)P.tiles.size();
@@ -896,6 +916,16 @@ ept_status enqueue_inputs(ept_ctx *c, cudaStream_t after) {
 ept_status enqueue_uploads(ept_ctx *c, const Plan &P, cudaStream_t s) {
     const Staging S = staging_layout(P);
     CK(cudaMemcpyAsync(c->arena, c->pinned + S.tables, P.tab_bytes, cudaMemcpyHostToDevice, s));
+    // the unit records stay in the arena while the same plan runs on it; a run of any
+    // other plan may overwrite them
+    if (P.urec.empty()) {
+        c->urec_serial = 0;
+    } else if (c->urec_serial != P.serial || c->urec_arena != c->arena) {
+        CK(cudaMemcpyAsync(c->arena + P.off_urec, P.urec.data(), sizeof(UnitRec) * P.urec.size(),
+                           cudaMemcpyHostToDevice, s));
+        c->urec_serial = P.serial;
+        c->urec_arena = c->arena;
+    }
     return enqueue_inputs(c, s);
 }
 

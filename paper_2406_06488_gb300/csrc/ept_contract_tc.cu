@@ -81,38 +81,8 @@ struct Bars {
 };
 static_assert(sizeof(Bars) <= 512, "barriers overlap the nibble table");
 
-// the test fields, chunk, relabeling tile and row half of global work unit u, read
-// once into registers (the asm statements' memory clobbers would otherwise force
-// reloads).  Units of a test are ordered (q, m, h).
-struct Unit {
-    Chunk ch;
-    int64_t q, m, h, Bp, mask0, part0, blk0, NKB;
-    int ncols;   // relabeling columns of the tile that exist, rounded up to 16 (the MMA's N)
-};
-
-__device__ __forceinline__ Unit decode_unit(const Batch &bt, int64_t u) {
-    const int t = find_test(bt.pre.units, bt.n_tests, u);
-    const TestDesc *d = &bt.desc[t];
-    Unit x;
-    const int64_t lu = u - bt.pre.units[t];
-    const int64_t MT = d->MT;
-    x.h = lu & 1;
-    x.q = (lu >> 1) / MT;
-    x.m = (lu >> 1) % MT;
-    x.Bp = d->Bp;
-    x.mask0 = d->mask0;
-    x.part0 = d->part0;
-    x.blk0 = d->blk0;
-    x.NKB = d->NKB;
-    x.ch = bt.chunks[d->chunk0 + x.q];
-    // the first two K-blocks of a panel's diagonal square lie below the diagonal for
-    // the second row half: all zero in C, skipped
-    if (x.h == 1 && x.ch.kb0 == KB_PER_PANEL * x.ch.I && x.ch.kb1 - x.ch.kb0 > 2) x.ch.kb0 += 2;
-    // the last relabeling tile of a test is partial: the MMA's N covers its columns only
-    const int64_t left = d->ncols - x.m * TC_N;
-    x.ncols = left >= TC_N ? TC_N : (int)((left + 15) / 16 * 16);
-    return x;
-}
+// MMA N for a unit: the tile's existing relabeling columns, rounded up to 16
+__device__ __forceinline__ int mma_n(const UnitRec &x) { return x.left >= TC_N ? TC_N : (x.left + 15) / 16 * 16; }
 
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_contract_tc(const __grid_constant__ CUtensorMap tmap_hi, const __grid_constant__ CUtensorMap tmap_lo,
@@ -126,12 +96,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     float *red = reinterpret_cast<float *>(smem + STAGES * STAGE_BYTES + 1024);
     volatile int *abort_flag = &bars->abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // this CTA's units: its slice of the schedule, or every gridDim.x-th unit
+    // this CTA's units: its slice of the schedule, or every gridDim.x-th unit; every
+    // role reads the record of its next unit while it works on the current one
     const int64_t k_first = bt.sched ? bt.sched_off[blockIdx.x] : (int64_t)blockIdx.x;
     const int64_t k_end = bt.sched ? bt.sched_off[blockIdx.x + 1] : nunits;
     const int64_t k_step = bt.sched ? 1 : (int64_t)gridDim.x;
-    const int64_t *sched = bt.sched;
-    auto unit_at = [sched](int64_t k) { return sched ? sched[k] : k; };
+    auto record = [&bt, k_end](int64_t k) { return k < k_end ? unit_at_position(bt, k) : UnitRec{}; };
 
     // nibble -> four FP16 values (1.0 where the bit is set), for the relabeling producers
     uint2 *lut = reinterpret_cast<uint2 *>(smem + STAGES * STAGE_BYTES + 512);
@@ -174,19 +144,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             int armed[STAGES];   // parity of the last phase armed on each stage, -1 = none
             for (int s2 = 0; s2 < STAGES; ++s2) armed[s2] = -1;
             bool ok = true;
+            UnitRec nx = record(k_first);
             for (int64_t k = k_first; k < k_end && ok; k += k_step) {
-                const int64_t u = unit_at(k);
-                const Unit x = decode_unit(bt, u);
-                const Chunk ch = x.ch;
-                const int row = (int)x.h * TC_M;
-                for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
+                const UnitRec x = nx;
+                nx = record(k + k_step);
+                const int row = x.h * TC_M;
+                for (int kb = x.kb0; kb < x.kb1; ++kb) {
                     if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_TMA, wait_ns)) {
                         ok = false;
                         break;
                     }
                     const uint32_t afull = su32(&bars->a_full[stage]);
                     mbar_arrive_tx(afull, 2 * A_BYTES);
-                    const int blk = (int)(x.blk0 + blk_index(ch.I, kb, x.NKB));
+                    const int blk = (int)(x.blk0 + blk_index(x.I, kb, x.NKB));
                     uint8_t *st = smem + stage * STAGE_BYTES;
                     tma_load_3d(su32(st), &tmap_hi, 0, row, blk, afull);
                     tma_load_3d(su32(st + A_BYTES), &tmap_lo, 0, row, blk, afull);
@@ -221,11 +191,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             // failure-path test hook: wait (bounded) on a flag that nothing sets; the
             // expiry takes the same abort path as any other expired wait
             if (bt.inject_stall && !flag_wait(&ctr->never_set, abort_flag, ctr, ERR_INJECTED, wait_ns)) ok = false;
+            UnitRec nx = record(k_first);
             for (int64_t k = k_first; k < k_end && ok; k += k_step) {
-                const int64_t u = unit_at(k);
-                const Unit x = decode_unit(bt, u);
-                const Chunk ch = x.ch;
-                const uint32_t idesc = (x.ncols == TC_N) ? IDESC : idesc_f16_f32(TC_M, x.ncols);
+                const UnitRec x = nx;
+                nx = record(k + k_step);
+                const int ncols = mma_n(x);
+                const uint32_t idesc = (ncols == TC_N) ? IDESC : idesc_f16_f32(TC_M, ncols);
                 if (!mbar_wait(su32(&bars->acc_empty[acc]), acc_phase ^ 1u, abort_flag, ctr, ERR_WAIT_MMA, wait_ns)) {
                     ok = false;
                     break;
@@ -233,7 +204,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 fence_after();
                 const uint32_t d_tmem = tmem_base + (uint32_t)(acc * TC_N);
                 bool first = true;
-                for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
+                for (int kb = x.kb0; kb < x.kb1; ++kb) {
                     if (!mbar_wait(su32(&bars->a_full[stage]), phase, abort_flag, ctr, ERR_WAIT_MMA, wait_ns) ||
                         !mbar_wait(su32(&bars->b_full[stage]), phase, abort_flag, ctr, ERR_WAIT_MMA, wait_ns)) {
                         ok = false;
@@ -281,14 +252,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         int acc = 0;
         uint32_t acc_phase = 0, red_phase = 0;
         int rbuf = 0;
+        UnitRec nx = record(k_first);
         for (int64_t k = k_first; k < k_end; k += k_step) {
-            const int64_t u = unit_at(k);
-            const Unit x = decode_unit(bt, u);
-            const Chunk ch = x.ch;
+            const UnitRec x = nx;
+            nx = record(k + k_step);
             const int64_t Bp = x.Bp;
             // mask word of this warp's 32 rows, for the warp's 128 relabelings
-            const uint32_t *wrow =
-                bt.maskT + x.mask0 + ((int64_t)ch.I * 8 + x.h * 4 + quarter) * Bp + x.m * TC_N + g0 * 32;
+            const uint32_t *wrow = bt.maskT + x.mask_col + ((int64_t)x.I * 8 + x.h * 4 + quarter) * Bp + g0 * 32;
             uint32_t words[4];
 #pragma unroll
             for (int g = 0; g < 4; ++g) words[g] = wrow[g * 32 + lane];
@@ -337,7 +307,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             mbar_arrive(su32(&bars->red));
             if (!mbar_wait(su32(&bars->red), red_phase, abort_flag, ctr, ERR_WAIT_EPI, wait_ns)) break;
             const float *rb = red + rbuf * 4 * TC_N;
-            float *out = bt.partial + x.part0 + (2 * x.q + x.h) * Bp + x.m * TC_N;
+            float *out = bt.partial + x.out_off;
             out[et] = (rb[et] + rb[TC_N + et]) + (rb[2 * TC_N + et] + rb[3 * TC_N + et]);
             red_phase ^= 1u;
             rbuf ^= 1;
@@ -354,12 +324,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
+        UnitRec nx = record(k_first);
         for (int64_t k = k_first; k < k_end && ok; k += k_step) {
-                const int64_t u = unit_at(k);
-            const Unit x = decode_unit(bt, u);
-            const Chunk ch = x.ch;
+            const UnitRec x = nx;
+            nx = record(k + k_step);
             const int64_t Bp = x.Bp;
-            const uint32_t *maskT = bt.maskT + x.mask0 + x.m * TC_N + r;
+            const uint32_t *maskT = bt.maskT + x.mask_col + r;
             // words 2 kb and 2 kb + 1 of relabeling r
             auto load2 = [&](int kb, uint2 &w) {
                 const uint32_t *p0 = maskT + (int64_t)(2 * kb) * Bp;
@@ -367,17 +337,18 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                 w.y = p0[Bp];
             };
             uint2 cur = make_uint2(0, 0), nxt = make_uint2(0, 0);
-            load2(ch.kb0, cur);
-            if (ch.kb0 + 1 < ch.kb1) load2(ch.kb0 + 1, nxt);
-            for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
+            load2(x.kb0, cur);
+            if (x.kb0 + 1 < x.kb1) load2(x.kb0 + 1, nxt);
+            const int ncols = mma_n(x);
+            for (int kb = x.kb0; kb < x.kb1; ++kb) {
                 uint2 nn = make_uint2(0, 0);
-                if (kb + 2 < ch.kb1) load2(kb + 2, nn);
+                if (kb + 2 < x.kb1) load2(kb + 2, nn);
                 if (!mbar_wait(su32(&bars->empty[stage]), phase ^ 1u, abort_flag, ctr, ERR_WAIT_MASK, wait_ns)) {
                     ok = false;
                     break;
                 }
                 uint8_t *brow = smem + stage * STAGE_BYTES + 2 * A_BYTES + r * 128;
-                if (r < x.ncols) {   // rows past the tile's columns are not read by the MMA
+                if (r < ncols) {   // rows past the tile's columns are not read by the MMA
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         const uint32_t w = c < 4 ? cur.x : cur.y;

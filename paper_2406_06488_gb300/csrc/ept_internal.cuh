@@ -135,6 +135,20 @@ __device__ __forceinline__ float packed_scale(const Counters &k) {
 
 // chunk q of a test's contraction: panel I, K-blocks [kb0, kb1)
 struct Chunk { int I, kb0, kb1, pad; };
+// A tensor-core contraction work unit as its kernels need it, built on the host for
+// every position of the schedule (so that a CTA reads its next unit with one 64-byte
+// load instead of walking the test, chunk and schedule tables): chunk (panel I,
+// K-blocks [kb0, kb1), the two all-zero K-blocks below the diagonal skipped for the
+// second row half), row half h, the relabeling columns of its 256-column tile that
+// exist (at most 256), the test's K-blocks per panel row (NKB) and column stride (Bp),
+// its first stored block, the maskT offset of the tile's first column and the
+// partials offset of the unit's row (part0 + (2q + h) Bp + 256 m).
+struct alignas(16) UnitRec {
+    int32_t I, kb0, kb1, h, left, NKB;
+    int64_t Bp, blk0, mask_col, out_off;
+    int32_t pad[2];
+};
+static_assert(sizeof(UnitRec) == 64, "unit record");
 // a stored block of the batch: test t, panel I, K-block kb
 struct BlkInfo { int t, I, kb, pad; };
 // a build tile of the batch: test t, rows of panel I (half h), columns of panel J >= I
@@ -188,6 +202,7 @@ struct Batch {
     const Tile *tiles;
     const Chunk *chunks;
     const int64_t *sched, *sched_off;    // contraction schedule per CTA (null: units strided over the grid)
+    const UnitRec *urec;                 // the scheduled units' records, in schedule order (null: none)
     int tc_grid;                         // contraction CTAs when scheduled
     int64_t nblk_total, ntiles, nrows_total, npan_total, ncols_total, nunits_total, nsimt_total;
     int64_t p_stride;                    // row stride of the FP16 rows (max p_pad)
@@ -209,6 +224,27 @@ struct Batch {
 
 // tensor-core contraction work units of a test: chunk x relabeling tile x row half
 __host__ __device__ inline int64_t tc_units(const TestDesc &d) { return d.nchunks * d.MT * 2; }
+
+// the record of local unit lu of test d (units of a test are ordered (q, m, h)), its chunk ch
+__host__ __device__ inline UnitRec unit_record(const TestDesc &d, int64_t lu, Chunk ch) {
+    UnitRec r;
+    const int64_t h = lu & 1, q = (lu >> 1) / d.MT, m = (lu >> 1) % d.MT;
+    if (h == 1 && ch.kb0 == KB_PER_PANEL * ch.I && ch.kb1 - ch.kb0 > 2) ch.kb0 += 2;
+    r.I = ch.I;
+    r.kb0 = ch.kb0;
+    r.kb1 = ch.kb1;
+    r.h = (int32_t)h;
+    const int64_t left = d.ncols - m * TC_TILE_N;
+    r.left = left > TC_TILE_N ? TC_TILE_N : (int32_t)left;
+    r.NKB = (int32_t)d.NKB;
+    r.Bp = d.Bp;
+    r.blk0 = d.blk0;
+    r.mask_col = d.mask0 + m * TC_TILE_N;
+    r.out_off = d.part0 + (2 * q + h) * d.Bp + m * TC_TILE_N;
+    r.pad[0] = r.pad[1] = 0;
+    return r;
+}
+
 
 // Contraction chunks of a test: panel I covers the L = NKBc - 4I K-blocks from its
 // diagonal to NKBc = ceil(n / KB), the last K-block holding real columns (the padding
@@ -298,6 +334,17 @@ __device__ __forceinline__ int find_test(const int64_t *pre, int nt, int64_t g) 
         else hi = mid - 1;
     }
     return lo;
+}
+
+// the record of schedule position k of a batch: the precomputed one, or built from
+// the unit's test and chunk (unscheduled runs: position k is unit k)
+__device__ __forceinline__ UnitRec unit_at_position(const Batch &bt, int64_t k) {
+    if (bt.urec) return bt.urec[k];
+    const int64_t u = bt.sched ? bt.sched[k] : k;
+    const int t = find_test(bt.pre.units, bt.n_tests, u);
+    const TestDesc &d = bt.desc[t];
+    const int64_t lu = u - bt.pre.units[t];
+    return unit_record(d, lu, bt.chunks[d.chunk0 + (lu >> 1) / d.MT]);
 }
 
 // ---- launchers (ept_kernels.cu) ----
