@@ -462,6 +462,7 @@ void launch_build_simt(const Batch &b, cudaStream_t s) {
 // precision at FP32 cost.  One CTA per stored block of the batch.
 __global__ void __launch_bounds__(256) k_blocksums(const Batch bt) {
     __shared__ double cs[8][64];
+    __shared__ float wmax[8];
     const int64_t gb = blockIdx.x;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     float *base = bt.D + gb * (int64_t)(PANEL * KB);
@@ -513,13 +514,13 @@ __global__ void __launch_bounds__(256) k_blocksums(const Batch bt) {
 #pragma unroll
         for (int q = 0; q < 16; ++q) mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[q].x), fabsf(v[q].y)), fmaxf(fabsf(v[q].z), fabsf(v[q].w))));
         for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
-        if (lane == 0) atomicMax(&bt.ctr[bt.blk[gb].t].max_d_bits, __float_as_uint(mx));
+        if (lane == 0) wmax[warp] = mx;   // one atomic per block below, not one per warp
     }
     // column sums: warp w covers rows 32w..32w+31, lane l columns 2l and 2l+1
     {
         const float *cbase = base + (int64_t)(warp * 32) * KB + 2 * lane;
         float ch0 = 0.f, cl0 = 0.f, ch1 = 0.f, cl1 = 0.f;
-#pragma unroll 1
+#pragma unroll
         for (int r0 = 0; r0 < 32; r0 += 8) {
             float2 v[8];
 #pragma unroll
@@ -544,6 +545,12 @@ __global__ void __launch_bounds__(256) k_blocksums(const Batch bt) {
 #pragma unroll
         for (int w = 0; w < 8; ++w) acc += cs[w][t];
         bt.colpart[gb * KB + t] = acc;
+    }
+    if (t == 64) {
+        float mx = wmax[0];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) mx = fmaxf(mx, wmax[w]);
+        atomicMax(&bt.ctr[bt.blk[gb].t].max_d_bits, __float_as_uint(mx));
     }
 }
 
@@ -946,6 +953,7 @@ __global__ void __launch_bounds__(256) k_combine_stats(const Batch bt) {
     const int64_t Bp = d.Bp, nparts = d.nparts;
     const float *part = bt.partial + d.part0 + c;
     double acc = 0.0, aabs = 0.0;
+#pragma unroll 4
     for (int64_t k = warp; k < nparts; k += 8) {
         const double v = (double)part[k * Bp];
         acc += v;
