@@ -112,6 +112,7 @@ struct Plan {
     std::vector<Chunk> chunks;
     std::vector<int64_t> sched, sched_off;   // contraction schedule: units of CTA c = sched[sched_off[c] ..)
     std::vector<UnitRec> urec;               // the scheduled units' records, in schedule order
+    std::vector<UnitRec> urec_pair;          // pair contraction (kernel 2): the record of unit 2 pu for pair unit pu
     uint64_t serial = 0;                     // distinct for every plan_batch (the records are uploaded once per plan)
     bool user_masks = false;                 // some test brings its own relabelings
     int draw_mode = 0;                       // relabeling-draw kernel of the run (0: the context's choice)
@@ -127,7 +128,7 @@ struct Plan {
     size_t in_bytes = 0;              // host inputs copied into the arena
     // byte offsets in the arena; the first tab_bytes are the uploaded tables
     size_t off_desc, off_pre_rows, off_pre_panels, off_pre_cols, off_pre_units, off_pre_simt, off_blk, off_tiles,
-        off_chunks, off_sched, off_sched_off, off_urec, tab_bytes;
+        off_chunks, off_sched, off_sched_off, off_urec, off_urec_pair, tab_bytes;
     size_t off_in, off_norms, off_iscale, off_u, off_Zh, off_Zl, off_D, off_Chi, off_rowpart, off_colpart,
         off_r, off_Spart, off_dcorr, off_Upart, off_Stpart, off_maskT, off_partial, off_stats, off_observed, off_ctr,
         total;
@@ -241,7 +242,7 @@ void plan_schedule(Plan &P, int num_sms, int unit_order = 0) {
 }
 
 void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host_in, int chunk_kb,
-                int num_sms = 160, bool debug = false, bool schedule = true, int order = 0) {
+                int num_sms = 160, bool debug = false, bool schedule = true, int order = 0, bool pair_records = false) {
     P = Plan();
     static std::atomic<uint64_t> plans{0};
     P.serial = ++plans;
@@ -302,6 +303,16 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
     P.ncols_pad = P.pre_cols.back();
     P.nunits = P.pre_units.back();
     if (tc && schedule) plan_schedule(P, num_sms, order);
+    if (tc && pair_records) {   // the pair kernel takes pair units in order (unit 2 pu: row half 0)
+        P.urec_pair.resize((size_t)(P.nunits / 2));
+        for (int64_t pu = 0; pu < P.nunits / 2; ++pu) {
+            const int64_t u = 2 * pu;
+            const int t = (int)(std::upper_bound(P.pre_units.begin(), P.pre_units.end(), u) - P.pre_units.begin()) - 1;
+            const TestDesc &d = P.desc[t];
+            const int64_t lu = u - P.pre_units[t];
+            P.urec_pair[(size_t)pu] = unit_record(d, lu, P.chunks[(size_t)(d.chunk0 + (lu >> 1) / d.MT)]);
+        }
+    }
     P.nsimt = P.pre_simt.back();
     P.in_bytes = in_bytes;
 
@@ -333,6 +344,7 @@ void plan_batch(Plan &P, const std::vector<TestSpec> &specs, int prec, bool host
     in_data = true;
     // the unit records: uploaded with the first run of the plan, not with every run
     P.off_urec = take(sizeof(UnitRec) * P.urec.size());
+    P.off_urec_pair = take(sizeof(UnitRec) * P.urec_pair.size());
     if (P.debug) {   // a band right after the tables as well
         P.guards.off[P.guards.n++] = o;
         o += GUARD_BYTES;
@@ -847,6 +859,7 @@ Batch device_view(ept_ctx *c, const Plan &P) {
     b.sched = P.sched.empty() ? nullptr : (const int64_t *)(A + P.off_sched);
     b.sched_off = P.sched.empty() ? nullptr : (const int64_t *)(A + P.off_sched_off);
     b.urec = P.urec.empty() ? nullptr : (const UnitRec *)(A + P.off_urec);
+    b.urec_pair = P.urec_pair.empty() ? nullptr : (const UnitRec *)(A + P.off_urec_pair);
     b.tc_grid = P.tc_grid;
     b.nblk_total = P.nblk;
     b.ntiles = (int64_t)P.tiles.size();
@@ -918,11 +931,15 @@ ept_status enqueue_uploads(ept_ctx *c, const Plan &P, cudaStream_t s) {
     CK(cudaMemcpyAsync(c->arena, c->pinned + S.tables, P.tab_bytes, cudaMemcpyHostToDevice, s));
     // the unit records stay in the arena while the same plan runs on it; a run of any
     // other plan may overwrite them
-    if (P.urec.empty()) {
+    if (P.urec.empty() && P.urec_pair.empty()) {
         c->urec_serial = 0;
     } else if (c->urec_serial != P.serial || c->urec_arena != c->arena) {
-        CK(cudaMemcpyAsync(c->arena + P.off_urec, P.urec.data(), sizeof(UnitRec) * P.urec.size(),
-                           cudaMemcpyHostToDevice, s));
+        if (!P.urec.empty())
+            CK(cudaMemcpyAsync(c->arena + P.off_urec, P.urec.data(), sizeof(UnitRec) * P.urec.size(),
+                               cudaMemcpyHostToDevice, s));
+        if (!P.urec_pair.empty())
+            CK(cudaMemcpyAsync(c->arena + P.off_urec_pair, P.urec_pair.data(), sizeof(UnitRec) * P.urec_pair.size(),
+                               cudaMemcpyHostToDevice, s));
         c->urec_serial = P.serial;
         c->urec_arena = c->arena;
     }
@@ -1340,7 +1357,8 @@ ept_status run_once(ept_ctx *c, const std::vector<TestSpec> &specs, int prec, bo
         if (!c->plan) return fail(EPT_ENOMEM, "host allocation failed");
     }
     if (c->plan_key != pkey) {
-        plan_batch(*c->plan, specs, prec, !on_device, chunk_kb, c->num_sms, c->debug, true, tn.order);
+        plan_batch(*c->plan, specs, prec, !on_device, chunk_kb, c->num_sms, c->debug, true, tn.order,
+                   (tn.kernel ? tn.kernel : contraction_kernel(c)) == 2);
         c->plan->draw_mode = tn.draw_mode;
         c->plan->contraction = tn.kernel;
         c->plan_key = pkey;
@@ -2212,7 +2230,8 @@ bool form_batch(Server *S, Lane &L) {
     std::vector<TestSpec> specs;
     for (Request *r : batch) specs.push_back(r->spec);
     while (!batch.empty()) {
-        plan_batch(L.plan, specs, prec, true, unit_kb(L.ctx), L.ctx->num_sms);
+        plan_batch(L.plan, specs, prec, true, unit_kb(L.ctx), L.ctx->num_sms, false, true, 0,
+                   contraction_kernel(S->owner) == 2);
         if (S->in_use + L.plan.total <= S->budget) break;
         // hand the last one back, at its place in arrival order
         Request *r = batch.back();

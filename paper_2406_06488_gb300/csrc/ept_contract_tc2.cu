@@ -147,28 +147,34 @@ __device__ __forceinline__ void mma2_commit_leader(uint32_t bar) {
         : "memory");
 }
 
-// the test fields, chunk and relabeling tile of pair unit pu (the units of the
-// single-CTA kernel with row half 0), read once into registers
+// the test fields, chunk and relabeling tile of a pair unit, in registers: from the
+// record of unit 2 pu (row half 0 of the single-CTA numbering), with the mask and
+// partial offsets of the tile folded into mask0 and part0 (so q = m = 0)
 struct Unit {
     Chunk ch;
     int64_t q, m, Bp, mask0, part0, blk0, NKB;
 };
 
-__device__ __forceinline__ Unit decode_pair_unit(const Batch &bt, int64_t pu) {
-    const int64_t u = 2 * pu;   // row half 0 of the single-CTA numbering
+__device__ __forceinline__ UnitRec pair_record(const Batch &bt, int64_t pu, int64_t npu) {
+    if (pu >= npu) return UnitRec{};
+    if (bt.urec_pair) return bt.urec_pair[pu];
+    const int64_t u = 2 * pu;
     const int t = find_test(bt.pre.units, bt.n_tests, u);
-    const TestDesc *d = &bt.desc[t];
-    Unit x;
+    const TestDesc &d = bt.desc[t];
     const int64_t lu = u - bt.pre.units[t];
-    const int64_t MT = d->MT;
-    x.q = (lu >> 1) / MT;
-    x.m = (lu >> 1) % MT;
-    x.Bp = d->Bp;
-    x.mask0 = d->mask0;
-    x.part0 = d->part0;
-    x.blk0 = d->blk0;
-    x.NKB = d->NKB;
-    x.ch = bt.chunks[d->chunk0 + x.q];
+    return unit_record(d, lu, bt.chunks[d.chunk0 + (lu >> 1) / d.MT]);
+}
+
+__device__ __forceinline__ Unit unit_of(const UnitRec &r) {
+    Unit x;
+    x.ch = Chunk{r.I, r.kb0, r.kb1, 0};
+    x.q = 0;
+    x.m = 0;
+    x.Bp = r.Bp;
+    x.mask0 = r.mask_col;
+    x.part0 = r.out_off;
+    x.blk0 = r.blk0;
+    x.NKB = r.NKB;
     return x;
 }
 
@@ -230,8 +236,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             int armed[STAGES];
             for (int s2 = 0; s2 < STAGES; ++s2) armed[s2] = -1;
             bool ok = true;
+            UnitRec nr = pair_record(bt, pair, npu);
             for (int64_t pu = pair; pu < npu && ok; pu += npairs) {
-                const Unit x = decode_pair_unit(bt, pu);
+                const Unit x = unit_of(nr);
+                nr = pair_record(bt, pu + npairs, npu);   // the next unit's record, read while this one runs
                 const Chunk ch = x.ch;
                 const int row = (int)rank * TC_M;
                 for (int kb = ch.kb0; kb < ch.kb1; ++kb) {
@@ -272,8 +280,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             uint32_t phase = 0, acc_phase = 0;
             bool ok = true;
             if (bt.inject_stall && !flag_wait(&ctr->never_set, abort_flag, ctr, ERR_INJECTED, wait_ns)) ok = false;
+            UnitRec nr = pair_record(bt, pair, npu);
             for (int64_t pu = pair; pu < npu && ok; pu += npairs) {
-                const Unit x = decode_pair_unit(bt, pu);
+                const Unit x = unit_of(nr);
+                nr = pair_record(bt, pu + npairs, npu);   // the next unit's record, read while this one runs
                 const Chunk ch = x.ch;
                 if (!mbar_wait_cluster(su32(&bars->acc_empty[acc]), acc_phase ^ 1u, abort_flag, ctr, ERR_WAIT_MMA,
                                        wait_ns)) {
@@ -328,8 +338,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
             int stage = 0;
             uint32_t phase = 0;
             bool ok = true;
+            UnitRec nr = pair_record(bt, pair, npu);
             for (int64_t pu = pair; pu < npu && ok; pu += npairs) {
-                const Unit x = decode_pair_unit(bt, pu);
+                const Unit x = unit_of(nr);
+                nr = pair_record(bt, pu + npairs, npu);   // the next unit's record, read while this one runs
                 for (int kb = x.ch.kb0; kb < x.ch.kb1; ++kb) {
                     if (!mbar_wait(su32(&bars->a_full[stage]), phase, abort_flag, ctr, ERR_WAIT_PEER, wait_ns) ||
                         !mbar_wait(su32(&bars->b_full[stage]), phase, abort_flag, ctr, ERR_WAIT_PEER, wait_ns)) {
@@ -352,8 +364,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         int acc = 0;
         uint32_t acc_phase = 0, red_phase = 0;
         int rbuf = 0;
+        UnitRec nr = pair_record(bt, pair, npu);
         for (int64_t pu = pair; pu < npu; pu += npairs) {
-            const Unit x = decode_pair_unit(bt, pu);
+            const Unit x = unit_of(nr);
+            nr = pair_record(bt, pu + npairs, npu);   // the next unit's record, read while this one runs
             const Chunk ch = x.ch;
             const int64_t Bp = x.Bp;
             const uint32_t *wrow =
@@ -418,8 +432,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
+        UnitRec nr = pair_record(bt, pair, npu);
         for (int64_t pu = pair; pu < npu && ok; pu += npairs) {
-            const Unit x = decode_pair_unit(bt, pu);
+            const Unit x = unit_of(nr);
+            nr = pair_record(bt, pu + npairs, npu);   // the next unit's record, read while this one runs
             const Chunk ch = x.ch;
             const int64_t Bp = x.Bp;
             const uint32_t *maskT = bt.maskT + x.mask0 + x.m * TC_N + rank * BH + r;

@@ -203,6 +203,7 @@ struct Batch {
     const Chunk *chunks;
     const int64_t *sched, *sched_off;    // contraction schedule per CTA (null: units strided over the grid)
     const UnitRec *urec;                 // the scheduled units' records, in schedule order (null: none)
+    const UnitRec *urec_pair;            // pair contraction: the record of unit 2 pu for pair unit pu (null: none)
     int tc_grid;                         // contraction CTAs when scheduled
     int64_t nblk_total, ntiles, nrows_total, npan_total, ncols_total, nunits_total, nsimt_total;
     int64_t p_stride;                    // row stride of the FP16 rows (max p_pad)
