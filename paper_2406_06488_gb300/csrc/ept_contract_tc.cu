@@ -30,6 +30,9 @@
 // Roles (576 threads): warp 0 = TMA producer, warp 1 = MMA issuer (and TMEM
 // owner), warps 2-9 = epilogue (two warps per TMEM lane quarter, each taking half
 // of the relabelings), warps 10-17 = relabeling-tile producers (one B row each).
+// Every role takes its units from the precomputed 64-byte records of the schedule
+// (UnitRec) and reads the next unit's record while it works on the current one, so
+// that no role waits on the schedule, test and chunk tables at a unit boundary.
 // Two epilogue and two producer warps per SM sub-partition hide each other's
 // shared-memory and L2 latencies.  Every wait on an mbarrier is bounded (2 s unless
 // the context sets another limit), and a waiting thread sleeps in the wait until its
