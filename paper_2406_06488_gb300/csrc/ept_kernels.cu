@@ -934,13 +934,15 @@ void launch_contract_simt(const Batch &b, cudaStream_t s) {
 // Final combination (Algorithm 1, statistic and p-value lines): per relabeling
 // column b, Q_b = sum of its partials, stat_b = sign * (cT Q_b + S~/o^2).  A CTA
 // covers 32 columns of one test (the column padding is a multiple of 256): lane l of
-// each of its 8 warps reads column l of every eighth partial (one coalesced 128-byte
-// row per load), and the 8 warp sums are added in a fixed order (deterministic).
+// each of its 16 warps reads column l of every 16th partial (one coalesced 128-byte
+// row per load, eight loads in flight), and the 16 warp sums are added in a fixed
+// order (deterministic).
 // Then k_combine_count compares against stat_0 (the identity, evaluated by the same
 // kernels): stat_b >= stat_0 and near-ties |stat_b - stat_0| <= 1e-5 |stat_0|.
-__global__ void __launch_bounds__(256) k_combine_stats(const Batch bt) {
+__global__ void __launch_bounds__(512) k_combine_stats(const Batch bt) {
+    constexpr int NW = 16;   // warps: parts k = warp, warp + NW, ...
     __shared__ double bSt;
-    __shared__ double ws[8][32], wa[8][32];
+    __shared__ double ws[NW][32], wa[NW][32];
     const int64_t gc0 = (int64_t)blockIdx.x * 32;
     const int t = find_test(bt.pre.cols, bt.n_tests, gc0);
     const TestDesc &d = bt.desc[t];
@@ -952,20 +954,26 @@ __global__ void __launch_bounds__(256) k_combine_stats(const Batch bt) {
     const int64_t c = gc0 + lane - bt.pre.cols[t];
     const int64_t Bp = d.Bp, nparts = d.nparts;
     const float *part = bt.partial + d.part0 + c;
-    double acc = 0.0, aabs = 0.0;
-#pragma unroll 4
-    for (int64_t k = warp; k < nparts; k += 8) {
-        const double v = (double)part[k * Bp];
-        acc += v;
-        aabs += fabs(v);
+    // a warp's parts summed as an unevaluated FP32 pair (TwoSum: each addition's
+    // rounding error is kept exactly), so that no FP64 operation runs per partial;
+    // the pairs of the warps then meet in FP64 in a fixed order
+    float h = 0.f, l = 0.f, aabs = 0.f;
+#pragma unroll 8
+    for (int64_t k = warp; k < nparts; k += NW) {
+        const float v = part[k * Bp];
+        float s2, e;
+        two_sum(h, v, s2, e);
+        h = s2;
+        l += e;
+        aabs += fabsf(v);
     }
-    ws[warp][lane] = acc;
-    wa[warp][lane] = aabs;
+    ws[warp][lane] = (double)h + (double)l;
+    wa[warp][lane] = (double)aabs;
     __syncthreads();
     if (warp == 0) {
         double q = 0.0, a = 0.0;
 #pragma unroll
-        for (int w = 0; w < 8; ++w) {
+        for (int w = 0; w < NW; ++w) {
             q += ws[w][lane];
             a += wa[w][lane];
         }
@@ -1059,7 +1067,7 @@ __global__ void __launch_bounds__(256) k_combine_count(const Batch bt, int flag)
 void launch_combine(const Batch &b, cudaStream_t s) {
     if (b.ncols_total <= 0) return;
     if (b.n_tests > 1) k_batch_status<<<1, 256, 0, s>>>(b);
-    k_combine_stats<<<(unsigned)(b.ncols_total / 32), 256, 0, s>>>(b);
+    k_combine_stats<<<(unsigned)(b.ncols_total / 32), 512, 0, s>>>(b);
     k_combine_count<<<(unsigned)(b.ncols_total / 256), 256, 0, s>>>(b, 1);
 }
 
