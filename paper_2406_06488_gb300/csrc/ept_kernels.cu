@@ -459,98 +459,108 @@ void launch_build_simt(const Batch &b, cudaStream_t s) {
 // their column sums supply it).  Sums are accumulated as unevaluated FP32 pairs
 // (hi, lo) with Knuth's TwoSum, an error-free transformation (the rounding error of
 // every addition is carried in lo), then widened to FP64: about twice the FP32
-// precision at FP32 cost.  One CTA per stored block of the batch.
+// precision at FP32 cost.  One CTA per stored block of the batch, taking the block
+// in four quarters of 64 rows: each quarter is read once with coalesced 16-byte loads
+// into shared memory (rows padded to 65 words, so that threads walking rows or
+// columns hit distinct banks), then four threads per row and four per column each
+// sum 16 values, and the four pairs meet in a fixed order.
+
+// (h, l) += (h2, l2), the rounding error of the hi addition kept in l
+__device__ __forceinline__ void pair_add(float &h, float &l, float h2, float l2) {
+    float s2, e;
+    two_sum(h, h2, s2, e);
+    h = s2;
+    l += l2 + e;
+}
+
 __global__ void __launch_bounds__(256) k_blocksums(const Batch bt) {
-    __shared__ double cs[8][64];
+    constexpr int QR = 64, LD = KB + 1;   // rows per quarter, padded row length
+    __shared__ float tile[QR * LD];
     __shared__ float wmax[8];
     const int64_t gb = blockIdx.x;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     float *base = bt.D + gb * (int64_t)(PANEL * KB);
-    {
-        // median-heuristic tests: the build wrote distances; now that the bandwidth is
-        // known, turn them into kernel values in place (padding stays 0)
-        const BlkInfo bi = bt.blk[gb];
-        const TestDesc &d = bt.desc[bi.t];
-        if (d.median) {
-            const float sigma = __uint_as_float(bt.ctr[bi.t].sel_prefix);
-            const float neg = -1.f / (2.f * sigma * sigma), inv = 1.f / sigma;
-            const int64_t i = (int64_t)bi.I * PANEL + t, n = d.n;
-            const bool gauss = d.stat == 1;
-            float4 *row = reinterpret_cast<float4 *>(base + (int64_t)t * KB);
-#pragma unroll 4
-            for (int q = 0; q < 16; ++q) {
-                float4 v = row[q];
+    const BlkInfo bi = bt.blk[gb];
+    const TestDesc &d = bt.desc[bi.t];
+    // median-heuristic tests: the build wrote distances; now that the bandwidth is
+    // known, they become kernel values in place as they are read (padding stays 0)
+    const bool median = d.median != 0;
+    float neg = 0.f, inv = 0.f;
+    if (median) {
+        const float sigma = __uint_as_float(bt.ctr[bi.t].sel_prefix);
+        neg = -1.f / (2.f * sigma * sigma);
+        inv = 1.f / sigma;
+    }
+    const bool gauss = d.stat == 1;
+    const int64_t n = d.n;
+    float mx = 0.f;
+    const int rr = t >> 2, part = t & 3;   // row rr (or column rr) of the quarter, its quarter `part`
+    float ch = 0.f, cl = 0.f;               // this thread's column partial over the block's quarters
+    for (int qtr = 0; qtr < PANEL / QR; ++qtr) {
+        float *qbase = base + (int64_t)qtr * QR * KB;
+        // coalesced load: float4 k = t + 256 i covers row k / 16, columns 4 (k % 16) ..
+#pragma unroll
+        for (int i = 0; i < QR * KB / 4 / 256; ++i) {
+            const int k = t + 256 * i, row = k >> 4, c4 = (k & 15) * 4;
+            float4 v = reinterpret_cast<const float4 *>(qbase)[k];
+            if (median) {
+                const int64_t gi = (int64_t)bi.I * PANEL + qtr * QR + row, gj = (int64_t)bi.kb * KB + c4;
                 float e4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int64_t j = (int64_t)bi.kb * KB + 4 * q + k;
-                    if (i < n && j < n) e4[k] = gauss ? exp_cw(e4[k] * e4[k] * neg) : exp_cw(-e4[k] * inv);
-                }
-                row[q] = make_float4(e4[0], e4[1], e4[2], e4[3]);
+                for (int e = 0; e < 4; ++e)
+                    if (gi < n && gj + e < n) e4[e] = gauss ? exp_cw(e4[e] * e4[e] * neg) : exp_cw(-e4[e] * inv);
+                v = make_float4(e4[0], e4[1], e4[2], e4[3]);
+                reinterpret_cast<float4 *>(qbase)[k] = v;
             }
-            __syncthreads();
+            mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+            float *dst = tile + row * LD + c4;
+            dst[0] = v.x;
+            dst[1] = v.y;
+            dst[2] = v.z;
+            dst[3] = v.w;
         }
+        __syncthreads();
+        // row rr of the quarter: columns 16 part .. 16 part + 15, then the four parts in order
+        {
+            float h = 0.f, l = 0.f;
+            const float *src = tile + rr * LD + 16 * part;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) pair_add(h, l, src[j], 0.f);
+            float h1 = __shfl_xor_sync(0xFFFFFFFFu, h, 1), l1 = __shfl_xor_sync(0xFFFFFFFFu, l, 1);
+            if (part & 1) { const float th = h, tl = l; h = h1; l = l1; h1 = th; l1 = tl; }
+            pair_add(h, l, h1, l1);   // (part 0 + part 1), (part 2 + part 3)
+            float h2 = __shfl_xor_sync(0xFFFFFFFFu, h, 2), l2 = __shfl_xor_sync(0xFFFFFFFFu, l, 2);
+            if (part & 2) { const float th = h, tl = l; h = h2; l = l2; h2 = th; l2 = tl; }
+            pair_add(h, l, h2, l2);   // (0 + 1) + (2 + 3)
+            if (part == 0) bt.rowpart[gb * PANEL + qtr * QR + rr] = (double)h + (double)l;
+        }
+        // column rr: rows 16 part .. 16 part + 15 of the quarter, into this thread's pair
+        {
+            const float *src = tile + (16 * part) * LD + rr;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) pair_add(ch, cl, src[i * LD], 0.f);
+        }
+        __syncthreads();
     }
-    // row sums: thread t owns row t (64 contiguous values, no cross-thread traffic)
+    // the column's four parts in order: (0 + 1) + (2 + 3)
     {
-        const float4 *row = reinterpret_cast<const float4 *>(base + (int64_t)t * KB);
-        float4 v[16];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = row[q];
-        float h = 0.f, l = 0.f;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const float e4[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                float s2, f;
-                two_sum(h, e4[k], s2, f);
-                h = s2;
-                l += f;
-            }
-        }
-        bt.rowpart[gb * PANEL + t] = (double)h + (double)l;
-        float mx = 0.f;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) mx = fmaxf(mx, fmaxf(fmaxf(fabsf(v[q].x), fabsf(v[q].y)), fmaxf(fabsf(v[q].z), fabsf(v[q].w))));
-        for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
-        if (lane == 0) wmax[warp] = mx;   // one atomic per block below, not one per warp
+        float h = ch, l = cl;
+        float h1 = __shfl_xor_sync(0xFFFFFFFFu, h, 1), l1 = __shfl_xor_sync(0xFFFFFFFFu, l, 1);
+        if (part & 1) { const float th = h, tl = l; h = h1; l = l1; h1 = th; l1 = tl; }
+        pair_add(h, l, h1, l1);
+        float h2 = __shfl_xor_sync(0xFFFFFFFFu, h, 2), l2 = __shfl_xor_sync(0xFFFFFFFFu, l, 2);
+        if (part & 2) { const float th = h, tl = l; h = h2; l = l2; h2 = th; l2 = tl; }
+        pair_add(h, l, h2, l2);
+        if (part == 0) bt.colpart[gb * KB + rr] = (double)h + (double)l;
     }
-    // column sums: warp w covers rows 32w..32w+31, lane l columns 2l and 2l+1
-    {
-        const float *cbase = base + (int64_t)(warp * 32) * KB + 2 * lane;
-        float ch0 = 0.f, cl0 = 0.f, ch1 = 0.f, cl1 = 0.f;
-#pragma unroll
-        for (int r0 = 0; r0 < 32; r0 += 8) {
-            float2 v[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = *reinterpret_cast<const float2 *>(cbase + (int64_t)(r0 + q) * KB);
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                float s2, f;
-                two_sum(ch0, v[q].x, s2, f);
-                ch0 = s2;
-                cl0 += f;
-                two_sum(ch1, v[q].y, s2, f);
-                ch1 = s2;
-                cl1 += f;
-            }
-        }
-        cs[warp][2 * lane] = (double)ch0 + (double)cl0;
-        cs[warp][2 * lane + 1] = (double)ch1 + (double)cl1;
-    }
+    for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, off));
+    if (lane == 0) wmax[warp] = mx;
     __syncthreads();
-    if (t < 64) {
-        double acc = 0.0;
+    if (t == 0) {
+        float m = wmax[0];
 #pragma unroll
-        for (int w = 0; w < 8; ++w) acc += cs[w][t];
-        bt.colpart[gb * KB + t] = acc;
-    }
-    if (t == 64) {
-        float mx = wmax[0];
-#pragma unroll
-        for (int w = 1; w < 8; ++w) mx = fmaxf(mx, wmax[w]);
-        atomicMax(&bt.ctr[bt.blk[gb].t].max_d_bits, __float_as_uint(mx));
+        for (int w = 1; w < 8; ++w) m = fmaxf(m, wmax[w]);
+        atomicMax(&bt.ctr[bi.t].max_d_bits, __float_as_uint(m));
     }
 }
 
