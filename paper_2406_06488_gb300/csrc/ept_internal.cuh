@@ -298,7 +298,12 @@ __device__ __forceinline__ double entry_from_d2(double d2, int kern, float neg_i
 __host__ __device__ __forceinline__ float exp_cw(float x) {
     if (!(x > -87.f)) return 0.f;
     x = x < 0.f ? x : 0.f;
-    const float k = rintf(x * 1.44269504f);
+    // k = x log2(e) rounded to an integer by adding 1.5 2^23 (the sum's unit is 1, so the
+    // addition rounds to the nearest integer, which then sits in the low mantissa bits):
+    // two additions instead of a rounding and a float-to-integer conversion, which run at
+    // a quarter of the FP32 rate
+    const float t = fmaf(x, 1.44269504f, 12582912.f);
+    const float k = t - 12582912.f;
     float r = fmaf(-k, 0.693359375f, x);     // head of ln 2: exact products with |k| <= 126
     r = fmaf(-k, -2.12194440e-4f, r);        // tail of ln 2
     float q = 2.48015873e-5f;                // 1/8!
@@ -310,7 +315,13 @@ __host__ __device__ __forceinline__ float exp_cw(float x) {
     q = fmaf(q, r, 0.5f);
     q = fmaf(q, r, 1.f);
     q = fmaf(q, r, 1.f);
-    const uint32_t bits = (uint32_t)((int)k + 127) << 23;
+#ifdef __CUDA_ARCH__
+    const uint32_t tb = __float_as_uint(t);
+#else
+    uint32_t tb;
+    memcpy(&tb, &t, sizeof(tb));
+#endif
+    const uint32_t bits = (tb - 0x4B400000u + 127u) << 23;   // (k + 127) << 23, k = low bits of t
 #ifdef __CUDA_ARCH__
     return q * __uint_as_float(bits);
 #else
