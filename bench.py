@@ -40,7 +40,7 @@ BATCH_KERNELS_PER_STEP = 12  # ept_test_batch: the same and the batch's error st
 # dram read + write bytes of one k_contract_tc launch on the highdim and mmd workloads, from the
 # ncu captures summarised in profiles/k_contract_tc_highdim_ed.md and k_contract_tc_mmd.md (to be
 # reset to {} whenever the kernel changes, until it is captured again)
-CONTRACT_TRAFFIC = {"highdim": 60.99e6, "mmd": 1064.5e6}
+CONTRACT_TRAFFIC = {"highdim": 61.57e6, "mmd": 1076.8e6}
 # streaming mode: DRAM bytes per stored block of the contraction, from the n = 60,000 capture summarised in
 # profiles/k_contract_tc_stream_60k.md (scaled to a launch by its window's blocks)
 STREAM_TRAFFIC_PER_BLOCK = 9119.0e6 / 110920
