@@ -359,7 +359,7 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    tensor-memory operand (M = 128 relabelings stored from registers with tcgen05.st,
    N = 128 rows of C from shared memory; each epilogue thread sums its own
    relabeling's row values, no transposes).  0: the library's choice (1).  Measured
-   on a GB300 (n = 5000, B = 10^4 contraction): 1 319 us, 2 324 us, 3 451 us (the
+   on a GB300 (n = 5000, B = 10^4 contraction): 1 303 us, 2 311 us, 3 451 us (the
    MMA pipe alone, with N = 128, needs 366 us for the work that N = 256 does in 254
    us).  The statistics agree to the accumulation order.
    EPT_OPT_SERVE_LANES (default 3, 1..16): serving batches in flight at once;

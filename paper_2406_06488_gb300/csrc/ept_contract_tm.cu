@@ -28,7 +28,7 @@
 // accumulators of 128 columns let the epilogue of one sub-unit overlap the main
 // loop of the next; the relabeling stages take another 32 columns each).
 //
-// Measured on a GB300 (n = 5000, B = 10^4): 451 us against 319 us for
+// Measured on a GB300 (n = 5000, B = 10^4): 451 us against 303 us for
 // ept_contract_tc.cu.  The MMAs alone (no copies, producers or epilogue) take 366 us
 // here against 254 us there for the same multiply-adds: an MMA with N = 128 does
 // less work per cycle than one with N = 256 (with the C half-block as the
