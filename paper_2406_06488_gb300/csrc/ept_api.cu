@@ -1178,11 +1178,13 @@ void load_tune_file(ept_ctx *c) {
 }
 
 // Recomputation of the statistics the error criterion flagged (ept_refine.cu), after
-// a finished run whose scratch is still in place: per test, the columns flagged for
-// an exact re-summation of the packed operand, then those flagged for entries rebuilt
-// in FP64 (W64 in row windows of at most REFINE_W64_BYTES); then the counts again and
-// the results read back as the run itself does.  Statistics that were not flagged
-// keep their values.
+// a finished run whose scratch is still in place: the flags of every flagged test are
+// read back together; the columns flagged for an exact re-summation of the packed
+// operand, of all tests, in one launch (a job per group of up to 16 columns of a
+// test); then, test by test, those flagged for entries rebuilt in FP64 (W64 in row
+// windows of at most REFINE_W64_BYTES); then the counts again and the results read
+// back as the run itself does, with one synchronisation for all of it.  Statistics
+// that were not flagged keep their values.
 const size_t REFINE_W64_BYTES = (size_t)2 << 30;
 
 // the recomputation's scratch: the context's buffer, grown when needed (the previous
