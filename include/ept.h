@@ -320,8 +320,9 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    in K-blocks of 64 pooled columns, that the autotuner may pick (untuned runs use 8).
    The tensor cores accumulate each unit in FP32, and the error grows faster than the
    unit's length (measured: the accumulation coefficient of the error estimate below
-   has to be 6.8, 15.4 and 51.4 for units of 8, 16 and 32 K-blocks); the estimate takes
-   8, 20 and 64, so every length keeps the returned statistics within 1e-5 of the FP64
+   has to be 6.8, 15.4 and 51.4 for units of 8, 16 and 32 K-blocks on one sweep of 200
+   problems, 23.6 for one statistic with units of 16 on 400 more); the estimate takes
+   8, 32 and 96, so every length keeps the returned statistics within 1e-5 of the FP64
    oracle through the recomputation of the flagged ones, and the autotuner, which
    times whole runs with their recomputation, picks a longer unit only where it is
    faster all included.  With EPT_OPT_REFINE = 0 the fast values of longer units can
@@ -332,7 +333,7 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    its error, E_b = k_b u cT A_b + 4 u Wbar / m: u = 2^-24, cT = (n/(nx ny))^2, A_b
    the sum of the absolute values of its contraction partial sums (the magnitudes its
    FP32 accumulations carried), Wbar the mean entry of the pooled matrix, m =
-   min(nx, ny), k_b = 8 for a relabeling (20 with units of 16 K-blocks, 64 with units
+   min(nx, ny), k_b = 8 for a relabeling (32 with units of 16 K-blocks, 96 with units
    of 32) and 8 times that for the observed statistic and every statistic within
    1e-5 |observed| + 2 E_0 of it.  A statistic with
    E_b > 1e-5 |stat_b| is recomputed: when its representation term (the second) is
