@@ -153,6 +153,9 @@ def test_statistics_and_p_values_equal_the_oracle(ctxs, L, block):
             # value may, rarely, equal the fast one bit for bit)
             changed = got != fast
             assert r.n_refined == f.n_refined and int(changed.sum()) <= r.n_refined, (k, prec)
+            # the recomputation's launches are reported (reset + recount + at least one job)
+            assert (r.refine_launches >= 4) if r.n_refined else (r.refine_launches == 0), (k, prec, r.refine_launches)
+            assert f.refine_launches == 0
             # sound: every fast statistic beyond the tolerance was recomputed
             fast_bad = np.abs(fast - want) > REL_TOL * np.abs(want)
             assert not (fast_bad & ~changed).any(), (k, prec, np.flatnonzero(fast_bad & ~changed))
