@@ -399,6 +399,27 @@ ept_status check_plan(const Plan &P) {
             if (u < 0 || u >= P.nunits || seen[(size_t)u]) return bad("schedule covers every unit once");
             seen[(size_t)u] = 1;
         }
+        // the unit records: each one the unit the schedule names, its offsets inside its test's arrays
+        if ((int64_t)P.urec.size() != P.nunits) return bad("one record per scheduled unit");
+        for (int64_t k = 0; k < P.nunits; ++k) {
+            const int64_t u = P.sched[(size_t)k];
+            int t = 0;
+            while (t + 1 < P.n_tests && P.pre_units[t + 1] <= u) ++t;
+            const TestDesc &d = P.desc[t];
+            const int64_t lu = u - P.pre_units[t], h = lu & 1, q = (lu >> 1) / d.MT, m = (lu >> 1) % d.MT;
+            const Chunk &ch = P.chunks[(size_t)(d.chunk0 + q)];
+            const bool skip = h == 1 && ch.kb0 == KB_PER_PANEL * ch.I && ch.kb1 - ch.kb0 > 2;
+            const UnitRec &r = P.urec[(size_t)k];
+            if (r.I != ch.I || r.kb0 != ch.kb0 + (skip ? 2 : 0) || r.kb1 != ch.kb1 || r.h != h)
+                return bad("unit record chunk");
+            if (r.left < 1 || r.left > TC_TILE_N || r.left != std::min<int64_t>(TC_TILE_N, d.ncols - m * TC_TILE_N))
+                return bad("unit record columns");
+            if (r.NKB != d.NKB || r.Bp != d.Bp || r.blk0 != d.blk0) return bad("unit record test fields");
+            if (r.mask_col < d.mask0 || r.mask_col + TC_TILE_N > d.mask0 + d.Bp) return bad("unit record mask offset");
+            if (r.out_off < d.part0 || r.out_off + TC_TILE_N > d.part0 + d.nparts * d.Bp ||
+                r.out_off != d.part0 + (2 * q + h) * d.Bp + m * TC_TILE_N)
+                return bad("unit record partial offset");
+        }
     }
     for (int k = 0; k < P.guards.n; ++k)
         if (P.guards.off[k] + GUARD_BYTES > P.total || P.guards.off[k] % 256) return bad("guard band");
