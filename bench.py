@@ -460,6 +460,7 @@ def run_ours(args):
         "result": {"observed": last.observed, "p_value": last.p_value, "n_near_tie": last.n_near_tie,
                    "sigma": last.sigma, "n_refined": last.n_refined},
         "autotune": _tuning(first),
+        "library": ept.build_info(),
     }
     if args.workload == "highdim" and not args.no_extras and ws == 1:
         line["mmd"] = _extra_mmd(ctx, flush, peaks)

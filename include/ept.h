@@ -131,6 +131,12 @@ typedef struct {
 /* Library ABI version (EPT_ABI_VERSION of the build). */
 int ept_abi_version(void);
 
+/* How this copy of the library was built: ABI version, host architecture
+   (aarch64 / x86_64), the GPU architecture its kernels were compiled for, the nvcc
+   version and the compile date and time.  A static string owned by the library;
+   never NULL.  Needs no GPU. */
+const char *ept_build_info(void);
+
 /* Message describing the last error on the calling thread (owned by the library;
    valid until the next call on this thread).  Never NULL. */
 const char *ept_last_error(void);

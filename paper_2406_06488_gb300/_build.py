@@ -20,7 +20,7 @@ ROOT = os.path.dirname(HERE)
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-              "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
+              "--expt-relaxed-constexpr", "-DEPT_DEVICE_ARCH=sm_103a", "-I" + os.path.join(ROOT, "include")]
 
 
 def _nvcc() -> str:

@@ -2406,9 +2406,28 @@ void serve_stop(ept_ctx *c) {
 
 }  // namespace
 
+#define EPT_STR2(x) #x
+#define EPT_STR(x) EPT_STR2(x)
+#if defined(__aarch64__)
+#define EPT_HOST_ARCH "aarch64"
+#elif defined(__x86_64__)
+#define EPT_HOST_ARCH "x86_64"
+#else
+#define EPT_HOST_ARCH "other"
+#endif
+#ifndef EPT_DEVICE_ARCH
+#define EPT_DEVICE_ARCH unspecified
+#endif
+
 extern "C" {
 
 int ept_abi_version(void) { return EPT_ABI_VERSION; }
+
+const char *ept_build_info(void) {
+    return "libept abi " EPT_STR(EPT_ABI_VERSION) "; host " EPT_HOST_ARCH "; device " EPT_STR(EPT_DEVICE_ARCH)
+           "; nvcc " EPT_STR(__CUDACC_VER_MAJOR__) "." EPT_STR(__CUDACC_VER_MINOR__) "." EPT_STR(
+               __CUDACC_VER_BUILD__) "; built " __DATE__ " " __TIME__;
+}
 
 const char *ept_last_error(void) { return g_err.c_str(); }
 

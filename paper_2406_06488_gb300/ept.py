@@ -28,7 +28,7 @@ STATUS = {0: "EPT_OK", 1: "EPT_EINVAL", 2: "EPT_ENOMEM", 3: "EPT_EBUSY", 4: "EPT
           6: "EPT_ECANCELLED", 7: "EPT_ENOTFOUND", 8: "EPT_EUNSUPPORTED", 9: "EPT_EINTERNAL"}
 
 # every entry point declared in include/ept.h
-EXPORTS = ["ept_abi_version", "ept_last_error", "ept_create", "ept_destroy", "ept_estimate_bytes", "ept_test",
+EXPORTS = ["ept_abi_version", "ept_build_info", "ept_last_error", "ept_create", "ept_destroy", "ept_estimate_bytes", "ept_test",
            "ept_test_masks", "ept_perm_masks", "ept_build_blocks", "ept_test_static", "ept_test_batch",
            "ept_set_option", "ept_submit", "ept_poll", "ept_wait", "ept_cancel", "ept_test_range",
            "ept_serving_stats", "ept_create_ex", "ept_plan_check", "ept_serving_lanes"]
@@ -117,6 +117,8 @@ def load():
                            % (lib.ept_abi_version(), ABI_VERSION))
     lib.ept_last_error.argtypes = []
     lib.ept_last_error.restype = ctypes.c_char_p
+    lib.ept_build_info.argtypes = []
+    lib.ept_build_info.restype = ctypes.c_char_p
     lib.ept_create.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_size_t]
     lib.ept_create.restype = i32
     lib.ept_create_ex.argtypes = [ctypes.POINTER(vp), i32, ctypes.c_size_t, ctypes.POINTER(_Allocator)]
@@ -190,6 +192,11 @@ def _prec(prec) -> int:
     if isinstance(prec, str):
         return PREC[prec.lower()]
     return int(prec)
+
+
+def build_info() -> str:
+    """How the loaded library was built (ABI, host and GPU architecture, nvcc, date)."""
+    return load().ept_build_info().decode()
 
 
 def estimate_bytes(nx: int, ny: int, p: int, B: int, prec="split_bf16") -> int:

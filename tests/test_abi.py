@@ -64,6 +64,15 @@ def test_abi_version_and_errors_without_gpu(lib_path):
     assert ept.estimate_bytes(1 << 21, (1 << 21) + 1, 1, 1) == 0  # nx + ny beyond 2^22
 
 
+def test_build_info_names_this_machine(lib_path):
+    # the library is compiled where it runs: its host architecture is this machine's
+    import platform
+    from paper_2406_06488_gb300 import ept
+    info = ept.build_info()
+    assert "host %s;" % platform.machine() in info, info
+    assert "device sm_103a;" in info and "abi %d;" % ept.ABI_VERSION in info, info
+
+
 def test_destroy_null_is_ok(lib_path):
     from paper_2406_06488_gb300 import ept
     assert ept.load().ept_destroy(None) == 0
