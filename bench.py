@@ -485,7 +485,8 @@ def _tuning(res):
     code = int(res.tuning)
     return {"contraction": ["default", "relabelings in shared memory (N = 256)", "pairs of SMs (M = 256)",
                             "relabelings in tensor memory (N = 128)"][code // 10000],
-            "unit_kblocks": code // 100 % 100, "draw_kernel": ["auto", "warp per column", "thread per column"][code // 10 % 10],
+            "unit_kblocks": code // 100 % 100, "draw_kernel": ["auto", "warp per column", "thread per column",
+                                                             "rank producers + scanner"][code // 10 % 10],
             "unit_order": ["auto", "by length", "by first K-block"][code % 10],
             "candidates_timed": int(res.tune_candidates)}
 

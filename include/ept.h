@@ -118,7 +118,7 @@ typedef struct {
     int64_t tuning;       /* parameters of the tensor-core run: 10000 x contraction kernel
                              (0 the context's, 1..3 as EPT_OPT_CONTRACTION) + 100 x unit
                              length in K-blocks + 10 x relabeling-draw kernel (0 automatic,
-                             1 a warp per column, 2 a thread per column) + unit order (0
+                             1..3 as EPT_OPT_DRAW_MODE) + unit order (0
                              automatic, 1 by length, 2 by first K-block); 0 for other paths */
     int64_t tune_candidates; /* parameter sets the autotuner timed in this call (its first
                              call of a batch shape); 0 when the parameters came from its
@@ -288,8 +288,10 @@ ept_status ept_test_batch(ept_ctx *ctx, const ept_test_desc *tests, int64_t n_te
    statistics except for the accumulation order.
    EPT_OPT_DRAW_MODE (default 0): relabeling-draw kernel, 0 = automatic (a thread
    per column when the batch has at least 1024 columns per SM, else a warp per
-   column), 1 = a warp per column, 2 = a thread per column; the draws are
-   identical in every mode.
+   column), 1 = a warp per column, 2 = a thread per column, 3 = groups of 32
+   columns, eight warps computing the slots' ranks and one warp the sequential
+   decisions; the draws are identical in every mode (caller relabelings always
+   take 1).
    EPT_OPT_FAULT_INJECT_ALLOC (test hook, default 0): the next `value` acquisitions
    of device scratch (a run's arena, a serving batch's pool allocation) fail with
    EPT_ENOMEM on the host, without touching the GPU, to exercise error paths.

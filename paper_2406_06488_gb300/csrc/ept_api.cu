@@ -71,7 +71,7 @@ struct TestSpec {
 };
 
 // The tunable parameters of a run: contraction unit length in K-blocks, the
-// relabeling-draw kernel (0 automatic, DRAW_WARPS, DRAW_LANES) and the order of the
+// relabeling-draw kernel (0 automatic, DRAW_WARPS, DRAW_LANES, DRAW_SCAN) and the order of the
 // contraction schedule's units (0 automatic, 1 by length, 2 by first K-block, then
 // length).  Every choice computes the same statistics bit for bit except the unit
 // length, which changes the FP32 accumulation order (every length offered keeps the
@@ -608,7 +608,7 @@ struct ept_ctx {
     bool autotune = true;
     bool graphs = true;                 // replay captured graphs of repeated batches
     bool debug = false;                 // guard bands around scratch regions, plan invariants checked
-    int draw_mode = 0;                  // relabeling draws: 0 automatic, DRAW_WARPS, DRAW_LANES
+    int draw_mode = 0;                  // relabeling draws: 0 automatic, DRAW_WARPS, DRAW_LANES, DRAW_SCAN
     int64_t stream_blocks = 0;          // streaming mode: 0 automatic, k > 0 windows of <= k blocks, -1 never
     unsigned long long wait_ns = 0;     // limit of the kernels' bounded waits (0: their default, 2 s)
     int max_chunk = 32;                 // longest contraction unit the autotuner may pick
@@ -921,13 +921,14 @@ Batch device_view(ept_ctx *c, const Plan &P) {
 }
 
 // relabeling-draw kernel of a run: the context's choice, else a thread per column
-// when there are at least 1024 columns per SM; caller relabelings always take the
-// warp kernel (it validates them)
+// when there are at least 1024 columns per SM and a warp per column otherwise (the
+// producer / scanner kernel is an option: slower beside the block build, whose SMs
+// have no room left for its 32 KB of shared memory); caller relabelings always take
+// the warp kernel (it validates them)
 int draw_mode_for(const ept_ctx *c, const Plan &P) {
     int mode = P.draw_mode ? P.draw_mode : c->draw_mode;
     if (mode == 0)
-        mode = (!P.user_masks && P.ncols_pad >= DRAW_LANES_MIN_COLS_PER_SM * (int64_t)c->num_sms) ? DRAW_LANES
-                                                                                                  : DRAW_WARPS;
+        mode = P.ncols_pad >= DRAW_LANES_MIN_COLS_PER_SM * (int64_t)c->num_sms ? DRAW_LANES : DRAW_WARPS;
     return P.user_masks ? DRAW_WARPS : mode;
 }
 
@@ -1191,7 +1192,7 @@ void load_tune_file(ept_ctx *c) {
         tn.order = (int)head[2];
         tn.kernel = (int)head[3];
         const bool ok = (tn.chunk_kb == 4 || tn.chunk_kb == 8 || tn.chunk_kb == 16 || tn.chunk_kb == 32) &&
-                        tn.draw_mode >= 0 && tn.draw_mode <= 2 && tn.order >= 0 && tn.order <= 2 &&
+                        tn.draw_mode >= 0 && tn.draw_mode <= 3 && tn.order >= 0 && tn.order <= 2 &&
                         tn.kernel >= 0 && tn.kernel <= 3;
         if (ok) c->tuned[key] = tn;
     }
@@ -2784,7 +2785,7 @@ ept_status ept_set_option(ept_ctx *c, int option, int64_t value) {
         drop_graph(c);
         return EPT_OK;
     case EPT_OPT_DRAW_MODE:
-        if (value < 0 || value > 2) return fail(EPT_EINVAL, "draw mode must be 0, 1 or 2");
+        if (value < 0 || value > 3) return fail(EPT_EINVAL, "draw mode must be 0, 1, 2 or 3");
         c->draw_mode = (int)value;
         c->plan_key.clear();   // a captured graph holds the previous draw kernel
         drop_graph(c);

@@ -369,8 +369,10 @@ void launch_rowsum_reduce(const Batch &b, cudaStream_t s);
 void launch_center(const Batch &b, cudaStream_t s);
 void launch_pack(const Batch &b, bool split, cudaStream_t s);   // split: FP16 hi/lo (tensor-core path)
 // draw kernels: a warp per relabeling column (caller relabelings, or few columns),
-// or a thread per column (many columns: 32 warps per SM or more)
-enum { DRAW_WARPS = 1, DRAW_LANES = 2 };
+// a thread per column (many columns: 32 warps per SM or more), or (an option) groups
+// of 32 columns whose ranks eight producer warps compute and one scanner warp turns
+// into decisions
+enum { DRAW_WARPS = 1, DRAW_LANES = 2, DRAW_SCAN = 3 };
 constexpr int64_t DRAW_LANES_MIN_COLS_PER_SM = 32 * 32;
 void launch_masks(const Batch &b, int num_sms, int mode, cudaStream_t s);   // draws or caller masks
 void launch_contract_simt(const Batch &b, cudaStream_t s);

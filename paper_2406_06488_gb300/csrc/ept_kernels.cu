@@ -255,6 +255,102 @@ __global__ void __launch_bounds__(256) k_masks_lanes(const Batch bt) {
     }
 }
 
+// Relabeling columns in groups of 32 per CTA, with Algorithm S split into its two
+// parts: a slot's rank r_t = floor(u_t (n - t) / 2^64) depends only on the stream
+// (the same Philox words as draw_column), and only the decisions "keep slot t iff
+// r_t < need" depend on each other.  Eight producer warps compute the ranks of the
+// next 128 slots of all 32 columns into shared memory (two buffers) while one
+// scanner warp, a lane per column, runs the sequential decisions over the previous
+// 128 (a compare and a subtraction per slot) and writes each 32-slot word, the 32
+// lanes storing neighbouring columns of a word together.  No ballots, shuffles or
+// fixed-point rounds: about half the instructions per slot of the warp kernel, with
+// the columns' Philox work spread over eight times as many threads as the thread
+// kernel.  The identity (column 0) and padding columns are written by the scanner
+// lane; caller relabelings take the warp kernel.  A group never straddles two tests
+// (every test's column count Bp is a multiple of 32).
+constexpr int SCAN_SLOTS = 128;                    // slots per chunk
+constexpr int SCAN_PRODUCERS = 256;                // eight producer warps
+constexpr int SCAN_THREADS = SCAN_PRODUCERS + 32;  // and the scanner warp
+static_assert(COL_PAD % 32 == 0, "column groups of 32 stay inside one test");
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_masks_scan(const Batch bt) {
+    __shared__ uint32_t rank[2][SCAN_SLOTS][32];   // [buffer][slot in chunk][column in group]
+    const int64_t gc0 = (int64_t)blockIdx.x * 32;  // first batch column of the group
+    if (gc0 >= bt.ncols_total) return;             // uniform over the CTA, before any barrier
+    const int t = find_test(bt.pre.cols, bt.n_tests, gc0);
+    const TestDesc &d = bt.desc[t];
+    const int64_t c0 = gc0 - bt.pre.cols[t];       // first column of the group within the test
+    const int n = (int)d.n, nw = (int)d.nw;
+    const int nchunks = nw * 32 / SCAN_SLOTS;      // nw is a multiple of 8
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t c = c0 + lane;                   // this lane's column (producers and scanner)
+
+    // producer state: round keys and the draw of this thread's column
+    uint32_t kx[10], ky[10];
+    kx[0] = (uint32_t)d.seed;
+    ky[0] = (uint32_t)(d.seed >> 32);
+#pragma unroll
+    for (int r = 1; r < 10; ++r) {
+        kx[r] = kx[r - 1] + 0x9E3779B9u;
+        ky[r] = ky[r - 1] + 0xBB67AE85u;
+    }
+    const uint64_t bdraw = (uint64_t)(d.b0 + c - 1);   // column c >= 1 holds draw b0 + c - 1
+    const uint32_t blo = (uint32_t)bdraw, bhi = (uint32_t)(bdraw >> 32);
+    const bool drawn = c >= 1 && c < d.ncols;
+    // ranks of chunk k into buffer buf: this thread's column, slot pairs warp + 8 i
+    auto produce = [&](int k, int buf) {
+        if (!drawn) return;
+#pragma unroll 2
+        for (int i = 0; i < SCAN_SLOTS / 2 / 8; ++i) {
+            const int jp = warp + 8 * i;                 // slot pair within the chunk
+            const int ts = k * SCAN_SLOTS + 2 * jp;      // its first slot
+            uint64_t u0, u1;
+            philox_words((uint32_t)(ts >> 1), blo, bhi, kx, ky, u0, u1);
+            rank[buf][2 * jp][lane] = ts < n ? (uint32_t)mulhi_64x32(u0, (uint32_t)(n - ts)) : 0xFFFFFFFFu;
+            rank[buf][2 * jp + 1][lane] =
+                ts + 1 < n ? (uint32_t)mulhi_64x32(u1, (uint32_t)(n - ts - 1)) : 0xFFFFFFFFu;
+        }
+    };
+
+    // scanner state
+    uint32_t *col = bt.maskT + d.mask0 + c;
+    const int64_t Bp = d.Bp;
+    const bool comp = d.comp != 0;
+    uint32_t need = (uint32_t)d.nx;
+
+    if (warp < 8) produce(0, 0);
+    __syncthreads();
+    for (int k = 0; k < nchunks; ++k) {
+        if (warp == 8) {
+            const int buf = k & 1;
+#pragma unroll 1
+            for (int q = 0; q < SCAN_SLOTS / 32; ++q) {
+                const int w = k * (SCAN_SLOTS / 32) + q;   // output word
+                uint32_t bits;
+                if (drawn) {
+                    uint32_t r[32];
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) r[e] = rank[buf][q * 32 + e][lane];
+                    bits = 0;
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) {
+                        const uint32_t keep = r[e] < need ? 1u : 0u;
+                        bits |= keep << e;
+                        need -= keep;
+                    }
+                } else {
+                    bits = (c == 0) ? valid_bits(w, (int)d.nx) : 0u;   // identity, or padding
+                }
+                if (c < d.ncols) bits = comp ? (~bits & valid_bits(w, n)) : bits;
+                col[(int64_t)w * Bp] = bits;
+            }
+        } else if (k + 1 < nchunks) {
+            produce(k + 1, (k + 1) & 1);
+        }
+        __syncthreads();
+    }
+}
+
 // Blocks per SM of the draw kernel: MASK_CTAS_PER_SM, or the environment's
 // EPT_MASK_BLOCKS_PER_SM (0: one warp per column, no cap).
 static int mask_blocks_per_sm() {
@@ -269,6 +365,10 @@ static int mask_blocks_per_sm() {
 
 void launch_masks(const Batch &b, int num_sms, int mode, cudaStream_t s) {
     if (b.ncols_total <= 0) return;
+    if (mode == DRAW_SCAN) {
+        k_masks_scan<<<(unsigned)((b.ncols_total + 31) / 32), SCAN_THREADS, 0, s>>>(b);
+        return;
+    }
     if (mode == DRAW_LANES) {
         // few columns: small blocks, so that they spread over the SMs beside the build
         const int threads = (b.ncols_total >= 1024 * (int64_t)(num_sms > 0 ? num_sms : 1)) ? 256 : 64;

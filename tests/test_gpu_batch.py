@@ -153,31 +153,35 @@ def test_repeated_shape_follows_stat_sigma_seed(ctx):
 
 @pytest.mark.parametrize("prec", ["split_bf16", "plain_fp32"])
 def test_draw_modes_agree_and_match_oracle(ctx, prec):
-    # a thread per column and a warp per column must write the same relabelings
+    # a warp per column, a thread per column and the rank producers with a scanner
+    # warp must write the same relabelings
     tests = _uneven(10, seed=8, max_n=700, max_p=20, max_B=900)
     tests[0].update(B=0)
     res = {}
     try:
-        for mode in (1, 2):
+        for mode in (1, 2, 3):
             ctx.set_option("draw_mode", mode)
             res[mode] = ctx.test_batch(tests, prec=prec)
     finally:
         ctx.set_option("draw_mode", 0)
-    for a, b, t in zip(res[1], res[2], tests):
-        assert a.observed == b.observed and a.n_ge == b.n_ge
-        if t["B"] > 0:
-            assert np.array_equal(np.asarray(a.stats), np.asarray(b.stats))
+    for mode in (2, 3):
+        for a, b, t in zip(res[1], res[mode], tests):
+            assert a.observed == b.observed and a.n_ge == b.n_ge, mode
+            if t["B"] > 0:
+                assert np.array_equal(np.asarray(a.stats), np.asarray(b.stats)), mode
     small = _uneven(4, seed=9, max_n=100, max_p=8, max_B=150)
-    ctx.set_option("draw_mode", 2)
-    try:
-        got = ctx.test_batch(small, prec=prec)
-    finally:
-        ctx.set_option("draw_mode", 0)
-    for t, r in zip(small, got):
-        ref = oracle.permutation_test(t["X"], t["Y"], B=t["B"], seed=t["seed"], stat=t["stat"], sigma=t["sigma"])
-        assert abs(r.observed - ref["observed"]) <= REL_TOL * abs(ref["observed"])
-        if t["B"] > 0:
-            assert _close(r.stats, ref["stats"])
+    for mode in (2, 3):
+        ctx.set_option("draw_mode", mode)
+        try:
+            got = ctx.test_batch(small, prec=prec)
+        finally:
+            ctx.set_option("draw_mode", 0)
+        for t, r in zip(small, got):
+            ref = oracle.permutation_test(t["X"], t["Y"], B=t["B"], seed=t["seed"], stat=t["stat"],
+                                          sigma=t["sigma"])
+            assert abs(r.observed - ref["observed"]) <= REL_TOL * abs(ref["observed"])
+            if t["B"] > 0:
+                assert _close(r.stats, ref["stats"])
 
 
 def test_page_locked_host_inputs(ctx):
