@@ -64,6 +64,22 @@ def test_abi_version_and_errors_without_gpu(lib_path):
     assert ept.estimate_bytes(1 << 21, (1 << 21) + 1, 1, 1) == 0  # nx + ny beyond 2^22
 
 
+def test_option_tables_agree():
+    # the header's option numbers, the binding's option names and the environment
+    # variables that give their starting values (every option but the test hooks)
+    from paper_2406_06488_gb300 import ept
+    hdr = open(os.path.join(ROOT, "include", "ept.h")).read()
+    declared = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"EPT_OPT_([A-Z_]+) = (\d+)", hdr)}
+    assert declared == ept.OPTION
+    src = open(os.path.join(ROOT, "paper_2406_06488_gb300", "csrc", "ept_api.cu")).read()
+    env = dict(re.findall(r'\{"EPT_([A-Z_]+)", EPT_OPT_([A-Z_]+)\}', src))
+    assert all(k == v for k, v in env.items())
+    hooks = {"fault_inject_alloc", "fault_inject_stall"}
+    assert {k.lower() for k in env} == set(declared) - hooks
+    for k in env:   # and the header's list of environment variables names each one
+        assert "EPT_" + k in hdr
+
+
 def test_build_info_names_this_machine(lib_path):
     # the library is compiled where it runs: its host architecture is this machine's
     import platform
