@@ -46,3 +46,22 @@ def test_direct_baseline_counts_what_it_timed():
     r, vals = bench._cpu_baseline(spec, X, Y, budget_s=5.0)
     assert r["kind"] == "oracle" and r["value"] > 0
     assert len(vals) == 64 and all(np.isfinite(vals))
+
+
+def test_tuning_code_decodes_every_choice():
+    # ept_result.tuning = 10000 kernel + 100 unit + 10 draw kernel + order (include/ept.h)
+    class R:
+        tune_candidates = 8
+
+    for kernel in range(4):
+        for unit in (0, 4, 8, 16, 32):
+            for draw in range(4):
+                for order in range(3):
+                    R.tuning = 10000 * kernel + 100 * unit + 10 * draw + order
+                    t = bench._tuning(R)
+                    assert t["unit_kblocks"] == unit and t["candidates_timed"] == 8
+                    assert t["contraction"] and t["draw_kernel"] and t["unit_order"]
+    R.tuning = 10000 * 2 + 100 * 16 + 10 * 3 + 2
+    t = bench._tuning(R)
+    assert t["contraction"].startswith("pairs of SMs") and t["draw_kernel"].startswith("rank producers")
+    assert t["unit_order"] == "by first K-block"
