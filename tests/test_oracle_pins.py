@@ -380,3 +380,22 @@ def test_median_pairs_matches_library_routine_and_ignores_the_split():
     W = W[perm]
     assert oracle.median_pairs(W[:10], W[10:]) == oracle.median_pairs(X, Y)
     assert oracle.median_pairs(Y, X) == oracle.median_pairs(X, Y)
+
+
+def test_mask_packing_bit_order():
+    # pooled row t is bit t % 32 of word t // 32 (the layout the library's relabeling
+    # words use); unpacking inverts it, padding bits stay zero
+    n = 70
+    for t in (0, 1, 31, 32, 33, 63, 64, 69):
+        sel = np.zeros((1, n), dtype=bool)
+        sel[0, t] = True
+        words = oracle.pack_masks(sel)
+        assert words.shape == (1, 3) and words.dtype == np.uint32
+        want = np.zeros(3, dtype=np.uint32)
+        want[t // 32] = np.uint32(1) << np.uint32(t % 32)
+        assert np.array_equal(words[0], want), t
+    rng = np.random.default_rng(5)
+    sel = rng.random((9, n)) < 0.4
+    words = oracle.pack_masks(sel)
+    assert np.array_equal(oracle.unpack_masks(words, n), sel)
+    assert not (words[:, 2] >> np.uint32(n - 64)).any()   # rows 70..95 do not exist
